@@ -1,0 +1,186 @@
+"""ctypes wrapper of the FP64 CPU oracle (``mbr_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, by ``__graft_entry__.smoke()`` and by the
+benchmark's CPU-baseline / reference leg.  The CUDA product path never imports it, and it imports
+nothing from the product package (only the seeded scene dictionaries produced by ``scenes``).
+
+Modes (see mbr_oracle.h):
+  ``exact``  -- PLAIN_EXACT: exact motion + projection at every sub-frame, direct solve per sample
+                (the per-sub-frame barycentric baseline of Sec. 3.1);
+  ``linear`` -- PLAIN_LINEAR: keyframe-lerped screen positions (Sec. 3.2), direct solve per sample;
+  ``fast``   -- FAST_REF: PLAIN_LINEAR with the keyframe closest-point approximation of
+                Eqs. euc-dist-approx-2/3 for background samples (what the fast solver computes).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int32, c_int64, c_uint8
+
+import numpy as np
+
+from .build import build, library_path
+
+MODES = {"exact": 0, "linear": 1, "fast": 2}
+SOFT_ALL = 1
+CNT_CAND, CNT_COVERED, CNT_AMBIG, CNT_HASH, CNT_SOFT = 0, 1, 2, 3, 4
+AMB_COVER, AMB_DEPTH, AMB_DEGEN, AMB_REGION = 1, 2, 4, 8
+
+
+class OrcScene(ctypes.Structure):
+    _fields_ = [
+        ("V", c_int32), ("F", c_int32),
+        ("verts", POINTER(c_double)), ("faces", POINTER(c_int32)), ("albedo", POINTER(c_double)),
+        ("motion_kind", c_int32), ("segments", c_int32),
+        ("offset", c_double * 3), ("dir", c_double * 3), ("axis", c_double * 3), ("omega", c_double),
+        ("view", c_double * 12), ("tan_half_fov", c_double), ("znear", c_double),
+        ("light_dir", c_double * 3), ("k_ambient", c_double), ("k_diffuse", c_double),
+        ("delta", c_double), ("time_rule", c_int32), ("T", c_int32), ("H", c_int32), ("W", c_int32),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            build()
+        L = ctypes.CDLL(path)
+        P = ctypes.POINTER
+        L.orc_num_segments.argtypes = [P(OrcScene)]
+        L.orc_num_segments.restype = c_int32
+        L.orc_sample_time.argtypes = [P(OrcScene), c_int32, P(c_int32), P(c_double), P(c_double)]
+        L.orc_vertex_normals.argtypes = [P(OrcScene), P(c_double)]
+        L.orc_vertex_state.argtypes = [P(OrcScene), P(c_double), c_double, P(c_double)]
+        L.orc_barycentric.argtypes = [P(c_double), c_double, c_double, P(c_double)]
+        L.orc_barycentric.restype = c_double
+        L.orc_closest_point.argtypes = [P(c_double), c_double, c_double, P(c_double), P(c_int32)]
+        L.orc_closest_point.restype = c_double
+        L.orc_render.argtypes = [P(OrcScene), c_int32, c_int32, c_int32, c_int32, c_int32, c_int32,
+                                 P(c_double), P(c_int32), P(c_uint8), P(c_int64)]
+        L.orc_render.restype = c_int32
+        L.orc_render_backward.argtypes = [P(OrcScene), c_int32, c_int32, c_int32, c_int32, c_int32,
+                                          c_int32, P(c_double), P(c_double), P(c_double), P(c_int64)]
+        L.orc_render_backward.restype = c_int32
+        _lib = L
+    return _lib
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(POINTER(ctype)) if a is not None else None
+
+
+class _Scene:
+    """Keeps the numpy buffers alive for the lifetime of the ctypes struct."""
+
+    def __init__(self, sc):
+        self.verts = np.ascontiguousarray(sc["verts"], dtype=np.float64)
+        self.faces = np.ascontiguousarray(sc["faces"], dtype=np.int32)
+        self.albedo = np.ascontiguousarray(sc["albedo"], dtype=np.float64)
+        m, c = sc["motion"], sc["camera"]
+        s = OrcScene()
+        s.V, s.F = len(self.verts), len(self.faces)
+        s.verts = _ptr(self.verts, c_double)
+        s.faces = _ptr(self.faces, c_int32)
+        s.albedo = _ptr(self.albedo, c_double)
+        s.motion_kind = 0 if m["kind"] == "translate" else 1
+        s.segments = int(m.get("segments", 0))
+        s.offset[:] = [float(x) for x in m["offset"]]
+        s.dir[:] = [float(x) for x in m["dir"]]
+        s.axis[:] = [float(x) for x in m["axis"]]
+        s.omega = float(m["omega"])
+        s.view[:] = [float(x) for x in np.asarray(c["view"]).reshape(-1)]
+        s.tan_half_fov = float(c["tan_half_fov"])
+        s.znear = float(c["znear"])
+        s.light_dir[:] = [float(x) for x in c["light_dir"]]
+        s.k_ambient = float(c["k_ambient"])
+        s.k_diffuse = float(c["k_diffuse"])
+        s.delta = float(c["delta"])
+        s.time_rule = 0 if c.get("time_rule", "paper") == "paper" else 1
+        s.T, s.H, s.W = int(sc["T"]), int(sc["H"]), int(sc["W"])
+        self.s = s
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.s)
+
+
+def num_segments(sc):
+    return lib().orc_num_segments(_Scene(sc).ref)
+
+
+def sample_time(sc, k):
+    seg, t, tau = c_int32(), c_double(), c_double()
+    lib().orc_sample_time(_Scene(sc).ref, int(k), ctypes.byref(seg), ctypes.byref(t), ctypes.byref(tau))
+    return seg.value, t.value, tau.value
+
+
+def vertex_normals(sc):
+    S = _Scene(sc)
+    out = np.zeros((S.s.V, 3))
+    lib().orc_vertex_normals(S.ref, _ptr(out, c_double))
+    return out
+
+
+def vertex_state(sc, t):
+    """[V,6]: ndc x, ndc y, camera z, world normal (x, y, z) at time t (exact motion)."""
+    S = _Scene(sc)
+    n = vertex_normals(sc)
+    out = np.zeros((S.s.V, 6))
+    lib().orc_vertex_state(S.ref, _ptr(n, c_double), float(t), _ptr(out, c_double))
+    return out
+
+
+def barycentric(tri, u, v):
+    tri = np.ascontiguousarray(tri, dtype=np.float64).reshape(6)
+    w = np.zeros(3)
+    det = lib().orc_barycentric(_ptr(tri, c_double), float(u), float(v), _ptr(w, c_double))
+    return w, det
+
+
+def closest_point(tri, px, py):
+    tri = np.ascontiguousarray(tri, dtype=np.float64).reshape(6)
+    w = np.zeros(3)
+    reg = c_int32()
+    d2 = lib().orc_closest_point(_ptr(tri, c_double), float(px), float(py), _ptr(w, c_double),
+                                 ctypes.byref(reg))
+    return d2, w, reg.value
+
+
+def render(sc, mode="fast", window=None, soft_all=False, winners=False, ambig=False):
+    """Blurred RGBA image of ``sc`` (or of ``window`` = (x0, y0, w, h)).
+
+    Returns dict(rgba [h,w,4] f64, winners [T,h,w] i32 | None, ambig [T,h,w] u8 | None,
+    counters [8] i64)."""
+    S = _Scene(sc)
+    x0, y0, w, h = window if window is not None else (0, 0, S.s.W, S.s.H)
+    T = S.s.T
+    rgba = np.zeros((h, w, 4))
+    win = np.zeros((T, h, w), dtype=np.int32) if winners else None
+    amb = np.zeros((T, h, w), dtype=np.uint8) if ambig else None
+    cnt = np.zeros(8, dtype=np.int64)
+    rc = lib().orc_render(S.ref, MODES[mode], SOFT_ALL if soft_all else 0, x0, y0, w, h,
+                          _ptr(rgba, c_double), _ptr(win, c_int32), _ptr(amb, c_uint8),
+                          _ptr(cnt, c_int64))
+    if rc != 0:
+        raise RuntimeError(f"orc_render failed ({rc})")
+    return dict(rgba=rgba, winners=win, ambig=amb, counters=cnt)
+
+
+def render_backward(sc, dl_drgba, mode="fast", window=None, soft_all=False):
+    """(dL/dverts [V,3], dL/dalbedo [V,3], counters) for the loss gradient ``dl_drgba`` [h,w,4]."""
+    S = _Scene(sc)
+    x0, y0, w, h = window if window is not None else (0, 0, S.s.W, S.s.H)
+    g = np.ascontiguousarray(dl_drgba, dtype=np.float64).reshape(h, w, 4)
+    gv = np.zeros((S.s.V, 3))
+    ga = np.zeros((S.s.V, 3))
+    cnt = np.zeros(8, dtype=np.int64)
+    rc = lib().orc_render_backward(S.ref, MODES[mode], SOFT_ALL if soft_all else 0, x0, y0, w, h,
+                                   _ptr(g, c_double), _ptr(gv, c_double), _ptr(ga, c_double),
+                                   _ptr(cnt, c_int64))
+    if rc != 0:
+        raise RuntimeError(f"orc_render_backward failed ({rc})")
+    return gv, ga, cnt

@@ -1,0 +1,89 @@
+/*
+ * mbr_oracle.h -- FP64, single-threaded CPU oracle of the motion-blurred differentiable mesh
+ * renderer in "Recovering 3D Shapes from Ultra-Fast Motion-Blurred Images" (arXiv 2602.07860).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the package smoke check and the benchmark's
+ * CPU-baseline leg may load this library.  It shares no code, header, table or helper with the
+ * CUDA path and includes nothing from it.
+ *
+ * The oracle evaluates the plain definitions: per sub-frame it places every vertex (exact motion,
+ * or the keyframe lerp of Sec. 3.2), solves F(t) w = p by Gaussian elimination (Eq. barycentric),
+ * z-tests the covering triangles (Sec. 3.1), shades the winner (Eq. fore + Lambert), and for
+ * uncovered samples aggregates exp(-d/delta) soft coverage (Eqs. probability-function and back)
+ * with d the exact squared distance (plain modes) or the keyframe approximation of
+ * Eqs. euc-dist-approx-2/3 (fast mode).  Sub-frame results are averaged (Sec. 3.3).
+ *
+ * Parity unpinned: the paper's own images, gradients and timings (figures stripped).
+ */
+#ifndef MBR_ORACLE_H
+#define MBR_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int32_t V, F;
+  const double* verts;    /* [V,3] base vertex positions (world)                         */
+  const int32_t* faces;   /* [F,3] vertex indices                                          */
+  const double* albedo;   /* [V,3] per-vertex colour                                       */
+  int32_t motion_kind;    /* 0: P(t) = v + offset + t*dir ; 1: P(t) = R(omega*t, axis) v   */
+  int32_t segments;       /* linear segments of the fast solver; 0 = default rule          */
+  double offset[3], dir[3], axis[3], omega;
+  double view[12];        /* 3x4 world->camera, camera +z forward                          */
+  double tan_half_fov, znear;
+  double light_dir[3];    /* direction towards the light, world space (normalised here)    */
+  double k_ambient, k_diffuse, delta;
+  int32_t time_rule;      /* 0: t_k = k/(T-1) (T=1: 0.5) ; 1: t_k = (k+0.5)/T             */
+  int32_t T, H, W;
+} orc_scene;
+
+enum { ORC_PLAIN_EXACT = 0, ORC_PLAIN_LINEAR = 1, ORC_FAST_REF = 2 };
+enum { ORC_SOFT_ALL = 1 };  /* flag: no soft-coverage truncation, every triangle at every pixel */
+
+/* counters[] written by orc_render / orc_render_backward */
+enum {
+  ORC_CNT_CAND = 0,       /* (pixel, sample, triangle) triples inside the dilated bbox            */
+  ORC_CNT_COVERED = 1,    /* covered samples                                                      */
+  ORC_CNT_AMBIG = 2,      /* samples flagged ambiguous for FP32 comparison                        */
+  ORC_CNT_HASH = 3,       /* 64-bit hash of every discrete decision                               */
+  ORC_CNT_SOFT = 4,       /* soft-coverage terms that entered a product                          */
+  ORC_CNT_N = 8
+};
+
+int32_t orc_num_segments(const orc_scene* s);
+/* sub-frame k -> time t, segment index and local time tau inside the segment */
+void orc_sample_time(const orc_scene* s, int32_t k, int32_t* seg, double* t, double* tau);
+/* area-weighted vertex normals of the base mesh, [V,3] */
+void orc_vertex_normals(const orc_scene* s, double* normals);
+/* exact per-vertex state at time t: [V,6] = ndc x, ndc y, camera z, world normal xyz */
+void orc_vertex_state(const orc_scene* s, const double* normals, double t, double* state);
+/* w = F^-1 p by Gaussian elimination with partial pivoting; returns det F */
+double orc_barycentric(const double tri[6], double u, double v, double w[3]);
+/* closest point of triangle tri (x0,y0,x1,y1,x2,y2) to (px,py) by the three clamped edge
+ * projections of the appendix; returns the squared distance, its barycentrics in w[3] and a
+ * region code (0..2: interior of edge (0,1), (1,2), (2,0); 3 + i: vertex i) */
+double orc_closest_point(const double tri[6], double px, double py, double w[3], int32_t* region);
+
+/* Render the window [x0, x0+w) x [y0, y0+h) of the H x W image.
+ *   rgba     [h*w*4]   blurred RGBA, row-major, pixel (0,0) at the window's top-left
+ *   winners  [T*h*w]   per-sample z-test winner (face id) or -1; may be NULL
+ *   ambig    [T*h*w]   per-sample ambiguity flags (bitmask); may be NULL
+ *   counters [ORC_CNT_N]
+ * returns 0, or -1 on bad arguments / allocation failure. */
+int32_t orc_render(const orc_scene* s, int32_t mode, int32_t flags, int32_t x0, int32_t y0,
+                   int32_t w, int32_t h, double* rgba, int32_t* winners, uint8_t* ambig,
+                   int64_t* counters);
+
+/* Reverse mode of orc_render over the same window: given dL/drgba [h*w*4], writes
+ * dL/dverts [V,3] and (if non-NULL) dL/dalbedo [V,3].  Discrete choices (coverage, winner,
+ * closest-point region, Lambert clamp, truncation) are held fixed. */
+int32_t orc_render_backward(const orc_scene* s, int32_t mode, int32_t flags, int32_t x0,
+                            int32_t y0, int32_t w, int32_t h, const double* dl_drgba,
+                            double* dl_dverts, double* dl_dalbedo, int64_t* counters);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,75 @@
+"""The oracle's hand-derived FP64 adjoint against central finite differences of its own forward
+(h = 1e-6), skipping coordinates where the +-h renders change any discrete choice (the oracle's
+decision hash), plus rigid-shift and albedo-linearity checks."""
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+
+def _loss(sc, G, mode, **kw):
+    r = oracle.render(sc, mode, **kw)
+    return float(np.sum(r["rgba"] * G)), int(r["counters"][oracle.CNT_HASH])
+
+
+def _scene(kind, delta):
+    sc = scenes.small_scene(kind, subdiv=1, T=4, H=22, W=26, lmax=3, sigma=0.08, d=(0.9, 0.2, 0.4))
+    sc["camera"] = dict(sc["camera"], delta=delta)
+    return sc
+
+
+@pytest.mark.parametrize("mode", ["exact", "linear", "fast"])
+@pytest.mark.parametrize("kind", ["rotate", "translate"])
+@pytest.mark.parametrize("delta", [1e-4, 2e-3])
+def test_adjoint_matches_central_differences(mode, kind, delta):
+    sc = _scene(kind, delta)
+    rng = np.random.default_rng(17)
+    G = rng.normal(size=(sc["H"], sc["W"], 4))
+    gv, ga, _ = oracle.render_backward(sc, G, mode)
+    _, h0 = _loss(sc, G, mode)
+    h = 1e-6
+    V = len(sc["verts"])
+    coords = [(int(v), int(c)) for v, c in zip(rng.integers(0, V, 40), rng.integers(0, 3, 40))]
+    checked = 0
+    scale = np.max(np.abs(gv))
+    for v, c in coords:
+        plus = dict(sc, verts=sc["verts"].copy())
+        minus = dict(sc, verts=sc["verts"].copy())
+        plus["verts"][v, c] += h
+        minus["verts"][v, c] -= h
+        lp, hp = _loss(plus, G, mode)
+        lm, hm = _loss(minus, G, mode)
+        if hp != h0 or hm != h0:
+            continue  # a discrete choice changed inside [-h, h]
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - gv[v, c]) <= 1e-5 * abs(fd) + 1e-7 * scale + 1e-9, (v, c, fd, gv[v, c])
+        checked += 1
+    assert checked >= 25
+    # albedo enters linearly: dL/dalbedo is exact
+    for v, c in coords[:10]:
+        plus = dict(sc, albedo=sc["albedo"].copy())
+        plus["albedo"][v, c] += 1.0
+        lp, _ = _loss(plus, G, mode)
+        l0, _ = _loss(sc, G, mode)
+        assert abs((lp - l0) - ga[v, c]) < 1e-9 * max(1.0, abs(ga[v, c]))
+
+
+@pytest.mark.parametrize("mode", ["exact", "fast"])
+def test_rigid_shift_gradient_sums(mode):
+    """Moving every vertex by the same small offset c: dL/dc = sum_v dL/dv (normals unchanged)."""
+    sc = _scene("translate", 2e-3)
+    rng = np.random.default_rng(23)
+    G = rng.normal(size=(sc["H"], sc["W"], 4))
+    gv, _, _ = oracle.render_backward(sc, G, mode)
+    h = 1e-7
+    for axis in range(3):
+        e = np.zeros(3)
+        e[axis] = h
+        lp, hp = _loss(dict(sc, verts=sc["verts"] + e), G, mode)
+        lm, hm = _loss(dict(sc, verts=sc["verts"] - e), G, mode)
+        _, h0 = _loss(sc, G, mode)
+        if hp != h0 or hm != h0:
+            continue
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - gv[:, axis].sum()) <= 1e-5 * abs(fd) + 1e-6 * np.abs(gv).max()

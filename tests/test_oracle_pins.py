@@ -1,0 +1,450 @@
+"""Pins of the FP64 oracle against things other than itself: the paper's printed appendix
+coefficients (symbolic identity), closed forms, invariants, special cases and brute force.
+
+Every test here runs on the CPU (no GPU marker)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "appendix_A_coefficients.txt")
+
+
+def _golden_exprs():
+    import sympy as sp
+    out = {}
+    with open(GOLDEN) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            name, expr = line.split("=", 1)
+            out[name.strip()] = sp.sympify(expr)
+    return out
+
+
+# ----------------------------------------------------------------------------- Appendix A
+
+def test_appendix_coefficients_equal_adjugate_expansion():
+    """Appendix A: adj(F(t)) p and det F(t) with linearly moving vertices expand to exactly the
+    printed A_1..A_3 and a_1..a_3 (symbolic identity, all components)."""
+    sp = pytest.importorskip("sympy")
+    g = _golden_exprs()
+    t, u, v = sp.symbols("t u v")
+    xs = {(i, T): sp.Symbol(f"x{i}{T}") for i in range(3) for T in range(2)}
+    ys = {(i, T): sp.Symbol(f"y{i}{T}") for i in range(3) for T in range(2)}
+    x = [(1 - t) * xs[(i, 0)] + t * xs[(i, 1)] for i in range(3)]
+    y = [(1 - t) * ys[(i, 0)] + t * ys[(i, 1)] for i in range(3)]
+    F = sp.Matrix([[x[0], x[1], x[2]], [y[0], y[1], y[2]], [1, 1, 1]])
+    num = F.adjugate() * sp.Matrix([u, v, 1])
+    det = sp.expand(F.det())
+    for i in range(3):
+        poly = sp.Poly(sp.expand(num[i]), t)
+        assert sp.expand(poly.coeff_monomial(t ** 2) - g[f"A1_{i}"]) == 0
+        assert sp.expand(poly.coeff_monomial(t) - g[f"A2_{i}"]) == 0
+        assert sp.expand(poly.coeff_monomial(1) - g[f"A3_{i}"]) == 0
+    dp = sp.Poly(det, t)
+    assert sp.expand(dp.coeff_monomial(t ** 2) - g["a1"]) == 0
+    assert sp.expand(dp.coeff_monomial(t) - g["a2"]) == 0
+    assert sp.expand(dp.coeff_monomial(1) - g["a3"]) == 0
+    # the numerators sum to the denominator: barycentrics sum to one at every t
+    for p, q in (("A1", "a1"), ("A2", "a2"), ("A3", "a3")):
+        assert sp.expand(g[f"{p}_0"] + g[f"{p}_1"] + g[f"{p}_2"] - g[q]) == 0
+
+
+def test_oracle_barycentric_matches_printed_quadratic_rational():
+    """The oracle's Gaussian-elimination solve of F(t) w = p equals Eq. time-dependent2 evaluated
+    with the printed coefficients, on random moving triangles and times."""
+    sp = pytest.importorskip("sympy")
+    g = _golden_exprs()
+    names = sorted({s.name for e in g.values() for s in e.free_symbols})
+    fns = {k: sp.lambdify([sp.Symbol(n) for n in names], e, "numpy") for k, e in g.items()}
+    rng = np.random.default_rng(7)
+    worst = 0.0
+    for _ in range(2000):
+        k0 = rng.uniform(-1, 1, 6)
+        k1 = k0 + rng.uniform(-0.5, 0.5, 6)
+        u, v = rng.uniform(-1, 1, 2)
+        t = rng.uniform(0, 1)
+        env = {f"x{i}0": k0[2 * i] for i in range(3)}
+        env.update({f"y{i}0": k0[2 * i + 1] for i in range(3)})
+        env.update({f"x{i}1": k1[2 * i] for i in range(3)})
+        env.update({f"y{i}1": k1[2 * i + 1] for i in range(3)})
+        env.update(u=u, v=v)
+        args = [env[n] for n in names]
+        den = fns["a1"](*args) * t * t + fns["a2"](*args) * t + fns["a3"](*args)
+        w_q = np.array([(fns[f"A1_{i}"](*args) * t * t + fns[f"A2_{i}"](*args) * t + fns[f"A3_{i}"](*args)) / den
+                        for i in range(3)])
+        tri = (1 - t) * k0 + t * k1
+        w_o, det = oracle.barycentric(tri, u, v)
+        if abs(det) < 1e-3:
+            continue
+        worst = max(worst, np.max(np.abs(w_o - w_q)) / max(1.0, np.max(np.abs(w_q))))
+    assert worst < 1e-9
+
+
+def test_barycentric_invariants():
+    """Sec. 3.1: sum_i w_i = 1 and sum_i w_i v_i = p (reproduces the pixel)."""
+    rng = np.random.default_rng(3)
+    for _ in range(2000):
+        tri = rng.uniform(-1, 1, 6)
+        u, v = rng.uniform(-1.5, 1.5, 2)
+        w, det = oracle.barycentric(tri, u, v)
+        if abs(det) < 1e-3:
+            continue
+        assert abs(w.sum() - 1.0) < 1e-12
+        assert abs(w @ tri[0::2] - u) < 1e-12 and abs(w @ tri[1::2] - v) < 1e-12
+        assert abs(det - np.linalg.det(np.array([tri[0::2], tri[1::2], [1, 1, 1]]))) < 1e-12
+
+
+# ----------------------------------------------------------------------------- closest point
+
+def _segment_min_dense(a, b, p, n=200001):
+    t = np.linspace(0.0, 1.0, n)
+    q = a[None, :] + t[:, None] * (b - a)[None, :]
+    d = np.sum((q - p[None, :]) ** 2, axis=1)
+    return d.min()
+
+
+def test_closest_point_matches_dense_boundary_sampling():
+    """Appendix (Euclidean distance approximation): for points outside the triangle the three
+    clamped edge projections give the exact squared distance; checked against dense sampling of
+    the boundary (2e5 points per edge; sampling error <= (edge/2e5)^2 / 4)."""
+    rng = np.random.default_rng(11)
+    checked = 0
+    while checked < 60:
+        tri = rng.uniform(-1, 1, 6)
+        p = rng.uniform(-1.5, 1.5, 2)
+        w, det = oracle.barycentric(tri, *p)
+        if abs(det) < 1e-2 or np.all(w >= 0):
+            continue
+        d2, wstar, region = oracle.closest_point(tri, *p)
+        V = tri.reshape(3, 2)
+        dense = min(_segment_min_dense(V[i], V[(i + 1) % 3], p) for i in range(3))
+        assert abs(d2 - dense) < 1e-9
+        assert abs(wstar.sum() - 1.0) < 1e-15 and np.all(wstar >= 0)
+        q = wstar @ V
+        assert abs(np.sum((q - p) ** 2) - d2) < 1e-12
+        checked += 1
+
+
+# ----------------------------------------------------------------------------- normals / motion / camera
+
+def test_vertex_normals_octahedron_closed_form():
+    """Area-weighted vertex normals: on a regular octahedron every vertex normal is the vertex
+    direction exactly (by symmetry of the four incident faces)."""
+    v = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], float)
+    f = np.array([[0, 2, 4], [2, 1, 4], [1, 3, 4], [3, 0, 4], [2, 0, 5], [1, 2, 5], [3, 1, 5], [0, 3, 5]],
+                 dtype=np.int32)
+    sc = scenes.scene(v, f, np.full_like(v, 0.5), scenes.translate((0, 0, 0)),
+                      scenes.camera(scenes.look_at((0, 0, -4))), 1, 8, 8)
+    n = oracle.vertex_normals(sc)
+    assert np.allclose(n, v, atol=1e-15)
+
+
+def test_camera_optical_axis_and_fov_edge():
+    """Camera (scene settings): a point on the optical axis projects to (0, 0); a point at the
+    half-FOV angle projects to ndc 1; camera z is the distance along the view direction."""
+    th = math.tan(math.radians(20))
+    pts = np.array([[0, 0, 0], [4 * th, 0, 0], [0, -4 * th, 0], [2 * th * 3, 0, 2.0]], float)
+    f = np.array([[0, 1, 2]], dtype=np.int32)
+    sc = scenes.scene(pts, np.array([[0, 1, 2], [1, 2, 3]], dtype=np.int32), np.full_like(pts, 0.5),
+                      scenes.translate((0, 0, 0)), scenes.camera(scenes.look_at((0, 0, -4))), 1, 8, 8)
+    st = oracle.vertex_state(sc, 0.0)
+    assert np.allclose(st[0, :3], [0, 0, 4])
+    assert np.allclose(st[1, :3], [1, 0, 4])
+    assert np.allclose(st[2, :3], [0, -1, 4])
+    assert np.allclose(st[3, :3], [1, 0, 6])
+    del f
+
+
+def test_motion_translation_and_rotation():
+    """Motion parameters: translation moves v to v + o + t d; rotation about +y by a quarter turn
+    maps +x to -z (right-handed, matching the parabolic-motion formula), a full turn is the
+    identity, and the axis itself is fixed."""
+    v = np.array([[1.0, 0, 0], [0, 1.0, 0], [0, 0, 1.0]])
+    f = np.array([[0, 1, 2]], dtype=np.int32)
+    cam = scenes.camera(scenes.look_at((0, 0, -4)))
+    th = cam["tan_half_fov"]
+    sc = scenes.scene(v, f, np.full_like(v, 0.5), scenes.rotate((0, 1, 0), 2 * math.pi), cam, 1, 8, 8)
+    s0, s1, sq = oracle.vertex_state(sc, 0.0), oracle.vertex_state(sc, 1.0), oracle.vertex_state(sc, 0.25)
+    assert np.allclose(s0, s1, atol=1e-12)
+    # +x rotated a quarter turn about +y lands at -z: ndc (0, 0), camera z = 4 - 1
+    assert np.allclose(sq[0, :3], [0, 0, 3.0], atol=1e-12)
+    assert np.allclose(sq[1, :3], s0[1, :3], atol=1e-12)  # on the axis
+    # +z lands at +x: x_c = 1, z_c = 4
+    assert np.allclose(sq[2, :3], [1 / (4 * th), 0, 4.0], atol=1e-12)
+    sct = scenes.scene(v, f, np.full_like(v, 0.5), scenes.translate((0.8, 0.0, 0.0)), cam, 1, 8, 8)
+    a, b = oracle.vertex_state(sct, 0.0), oracle.vertex_state(sct, 1.0)
+    # v + o (o = -d/2) and v + o + d: screen x differs by d / (z tan)
+    assert np.allclose(b[:, 0] - a[:, 0], 0.8 / (a[:, 2] * th))
+    assert np.allclose(a[0, 0], (1 - 0.4) / (4 * th))
+
+
+def test_sample_times_and_segments():
+    """Sec. 3.2: t_k = k/(K-1) with both endpoints; Sec. 3.3: 12 segments per turn, t = (s+tau)/S."""
+    sc = scenes.small_scene("rotate", T=64)
+    assert oracle.num_segments(sc) == 12
+    ts = [oracle.sample_time(sc, k) for k in range(64)]
+    for k, (s, t, tau) in enumerate(ts):
+        assert abs(t - k / 63) < 1e-15
+        assert 0 <= s < 12 and 0.0 <= tau <= 1.0
+        assert abs((s + tau) / 12 - t) < 1e-14
+    assert ts[-1][0] == 11 and ts[-1][2] == 1.0
+    one = dict(sc, T=1)
+    assert oracle.sample_time(one, 0)[1] == 0.5
+    mid = dict(sc, camera=dict(sc["camera"], time_rule="midpoint"))
+    assert abs(oracle.sample_time(mid, 0)[1] - 0.5 / 64) < 1e-15
+    tr = scenes.small_scene("translate")
+    assert oracle.num_segments(tr) == 1
+    assert oracle.num_segments(dict(sc, motion=dict(sc["motion"], omega=16 * math.pi))) == 96
+
+
+# ----------------------------------------------------------------------------- special cases
+
+def _static_copy(sc, t):
+    """The scene with the motion at time t baked into the base vertices and no motion left."""
+    m = sc["motion"]
+    v = sc["verts"]
+    if m["kind"] == "translate":
+        v = v + m["offset"] + t * m["dir"]
+    else:
+        k = np.asarray(m["axis"], float) / np.linalg.norm(m["axis"])
+        th = m["omega"] * t
+        K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+        R = np.eye(3) + math.sin(th) * K + (1 - math.cos(th)) * K @ K
+        v = v @ R.T
+    return dict(sc, verts=v, motion=scenes.translate((0, 0, 0)), T=1)
+
+
+@pytest.mark.parametrize("kind", ["rotate", "translate"])
+@pytest.mark.parametrize("mode", ["exact", "linear", "fast"])
+def test_single_subframe_equals_static_render(kind, mode):
+    """T = 1 renders the pose at t = 0.5, equal to a static render of that pose.  In fast mode the
+    background distance is measured through keyframe F(X) (Eq. euc-dist-approx-2), which a moving
+    scene does not share with its static copy, so there only the foreground must agree."""
+    sc = dict(scenes.small_scene(kind, T=1, H=33, W=47), T=1)
+    a = oracle.render(sc, mode)["rgba"]
+    b = oracle.render(_static_copy(sc, 0.5), mode)["rgba"]
+    ch = slice(0, 3) if mode == "fast" else slice(0, 4)
+    assert np.max(np.abs(a[..., ch] - b[..., ch])) < 1e-12
+    assert a[..., 3].max() > 0.99  # the object is in view
+
+
+def _quad_scene(T, D, L0=-0.37, R0=0.113, B=-0.29, Tp=0.41, H=24, W=40, rule="paper"):
+    cam = scenes.camera(scenes.look_at((0, 0, -4)), time_rule=rule)
+    th = cam["tan_half_fov"]
+    z = 4.0
+    # world quad in the plane z = 0 whose screen extent at t = 0 is [L0, R0] x [B, Tp]
+    xs = np.array([L0, R0]) * z * th
+    ys = np.array([B, Tp]) * z * th
+    v = np.array([[xs[0], ys[0], 0], [xs[1], ys[0], 0], [xs[1], ys[1], 0], [xs[0], ys[1], 0]], float)
+    f = np.array([[0, 2, 1], [0, 3, 2]], dtype=np.int32)
+    d = D * z * th  # world translation giving a screen shift of D
+    return scenes.scene(v, f, np.full((4, 3), 0.6), scenes.translate((d, 0, 0), offset=(0, 0, 0)), cam, T, H, W)
+
+
+def _quad_counts(sc, L0, R0, B, Tp, D):
+    """#{k : L0 + t_k D <= u <= R0 + t_k D} for every pixel centre inside [B, Tp] vertically,
+    computed by enumerating the sample times."""
+    H, W, T = sc["H"], sc["W"], sc["T"]
+    u = 2 * (np.arange(W) + 0.5) / W - 1
+    v = 1 - 2 * (np.arange(H) + 0.5) / H
+    t = np.arange(T) / (T - 1) if sc["camera"]["time_rule"] == "paper" else (np.arange(T) + 0.5) / T
+    inside = (u[None, :] >= L0 + t[:, None] * D) & (u[None, :] <= R0 + t[:, None] * D)
+    cnt = inside.sum(0)
+    rows = (v >= B) & (v <= Tp)
+    return rows[:, None] * cnt[None, :]
+
+
+@pytest.mark.parametrize("mode", ["exact", "linear", "fast"])
+def test_translating_quad_box_count_closed_form(mode):
+    """A constant-colour, screen-aligned quad translating along x: pixel RGB = c_full * n/T with
+    n the number of sample times whose shifted quad covers the pixel centre."""
+    L0, R0, B, Tp, D = -0.37, 0.113, -0.29, 0.41, 0.6131
+    sc = _quad_scene(17, D, L0, R0, B, Tp)
+    img = oracle.render(sc, mode)["rgba"]
+    cam = sc["camera"]
+    # one covered sample: albedo 0.6 under Lambert with the quad normal (0, 0, -1) facing the camera
+    full = 0.6 * (cam["k_ambient"] + cam["k_diffuse"] * -cam["light_dir"][2] / np.linalg.norm(cam["light_dir"]))
+    cnt = _quad_counts(sc, L0, R0, B, Tp, D)
+    assert np.max(np.abs(img[..., 0] - full * cnt / sc["T"])) < 1e-12
+    assert np.max(np.abs(img[..., :3] - img[..., :1])) < 1e-12  # grey albedo -> equal channels
+    covered = cnt > 0
+    assert np.all(img[..., 3][cnt == sc["T"]] > 1 - 1e-12)
+    assert covered.any()
+
+
+def test_translating_quad_converges_to_box_filter():
+    """As T grows the box count tends to the box-filtered edge profile
+    |[(u - R0)/D, (u - L0)/D] intersect [0, 1]|, with O(1/T) error."""
+    L0, R0, B, Tp, D = -0.37, 0.113, -0.29, 0.41, 0.6131
+    T = 4096
+    sc = _quad_scene(T, D, L0, R0, B, Tp, H=8, W=40)
+    img = oracle.render(sc, "fast")["rgba"]
+    full = 0.6 * (sc["camera"]["k_ambient"] + sc["camera"]["k_diffuse"] *
+                  0.7 / np.linalg.norm(sc["camera"]["light_dir"]))
+    u = 2 * (np.arange(40) + 0.5) / 40 - 1
+    prof = np.clip(np.minimum(1.0, (u - L0) / D) - np.maximum(0.0, (u - R0) / D), 0.0, None)
+    row = 4  # a row inside [B, Tp]
+    assert np.max(np.abs(img[row, :, 0] / full - prof)) < 2.0 / T
+
+
+def test_rotation_relabel_invariance_midpoint_rule():
+    """With t_k = (k + 0.5)/T, omega = 2 pi and T a multiple of n, pre-rotating the mesh by 2 pi/n
+    about the motion axis permutes the sub-frames and leaves the blurred image unchanged."""
+    sc = scenes.small_scene("rotate", T=12, H=30, W=38, time_rule="midpoint")
+    n = 4
+    m = sc["motion"]
+    k = np.asarray(m["axis"])
+    th = 2 * math.pi / n
+    K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    R = np.eye(3) + math.sin(th) * K + (1 - math.cos(th)) * K @ K
+    sc2 = dict(sc, verts=sc["verts"] @ R.T)
+    a = oracle.render(sc, "exact")["rgba"]
+    b = oracle.render(sc2, "exact")["rgba"]
+    assert np.max(np.abs(a - b)) < 1e-9
+
+
+def test_full_turn_endpoints_identical_paper_rule():
+    """With the paper's t_k = k/(K-1) over one full turn, the first and last sub-frames show the
+    same pose: identical z-test winners."""
+    sc = scenes.small_scene("rotate", T=7, H=30, W=38)
+    r = oracle.render(sc, "exact", winners=True)
+    assert np.array_equal(r["winners"][0], r["winners"][-1])
+
+
+def test_fast_foreground_equals_plain_linear():
+    """Sec. 4.1: under linear motion the fast solver's foreground equals per-frame rendering;
+    only background alpha differs (distance approximation)."""
+    sc = scenes.small_scene("rotate", T=9, H=36, W=44)
+    a = oracle.render(sc, "linear", winners=True)
+    b = oracle.render(sc, "fast", winners=True)
+    assert np.array_equal(a["winners"], b["winners"])
+    assert np.max(np.abs(a["rgba"][..., :3] - b["rgba"][..., :3])) == 0.0
+
+
+def test_linear_screen_motion_exact_equals_linear():
+    """Translation perpendicular to the optical axis keeps camera z fixed, so projected motion is
+    exactly linear: PLAIN_EXACT and PLAIN_LINEAR agree on the whole image."""
+    sc = scenes.config1()
+    a = oracle.render(sc, "exact")["rgba"]
+    b = oracle.render(sc, "linear")["rgba"]
+    assert np.max(np.abs(a - b)) < 1e-12
+
+
+def test_soft_truncation_bound():
+    """Dropping terms with d > delta ln 1e12 changes alpha by at most F * 1e-12."""
+    sc = scenes.small_scene("rotate", subdiv=1, T=4, H=20, W=26)
+    for mode in ("exact", "fast"):
+        a = oracle.render(sc, mode)["rgba"]
+        b = oracle.render(sc, mode, soft_all=True)["rgba"]
+        assert np.max(np.abs(a - b)) <= len(sc["faces"]) * 1e-12 + 1e-15
+
+
+# ----------------------------------------------------------------------------- brute force
+
+def _seg_min_ternary(a, b, p, iters=100):
+    """min_t |a + t (b - a) - p|^2 on [0, 1] by ternary search (vectorised over leading axes)."""
+    lo = np.zeros(p.shape[:-1])
+    hi = np.ones(p.shape[:-1])
+    f = lambda t: np.sum((a + t[..., None] * (b - a) - p) ** 2, axis=-1)
+    for _ in range(iters):
+        m1 = lo + (hi - lo) / 3
+        m2 = hi - (hi - lo) / 3
+        left = f(m1) < f(m2)
+        hi = np.where(left, m2, hi)
+        lo = np.where(left, lo, m1)
+    t = 0.5 * (lo + hi)
+    return f(t), t
+
+
+def _brute_force(sc, mode):
+    """All pixel x triangle x sample triples, no bounding boxes, no truncation, np.linalg.solve
+    barycentrics, closest points by ternary search along the edges."""
+    V, F = sc["verts"], sc["faces"]
+    T, H, W = sc["T"], sc["H"], sc["W"]
+    cam = sc["camera"]
+    L = np.asarray(cam["light_dir"]) / np.linalg.norm(cam["light_dir"])
+    S = oracle.num_segments(sc)
+    u = 2 * (np.arange(W) + 0.5) / W - 1
+    v = 1 - 2 * (np.arange(H) + 0.5) / H
+    P = np.stack(np.meshgrid(u, v), -1).reshape(-1, 2)
+    img = np.zeros((H * W, 4))
+    for k in range(T):
+        s, t, tau = oracle.sample_time(sc, k)
+        if mode == "exact":
+            st = oracle.vertex_state(sc, t)
+        else:
+            k0, k1 = oracle.vertex_state(sc, s / S), oracle.vertex_state(sc, (s + 1) / S)
+            st = (1 - tau) * k0 + tau * k1
+            X = 0 if tau <= 0.5 else 1
+            kx = k0 if X == 0 else k1
+        best = np.full(len(P), -np.inf)
+        bw = np.zeros((len(P), 3))
+        bf = np.full(len(P), -1)
+        prod = np.ones(len(P))
+        for f in range(len(F)):
+            tri = st[F[f]]
+            M = np.array([tri[:, 0], tri[:, 1], [1, 1, 1]])
+            if abs(np.linalg.det(M)) <= 1e-10:
+                continue
+            w = np.linalg.solve(M[None], np.concatenate([P, np.ones((len(P), 1))], 1)[..., None])[..., 0]
+            cov = np.all(w >= 0, axis=1)
+            key = w @ (1 / tri[:, 2])
+            upd = cov & ((key > best) | ((key == best) & (f < bf)))
+            best[upd], bf[upd], bw[upd] = key[upd], f, w[upd]
+            if mode == "fast":
+                trx = kx[F[f]][:, :2]
+                pp = w @ trx
+                base = trx
+            else:
+                pp = P
+                base = tri[:, :2]
+            ds, ts = [], []
+            for e in range(3):
+                d, tt = _seg_min_ternary(base[e][None], base[(e + 1) % 3][None], pp)
+                ds.append(d)
+                ts.append(tt)
+            ds = np.stack(ds, 1)
+            ei = np.argmin(ds, 1)
+            tt = np.stack(ts, 1)[np.arange(len(P)), ei]
+            a_i = tri[ei, :2]
+            b_i = tri[(ei + 1) % 3, :2]
+            q = a_i + tt[:, None] * (b_i - a_i)
+            d = np.sum((P - q) ** 2, 1)
+            prod[~cov] *= 1 - np.exp(-d[~cov] / cam["delta"])
+        for p in range(len(P)):
+            if bf[p] >= 0:
+                ids = F[bf[p]]
+                col = bw[p] @ sc["albedo"][ids]
+                n = bw[p] @ st[ids, 3:6]
+                sh = cam["k_ambient"] + cam["k_diffuse"] * max(0.0, n @ L / np.linalg.norm(n))
+                img[p, :3] += col * sh
+                img[p, 3] += 1
+            else:
+                img[p, 3] += 1 - prod[p]
+    return (img / T).reshape(H, W, 4)
+
+
+@pytest.mark.parametrize("mode", ["exact", "linear", "fast"])
+def test_brute_force_tiny_mesh(mode):
+    """Brute-force enumeration on an 8-triangle mesh (octahedron, albedo per vertex) at 12x14 px."""
+    rng = np.random.default_rng(5)
+    v = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], float) * 0.6
+    v += rng.normal(0, 0.05, v.shape)
+    f = np.array([[0, 2, 4], [2, 1, 4], [1, 3, 4], [3, 0, 4], [2, 0, 5], [1, 2, 5], [3, 1, 5], [0, 3, 5]],
+                 dtype=np.int32)
+    f = scenes._orient_outward(v, f)
+    cam = scenes.camera(scenes.look_at(scenes.orbit_eye(4.0, 20, 10)))
+    cam["delta"] = 3e-3  # a wide soft band so the background term is exercised on a 12x14 grid
+    sc = scenes.scene(v, f, rng.uniform(0.2, 0.9, (6, 3)), scenes.rotate((0.3, 1, 0.2), 1.3, segments=2),
+                      cam, 5, 12, 14)
+    a = oracle.render(sc, mode, soft_all=True)["rgba"]
+    b = _brute_force(sc, mode)
+    assert np.max(np.abs(a - b)) < 1e-9
+    assert a[..., 3].max() > 0.5 and (a[..., 3] > 0).mean() < 1.0
