@@ -30,7 +30,9 @@
 #define ETA_DET 1e-5       /* ambiguity: |det F| <= D_MIN + ETA_DET * (longest edge)^2          */
 #define ETA_REGION 1e-6    /* ambiguity: fast-mode closest-edge tie (relative)                   */
 
-enum { AMB_COVER = 1, AMB_DEPTH = 2, AMB_DEGEN = 4, AMB_REGION = 8 };
+enum { AMB_COVER = 1, AMB_DEPTH = 2, AMB_DEGEN = 4, AMB_REGION = 8, AMB_CLAMP = 16, AMB_LAMBERT = 32 };
+#define ETA_CLAMP 1e-5     /* gradient-only flag: closest-point parameter within this of 0 or 1 */
+#define ETA_LAMBERT 1e-5   /* gradient-only flag: |n.l| below this (Lambert clamp switches)     */
 
 /* ------------------------------------------------------------------ small helpers */
 
@@ -64,7 +66,7 @@ int32_t orc_num_segments(const orc_scene* s) {
   if (s->motion_kind == 0) return 1; /* translation: one linear segment (visualisation details) */
   /* rotation: 12 segments per full turn (Sec. 3.3, segmentation analysis) */
   double x = 12.0 * fabs(s->omega) / (2.0 * PI_D);
-  int32_t n = (int32_t)ceil(x - 1e-9);
+  int32_t n = (int32_t)ceil(x - 1e-4); /* tolerance: omega = 2 pi rounded to float is 12 segments */
   return n < 1 ? 1 : n;
 }
 
@@ -218,6 +220,7 @@ typedef struct {
   double t;       /* clamped edge parameter */
   double d2_second; /* second-best edge distance (for tie detection) */
   double w_second[3];
+  double traw[3], d2e[3]; /* per edge: unclamped projection parameter and squared distance */
 } closest_t;
 
 /* For each edge v_i v_j: t = ((p - v_i).(v_j - v_i)) / |v_j - v_i|^2 clamped to [0, 1]
@@ -231,12 +234,14 @@ static void closest_point(const double tri[6], double px, double py, closest_t* 
     double xi = tri[2 * i], yi = tri[2 * i + 1], xj = tri[2 * j], yj = tri[2 * j + 1];
     double ex = xj - xi, ey = yj - yi, L2 = ex * ex + ey * ey;
     double t = L2 > 0 ? ((px - xi) * ex + (py - yi) * ey) / L2 : 0.0;
+    out->traw[e] = t;
     int32_t reg = e;
     double qx, qy;
     if (t <= 0.0) { t = 0.0; qx = xi; qy = yi; reg = 3 + i; }
     else if (t >= 1.0) { t = 1.0; qx = xj; qy = yj; reg = 3 + j; }
     else { qx = xi + t * ex; qy = yi + t * ey; }
     double d2 = (px - qx) * (px - qx) + (py - qy) * (py - qy);
+    out->d2e[e] = d2;
     double w[3] = {0, 0, 0};
     w[i] = 1.0 - t;
     w[j] = t;
@@ -538,6 +543,14 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
               d = c.d2;
             }
             const int include = soft_all || d <= r2;
+            if (include) {
+              /* an edge attaining the minimum whose unclamped projection lies near an end: the
+               * region (edge interior vs vertex) may switch in FP32, which changes the gradient */
+              for (int q = 0; q < 3; ++q)
+                if (c.d2e[q] <= c.d2 * (1.0 + 1e-9) + 1e-300 &&
+                    (fabs(c.traw[q]) < ETA_CLAMP || fabs(c.traw[q] - 1.0) < ETA_CLAMP))
+                  amb[p] |= AMB_CLAMP;
+            }
             hash = fnv(fnv(fnv(hash, k * 7919 + 1), (int64_t)p * 104729 + f), c.region * 2 + include);
             if (include) {
               double A = exp(-d / s->delta);
@@ -577,6 +590,7 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
         double dot = len > 0 ? (nn[0] * Ld[0] + nn[1] * Ld[1] + nn[2] * Ld[2]) / len : 0.0;
         double shade = s->k_ambient + s->k_diffuse * (dot > 0 ? dot : 0.0);
         hash = fnv(hash, dot > 0);
+        if (fabs(dot) < ETA_LAMBERT) amb[p] |= AMB_LAMBERT;
         if (rgba) {
           for (int c = 0; c < 3; ++c) rgba[4 * p + c] += col[c] * shade;
           rgba[4 * p + 3] += 1.0;

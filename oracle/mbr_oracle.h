@@ -69,7 +69,11 @@ double orc_closest_point(const double tri[6], double px, double py, double w[3],
 /* Render the window [x0, x0+w) x [y0, y0+h) of the H x W image.
  *   rgba     [h*w*4]   blurred RGBA, row-major, pixel (0,0) at the window's top-left
  *   winners  [T*h*w]   per-sample z-test winner (face id) or -1; may be NULL
- *   ambig    [T*h*w]   per-sample ambiguity flags (bitmask); may be NULL
+ *   ambig    [T*h*w]   per-sample flags (bitmask) where FP32 may take another discrete choice:
+ *                      1 coverage (pixel within 2e-6 of a triangle boundary), 2 depth tie,
+ *                      4 near-degenerate triangle, 8 fast-mode closest-edge tie (these four can
+ *                      change a pixel); 16 closest-point clamp boundary, 32 Lambert clamp
+ *                      (these two only change gradients); may be NULL
  *   counters [ORC_CNT_N]
  * returns 0, or -1 on bad arguments / allocation failure. */
 int32_t orc_render(const orc_scene* s, int32_t mode, int32_t flags, int32_t x0, int32_t y0,

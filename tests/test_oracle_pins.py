@@ -201,6 +201,9 @@ def test_sample_times_and_segments():
     assert abs(oracle.sample_time(mid, 0)[1] - 0.5 / 64) < 1e-15
     tr = scenes.small_scene("translate")
     assert oracle.num_segments(tr) == 1
+    # omega = 2 pi rounded to single precision (how the CUDA path receives it) is still 12 segments
+    f32 = dict(sc, motion=dict(sc["motion"], omega=float(np.float32(2 * math.pi))))
+    assert oracle.num_segments(f32) == 12
     assert oracle.num_segments(dict(sc, motion=dict(sc["motion"], omega=16 * math.pi))) == 96
 
 
