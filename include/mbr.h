@@ -1,0 +1,148 @@
+/*
+ * mbr.h -- C ABI of the GB300 (sm_103a) motion-blurred differentiable mesh renderer.
+ *
+ * Operation (paper: "Recovering 3D Shapes from Ultra-Fast Motion-Blurred Images",
+ * arXiv 2602.07860): a triangle mesh moves rigidly over one exposure (Sec. "Motion Parameters":
+ * translation, or rotation about an axis through the origin).  At T sub-frame times
+ * t_k = k/(T-1) (Sec. 3.2) every pixel centre p = [u, v, 1] gets barycentric coordinates
+ * w = F(t)^-1 p for the triangles near it (Eq. barycentric), the nearest covering triangle wins
+ * the z-test (Sec. 3.1), its interpolated colour and normal are shaded (Eq. fore, Lambert), and
+ * uncovered samples get the soft coverage alpha 1 - prod_j (1 - exp(-d_j/delta))
+ * (Eqs. probability-function, back).  The T sub-frames are averaged into one RGBA image
+ * (Sec. 3.3).  Two solvers compute the sub-frame barycentrics:
+ *   MBR_PLAIN -- per sub-frame: exact motion and projection at every t_k, F(t_k)^-1 p per sample;
+ *   MBR_FAST  -- the paper's fast solver (Sec. 3.2, Eq. time-dependent2): motion split into S
+ *                linear segments; per (pixel, triangle, segment) the quadratic-rational
+ *                coefficients are formed once and w(tau) is evaluated per sample; background
+ *                distances use keyframe F(X) (Eqs. euc-dist-approx-2/3).
+ *
+ * Conventions
+ *   - NDC: pixel (i, j) has centre u = 2(i+0.5)/W - 1, v = 1 - 2(j+0.5)/H (row 0 at the top);
+ *     projection x = x_c / (z_c tan_half_fov), y = y_c / (z_c tan_half_fov) (Sec. "Camera").
+ *   - Images are [H, W, 4] float32 RGBA, row-major, device memory.
+ *   - All pointers in mbr_mesh and all image / gradient buffers are DEVICE pointers owned by the
+ *     caller; the library never frees them.  The context owns its scratch (vertex states,
+ *     triangle records, tile bins, gradient slots), grows it on demand and frees it in
+ *     mbr_destroy.
+ *   - Every call is enqueued on the caller's CUDA stream (cudaStream_t passed as void*; NULL =
+ *     legacy default stream).  mbr_render_blur and mbr_render_blur_backward synchronise that
+ *     stream once, after binning, to size the tile lists.
+ *   - Errors: every call returns MBR_OK (0) or an MBR_ERR_* code and never aborts; the message
+ *     of the last failure is returned by mbr_last_error.  A context is used by one host thread
+ *     at a time.
+ */
+#ifndef MBR_H
+#define MBR_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MBR_OK 0
+#define MBR_ERR_ARG 1     /* invalid argument (null pointer, bad size, unsupported value)      */
+#define MBR_ERR_CUDA 2    /* a CUDA runtime call failed                                        */
+#define MBR_ERR_OOM 3     /* device allocation failed                                          */
+#define MBR_ERR_TIMEOUT 4 /* a bounded device-side wait ran out (batch scheduler)              */
+#define MBR_ERR_DEVICE 5  /* a kernel reported an error through the device status word        */
+
+#define MBR_PLAIN 0
+#define MBR_FAST 1
+
+#define MBR_TRANSLATE 0
+#define MBR_ROTATE 1
+
+#define MBR_TIME_PAPER 0    /* t_k = k/(T-1), T = 1 -> 0.5 (Sec. 3.2)  */
+#define MBR_TIME_MIDPOINT 1 /* t_k = (k + 0.5)/T                        */
+
+typedef struct mbr_ctx mbr_ctx;
+
+/* Triangle mesh (device pointers). */
+typedef struct {
+  int32_t V, F;
+  const float* verts;   /* [V,3] base vertex positions, world units                    */
+  const int32_t* faces; /* [F,3] vertex indices in [0, V)                               */
+  const float* albedo;  /* [V,3] per-vertex colour (the c_i of Eq. fore)                */
+} mbr_mesh;
+
+/* Rigid motion over the exposure, t in [0, 1] (Sec. "Motion Parameters"). */
+typedef struct {
+  int32_t kind;     /* MBR_TRANSLATE: P(t) = v + offset + t dir
+                       MBR_ROTATE:    P(t) = R(omega t) v, right-handed about unit(axis)   */
+  int32_t segments; /* fast solver's linear segments; 0 = 1 (translation) or
+                       ceil(12 |omega| / 2 pi) (rotation; 12 per turn, Sec. 3.3)           */
+  float offset[3], dir[3], axis[3], omega;
+} mbr_motion;
+
+/* Camera, shading and soft-coverage parameters. */
+typedef struct {
+  float view[12];       /* 3x4 world->camera matrix, camera +z forward                        */
+  float tan_half_fov;   /* tan of half the field of view                                      */
+  float znear;          /* triangles with a vertex at camera z <= znear are skipped           */
+  float light_dir[3];   /* direction towards the light, world space (normalised internally)  */
+  float k_ambient, k_diffuse; /* I = c (k_ambient + k_diffuse max(0, n.l))                   */
+  float delta;          /* soft-coverage temperature of Eq. probability-function (1e-4)      */
+  int32_t time_rule;    /* MBR_TIME_PAPER or MBR_TIME_MIDPOINT                                */
+} mbr_camera;
+
+/* One render of a batch (device pointers; see mbr_render_blur_batch). */
+typedef struct {
+  mbr_mesh mesh;
+  mbr_motion motion;
+  mbr_camera camera;
+  int32_t T, H, W, solver;
+  float* image;            /* [H,W,4] out                                               */
+  const float* dl_dimage;  /* [H,W,4] in, read when with_backward                       */
+  float* dl_dverts;        /* [V,3] out (overwritten) when with_backward                */
+  float* dl_dalbedo;       /* [V,3] out (overwritten) when with_backward, may be NULL   */
+} mbr_item;
+
+/* Create / destroy a context on the current CUDA device.  Returns MBR_OK or MBR_ERR_*. */
+int mbr_create(mbr_ctx** out);
+void mbr_destroy(mbr_ctx* ctx);
+
+/* Forward render (Secs. 3.1-3.3).  T >= 1, H, W >= 1, V >= 1, F >= 0.  image [H,W,4] is
+ * overwritten with the blurred RGBA.  MBR_ERR_ARG on invalid sizes / null pointers. */
+int mbr_render_blur(mbr_ctx* ctx, const mbr_mesh* mesh, const mbr_motion* motion,
+                    const mbr_camera* camera, int32_t T, int32_t H, int32_t W, int32_t solver,
+                    float* image, void* cuda_stream);
+
+/* Adjoint of mbr_render_blur ("Gradient Computation", Sec. 3.3): given dL/dimage [H,W,4],
+ * writes dL/dverts [V,3] (overwritten) and, if non-NULL, dL/dalbedo [V,3].  The forward state
+ * of every sample is recomputed, not stored.  Discrete choices (coverage, z-test winner,
+ * closest-point region, Lambert clamp) carry no gradient. */
+int mbr_render_blur_backward(mbr_ctx* ctx, const mbr_mesh* mesh, const mbr_motion* motion,
+                             const mbr_camera* camera, int32_t T, int32_t H, int32_t W,
+                             int32_t solver, const float* dl_dimage, float* dl_dverts,
+                             float* dl_dalbedo, void* cuda_stream);
+
+/* Render n independent items (objects, motions, sub-frame counts and resolutions may differ)
+ * with one persistent raster launch per pass, forward and (with_backward != 0) backward. */
+int mbr_render_blur_batch(mbr_ctx* ctx, int32_t n, const mbr_item* items, int32_t with_backward,
+                          void* cuda_stream);
+
+/* Test hook: the z-test winner (face id, -1 = background) of every pixel at sub-frame k,
+ * written to ids [H,W] (device).  Same arguments as mbr_render_blur otherwise. */
+int mbr_debug_winners(mbr_ctx* ctx, const mbr_mesh* mesh, const mbr_motion* motion,
+                      const mbr_camera* camera, int32_t T, int32_t H, int32_t W, int32_t solver,
+                      int32_t k, int32_t* ids, void* cuda_stream);
+
+/* Measurement hook: count N_cand, the (pixel, sub-frame, triangle) triples whose triangle's
+ * bounding box at that sub-frame, dilated by sqrt(delta ln 1e12), contains the pixel centre
+ * (plain solver: exact positions; fast solver: keyframe-lerped positions).  *out is a HOST
+ * int64; the call synchronises the stream. */
+int mbr_count_candidates(mbr_ctx* ctx, const mbr_mesh* mesh, const mbr_motion* motion,
+                         const mbr_camera* camera, int32_t T, int32_t H, int32_t W,
+                         int32_t solver, int64_t* out, void* cuda_stream);
+
+/* Tuning knobs (autotuner): tile edge in pixels (8 or 16), sub-frames per thread for the fast
+ * solver (1..16), and the number of sub-frame groups split across CTAs (0 = automatic). */
+int mbr_set_tuning(mbr_ctx* ctx, int32_t tile, int32_t spt, int32_t splits);
+
+/* Message of the last failed call on ctx ("" if none).  Valid until the next call. */
+const char* mbr_last_error(mbr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

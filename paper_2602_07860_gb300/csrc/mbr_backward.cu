@@ -1,0 +1,498 @@
+// mbr_backward.cu -- adjoint kernels of the sm_103a motion-blurred renderer (a9).
+//
+//   raster_bwd_kernel  recomputes passes 1-2 of the forward per sample (nothing is stored),
+//                      then back-propagates dL/dimage through shading (Eq. fore + Lambert),
+//                      the barycentric edge functions, and the soft-coverage product
+//                      (Eqs. probability-function .. back, exclusive products) into gradients on
+//                      the slot vertex states (ndc x, y and world normal); soft-term gradients
+//                      are warp-reduced per candidate before the atomics
+//   slot_chain_kernel  slot-state gradients -> base vertex gradients through projection, camera
+//                      and motion; base-normal gradient -> area-weighted-normal gradient
+//   normals_bwd_kernel adjoint of the face cross products of the vertex normals (a0)
+#include <cstdint>
+
+#include "mbr_internal.h"
+#include "mbr_raster.cuh"
+
+namespace mbr {
+
+constexpr float kTinyFactor = 1e-30f;
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// gradient of the edge functions N_q (at tau, local frame) w.r.t. the three vertex positions:
+// N0 = cross(a1, a2), N1 = cross(a2, a0), N2 = cross(a0, a1) with a_i = v_i(tau) - p.
+__device__ __forceinline__ void edge_backward(float gN0, float gN1, float gN2, const float ax[3],
+                                              const float ay[3], float gx[3], float gy[3]) {
+  // d cross(a, b) / da = (b.y, -b.x), / db = (-a.y, a.x)
+  gx[0] = gN1 * -ay[2] + gN2 * ay[1];
+  gy[0] = gN1 * ax[2] + gN2 * -ax[1];
+  gx[1] = gN0 * ay[2] + gN2 * -ay[0];
+  gy[1] = gN0 * -ax[2] + gN2 * ax[0];
+  gx[2] = gN0 * -ay[1] + gN1 * ay[0];
+  gy[2] = gN0 * ax[1] + gN1 * -ax[0];
+}
+
+// vertex positions relative to the pixel at tau: a_i = v_i(tau) - p
+template <bool MOVING>
+__device__ __forceinline__ void rel_vertices(const float4* r, const PixelSetup<MOVING>& ps, float tau,
+                                             float ax[3], float ay[3]) {
+  const float qtx = MOVING ? fmaf(-tau, r[4].x, ps.q0x) : ps.q0x;
+  const float qty = MOVING ? fmaf(-tau, r[4].y, ps.q0y) : ps.q0y;
+  const float e1x = MOVING ? fmaf(tau, r[3].x, r[0].z) : r[0].z;
+  const float e1y = MOVING ? fmaf(tau, r[3].y, r[0].w) : r[0].w;
+  const float e2x = MOVING ? fmaf(tau, r[3].z, r[1].x) : r[1].x;
+  const float e2y = MOVING ? fmaf(tau, r[3].w, r[1].y) : r[1].y;
+  ax[0] = -qtx; ay[0] = -qty;
+  ax[1] = e1x - qtx; ay[1] = e1y - qty;
+  ax[2] = e2x - qtx; ay[2] = e2y - qty;
+}
+
+template <int TW, int TH, int SPT, bool MOVING>
+__global__ void __launch_bounds__(TW * TH) raster_bwd_kernel(RasterParams P) {
+  constexpr int NT = TW * TH;
+  __shared__ float4 s_rec[kStageCap * kRecF4];
+  __shared__ Group s_grp;
+  const int n_tiles = P.tiles_x * P.tiles_y;
+  const int tile = blockIdx.x % n_tiles, split = blockIdx.x / n_tiles;
+  const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
+  const int px = tx * TW + (int)(threadIdx.x % TW), py = ty * TH + (int)(threadIdx.x / TW);
+  const bool in_img = px < P.W && py < P.H;
+  const float u = (2.f * px + 1.f) / P.W - 1.f;
+  const float v = 1.f - (2.f * py + 1.f) / P.H;
+  const int g_begin = (int)((long long)P.G * split / P.n_split);
+  const int g_end = (int)((long long)P.G * (split + 1) / P.n_split);
+  float4 G4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (in_img) G4 = __ldg(P.dl_dimage + (size_t)py * P.W + px);
+  const float gr = G4.x * P.inv_T, gg = G4.y * P.inv_T, gb = G4.z * P.inv_T, ga = G4.w * P.inv_T;
+  const int lane = threadIdx.x & 31;
+
+  for (int g = g_begin; g < g_end; ++g) {
+    __syncthreads();
+    if (threadIdx.x < sizeof(Group) / 4)
+      reinterpret_cast<int*>(&s_grp)[threadIdx.x] = reinterpret_cast<const int*>(P.groups + g)[threadIdx.x];
+    __syncthreads();
+    const int n = s_grp.n;
+    const TriRec* recs_set = P.recs + (size_t)s_grp.rec_set * P.F;
+    const int beg = P.bin_off[(size_t)g * n_tiles + tile], end = P.bin_off[(size_t)g * n_tiles + tile + 1];
+    float* gslot_a = P.g_slot + (size_t)s_grp.slot_a * P.V * 5;
+    float* gslot_b = P.g_slot + (size_t)s_grp.slot_b * P.V * 5;
+    float bestk[SPT];
+    int bestf[SPT];
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) { bestk[i] = -INFINITY; bestf[i] = -1; }
+
+    // ---- pass 1 (recomputed): z-test winners
+    for (int c0 = beg; c0 < end; c0 += kStageCap) {
+      const int cnt = min(kStageCap, end - c0);
+      __syncthreads();
+      stage_records<NT, MOVING>(s_rec, recs_set, P.bin_faces + c0, cnt);
+      __syncthreads();
+      if (in_img) {
+        for (int j = 0; j < cnt; ++j) {
+          const float4* r = s_rec + j * kRecF4;
+          const int face = __float_as_int(r[1].w);
+          const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
+#pragma unroll
+          for (int i = 0; i < SPT; ++i) {
+            if (i < n) {
+              const float tau = s_grp.tau[i];
+              const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
+              if (covers(e)) {
+                const float key = inv_depth<MOVING>(r, e, tau);
+                if (key > bestk[i] || (key == bestk[i] && face < bestf[i])) {
+                  bestk[i] = key;
+                  bestf[i] = face;
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+
+    // ---- pass 2 (recomputed): soft products, with a count of vanishing factors so that the
+    // exclusive product prod_{l != j} (1 - A_l) never divides by a zero factor
+    bool any_unc = false;
+#pragma unroll
+    for (int i = 0; i < SPT; ++i)
+      if (i < n && bestf[i] < 0) any_unc = true;
+    const bool need_soft = __syncthreads_or(in_img && any_unc && end > beg && ga != 0.f);
+    float prod[SPT];
+    int nzero[SPT];
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) { prod[i] = 1.f; nzero[i] = 0; }
+    if (need_soft) {
+      for (int c0 = beg; c0 < end; c0 += kStageCap) {
+        const int cnt = min(kStageCap, end - c0);
+        __syncthreads();
+        stage_records<NT, MOVING>(s_rec, recs_set, P.bin_faces + c0, cnt);
+        __syncthreads();
+        if (in_img && any_unc) {
+          for (int j = 0; j < cnt; ++j) {
+            const float4* r = s_rec + j * kRecF4;
+            const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
+#pragma unroll
+            for (int i = 0; i < SPT; ++i) {
+              if (i < n && bestf[i] < 0) {
+                const float tau = s_grp.tau[i];
+                const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
+                if (fabsf(e.D) > kDetMin) {
+                  const SoftGeom sg = soft_geom<MOVING>(r, ps, e, tau, (s_grp.xbits >> i) & 1u);
+                  if (sg.d <= P.r2) {
+                    const float f = -expm1f(-sg.d * P.inv_delta);
+                    if (f > kTinyFactor) prod[i] *= f; else nzero[i] += 1;
+                  }
+                }
+              }
+            }
+          }
+        }
+      }
+
+      // ---- pass 3: soft-coverage adjoint, warp-reduced per candidate triangle
+      for (int c0 = beg; c0 < end; c0 += kStageCap) {
+        const int cnt = min(kStageCap, end - c0);
+        __syncthreads();
+        stage_records<NT, MOVING>(s_rec, recs_set, P.bin_faces + c0, cnt);
+        __syncthreads();
+        for (int j = 0; j < cnt; ++j) {
+          const float4* r = s_rec + j * kRecF4;
+          const int face = __float_as_int(r[1].w);
+          // per-candidate accumulators: (x, y) of the 3 vertices at slot_a and slot_b
+          float ga_x[3] = {0.f, 0.f, 0.f}, ga_y[3] = {0.f, 0.f, 0.f};
+          float gb_x[3] = {0.f, 0.f, 0.f}, gb_y[3] = {0.f, 0.f, 0.f};
+          bool any = false;
+          if (in_img && any_unc && ga != 0.f) {
+            const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
+#pragma unroll
+            for (int i = 0; i < SPT; ++i) {
+              if (i < n && bestf[i] < 0) {
+                const float tau = s_grp.tau[i];
+                const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
+                if (fabsf(e.D) <= kDetMin) continue;
+                const int X = (s_grp.xbits >> i) & 1u;
+                const SoftGeom sg = soft_geom<MOVING>(r, ps, e, tau, X);
+                if (sg.d > P.r2) continue;
+                const float f = -expm1f(-sg.d * P.inv_delta);
+                const float A = __expf(-sg.d * P.inv_delta);
+                float excl;
+                if (nzero[i] == 0) excl = prod[i] / f;
+                else excl = (nzero[i] == 1 && f <= kTinyFactor) ? prod[i] : 0.f;
+                // alpha = 1 - prod(1 - A_l): d alpha / d d_j = -excl A_j / delta
+                const float gd = ga * excl * (-A * P.inv_delta);
+                if (gd == 0.f) continue;
+                any = true;
+                const float grx = 2.f * sg.rx * gd, gry = 2.f * sg.ry * gd;  // d/d(F(tau) w* - p)
+                const float ws[3] = {sg.c.w0, sg.c.w1, sg.c.w2};
+                float gtx[3], gty[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) { gtx[q] = ws[q] * grx; gty[q] = ws[q] * gry; }
+                if (MOVING) {
+                  // local vertex positions at tau and at keyframe X
+                  const float e1tx = fmaf(tau, r[3].x, r[0].z), e1ty = fmaf(tau, r[3].y, r[0].w);
+                  const float e2tx = fmaf(tau, r[3].z, r[1].x), e2ty = fmaf(tau, r[3].w, r[1].y);
+                  const float fx = (float)X;
+                  const float e1Xx = fmaf(fx, r[3].x, r[0].z), e1Xy = fmaf(fx, r[3].y, r[0].w);
+                  const float e2Xx = fmaf(fx, r[3].z, r[1].x), e2Xy = fmaf(fx, r[3].w, r[1].y);
+                  const float Vtx[3] = {0.f, e1tx, e2tx}, Vty[3] = {0.f, e1ty, e2ty};
+                  const float VXx[3] = {0.f, e1Xx, e2Xx}, VXy[3] = {0.f, e1Xy, e2Xy};
+                  float gXx[3] = {0.f, 0.f, 0.f}, gXy[3] = {0.f, 0.f, 0.f};
+                  float gpx = 0.f, gpy = 0.f;
+                  if (sg.c.region < 3) {
+                    // w*_i = 1 - t, w*_j = t, t = ((p' - V_i) . E) / |E|^2 on edge (i, j) of F(X)
+                    const int ei = sg.c.ei, ej = sg.c.ej;
+                    float gti = 0.f, gtj = 0.f, Ex = 0.f, Ey = 0.f, Rx = 0.f, Ry = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                      if (q == ei) { gti = Vtx[q] * grx + Vty[q] * gry; Rx = sg.ppx - VXx[q]; Ry = sg.ppy - VXy[q]; Ex -= VXx[q]; Ey -= VXy[q]; }
+                      if (q == ej) { gtj = Vtx[q] * grx + Vty[q] * gry; Ex += VXx[q]; Ey += VXy[q]; }
+                    }
+                    const float L2 = fmaf(Ex, Ex, Ey * Ey);
+                    const float gt = (gtj - gti) / L2, t = sg.c.t;
+                    gpx = gt * Ex;
+                    gpy = gt * Ey;
+                    const float gix = gt * (-Ex - Rx + 2.f * t * Ex), giy = gt * (-Ey - Ry + 2.f * t * Ey);
+                    const float gjx = gt * (Rx - 2.f * t * Ex), gjy = gt * (Ry - 2.f * t * Ey);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                      if (q == ei) { gXx[q] += gix; gXy[q] += giy; }
+                      if (q == ej) { gXx[q] += gjx; gXy[q] += gjy; }
+                    }
+                  }
+                  // p' = F(X) w(tau)
+                  const float w1 = sg.w1, w2 = sg.w2, w0 = 1.f - w1 - w2;
+                  const float wv[3] = {w0, w1, w2};
+                  float gw[3];
+#pragma unroll
+                  for (int q = 0; q < 3; ++q) {
+                    gXx[q] = fmaf(wv[q], gpx, gXx[q]);
+                    gXy[q] = fmaf(wv[q], gpy, gXy[q]);
+                    gw[q] = VXx[q] * gpx + VXy[q] * gpy;
+                  }
+                  // w = N / D with D = N0 + N1 + N2
+                  const float sw = wv[0] * gw[0] + wv[1] * gw[1] + wv[2] * gw[2];
+                  const float invD = 1.f / e.D;
+                  float ax[3], ay[3], ex[3], ey[3];
+                  rel_vertices<MOVING>(r, ps, tau, ax, ay);
+                  edge_backward((gw[0] - sw) * invD, (gw[1] - sw) * invD, (gw[2] - sw) * invD, ax, ay, ex, ey);
+#pragma unroll
+                  for (int q = 0; q < 3; ++q) { gtx[q] += ex[q]; gty[q] += ey[q]; }
+                  // F(tau) = lerp of the two keyframes; F(X) is keyframe X
+#pragma unroll
+                  for (int q = 0; q < 3; ++q) {
+                    ga_x[q] = fmaf(1.f - tau, gtx[q], ga_x[q]);
+                    ga_y[q] = fmaf(1.f - tau, gty[q], ga_y[q]);
+                    gb_x[q] = fmaf(tau, gtx[q], gb_x[q]);
+                    gb_y[q] = fmaf(tau, gty[q], gb_y[q]);
+                    if (X == 0) { ga_x[q] += gXx[q]; ga_y[q] += gXy[q]; }
+                    else { gb_x[q] += gXx[q]; gb_y[q] += gXy[q]; }
+                  }
+                } else {
+                  // exact distance: d d / d v_i = 2 (F w* - p) w*_i
+#pragma unroll
+                  for (int q = 0; q < 3; ++q) { ga_x[q] += gtx[q]; ga_y[q] += gty[q]; }
+                }
+              }
+            }
+          }
+          if (__any_sync(0xffffffffu, any)) {
+            float vals[12];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              vals[2 * q] = warp_sum(ga_x[q]);
+              vals[2 * q + 1] = warp_sum(ga_y[q]);
+              vals[6 + 2 * q] = MOVING ? warp_sum(gb_x[q]) : 0.f;
+              vals[7 + 2 * q] = MOVING ? warp_sum(gb_y[q]) : 0.f;
+            }
+            if (lane == 0) {
+#pragma unroll
+              for (int q = 0; q < 3; ++q) {
+                const int vid = __ldg(P.faces + 3 * face + q);
+                atomicAdd(gslot_a + (size_t)vid * 5, vals[2 * q]);
+                atomicAdd(gslot_a + (size_t)vid * 5 + 1, vals[2 * q + 1]);
+                if (MOVING) {
+                  atomicAdd(gslot_b + (size_t)vid * 5, vals[6 + 2 * q]);
+                  atomicAdd(gslot_b + (size_t)vid * 5 + 1, vals[7 + 2 * q]);
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+
+    // ---- covered samples: shading adjoint and barycentric adjoint of the winner
+    if (in_img) {
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) {
+        if (i < n && bestf[i] >= 0) {
+          const int f = bestf[i];
+          const float tau = s_grp.tau[i];
+          float4 r[kRecF4];
+          const TriRec* src = recs_set + f;
+#pragma unroll
+          for (int q = 0; q < (MOVING ? kRecF4 : 3); ++q) r[q] = __ldg(&src->f4[q]);
+          const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
+          const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
+          const float invD = 1.0f / e.D;
+          const float w[3] = {e.N0 * invD, e.N1 * invD, e.N2 * invD};
+          int vid[3];
+          float al[3][3], nv[3][3];
+          float cr = 0.f, cg = 0.f, cb = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            vid[q] = __ldg(P.faces + 3 * f + q);
+            al[q][0] = __ldg(P.albedo + 3 * vid[q]);
+            al[q][1] = __ldg(P.albedo + 3 * vid[q] + 1);
+            al[q][2] = __ldg(P.albedo + 3 * vid[q] + 2);
+            float4 na = __ldg(P.slot_nrm + (size_t)s_grp.slot_a * P.V + vid[q]);
+            if (MOVING) {
+              const float4 nb = __ldg(P.slot_nrm + (size_t)s_grp.slot_b * P.V + vid[q]);
+              na.x = fmaf(tau, nb.x - na.x, na.x);
+              na.y = fmaf(tau, nb.y - na.y, na.y);
+              na.z = fmaf(tau, nb.z - na.z, na.z);
+            }
+            nv[q][0] = na.x; nv[q][1] = na.y; nv[q][2] = na.z;
+            cr = fmaf(w[q], al[q][0], cr);
+            cg = fmaf(w[q], al[q][1], cg);
+            cb = fmaf(w[q], al[q][2], cb);
+            nx = fmaf(w[q], na.x, nx);
+            ny = fmaf(w[q], na.y, ny);
+            nz = fmaf(w[q], na.z, nz);
+          }
+          const float len = sqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+          const float dot = len > 0.f ? fmaf(nx, P.lx, fmaf(ny, P.ly, nz * P.lz)) / len : 0.f;
+          const float shade = fmaf(P.kd, fmaxf(dot, 0.f), P.ka);
+          // I = c shade
+          const float gcr = gr * shade, gcg = gg * shade, gcb = gb * shade;
+          const float gshade = gr * cr + gg * cg + gb * cb;
+          float gw[3];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            gw[q] = al[q][0] * gcr + al[q][1] * gcg + al[q][2] * gcb;
+            if (P.g_albedo) {
+              atomicAdd(P.g_albedo + 3 * vid[q], w[q] * gcr);
+              atomicAdd(P.g_albedo + 3 * vid[q] + 1, w[q] * gcg);
+              atomicAdd(P.g_albedo + 3 * vid[q] + 2, w[q] * gcb);
+            }
+          }
+          if (len > 0.f && dot > 0.f) {
+            const float il = 1.f / len;
+            const float hx = nx * il, hy = ny * il, hz = nz * il;
+            const float gx = P.kd * gshade * P.lx, gy = P.kd * gshade * P.ly, gz = P.kd * gshade * P.lz;
+            const float hg = hx * gx + hy * gy + hz * gz;
+            const float gnx = (gx - hx * hg) * il, gny = (gy - hy * hg) * il, gnz = (gz - hz * hg) * il;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              gw[q] += nv[q][0] * gnx + nv[q][1] * gny + nv[q][2] * gnz;
+              float* pa = gslot_a + (size_t)vid[q] * 5 + 2;
+              const float sa = MOVING ? (1.f - tau) * w[q] : w[q];
+              atomicAdd(pa, sa * gnx);
+              atomicAdd(pa + 1, sa * gny);
+              atomicAdd(pa + 2, sa * gnz);
+              if (MOVING) {
+                float* pb = gslot_b + (size_t)vid[q] * 5 + 2;
+                atomicAdd(pb, tau * w[q] * gnx);
+                atomicAdd(pb + 1, tau * w[q] * gny);
+                atomicAdd(pb + 2, tau * w[q] * gnz);
+              }
+            }
+          }
+          // w = N / D -> vertex positions at tau
+          const float sw = w[0] * gw[0] + w[1] * gw[1] + w[2] * gw[2];
+          float ax[3], ay[3], ex[3], ey[3];
+          rel_vertices<MOVING>(r, ps, tau, ax, ay);
+          edge_backward((gw[0] - sw) * invD, (gw[1] - sw) * invD, (gw[2] - sw) * invD, ax, ay, ex, ey);
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            float* pa = gslot_a + (size_t)vid[q] * 5;
+            const float sa = MOVING ? 1.f - tau : 1.f;
+            atomicAdd(pa, sa * ex[q]);
+            atomicAdd(pa + 1, sa * ey[q]);
+            if (MOVING) {
+              float* pb = gslot_b + (size_t)vid[q] * 5;
+              atomicAdd(pb, tau * ex[q]);
+              atomicAdd(pb + 1, tau * ey[q]);
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- slot gradients -> vertices
+// one thread per vertex, looping over slots (no atomics); writes dL/dv and dL/dm (m = normal sum)
+__global__ void slot_chain_kernel(const float* __restrict__ verts, const float* __restrict__ nacc, int V,
+                                  const SlotXform* __restrict__ xf, int n_slots, float th,
+                                  const float* __restrict__ g_slot, float* __restrict__ g_verts,
+                                  float* __restrict__ g_m) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const float px = verts[3 * v], py = verts[3 * v + 1], pz = verts[3 * v + 2];
+  float gvx = 0.f, gvy = 0.f, gvz = 0.f, gnx = 0.f, gny = 0.f, gnz = 0.f;
+  for (int s = 0; s < n_slots; ++s) {
+    const float* g = g_slot + ((size_t)s * V + v) * 5;
+    const float g0 = g[0], g1 = g[1], g2 = g[2], g3 = g[3], g4 = g[4];
+    if (g0 == 0.f && g1 == 0.f && g2 == 0.f && g3 == 0.f && g4 == 0.f) continue;
+    const float* A = xf[s].A;
+    const float* R = xf[s].R;
+    const float xc = fmaf(A[0], px, fmaf(A[1], py, fmaf(A[2], pz, A[3])));
+    const float yc = fmaf(A[4], px, fmaf(A[5], py, fmaf(A[6], pz, A[7])));
+    const float zc = fmaf(A[8], px, fmaf(A[9], py, fmaf(A[10], pz, A[11])));
+    const float den = zc * th;
+    // x = xc / (zc th), y = yc / (zc th)
+    const float dxc = g0 / den, dyc = g1 / den;
+    const float dzc = -(g0 * xc + g1 * yc) / (den * zc);
+    gvx += A[0] * dxc + A[4] * dyc + A[8] * dzc;
+    gvy += A[1] * dxc + A[5] * dyc + A[9] * dzc;
+    gvz += A[2] * dxc + A[6] * dyc + A[10] * dzc;
+    gnx += R[0] * g2 + R[3] * g3 + R[6] * g4;
+    gny += R[1] * g2 + R[4] * g3 + R[7] * g4;
+    gnz += R[2] * g2 + R[5] * g3 + R[8] * g4;
+  }
+  g_verts[3 * v] = gvx;
+  g_verts[3 * v + 1] = gvy;
+  g_verts[3 * v + 2] = gvz;
+  // n = m / |m|: dL/dm = (g - n (n.g)) / |m|
+  const float mx = nacc[3 * v], my = nacc[3 * v + 1], mz = nacc[3 * v + 2];
+  const float len = sqrtf(fmaf(mx, mx, fmaf(my, my, mz * mz)));
+  float ox = 0.f, oy = 0.f, oz = 0.f;
+  if (len > 0.f) {
+    const float il = 1.f / len;
+    const float hx = mx * il, hy = my * il, hz = mz * il;
+    const float hg = hx * gnx + hy * gny + hz * gnz;
+    ox = (gnx - hx * hg) * il;
+    oy = (gny - hy * hg) * il;
+    oz = (gnz - hz * hg) * il;
+  }
+  g_m[3 * v] = ox;
+  g_m[3 * v + 1] = oy;
+  g_m[3 * v + 2] = oz;
+}
+
+// m_v += (b - a) x (c - a) for every face f = (a, b, c):  dL/db = (c - a) x G, dL/dc = G x (b - a)
+__global__ void normals_bwd_kernel(const float* __restrict__ verts, const int32_t* __restrict__ faces, int F, int V,
+                                   const float* __restrict__ g_m, float* __restrict__ g_verts) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  const int a = faces[3 * f], b = faces[3 * f + 1], c = faces[3 * f + 2];
+  if (a < 0 || b < 0 || c < 0 || a >= V || b >= V || c >= V) return;
+  const float Gx = g_m[3 * a] + g_m[3 * b] + g_m[3 * c];
+  const float Gy = g_m[3 * a + 1] + g_m[3 * b + 1] + g_m[3 * c + 1];
+  const float Gz = g_m[3 * a + 2] + g_m[3 * b + 2] + g_m[3 * c + 2];
+  if (Gx == 0.f && Gy == 0.f && Gz == 0.f) return;
+  const float ax = verts[3 * a], ay = verts[3 * a + 1], az = verts[3 * a + 2];
+  const float ux = verts[3 * b] - ax, uy = verts[3 * b + 1] - ay, uz = verts[3 * b + 2] - az;
+  const float wx = verts[3 * c] - ax, wy = verts[3 * c + 1] - ay, wz = verts[3 * c + 2] - az;
+  const float bx = wy * Gz - wz * Gy, by = wz * Gx - wx * Gz, bz = wx * Gy - wy * Gx;
+  const float cx = Gy * uz - Gz * uy, cy = Gz * ux - Gx * uz, cz = Gx * uy - Gy * ux;
+  atomicAdd(g_verts + 3 * b, bx);
+  atomicAdd(g_verts + 3 * b + 1, by);
+  atomicAdd(g_verts + 3 * b + 2, bz);
+  atomicAdd(g_verts + 3 * c, cx);
+  atomicAdd(g_verts + 3 * c + 1, cy);
+  atomicAdd(g_verts + 3 * c + 2, cz);
+  atomicAdd(g_verts + 3 * a, -(bx + cx));
+  atomicAdd(g_verts + 3 * a + 1, -(by + cy));
+  atomicAdd(g_verts + 3 * a + 2, -(bz + cz));
+}
+
+template <int TW, int TH>
+static void launch_raster_bwd_tile(const RasterParams& P, int spt, bool moving, unsigned blocks, cudaStream_t st) {
+  if (!moving) {
+    raster_bwd_kernel<TW, TH, 1, false><<<blocks, TW * TH, 0, st>>>(P);
+  } else if (spt <= 4) {
+    raster_bwd_kernel<TW, TH, 4, true><<<blocks, TW * TH, 0, st>>>(P);
+  } else if (spt <= 8) {
+    raster_bwd_kernel<TW, TH, 8, true><<<blocks, TW * TH, 0, st>>>(P);
+  } else {
+    raster_bwd_kernel<TW, TH, 16, true><<<blocks, TW * TH, 0, st>>>(P);
+  }
+}
+
+void launch_raster_bwd(const RasterParams& P, int tile, int spt, bool moving, cudaStream_t st) {
+  const unsigned blocks = (unsigned)(P.tiles_x * P.tiles_y * P.n_split);
+  if (!blocks) return;
+  if (tile == 8)
+    launch_raster_bwd_tile<8, 8>(P, spt, moving, blocks, st);
+  else
+    launch_raster_bwd_tile<16, 16>(P, spt, moving, blocks, st);
+}
+
+void launch_slot_chain(const float* verts, const float* nacc, int V, const SlotXform* xf, int n_slots, float th,
+                       const float* g_slot, float* g_verts, float* g_m, cudaStream_t st) {
+  if (V > 0) slot_chain_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, nacc, V, xf, n_slots, th, g_slot, g_verts, g_m);
+}
+
+void launch_normals_bwd(const float* verts, const int32_t* faces, int F, int V, const float* g_m, float* g_verts,
+                        cudaStream_t st) {
+  if (F > 0) normals_bwd_kernel<<<(F + 255) / 256, 256, 0, st>>>(verts, faces, F, V, g_m, g_verts);
+}
+
+}  // namespace mbr

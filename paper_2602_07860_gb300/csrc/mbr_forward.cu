@@ -1,0 +1,512 @@
+// mbr_forward.cu -- forward kernels of the sm_103a motion-blurred renderer.
+//
+//   face_normals_kernel  a0: area-weighted vertex normals (face cross products, atomics)
+//   xform_kernel         a1: motion + camera + projection of every vertex at every slot time
+//   setup_kernel         a4 setup: per (record set, face) local-frame coefficients (TriRec)
+//   bin_kernel<FILL>     a3: per (group, face) swept r_soft-dilated bounding box -> tile bins
+//   scan kernels         exclusive scan of the bin counts (CSR offsets)
+//   raster_fwd_kernel    a4-a8: barycentric solve, coverage, z-test, soft alpha, shading,
+//                        temporal average, one float4 store per pixel
+//   finalize_kernel      sums the per-split partial images
+//   count_kernel         N_cand (measurement)
+#include <cstdint>
+
+#include "mbr_internal.h"
+#include "mbr_raster.cuh"
+
+namespace mbr {
+
+// ---------------------------------------------------------------- a0: vertex normals
+__global__ void face_normals_kernel(const float* __restrict__ verts, const int32_t* __restrict__ faces,
+                                    int F, int V, float* __restrict__ nacc, int* __restrict__ status) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  const int a = faces[3 * f], b = faces[3 * f + 1], c = faces[3 * f + 2];
+  if (a < 0 || b < 0 || c < 0 || a >= V || b >= V || c >= V) {
+    atomicOr(status, kStatusBadFace);
+    return;
+  }
+  const float ax = verts[3 * a], ay = verts[3 * a + 1], az = verts[3 * a + 2];
+  const float ux = verts[3 * b] - ax, uy = verts[3 * b + 1] - ay, uz = verts[3 * b + 2] - az;
+  const float wx = verts[3 * c] - ax, wy = verts[3 * c + 1] - ay, wz = verts[3 * c + 2] - az;
+  const float nx = uy * wz - uz * wy, ny = uz * wx - ux * wz, nz = ux * wy - uy * wx;
+  const int id[3] = {a, b, c};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    atomicAdd(nacc + 3 * id[i], nx);
+    atomicAdd(nacc + 3 * id[i] + 1, ny);
+    atomicAdd(nacc + 3 * id[i] + 2, nz);
+  }
+}
+
+// ---------------------------------------------------------------- a1: motion + camera
+// grid.y = slot; camera = A [v;1] with A = view o motion(t_slot); ndc = (x, y) / (z tan).
+__global__ void xform_kernel(const float* __restrict__ verts, const float* __restrict__ nacc, int V,
+                             const SlotXform* __restrict__ xf, float tan_half_fov,
+                             float4* __restrict__ pos, float4* __restrict__ nrm) {
+  __shared__ SlotXform s;
+  const int slot = blockIdx.y;
+  if (threadIdx.x < sizeof(SlotXform) / 4)
+    reinterpret_cast<float*>(&s)[threadIdx.x] = reinterpret_cast<const float*>(xf + slot)[threadIdx.x];
+  __syncthreads();
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const float px = verts[3 * v], py = verts[3 * v + 1], pz = verts[3 * v + 2];
+  const float xc = fmaf(s.A[0], px, fmaf(s.A[1], py, fmaf(s.A[2], pz, s.A[3])));
+  const float yc = fmaf(s.A[4], px, fmaf(s.A[5], py, fmaf(s.A[6], pz, s.A[7])));
+  const float zc = fmaf(s.A[8], px, fmaf(s.A[9], py, fmaf(s.A[10], pz, s.A[11])));
+  const float den = zc * tan_half_fov;
+  float nx = nacc[3 * v], ny = nacc[3 * v + 1], nz = nacc[3 * v + 2];
+  const float len = sqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+  if (len > 0.f) { nx /= len; ny /= len; nz /= len; }
+  const size_t o = (size_t)slot * V + v;
+  pos[o] = make_float4(xc / den, yc / den, zc, 0.f);
+  nrm[o] = make_float4(fmaf(s.R[0], nx, fmaf(s.R[1], ny, s.R[2] * nz)),
+                       fmaf(s.R[3], nx, fmaf(s.R[4], ny, s.R[5] * nz)),
+                       fmaf(s.R[6], nx, fmaf(s.R[7], ny, s.R[8] * nz)), 0.f);
+}
+
+// ---------------------------------------------------------------- a4 setup: triangle records
+__global__ void setup_kernel(const float4* __restrict__ pos, const int32_t* __restrict__ faces, int F,
+                             int V, const int2* __restrict__ set_slots, int n_sets, float znear,
+                             TriRec* __restrict__ recs) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n_sets * F) return;
+  const int set = (int)(idx / F), f = (int)(idx - (size_t)set * F);
+  const int2 sl = set_slots[set];
+  const int i0 = faces[3 * f], i1 = faces[3 * f + 1], i2 = faces[3 * f + 2];
+  if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= V || i1 >= V || i2 >= V) {
+    // invalid face: culled (never binned, never dereferenced again)
+    TriRec* dst = recs + idx;
+    dst->f4[1] = make_float4(0.f, 0.f, 0.f, __int_as_float(f));
+    dst->f4[2] = make_float4(1.f, 1.f, 1.f, __uint_as_float(kFlagCulled));
+    return;
+  }
+  const float4 a0 = pos[(size_t)sl.x * V + i0], a1 = pos[(size_t)sl.x * V + i1], a2 = pos[(size_t)sl.x * V + i2];
+  const float4 b0 = pos[(size_t)sl.y * V + i0], b1 = pos[(size_t)sl.y * V + i1], b2 = pos[(size_t)sl.y * V + i2];
+  const float e1x = a1.x - a0.x, e1y = a1.y - a0.y, e2x = a2.x - a0.x, e2y = a2.y - a0.y;
+  const float d1x = (b1.x - b0.x) - e1x, d1y = (b1.y - b0.y) - e1y;
+  const float d2x = (b2.x - b0.x) - e2x, d2y = (b2.y - b0.y) - e2y;
+  const float gx = b0.x - a0.x, gy = b0.y - a0.y;
+  uint32_t flags = 0;
+  if (a0.z <= znear || a1.z <= znear || a2.z <= znear || b0.z <= znear || b1.z <= znear || b2.z <= znear)
+    flags |= kFlagCulled;
+  TriRec r;
+  r.f4[0] = make_float4(a0.x, a0.y, e1x, e1y);
+  r.f4[1] = make_float4(e2x, e2y, cross2(e1x, e1y, e2x, e2y), __int_as_float(f));
+  r.f4[2] = make_float4(a0.z, a1.z, a2.z, __uint_as_float(flags));
+  r.f4[3] = make_float4(d1x, d1y, d2x, d2y);
+  r.f4[4] = make_float4(gx, gy, -cross2(gx, gy, e2x, e2y), -cross2(e1x, e1y, gx, gy));
+  r.f4[5] = make_float4(-cross2(gx, gy, d2x, d2y), -cross2(d1x, d1y, gx, gy),
+                        cross2(e1x, e1y, d2x, d2y) + cross2(d1x, d1y, e2x, e2y), cross2(d1x, d1y, d2x, d2y));
+  r.f4[6] = make_float4(b0.z - a0.z, b1.z - a1.z, b2.z - a2.z, 0.f);
+  TriRec* dst = recs + idx;
+#pragma unroll
+  for (int q = 0; q < kRecF4; ++q) dst->f4[q] = r.f4[q];
+}
+
+// swept bounding box of a record over [tau_lo, tau_hi] (linear motion: union of the two ends)
+__device__ __forceinline__ void swept_bbox(const TriRec& r, float tlo, float thi, float& xmin,
+                                           float& xmax, float& ymin, float& ymax) {
+  const float ox = r.f4[0].x, oy = r.f4[0].y;
+  const float e1x = r.f4[0].z, e1y = r.f4[0].w, e2x = r.f4[1].x, e2y = r.f4[1].y;
+  const float d1x = r.f4[3].x, d1y = r.f4[3].y, d2x = r.f4[3].z, d2y = r.f4[3].w;
+  const float gx = r.f4[4].x, gy = r.f4[4].y;
+  xmin = ymin = INFINITY;
+  xmax = ymax = -INFINITY;
+  const float ts[2] = {tlo, thi};
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const float t = ts[q];
+    const float v0x = fmaf(t, gx, ox), v0y = fmaf(t, gy, oy);
+    const float v1x = v0x + fmaf(t, d1x, e1x), v1y = v0y + fmaf(t, d1y, e1y);
+    const float v2x = v0x + fmaf(t, d2x, e2x), v2y = v0y + fmaf(t, d2y, e2y);
+    xmin = fminf(xmin, fminf(v0x, fminf(v1x, v2x)));
+    xmax = fmaxf(xmax, fmaxf(v0x, fmaxf(v1x, v2x)));
+    ymin = fminf(ymin, fminf(v0y, fminf(v1y, v2y)));
+    ymax = fmaxf(ymax, fmaxf(v0y, fmaxf(v1y, v2y)));
+  }
+}
+
+// pixel index ranges of the centres inside [xmin, xmax] x [ymin, ymax]; false if empty
+__device__ __forceinline__ bool pixel_range(float xmin, float xmax, float ymin, float ymax, int W, int H,
+                                            int& i0, int& i1, int& j0, int& j1) {
+  i0 = max(0, (int)ceilf((xmin + 1.f) * 0.5f * W - 0.5f));
+  i1 = min(W - 1, (int)floorf((xmax + 1.f) * 0.5f * W - 0.5f));
+  j0 = max(0, (int)ceilf((1.f - ymax) * 0.5f * H - 0.5f));
+  j1 = min(H - 1, (int)floorf((1.f - ymin) * 0.5f * H - 0.5f));
+  return i0 <= i1 && j0 <= j1 && isfinite(xmin) && isfinite(ymin);
+}
+
+// ---------------------------------------------------------------- a3: tile binning
+template <bool FILL>
+__global__ void bin_kernel(const TriRec* __restrict__ recs, int F, const Group* __restrict__ groups,
+                           int G, int W, int H, int tw, int th, int tiles_x, int n_tiles, float r,
+                           int32_t* __restrict__ counts_or_cursor, int32_t* __restrict__ list,
+                           const int32_t* __restrict__ bin_end, int* __restrict__ status) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)G * F) return;
+  const int g = (int)(idx / F), f = (int)(idx - (size_t)g * F);
+  const Group& gr = groups[g];
+  const TriRec& rec = recs[(size_t)gr.rec_set * F + f];
+  if (__float_as_uint(rec.f4[2].w) & kFlagCulled) return;
+  float xmin, xmax, ymin, ymax;
+  swept_bbox(rec, gr.tau_lo, gr.tau_hi, xmin, xmax, ymin, ymax);
+  int i0, i1, j0, j1;
+  if (!pixel_range(xmin - r, xmax + r, ymin - r, ymax + r, W, H, i0, i1, j0, j1)) return;
+  const int tx0 = i0 / tw, tx1 = i1 / tw, ty0 = j0 / th, ty1 = j1 / th;
+  int32_t* base = counts_or_cursor + (size_t)g * n_tiles;
+  for (int ty = ty0; ty <= ty1; ++ty)
+    for (int tx = tx0; tx <= tx1; ++tx) {
+      const int b = ty * tiles_x + tx;
+      const int slot = atomicAdd(base + b, 1);
+      if (FILL) {
+        // the fill pass revisits exactly the counted (group, face, tile) triples; the check
+        // only guards the list against a mismatch
+        if (slot < bin_end[(size_t)g * n_tiles + b + 1]) list[slot] = f;
+        else atomicOr(status, kStatusBinOverflow);
+      }
+    }
+}
+
+// ---------------------------------------------------------------- exclusive scan (CSR offsets)
+constexpr int kScanThreads = 1024, kScanPer = 4, kScanBlock = kScanThreads * kScanPer;
+
+__device__ __forceinline__ int block_exclusive_scan(int x, int* s_warp, int& total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    s_warp[lane] = wi - w;
+    if (lane == 31) s_warp[32] = wi;
+  }
+  __syncthreads();
+  total = s_warp[32];
+  const int r = s_warp[wid] + incl - x;
+  __syncthreads();
+  return r;
+}
+
+__global__ void scan_reduce_kernel(const int32_t* __restrict__ in, int n, int32_t* __restrict__ sums) {
+  __shared__ int s_warp[33];
+  const size_t base = (size_t)blockIdx.x * kScanBlock + (size_t)threadIdx.x * kScanPer;
+  int x = 0;
+#pragma unroll
+  for (int q = 0; q < kScanPer; ++q)
+    if (base + q < (size_t)n) x += in[base + q];
+  int total;
+  block_exclusive_scan(x, s_warp, total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void scan_sums_kernel(int32_t* __restrict__ sums, int nb) {
+  __shared__ int s_warp[33];
+  int carry = 0;
+  for (int c = 0; c < nb; c += kScanThreads) {
+    const int i = c + threadIdx.x;
+    const int x = i < nb ? sums[i] : 0;
+    int total;
+    const int ex = block_exclusive_scan(x, s_warp, total);
+    if (i < nb) sums[i] = ex + carry;
+    carry += total;
+  }
+  if (threadIdx.x == 0) sums[nb] = carry;
+}
+
+__global__ void scan_apply_kernel(const int32_t* __restrict__ in, int n, const int32_t* __restrict__ sums,
+                                  int32_t* __restrict__ out) {
+  __shared__ int s_warp[33];
+  const size_t base = (size_t)blockIdx.x * kScanBlock + (size_t)threadIdx.x * kScanPer;
+  int v[kScanPer];
+  int x = 0;
+#pragma unroll
+  for (int q = 0; q < kScanPer; ++q) {
+    v[q] = base + q < (size_t)n ? in[base + q] : 0;
+    x += v[q];
+  }
+  int total;
+  int ex = block_exclusive_scan(x, s_warp, total) + sums[blockIdx.x];
+#pragma unroll
+  for (int q = 0; q < kScanPer; ++q) {
+    if (base + q < (size_t)n) out[base + q] = ex;
+    ex += v[q];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = sums[gridDim.x];
+}
+
+// ---------------------------------------------------------------- a4-a8: forward raster
+template <int TW, int TH, int SPT, bool MOVING>
+__global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(RasterParams P) {
+  constexpr int NT = TW * TH;
+  __shared__ float4 s_rec[kStageCap * kRecF4];
+  __shared__ Group s_grp;
+  const int n_tiles = P.tiles_x * P.tiles_y;
+  const int tile = blockIdx.x % n_tiles, split = blockIdx.x / n_tiles;
+  const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
+  const int px = tx * TW + (int)(threadIdx.x % TW), py = ty * TH + (int)(threadIdx.x / TW);
+  const bool in_img = px < P.W && py < P.H;
+  const float u = (2.f * px + 1.f) / P.W - 1.f;
+  const float v = 1.f - (2.f * py + 1.f) / P.H;
+  const int g_begin = (int)((long long)P.G * split / P.n_split);
+  const int g_end = (int)((long long)P.G * (split + 1) / P.n_split);
+  float acc_r = 0.f, acc_g = 0.f, acc_b = 0.f, acc_a = 0.f;
+
+  for (int g = g_begin; g < g_end; ++g) {
+    __syncthreads();
+    if (threadIdx.x < sizeof(Group) / 4)
+      reinterpret_cast<int*>(&s_grp)[threadIdx.x] = reinterpret_cast<const int*>(P.groups + g)[threadIdx.x];
+    __syncthreads();
+    const int n = s_grp.n;
+    const TriRec* recs_set = P.recs + (size_t)s_grp.rec_set * P.F;
+    const int beg = P.bin_off[(size_t)g * n_tiles + tile], end = P.bin_off[(size_t)g * n_tiles + tile + 1];
+    float bestk[SPT];
+    int bestf[SPT];
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) { bestk[i] = -INFINITY; bestf[i] = -1; }
+
+    // ---- pass 1: coverage + z-test (Sec. 3.1) with w(tau) of Eq. time-dependent2
+    for (int c0 = beg; c0 < end; c0 += kStageCap) {
+      const int cnt = min(kStageCap, end - c0);
+      __syncthreads();
+      stage_records<NT, MOVING>(s_rec, recs_set, P.bin_faces + c0, cnt);
+      __syncthreads();
+      if (in_img) {
+        for (int j = 0; j < cnt; ++j) {
+          const float4* r = s_rec + j * kRecF4;
+          const int face = __float_as_int(r[1].w);
+          const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
+#pragma unroll
+          for (int i = 0; i < SPT; ++i) {
+            if (i < n) {
+              const float tau = s_grp.tau[i];
+              const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
+              if (covers(e)) {
+                const float key = inv_depth<MOVING>(r, e, tau);
+                if (key > bestk[i] || (key == bestk[i] && face < bestf[i])) {
+                  bestk[i] = key;
+                  bestf[i] = face;
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+
+    // ---- pass 2: soft coverage of uncovered samples (Eqs. probability-function .. back)
+    bool any_unc = false;
+#pragma unroll
+    for (int i = 0; i < SPT; ++i)
+      if (i < n && bestf[i] < 0) any_unc = true;
+    float prod[SPT];
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) prod[i] = 1.f;
+    if (__syncthreads_or(in_img && any_unc && end > beg)) {
+      for (int c0 = beg; c0 < end; c0 += kStageCap) {
+        const int cnt = min(kStageCap, end - c0);
+        __syncthreads();
+        stage_records<NT, MOVING>(s_rec, recs_set, P.bin_faces + c0, cnt);
+        __syncthreads();
+        if (in_img && any_unc) {
+          for (int j = 0; j < cnt; ++j) {
+            const float4* r = s_rec + j * kRecF4;
+            const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
+#pragma unroll
+            for (int i = 0; i < SPT; ++i) {
+              if (i < n && bestf[i] < 0) {
+                const float tau = s_grp.tau[i];
+                const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
+                if (fabsf(e.D) > kDetMin) {
+                  const SoftGeom sg = soft_geom<MOVING>(r, ps, e, tau, (s_grp.xbits >> i) & 1u);
+                  if (sg.d <= P.r2) prod[i] *= -expm1f(-sg.d * P.inv_delta);
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+
+    // ---- shading of the winners (Eq. fore + Lambert) and temporal accumulation (Sec. 3.3)
+    if (in_img) {
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) {
+        if (i < n) {
+          const int f = bestf[i];
+          if (P.dbg_ids && s_grp.k0 + i == P.dbg_k) P.dbg_ids[(size_t)py * P.W + px] = f;
+          if (f >= 0) {
+            const float tau = s_grp.tau[i];
+            float4 r[kRecF4];
+            const TriRec* src = recs_set + f;
+#pragma unroll
+            for (int q = 0; q < (MOVING ? kRecF4 : 3); ++q) r[q] = __ldg(&src->f4[q]);
+            const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
+            const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
+            const float invD = 1.0f / e.D;
+            const float w[3] = {e.N0 * invD, e.N1 * invD, e.N2 * invD};
+            float cr = 0.f, cg = 0.f, cb = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              const int vid = __ldg(P.faces + 3 * f + q);
+              cr = fmaf(w[q], __ldg(P.albedo + 3 * vid), cr);
+              cg = fmaf(w[q], __ldg(P.albedo + 3 * vid + 1), cg);
+              cb = fmaf(w[q], __ldg(P.albedo + 3 * vid + 2), cb);
+              float4 na = __ldg(P.slot_nrm + (size_t)s_grp.slot_a * P.V + vid);
+              if (MOVING) {
+                const float4 nb = __ldg(P.slot_nrm + (size_t)s_grp.slot_b * P.V + vid);
+                na.x = fmaf(tau, nb.x - na.x, na.x);
+                na.y = fmaf(tau, nb.y - na.y, na.y);
+                na.z = fmaf(tau, nb.z - na.z, na.z);
+              }
+              nx = fmaf(w[q], na.x, nx);
+              ny = fmaf(w[q], na.y, ny);
+              nz = fmaf(w[q], na.z, nz);
+            }
+            const float len = sqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+            const float dot = len > 0.f ? fmaf(nx, P.lx, fmaf(ny, P.ly, nz * P.lz)) / len : 0.f;
+            const float shade = fmaf(P.kd, fmaxf(dot, 0.f), P.ka);
+            acc_r = fmaf(cr, shade, acc_r);
+            acc_g = fmaf(cg, shade, acc_g);
+            acc_b = fmaf(cb, shade, acc_b);
+            acc_a += 1.f;
+          } else {
+            acc_a += 1.f - prod[i];
+          }
+        }
+      }
+    }
+  }
+  if (in_img) {
+    const size_t o = (size_t)py * P.W + px;
+    if (P.n_split == 1)
+      P.out[o] = make_float4(acc_r * P.inv_T, acc_g * P.inv_T, acc_b * P.inv_T, acc_a * P.inv_T);
+    else
+      P.out[(size_t)split * P.H * P.W + o] = make_float4(acc_r, acc_g, acc_b, acc_a);
+  }
+}
+
+__global__ void finalize_kernel(const float4* __restrict__ partial, int n_split, size_t npix, float inv_T,
+                                float4* __restrict__ image) {
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npix) return;
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int q = 0; q < n_split; ++q) {
+    const float4 x = partial[(size_t)q * npix + p];
+    s.x += x.x; s.y += x.y; s.z += x.z; s.w += x.w;
+  }
+  image[p] = make_float4(s.x * inv_T, s.y * inv_T, s.z * inv_T, s.w * inv_T);
+}
+
+// ---------------------------------------------------------------- N_cand (measurement)
+__global__ void count_kernel(const TriRec* __restrict__ recs, int F, const Group* __restrict__ groups, int G,
+                             int W, int H, float r, unsigned long long* __restrict__ out) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long c = 0;
+  if (idx < (size_t)G * F) {
+    const int g = (int)(idx / F), f = (int)(idx - (size_t)g * F);
+    const Group& gr = groups[g];
+    const TriRec& rec = recs[(size_t)gr.rec_set * F + f];
+    const bool culled = (__float_as_uint(rec.f4[2].w) & kFlagCulled) != 0;
+    for (int i = 0; i < gr.n && !culled; ++i) {
+      float xmin, xmax, ymin, ymax;
+      swept_bbox(rec, gr.tau[i], gr.tau[i], xmin, xmax, ymin, ymax);
+      int i0, i1, j0, j1;
+      if (pixel_range(xmin - r, xmax + r, ymin - r, ymax + r, W, H, i0, i1, j0, j1))
+        c += (unsigned long long)(i1 - i0 + 1) * (unsigned long long)(j1 - j0 + 1);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+// ---------------------------------------------------------------- launch wrappers
+void launch_face_normals(const float* verts, const int32_t* faces, int F, int V, float* nacc, int* status,
+                         cudaStream_t st) {
+  if (F > 0) face_normals_kernel<<<(F + 255) / 256, 256, 0, st>>>(verts, faces, F, V, nacc, status);
+}
+
+void launch_xform(const float* verts, const float* nacc, int V, const SlotXform* xf, int n_slots, float th,
+                  float4* pos, float4* nrm, cudaStream_t st) {
+  dim3 grid((V + 255) / 256, n_slots);
+  xform_kernel<<<grid, 256, 0, st>>>(verts, nacc, V, xf, th, pos, nrm);
+}
+
+void launch_setup(const float4* pos, const int32_t* faces, int F, int V, const int2* set_slots, int n_sets,
+                  float znear, TriRec* recs, cudaStream_t st) {
+  const size_t n = (size_t)n_sets * F;
+  if (n) setup_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pos, faces, F, V, set_slots, n_sets, znear, recs);
+}
+
+void launch_bin(bool fill, const TriRec* recs, int F, const Group* groups, int G, int W, int H, int tw, int th,
+                int tiles_x, int n_tiles, float r, int32_t* counts_or_cursor, int32_t* list,
+                const int32_t* bin_off, int* status, cudaStream_t st) {
+  const size_t n = (size_t)G * F;
+  if (!n) return;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (fill)
+    bin_kernel<true><<<blocks, 256, 0, st>>>(recs, F, groups, G, W, H, tw, th, tiles_x, n_tiles, r, counts_or_cursor,
+                                             list, bin_off, status);
+  else
+    bin_kernel<false><<<blocks, 256, 0, st>>>(recs, F, groups, G, W, H, tw, th, tiles_x, n_tiles, r, counts_or_cursor,
+                                              list, bin_off, status);
+}
+
+size_t scan_temp_ints(int n) { return (size_t)(n + kScanBlock - 1) / kScanBlock + 1; }
+
+void launch_scan(const int32_t* in, int n, int32_t* out, int32_t* temp, cudaStream_t st) {
+  const int nb = (n + kScanBlock - 1) / kScanBlock;
+  if (nb == 0) {
+    cudaMemsetAsync(out, 0, sizeof(int32_t), st);
+    return;
+  }
+  scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(in, n, temp);
+  scan_sums_kernel<<<1, kScanThreads, 0, st>>>(temp, nb);
+  scan_apply_kernel<<<nb, kScanThreads, 0, st>>>(in, n, temp, out);
+}
+
+template <int TW, int TH>
+static void launch_raster_fwd_tile(const RasterParams& P, int spt, bool moving, unsigned blocks, cudaStream_t st) {
+  if (!moving) {
+    raster_fwd_kernel<TW, TH, 1, false><<<blocks, TW * TH, 0, st>>>(P);
+  } else if (spt <= 4) {
+    raster_fwd_kernel<TW, TH, 4, true><<<blocks, TW * TH, 0, st>>>(P);
+  } else if (spt <= 8) {
+    raster_fwd_kernel<TW, TH, 8, true><<<blocks, TW * TH, 0, st>>>(P);
+  } else {
+    raster_fwd_kernel<TW, TH, 16, true><<<blocks, TW * TH, 0, st>>>(P);
+  }
+}
+
+void launch_raster_fwd(const RasterParams& P, int tile, int spt, bool moving, cudaStream_t st) {
+  const unsigned blocks = (unsigned)(P.tiles_x * P.tiles_y * P.n_split);
+  if (!blocks) return;
+  if (tile == 8)
+    launch_raster_fwd_tile<8, 8>(P, spt, moving, blocks, st);
+  else
+    launch_raster_fwd_tile<16, 16>(P, spt, moving, blocks, st);
+}
+
+void launch_finalize(const float4* partial, int n_split, size_t npix, float inv_T, float4* image, cudaStream_t st) {
+  if (npix) finalize_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(partial, n_split, npix, inv_T, image);
+}
+
+void launch_count(const TriRec* recs, int F, const Group* groups, int G, int W, int H, float r,
+                  unsigned long long* out, cudaStream_t st) {
+  const size_t n = (size_t)G * F;
+  if (n) count_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(recs, F, groups, G, W, H, r, out);
+}
+
+}  // namespace mbr

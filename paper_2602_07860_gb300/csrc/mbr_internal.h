@@ -1,0 +1,35 @@
+// mbr_internal.h -- launch wrappers shared between the kernel translation units and the C ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mbr_common.cuh"
+
+namespace mbr {
+
+struct RasterParams;
+
+void launch_face_normals(const float* verts, const int32_t* faces, int F, int V, float* nacc, int* status,
+                         cudaStream_t st);
+void launch_xform(const float* verts, const float* nacc, int V, const SlotXform* xf, int n_slots, float th,
+                  float4* pos, float4* nrm, cudaStream_t st);
+void launch_setup(const float4* pos, const int32_t* faces, int F, int V, const int2* set_slots, int n_sets,
+                  float znear, TriRec* recs, cudaStream_t st);
+void launch_bin(bool fill, const TriRec* recs, int F, const Group* groups, int G, int W, int H, int tw, int th,
+                int tiles_x, int n_tiles, float r, int32_t* counts_or_cursor, int32_t* list,
+                const int32_t* bin_off, int* status, cudaStream_t st);
+size_t scan_temp_ints(int n);
+void launch_scan(const int32_t* in, int n, int32_t* out, int32_t* temp, cudaStream_t st);
+void launch_raster_fwd(const RasterParams& P, int tile, int spt, bool moving, cudaStream_t st);
+void launch_finalize(const float4* partial, int n_split, size_t npix, float inv_T, float4* image, cudaStream_t st);
+void launch_count(const TriRec* recs, int F, const Group* groups, int G, int W, int H, float r,
+                  unsigned long long* out, cudaStream_t st);
+
+void launch_raster_bwd(const RasterParams& P, int tile, int spt, bool moving, cudaStream_t st);
+void launch_slot_chain(const float* verts, const float* nacc, int V, const SlotXform* xf, int n_slots, float th,
+                       const float* g_slot, float* g_verts, float* g_m, cudaStream_t st);
+void launch_normals_bwd(const float* verts, const int32_t* faces, int F, int V, const float* g_m, float* g_verts,
+                        cudaStream_t st);
+
+}  // namespace mbr

@@ -1,0 +1,229 @@
+"""PyTorch-facing API of the motion-blurred renderer: device tensors in, device tensors out, the
+caller's current CUDA stream, and a ``torch.autograd.Function`` whose backward is the library's
+hand-written adjoint.  PyTorch supplies device memory and streams only; all arithmetic of the
+renderer runs in the CUDA kernels behind the C ABI."""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import MbrCamera, MbrError, MbrItem, MbrMesh, MbrMotion
+
+
+@dataclass
+class Motion:
+    kind: str = "translate"          # 'translate' | 'rotate'
+    offset: tuple = (0.0, 0.0, 0.0)
+    dir: tuple = (0.0, 0.0, 0.0)
+    axis: tuple = (0.0, 1.0, 0.0)
+    omega: float = 0.0
+    segments: int = 0
+
+    def c(self):
+        m = MbrMotion()
+        m.kind = _lib.MBR_TRANSLATE if self.kind == "translate" else _lib.MBR_ROTATE
+        m.segments = int(self.segments)
+        m.offset[:] = [float(x) for x in self.offset]
+        m.dir[:] = [float(x) for x in self.dir]
+        m.axis[:] = [float(x) for x in self.axis]
+        m.omega = float(self.omega)
+        return m
+
+
+@dataclass
+class Camera:
+    view: tuple                      # 12 floats, 3x4 row-major world->camera
+    tan_half_fov: float
+    znear: float = 0.1
+    light_dir: tuple = (0.4, 0.6, -0.7)
+    k_ambient: float = 0.3
+    k_diffuse: float = 0.7
+    delta: float = 1e-4
+    time_rule: str = "paper"         # 'paper' | 'midpoint'
+
+    def c(self):
+        c = MbrCamera()
+        c.view[:] = [float(x) for x in np.asarray(self.view, dtype=np.float64).reshape(-1)]
+        c.tan_half_fov = float(self.tan_half_fov)
+        c.znear = float(self.znear)
+        c.light_dir[:] = [float(x) for x in self.light_dir]
+        c.k_ambient = float(self.k_ambient)
+        c.k_diffuse = float(self.k_diffuse)
+        c.delta = float(self.delta)
+        c.time_rule = _lib.MBR_TIME_PAPER if self.time_rule == "paper" else _lib.MBR_TIME_MIDPOINT
+        return c
+
+
+def motion_from_dict(m):
+    return Motion(kind=m["kind"], offset=tuple(m["offset"]), dir=tuple(m["dir"]), axis=tuple(m["axis"]),
+                  omega=float(m["omega"]), segments=int(m.get("segments", 0)))
+
+
+def camera_from_dict(c):
+    return Camera(view=tuple(np.asarray(c["view"]).reshape(-1)), tan_half_fov=c["tan_half_fov"], znear=c["znear"],
+                  light_dir=tuple(c["light_dir"]), k_ambient=c["k_ambient"], k_diffuse=c["k_diffuse"],
+                  delta=c["delta"], time_rule=c.get("time_rule", "paper"))
+
+
+def mesh_tensors(scene, device="cuda"):
+    """(verts f32 [V,3], faces i32 [F,3], albedo f32 [V,3]) on ``device`` from a scene dict."""
+    v = torch.as_tensor(np.asarray(scene["verts"], dtype=np.float32), device=device).contiguous()
+    f = torch.as_tensor(np.asarray(scene["faces"], dtype=np.int32), device=device).contiguous()
+    a = torch.as_tensor(np.asarray(scene["albedo"], dtype=np.float32), device=device).contiguous()
+    return v, f, a
+
+
+def _check(t, dtype, shape, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous() or tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected contiguous {dtype} {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """Owns one library context (scratch memory) on the current CUDA device."""
+
+    def __init__(self):
+        self.L = _lib.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("the motion-blur renderer needs a CUDA device (no CPU fallback)")
+        torch.cuda.init()
+        h = ctypes.c_void_p()
+        rc = self.L.mbr_create(ctypes.byref(h))
+        if rc != _lib.MBR_OK:
+            raise MbrError(rc, "mbr_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.mbr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _raise(self, rc):
+        if rc != _lib.MBR_OK:
+            raise MbrError(rc, self.L.mbr_last_error(self.h).decode())
+
+    @staticmethod
+    def _mesh(verts, faces, albedo):
+        V, F = verts.shape[0], faces.shape[0]
+        _check(verts, torch.float32, (V, 3), "verts")
+        _check(faces, torch.int32, (F, 3), "faces")
+        _check(albedo, torch.float32, (V, 3), "albedo")
+        m = MbrMesh()
+        m.V, m.F = V, F
+        m.verts, m.faces, m.albedo = verts.data_ptr(), faces.data_ptr(), albedo.data_ptr()
+        return m
+
+    def set_tuning(self, tile=16, spt=8, splits=0):
+        self._raise(self.L.mbr_set_tuning(self.h, int(tile), int(spt), int(splits)))
+
+    def render_blur(self, verts, faces, albedo, motion: Motion, camera: Camera, T, H, W, solver="fast", out=None):
+        m = self._mesh(verts, faces, albedo)
+        if out is None:
+            out = torch.empty((H, W, 4), dtype=torch.float32, device=verts.device)
+        _check(out, torch.float32, (H, W, 4), "image")
+        mo, ca = motion.c(), camera.c()
+        self._raise(self.L.mbr_render_blur(self.h, ctypes.byref(m), ctypes.byref(mo), ctypes.byref(ca), T, H, W,
+                                           _lib.SOLVERS[solver], ctypes.c_void_p(out.data_ptr()), _stream()))
+        return out
+
+    def render_blur_backward(self, verts, faces, albedo, motion, camera, T, H, W, dl_dimage, solver="fast",
+                             want_albedo=True):
+        m = self._mesh(verts, faces, albedo)
+        _check(dl_dimage, torch.float32, (H, W, 4), "dl_dimage")
+        gv = torch.empty_like(verts)
+        ga = torch.empty_like(albedo) if want_albedo else None
+        mo, ca = motion.c(), camera.c()
+        self._raise(self.L.mbr_render_blur_backward(
+            self.h, ctypes.byref(m), ctypes.byref(mo), ctypes.byref(ca), T, H, W, _lib.SOLVERS[solver],
+            ctypes.c_void_p(dl_dimage.data_ptr()), ctypes.c_void_p(gv.data_ptr()),
+            ctypes.c_void_p(ga.data_ptr() if ga is not None else 0), _stream()))
+        return gv, ga
+
+    def debug_winners(self, verts, faces, albedo, motion, camera, T, H, W, k, solver="fast"):
+        m = self._mesh(verts, faces, albedo)
+        ids = torch.empty((H, W), dtype=torch.int32, device=verts.device)
+        mo, ca = motion.c(), camera.c()
+        self._raise(self.L.mbr_debug_winners(self.h, ctypes.byref(m), ctypes.byref(mo), ctypes.byref(ca), T, H, W,
+                                             _lib.SOLVERS[solver], int(k), ctypes.c_void_p(ids.data_ptr()),
+                                             _stream()))
+        return ids
+
+    def count_candidates(self, verts, faces, albedo, motion, camera, T, H, W, solver="fast"):
+        m = self._mesh(verts, faces, albedo)
+        out = ctypes.c_int64()
+        mo, ca = motion.c(), camera.c()
+        self._raise(self.L.mbr_count_candidates(self.h, ctypes.byref(m), ctypes.byref(mo), ctypes.byref(ca), T, H,
+                                                W, _lib.SOLVERS[solver], ctypes.byref(out), _stream()))
+        return out.value
+
+    def render_batch(self, items, with_backward=False):
+        """items: list of dicts(verts, faces, albedo, motion, camera, T, H, W, solver, image,
+        [dl_dimage, dl_dverts, dl_dalbedo]) with preallocated CUDA tensors."""
+        arr = (MbrItem * len(items))()
+        keep = []
+        for i, it in enumerate(items):
+            a = arr[i]
+            a.mesh = self._mesh(it["verts"], it["faces"], it["albedo"])
+            a.motion = it["motion"].c()
+            a.camera = it["camera"].c()
+            a.T, a.H, a.W = it["T"], it["H"], it["W"]
+            a.solver = _lib.SOLVERS[it.get("solver", "fast")]
+            a.image = it["image"].data_ptr()
+            if with_backward:
+                a.dl_dimage = it["dl_dimage"].data_ptr()
+                a.dl_dverts = it["dl_dverts"].data_ptr()
+                a.dl_dalbedo = it["dl_dalbedo"].data_ptr() if it.get("dl_dalbedo") is not None else 0
+            keep.append(it)
+        self._raise(self.L.mbr_render_blur_batch(self.h, len(items), arr, int(bool(with_backward)), _stream()))
+
+
+_default_ctx = {}
+
+
+def default_context():
+    dev = torch.cuda.current_device()
+    if dev not in _default_ctx:
+        _default_ctx[dev] = Context()
+    return _default_ctx[dev]
+
+
+class RenderBlur(torch.autograd.Function):
+    """image = render_blur(verts, albedo); backward gives dL/dverts and dL/dalbedo through the
+    library's adjoint kernels (sub-frame state recomputed, not stored)."""
+
+    @staticmethod
+    def forward(ctx, verts, albedo, faces, motion, camera, T, H, W, solver, rctx):
+        verts = verts.contiguous()
+        albedo = albedo.contiguous()
+        img = rctx.render_blur(verts, faces, albedo, motion, camera, T, H, W, solver)
+        ctx.save_for_backward(verts, albedo, faces)
+        ctx.args = (motion, camera, T, H, W, solver, rctx)
+        return img
+
+    @staticmethod
+    def backward(ctx, g):
+        verts, albedo, faces = ctx.saved_tensors
+        motion, camera, T, H, W, solver, rctx = ctx.args
+        gv, ga = rctx.render_blur_backward(verts, faces, albedo, motion, camera, T, H, W, g.contiguous(), solver,
+                                           want_albedo=ctx.needs_input_grad[1])
+        return gv, ga, None, None, None, None, None, None, None, None
+
+
+def render_blur(verts, albedo, faces, motion, camera, T, H, W, solver="fast", rctx=None):
+    """Differentiable blurred render [H,W,4] of the mesh (see include/mbr.h)."""
+    return RenderBlur.apply(verts, albedo, faces, motion, camera, T, H, W, solver, rctx or default_context())

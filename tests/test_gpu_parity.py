@@ -1,0 +1,144 @@
+"""CUDA path vs the FP64 oracle, element by element, on seeded scenes (GPU required).
+
+Bound: |gpu - oracle| <= 1e-4 absolute per channel on every pixel none of whose samples the
+oracle flags as ambiguous for FP32 (within 2e-6 NDC of a triangle boundary, inverse-depth gap
+below 2e-5 relative, near-degenerate triangle, or a fast-mode closest-edge tie); flagged pixels
+may differ by at most (flagged samples)/T.  z-test winner ids are bit-exact on unflagged samples.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import scenes
+from gpu_util import ORACLE_MODE, TOL, compare_images, gpu_inputs, gpu_render
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2602_07860_gb300 as mbr
+    return mbr.Context()
+
+
+def _check(ctx, sc, solver, max_flag_frac=0.05):
+    r = oracle.render(sc, ORACLE_MODE[solver], ambig=True)
+    g = gpu_render(ctx, sc, solver)
+    assert np.isfinite(g).all()
+    max_clean, frac, excess = compare_images(g, r["rgba"], r["ambig"], sc["T"])
+    assert max_clean <= TOL, (max_clean, frac)
+    assert excess <= 0.0, (excess, frac)
+    assert frac <= max_flag_frac, frac
+    return r, g
+
+
+SCENES = {
+    "c1_translate_64": lambda: scenes.config1(),
+    "rotate_ragged_72x40": lambda: scenes.small_scene("rotate", subdiv=2, T=8, H=40, W=72),
+    "translate_depth_motion": lambda: scenes.small_scene("translate", subdiv=2, T=12, H=48, W=56, d=(0.9, -0.3, 1.1)),
+    "rotate_midpoint": lambda: scenes.small_scene("rotate", subdiv=3, T=10, H=50, W=66, time_rule="midpoint"),
+    "rotate_fast_spin_S_gt_T": lambda: scenes.small_scene("rotate", subdiv=2, T=5, H=36, W=36, omega=6 * math.pi),
+    "subdiv4_sh_96x80": lambda: scenes.config2(T=16, H=80, W=96),
+    "single_subframe": lambda: scenes.small_scene("rotate", subdiv=2, T=1, H=33, W=47),
+}
+
+
+@pytest.mark.parametrize("solver", ["plain", "fast"])
+@pytest.mark.parametrize("name", sorted(SCENES))
+def test_forward_matches_oracle(ctx, name, solver):
+    _check(ctx, SCENES[name](), solver)
+
+
+@pytest.mark.parametrize("solver", ["plain", "fast"])
+def test_winner_ids_bit_exact(ctx, solver):
+    sc = scenes.small_scene("rotate", subdiv=3, T=6, H=44, W=52)
+    r = oracle.render(sc, ORACLE_MODE[solver], winners=True, ambig=True)
+    v, f, a, mo, ca = gpu_inputs(sc)
+    for k in range(sc["T"]):
+        ids = ctx.debug_winners(v, f, a, mo, ca, sc["T"], sc["H"], sc["W"], k, solver).cpu().numpy()
+        clean = r["ambig"][k] == 0
+        assert np.array_equal(ids[clean], r["winners"][k][clean]), k
+        assert (ids >= 0).sum() > 50
+
+
+@pytest.mark.parametrize("tile,spt", [(16, 8), (8, 4), (16, 16), (8, 1)])
+def test_tuning_variants_agree(ctx, tile, spt):
+    sc = scenes.small_scene("rotate", subdiv=2, T=20, H=45, W=61)
+    ref = gpu_render(ctx, sc, "fast")
+    ctx.set_tuning(tile, spt, 0)
+    try:
+        for solver in ("fast", "plain"):
+            _check(ctx, sc, solver)
+        g = gpu_render(ctx, sc, "fast")
+        assert np.max(np.abs(g - ref)) < 2e-6
+    finally:
+        ctx.set_tuning(16, 8, 0)
+
+
+def test_splits_agree(ctx):
+    sc = scenes.small_scene("rotate", subdiv=2, T=24, H=40, W=40)
+    imgs = []
+    for splits in (1, 3, 24):
+        ctx.set_tuning(16, 8, splits)
+        imgs.append(gpu_render(ctx, sc, "plain"))
+    ctx.set_tuning(16, 8, 0)
+    assert np.max(np.abs(imgs[0] - imgs[1])) < 2e-6 and np.max(np.abs(imgs[0] - imgs[2])) < 2e-6
+
+
+def test_empty_mesh_and_offscreen(ctx):
+    sc = scenes.small_scene("translate", subdiv=1, T=4, H=20, W=24)
+    empty = dict(sc, faces=np.zeros((0, 3), dtype=np.int32))
+    for solver in ("plain", "fast"):
+        assert np.all(gpu_render(ctx, empty, solver) == 0.0)
+    far = dict(sc, verts=sc["verts"] + np.array([50.0, 0.0, 0.0]))
+    for solver in ("plain", "fast"):
+        assert np.all(gpu_render(ctx, far, solver) == 0.0)
+
+
+def test_behind_camera_is_skipped(ctx):
+    """Triangles with a vertex at camera z <= znear are skipped, identically in both paths."""
+    sc = scenes.small_scene("translate", subdiv=2, T=6, H=30, W=30, d=(0.0, 0.0, -3.5))
+    for solver in ("plain", "fast"):
+        _check(ctx, sc, solver)
+
+
+def test_full_size_rotation_windows(ctx):
+    """Full-size rotation workload (subdiv-4 SH sphere, T = 64, 256x256, 12 segments), the launch
+    configuration the benchmark times, against the oracle on sampled 16x16 windows."""
+    sc = scenes.config2()
+    for solver in ("fast", "plain"):
+        g = gpu_render(ctx, sc, solver)
+        for (x0, y0) in [(120, 120), (60, 128), (176, 72), (8, 8)]:
+            win = (x0, y0, 16, 16)
+            r = oracle.render(sc, ORACLE_MODE[solver], window=win, ambig=True)
+            gw = g[y0:y0 + 16, x0:x0 + 16]
+            max_clean, frac, excess = compare_images(gw, r["rgba"], r["ambig"], sc["T"])
+            assert max_clean <= TOL and excess <= 0.0, (solver, win, max_clean, excess, frac)
+
+
+def test_candidate_count_matches_oracle(ctx):
+    sc = scenes.small_scene("rotate", subdiv=2, T=8, H=40, W=72)
+    v, f, a, mo, ca = gpu_inputs(sc)
+    for solver in ("plain", "fast"):
+        n = ctx.count_candidates(v, f, a, mo, ca, sc["T"], sc["H"], sc["W"], solver)
+        ref = oracle.render(sc, ORACLE_MODE[solver])["counters"][oracle.CNT_CAND]
+        assert abs(n - ref) <= 1e-3 * ref, (solver, n, ref)
+
+
+def test_bad_arguments_return_errors(ctx):
+    import paper_2602_07860_gb300 as mbr
+    from paper_2602_07860_gb300._lib import MbrError
+    sc = scenes.small_scene("rotate", subdiv=1, T=4, H=16, W=16)
+    v, f, a, mo, ca = gpu_inputs(sc)
+    with pytest.raises(MbrError):
+        ctx.render_blur(v, f, a, mo, ca, 0, 16, 16, "fast")
+    bad = mbr.Motion(kind="rotate", axis=(0.0, 0.0, 0.0), omega=1.0)
+    with pytest.raises(MbrError):
+        ctx.render_blur(v, f, a, bad, ca, 4, 16, 16, "fast")
+    with pytest.raises(MbrError):
+        ctx.set_tuning(12, 8, 0)
+    # the context stays usable after errors
+    assert np.isfinite(gpu_render(ctx, sc, "fast")).all()
