@@ -30,8 +30,13 @@
 #define ETA_DET 1e-5       /* ambiguity: |det F| <= D_MIN + ETA_DET * (longest edge)^2          */
 #define ETA_REGION 1e-6    /* ambiguity: fast-mode closest-edge tie (relative)                   */
 
-enum { AMB_COVER = 1, AMB_DEPTH = 2, AMB_DEGEN = 4, AMB_REGION = 8, AMB_CLAMP = 16, AMB_LAMBERT = 32 };
-#define ETA_CLAMP 1e-5     /* gradient-only flag: closest-point parameter within this of 0 or 1 */
+enum { AMB_COVER = 1, AMB_DEPTH = 2, AMB_DEGEN = 4, AMB_REGION = 8, AMB_CLAMP = 16, AMB_LAMBERT = 32, AMB_COND = 64 };
+/* gradient-only flag: single-precision conditioning.  The FP32 relative error of a gradient term
+ * that passes through w = F^-1 p grows like eps32 (Lmax^2 / |det F|) max(1, |w|); flag when that
+ * estimate exceeds 1e-4 (a tenth of the gradient tolerance). */
+#define EPS32 5.96e-8
+#define COND_LIMIT 1e-4
+#define ETA_CLAMP 1e-5     /* gradient-only flag: closest-feature switch within this relative d^2 */
 #define ETA_LAMBERT 1e-5   /* gradient-only flag: |n.l| below this (Lambert clamp switches)     */
 
 /* ------------------------------------------------------------------ small helpers */
@@ -220,7 +225,7 @@ typedef struct {
   double t;       /* clamped edge parameter */
   double d2_second; /* second-best edge distance (for tie detection) */
   double w_second[3];
-  double traw[3], d2e[3]; /* per edge: unclamped projection parameter and squared distance */
+  double traw[3], d2e[3], L2e[3]; /* per edge: unclamped parameter, squared distance, length^2 */
 } closest_t;
 
 /* For each edge v_i v_j: t = ((p - v_i).(v_j - v_i)) / |v_j - v_i|^2 clamped to [0, 1]
@@ -235,6 +240,7 @@ static void closest_point(const double tri[6], double px, double py, closest_t* 
     double ex = xj - xi, ey = yj - yi, L2 = ex * ex + ey * ey;
     double t = L2 > 0 ? ((px - xi) * ex + (py - yi) * ey) / L2 : 0.0;
     out->traw[e] = t;
+    out->L2e[e] = L2;
     int32_t reg = e;
     double qx, qy;
     if (t <= 0.0) { t = 0.0; qx = xi; qy = yi; reg = 3 + i; }
@@ -393,13 +399,14 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
   double* prod = (double*)malloc(sizeof(double) * (npix + 1));
   int32_t* bestf = (int32_t*)malloc(sizeof(int32_t) * (npix + 1));
   uint8_t* amb = (uint8_t*)malloc(npix + 1);
+  uint8_t* samb = (uint8_t*)malloc(npix + 1); /* flags of soft terms: count only if uncovered */
   double* gcur = backward ? (double*)calloc(5 * (size_t)V, sizeof(double)) : NULL;
   double* gslot = backward ? (double*)calloc(5 * (size_t)V * (S + 1), sizeof(double)) : NULL;
   double* gnb = backward ? (double*)calloc(3 * (size_t)V, sizeof(double)) : NULL;
   size_t* pstart = backward ? (size_t*)malloc(sizeof(size_t) * (npix + 2)) : NULL;
   soft_entry* sorted = NULL;
   entry_list L = {NULL, 0, 0};
-  int ok = nrm && cur && key0 && key1 && bestk && secondk && bestw && prod && bestf && amb &&
+  int ok = nrm && cur && key0 && key1 && bestk && secondk && bestw && prod && bestf && amb && samb &&
            (!backward || (gcur && gslot && gnb && pstart));
   if (!ok) goto fail;
 
@@ -434,6 +441,7 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
       bestf[p] = -1;
       prod[p] = 1.0;
       amb[p] = 0;
+      samb[p] = 0;
     }
     L.n = 0;
 
@@ -506,6 +514,9 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
           }
           if (mn >= -ETA_COV && mn <= ETA_COV) amb[p] |= AMB_COVER;
           const int covered = wb[0] >= 0.0 && wb[1] >= 0.0 && wb[2] >= 0.0;
+          const double wmax = fmax(1.0, fmax(fabs(wb[0]), fmax(fabs(wb[1]), fabs(wb[2]))));
+          const double cond = EPS32 * lmax2 / fabs(D) * wmax;
+          if (covered && cond > COND_LIMIT) amb[p] |= AMB_COND;
           if (covered) {
             /* z-test on perspective-correct inverse depth: larger is nearer */
             double key = wb[0] / z[0] + wb[1] / z[1] + wb[2] / z[2];
@@ -530,26 +541,38 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
               double pxp = wb[0] * trX[0] + wb[1] * trX[2] + wb[2] * trX[4];
               double pyp = wb[0] * trX[1] + wb[1] * trX[3] + wb[2] * trX[5];
               closest_point(trX, pxp, pyp, &c);
-              if (c.d2_second <= c.d2 * (1.0 + ETA_REGION) + 1e-30) {
-                double dw = fabs(c.w[0] - c.w_second[0]) + fabs(c.w[1] - c.w_second[1]) +
-                            fabs(c.w[2] - c.w_second[2]);
-                if (dw > 1e-9) amb[p] |= AMB_REGION;
-              }
               double qx = c.w[0] * tri[0] + c.w[1] * tri[2] + c.w[2] * tri[4];
               double qy = c.w[0] * tri[1] + c.w[1] * tri[3] + c.w[2] * tri[5];
               d = (u - qx) * (u - qx) + (v - qy) * (v - qy);
+              if (c.d2_second <= c.d2 * (1.0 + ETA_REGION) + 1e-30) {
+                /* a near tie between two edge candidates in F(X): it matters only if the two
+                 * closest points give different soft terms at F(tau) */
+                double ax = c.w_second[0] * tri[0] + c.w_second[1] * tri[2] + c.w_second[2] * tri[4];
+                double ay = c.w_second[0] * tri[1] + c.w_second[1] * tri[3] + c.w_second[2] * tri[5];
+                double d_alt = (u - ax) * (u - ax) + (v - ay) * (v - ay);
+                if (fmin(d, d_alt) <= r2 && fabs(exp(-d / s->delta) - exp(-d_alt / s->delta)) > 1e-6)
+                  samb[p] |= AMB_REGION;
+              }
             } else {
               closest_point(tri, u, v, &c);
               d = c.d2;
             }
             const int include = soft_all || d <= r2;
-            if (include) {
-              /* an edge attaining the minimum whose unclamped projection lies near an end: the
-               * region (edge interior vs vertex) may switch in FP32, which changes the gradient */
-              for (int q = 0; q < 3; ++q)
-                if (c.d2e[q] <= c.d2 * (1.0 + 1e-9) + 1e-300 &&
-                    (fabs(c.traw[q]) < ETA_CLAMP || fabs(c.traw[q] - 1.0) < ETA_CLAMP))
-                  amb[p] |= AMB_CLAMP;
+            if (include && mode == ORC_FAST_REF && cond > COND_LIMIT) samb[p] |= AMB_COND;
+            if (include && mode == ORC_FAST_REF) {
+              /* The fast-mode gradient flows through w* only inside an edge region, so it jumps
+               * where the search in F(X) switches feature.  Flag when the switch is within FP32
+               * reach: an attaining edge whose projection lies near an end (the vertex
+               * alternative is (m L)^2 farther), or a near tie between different features. (The
+               * exact distance of the plain modes has a continuous gradient there.) */
+              for (int q = 0; q < 3; ++q) {
+                if (c.d2e[q] > c.d2 * (1.0 + 1e-9) + 1e-300) continue;
+                double m = fmin(fabs(c.traw[q]), fabs(1.0 - c.traw[q]));
+                if (m * m * c.L2e[q] <= ETA_CLAMP * c.d2) samb[p] |= AMB_CLAMP;
+              }
+              if (c.d2_second <= c.d2 * (1.0 + ETA_CLAMP) + 1e-30 &&
+                  fabs(c.w[0] - c.w_second[0]) + fabs(c.w[1] - c.w_second[1]) + fabs(c.w[2] - c.w_second[2]) > 1e-9)
+                samb[p] |= AMB_CLAMP;
             }
             hash = fnv(fnv(fnv(hash, k * 7919 + 1), (int64_t)p * 104729 + f), c.region * 2 + include);
             if (include) {
@@ -572,6 +595,7 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
       int32_t f = bestf[p];
       if (f >= 0 && secondk[p] > -INFINITY && bestk[p] - secondk[p] <= ETA_DEPTH * fabs(bestk[p]))
         amb[p] |= AMB_DEPTH;
+      if (f < 0) amb[p] |= samb[p];
       if (amb[p]) ++n_amb;
       if (winners) winners[(size_t)k * npix + p] = f;
       if (ambig) ambig[(size_t)k * npix + p] = amb[p];
@@ -772,12 +796,12 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
     cnt[ORC_CNT_SOFT] = n_soft;
   }
   free(nrm); free(cur); free(key0); free(key1); free(bestk); free(secondk); free(bestw);
-  free(prod); free(bestf); free(amb); free(gcur); free(gslot); free(gnb); free(pstart);
+  free(prod); free(bestf); free(amb); free(samb); free(gcur); free(gslot); free(gnb); free(pstart);
   free(sorted); free(L.e);
   return 0;
 fail:
   free(nrm); free(cur); free(key0); free(key1); free(bestk); free(secondk); free(bestw);
-  free(prod); free(bestf); free(amb); free(gcur); free(gslot); free(gnb); free(pstart);
+  free(prod); free(bestf); free(amb); free(samb); free(gcur); free(gslot); free(gnb); free(pstart);
   free(sorted); free(L.e);
   return -1;
 }

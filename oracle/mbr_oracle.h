@@ -72,8 +72,10 @@ double orc_closest_point(const double tri[6], double px, double py, double w[3],
  *   ambig    [T*h*w]   per-sample flags (bitmask) where FP32 may take another discrete choice:
  *                      1 coverage (pixel within 2e-6 of a triangle boundary), 2 depth tie,
  *                      4 near-degenerate triangle, 8 fast-mode closest-edge tie (these four can
- *                      change a pixel); 16 closest-point clamp boundary, 32 Lambert clamp
- *                      (these two only change gradients); may be NULL
+ *                      change a pixel); 16 fast-mode closest-feature switch (edge interior vs
+ *                      vertex, or a near tie), 32 Lambert clamp, 64 single-precision
+ *                      conditioning eps32 Lmax^2/|det F| max(1,|w|) > 1e-4 of a term through
+ *                      w = F^-1 p (these three only change gradients); may be NULL
  *   counters [ORC_CNT_N]
  * returns 0, or -1 on bad arguments / allocation failure. */
 int32_t orc_render(const orc_scene* s, int32_t mode, int32_t flags, int32_t x0, int32_t y0,
