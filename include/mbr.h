@@ -139,6 +139,25 @@ int mbr_count_candidates(mbr_ctx* ctx, const mbr_mesh* mesh, const mbr_motion* m
  * solver (1..16), and the number of sub-frame groups split across CTAs (0 = automatic). */
 int mbr_set_tuning(mbr_ctx* ctx, int32_t tile, int32_t spt, int32_t splits);
 
+/* Measurement counters of a context. */
+typedef struct {
+  int64_t launches;          /* kernels this context has launched (cumulative)                 */
+  int64_t bin_entries;       /* (group, tile, face) entries of the last binning                */
+  double raster_fwd_ms;      /* summed duration of the timed forward raster launches          */
+  double raster_bwd_ms;      /* summed duration of the timed adjoint raster launches          */
+  int64_t raster_fwd_count;  /* forward raster launches timed since profiling was switched on  */
+  int64_t raster_bwd_count;  /* adjoint raster launches timed                                  */
+  int32_t n_split;           /* sub-frame group splits of the last raster launch                */
+  int32_t groups;            /* sample groups of the last call                                   */
+} mbr_stats;
+
+/* Switch CUDA-event timing of the raster kernels on (1, and reset the sums) or off (0).  Events
+ * are recorded on the caller's stream around each raster launch without synchronising; their
+ * durations are collected at the next call's existing binning sync or by mbr_get_stats (which
+ * waits for the last recorded event). */
+int mbr_set_profiling(mbr_ctx* ctx, int32_t on);
+int mbr_get_stats(mbr_ctx* ctx, mbr_stats* out);
+
 /* Message of the last failed call on ctx ("" if none).  Valid until the next call. */
 const char* mbr_last_error(mbr_ctx* ctx);
 

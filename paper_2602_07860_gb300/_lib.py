@@ -16,7 +16,8 @@ MBR_TIME_PAPER, MBR_TIME_MIDPOINT = 0, 1
 SOLVERS = {"plain": MBR_PLAIN, "fast": MBR_FAST}
 
 EXPORTS = ["mbr_create", "mbr_destroy", "mbr_render_blur", "mbr_render_blur_backward", "mbr_render_blur_batch",
-           "mbr_debug_winners", "mbr_count_candidates", "mbr_set_tuning", "mbr_last_error"]
+           "mbr_debug_winners", "mbr_count_candidates", "mbr_set_tuning", "mbr_set_profiling", "mbr_get_stats",
+           "mbr_last_error"]
 
 
 class MbrMesh(ctypes.Structure):
@@ -37,6 +38,12 @@ class MbrItem(ctypes.Structure):
     _fields_ = [("mesh", MbrMesh), ("motion", MbrMotion), ("camera", MbrCamera), ("T", c_int32), ("H", c_int32),
                 ("W", c_int32), ("solver", c_int32), ("image", c_void_p), ("dl_dimage", c_void_p),
                 ("dl_dverts", c_void_p), ("dl_dalbedo", c_void_p)]
+
+
+class MbrStats(ctypes.Structure):
+    _fields_ = [("launches", c_int64), ("bin_entries", c_int64), ("raster_fwd_ms", ctypes.c_double),
+                ("raster_bwd_ms", ctypes.c_double), ("raster_fwd_count", c_int64), ("raster_bwd_count", c_int64),
+                ("n_split", c_int32), ("groups", c_int32)]
 
 
 class MbrError(RuntimeError):
@@ -81,6 +88,10 @@ def load(build_if_missing=True):
     L.mbr_render_blur_batch.restype = c_int32
     L.mbr_set_tuning.argtypes = [c_void_p, c_int32, c_int32, c_int32]
     L.mbr_set_tuning.restype = c_int32
+    L.mbr_set_profiling.argtypes = [c_void_p, c_int32]
+    L.mbr_set_profiling.restype = c_int32
+    L.mbr_get_stats.argtypes = [c_void_p, P(MbrStats)]
+    L.mbr_get_stats.restype = c_int32
     L.mbr_last_error.argtypes = [c_void_p]
     L.mbr_last_error.restype = ctypes.c_char_p
     _lib = L

@@ -26,6 +26,11 @@ struct DevBuf {
   size_t cap = 0;
 };
 
+// one CSR binning of (group, tile) -> face lists
+struct BinSet {
+  DevBuf counts, offsets, cursor, list, scan_tmp;
+};
+
 }  // namespace
 
 struct mbr_ctx {
@@ -35,10 +40,16 @@ struct mbr_ctx {
   // tuning
   int tile = 16, spt = 8, splits = 0;
   // scratch
-  DevBuf nacc, pos, nrm, recs, tables, counts, offsets, cursor, list, scan_tmp, partial, gslot, gm, cnt64, status;
+  DevBuf nacc, pos, nrm, recs, tables, partial, gslot, gm, cnt64, status;
+  BinSet core, soft;  // undilated bins (coverage) and r_soft-dilated bins (soft coverage)
   void* host_stage = nullptr;
   size_t host_stage_cap = 0;
   int32_t* host_total = nullptr;
+  // measurement: one event pair per raster kind (0 forward, 1 adjoint), harvested lazily
+  bool profiling = false;
+  cudaEvent_t ev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  bool pending[2] = {false, false};
+  mbr_stats stats{};
 };
 
 namespace {
@@ -175,6 +186,45 @@ int validate(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const m
   return MBR_OK;
 }
 
+// kernels launched by the front half: normals, transform, setup (+ bins: count, 3 scan, fill)
+constexpr int kFrontLaunches = 3, kBinLaunches = 5;
+
+// add the duration of a recorded event pair to the sums (waits for its end event)
+int harvest(mbr_ctx* c, int kind) {
+  if (!c->pending[kind]) return MBR_OK;
+  CUDA_TRY(c, cudaEventSynchronize(c->ev[kind][1]));
+  float ms = 0.f;
+  CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev[kind][0], c->ev[kind][1]));
+  if (kind == 0) {
+    c->stats.raster_fwd_ms += ms;
+    c->stats.raster_fwd_count += 1;
+  } else {
+    c->stats.raster_bwd_ms += ms;
+    c->stats.raster_bwd_count += 1;
+  }
+  c->pending[kind] = false;
+  return MBR_OK;
+}
+
+int time_begin(mbr_ctx* c, int kind, cudaStream_t st) {
+  if (!c->profiling) return MBR_OK;
+  int rc = harvest(c, kind);
+  if (rc) return rc;
+  if (!c->ev[kind][0]) {
+    CUDA_TRY(c, cudaEventCreate(&c->ev[kind][0]));
+    CUDA_TRY(c, cudaEventCreate(&c->ev[kind][1]));
+  }
+  CUDA_TRY(c, cudaEventRecord(c->ev[kind][0], st));
+  return MBR_OK;
+}
+
+int time_end(mbr_ctx* c, int kind, cudaStream_t st) {
+  if (!c->profiling) return MBR_OK;
+  CUDA_TRY(c, cudaEventRecord(c->ev[kind][1], st));
+  c->pending[kind] = true;
+  return MBR_OK;
+}
+
 // Everything the raster kernels need; built by prepare().
 struct Prepared {
   int S = 1, n_slots = 0, n_sets = 0, G = 0;
@@ -294,6 +344,8 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
   launch_setup((const float4*)c->pos.p, mesh->faces, F, V, d_sets, pp.n_sets, cam->znear, (TriRec*)c->recs.p, st);
   CUDA_TRY(c, cudaGetLastError());
   pp.r = (float)std::sqrt((double)cam->delta * std::log(1e12));
+  c->stats.launches += (F > 0 ? 1 : 0) + 1 + (F > 0 ? 1 : 0);
+  c->stats.groups = pp.G;
   if (!do_bins) {
     CUDA_TRY(c, cudaMemcpyAsync(c->host_total + 1, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(c, cudaStreamSynchronize(st));
@@ -301,37 +353,48 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
     return MBR_OK;
   }
 
-  // a3 binning: count -> scan -> (sync: total) -> fill
+  // a3 binning: core and soft bins: count -> scan (both) -> one sync for the totals -> fill
   const int tw = c->tile, th = c->tile;
   pp.tiles_x = (W + tw - 1) / tw;
   pp.tiles_y = (H + th - 1) / th;
   pp.n_tiles = pp.tiles_x * pp.tiles_y;
   const long long nb = (long long)pp.G * pp.n_tiles;
   if (nb > (1LL << 30)) return fail(c, MBR_ERR_ARG, "too many (group, tile) bins: %lld", nb);
-  if ((rc = ensure(c, c->counts, sizeof(int32_t) * (size_t)nb, st))) return rc;
-  if ((rc = ensure(c, c->offsets, sizeof(int32_t) * (size_t)(nb + 1), st))) return rc;
-  if ((rc = ensure(c, c->scan_tmp, sizeof(int32_t) * scan_temp_ints((int)nb), st))) return rc;
-  CUDA_TRY(c, cudaMemsetAsync(c->counts.p, 0, sizeof(int32_t) * (size_t)nb, st));
-  launch_bin(false, (const TriRec*)c->recs.p, F, pp.d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles, pp.r,
-             (int32_t*)c->counts.p, nullptr, nullptr, d_status, st);
-  launch_scan((const int32_t*)c->counts.p, (int)nb, (int32_t*)c->offsets.p, (int32_t*)c->scan_tmp.p, st);
-  CUDA_TRY(c, cudaGetLastError());
-  CUDA_TRY(c, cudaMemcpyAsync(c->host_total, (int32_t*)c->offsets.p + nb, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  BinSet* sets2[2] = {&c->core, &c->soft};
+  const float margins[2] = {kCoreMargin, pp.r + kCoreMargin};
+  for (int q = 0; q < 2; ++q) {
+    BinSet& bs = *sets2[q];
+    if ((rc = ensure(c, bs.counts, sizeof(int32_t) * (size_t)nb, st))) return rc;
+    if ((rc = ensure(c, bs.offsets, sizeof(int32_t) * (size_t)(nb + 1), st))) return rc;
+    if ((rc = ensure(c, bs.scan_tmp, sizeof(int32_t) * scan_temp_ints((int)nb), st))) return rc;
+    CUDA_TRY(c, cudaMemsetAsync(bs.counts.p, 0, sizeof(int32_t) * (size_t)nb, st));
+    launch_bin(false, (const TriRec*)c->recs.p, F, pp.d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles,
+               margins[q], (int32_t*)bs.counts.p, nullptr, nullptr, d_status, st);
+    launch_scan((const int32_t*)bs.counts.p, (int)nb, (int32_t*)bs.offsets.p, (int32_t*)bs.scan_tmp.p, st);
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaMemcpyAsync(c->host_total + 2 * q, (int32_t*)bs.offsets.p + nb, sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, st));
+  }
   CUDA_TRY(c, cudaMemcpyAsync(c->host_total + 1, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(c, cudaStreamSynchronize(st));
-  const long long total = c->host_total[0];
   if (c->host_total[1] & kStatusBadFace) return fail(c, MBR_ERR_ARG, "face index outside [0, V)");
-  if (total < 0) return fail(c, MBR_ERR_DEVICE, "bin total overflow");
-  if ((rc = ensure(c, c->list, sizeof(int32_t) * (size_t)std::max<long long>(total, 1), st))) return rc;
-  if ((rc = ensure(c, c->cursor, sizeof(int32_t) * (size_t)nb, st))) return rc;
-  CUDA_TRY(c, cudaMemcpyAsync(c->cursor.p, c->offsets.p, sizeof(int32_t) * (size_t)nb, cudaMemcpyDeviceToDevice, st));
-  launch_bin(true, (const TriRec*)c->recs.p, F, pp.d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles, pp.r,
-             (int32_t*)c->cursor.p, (int32_t*)c->list.p, (const int32_t*)c->offsets.p, d_status, st);
-  CUDA_TRY(c, cudaGetLastError());
-
+  long long totals[2] = {c->host_total[0], c->host_total[2]};
+  for (int q = 0; q < 2; ++q) {
+    BinSet& bs = *sets2[q];
+    if (totals[q] < 0) return fail(c, MBR_ERR_DEVICE, "bin total overflow");
+    if ((rc = ensure(c, bs.list, sizeof(int32_t) * (size_t)std::max<long long>(totals[q], 1), st))) return rc;
+    if ((rc = ensure(c, bs.cursor, sizeof(int32_t) * (size_t)nb, st))) return rc;
+    CUDA_TRY(c, cudaMemcpyAsync(bs.cursor.p, bs.offsets.p, sizeof(int32_t) * (size_t)nb, cudaMemcpyDeviceToDevice,
+                                st));
+    launch_bin(true, (const TriRec*)c->recs.p, F, pp.d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles,
+               margins[q], (int32_t*)bs.cursor.p, (int32_t*)bs.list.p, (const int32_t*)bs.offsets.p, d_status, st);
+    CUDA_TRY(c, cudaGetLastError());
+  }
+  c->stats.launches += 2 * ((F > 0 ? 2 : 0) + 3);
+  c->stats.bin_entries = totals[0] + totals[1];
   // work split over sub-frame groups so that small images still fill the SMs
   int ns = c->splits;
-  if (ns <= 0) ns = (4 * c->num_sms + pp.n_tiles - 1) / pp.n_tiles;
+  if (ns <= 0) ns = (8 * c->num_sms + pp.n_tiles - 1) / pp.n_tiles;
   pp.n_split = std::max(1, std::min(ns, pp.G));
   return MBR_OK;
 }
@@ -342,8 +405,10 @@ RasterParams raster_params(mbr_ctx* c, const mbr_mesh* mesh, const mbr_camera* c
   std::memset(&P, 0, sizeof(P));
   P.recs = (const TriRec*)c->recs.p;
   P.groups = pp.d_groups;
-  P.bin_off = (const int32_t*)c->offsets.p;
-  P.bin_faces = (const int32_t*)c->list.p;
+  P.core.off = (const int32_t*)c->core.offsets.p;
+  P.core.faces = (const int32_t*)c->core.list.p;
+  P.soft.off = (const int32_t*)c->soft.offsets.p;
+  P.soft.faces = (const int32_t*)c->soft.list.p;
   P.slot_nrm = (const float4*)c->nrm.p;
   P.faces = mesh->faces;
   P.albedo = mesh->albedo;
@@ -355,6 +420,7 @@ RasterParams raster_params(mbr_ctx* c, const mbr_mesh* mesh, const mbr_camera* c
   P.tiles_x = pp.tiles_x;
   P.tiles_y = pp.tiles_y;
   P.n_split = pp.n_split;
+  P.r = pp.r;
   P.r2 = pp.r * pp.r;
   P.delta = cam->delta;
   P.inv_delta = 1.0f / cam->delta;
@@ -390,11 +456,16 @@ int forward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, con
   } else {
     P.out = (float4*)image;
   }
+  if ((rc = time_begin(c, 0, st))) return rc;
   launch_raster_fwd(P, c->tile, pp.spt, pp.moving, st);
   CUDA_TRY(c, cudaGetLastError());
+  if ((rc = time_end(c, 0, st))) return rc;
+  c->stats.launches += 1;
+  c->stats.n_split = pp.n_split;
   if (pp.n_split > 1 && image) {
     launch_finalize((const float4*)c->partial.p, pp.n_split, npix, P.inv_T, (float4*)image, st);
     CUDA_TRY(c, cudaGetLastError());
+    c->stats.launches += 1;
   }
   return MBR_OK;
 }
@@ -424,14 +495,37 @@ int mbr_create(mbr_ctx** out) {
 
 void mbr_destroy(mbr_ctx* c) {
   if (!c) return;
-  DevBuf* bufs[] = {&c->nacc, &c->pos, &c->nrm, &c->recs, &c->tables, &c->counts, &c->offsets, &c->cursor,
-                    &c->list, &c->scan_tmp, &c->partial, &c->gslot, &c->gm, &c->cnt64, &c->status};
+  DevBuf* bufs[] = {&c->nacc, &c->pos, &c->nrm, &c->recs, &c->tables, &c->partial, &c->gslot, &c->gm, &c->cnt64,
+                    &c->status, &c->core.counts, &c->core.offsets, &c->core.cursor, &c->core.list,
+                    &c->core.scan_tmp, &c->soft.counts, &c->soft.offsets, &c->soft.cursor, &c->soft.list,
+                    &c->soft.scan_tmp};
   cudaDeviceSynchronize();
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->host_stage) cudaFreeHost(c->host_stage);
   if (c->host_total) cudaFreeHost(c->host_total);
+  for (int k = 0; k < 2; ++k)
+    for (int q = 0; q < 2; ++q)
+      if (c->ev[k][q]) cudaEventDestroy(c->ev[k][q]);
   delete c;
+}
+
+int mbr_set_profiling(mbr_ctx* c, int32_t on) {
+  if (!c) return MBR_ERR_ARG;
+  c->pending[0] = c->pending[1] = false;
+  c->profiling = on != 0;
+  c->stats.raster_fwd_ms = c->stats.raster_bwd_ms = 0.0;
+  c->stats.raster_fwd_count = c->stats.raster_bwd_count = 0;
+  return MBR_OK;
+}
+
+int mbr_get_stats(mbr_ctx* c, mbr_stats* out) {
+  if (!c || !out) return MBR_ERR_ARG;
+  int rc = harvest(c, 0);
+  if (!rc) rc = harvest(c, 1);
+  if (rc) return rc;
+  *out = c->stats;
+  return MBR_OK;
 }
 
 const char* mbr_last_error(mbr_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -484,8 +578,12 @@ int mbr_render_blur_backward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion*
   P.dl_dimage = (const float4*)dl_dimage;
   P.g_slot = (float*)c->gslot.p;
   P.g_albedo = dl_dalbedo;
+  if ((rc = time_begin(c, 1, st))) return rc;
   launch_raster_bwd(P, c->tile, pp.spt, pp.moving, st);
   CUDA_TRY(c, cudaGetLastError());
+  if ((rc = time_end(c, 1, st))) return rc;
+  c->stats.launches += 1 + 1 + (mesh->F > 0 ? 1 : 0);
+  c->stats.n_split = pp.n_split;
   launch_slot_chain(mesh->verts, (const float*)c->nacc.p, V, pp.d_xf, pp.n_slots, cam->tan_half_fov,
                     (const float*)c->gslot.p, dl_dverts, (float*)c->gm.p, st);
   launch_normals_bwd(mesh->verts, mesh->faces, mesh->F, V, (const float*)c->gm.p, dl_dverts, st);
@@ -507,6 +605,7 @@ int mbr_count_candidates(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* mot
   CUDA_TRY(c, cudaMemsetAsync(c->cnt64.p, 0, sizeof(unsigned long long), st));
   launch_count((const TriRec*)c->recs.p, mesh->F, pp.d_groups, pp.G, W, H, pp.r,
                (unsigned long long*)c->cnt64.p, st);
+  c->stats.launches += mesh->F > 0 ? 1 : 0;
   CUDA_TRY(c, cudaGetLastError());
   unsigned long long h = 0;
   CUDA_TRY(c, cudaMemcpyAsync(&h, c->cnt64.p, sizeof(h), cudaMemcpyDeviceToHost, st));

@@ -41,22 +41,199 @@ __device__ __forceinline__ void edge_backward(float gN0, float gN1, float gN2, c
 template <bool MOVING>
 __device__ __forceinline__ void rel_vertices(const float4* r, const PixelSetup<MOVING>& ps, float tau,
                                              float ax[3], float ay[3]) {
-  const float qtx = MOVING ? fmaf(-tau, r[4].x, ps.q0x) : ps.q0x;
-  const float qty = MOVING ? fmaf(-tau, r[4].y, ps.q0y) : ps.q0y;
-  const float e1x = MOVING ? fmaf(tau, r[3].x, r[0].z) : r[0].z;
-  const float e1y = MOVING ? fmaf(tau, r[3].y, r[0].w) : r[0].w;
-  const float e2x = MOVING ? fmaf(tau, r[3].z, r[1].x) : r[1].x;
-  const float e2y = MOVING ? fmaf(tau, r[3].w, r[1].y) : r[1].y;
+  const float qtx = MOVING ? fmaf(-tau, r[kR_G].x, ps.q0x) : ps.q0x;
+  const float qty = MOVING ? fmaf(-tau, r[kR_G].y, ps.q0y) : ps.q0y;
+  const float e1x = MOVING ? fmaf(tau, r[kR_D].x, r[kR_O].z) : r[kR_O].z;
+  const float e1y = MOVING ? fmaf(tau, r[kR_D].y, r[kR_O].w) : r[kR_O].w;
+  const float e2x = MOVING ? fmaf(tau, r[kR_D].z, r[kR_E2].x) : r[kR_E2].x;
+  const float e2y = MOVING ? fmaf(tau, r[kR_D].w, r[kR_E2].y) : r[kR_E2].y;
   ax[0] = -qtx; ay[0] = -qty;
   ax[1] = e1x - qtx; ay[1] = e1y - qty;
   ax[2] = e2x - qtx; ay[2] = e2y - qty;
 }
 
+// pass 2 of the adjoint: soft products, counting vanishing factors separately so that the
+// exclusive product prod_{l != j} (1 - A_l) never divides by a zero factor
+template <int SPT>
+struct BwdSoftProduct {
+  float prod[SPT];
+  int nzero[SPT];
+  float inv_delta;
+  __device__ __forceinline__ void begin(int) {}
+  template <typename PS>
+  __device__ __forceinline__ void term(int, const float4*, const PS&, const EdgeVals&, const SoftGeom& sg, int i,
+                                       float, int) {
+    const float f = -expm1f(-sg.d * inv_delta);
+#pragma unroll
+    for (int q = 0; q < SPT; ++q)
+      if (q == i) {
+        if (f > kTinyFactor) prod[q] *= f;
+        else nzero[q] += 1;
+      }
+  }
+  __device__ __forceinline__ void end(int, float) {}
+};
+
+// pass 3 of the adjoint: gradient of alpha = 1 - prod_j (1 - A_j) w.r.t. the vertex positions of
+// every soft candidate, accumulated per candidate over the thread's samples, warp-reduced, and
+// added to the slot gradients by one lane
+template <int SPT, bool MOVING>
+struct BwdSoftGrad {
+  float prod[SPT];
+  int nzero[SPT];
+  float ga, inv_delta;
+  const float4* rec;          // staged records (shared memory)
+  const int32_t* faces;
+  float* gslot_a;
+  float* gslot_b;
+  float gax[3], gay[3], gbx[3], gby[3];
+  bool any;
+
+  __device__ __forceinline__ void begin(int) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) gax[q] = gay[q] = gbx[q] = gby[q] = 0.f;
+    any = false;
+  }
+
+  __device__ __forceinline__ void term(int, const float4* r, const PixelSetup<MOVING>& ps, const EdgeVals& e,
+                                       const SoftGeom& sg, int i, float tau, int X) {
+    const float f = -expm1f(-sg.d * inv_delta);
+    const float A = __expf(-sg.d * inv_delta);
+    float pr = 1.f;
+    int nz = 0;
+#pragma unroll
+    for (int q = 0; q < SPT; ++q)
+      if (q == i) { pr = prod[q]; nz = nzero[q]; }
+    float excl;
+    if (nz == 0) excl = pr / f;
+    else excl = (nz == 1 && f <= kTinyFactor) ? pr : 0.f;
+    // alpha = 1 - prod(1 - A_l): d alpha / d d_j = -excl A_j / delta
+    const float gd = ga * excl * (-A * inv_delta);
+    if (gd == 0.f) return;
+    any = true;
+    const float grx = 2.f * sg.rx * gd, gry = 2.f * sg.ry * gd;  // d/d(F(tau) w* - p)
+    const float ws[3] = {sg.c.w0, sg.c.w1, sg.c.w2};
+    float gtx[3], gty[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) { gtx[q] = ws[q] * grx; gty[q] = ws[q] * gry; }
+    if (MOVING) {
+      // local vertex positions at tau and at keyframe X
+      const float e1tx = fmaf(tau, r[kR_D].x, r[kR_O].z), e1ty = fmaf(tau, r[kR_D].y, r[kR_O].w);
+      const float e2tx = fmaf(tau, r[kR_D].z, r[kR_E2].x), e2ty = fmaf(tau, r[kR_D].w, r[kR_E2].y);
+      const float fx = (float)X;
+      const float e1Xx = fmaf(fx, r[kR_D].x, r[kR_O].z), e1Xy = fmaf(fx, r[kR_D].y, r[kR_O].w);
+      const float e2Xx = fmaf(fx, r[kR_D].z, r[kR_E2].x), e2Xy = fmaf(fx, r[kR_D].w, r[kR_E2].y);
+      const float Vtx[3] = {0.f, e1tx, e2tx}, Vty[3] = {0.f, e1ty, e2ty};
+      const float VXx[3] = {0.f, e1Xx, e2Xx}, VXy[3] = {0.f, e1Xy, e2Xy};
+      float gXx[3] = {0.f, 0.f, 0.f}, gXy[3] = {0.f, 0.f, 0.f};
+      float gpx = 0.f, gpy = 0.f;
+      if (sg.c.region < 3) {
+        // w*_i = 1 - t, w*_j = t, t = ((p' - V_i) . E) / |E|^2 on edge (i, j) of F(X)
+        const int ei = sg.c.ei, ej = sg.c.ej;
+        float gti = 0.f, gtj = 0.f, Ex = 0.f, Ey = 0.f, Rx = 0.f, Ry = 0.f;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          if (q == ei) {
+            gti = Vtx[q] * grx + Vty[q] * gry;
+            Rx = sg.ppx - VXx[q];
+            Ry = sg.ppy - VXy[q];
+            Ex -= VXx[q];
+            Ey -= VXy[q];
+          }
+          if (q == ej) {
+            gtj = Vtx[q] * grx + Vty[q] * gry;
+            Ex += VXx[q];
+            Ey += VXy[q];
+          }
+        }
+        const float L2 = fmaf(Ex, Ex, Ey * Ey);
+        const float gt = (gtj - gti) / L2, t = sg.c.t;
+        gpx = gt * Ex;
+        gpy = gt * Ey;
+        const float gix = gt * (-Ex - Rx + 2.f * t * Ex), giy = gt * (-Ey - Ry + 2.f * t * Ey);
+        const float gjx = gt * (Rx - 2.f * t * Ex), gjy = gt * (Ry - 2.f * t * Ey);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          if (q == ei) { gXx[q] += gix; gXy[q] += giy; }
+          if (q == ej) { gXx[q] += gjx; gXy[q] += gjy; }
+        }
+      }
+      // p' = F(X) w(tau)
+      const float w1 = sg.w1, w2 = sg.w2, w0 = 1.f - w1 - w2;
+      const float wv[3] = {w0, w1, w2};
+      float gw[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        gXx[q] = fmaf(wv[q], gpx, gXx[q]);
+        gXy[q] = fmaf(wv[q], gpy, gXy[q]);
+        gw[q] = VXx[q] * gpx + VXy[q] * gpy;
+      }
+      // w = N / D with D = N0 + N1 + N2
+      const float sw = wv[0] * gw[0] + wv[1] * gw[1] + wv[2] * gw[2];
+      const float invD = 1.f / e.D;
+      float ax[3], ay[3], ex[3], ey[3];
+      rel_vertices<MOVING>(r, ps, tau, ax, ay);
+      edge_backward((gw[0] - sw) * invD, (gw[1] - sw) * invD, (gw[2] - sw) * invD, ax, ay, ex, ey);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        gtx[q] += ex[q];
+        gty[q] += ey[q];
+      }
+      // F(tau) = lerp of the two keyframes; F(X) is keyframe X
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        gax[q] = fmaf(1.f - tau, gtx[q], gax[q]);
+        gay[q] = fmaf(1.f - tau, gty[q], gay[q]);
+        gbx[q] = fmaf(tau, gtx[q], gbx[q]);
+        gby[q] = fmaf(tau, gty[q], gby[q]);
+        if (X == 0) {
+          gax[q] += gXx[q];
+          gay[q] += gXy[q];
+        } else {
+          gbx[q] += gXx[q];
+          gby[q] += gXy[q];
+        }
+      }
+    } else {
+      // exact distance: d d / d v_i = 2 (F w* - p) w*_i
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        gax[q] += gtx[q];
+        gay[q] += gty[q];
+      }
+    }
+  }
+
+  __device__ __forceinline__ void end(int j, float) {
+    if (!__any_sync(0xffffffffu, any)) return;
+    float vals[12];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      vals[2 * q] = warp_sum(gax[q]);
+      vals[2 * q + 1] = warp_sum(gay[q]);
+      vals[6 + 2 * q] = MOVING ? warp_sum(gbx[q]) : 0.f;
+      vals[7 + 2 * q] = MOVING ? warp_sum(gby[q]) : 0.f;
+    }
+    if ((threadIdx.x & 31) == 0) {
+      const int face = __float_as_int(rec[j * kRecF4 + kR_E2].w);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int vid = __ldg(faces + 3 * face + q);
+        atomicAdd(gslot_a + (size_t)vid * 5, vals[2 * q]);
+        atomicAdd(gslot_a + (size_t)vid * 5 + 1, vals[2 * q + 1]);
+        if (MOVING) {
+          atomicAdd(gslot_b + (size_t)vid * 5, vals[6 + 2 * q]);
+          atomicAdd(gslot_b + (size_t)vid * 5 + 1, vals[7 + 2 * q]);
+        }
+      }
+    }
+  }
+};
+
 template <int TW, int TH, int SPT, bool MOVING>
 __global__ void __launch_bounds__(TW * TH) raster_bwd_kernel(RasterParams P) {
   constexpr int NT = TW * TH;
-  __shared__ float4 s_rec[kStageCap * kRecF4];
-  __shared__ Group s_grp;
+  __shared__ RasterSmem sm;
   const int n_tiles = P.tiles_x * P.tiles_y;
   const int tile = blockIdx.x % n_tiles, split = blockIdx.x / n_tiles;
   const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
@@ -64,226 +241,46 @@ __global__ void __launch_bounds__(TW * TH) raster_bwd_kernel(RasterParams P) {
   const bool in_img = px < P.W && py < P.H;
   const float u = (2.f * px + 1.f) / P.W - 1.f;
   const float v = 1.f - (2.f * py + 1.f) / P.H;
+  const TileBox tb = tile_box<TW, TH>(tx, ty, P.W, P.H);
   const int g_begin = (int)((long long)P.G * split / P.n_split);
   const int g_end = (int)((long long)P.G * (split + 1) / P.n_split);
   float4 G4 = make_float4(0.f, 0.f, 0.f, 0.f);
   if (in_img) G4 = __ldg(P.dl_dimage + (size_t)py * P.W + px);
   const float gr = G4.x * P.inv_T, gg = G4.y * P.inv_T, gb = G4.z * P.inv_T, ga = G4.w * P.inv_T;
-  const int lane = threadIdx.x & 31;
 
   for (int g = g_begin; g < g_end; ++g) {
-    __syncthreads();
-    if (threadIdx.x < sizeof(Group) / 4)
-      reinterpret_cast<int*>(&s_grp)[threadIdx.x] = reinterpret_cast<const int*>(P.groups + g)[threadIdx.x];
-    __syncthreads();
-    const int n = s_grp.n;
-    const TriRec* recs_set = P.recs + (size_t)s_grp.rec_set * P.F;
-    const int beg = P.bin_off[(size_t)g * n_tiles + tile], end = P.bin_off[(size_t)g * n_tiles + tile + 1];
-    float* gslot_a = P.g_slot + (size_t)s_grp.slot_a * P.V * 5;
-    float* gslot_b = P.g_slot + (size_t)s_grp.slot_b * P.V * 5;
+    load_group<NT>(sm, P.groups, g);
+    const int n = sm.grp.n;
+    const TriRec* recs_set = P.recs + (size_t)sm.grp.rec_set * P.F;
+    const size_t bi = (size_t)g * n_tiles + tile;
+    float* gslot_a = P.g_slot + (size_t)sm.grp.slot_a * P.V * 5;
+    float* gslot_b = P.g_slot + (size_t)sm.grp.slot_b * P.V * 5;
     float bestk[SPT];
     int bestf[SPT];
-#pragma unroll
-    for (int i = 0; i < SPT; ++i) { bestk[i] = -INFINITY; bestf[i] = -1; }
-
-    // ---- pass 1 (recomputed): z-test winners
-    for (int c0 = beg; c0 < end; c0 += kStageCap) {
-      const int cnt = min(kStageCap, end - c0);
-      __syncthreads();
-      stage_records<NT, MOVING>(s_rec, recs_set, P.bin_faces + c0, cnt);
-      __syncthreads();
-      if (in_img) {
-        for (int j = 0; j < cnt; ++j) {
-          const float4* r = s_rec + j * kRecF4;
-          const int face = __float_as_int(r[1].w);
-          const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
-#pragma unroll
-          for (int i = 0; i < SPT; ++i) {
-            if (i < n) {
-              const float tau = s_grp.tau[i];
-              const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
-              if (covers(e)) {
-                const float key = inv_depth<MOVING>(r, e, tau);
-                if (key > bestk[i] || (key == bestk[i] && face < bestf[i])) {
-                  bestk[i] = key;
-                  bestf[i] = face;
-                }
-              }
-            }
-          }
-        }
-      }
-    }
-
-    // ---- pass 2 (recomputed): soft products, with a count of vanishing factors so that the
-    // exclusive product prod_{l != j} (1 - A_l) never divides by a zero factor
-    bool any_unc = false;
+    pass_winners<NT, SPT, MOVING>(sm, recs_set, P.core.faces, P.core.off[bi], P.core.off[bi + 1], tb, in_img, u,
+                                  v, bestk, bestf);
+    uint32_t uncov = 0;
 #pragma unroll
     for (int i = 0; i < SPT; ++i)
-      if (i < n && bestf[i] < 0) any_unc = true;
-    const bool need_soft = __syncthreads_or(in_img && any_unc && end > beg && ga != 0.f);
-    float prod[SPT];
-    int nzero[SPT];
+      if (i < n && bestf[i] < 0) uncov |= 1u << i;
+    const int sb = P.soft.off[bi], se = P.soft.off[bi + 1];
+    const bool active = in_img && ga != 0.f;
+    if (__syncthreads_or(active && uncov != 0 && se > sb)) {
+      BwdSoftProduct<SPT> p2;
 #pragma unroll
-    for (int i = 0; i < SPT; ++i) { prod[i] = 1.f; nzero[i] = 0; }
-    if (need_soft) {
-      for (int c0 = beg; c0 < end; c0 += kStageCap) {
-        const int cnt = min(kStageCap, end - c0);
-        __syncthreads();
-        stage_records<NT, MOVING>(s_rec, recs_set, P.bin_faces + c0, cnt);
-        __syncthreads();
-        if (in_img && any_unc) {
-          for (int j = 0; j < cnt; ++j) {
-            const float4* r = s_rec + j * kRecF4;
-            const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
+      for (int i = 0; i < SPT; ++i) { p2.prod[i] = 1.f; p2.nzero[i] = 0; }
+      p2.inv_delta = P.inv_delta;
+      for_soft_terms<NT, SPT, MOVING>(sm, recs_set, P.soft.faces, sb, se, tb, active, u, v, uncov, P.r, P.r2, p2);
+      BwdSoftGrad<SPT, MOVING> p3;
 #pragma unroll
-            for (int i = 0; i < SPT; ++i) {
-              if (i < n && bestf[i] < 0) {
-                const float tau = s_grp.tau[i];
-                const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
-                if (fabsf(e.D) > kDetMin) {
-                  const SoftGeom sg = soft_geom<MOVING>(r, ps, e, tau, (s_grp.xbits >> i) & 1u);
-                  if (sg.d <= P.r2) {
-                    const float f = -expm1f(-sg.d * P.inv_delta);
-                    if (f > kTinyFactor) prod[i] *= f; else nzero[i] += 1;
-                  }
-                }
-              }
-            }
-          }
-        }
-      }
-
-      // ---- pass 3: soft-coverage adjoint, warp-reduced per candidate triangle
-      for (int c0 = beg; c0 < end; c0 += kStageCap) {
-        const int cnt = min(kStageCap, end - c0);
-        __syncthreads();
-        stage_records<NT, MOVING>(s_rec, recs_set, P.bin_faces + c0, cnt);
-        __syncthreads();
-        for (int j = 0; j < cnt; ++j) {
-          const float4* r = s_rec + j * kRecF4;
-          const int face = __float_as_int(r[1].w);
-          // per-candidate accumulators: (x, y) of the 3 vertices at slot_a and slot_b
-          float ga_x[3] = {0.f, 0.f, 0.f}, ga_y[3] = {0.f, 0.f, 0.f};
-          float gb_x[3] = {0.f, 0.f, 0.f}, gb_y[3] = {0.f, 0.f, 0.f};
-          bool any = false;
-          if (in_img && any_unc && ga != 0.f) {
-            const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
-#pragma unroll
-            for (int i = 0; i < SPT; ++i) {
-              if (i < n && bestf[i] < 0) {
-                const float tau = s_grp.tau[i];
-                const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
-                if (fabsf(e.D) <= kDetMin) continue;
-                const int X = (s_grp.xbits >> i) & 1u;
-                const SoftGeom sg = soft_geom<MOVING>(r, ps, e, tau, X);
-                if (sg.d > P.r2) continue;
-                const float f = -expm1f(-sg.d * P.inv_delta);
-                const float A = __expf(-sg.d * P.inv_delta);
-                float excl;
-                if (nzero[i] == 0) excl = prod[i] / f;
-                else excl = (nzero[i] == 1 && f <= kTinyFactor) ? prod[i] : 0.f;
-                // alpha = 1 - prod(1 - A_l): d alpha / d d_j = -excl A_j / delta
-                const float gd = ga * excl * (-A * P.inv_delta);
-                if (gd == 0.f) continue;
-                any = true;
-                const float grx = 2.f * sg.rx * gd, gry = 2.f * sg.ry * gd;  // d/d(F(tau) w* - p)
-                const float ws[3] = {sg.c.w0, sg.c.w1, sg.c.w2};
-                float gtx[3], gty[3];
-#pragma unroll
-                for (int q = 0; q < 3; ++q) { gtx[q] = ws[q] * grx; gty[q] = ws[q] * gry; }
-                if (MOVING) {
-                  // local vertex positions at tau and at keyframe X
-                  const float e1tx = fmaf(tau, r[3].x, r[0].z), e1ty = fmaf(tau, r[3].y, r[0].w);
-                  const float e2tx = fmaf(tau, r[3].z, r[1].x), e2ty = fmaf(tau, r[3].w, r[1].y);
-                  const float fx = (float)X;
-                  const float e1Xx = fmaf(fx, r[3].x, r[0].z), e1Xy = fmaf(fx, r[3].y, r[0].w);
-                  const float e2Xx = fmaf(fx, r[3].z, r[1].x), e2Xy = fmaf(fx, r[3].w, r[1].y);
-                  const float Vtx[3] = {0.f, e1tx, e2tx}, Vty[3] = {0.f, e1ty, e2ty};
-                  const float VXx[3] = {0.f, e1Xx, e2Xx}, VXy[3] = {0.f, e1Xy, e2Xy};
-                  float gXx[3] = {0.f, 0.f, 0.f}, gXy[3] = {0.f, 0.f, 0.f};
-                  float gpx = 0.f, gpy = 0.f;
-                  if (sg.c.region < 3) {
-                    // w*_i = 1 - t, w*_j = t, t = ((p' - V_i) . E) / |E|^2 on edge (i, j) of F(X)
-                    const int ei = sg.c.ei, ej = sg.c.ej;
-                    float gti = 0.f, gtj = 0.f, Ex = 0.f, Ey = 0.f, Rx = 0.f, Ry = 0.f;
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                      if (q == ei) { gti = Vtx[q] * grx + Vty[q] * gry; Rx = sg.ppx - VXx[q]; Ry = sg.ppy - VXy[q]; Ex -= VXx[q]; Ey -= VXy[q]; }
-                      if (q == ej) { gtj = Vtx[q] * grx + Vty[q] * gry; Ex += VXx[q]; Ey += VXy[q]; }
-                    }
-                    const float L2 = fmaf(Ex, Ex, Ey * Ey);
-                    const float gt = (gtj - gti) / L2, t = sg.c.t;
-                    gpx = gt * Ex;
-                    gpy = gt * Ey;
-                    const float gix = gt * (-Ex - Rx + 2.f * t * Ex), giy = gt * (-Ey - Ry + 2.f * t * Ey);
-                    const float gjx = gt * (Rx - 2.f * t * Ex), gjy = gt * (Ry - 2.f * t * Ey);
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                      if (q == ei) { gXx[q] += gix; gXy[q] += giy; }
-                      if (q == ej) { gXx[q] += gjx; gXy[q] += gjy; }
-                    }
-                  }
-                  // p' = F(X) w(tau)
-                  const float w1 = sg.w1, w2 = sg.w2, w0 = 1.f - w1 - w2;
-                  const float wv[3] = {w0, w1, w2};
-                  float gw[3];
-#pragma unroll
-                  for (int q = 0; q < 3; ++q) {
-                    gXx[q] = fmaf(wv[q], gpx, gXx[q]);
-                    gXy[q] = fmaf(wv[q], gpy, gXy[q]);
-                    gw[q] = VXx[q] * gpx + VXy[q] * gpy;
-                  }
-                  // w = N / D with D = N0 + N1 + N2
-                  const float sw = wv[0] * gw[0] + wv[1] * gw[1] + wv[2] * gw[2];
-                  const float invD = 1.f / e.D;
-                  float ax[3], ay[3], ex[3], ey[3];
-                  rel_vertices<MOVING>(r, ps, tau, ax, ay);
-                  edge_backward((gw[0] - sw) * invD, (gw[1] - sw) * invD, (gw[2] - sw) * invD, ax, ay, ex, ey);
-#pragma unroll
-                  for (int q = 0; q < 3; ++q) { gtx[q] += ex[q]; gty[q] += ey[q]; }
-                  // F(tau) = lerp of the two keyframes; F(X) is keyframe X
-#pragma unroll
-                  for (int q = 0; q < 3; ++q) {
-                    ga_x[q] = fmaf(1.f - tau, gtx[q], ga_x[q]);
-                    ga_y[q] = fmaf(1.f - tau, gty[q], ga_y[q]);
-                    gb_x[q] = fmaf(tau, gtx[q], gb_x[q]);
-                    gb_y[q] = fmaf(tau, gty[q], gb_y[q]);
-                    if (X == 0) { ga_x[q] += gXx[q]; ga_y[q] += gXy[q]; }
-                    else { gb_x[q] += gXx[q]; gb_y[q] += gXy[q]; }
-                  }
-                } else {
-                  // exact distance: d d / d v_i = 2 (F w* - p) w*_i
-#pragma unroll
-                  for (int q = 0; q < 3; ++q) { ga_x[q] += gtx[q]; ga_y[q] += gty[q]; }
-                }
-              }
-            }
-          }
-          if (__any_sync(0xffffffffu, any)) {
-            float vals[12];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-              vals[2 * q] = warp_sum(ga_x[q]);
-              vals[2 * q + 1] = warp_sum(ga_y[q]);
-              vals[6 + 2 * q] = MOVING ? warp_sum(gb_x[q]) : 0.f;
-              vals[7 + 2 * q] = MOVING ? warp_sum(gb_y[q]) : 0.f;
-            }
-            if (lane == 0) {
-#pragma unroll
-              for (int q = 0; q < 3; ++q) {
-                const int vid = __ldg(P.faces + 3 * face + q);
-                atomicAdd(gslot_a + (size_t)vid * 5, vals[2 * q]);
-                atomicAdd(gslot_a + (size_t)vid * 5 + 1, vals[2 * q + 1]);
-                if (MOVING) {
-                  atomicAdd(gslot_b + (size_t)vid * 5, vals[6 + 2 * q]);
-                  atomicAdd(gslot_b + (size_t)vid * 5 + 1, vals[7 + 2 * q]);
-                }
-              }
-            }
-          }
-        }
-      }
+      for (int i = 0; i < SPT; ++i) { p3.prod[i] = p2.prod[i]; p3.nzero[i] = p2.nzero[i]; }
+      p3.ga = ga;
+      p3.inv_delta = P.inv_delta;
+      p3.rec = sm.rec;
+      p3.faces = P.faces;
+      p3.gslot_a = gslot_a;
+      p3.gslot_b = gslot_b;
+      for_soft_terms<NT, SPT, MOVING>(sm, recs_set, P.soft.faces, sb, se, tb, active, u, v, uncov, P.r, P.r2, p3);
     }
 
     // ---- covered samples: shading adjoint and barycentric adjoint of the winner
@@ -292,11 +289,16 @@ __global__ void __launch_bounds__(TW * TH) raster_bwd_kernel(RasterParams P) {
       for (int i = 0; i < SPT; ++i) {
         if (i < n && bestf[i] >= 0) {
           const int f = bestf[i];
-          const float tau = s_grp.tau[i];
+          const float tau = MOVING ? sm.grp.tau[i] : 0.f;
           float4 r[kRecF4];
           const TriRec* src = recs_set + f;
-#pragma unroll
-          for (int q = 0; q < (MOVING ? kRecF4 : 3); ++q) r[q] = __ldg(&src->f4[q]);
+          r[kR_O] = __ldg(&src->f4[kR_O]);
+          r[kR_E2] = __ldg(&src->f4[kR_E2]);
+          if (MOVING) {
+            r[kR_D] = __ldg(&src->f4[kR_D]);
+            r[kR_G] = __ldg(&src->f4[kR_G]);
+            r[kR_A] = __ldg(&src->f4[kR_A]);
+          }
           const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
           const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
           const float invD = 1.0f / e.D;
@@ -310,9 +312,9 @@ __global__ void __launch_bounds__(TW * TH) raster_bwd_kernel(RasterParams P) {
             al[q][0] = __ldg(P.albedo + 3 * vid[q]);
             al[q][1] = __ldg(P.albedo + 3 * vid[q] + 1);
             al[q][2] = __ldg(P.albedo + 3 * vid[q] + 2);
-            float4 na = __ldg(P.slot_nrm + (size_t)s_grp.slot_a * P.V + vid[q]);
+            float4 na = __ldg(P.slot_nrm + (size_t)sm.grp.slot_a * P.V + vid[q]);
             if (MOVING) {
-              const float4 nb = __ldg(P.slot_nrm + (size_t)s_grp.slot_b * P.V + vid[q]);
+              const float4 nb = __ldg(P.slot_nrm + (size_t)sm.grp.slot_b * P.V + vid[q]);
               na.x = fmaf(tau, nb.x - na.x, na.x);
               na.y = fmaf(tau, nb.y - na.y, na.y);
               na.z = fmaf(tau, nb.z - na.z, na.z);

@@ -17,7 +17,8 @@ namespace mbr {
 
 constexpr int kMaxSpt = 16;           // sub-frames per thread held in registers (max)
 constexpr float kDetMin = 1e-10f;     // |det F| at or below: triangle skipped at that sample
-constexpr int kRecF4 = 7;             // float4s per triangle record
+constexpr int kRecF4 = 9;             // float4s per triangle record
+constexpr int kRecF4Static = 4;       // float4s a static (plain-solver) record needs
 
 // Per (record set, face) triangle record.  Local frame: origin o = v0 at the set's first
 // keyframe; e1 = v1 - v0, e2 = v2 - v0 at that keyframe; d1, d2 = change of e1, e2 over the
@@ -27,12 +28,15 @@ constexpr int kRecF4 = 7;             // float4s per triangle record
 // i.e. the numerators / denominator of Eq. time-dependent2 written about a moving local origin
 // (the coefficients are the appendix's A_1..A_3, a_1..a_3 up to the change of origin).
 //   f4[0] = (ox, oy, e1x, e1y)        f4[1] = (e2x, e2y, D0, face bits)
-//   f4[2] = (z0_0, z0_1, z0_2, flags) f4[3] = (d1x, d1y, d2x, d2y)
-//   f4[4] = (gx, gy, c1, c2)          f4[5] = (a11, a12, D1, D2)
-//   f4[6] = (dz0, dz1, dz2, 0)
+//   f4[2] = (z0_0, z0_1, z0_2, flags) f4[3] = bounding box at the first keyframe
+//                                              (xmin, xmax, ymin, ymax)
+//   f4[4] = change of that box over the segment (the box of the lerped triangle at tau lies in
+//           the lerp of the two keyframe boxes)
+//   f4[5] = (d1x, d1y, d2x, d2y)      f4[6] = (gx, gy, c1, c2)
+//   f4[7] = (a11, a12, D1, D2)        f4[8] = (dz0, dz1, dz2, 0)
 // with c1 = -cross(g, e2), c2 = -cross(e1, g), a11 = -cross(g, d2), a12 = -cross(d1, g),
 // D0 = cross(e1, e2), D1 = cross(e1, d2) + cross(d1, e2), D2 = cross(d1, d2).
-// Static (plain) records only use f4[0..2].
+// Static (plain) records only use f4[0..3].
 struct TriRec {
   float4 f4[kRecF4];
 };

@@ -78,8 +78,8 @@ __global__ void setup_kernel(const float4* __restrict__ pos, const int32_t* __re
   if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= V || i1 >= V || i2 >= V) {
     // invalid face: culled (never binned, never dereferenced again)
     TriRec* dst = recs + idx;
-    dst->f4[1] = make_float4(0.f, 0.f, 0.f, __int_as_float(f));
-    dst->f4[2] = make_float4(1.f, 1.f, 1.f, __uint_as_float(kFlagCulled));
+    dst->f4[kR_E2] = make_float4(0.f, 0.f, 0.f, __int_as_float(f));
+    dst->f4[kR_Z] = make_float4(1.f, 1.f, 1.f, __uint_as_float(kFlagCulled));
     return;
   }
   const float4 a0 = pos[(size_t)sl.x * V + i0], a1 = pos[(size_t)sl.x * V + i1], a2 = pos[(size_t)sl.x * V + i2];
@@ -92,14 +92,20 @@ __global__ void setup_kernel(const float4* __restrict__ pos, const int32_t* __re
   if (a0.z <= znear || a1.z <= znear || a2.z <= znear || b0.z <= znear || b1.z <= znear || b2.z <= znear)
     flags |= kFlagCulled;
   TriRec r;
-  r.f4[0] = make_float4(a0.x, a0.y, e1x, e1y);
-  r.f4[1] = make_float4(e2x, e2y, cross2(e1x, e1y, e2x, e2y), __int_as_float(f));
-  r.f4[2] = make_float4(a0.z, a1.z, a2.z, __uint_as_float(flags));
-  r.f4[3] = make_float4(d1x, d1y, d2x, d2y);
-  r.f4[4] = make_float4(gx, gy, -cross2(gx, gy, e2x, e2y), -cross2(e1x, e1y, gx, gy));
-  r.f4[5] = make_float4(-cross2(gx, gy, d2x, d2y), -cross2(d1x, d1y, gx, gy),
-                        cross2(e1x, e1y, d2x, d2y) + cross2(d1x, d1y, e2x, e2y), cross2(d1x, d1y, d2x, d2y));
-  r.f4[6] = make_float4(b0.z - a0.z, b1.z - a1.z, b2.z - a2.z, 0.f);
+  r.f4[kR_O] = make_float4(a0.x, a0.y, e1x, e1y);
+  r.f4[kR_E2] = make_float4(e2x, e2y, cross2(e1x, e1y, e2x, e2y), __int_as_float(f));
+  r.f4[kR_Z] = make_float4(a0.z, a1.z, a2.z, __uint_as_float(flags));
+  const float4 ba = make_float4(fminf(a0.x, fminf(a1.x, a2.x)), fmaxf(a0.x, fmaxf(a1.x, a2.x)),
+                                fminf(a0.y, fminf(a1.y, a2.y)), fmaxf(a0.y, fmaxf(a1.y, a2.y)));
+  const float4 bb = make_float4(fminf(b0.x, fminf(b1.x, b2.x)), fmaxf(b0.x, fmaxf(b1.x, b2.x)),
+                                fminf(b0.y, fminf(b1.y, b2.y)), fmaxf(b0.y, fmaxf(b1.y, b2.y)));
+  r.f4[kR_BB] = ba;
+  r.f4[kR_DBB] = make_float4(bb.x - ba.x, bb.y - ba.y, bb.z - ba.z, bb.w - ba.w);
+  r.f4[kR_D] = make_float4(d1x, d1y, d2x, d2y);
+  r.f4[kR_G] = make_float4(gx, gy, -cross2(gx, gy, e2x, e2y), -cross2(e1x, e1y, gx, gy));
+  r.f4[kR_A] = make_float4(-cross2(gx, gy, d2x, d2y), -cross2(d1x, d1y, gx, gy),
+                           cross2(e1x, e1y, d2x, d2y) + cross2(d1x, d1y, e2x, e2y), cross2(d1x, d1y, d2x, d2y));
+  r.f4[kR_DZ] = make_float4(b0.z - a0.z, b1.z - a1.z, b2.z - a2.z, 0.f);
   TriRec* dst = recs + idx;
 #pragma unroll
   for (int q = 0; q < kRecF4; ++q) dst->f4[q] = r.f4[q];
@@ -108,10 +114,10 @@ __global__ void setup_kernel(const float4* __restrict__ pos, const int32_t* __re
 // swept bounding box of a record over [tau_lo, tau_hi] (linear motion: union of the two ends)
 __device__ __forceinline__ void swept_bbox(const TriRec& r, float tlo, float thi, float& xmin,
                                            float& xmax, float& ymin, float& ymax) {
-  const float ox = r.f4[0].x, oy = r.f4[0].y;
-  const float e1x = r.f4[0].z, e1y = r.f4[0].w, e2x = r.f4[1].x, e2y = r.f4[1].y;
-  const float d1x = r.f4[3].x, d1y = r.f4[3].y, d2x = r.f4[3].z, d2y = r.f4[3].w;
-  const float gx = r.f4[4].x, gy = r.f4[4].y;
+  const float ox = r.f4[kR_O].x, oy = r.f4[kR_O].y;
+  const float e1x = r.f4[kR_O].z, e1y = r.f4[kR_O].w, e2x = r.f4[kR_E2].x, e2y = r.f4[kR_E2].y;
+  const float d1x = r.f4[kR_D].x, d1y = r.f4[kR_D].y, d2x = r.f4[kR_D].z, d2y = r.f4[kR_D].w;
+  const float gx = r.f4[kR_G].x, gy = r.f4[kR_G].y;
   xmin = ymin = INFINITY;
   xmax = ymax = -INFINITY;
   const float ts[2] = {tlo, thi};
@@ -149,7 +155,7 @@ __global__ void bin_kernel(const TriRec* __restrict__ recs, int F, const Group* 
   const int g = (int)(idx / F), f = (int)(idx - (size_t)g * F);
   const Group& gr = groups[g];
   const TriRec& rec = recs[(size_t)gr.rec_set * F + f];
-  if (__float_as_uint(rec.f4[2].w) & kFlagCulled) return;
+  if (__float_as_uint(rec.f4[kR_Z].w) & kFlagCulled) return;
   float xmin, xmax, ymin, ymax;
   swept_bbox(rec, gr.tau_lo, gr.tau_hi, xmin, xmax, ymin, ymax);
   int i0, i1, j0, j1;
@@ -248,11 +254,26 @@ __global__ void scan_apply_kernel(const int32_t* __restrict__ in, int n, const i
 }
 
 // ---------------------------------------------------------------- a4-a8: forward raster
+template <int SPT>
+struct FwdSoftProduct {
+  float prod[SPT];
+  float inv_delta;
+  __device__ __forceinline__ void begin(int) {}
+  template <typename PS>
+  __device__ __forceinline__ void term(int, const float4*, const PS&, const EdgeVals&, const SoftGeom& sg, int i,
+                                       float, int) {
+    const float f = -expm1f(-sg.d * inv_delta);
+#pragma unroll
+    for (int q = 0; q < SPT; ++q)
+      if (q == i) prod[q] *= f;
+  }
+  __device__ __forceinline__ void end(int, float) {}
+};
+
 template <int TW, int TH, int SPT, bool MOVING>
 __global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(RasterParams P) {
   constexpr int NT = TW * TH;
-  __shared__ float4 s_rec[kStageCap * kRecF4];
-  __shared__ Group s_grp;
+  __shared__ RasterSmem sm;
   const int n_tiles = P.tiles_x * P.tiles_y;
   const int tile = blockIdx.x % n_tiles, split = blockIdx.x / n_tiles;
   const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
@@ -260,85 +281,31 @@ __global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(RasterParams P) {
   const bool in_img = px < P.W && py < P.H;
   const float u = (2.f * px + 1.f) / P.W - 1.f;
   const float v = 1.f - (2.f * py + 1.f) / P.H;
+  const TileBox tb = tile_box<TW, TH>(tx, ty, P.W, P.H);
   const int g_begin = (int)((long long)P.G * split / P.n_split);
   const int g_end = (int)((long long)P.G * (split + 1) / P.n_split);
   float acc_r = 0.f, acc_g = 0.f, acc_b = 0.f, acc_a = 0.f;
 
   for (int g = g_begin; g < g_end; ++g) {
-    __syncthreads();
-    if (threadIdx.x < sizeof(Group) / 4)
-      reinterpret_cast<int*>(&s_grp)[threadIdx.x] = reinterpret_cast<const int*>(P.groups + g)[threadIdx.x];
-    __syncthreads();
-    const int n = s_grp.n;
-    const TriRec* recs_set = P.recs + (size_t)s_grp.rec_set * P.F;
-    const int beg = P.bin_off[(size_t)g * n_tiles + tile], end = P.bin_off[(size_t)g * n_tiles + tile + 1];
+    load_group<NT>(sm, P.groups, g);
+    const int n = sm.grp.n;
+    const TriRec* recs_set = P.recs + (size_t)sm.grp.rec_set * P.F;
+    const size_t bi = (size_t)g * n_tiles + tile;
     float bestk[SPT];
     int bestf[SPT];
-#pragma unroll
-    for (int i = 0; i < SPT; ++i) { bestk[i] = -INFINITY; bestf[i] = -1; }
-
-    // ---- pass 1: coverage + z-test (Sec. 3.1) with w(tau) of Eq. time-dependent2
-    for (int c0 = beg; c0 < end; c0 += kStageCap) {
-      const int cnt = min(kStageCap, end - c0);
-      __syncthreads();
-      stage_records<NT, MOVING>(s_rec, recs_set, P.bin_faces + c0, cnt);
-      __syncthreads();
-      if (in_img) {
-        for (int j = 0; j < cnt; ++j) {
-          const float4* r = s_rec + j * kRecF4;
-          const int face = __float_as_int(r[1].w);
-          const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
-#pragma unroll
-          for (int i = 0; i < SPT; ++i) {
-            if (i < n) {
-              const float tau = s_grp.tau[i];
-              const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
-              if (covers(e)) {
-                const float key = inv_depth<MOVING>(r, e, tau);
-                if (key > bestk[i] || (key == bestk[i] && face < bestf[i])) {
-                  bestk[i] = key;
-                  bestf[i] = face;
-                }
-              }
-            }
-          }
-        }
-      }
-    }
-
-    // ---- pass 2: soft coverage of uncovered samples (Eqs. probability-function .. back)
-    bool any_unc = false;
+    pass_winners<NT, SPT, MOVING>(sm, recs_set, P.core.faces, P.core.off[bi], P.core.off[bi + 1], tb, in_img, u,
+                                  v, bestk, bestf);
+    uint32_t uncov = 0;
 #pragma unroll
     for (int i = 0; i < SPT; ++i)
-      if (i < n && bestf[i] < 0) any_unc = true;
-    float prod[SPT];
+      if (i < n && bestf[i] < 0) uncov |= 1u << i;
+    FwdSoftProduct<SPT> soft;
 #pragma unroll
-    for (int i = 0; i < SPT; ++i) prod[i] = 1.f;
-    if (__syncthreads_or(in_img && any_unc && end > beg)) {
-      for (int c0 = beg; c0 < end; c0 += kStageCap) {
-        const int cnt = min(kStageCap, end - c0);
-        __syncthreads();
-        stage_records<NT, MOVING>(s_rec, recs_set, P.bin_faces + c0, cnt);
-        __syncthreads();
-        if (in_img && any_unc) {
-          for (int j = 0; j < cnt; ++j) {
-            const float4* r = s_rec + j * kRecF4;
-            const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
-#pragma unroll
-            for (int i = 0; i < SPT; ++i) {
-              if (i < n && bestf[i] < 0) {
-                const float tau = s_grp.tau[i];
-                const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
-                if (fabsf(e.D) > kDetMin) {
-                  const SoftGeom sg = soft_geom<MOVING>(r, ps, e, tau, (s_grp.xbits >> i) & 1u);
-                  if (sg.d <= P.r2) prod[i] *= -expm1f(-sg.d * P.inv_delta);
-                }
-              }
-            }
-          }
-        }
-      }
-    }
+    for (int i = 0; i < SPT; ++i) soft.prod[i] = 1.f;
+    soft.inv_delta = P.inv_delta;
+    const int sb = P.soft.off[bi], se = P.soft.off[bi + 1];
+    if (__syncthreads_or(in_img && uncov != 0 && se > sb))
+      for_soft_terms<NT, SPT, MOVING>(sm, recs_set, P.soft.faces, sb, se, tb, in_img, u, v, uncov, P.r, P.r2, soft);
 
     // ---- shading of the winners (Eq. fore + Lambert) and temporal accumulation (Sec. 3.3)
     if (in_img) {
@@ -346,13 +313,18 @@ __global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(RasterParams P) {
       for (int i = 0; i < SPT; ++i) {
         if (i < n) {
           const int f = bestf[i];
-          if (P.dbg_ids && s_grp.k0 + i == P.dbg_k) P.dbg_ids[(size_t)py * P.W + px] = f;
+          if (P.dbg_ids && sm.grp.k0 + i == P.dbg_k) P.dbg_ids[(size_t)py * P.W + px] = f;
           if (f >= 0) {
-            const float tau = s_grp.tau[i];
+            const float tau = MOVING ? sm.grp.tau[i] : 0.f;
             float4 r[kRecF4];
             const TriRec* src = recs_set + f;
-#pragma unroll
-            for (int q = 0; q < (MOVING ? kRecF4 : 3); ++q) r[q] = __ldg(&src->f4[q]);
+            r[kR_O] = __ldg(&src->f4[kR_O]);
+            r[kR_E2] = __ldg(&src->f4[kR_E2]);
+            if (MOVING) {
+              r[kR_D] = __ldg(&src->f4[kR_D]);
+              r[kR_G] = __ldg(&src->f4[kR_G]);
+              r[kR_A] = __ldg(&src->f4[kR_A]);
+            }
             const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
             const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
             const float invD = 1.0f / e.D;
@@ -364,9 +336,9 @@ __global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(RasterParams P) {
               cr = fmaf(w[q], __ldg(P.albedo + 3 * vid), cr);
               cg = fmaf(w[q], __ldg(P.albedo + 3 * vid + 1), cg);
               cb = fmaf(w[q], __ldg(P.albedo + 3 * vid + 2), cb);
-              float4 na = __ldg(P.slot_nrm + (size_t)s_grp.slot_a * P.V + vid);
+              float4 na = __ldg(P.slot_nrm + (size_t)sm.grp.slot_a * P.V + vid);
               if (MOVING) {
-                const float4 nb = __ldg(P.slot_nrm + (size_t)s_grp.slot_b * P.V + vid);
+                const float4 nb = __ldg(P.slot_nrm + (size_t)sm.grp.slot_b * P.V + vid);
                 na.x = fmaf(tau, nb.x - na.x, na.x);
                 na.y = fmaf(tau, nb.y - na.y, na.y);
                 na.z = fmaf(tau, nb.z - na.z, na.z);
@@ -383,7 +355,7 @@ __global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(RasterParams P) {
             acc_b = fmaf(cb, shade, acc_b);
             acc_a += 1.f;
           } else {
-            acc_a += 1.f - prod[i];
+            acc_a += 1.f - soft.prod[i];
           }
         }
       }
@@ -419,7 +391,7 @@ __global__ void count_kernel(const TriRec* __restrict__ recs, int F, const Group
     const int g = (int)(idx / F), f = (int)(idx - (size_t)g * F);
     const Group& gr = groups[g];
     const TriRec& rec = recs[(size_t)gr.rec_set * F + f];
-    const bool culled = (__float_as_uint(rec.f4[2].w) & kFlagCulled) != 0;
+    const bool culled = (__float_as_uint(rec.f4[kR_Z].w) & kFlagCulled) != 0;
     for (int i = 0; i < gr.n && !culled; ++i) {
       float xmin, xmax, ymin, ymax;
       swept_bbox(rec, gr.tau[i], gr.tau[i], xmin, xmax, ymin, ymax);

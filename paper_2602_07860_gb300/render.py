@@ -128,6 +128,14 @@ class Context:
         m.verts, m.faces, m.albedo = verts.data_ptr(), faces.data_ptr(), albedo.data_ptr()
         return m
 
+    def set_profiling(self, on=True):
+        self._raise(self.L.mbr_set_profiling(self.h, int(bool(on))))
+
+    def stats(self):
+        st = _lib.MbrStats()
+        self._raise(self.L.mbr_get_stats(self.h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
     def set_tuning(self, tile=16, spt=8, splits=0):
         self._raise(self.L.mbr_set_tuning(self.h, int(tile), int(spt), int(splits)))
 
