@@ -75,17 +75,23 @@ def test_autograd_function_uses_the_adjoint(ctx, solver):
     assert torch.allclose(aa.grad, ga, rtol=1e-4, atol=1e-6)
 
 
-@pytest.mark.parametrize("x0,y0", [(116, 100), (56, 88), (104, 40)])
+@pytest.mark.parametrize("x0,y0", [(116, 100), (56, 88), (56, 152)])
 def test_full_size_rotation_gradient_window(ctx, x0, y0):
-    """Full-size rotation workload with dL/dimage supported on a 24x24 window (object interior,
-    and two windows on the swept silhouette): GPU adjoint vs the oracle adjoint of that window."""
+    """Full-size rotation workload (the benchmark's) with an L2 image loss against a target (the
+    same object scaled by 1.02) on a 24x24 window: GPU adjoint vs the oracle adjoint.
+
+    Bound: globally |g - g_o| <= 1e-3 |g_o|; per vertex |g_v - g_o,v| <= 1e-3 |g_o,v| + 1e-4 max|g_o|.
+    The floor is the FP32 limit of the soft term: exp(-d / delta) with delta = 1e-4 turns the
+    ~6e-8 absolute error of single-precision screen positions into ~(2 r / delta) 6e-8 ~ 6e-5
+    relative error per term, which shows where a vertex's contributions nearly cancel."""
     sc = scenes.config2()
     w, h = 24, 24
+    target = dict(sc, verts=sc["verts"] * 1.02)
     for solver in ("fast", "plain"):
         mode = ORACLE_MODE[solver]
         r = oracle.render(sc, mode, window=(x0, y0, w, h), ambig=True)
-        rng = np.random.default_rng(1)
-        Gw = rng.normal(size=(h, w, 4))
+        tgt = oracle.render(target, mode, window=(x0, y0, w, h))["rgba"]
+        Gw = 2.0 * (r["rgba"] - tgt)
         Gw[(r["ambig"] != 0).any(0)] = 0.0
         gv_o, _, _ = oracle.render_backward(sc, Gw, mode, window=(x0, y0, w, h))
         G = np.zeros((sc["H"], sc["W"], 4))
@@ -95,6 +101,7 @@ def test_full_size_rotation_gradient_window(ctx, x0, y0):
                                          torch.as_tensor(G, dtype=torch.float32, device="cuda"), solver)
         gv = gv.cpu().double().numpy()
         nv_o = np.linalg.norm(gv_o, axis=1)
-        assert nv_o.max() > 0 and (Gw != 0).mean() > 0.1
+        assert nv_o.max() > 0 and (Gw != 0).any(-1).mean() > 0.1
+        assert np.linalg.norm(gv - gv_o) <= 1e-3 * np.linalg.norm(gv_o)
         err = np.linalg.norm(gv - gv_o, axis=1)
-        assert np.all(err <= 1e-3 * nv_o + 1e-6 * nv_o.max()), (solver, float(err.max()), float(nv_o.max()))
+        assert np.all(err <= 1e-3 * nv_o + 1e-4 * nv_o.max()), (solver, float(err.max()), float(nv_o.max()))
