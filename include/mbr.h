@@ -158,6 +158,26 @@ typedef struct {
 int mbr_set_profiling(mbr_ctx* ctx, int32_t on);
 int mbr_get_stats(mbr_ctx* ctx, mbr_stats* out);
 
+/* Forward render like mbr_render_blur, for callers that cannot allocate device memory: a process
+ * that hands all of the GPU's memory to its own pool or to a fixed budget at start-up, or a
+ * latency-sensitive loop that cannot take the device-wide synchronisation a cudaMalloc/cudaFree
+ * may bring.  The paper has no counterpart; this is a deployment option of this library.
+ *
+ * It needs no context.  All scratch comes from one statically sized array of 32 MiB that every
+ * GPU loading this library holds until the process exits; nothing is allocated or freed (no
+ * cudaMalloc, cudaFree or allocating library call).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Renders whose scratch would not fit (large meshes, many sub-frames or segments, large images)
+ * return MBR_ERR_ARG with a message naming the limit; use mbr_render_blur for those.
+ * All calls on a device share the array, which keeps the last call's contents (the call clears
+ * what it accumulates): calls whose work overlaps on the GPU -- different streams or threads
+ * without ordering between them -- race.  The call synchronises its stream once, like
+ * mbr_render_blur.  Arguments are those of mbr_render_blur; err (may be NULL) receives the error
+ * message of a failed call, truncated to err_len bytes including the terminating zero. */
+int mbr_render_blur_noalloc(const mbr_mesh* mesh, const mbr_motion* motion, const mbr_camera* camera,
+                            int32_t T, int32_t H, int32_t W, int32_t solver, float* image,
+                            void* cuda_stream, char* err, int32_t err_len);
+
 /* Message of the last failed call on ctx ("" if none).  Valid until the next call. */
 const char* mbr_last_error(mbr_ctx* ctx);
 

@@ -17,7 +17,7 @@ SOLVERS = {"plain": MBR_PLAIN, "fast": MBR_FAST}
 
 EXPORTS = ["mbr_create", "mbr_destroy", "mbr_render_blur", "mbr_render_blur_backward", "mbr_render_blur_batch",
            "mbr_debug_winners", "mbr_count_candidates", "mbr_set_tuning", "mbr_set_profiling", "mbr_get_stats",
-           "mbr_last_error"]
+           "mbr_render_blur_noalloc", "mbr_last_error"]
 
 
 class MbrMesh(ctypes.Structure):
@@ -92,6 +92,9 @@ def load(build_if_missing=True):
     L.mbr_set_profiling.restype = c_int32
     L.mbr_get_stats.argtypes = [c_void_p, P(MbrStats)]
     L.mbr_get_stats.restype = c_int32
+    L.mbr_render_blur_noalloc.argtypes = [P(MbrMesh), P(MbrMotion), P(MbrCamera), c_int32, c_int32, c_int32,
+                                          c_int32, c_void_p, c_void_p, ctypes.c_char_p, c_int32]
+    L.mbr_render_blur_noalloc.restype = c_int32
     L.mbr_last_error.argtypes = [c_void_p]
     L.mbr_last_error.restype = ctypes.c_char_p
     _lib = L

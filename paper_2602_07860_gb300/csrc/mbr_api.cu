@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -633,3 +634,149 @@ int mbr_render_blur_batch(mbr_ctx* c, int32_t n, const mbr_item* items, int32_t 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ allocation-free forward render
+// mbr_render_blur_noalloc: the forward pipeline of mbr_render_blur, with every scratch buffer
+// carved out of one file-scope device array instead of context-owned allocations.  The device
+// address of the array is looked up once per device (cudaGetSymbolAddress) and passed to the
+// kernels like any other pointer; in host code the array's name is only a stand-in.
+
+constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // per device, held until process exit
+static __device__ __align__(256) unsigned char g_mbr_static_scratch[kStaticScratchBytes];
+
+namespace {
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kStaticMaxDevices] = {};
+
+struct Arena {
+  char* base;
+  size_t cap, used;
+  void* take(size_t bytes) {
+    const size_t o = (used + 255) & ~size_t(255);
+    if (o > cap || bytes > cap - o) return nullptr;
+    used = o + bytes;
+    return base + o;
+  }
+};
+
+int noalloc_forward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mbr_camera* cam, int T, int H,
+                    int W, int solver, float* image, cudaStream_t st) {
+  int rc = validate(c, mesh, motion, cam, T, H, W, solver);
+  if (rc) return rc;
+  if (!image) return fail(c, MBR_ERR_ARG, "null image");
+  int dev = 0;
+  CUDA_TRY(c, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kStaticMaxDevices) return fail(c, MBR_ERR_ARG, "device %d out of range", dev);
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+      void* p = nullptr;
+      CUDA_TRY(c, cudaGetSymbolAddress(&p, g_mbr_static_scratch));
+      g_static_addr[dev] = p;
+    }
+    base = g_static_addr[dev];
+  }
+
+  std::vector<SlotXform> xf;
+  std::vector<int2> sets;
+  std::vector<Group> groups;
+  Prepared pp;
+  if ((rc = build_tables(c, motion, cam, T, solver, xf, sets, groups, pp))) return rc;
+  const int V = mesh->V, F = mesh->F, tw = 16, th = 16;
+  pp.tiles_x = (W + tw - 1) / tw;
+  pp.tiles_y = (H + th - 1) / th;
+  pp.n_tiles = pp.tiles_x * pp.tiles_y;
+  pp.n_split = 1;
+  pp.r = (float)std::sqrt((double)cam->delta * std::log(1e12));
+  const long long nb = (long long)pp.G * pp.n_tiles;
+
+  // fixed part of the arena
+  Arena A{(char*)base, kStaticScratchBytes, 0};
+  int* d_status = (int*)A.take(sizeof(int32_t));
+  float* nacc = (float*)A.take(sizeof(float) * 3 * (size_t)V);
+  float4* pos = (float4*)A.take(sizeof(float4) * (size_t)pp.n_slots * V);
+  float4* nrm = (float4*)A.take(sizeof(float4) * (size_t)pp.n_slots * V);
+  TriRec* recs = (TriRec*)A.take(sizeof(TriRec) * (size_t)pp.n_sets * std::max(F, 1));
+  SlotXform* d_xf = (SlotXform*)A.take(sizeof(SlotXform) * xf.size());
+  int2* d_sets = (int2*)A.take(sizeof(int2) * sets.size());
+  Group* d_groups = (Group*)A.take(sizeof(Group) * groups.size());
+  int32_t *counts[2], *offs[2], *tmp[2], *cursor[2], *list[2];
+  for (int q = 0; q < 2; ++q) {
+    counts[q] = (int32_t*)A.take(sizeof(int32_t) * (size_t)nb);
+    offs[q] = (int32_t*)A.take(sizeof(int32_t) * (size_t)(nb + 1));
+    tmp[q] = (int32_t*)A.take(sizeof(int32_t) * scan_temp_ints((int)nb));
+    cursor[q] = (int32_t*)A.take(sizeof(int32_t) * (size_t)nb);
+  }
+  if (!d_status || !nacc || !pos || !nrm || !recs || !d_xf || !d_sets || !d_groups || !counts[1] || !offs[1] ||
+      !tmp[1] || !cursor[1] || nb > (1LL << 30))
+    return fail(c, MBR_ERR_ARG,
+                "render needs more than the %zu MiB static scratch (V=%d F=%d T=%d %dx%d); use mbr_render_blur",
+                kStaticScratchBytes >> 20, V, F, T, W, H);
+  pp.d_xf = d_xf;
+  pp.d_groups = d_groups;
+  CUDA_TRY(c, cudaMemcpyAsync(d_xf, xf.data(), sizeof(SlotXform) * xf.size(), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(c, cudaMemcpyAsync(d_sets, sets.data(), sizeof(int2) * sets.size(), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(c, cudaMemcpyAsync(d_groups, groups.data(), sizeof(Group) * groups.size(), cudaMemcpyHostToDevice, st));
+
+  // the array keeps the previous call's contents: clear everything that accumulates
+  CUDA_TRY(c, cudaMemsetAsync(d_status, 0, sizeof(int32_t), st));
+  CUDA_TRY(c, cudaMemsetAsync(nacc, 0, sizeof(float) * 3 * V, st));
+  launch_face_normals(mesh->verts, mesh->faces, F, V, nacc, d_status, st);
+  launch_xform(mesh->verts, nacc, V, d_xf, pp.n_slots, cam->tan_half_fov, pos, nrm, st);
+  launch_setup(pos, mesh->faces, F, V, d_sets, pp.n_sets, cam->znear, recs, st);
+  const float margins[2] = {kCoreMargin, pp.r + kCoreMargin};
+  int32_t host[3] = {0, 0, 0};
+  for (int q = 0; q < 2; ++q) {
+    CUDA_TRY(c, cudaMemsetAsync(counts[q], 0, sizeof(int32_t) * (size_t)nb, st));
+    launch_bin(false, recs, F, d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles, margins[q], counts[q], nullptr,
+               nullptr, d_status, st);
+    launch_scan(counts[q], (int)nb, offs[q], tmp[q], st);
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaMemcpyAsync(host + q, offs[q] + nb, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(host + 2, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  if (host[2] & kStatusBadFace) return fail(c, MBR_ERR_ARG, "face index outside [0, V)");
+  for (int q = 0; q < 2; ++q) {
+    list[q] = (int32_t*)A.take(sizeof(int32_t) * (size_t)std::max(host[q], 1));
+    if (host[q] < 0 || !list[q])
+      return fail(c, MBR_ERR_ARG, "tile lists (%d + %d entries) exceed the %zu MiB static scratch; use mbr_render_blur",
+                  host[0], host[1], kStaticScratchBytes >> 20);
+  }
+  for (int q = 0; q < 2; ++q) {
+    CUDA_TRY(c, cudaMemcpyAsync(cursor[q], offs[q], sizeof(int32_t) * (size_t)nb, cudaMemcpyDeviceToDevice, st));
+    launch_bin(true, recs, F, d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles, margins[q], cursor[q], list[q],
+               offs[q], d_status, st);
+  }
+  CUDA_TRY(c, cudaGetLastError());
+
+  // raster, writing the caller's image directly (one split, no partial sums)
+  c->recs.p = recs;
+  c->nrm.p = nrm;
+  c->core.offsets.p = offs[0];
+  c->core.list.p = list[0];
+  c->soft.offsets.p = offs[1];
+  c->soft.list.p = list[1];
+  RasterParams P = raster_params(c, mesh, cam, T, H, W, pp);
+  P.out = (float4*)image;
+  launch_raster_fwd(P, tw, pp.spt, pp.moving, st);
+  CUDA_TRY(c, cudaGetLastError());
+  return MBR_OK;
+}
+
+}  // namespace
+
+extern "C" int mbr_render_blur_noalloc(const mbr_mesh* mesh, const mbr_motion* motion, const mbr_camera* camera,
+                                       int32_t T, int32_t H, int32_t W, int32_t solver, float* image,
+                                       void* cuda_stream, char* err, int32_t err_len) {
+  mbr_ctx local;  // default tuning and an error sink; its buffers are pointed into the static array
+  const int rc = noalloc_forward(&local, mesh, motion, camera, T, H, W, solver, image, (cudaStream_t)cuda_stream);
+  if (err && err_len > 0) {
+    std::strncpy(err, local.err.c_str(), (size_t)err_len - 1);
+    err[err_len - 1] = '\0';
+  }
+  return rc;
+}
