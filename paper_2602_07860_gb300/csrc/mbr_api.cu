@@ -41,7 +41,7 @@ struct mbr_ctx {
   // tuning
   int tile = 16, spt = 8, splits = 0;
   // scratch
-  DevBuf nacc, pos, nrm, recs, tables, partial, gslot, gm, cnt64, status;
+  DevBuf nacc, pos, nrm, recs, tables, partial, gslot, galb, gm, cnt64, status;
   BinSet core, soft;  // undilated bins (coverage) and r_soft-dilated bins (soft coverage)
   void* host_stage = nullptr;
   size_t host_stage_cap = 0;
@@ -344,7 +344,7 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
                (float4*)c->pos.p, (float4*)c->nrm.p, st);
   launch_setup((const float4*)c->pos.p, mesh->faces, F, V, d_sets, pp.n_sets, cam->znear, (TriRec*)c->recs.p, st);
   CUDA_TRY(c, cudaGetLastError());
-  pp.r = (float)std::sqrt((double)cam->delta * std::log(1e12));
+  pp.r = (float)std::sqrt((double)cam->delta * (double)kSoftCutoff);
   c->stats.launches += (F > 0 ? 1 : 0) + 1 + (F > 0 ? 1 : 0);
   c->stats.groups = pp.G;
   if (!do_bins) {
@@ -496,7 +496,8 @@ int mbr_create(mbr_ctx** out) {
 
 void mbr_destroy(mbr_ctx* c) {
   if (!c) return;
-  DevBuf* bufs[] = {&c->nacc, &c->pos, &c->nrm, &c->recs, &c->tables, &c->partial, &c->gslot, &c->gm, &c->cnt64,
+  DevBuf* bufs[] = {&c->nacc, &c->pos, &c->nrm, &c->recs, &c->tables, &c->partial, &c->gslot, &c->galb, &c->gm,
+                    &c->cnt64,
                     &c->status, &c->core.counts, &c->core.offsets, &c->core.cursor, &c->core.list,
                     &c->core.scan_tmp, &c->soft.counts, &c->soft.offsets, &c->soft.cursor, &c->soft.list,
                     &c->soft.scan_tmp};
@@ -571,14 +572,15 @@ int mbr_render_blur_backward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion*
   if ((rc = prepare(c, mesh, motion, cam, T, H, W, solver, st, true, pp))) return rc;
   RasterParams P = raster_params(c, mesh, cam, T, H, W, pp);
   const int V = mesh->V;
-  const size_t gbytes = sizeof(float) * 5 * (size_t)V * pp.n_slots;
+  const size_t gbytes = sizeof(float4) * 2 * (size_t)V * pp.n_slots;
   if ((rc = ensure(c, c->gslot, gbytes, st))) return rc;
   if ((rc = ensure(c, c->gm, sizeof(float) * 3 * V, st))) return rc;
+  if ((rc = ensure(c, c->galb, sizeof(float4) * V, st))) return rc;
   CUDA_TRY(c, cudaMemsetAsync(c->gslot.p, 0, gbytes, st));
-  if (dl_dalbedo) CUDA_TRY(c, cudaMemsetAsync(dl_dalbedo, 0, sizeof(float) * 3 * V, st));
+  if (dl_dalbedo) CUDA_TRY(c, cudaMemsetAsync(c->galb.p, 0, sizeof(float4) * V, st));
   P.dl_dimage = (const float4*)dl_dimage;
-  P.g_slot = (float*)c->gslot.p;
-  P.g_albedo = dl_dalbedo;
+  P.g_slot = (float4*)c->gslot.p;
+  P.g_albedo = dl_dalbedo ? (float4*)c->galb.p : nullptr;
   if ((rc = time_begin(c, 1, st))) return rc;
   launch_raster_bwd(P, c->tile, pp.spt, pp.moving, st);
   CUDA_TRY(c, cudaGetLastError());
@@ -586,7 +588,7 @@ int mbr_render_blur_backward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion*
   c->stats.launches += 1 + 1 + (mesh->F > 0 ? 1 : 0);
   c->stats.n_split = pp.n_split;
   launch_slot_chain(mesh->verts, (const float*)c->nacc.p, V, pp.d_xf, pp.n_slots, cam->tan_half_fov,
-                    (const float*)c->gslot.p, dl_dverts, (float*)c->gm.p, st);
+                    (const float4*)c->gslot.p, (const float4*)c->galb.p, dl_dverts, (float*)c->gm.p, dl_dalbedo, st);
   launch_normals_bwd(mesh->verts, mesh->faces, mesh->F, V, (const float*)c->gm.p, dl_dverts, st);
   CUDA_TRY(c, cudaGetLastError());
   return MBR_OK;
@@ -604,7 +606,9 @@ int mbr_count_candidates(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* mot
   if ((rc = prepare(c, mesh, motion, cam, T, H, W, solver, st, false, pp))) return rc;
   if ((rc = ensure(c, c->cnt64, sizeof(unsigned long long), st))) return rc;
   CUDA_TRY(c, cudaMemsetAsync(c->cnt64.p, 0, sizeof(unsigned long long), st));
-  launch_count((const TriRec*)c->recs.p, mesh->F, pp.d_groups, pp.G, W, H, pp.r,
+  // N_cand keeps its definition: boxes dilated by sqrt(delta ln 1e12)
+  const float r_count = (float)std::sqrt((double)cam->delta * std::log(1e12));
+  launch_count((const TriRec*)c->recs.p, mesh->F, pp.d_groups, pp.G, W, H, r_count,
                (unsigned long long*)c->cnt64.p, st);
   c->stats.launches += mesh->F > 0 ? 1 : 0;
   CUDA_TRY(c, cudaGetLastError());
@@ -690,7 +694,7 @@ int noalloc_forward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, 
   pp.tiles_y = (H + th - 1) / th;
   pp.n_tiles = pp.tiles_x * pp.tiles_y;
   pp.n_split = 1;
-  pp.r = (float)std::sqrt((double)cam->delta * std::log(1e12));
+  pp.r = (float)std::sqrt((double)cam->delta * (double)kSoftCutoff);
   const long long nb = (long long)pp.G * pp.n_tiles;
 
   // fixed part of the arena

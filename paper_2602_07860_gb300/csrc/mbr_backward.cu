@@ -59,10 +59,10 @@ struct BwdSoftProduct {
   float prod[SPT];
   int nzero[SPT];
   float inv_delta;
-  __device__ __forceinline__ void begin(int) {}
+  __device__ __forceinline__ void begin() {}
   template <typename PS>
-  __device__ __forceinline__ void term(int, const float4*, const PS&, const EdgeVals&, const SoftGeom& sg, int i,
-                                       float, int) {
+  __device__ __forceinline__ void term(const float4*, const PS&, const EdgeVals&, const SoftGeom& sg, int i, float,
+                                       int) {
     const float f = -expm1f(-sg.d * inv_delta);
 #pragma unroll
     for (int q = 0; q < SPT; ++q)
@@ -71,7 +71,7 @@ struct BwdSoftProduct {
         else nzero[q] += 1;
       }
   }
-  __device__ __forceinline__ void end(int, float) {}
+  __device__ __forceinline__ void end(int) {}
 };
 
 // pass 3 of the adjoint: gradient of alpha = 1 - prod_j (1 - A_j) w.r.t. the vertex positions of
@@ -82,20 +82,19 @@ struct BwdSoftGrad {
   float prod[SPT];
   int nzero[SPT];
   float ga, inv_delta;
-  const float4* rec;          // staged records (shared memory)
   const int32_t* faces;
-  float* gslot_a;
-  float* gslot_b;
+  float4* gslot_a;
+  float4* gslot_b;
   float gax[3], gay[3], gbx[3], gby[3];
   bool any;
 
-  __device__ __forceinline__ void begin(int) {
+  __device__ __forceinline__ void begin() {
 #pragma unroll
     for (int q = 0; q < 3; ++q) gax[q] = gay[q] = gbx[q] = gby[q] = 0.f;
     any = false;
   }
 
-  __device__ __forceinline__ void term(int, const float4* r, const PixelSetup<MOVING>& ps, const EdgeVals& e,
+  __device__ __forceinline__ void term(const float4* r, const PixelSetup<MOVING>& ps, const EdgeVals& e,
                                        const SoftGeom& sg, int i, float tau, int X) {
     const float f = -expm1f(-sg.d * inv_delta);
     const float A = __expf(-sg.d * inv_delta);
@@ -204,8 +203,21 @@ struct BwdSoftGrad {
     }
   }
 
-  __device__ __forceinline__ void end(int j, float) {
-    if (!__any_sync(0xffffffffu, any)) return;
+  __device__ __forceinline__ void end(int face) {
+    const uint32_t am = __ballot_sync(0xffffffffu, any);
+    if (!am) return;
+    if (__popc(am) == 1) {
+      if (any) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const int vid = __ldg(faces + 3 * face + q);
+          atomicAdd(reinterpret_cast<float2*>(gslot_a + (size_t)vid * 2), make_float2(gax[q], gay[q]));
+          if (MOVING)
+            atomicAdd(reinterpret_cast<float2*>(gslot_b + (size_t)vid * 2), make_float2(gbx[q], gby[q]));
+        }
+      }
+      return;
+    }
     float vals[12];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -215,33 +227,161 @@ struct BwdSoftGrad {
       vals[7 + 2 * q] = MOVING ? warp_sum(gby[q]) : 0.f;
     }
     if ((threadIdx.x & 31) == 0) {
-      const int face = __float_as_int(rec[j * kRecF4 + kR_E2].w);
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         const int vid = __ldg(faces + 3 * face + q);
-        atomicAdd(gslot_a + (size_t)vid * 5, vals[2 * q]);
-        atomicAdd(gslot_a + (size_t)vid * 5 + 1, vals[2 * q + 1]);
-        if (MOVING) {
-          atomicAdd(gslot_b + (size_t)vid * 5, vals[6 + 2 * q]);
-          atomicAdd(gslot_b + (size_t)vid * 5 + 1, vals[7 + 2 * q]);
-        }
+        atomicAdd(reinterpret_cast<float2*>(gslot_a + (size_t)vid * 2), make_float2(vals[2 * q], vals[2 * q + 1]));
+        if (MOVING)
+          atomicAdd(reinterpret_cast<float2*>(gslot_b + (size_t)vid * 2),
+                    make_float2(vals[6 + 2 * q], vals[7 + 2 * q]));
       }
     }
   }
 };
 
+// Adjoint of one covered sample: shading (Eq. fore + Lambert) and w = N / D through the edge
+// functions to the slot states of the winner's vertices.  Lanes that share a winner face are
+// reduced together (one leader adds them), so each distinct face of the warp costs one set of
+// vector atomics.  Warp-collective: every lane calls it; lanes without a covered sample pass
+// has = false.
+template <bool MOVING>
+__device__ __forceinline__ void covered_adjoint(const RasterParams& P, const TriRec* recs_set, int slot_a, int slot_b,
+                                                bool has, int f, float tau, float u, float v, float gr, float gg,
+                                                float gb) {
+  // per-vertex contributions: slot a (dx, dy, dnx, dny | dnz), slot b (same), albedo (r, g, b)
+  float4 ca[3], cb[3], cal[3];
+  float ca_z[3], cb_z[3];
+  int vid[3] = {0, 0, 0};
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    ca[q] = cb[q] = cal[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    ca_z[q] = cb_z[q] = 0.f;
+  }
+  if (has) {
+    float4 r[kRecF4];
+    load_record<MOVING>(recs_set + f, r, false, false);
+    const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
+    const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
+    const float invD = 1.0f / e.D;
+    const float w[3] = {e.N0 * invD, e.N1 * invD, e.N2 * invD};
+    float al[3][3], nv[3][3];
+    float cr = 0.f, cg = 0.f, cbl = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      vid[q] = __ldg(P.faces + 3 * f + q);
+      al[q][0] = __ldg(P.albedo + 3 * vid[q]);
+      al[q][1] = __ldg(P.albedo + 3 * vid[q] + 1);
+      al[q][2] = __ldg(P.albedo + 3 * vid[q] + 2);
+      float4 na = __ldg(P.slot_nrm + (size_t)slot_a * P.V + vid[q]);
+      if (MOVING) {
+        const float4 nb = __ldg(P.slot_nrm + (size_t)slot_b * P.V + vid[q]);
+        na.x = fmaf(tau, nb.x - na.x, na.x);
+        na.y = fmaf(tau, nb.y - na.y, na.y);
+        na.z = fmaf(tau, nb.z - na.z, na.z);
+      }
+      nv[q][0] = na.x; nv[q][1] = na.y; nv[q][2] = na.z;
+      cr = fmaf(w[q], al[q][0], cr);
+      cg = fmaf(w[q], al[q][1], cg);
+      cbl = fmaf(w[q], al[q][2], cbl);
+      nx = fmaf(w[q], na.x, nx);
+      ny = fmaf(w[q], na.y, ny);
+      nz = fmaf(w[q], na.z, nz);
+    }
+    const float len = sqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+    const float dot = len > 0.f ? fmaf(nx, P.lx, fmaf(ny, P.ly, nz * P.lz)) / len : 0.f;
+    const float shade = fmaf(P.kd, fmaxf(dot, 0.f), P.ka);
+    // I = c shade
+    const float gcr = gr * shade, gcg = gg * shade, gcb = gb * shade;
+    const float gshade = gr * cr + gg * cg + gb * cbl;
+    float gw[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      gw[q] = al[q][0] * gcr + al[q][1] * gcg + al[q][2] * gcb;
+      cal[q] = make_float4(w[q] * gcr, w[q] * gcg, w[q] * gcb, 0.f);
+    }
+    if (len > 0.f && dot > 0.f) {
+      const float il = 1.f / len;
+      const float hx = nx * il, hy = ny * il, hz = nz * il;
+      const float gx = P.kd * gshade * P.lx, gy = P.kd * gshade * P.ly, gz = P.kd * gshade * P.lz;
+      const float hg = hx * gx + hy * gy + hz * gz;
+      const float gnx = (gx - hx * hg) * il, gny = (gy - hy * hg) * il, gnz = (gz - hz * hg) * il;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        gw[q] += nv[q][0] * gnx + nv[q][1] * gny + nv[q][2] * gnz;
+        const float sa = MOVING ? (1.f - tau) * w[q] : w[q];
+        ca[q].z = sa * gnx;
+        ca[q].w = sa * gny;
+        ca_z[q] = sa * gnz;
+        if (MOVING) {
+          cb[q].z = tau * w[q] * gnx;
+          cb[q].w = tau * w[q] * gny;
+          cb_z[q] = tau * w[q] * gnz;
+        }
+      }
+    }
+    // w = N / D -> vertex positions at tau
+    const float sw = w[0] * gw[0] + w[1] * gw[1] + w[2] * gw[2];
+    float ax[3], ay[3], ex[3], ey[3];
+    rel_vertices<MOVING>(r, ps, tau, ax, ay);
+    edge_backward((gw[0] - sw) * invD, (gw[1] - sw) * invD, (gw[2] - sw) * invD, ax, ay, ex, ey);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float sa = MOVING ? 1.f - tau : 1.f;
+      ca[q].x = sa * ex[q];
+      ca[q].y = sa * ey[q];
+      if (MOVING) {
+        cb[q].x = tau * ex[q];
+        cb[q].y = tau * ey[q];
+      }
+    }
+  }
+  float4* ga_ = P.g_slot + (size_t)slot_a * P.V * 2;
+  float4* gb_ = P.g_slot + (size_t)slot_b * P.V * 2;
+  // one reduction when every covered lane of the warp has the same winner, else per-lane adds
+  const uint32_t hmask = __ballot_sync(0xffffffffu, has);
+  if (!hmask) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(hmask) - 1;
+  const int fl = __shfl_sync(0xffffffffu, f, leader);
+  const bool uniform = __all_sync(0xffffffffu, !has || f == fl) && __popc(hmask) > 1;
+  if (uniform) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      ca[q] = make_float4(warp_sum(ca[q].x), warp_sum(ca[q].y), warp_sum(ca[q].z), warp_sum(ca[q].w));
+      ca_z[q] = warp_sum(ca_z[q]);
+      if (MOVING) {
+        cb[q] = make_float4(warp_sum(cb[q].x), warp_sum(cb[q].y), warp_sum(cb[q].z), warp_sum(cb[q].w));
+        cb_z[q] = warp_sum(cb_z[q]);
+      }
+      if (P.g_albedo) cal[q] = make_float4(warp_sum(cal[q].x), warp_sum(cal[q].y), warp_sum(cal[q].z), 0.f);
+    }
+  }
+  if (uniform ? lane == leader : has) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      atomicAdd(ga_ + (size_t)vid[q] * 2, ca[q]);
+      atomicAdd(reinterpret_cast<float*>(ga_ + (size_t)vid[q] * 2 + 1), ca_z[q]);
+      if (MOVING) {
+        atomicAdd(gb_ + (size_t)vid[q] * 2, cb[q]);
+        atomicAdd(reinterpret_cast<float*>(gb_ + (size_t)vid[q] * 2 + 1), cb_z[q]);
+      }
+      if (P.g_albedo) atomicAdd(P.g_albedo + vid[q], cal[q]);
+    }
+  }
+}
+
 template <int TW, int TH, int SPT, bool MOVING>
 __global__ void __launch_bounds__(TW * TH) raster_bwd_kernel(RasterParams P) {
-  constexpr int NT = TW * TH;
-  __shared__ RasterSmem sm;
+  __shared__ Group s_grp;
   const int n_tiles = P.tiles_x * P.tiles_y;
   const int tile = blockIdx.x % n_tiles, split = blockIdx.x / n_tiles;
   const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
-  const int px = tx * TW + (int)(threadIdx.x % TW), py = ty * TH + (int)(threadIdx.x / TW);
+  int px, py;
+  PixelMap<TW, TH>::pixel(tx, ty, px, py);
   const bool in_img = px < P.W && py < P.H;
   const float u = (2.f * px + 1.f) / P.W - 1.f;
   const float v = 1.f - (2.f * py + 1.f) / P.H;
-  const TileBox tb = tile_box<TW, TH>(tx, ty, P.W, P.H);
+  const TileBox tb = PixelMap<TW, TH>::warp_box(tx, ty, P.W, P.H);
   const int g_begin = (int)((long long)P.G * split / P.n_split);
   const int g_end = (int)((long long)P.G * (split + 1) / P.n_split);
   float4 G4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -249,140 +389,46 @@ __global__ void __launch_bounds__(TW * TH) raster_bwd_kernel(RasterParams P) {
   const float gr = G4.x * P.inv_T, gg = G4.y * P.inv_T, gb = G4.z * P.inv_T, ga = G4.w * P.inv_T;
 
   for (int g = g_begin; g < g_end; ++g) {
-    load_group<NT>(sm, P.groups, g);
-    const int n = sm.grp.n;
-    const TriRec* recs_set = P.recs + (size_t)sm.grp.rec_set * P.F;
+    load_group(s_grp, P.groups, g);
+    const int n = s_grp.n;
+    const TriRec* recs_set = P.recs + (size_t)s_grp.rec_set * P.F;
     const size_t bi = (size_t)g * n_tiles + tile;
-    float* gslot_a = P.g_slot + (size_t)sm.grp.slot_a * P.V * 5;
-    float* gslot_b = P.g_slot + (size_t)sm.grp.slot_b * P.V * 5;
+    float4* gslot_a = P.g_slot + (size_t)s_grp.slot_a * P.V * 2;
+    float4* gslot_b = P.g_slot + (size_t)s_grp.slot_b * P.V * 2;
     float bestk[SPT];
     int bestf[SPT];
-    pass_winners<NT, SPT, MOVING>(sm, recs_set, P.core.faces, P.core.off[bi], P.core.off[bi + 1], tb, in_img, u,
-                                  v, bestk, bestf);
+    pass_winners<SPT, MOVING>(s_grp, recs_set, P.core.faces, P.core.off[bi], P.core.off[bi + 1], tb, in_img, u, v,
+                              bestk, bestf);
     uint32_t uncov = 0;
 #pragma unroll
     for (int i = 0; i < SPT; ++i)
       if (i < n && bestf[i] < 0) uncov |= 1u << i;
     const int sb = P.soft.off[bi], se = P.soft.off[bi + 1];
     const bool active = in_img && ga != 0.f;
-    if (__syncthreads_or(active && uncov != 0 && se > sb)) {
+    if (se > sb && __any_sync(0xffffffffu, active && uncov != 0)) {
       BwdSoftProduct<SPT> p2;
 #pragma unroll
       for (int i = 0; i < SPT; ++i) { p2.prod[i] = 1.f; p2.nzero[i] = 0; }
       p2.inv_delta = P.inv_delta;
-      for_soft_terms<NT, SPT, MOVING>(sm, recs_set, P.soft.faces, sb, se, tb, active, u, v, uncov, P.r, P.r2, p2);
+      for_soft_terms<SPT, MOVING>(s_grp, recs_set, P.soft.faces, sb, se, tb, active, u, v, uncov, P.r, P.r2, p2);
       BwdSoftGrad<SPT, MOVING> p3;
 #pragma unroll
       for (int i = 0; i < SPT; ++i) { p3.prod[i] = p2.prod[i]; p3.nzero[i] = p2.nzero[i]; }
       p3.ga = ga;
       p3.inv_delta = P.inv_delta;
-      p3.rec = sm.rec;
       p3.faces = P.faces;
       p3.gslot_a = gslot_a;
       p3.gslot_b = gslot_b;
-      for_soft_terms<NT, SPT, MOVING>(sm, recs_set, P.soft.faces, sb, se, tb, active, u, v, uncov, P.r, P.r2, p3);
+      for_soft_terms<SPT, MOVING>(s_grp, recs_set, P.soft.faces, sb, se, tb, active, u, v, uncov, P.r, P.r2, p3);
     }
 
     // ---- covered samples: shading adjoint and barycentric adjoint of the winner
-    if (in_img) {
 #pragma unroll
-      for (int i = 0; i < SPT; ++i) {
-        if (i < n && bestf[i] >= 0) {
-          const int f = bestf[i];
-          const float tau = MOVING ? sm.grp.tau[i] : 0.f;
-          float4 r[kRecF4];
-          const TriRec* src = recs_set + f;
-          r[kR_O] = __ldg(&src->f4[kR_O]);
-          r[kR_E2] = __ldg(&src->f4[kR_E2]);
-          if (MOVING) {
-            r[kR_D] = __ldg(&src->f4[kR_D]);
-            r[kR_G] = __ldg(&src->f4[kR_G]);
-            r[kR_A] = __ldg(&src->f4[kR_A]);
-          }
-          const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
-          const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
-          const float invD = 1.0f / e.D;
-          const float w[3] = {e.N0 * invD, e.N1 * invD, e.N2 * invD};
-          int vid[3];
-          float al[3][3], nv[3][3];
-          float cr = 0.f, cg = 0.f, cb = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            vid[q] = __ldg(P.faces + 3 * f + q);
-            al[q][0] = __ldg(P.albedo + 3 * vid[q]);
-            al[q][1] = __ldg(P.albedo + 3 * vid[q] + 1);
-            al[q][2] = __ldg(P.albedo + 3 * vid[q] + 2);
-            float4 na = __ldg(P.slot_nrm + (size_t)sm.grp.slot_a * P.V + vid[q]);
-            if (MOVING) {
-              const float4 nb = __ldg(P.slot_nrm + (size_t)sm.grp.slot_b * P.V + vid[q]);
-              na.x = fmaf(tau, nb.x - na.x, na.x);
-              na.y = fmaf(tau, nb.y - na.y, na.y);
-              na.z = fmaf(tau, nb.z - na.z, na.z);
-            }
-            nv[q][0] = na.x; nv[q][1] = na.y; nv[q][2] = na.z;
-            cr = fmaf(w[q], al[q][0], cr);
-            cg = fmaf(w[q], al[q][1], cg);
-            cb = fmaf(w[q], al[q][2], cb);
-            nx = fmaf(w[q], na.x, nx);
-            ny = fmaf(w[q], na.y, ny);
-            nz = fmaf(w[q], na.z, nz);
-          }
-          const float len = sqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
-          const float dot = len > 0.f ? fmaf(nx, P.lx, fmaf(ny, P.ly, nz * P.lz)) / len : 0.f;
-          const float shade = fmaf(P.kd, fmaxf(dot, 0.f), P.ka);
-          // I = c shade
-          const float gcr = gr * shade, gcg = gg * shade, gcb = gb * shade;
-          const float gshade = gr * cr + gg * cg + gb * cb;
-          float gw[3];
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            gw[q] = al[q][0] * gcr + al[q][1] * gcg + al[q][2] * gcb;
-            if (P.g_albedo) {
-              atomicAdd(P.g_albedo + 3 * vid[q], w[q] * gcr);
-              atomicAdd(P.g_albedo + 3 * vid[q] + 1, w[q] * gcg);
-              atomicAdd(P.g_albedo + 3 * vid[q] + 2, w[q] * gcb);
-            }
-          }
-          if (len > 0.f && dot > 0.f) {
-            const float il = 1.f / len;
-            const float hx = nx * il, hy = ny * il, hz = nz * il;
-            const float gx = P.kd * gshade * P.lx, gy = P.kd * gshade * P.ly, gz = P.kd * gshade * P.lz;
-            const float hg = hx * gx + hy * gy + hz * gz;
-            const float gnx = (gx - hx * hg) * il, gny = (gy - hy * hg) * il, gnz = (gz - hz * hg) * il;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-              gw[q] += nv[q][0] * gnx + nv[q][1] * gny + nv[q][2] * gnz;
-              float* pa = gslot_a + (size_t)vid[q] * 5 + 2;
-              const float sa = MOVING ? (1.f - tau) * w[q] : w[q];
-              atomicAdd(pa, sa * gnx);
-              atomicAdd(pa + 1, sa * gny);
-              atomicAdd(pa + 2, sa * gnz);
-              if (MOVING) {
-                float* pb = gslot_b + (size_t)vid[q] * 5 + 2;
-                atomicAdd(pb, tau * w[q] * gnx);
-                atomicAdd(pb + 1, tau * w[q] * gny);
-                atomicAdd(pb + 2, tau * w[q] * gnz);
-              }
-            }
-          }
-          // w = N / D -> vertex positions at tau
-          const float sw = w[0] * gw[0] + w[1] * gw[1] + w[2] * gw[2];
-          float ax[3], ay[3], ex[3], ey[3];
-          rel_vertices<MOVING>(r, ps, tau, ax, ay);
-          edge_backward((gw[0] - sw) * invD, (gw[1] - sw) * invD, (gw[2] - sw) * invD, ax, ay, ex, ey);
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            float* pa = gslot_a + (size_t)vid[q] * 5;
-            const float sa = MOVING ? 1.f - tau : 1.f;
-            atomicAdd(pa, sa * ex[q]);
-            atomicAdd(pa + 1, sa * ey[q]);
-            if (MOVING) {
-              float* pb = gslot_b + (size_t)vid[q] * 5;
-              atomicAdd(pb, tau * ex[q]);
-              atomicAdd(pb + 1, tau * ey[q]);
-            }
-          }
-        }
+    for (int i = 0; i < SPT; ++i) {
+      if (i < n) {
+        const bool has = in_img && bestf[i] >= 0;
+        covered_adjoint<MOVING>(P, recs_set, s_grp.slot_a, s_grp.slot_b, has, has ? bestf[i] : 0,
+                                MOVING ? s_grp.tau[i] : 0.f, u, v, gr, gg, gb);
       }
     }
   }
@@ -392,15 +438,22 @@ __global__ void __launch_bounds__(TW * TH) raster_bwd_kernel(RasterParams P) {
 // one thread per vertex, looping over slots (no atomics); writes dL/dv and dL/dm (m = normal sum)
 __global__ void slot_chain_kernel(const float* __restrict__ verts, const float* __restrict__ nacc, int V,
                                   const SlotXform* __restrict__ xf, int n_slots, float th,
-                                  const float* __restrict__ g_slot, float* __restrict__ g_verts,
-                                  float* __restrict__ g_m) {
+                                  const float4* __restrict__ g_slot, const float4* __restrict__ g_alb4,
+                                  float* __restrict__ g_verts, float* __restrict__ g_m,
+                                  float* __restrict__ g_albedo) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V) return;
+  if (g_albedo) {
+    const float4 a = g_alb4[v];
+    g_albedo[3 * v] = a.x;
+    g_albedo[3 * v + 1] = a.y;
+    g_albedo[3 * v + 2] = a.z;
+  }
   const float px = verts[3 * v], py = verts[3 * v + 1], pz = verts[3 * v + 2];
   float gvx = 0.f, gvy = 0.f, gvz = 0.f, gnx = 0.f, gny = 0.f, gnz = 0.f;
   for (int s = 0; s < n_slots; ++s) {
-    const float* g = g_slot + ((size_t)s * V + v) * 5;
-    const float g0 = g[0], g1 = g[1], g2 = g[2], g3 = g[3], g4 = g[4];
+    const float4 ga = g_slot[((size_t)s * V + v) * 2];
+    const float g0 = ga.x, g1 = ga.y, g2 = ga.z, g3 = ga.w, g4 = g_slot[((size_t)s * V + v) * 2 + 1].x;
     if (g0 == 0.f && g1 == 0.f && g2 == 0.f && g3 == 0.f && g4 == 0.f) continue;
     const float* A = xf[s].A;
     const float* R = xf[s].R;
@@ -488,8 +541,11 @@ void launch_raster_bwd(const RasterParams& P, int tile, int spt, bool moving, cu
 }
 
 void launch_slot_chain(const float* verts, const float* nacc, int V, const SlotXform* xf, int n_slots, float th,
-                       const float* g_slot, float* g_verts, float* g_m, cudaStream_t st) {
-  if (V > 0) slot_chain_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, nacc, V, xf, n_slots, th, g_slot, g_verts, g_m);
+                       const float4* g_slot, const float4* g_alb4, float* g_verts, float* g_m, float* g_albedo,
+                       cudaStream_t st) {
+  if (V > 0)
+    slot_chain_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, nacc, V, xf, n_slots, th, g_slot, g_alb4, g_verts, g_m,
+                                                       g_albedo);
 }
 
 void launch_normals_bwd(const float* verts, const int32_t* faces, int F, int V, const float* g_m, float* g_verts,

@@ -17,7 +17,7 @@ namespace mbr {
 
 constexpr int kMaxSpt = 16;           // sub-frames per thread held in registers (max)
 constexpr float kDetMin = 1e-10f;     // |det F| at or below: triangle skipped at that sample
-constexpr int kRecF4 = 9;             // float4s per triangle record
+constexpr int kRecF4 = 11;            // float4s per triangle record
 constexpr int kRecF4Static = 4;       // float4s a static (plain-solver) record needs
 
 // Per (record set, face) triangle record.  Local frame: origin o = v0 at the set's first
@@ -34,6 +34,8 @@ constexpr int kRecF4Static = 4;       // float4s a static (plain-solver) record 
 //           the lerp of the two keyframe boxes)
 //   f4[5] = (d1x, d1y, d2x, d2y)      f4[6] = (gx, gy, c1, c2)
 //   f4[7] = (a11, a12, D1, D2)        f4[8] = (dz0, dz1, dz2, 0)
+//   f4[9], f4[10] = 1 / |edge|^2 of the edges (v0,v1), (v1,v2), (v2,v0) at the first / second
+//           keyframe (0 for a zero-length edge) -- the closest-point search of the soft term
 // with c1 = -cross(g, e2), c2 = -cross(e1, g), a11 = -cross(g, d2), a12 = -cross(d1, g),
 // D0 = cross(e1, e2), D1 = cross(e1, d2) + cross(d1, e2), D2 = cross(d1, d2).
 // Static (plain) records only use f4[0..3].
@@ -81,7 +83,7 @@ struct Closest {
 };
 
 __device__ __forceinline__ Closest closest_local(float e1x, float e1y, float e2x, float e2y,
-                                                float px, float py) {
+                                                float px, float py, const float4& inv_len2) {
   Closest c;
   c.d2 = INFINITY;
   c.w0 = c.w1 = c.w2 = 0.f;
@@ -91,14 +93,14 @@ __device__ __forceinline__ Closest closest_local(float e1x, float e1y, float e2x
   c.ej = 1;
   const float vx[3] = {0.f, e1x, e2x};
   const float vy[3] = {0.f, e1y, e2y};
+  const float iL[3] = {inv_len2.x, inv_len2.y, inv_len2.z};
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
     const int i = e, j = (e + 1) % 3;
     const float ax = vx[i], ay = vy[i];
     const float ex = vx[j] - ax, ey = vy[j] - ay;
-    const float L2 = fmaf(ex, ex, ey * ey);
     const float rx = px - ax, ry = py - ay;
-    float t = L2 > 0.f ? fmaf(rx, ex, ry * ey) / L2 : 0.f;
+    float t = fmaf(rx, ex, ry * ey) * iL[e];
     int reg = e;
     float qx, qy;
     if (t <= 0.f) {

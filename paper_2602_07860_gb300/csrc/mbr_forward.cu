@@ -106,6 +106,16 @@ __global__ void setup_kernel(const float4* __restrict__ pos, const int32_t* __re
   r.f4[kR_A] = make_float4(-cross2(gx, gy, d2x, d2y), -cross2(d1x, d1y, gx, gy),
                            cross2(e1x, e1y, d2x, d2y) + cross2(d1x, d1y, e2x, e2y), cross2(d1x, d1y, d2x, d2y));
   r.f4[kR_DZ] = make_float4(b0.z - a0.z, b1.z - a1.z, b2.z - a2.z, 0.f);
+  {
+    // 1 / |edge|^2 of (v0,v1), (v1,v2), (v2,v0) at both keyframes (0 for a zero-length edge)
+    auto inv = [](float x, float y) {
+      const float l2 = fmaf(x, x, y * y);
+      return l2 > 0.f ? 1.0f / l2 : 0.f;
+    };
+    const float f1x = e1x + d1x, f1y = e1y + d1y, f2x = e2x + d2x, f2y = e2y + d2y;
+    r.f4[kR_IL0] = make_float4(inv(e1x, e1y), inv(e2x - e1x, e2y - e1y), inv(e2x, e2y), 0.f);
+    r.f4[kR_IL1] = make_float4(inv(f1x, f1y), inv(f2x - f1x, f2y - f1y), inv(f2x, f2y), 0.f);
+  }
   TriRec* dst = recs + idx;
 #pragma unroll
   for (int q = 0; q < kRecF4; ++q) dst->f4[q] = r.f4[q];
@@ -258,43 +268,43 @@ template <int SPT>
 struct FwdSoftProduct {
   float prod[SPT];
   float inv_delta;
-  __device__ __forceinline__ void begin(int) {}
+  __device__ __forceinline__ void begin() {}
   template <typename PS>
-  __device__ __forceinline__ void term(int, const float4*, const PS&, const EdgeVals&, const SoftGeom& sg, int i,
-                                       float, int) {
+  __device__ __forceinline__ void term(const float4*, const PS&, const EdgeVals&, const SoftGeom& sg, int i, float,
+                                       int) {
     const float f = -expm1f(-sg.d * inv_delta);
 #pragma unroll
     for (int q = 0; q < SPT; ++q)
       if (q == i) prod[q] *= f;
   }
-  __device__ __forceinline__ void end(int, float) {}
+  __device__ __forceinline__ void end(int) {}
 };
 
 template <int TW, int TH, int SPT, bool MOVING>
 __global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(RasterParams P) {
-  constexpr int NT = TW * TH;
-  __shared__ RasterSmem sm;
+  __shared__ Group s_grp;
   const int n_tiles = P.tiles_x * P.tiles_y;
   const int tile = blockIdx.x % n_tiles, split = blockIdx.x / n_tiles;
   const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
-  const int px = tx * TW + (int)(threadIdx.x % TW), py = ty * TH + (int)(threadIdx.x / TW);
+  int px, py;
+  PixelMap<TW, TH>::pixel(tx, ty, px, py);
   const bool in_img = px < P.W && py < P.H;
   const float u = (2.f * px + 1.f) / P.W - 1.f;
   const float v = 1.f - (2.f * py + 1.f) / P.H;
-  const TileBox tb = tile_box<TW, TH>(tx, ty, P.W, P.H);
+  const TileBox tb = PixelMap<TW, TH>::warp_box(tx, ty, P.W, P.H);
   const int g_begin = (int)((long long)P.G * split / P.n_split);
   const int g_end = (int)((long long)P.G * (split + 1) / P.n_split);
   float acc_r = 0.f, acc_g = 0.f, acc_b = 0.f, acc_a = 0.f;
 
   for (int g = g_begin; g < g_end; ++g) {
-    load_group<NT>(sm, P.groups, g);
-    const int n = sm.grp.n;
-    const TriRec* recs_set = P.recs + (size_t)sm.grp.rec_set * P.F;
+    load_group(s_grp, P.groups, g);
+    const int n = s_grp.n;
+    const TriRec* recs_set = P.recs + (size_t)s_grp.rec_set * P.F;
     const size_t bi = (size_t)g * n_tiles + tile;
     float bestk[SPT];
     int bestf[SPT];
-    pass_winners<NT, SPT, MOVING>(sm, recs_set, P.core.faces, P.core.off[bi], P.core.off[bi + 1], tb, in_img, u,
-                                  v, bestk, bestf);
+    pass_winners<SPT, MOVING>(s_grp, recs_set, P.core.faces, P.core.off[bi], P.core.off[bi + 1], tb, in_img, u, v,
+                              bestk, bestf);
     uint32_t uncov = 0;
 #pragma unroll
     for (int i = 0; i < SPT; ++i)
@@ -304,8 +314,8 @@ __global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(RasterParams P) {
     for (int i = 0; i < SPT; ++i) soft.prod[i] = 1.f;
     soft.inv_delta = P.inv_delta;
     const int sb = P.soft.off[bi], se = P.soft.off[bi + 1];
-    if (__syncthreads_or(in_img && uncov != 0 && se > sb))
-      for_soft_terms<NT, SPT, MOVING>(sm, recs_set, P.soft.faces, sb, se, tb, in_img, u, v, uncov, P.r, P.r2, soft);
+    if (se > sb && __any_sync(0xffffffffu, in_img && uncov != 0))
+      for_soft_terms<SPT, MOVING>(s_grp, recs_set, P.soft.faces, sb, se, tb, in_img, u, v, uncov, P.r, P.r2, soft);
 
     // ---- shading of the winners (Eq. fore + Lambert) and temporal accumulation (Sec. 3.3)
     if (in_img) {
@@ -313,9 +323,9 @@ __global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(RasterParams P) {
       for (int i = 0; i < SPT; ++i) {
         if (i < n) {
           const int f = bestf[i];
-          if (P.dbg_ids && sm.grp.k0 + i == P.dbg_k) P.dbg_ids[(size_t)py * P.W + px] = f;
+          if (P.dbg_ids && s_grp.k0 + i == P.dbg_k) P.dbg_ids[(size_t)py * P.W + px] = f;
           if (f >= 0) {
-            const float tau = MOVING ? sm.grp.tau[i] : 0.f;
+            const float tau = MOVING ? s_grp.tau[i] : 0.f;
             float4 r[kRecF4];
             const TriRec* src = recs_set + f;
             r[kR_O] = __ldg(&src->f4[kR_O]);
@@ -336,9 +346,9 @@ __global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(RasterParams P) {
               cr = fmaf(w[q], __ldg(P.albedo + 3 * vid), cr);
               cg = fmaf(w[q], __ldg(P.albedo + 3 * vid + 1), cg);
               cb = fmaf(w[q], __ldg(P.albedo + 3 * vid + 2), cb);
-              float4 na = __ldg(P.slot_nrm + (size_t)sm.grp.slot_a * P.V + vid);
+              float4 na = __ldg(P.slot_nrm + (size_t)s_grp.slot_a * P.V + vid);
               if (MOVING) {
-                const float4 nb = __ldg(P.slot_nrm + (size_t)sm.grp.slot_b * P.V + vid);
+                const float4 nb = __ldg(P.slot_nrm + (size_t)s_grp.slot_b * P.V + vid);
                 na.x = fmaf(tau, nb.x - na.x, na.x);
                 na.y = fmaf(tau, nb.y - na.y, na.y);
                 na.z = fmaf(tau, nb.z - na.z, na.z);

@@ -28,7 +28,8 @@ void launch_count(const TriRec* recs, int F, const Group* groups, int G, int W, 
 
 void launch_raster_bwd(const RasterParams& P, int tile, int spt, bool moving, cudaStream_t st);
 void launch_slot_chain(const float* verts, const float* nacc, int V, const SlotXform* xf, int n_slots, float th,
-                       const float* g_slot, float* g_verts, float* g_m, cudaStream_t st);
+                       const float4* g_slot, const float4* g_alb4, float* g_verts, float* g_m, float* g_albedo,
+                       cudaStream_t st);
 void launch_normals_bwd(const float* verts, const int32_t* faces, int F, int V, const float* g_m, float* g_verts,
                         cudaStream_t st);
 

@@ -2,14 +2,15 @@
 // (forward and adjoint).
 //
 // One CTA owns a TW x TH pixel tile (one pixel per thread) and a contiguous range of sample
-// groups.  For each group:
-//   pass 1  the tile's "core" candidates (swept bounding box, no soft dilation) are staged in
-//           shared memory in chunks; while staging, one thread per candidate marks which of the
-//           group's samples can touch the tile and a pixel-reject box.  Each thread evaluates the
-//           surviving (candidate, sample) pairs: edge functions of Eq. time-dependent2, coverage,
-//           perspective-correct z-test (Sec. 3.1).  Samples live in registers (SPT of them).
-//   pass 2  only if some pixel of the tile has an uncovered sample: the r_soft-dilated candidate
-//           list, staged the same way, multiplies the soft-coverage factors 1 - exp(-d/delta)
+// groups; each warp owns an 8 x 4 pixel block of the tile and walks the tile's bin lists on its
+// own (no block-wide barriers inside a group).  For each group:
+//   pass 1  the tile's "core" candidates (swept bounding box, no soft dilation), 32 at a time:
+//           each lane marks which of the group's samples of one candidate can touch the warp's
+//           block and a pixel-reject box; a ballot keeps the live candidates and the warp
+//           evaluates them: edge functions of Eq. time-dependent2, coverage, perspective-correct
+//           z-test (Sec. 3.1).  Samples live in registers (SPT of them).
+//   pass 2  only if some pixel of the warp has an uncovered sample: the r_soft-dilated list,
+//           walked the same way, multiplies the soft-coverage factors 1 - exp(-d/delta)
 //           (Eqs. probability-function .. back) of the uncovered samples.
 // The forward then shades the winners (Eq. fore + Lambert) and accumulates; the adjoint adds a
 // third pass for the soft-term gradients.
@@ -18,9 +19,12 @@
 
 namespace mbr {
 
-constexpr int kStageCap = 64;  // candidate records staged per chunk
 // record field slots (see TriRec)
-constexpr int kR_O = 0, kR_E2 = 1, kR_Z = 2, kR_BB = 3, kR_DBB = 4, kR_D = 5, kR_G = 6, kR_A = 7, kR_DZ = 8;
+constexpr int kR_O = 0, kR_E2 = 1, kR_Z = 2, kR_BB = 3, kR_DBB = 4, kR_D = 5, kR_G = 6, kR_A = 7, kR_DZ = 8,
+              kR_IL0 = 9, kR_IL1 = 10;
+// Soft-coverage terms with exp(-d/delta) <= 2^-25 leave 1 - A == 1 in single precision, so they
+// cannot change the product of Eq. back: the soft radius is sqrt(delta * 25 ln 2).
+constexpr float kSoftCutoff = 17.328679514f;  // 25 ln 2
 constexpr float kCoreMargin = 1e-5f;  // NDC slack of the undilated boxes (covers FP32 rounding)
 
 struct BinLists {
@@ -45,8 +49,8 @@ struct RasterParams {
   int32_t* dbg_ids;
   // adjoint only
   const float4* dl_dimage;   // [H*W]
-  float* g_slot;             // [slots][V][5] gradients on (x, y, nx, ny, nz)
-  float* g_albedo;           // [V,3] or null
+  float4* g_slot;            // [slots][V][2]: (dx, dy, dnx, dny), (dnz, 0, 0, 0) of the slot states
+  float4* g_albedo;          // [V] (dr, dg, db, 0), or null
 };
 
 // Edge-function values of one candidate at one sample (local frame; see TriRec).
@@ -108,7 +112,7 @@ __device__ __forceinline__ float inv_depth(const float4* r, const EdgeVals& e, f
     z1 = fmaf(tau, r[kR_DZ].y, z1);
     z2 = fmaf(tau, r[kR_DZ].z, z2);
   }
-  return (e.N0 / z0 + e.N1 / z1 + e.N2 / z2) / e.D;
+  return __fdividef(__fdividef(e.N0, z0) + __fdividef(e.N1, z1) + __fdividef(e.N2, z2), e.D);
 }
 
 // Soft-coverage distance of an uncovered sample (Eqs. probability-function .. euc-dist-approx-3).
@@ -135,7 +139,7 @@ __device__ __forceinline__ SoftGeom soft_geom(const float4* r, const PixelSetup<
     g.w2 = e.N2 * invD;
     g.ppx = fmaf(g.w1, e1Xx, g.w2 * e2Xx);
     g.ppy = fmaf(g.w1, e1Xy, g.w2 * e2Xy);
-    g.c = closest_local(e1Xx, e1Xy, e2Xx, e2Xy, g.ppx, g.ppy);
+    g.c = closest_local(e1Xx, e1Xy, e2Xx, e2Xy, g.ppx, g.ppy, X ? r[kR_IL1] : r[kR_IL0]);
     const float e1tx = fmaf(tau, r[kR_D].x, r[kR_O].z), e1ty = fmaf(tau, r[kR_D].y, r[kR_O].w);
     const float e2tx = fmaf(tau, r[kR_D].z, r[kR_E2].x), e2ty = fmaf(tau, r[kR_D].w, r[kR_E2].y);
     const float qtx = fmaf(-tau, r[kR_G].x, s.q0x), qty = fmaf(-tau, r[kR_G].y, s.q0y);
@@ -143,7 +147,7 @@ __device__ __forceinline__ SoftGeom soft_geom(const float4* r, const PixelSetup<
     g.ry = fmaf(g.c.w1, e1ty, fmaf(g.c.w2, e2ty, -qty));
     g.d = fmaf(g.rx, g.rx, g.ry * g.ry);
   } else {
-    g.c = closest_local(r[kR_O].z, r[kR_O].w, r[kR_E2].x, r[kR_E2].y, s.q0x, s.q0y);
+    g.c = closest_local(r[kR_O].z, r[kR_O].w, r[kR_E2].x, r[kR_E2].y, s.q0x, s.q0y, r[kR_IL0]);
     g.w1 = g.w2 = g.ppx = g.ppy = 0.f;
     g.rx = fmaf(g.c.w1, r[kR_O].z, fmaf(g.c.w2, r[kR_E2].x, -s.q0x));
     g.ry = fmaf(g.c.w1, r[kR_O].w, fmaf(g.c.w2, r[kR_E2].y, -s.q0y));
@@ -160,87 +164,130 @@ __device__ __forceinline__ bool in_box_at(const float4* r, float tau, float m, f
          v <= fmaf(tau, db.w, b.w) + m;
 }
 
-// Tile geometry in NDC (pixel centres of the tile, clipped to the image).
+// Pixel-centre rectangle in NDC of a warp's 8 x 4 pixel block (clipped to the image).
 struct TileBox {
   float u_lo, u_hi, v_lo, v_hi;
+  bool empty;
 };
 
+// Warp w of a TW x TH tile owns the 8 x 4 pixel block (w % (TW/8), w / (TW/8)); lane l is pixel
+// (l % 8, l / 8) of that block.
 template <int TW, int TH>
-__device__ __forceinline__ TileBox tile_box(int tx, int ty, int W, int H) {
-  const int x0 = tx * TW, x1 = min(W, x0 + TW) - 1, y0 = ty * TH, y1 = min(H, y0 + TH) - 1;
-  TileBox t;
-  t.u_lo = (2.f * x0 + 1.f) / W - 1.f;
-  t.u_hi = (2.f * x1 + 1.f) / W - 1.f;
-  t.v_hi = 1.f - (2.f * y0 + 1.f) / H;
-  t.v_lo = 1.f - (2.f * y1 + 1.f) / H;
-  return t;
-}
-
-// Cooperative stage of candidates [0, cnt) of a bin list into shared memory.  All threads load
-// the record float4s; thread j < cnt also derives the candidate's sample mask (samples whose box,
-// dilated by m, meets the tile) and a pixel-reject box (union of those samples' boxes).
-template <int NT, bool MOVING>
-__device__ __forceinline__ void stage_candidates(float4* s_rec, float4* s_box, uint32_t* s_mask,
-                                                 const TriRec* recs_set, const int32_t* list, int cnt,
-                                                 const Group& grp, const TileBox& tb, float m) {
-  constexpr int NF4 = MOVING ? kRecF4 : kRecF4Static;
-  for (int idx = threadIdx.x; idx < cnt * NF4; idx += NT) {
-    const int j = idx / NF4, q = idx - j * NF4;
-    const int f = __ldg(list + j);
-    s_rec[j * kRecF4 + q] = __ldg(&recs_set[f].f4[q]);
+struct PixelMap {
+  static_assert(TW % 8 == 0 && TH % 4 == 0, "tile must be a multiple of 8 x 4 pixels");
+  static __device__ __forceinline__ void pixel(int tx, int ty, int& px, int& py) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    px = tx * TW + (w % (TW / 8)) * 8 + (l & 7);
+    py = ty * TH + (w / (TW / 8)) * 4 + (l >> 3);
   }
-  if ((int)threadIdx.x < cnt) {
-    const int f = __ldg(list + threadIdx.x);
-    const float4 b = __ldg(&recs_set[f].f4[kR_BB]);
-    float4 db = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (MOVING) db = __ldg(&recs_set[f].f4[kR_DBB]);
-    uint32_t mask = 0;
-    float tlo = INFINITY, thi = -INFINITY;
-    for (int i = 0; i < grp.n; ++i) {
-      const float tau = MOVING ? grp.tau[i] : 0.f;
-      const bool hit = fmaf(tau, db.x, b.x) - m <= tb.u_hi && fmaf(tau, db.y, b.y) + m >= tb.u_lo &&
-                       fmaf(tau, db.z, b.z) - m <= tb.v_hi && fmaf(tau, db.w, b.w) + m >= tb.v_lo;
-      if (hit) {
-        mask |= 1u << i;
-        tlo = fminf(tlo, tau);
-        thi = fmaxf(thi, tau);
-      }
-    }
-    float4 box = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
-    if (mask) {
-      box.x = fminf(fmaf(tlo, db.x, b.x), fmaf(thi, db.x, b.x)) - m;
-      box.y = fmaxf(fmaf(tlo, db.y, b.y), fmaf(thi, db.y, b.y)) + m;
-      box.z = fminf(fmaf(tlo, db.z, b.z), fmaf(thi, db.z, b.z)) - m;
-      box.w = fmaxf(fmaf(tlo, db.w, b.w), fmaf(thi, db.w, b.w)) + m;
-    }
-    s_box[threadIdx.x] = box;
-    s_mask[threadIdx.x] = mask;
+  static __device__ __forceinline__ TileBox warp_box(int tx, int ty, int W, int H) {
+    const int w = threadIdx.x >> 5;
+    const int x0 = tx * TW + (w % (TW / 8)) * 8, y0 = ty * TH + (w / (TW / 8)) * 4;
+    const int x1 = min(W, x0 + 8) - 1, y1 = min(H, y0 + 4) - 1;
+    TileBox t;
+    t.empty = x0 >= W || y0 >= H;
+    t.u_lo = (2.f * x0 + 1.f) / W - 1.f;
+    t.u_hi = (2.f * x1 + 1.f) / W - 1.f;
+    t.v_hi = 1.f - (2.f * y0 + 1.f) / H;
+    t.v_lo = 1.f - (2.f * y1 + 1.f) / H;
+    return t;
   }
-}
+};
 
 __device__ __forceinline__ bool in_box(const float4& b, float u, float v) {
   return u >= b.x && u <= b.y && v >= b.z && v <= b.w;
 }
 
-// Shared memory of a raster CTA.
-struct RasterSmem {
-  float4 rec[kStageCap * kRecF4];
-  float4 box[kStageCap];
-  uint32_t mask[kStageCap];
-  Group grp;
-};
-
-template <int NT>
-__device__ __forceinline__ void load_group(RasterSmem& sm, const Group* groups, int g) {
-  __syncthreads();
-  if (threadIdx.x < sizeof(Group) / 4)
-    reinterpret_cast<int*>(&sm.grp)[threadIdx.x] = reinterpret_cast<const int*>(groups + g)[threadIdx.x];
-  __syncthreads();
+// Candidate meta-data for a warp: the samples whose box (dilated by m) meets the warp's pixel
+// rectangle, and a pixel-reject box (union of those samples' boxes).  Computed by one lane per
+// candidate.
+template <bool MOVING>
+__device__ __forceinline__ uint32_t candidate_meta(const TriRec* rec, const Group& grp, const TileBox& tb, float m,
+                                                   float4& box) {
+  const float4 b = __ldg(&rec->f4[kR_BB]);
+  float4 db = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (MOVING) db = __ldg(&rec->f4[kR_DBB]);
+  uint32_t mask = 0;
+  float tlo = INFINITY, thi = -INFINITY;
+  const int n = MOVING ? grp.n : 1;
+  for (int i = 0; i < n; ++i) {
+    const float tau = MOVING ? grp.tau[i] : 0.f;
+    const bool hit = fmaf(tau, db.x, b.x) - m <= tb.u_hi && fmaf(tau, db.y, b.y) + m >= tb.u_lo &&
+                     fmaf(tau, db.z, b.z) - m <= tb.v_hi && fmaf(tau, db.w, b.w) + m >= tb.v_lo;
+    if (hit) {
+      mask |= 1u << i;
+      tlo = fminf(tlo, tau);
+      thi = fmaxf(thi, tau);
+    }
+  }
+  box = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
+  if (mask) {
+    box.x = fminf(fmaf(tlo, db.x, b.x), fmaf(thi, db.x, b.x)) - m;
+    box.y = fmaxf(fmaf(tlo, db.y, b.y), fmaf(thi, db.y, b.y)) + m;
+    box.z = fminf(fmaf(tlo, db.z, b.z), fmaf(thi, db.z, b.z)) - m;
+    box.w = fmaxf(fmaf(tlo, db.w, b.w), fmaf(thi, db.w, b.w)) + m;
+  }
+  return mask;
 }
 
-// pass 1: z-test winners of the group's samples for this pixel
-template <int NT, int SPT, bool MOVING>
-__device__ __forceinline__ void pass_winners(RasterSmem& sm, const TriRec* recs_set, const int32_t* list, int beg,
+// Load the record fields a pass needs (broadcast loads: every lane reads the same record).
+template <bool MOVING>
+__device__ __forceinline__ void load_record(const TriRec* src, float4 (&r)[kRecF4], bool with_z, bool with_box) {
+  r[kR_O] = __ldg(&src->f4[kR_O]);
+  r[kR_E2] = __ldg(&src->f4[kR_E2]);
+  if (with_z) r[kR_Z] = __ldg(&src->f4[kR_Z]);
+  if (with_box) {
+    r[kR_IL0] = __ldg(&src->f4[kR_IL0]);
+    if (MOVING) r[kR_IL1] = __ldg(&src->f4[kR_IL1]);
+  }
+  if (MOVING) {
+    if (with_box) {
+      r[kR_BB] = __ldg(&src->f4[kR_BB]);
+      r[kR_DBB] = __ldg(&src->f4[kR_DBB]);
+    }
+    r[kR_D] = __ldg(&src->f4[kR_D]);
+    r[kR_G] = __ldg(&src->f4[kR_G]);
+    r[kR_A] = __ldg(&src->f4[kR_A]);
+    if (with_z) r[kR_DZ] = __ldg(&src->f4[kR_DZ]);
+  }
+}
+
+__device__ __forceinline__ float4 shfl_box(const float4& b, int src) {
+  return make_float4(__shfl_sync(0xffffffffu, b.x, src), __shfl_sync(0xffffffffu, b.y, src),
+                     __shfl_sync(0xffffffffu, b.z, src), __shfl_sync(0xffffffffu, b.w, src));
+}
+
+// Walk a bin list 32 candidates at a time: each lane derives one candidate's meta-data, a ballot
+// keeps the candidates that touch the warp's rectangle, and the warp visits them in order with
+// fn(face, rec, mask, box).  Warp-collective: every lane of the warp must call it.
+template <bool MOVING, typename Fn>
+__device__ __forceinline__ void for_warp_candidates(const TriRec* recs_set, const int32_t* list, int beg, int end,
+                                                    const Group& grp, const TileBox& tb, float m, uint32_t samples,
+                                                    Fn&& fn) {
+  for (int c0 = beg; c0 < end; c0 += 32) {
+    const int j = c0 + (int)(threadIdx.x & 31);
+    int f = 0;
+    uint32_t mask = 0;
+    float4 box = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
+    if (j < end && !tb.empty) {
+      f = __ldg(list + j);
+      mask = candidate_meta<MOVING>(recs_set + f, grp, tb, m, box) & samples;
+    }
+    uint32_t live = __ballot_sync(0xffffffffu, mask != 0);
+    while (live) {
+      const int src = __ffs(live) - 1;
+      live &= live - 1;
+      const int fj = __shfl_sync(0xffffffffu, f, src);
+      const uint32_t mj = __shfl_sync(0xffffffffu, mask, src);
+      const float4 bj = shfl_box(box, src);
+      fn(fj, recs_set + fj, mj, bj);
+    }
+  }
+}
+
+// pass 1: z-test winners of the group's samples for this pixel (warp-collective)
+template <int SPT, bool MOVING>
+__device__ __forceinline__ void pass_winners(const Group& grp, const TriRec* recs_set, const int32_t* list, int beg,
                                              int end, const TileBox& tb, bool in_img, float u, float v,
                                              float (&bestk)[SPT], int (&bestf)[SPT]) {
 #pragma unroll
@@ -248,71 +295,68 @@ __device__ __forceinline__ void pass_winners(RasterSmem& sm, const TriRec* recs_
     bestk[i] = -INFINITY;
     bestf[i] = -1;
   }
-  for (int c0 = beg; c0 < end; c0 += kStageCap) {
-    const int cnt = min(kStageCap, end - c0);
-    __syncthreads();
-    stage_candidates<NT, MOVING>(sm.rec, sm.box, sm.mask, recs_set, list + c0, cnt, sm.grp, tb, kCoreMargin);
-    __syncthreads();
-    if (!in_img) continue;
-    for (int j = 0; j < cnt; ++j) {
-      const uint32_t mask = sm.mask[j];
-      if (!mask || !in_box(sm.box[j], u, v)) continue;
-      const float4* r = sm.rec + j * kRecF4;
-      const int face = __float_as_int(r[kR_E2].w);
+  for_warp_candidates<MOVING>(recs_set, list, beg, end, grp, tb, kCoreMargin, 0xffffffffu,
+                              [&](int face, const TriRec* src, uint32_t mask, const float4& box) {
+    if (!in_img || !in_box(box, u, v)) return;
+    float4 r[kRecF4];
+    load_record<MOVING>(src, r, true, false);
+    const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) {
+      if (mask & (1u << i)) {
+        const float tau = MOVING ? grp.tau[i] : 0.f;
+        const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
+        if (covers(e)) {
+          const float key = inv_depth<MOVING>(r, e, tau);
+          if (key > bestk[i] || (key == bestk[i] && face < bestf[i])) {
+            bestk[i] = key;
+            bestf[i] = face;
+          }
+        }
+      }
+    }
+  });
+}
+
+// Visit every soft-coverage term of the uncovered samples (uncov bit i) of this pixel:
+// fn.term(r, ps, e, sg, i, tau, X) for each (candidate, sample) with d <= r^2, bracketed by
+// fn.begin() and fn.end(face) per candidate.  Warp-collective: begin/end run on every lane.
+template <int SPT, bool MOVING, typename Fn>
+__device__ __forceinline__ void for_soft_terms(const Group& grp, const TriRec* recs_set, const int32_t* list, int beg,
+                                               int end, const TileBox& tb, bool active, float u, float v,
+                                               uint32_t uncov, float r_soft, float r2, Fn&& fn) {
+  const float m = r_soft + kCoreMargin;
+  const uint32_t warp_uncov = __reduce_or_sync(0xffffffffu, active ? uncov : 0u);
+  for_warp_candidates<MOVING>(recs_set, list, beg, end, grp, tb, m, warp_uncov,
+                              [&](int face, const TriRec* src, uint32_t mask_all, const float4& box) {
+    const uint32_t mask = active ? (mask_all & uncov) : 0u;
+    fn.begin();
+    if (mask && in_box(box, u, v)) {
+      float4 r[kRecF4];
+      load_record<MOVING>(src, r, false, true);
       const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
 #pragma unroll
       for (int i = 0; i < SPT; ++i) {
         if (mask & (1u << i)) {
-          const float tau = MOVING ? sm.grp.tau[i] : 0.f;
+          const float tau = MOVING ? grp.tau[i] : 0.f;
+          if (MOVING && !in_box_at(r, tau, m, u, v)) continue;
           const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
-          if (covers(e)) {
-            const float key = inv_depth<MOVING>(r, e, tau);
-            if (key > bestk[i] || (key == bestk[i] && face < bestf[i])) {
-              bestk[i] = key;
-              bestf[i] = face;
-            }
-          }
+          if (fabsf(e.D) <= kDetMin) continue;
+          const int X = (grp.xbits >> i) & 1u;
+          const SoftGeom sg = soft_geom<MOVING>(r, ps, e, tau, X);
+          if (sg.d <= r2) fn.term(r, ps, e, sg, i, tau, X);
         }
       }
     }
-  }
+    fn.end(face);
+  });
 }
 
-// Visit every soft-coverage term of the uncovered samples (uncov bit i) of this pixel:
-// fn(j, r, ps, e, sg, i, tau, X) for each (candidate, sample) with d <= r^2.  The staging (and
-// the __syncthreads inside) is executed by every thread of the CTA.
-template <int NT, int SPT, bool MOVING, typename Fn>
-__device__ __forceinline__ void for_soft_terms(RasterSmem& sm, const TriRec* recs_set, const int32_t* list, int beg,
-                                               int end, const TileBox& tb, bool active, float u, float v,
-                                               uint32_t uncov, float r_soft, float r2, Fn&& fn) {
-  for (int c0 = beg; c0 < end; c0 += kStageCap) {
-    const int cnt = min(kStageCap, end - c0);
-    __syncthreads();
-    stage_candidates<NT, MOVING>(sm.rec, sm.box, sm.mask, recs_set, list + c0, cnt, sm.grp, tb, r_soft + kCoreMargin);
-    __syncthreads();
-    for (int j = 0; j < cnt; ++j) {
-      const uint32_t mask = sm.mask[j] & (active ? uncov : 0u);
-      const bool hit = mask && in_box(sm.box[j], u, v);
-      fn.begin(j);
-      if (hit) {
-        const float4* r = sm.rec + j * kRecF4;
-        const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
-#pragma unroll
-        for (int i = 0; i < SPT; ++i) {
-          if (mask & (1u << i)) {
-            const float tau = MOVING ? sm.grp.tau[i] : 0.f;
-            if (MOVING && !in_box_at(r, tau, r_soft + kCoreMargin, u, v)) continue;
-            const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
-            if (fabsf(e.D) <= kDetMin) continue;
-            const int X = (sm.grp.xbits >> i) & 1u;
-            const SoftGeom sg = soft_geom<MOVING>(r, ps, e, tau, X);
-            if (sg.d <= r2) fn.term(j, r, ps, e, sg, i, tau, X);
-          }
-        }
-      }
-      fn.end(j, r_soft);
-    }
-  }
+__device__ __forceinline__ void load_group(Group& s_grp, const Group* groups, int g) {
+  __syncthreads();
+  if (threadIdx.x < sizeof(Group) / 4)
+    reinterpret_cast<int*>(&s_grp)[threadIdx.x] = reinterpret_cast<const int*>(groups + g)[threadIdx.x];
+  __syncthreads();
 }
 
 }  // namespace mbr
