@@ -372,7 +372,6 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
 
 template <int TW, int TH, int SPT, bool MOVING>
 __global__ void __launch_bounds__(TW * TH) raster_bwd_kernel(RasterParams P) {
-  __shared__ Group s_grp;
   const int n_tiles = P.tiles_x * P.tiles_y;
   const int tile = blockIdx.x % n_tiles, split = blockIdx.x / n_tiles;
   const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
@@ -389,16 +388,18 @@ __global__ void __launch_bounds__(TW * TH) raster_bwd_kernel(RasterParams P) {
   const float gr = G4.x * P.inv_T, gg = G4.y * P.inv_T, gb = G4.z * P.inv_T, ga = G4.w * P.inv_T;
 
   for (int g = g_begin; g < g_end; ++g) {
-    load_group(s_grp, P.groups, g);
-    const int n = s_grp.n;
-    const TriRec* recs_set = P.recs + (size_t)s_grp.rec_set * P.F;
+    const Group* grp = P.groups + g;
+    GroupRegs<SPT> gq;
+    gq.load(grp);
+    const int n = gq.n;
+    const TriRec* recs_set = P.recs + (size_t)gq.rec_set * P.F;
     const size_t bi = (size_t)g * n_tiles + tile;
-    float4* gslot_a = P.g_slot + (size_t)s_grp.slot_a * P.V * 2;
-    float4* gslot_b = P.g_slot + (size_t)s_grp.slot_b * P.V * 2;
+    float4* gslot_a = P.g_slot + (size_t)gq.slot_a * P.V * 2;
+    float4* gslot_b = P.g_slot + (size_t)gq.slot_b * P.V * 2;
     float bestk[SPT];
     int bestf[SPT];
-    pass_winners<SPT, MOVING>(s_grp, recs_set, P.core.faces, P.core.off[bi], P.core.off[bi + 1], tb, in_img, u, v,
-                              bestk, bestf);
+    pass_winners<SPT, MOVING>(grp, n, gq.tau, recs_set, P.core.faces, P.core.off[bi], P.core.off[bi + 1], tb, in_img,
+                              u, v, bestk, bestf);
     uint32_t uncov = 0;
 #pragma unroll
     for (int i = 0; i < SPT; ++i)
@@ -410,7 +411,8 @@ __global__ void __launch_bounds__(TW * TH) raster_bwd_kernel(RasterParams P) {
 #pragma unroll
       for (int i = 0; i < SPT; ++i) { p2.prod[i] = 1.f; p2.nzero[i] = 0; }
       p2.inv_delta = P.inv_delta;
-      for_soft_terms<SPT, MOVING>(s_grp, recs_set, P.soft.faces, sb, se, tb, active, u, v, uncov, P.r, P.r2, p2);
+      for_soft_terms<SPT, MOVING>(grp, n, gq.xbits, recs_set, P.soft.faces, sb, se, tb, active, u, v, uncov, P.r,
+                                  P.r2, p2);
       BwdSoftGrad<SPT, MOVING> p3;
 #pragma unroll
       for (int i = 0; i < SPT; ++i) { p3.prod[i] = p2.prod[i]; p3.nzero[i] = p2.nzero[i]; }
@@ -419,17 +421,24 @@ __global__ void __launch_bounds__(TW * TH) raster_bwd_kernel(RasterParams P) {
       p3.faces = P.faces;
       p3.gslot_a = gslot_a;
       p3.gslot_b = gslot_b;
-      for_soft_terms<SPT, MOVING>(s_grp, recs_set, P.soft.faces, sb, se, tb, active, u, v, uncov, P.r, P.r2, p3);
+      for_soft_terms<SPT, MOVING>(grp, n, gq.xbits, recs_set, P.soft.faces, sb, se, tb, active, u, v, uncov, P.r,
+                                  P.r2, p3);
     }
 
-    // ---- covered samples: shading adjoint and barycentric adjoint of the winner
+    // ---- covered samples: shading adjoint and barycentric adjoint of the winner (one copy of
+    // the code, looping over the group's samples)
+#pragma unroll 1
+    for (int i = 0; i < n; ++i) {
+      int f = -1;
+      float tau = 0.f;
 #pragma unroll
-    for (int i = 0; i < SPT; ++i) {
-      if (i < n) {
-        const bool has = in_img && bestf[i] >= 0;
-        covered_adjoint<MOVING>(P, recs_set, s_grp.slot_a, s_grp.slot_b, has, has ? bestf[i] : 0,
-                                MOVING ? s_grp.tau[i] : 0.f, u, v, gr, gg, gb);
-      }
+      for (int q = 0; q < SPT; ++q)
+        if (q == i) {
+          f = bestf[q];
+          tau = gq.tau[q];
+        }
+      const bool has = in_img && f >= 0;
+      covered_adjoint<MOVING>(P, recs_set, gq.slot_a, gq.slot_b, has, has ? f : 0, tau, u, v, gr, gg, gb);
     }
   }
 }

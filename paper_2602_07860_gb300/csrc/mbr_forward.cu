@@ -282,7 +282,6 @@ struct FwdSoftProduct {
 
 template <int TW, int TH, int SPT, bool MOVING>
 __global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(RasterParams P) {
-  __shared__ Group s_grp;
   const int n_tiles = P.tiles_x * P.tiles_y;
   const int tile = blockIdx.x % n_tiles, split = blockIdx.x / n_tiles;
   const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
@@ -297,14 +296,16 @@ __global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(RasterParams P) {
   float acc_r = 0.f, acc_g = 0.f, acc_b = 0.f, acc_a = 0.f;
 
   for (int g = g_begin; g < g_end; ++g) {
-    load_group(s_grp, P.groups, g);
-    const int n = s_grp.n;
-    const TriRec* recs_set = P.recs + (size_t)s_grp.rec_set * P.F;
+    const Group* grp = P.groups + g;
+    GroupRegs<SPT> gr;
+    gr.load(grp);
+    const int n = gr.n;
+    const TriRec* recs_set = P.recs + (size_t)gr.rec_set * P.F;
     const size_t bi = (size_t)g * n_tiles + tile;
     float bestk[SPT];
     int bestf[SPT];
-    pass_winners<SPT, MOVING>(s_grp, recs_set, P.core.faces, P.core.off[bi], P.core.off[bi + 1], tb, in_img, u, v,
-                              bestk, bestf);
+    pass_winners<SPT, MOVING>(grp, n, gr.tau, recs_set, P.core.faces, P.core.off[bi], P.core.off[bi + 1], tb, in_img,
+                              u, v, bestk, bestf);
     uint32_t uncov = 0;
 #pragma unroll
     for (int i = 0; i < SPT; ++i)
@@ -315,7 +316,8 @@ __global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(RasterParams P) {
     soft.inv_delta = P.inv_delta;
     const int sb = P.soft.off[bi], se = P.soft.off[bi + 1];
     if (se > sb && __any_sync(0xffffffffu, in_img && uncov != 0))
-      for_soft_terms<SPT, MOVING>(s_grp, recs_set, P.soft.faces, sb, se, tb, in_img, u, v, uncov, P.r, P.r2, soft);
+      for_soft_terms<SPT, MOVING>(grp, n, gr.xbits, recs_set, P.soft.faces, sb, se, tb, in_img, u, v, uncov, P.r,
+                                  P.r2, soft);
 
     // ---- shading of the winners (Eq. fore + Lambert) and temporal accumulation (Sec. 3.3)
     if (in_img) {
@@ -323,18 +325,11 @@ __global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(RasterParams P) {
       for (int i = 0; i < SPT; ++i) {
         if (i < n) {
           const int f = bestf[i];
-          if (P.dbg_ids && s_grp.k0 + i == P.dbg_k) P.dbg_ids[(size_t)py * P.W + px] = f;
+          if (P.dbg_ids && gr.k0 + i == P.dbg_k) P.dbg_ids[(size_t)py * P.W + px] = f;
           if (f >= 0) {
-            const float tau = MOVING ? s_grp.tau[i] : 0.f;
+            const float tau = gr.tau[i];
             float4 r[kRecF4];
-            const TriRec* src = recs_set + f;
-            r[kR_O] = __ldg(&src->f4[kR_O]);
-            r[kR_E2] = __ldg(&src->f4[kR_E2]);
-            if (MOVING) {
-              r[kR_D] = __ldg(&src->f4[kR_D]);
-              r[kR_G] = __ldg(&src->f4[kR_G]);
-              r[kR_A] = __ldg(&src->f4[kR_A]);
-            }
+            load_record<MOVING>(recs_set + f, r, false, false);
             const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
             const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
             const float invD = 1.0f / e.D;
@@ -346,9 +341,9 @@ __global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(RasterParams P) {
               cr = fmaf(w[q], __ldg(P.albedo + 3 * vid), cr);
               cg = fmaf(w[q], __ldg(P.albedo + 3 * vid + 1), cg);
               cb = fmaf(w[q], __ldg(P.albedo + 3 * vid + 2), cb);
-              float4 na = __ldg(P.slot_nrm + (size_t)s_grp.slot_a * P.V + vid);
+              float4 na = __ldg(P.slot_nrm + (size_t)gr.slot_a * P.V + vid);
               if (MOVING) {
-                const float4 nb = __ldg(P.slot_nrm + (size_t)s_grp.slot_b * P.V + vid);
+                const float4 nb = __ldg(P.slot_nrm + (size_t)gr.slot_b * P.V + vid);
                 na.x = fmaf(tau, nb.x - na.x, na.x);
                 na.y = fmaf(tau, nb.y - na.y, na.y);
                 na.z = fmaf(tau, nb.z - na.z, na.z);

@@ -202,16 +202,16 @@ __device__ __forceinline__ bool in_box(const float4& b, float u, float v) {
 // rectangle, and a pixel-reject box (union of those samples' boxes).  Computed by one lane per
 // candidate.
 template <bool MOVING>
-__device__ __forceinline__ uint32_t candidate_meta(const TriRec* rec, const Group& grp, const TileBox& tb, float m,
-                                                   float4& box) {
+__device__ __forceinline__ uint32_t candidate_meta(const TriRec* rec, const Group* grp, int n, const TileBox& tb,
+                                                   float m, float4& box) {
   const float4 b = __ldg(&rec->f4[kR_BB]);
   float4 db = make_float4(0.f, 0.f, 0.f, 0.f);
   if (MOVING) db = __ldg(&rec->f4[kR_DBB]);
   uint32_t mask = 0;
   float tlo = INFINITY, thi = -INFINITY;
-  const int n = MOVING ? grp.n : 1;
+  if (!MOVING) n = 1;
   for (int i = 0; i < n; ++i) {
-    const float tau = MOVING ? grp.tau[i] : 0.f;
+    const float tau = MOVING ? __ldg(&grp->tau[i]) : 0.f;
     const bool hit = fmaf(tau, db.x, b.x) - m <= tb.u_hi && fmaf(tau, db.y, b.y) + m >= tb.u_lo &&
                      fmaf(tau, db.z, b.z) - m <= tb.v_hi && fmaf(tau, db.w, b.w) + m >= tb.v_lo;
     if (hit) {
@@ -262,8 +262,8 @@ __device__ __forceinline__ float4 shfl_box(const float4& b, int src) {
 // fn(face, rec, mask, box).  Warp-collective: every lane of the warp must call it.
 template <bool MOVING, typename Fn>
 __device__ __forceinline__ void for_warp_candidates(const TriRec* recs_set, const int32_t* list, int beg, int end,
-                                                    const Group& grp, const TileBox& tb, float m, uint32_t samples,
-                                                    Fn&& fn) {
+                                                    const Group* grp, int n, const TileBox& tb, float m,
+                                                    uint32_t samples, Fn&& fn) {
   for (int c0 = beg; c0 < end; c0 += 32) {
     const int j = c0 + (int)(threadIdx.x & 31);
     int f = 0;
@@ -271,7 +271,7 @@ __device__ __forceinline__ void for_warp_candidates(const TriRec* recs_set, cons
     float4 box = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
     if (j < end && !tb.empty) {
       f = __ldg(list + j);
-      mask = candidate_meta<MOVING>(recs_set + f, grp, tb, m, box) & samples;
+      mask = candidate_meta<MOVING>(recs_set + f, grp, n, tb, m, box) & samples;
     }
     uint32_t live = __ballot_sync(0xffffffffu, mask != 0);
     while (live) {
@@ -287,15 +287,16 @@ __device__ __forceinline__ void for_warp_candidates(const TriRec* recs_set, cons
 
 // pass 1: z-test winners of the group's samples for this pixel (warp-collective)
 template <int SPT, bool MOVING>
-__device__ __forceinline__ void pass_winners(const Group& grp, const TriRec* recs_set, const int32_t* list, int beg,
-                                             int end, const TileBox& tb, bool in_img, float u, float v,
-                                             float (&bestk)[SPT], int (&bestf)[SPT]) {
+__device__ __forceinline__ void pass_winners(const Group* grp, int n, const float (&taus)[SPT],
+                                             const TriRec* recs_set, const int32_t* list, int beg, int end,
+                                             const TileBox& tb, bool in_img, float u, float v, float (&bestk)[SPT],
+                                             int (&bestf)[SPT]) {
 #pragma unroll
   for (int i = 0; i < SPT; ++i) {
     bestk[i] = -INFINITY;
     bestf[i] = -1;
   }
-  for_warp_candidates<MOVING>(recs_set, list, beg, end, grp, tb, kCoreMargin, 0xffffffffu,
+  for_warp_candidates<MOVING>(recs_set, list, beg, end, grp, n, tb, kCoreMargin, 0xffffffffu,
                               [&](int face, const TriRec* src, uint32_t mask, const float4& box) {
     if (!in_img || !in_box(box, u, v)) return;
     float4 r[kRecF4];
@@ -304,7 +305,7 @@ __device__ __forceinline__ void pass_winners(const Group& grp, const TriRec* rec
 #pragma unroll
     for (int i = 0; i < SPT; ++i) {
       if (mask & (1u << i)) {
-        const float tau = MOVING ? grp.tau[i] : 0.f;
+        const float tau = taus[i];
         const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
         if (covers(e)) {
           const float key = inv_depth<MOVING>(r, e, tau);
@@ -322,41 +323,53 @@ __device__ __forceinline__ void pass_winners(const Group& grp, const TriRec* rec
 // fn.term(r, ps, e, sg, i, tau, X) for each (candidate, sample) with d <= r^2, bracketed by
 // fn.begin() and fn.end(face) per candidate.  Warp-collective: begin/end run on every lane.
 template <int SPT, bool MOVING, typename Fn>
-__device__ __forceinline__ void for_soft_terms(const Group& grp, const TriRec* recs_set, const int32_t* list, int beg,
-                                               int end, const TileBox& tb, bool active, float u, float v,
-                                               uint32_t uncov, float r_soft, float r2, Fn&& fn) {
+__device__ __forceinline__ void for_soft_terms(const Group* grp, int n, uint32_t xbits, const TriRec* recs_set,
+                                               const int32_t* list, int beg, int end, const TileBox& tb,
+                                               bool active, float u, float v, uint32_t uncov, float r_soft, float r2,
+                                               Fn&& fn) {
   const float m = r_soft + kCoreMargin;
   const uint32_t warp_uncov = __reduce_or_sync(0xffffffffu, active ? uncov : 0u);
-  for_warp_candidates<MOVING>(recs_set, list, beg, end, grp, tb, m, warp_uncov,
+  for_warp_candidates<MOVING>(recs_set, list, beg, end, grp, n, tb, m, warp_uncov,
                               [&](int face, const TriRec* src, uint32_t mask_all, const float4& box) {
-    const uint32_t mask = active ? (mask_all & uncov) : 0u;
+    uint32_t mask = active ? (mask_all & uncov) : 0u;
     fn.begin();
     if (mask && in_box(box, u, v)) {
       float4 r[kRecF4];
       load_record<MOVING>(src, r, false, true);
       const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
-#pragma unroll
-      for (int i = 0; i < SPT; ++i) {
-        if (mask & (1u << i)) {
-          const float tau = MOVING ? grp.tau[i] : 0.f;
-          if (MOVING && !in_box_at(r, tau, m, u, v)) continue;
-          const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
-          if (fabsf(e.D) <= kDetMin) continue;
-          const int X = (grp.xbits >> i) & 1u;
-          const SoftGeom sg = soft_geom<MOVING>(r, ps, e, tau, X);
-          if (sg.d <= r2) fn.term(r, ps, e, sg, i, tau, X);
-        }
+      // one copy of the (large) soft-term code: walk the set sample bits
+      while (mask) {
+        const int i = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const float tau = MOVING ? __ldg(&grp->tau[i]) : 0.f;
+        if (MOVING && !in_box_at(r, tau, m, u, v)) continue;
+        const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
+        if (fabsf(e.D) <= kDetMin) continue;
+        const int X = (xbits >> i) & 1u;
+        const SoftGeom sg = soft_geom<MOVING>(r, ps, e, tau, X);
+        if (sg.d <= r2) fn.term(r, ps, e, sg, i, tau, X);
       }
     }
     fn.end(face);
   });
 }
 
-__device__ __forceinline__ void load_group(Group& s_grp, const Group* groups, int g) {
-  __syncthreads();
-  if (threadIdx.x < sizeof(Group) / 4)
-    reinterpret_cast<int*>(&s_grp)[threadIdx.x] = reinterpret_cast<const int*>(groups + g)[threadIdx.x];
-  __syncthreads();
-}
+// per-group values every thread keeps in registers
+template <int SPT>
+struct GroupRegs {
+  int n, rec_set, slot_a, slot_b, k0;
+  uint32_t xbits;
+  float tau[SPT];
+  __device__ __forceinline__ void load(const Group* g) {
+    n = __ldg(&g->n);
+    rec_set = __ldg(&g->rec_set);
+    slot_a = __ldg(&g->slot_a);
+    slot_b = __ldg(&g->slot_b);
+    k0 = __ldg(&g->k0);
+    xbits = __ldg(&g->xbits);
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) tau[i] = i < n ? __ldg(&g->tau[i]) : 0.f;
+  }
+};
 
 }  // namespace mbr
