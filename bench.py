@@ -33,7 +33,7 @@ METRIC = "pixel x sub-frame samples/s, fast solver forward+backward"
 UNIT = "samples/s"
 WORKLOAD = ("rotation: icosphere subdiv 4 + SH degree 6 (2562 v, 5120 f), one turn about a seeded axis, "
             "T=64, 256x256, 12 segments; step = forward + adjoint")
-CPU_WINDOW = (96, 96, 64, 64)     # bounded oracle sample for the CPU baseline (~10 s)
+CPU_WINDOW = (64, 64, 128, 128)   # bounded oracle sample for the CPU baseline (~15 s)
 REF_WINDOW = (120, 120, 16, 16)   # per-step oracle sample of the reference arm
 
 

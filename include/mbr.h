@@ -116,10 +116,26 @@ int mbr_render_blur_backward(mbr_ctx* ctx, const mbr_mesh* mesh, const mbr_motio
                              int32_t solver, const float* dl_dimage, float* dl_dverts,
                              float* dl_dalbedo, void* cuda_stream);
 
-/* Render n independent items (objects, motions, sub-frame counts and resolutions may differ)
- * with one persistent raster launch per pass, forward and (with_backward != 0) backward. */
+/* Render n independent items (objects, motions, solvers, sub-frame counts and resolutions may
+ * differ), forward and, if with_backward != 0, the adjoint too.  The front halves of all items run
+ * first, one stream sync sizes every item's tile lists, then a single persistent raster launch
+ * covers every item's work (largest renders first), and likewise for the adjoint.  The sequence
+ * is captured in a CUDA graph owned by the context: a later call with the same structure (item
+ * count, sizes, solvers, segment counts, device buffers, camera fov/znear/delta and tuning) only
+ * refreshes the motion/camera tables and replays the graph.  Replays bin into lists with 25%
+ * headroom; if geometry changed enough to overflow them, the call re-plans and recaptures by
+ * itself.  The call synchronises its stream before returning.  Motivated by the paper's
+ * optimisation loops that render many views per iteration (Sec. 5); the batching itself is a
+ * design of this library. */
 int mbr_render_blur_batch(mbr_ctx* ctx, int32_t n, const mbr_item* items, int32_t with_backward,
                           void* cuda_stream);
+
+/* Autotuner: times mbr_render_blur_batch on these items for every candidate tile shape (16x16,
+ * 8x8 pixels) and, when a fast-solver item is present, sub-frames per thread (4, 8, 16), keeps
+ * the fastest on the context (as mbr_set_tuning would) and reports it.  Any out pointer may be
+ * NULL.  The items are rendered several times (their outputs are overwritten). */
+int mbr_autotune(mbr_ctx* ctx, int32_t n, const mbr_item* items, int32_t with_backward,
+                 int32_t* best_tile, int32_t* best_spt, float* best_ms, void* cuda_stream);
 
 /* Test hook: the z-test winner (face id, -1 = background) of every pixel at sub-frame k,
  * written to ids [H,W] (device).  Same arguments as mbr_render_blur otherwise. */

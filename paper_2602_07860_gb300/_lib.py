@@ -17,7 +17,7 @@ SOLVERS = {"plain": MBR_PLAIN, "fast": MBR_FAST}
 
 EXPORTS = ["mbr_create", "mbr_destroy", "mbr_render_blur", "mbr_render_blur_backward", "mbr_render_blur_batch",
            "mbr_debug_winners", "mbr_count_candidates", "mbr_set_tuning", "mbr_set_profiling", "mbr_get_stats",
-           "mbr_render_blur_noalloc", "mbr_last_error"]
+           "mbr_render_blur_noalloc", "mbr_autotune", "mbr_last_error"]
 
 
 class MbrMesh(ctypes.Structure):
@@ -86,6 +86,8 @@ def load(build_if_missing=True):
     L.mbr_count_candidates.restype = c_int32
     L.mbr_render_blur_batch.argtypes = [c_void_p, c_int32, P(MbrItem), c_int32, c_void_p]
     L.mbr_render_blur_batch.restype = c_int32
+    L.mbr_autotune.argtypes = [c_void_p, c_int32, P(MbrItem), c_int32, P(c_int32), P(c_int32), P(c_float), c_void_p]
+    L.mbr_autotune.restype = c_int32
     L.mbr_set_tuning.argtypes = [c_void_p, c_int32, c_int32, c_int32]
     L.mbr_set_tuning.restype = c_int32
     L.mbr_set_profiling.argtypes = [c_void_p, c_int32]

@@ -32,6 +32,8 @@ struct BinSet {
   DevBuf counts, offsets, cursor, list, scan_tmp;
 };
 
+struct BatchState;  // batched renders (defined with mbr_render_blur_batch)
+
 }  // namespace
 
 struct mbr_ctx {
@@ -46,6 +48,13 @@ struct mbr_ctx {
   void* host_stage = nullptr;
   size_t host_stage_cap = 0;
   int32_t* host_total = nullptr;
+  // persistent-raster work queue of single renders: params + offsets + counter (device), and a
+  // pinned host copy of the params
+  DevBuf queue;
+  void* host_queue = nullptr;
+  size_t host_queue_cap = 0;
+  // batch plans (mbr_render_blur_batch): arena per plan, captured graph, pinned staging
+  BatchState* batch = nullptr;
   // measurement: one event pair per raster kind (0 forward, 1 adjoint), harvested lazily
   bool profiling = false;
   cudaEvent_t ev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -235,6 +244,7 @@ struct Prepared {
   SlotXform* d_xf = nullptr;
   Group* d_groups = nullptr;
   float r = 0.f;
+  int core_cap = 0, soft_cap = 0;  // bin list capacities
 };
 
 int build_tables(mbr_ctx* c, const mbr_motion* motion, const mbr_camera* cam, int T, int solver,
@@ -370,7 +380,7 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
     if ((rc = ensure(c, bs.scan_tmp, sizeof(int32_t) * scan_temp_ints((int)nb), st))) return rc;
     CUDA_TRY(c, cudaMemsetAsync(bs.counts.p, 0, sizeof(int32_t) * (size_t)nb, st));
     launch_bin(false, (const TriRec*)c->recs.p, F, pp.d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles,
-               margins[q], (int32_t*)bs.counts.p, nullptr, nullptr, d_status, st);
+               margins[q], (int32_t*)bs.counts.p, nullptr, nullptr, 0, d_status, st);
     launch_scan((const int32_t*)bs.counts.p, (int)nb, (int32_t*)bs.offsets.p, (int32_t*)bs.scan_tmp.p, st);
     CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaMemcpyAsync(c->host_total + 2 * q, (int32_t*)bs.offsets.p + nb, sizeof(int32_t),
@@ -388,11 +398,14 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
     CUDA_TRY(c, cudaMemcpyAsync(bs.cursor.p, bs.offsets.p, sizeof(int32_t) * (size_t)nb, cudaMemcpyDeviceToDevice,
                                 st));
     launch_bin(true, (const TriRec*)c->recs.p, F, pp.d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles,
-               margins[q], (int32_t*)bs.cursor.p, (int32_t*)bs.list.p, (const int32_t*)bs.offsets.p, d_status, st);
+               margins[q], (int32_t*)bs.cursor.p, (int32_t*)bs.list.p, (const int32_t*)bs.offsets.p, (int)totals[q],
+             d_status, st);
     CUDA_TRY(c, cudaGetLastError());
   }
   c->stats.launches += 2 * ((F > 0 ? 2 : 0) + 3);
   c->stats.bin_entries = totals[0] + totals[1];
+  pp.core_cap = (int)totals[0];
+  pp.soft_cap = (int)totals[1];
   // work split over sub-frame groups so that small images still fill the SMs
   int ns = c->splits;
   if (ns <= 0) ns = (8 * c->num_sms + pp.n_tiles - 1) / pp.n_tiles;
@@ -400,17 +413,33 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
   return MBR_OK;
 }
 
-RasterParams raster_params(mbr_ctx* c, const mbr_mesh* mesh, const mbr_camera* cam, int T, int H, int W,
-                           const Prepared& pp) {
+int render_work(int tile, int tiles, int n_split);
+
+// device buffers one render's raster reads (the context's own, a batch slice or the static scratch)
+struct RasterBufs {
+  const void* recs;
+  const void* nrm;
+  const void* off[2];   // core, soft bin offsets
+  const void* list[2];  // core, soft face lists
+};
+
+RasterBufs ctx_bufs(const mbr_ctx* c) {
+  return RasterBufs{c->recs.p, c->nrm.p, {c->core.offsets.p, c->soft.offsets.p}, {c->core.list.p, c->soft.list.p}};
+}
+
+RasterParams raster_params(const mbr_ctx* c, const RasterBufs& b, const mbr_mesh* mesh, const mbr_camera* cam, int T,
+                           int H, int W, const Prepared& pp) {
   RasterParams P;
   std::memset(&P, 0, sizeof(P));
-  P.recs = (const TriRec*)c->recs.p;
+  P.recs = (const TriRec*)b.recs;
   P.groups = pp.d_groups;
-  P.core.off = (const int32_t*)c->core.offsets.p;
-  P.core.faces = (const int32_t*)c->core.list.p;
-  P.soft.off = (const int32_t*)c->soft.offsets.p;
-  P.soft.faces = (const int32_t*)c->soft.list.p;
-  P.slot_nrm = (const float4*)c->nrm.p;
+  P.core.off = (const int32_t*)b.off[0];
+  P.core.faces = (const int32_t*)b.list[0];
+  P.soft.off = (const int32_t*)b.off[1];
+  P.soft.faces = (const int32_t*)b.list[1];
+  P.core.cap = pp.core_cap;
+  P.soft.cap = pp.soft_cap;
+  P.slot_nrm = (const float4*)b.nrm;
   P.faces = mesh->faces;
   P.albedo = mesh->albedo;
   P.F = mesh->F;
@@ -435,7 +464,46 @@ RasterParams raster_params(mbr_ctx* c, const mbr_mesh* mesh, const mbr_camera* c
   P.kd = cam->k_diffuse;
   P.inv_T = (float)(1.0 / T);
   P.dbg_k = -1;
+  P.moving = pp.moving ? 1 : 0;
+  P.work = render_work(c->tile, pp.n_tiles, pp.n_split);
   return P;
+}
+
+// work units of one render (see UnitMap)
+int render_work(int tile, int tiles, int n_split) {
+  return tile == 8 ? UnitMap<8, 8>::units(tiles, n_split) : UnitMap<16, 16>::units(tiles, n_split);
+}
+
+// Upload the params of the renders and their work offsets; the queue's counter is zeroed on st.
+int upload_queue(mbr_ctx* c, const RasterParams* items, int n, cudaStream_t st, WorkQueue& Q) {
+  const size_t par_b = sizeof(RasterParams) * n, off_b = sizeof(int32_t) * (n + 1);
+  const size_t off_at = (par_b + 255) & ~size_t(255), cnt_at = (off_at + off_b + 255) & ~size_t(255);
+  const size_t total = cnt_at + 256;
+  int rc;
+  if ((rc = ensure(c, c->queue, total, st))) return rc;
+  if (total > c->host_queue_cap) {
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    if (c->host_queue) cudaFreeHost(c->host_queue);
+    c->host_queue = nullptr;
+    c->host_queue_cap = 0;
+    if (cudaMallocHost(&c->host_queue, total + total / 4) != cudaSuccess)
+      return fail(c, MBR_ERR_OOM, "cudaMallocHost(%zu) failed", total);
+    c->host_queue_cap = total + total / 4;
+  }
+  char* h = (char*)c->host_queue;
+  std::memcpy(h, items, par_b);
+  int32_t* off = (int32_t*)(h + off_at);
+  off[0] = 0;
+  for (int i = 0; i < n; ++i) off[i + 1] = off[i] + items[i].work;
+  char* d = (char*)c->queue.p;
+  CUDA_TRY(c, cudaMemcpyAsync(d, h, cnt_at, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(c, cudaMemsetAsync(d + cnt_at, 0, sizeof(int32_t), st));
+  Q.items = (const RasterParams*)d;
+  Q.item_off = (const int32_t*)(d + off_at);
+  Q.n_items = n;
+  Q.n_work = off[n];
+  Q.counter = (int32_t*)(d + cnt_at);
+  return MBR_OK;
 }
 
 int forward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mbr_camera* cam, int T, int H,
@@ -445,7 +513,7 @@ int forward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, con
   if (!image && !dbg_ids) return fail(c, MBR_ERR_ARG, "null image");
   Prepared pp;
   if ((rc = prepare(c, mesh, motion, cam, T, H, W, solver, st, true, pp))) return rc;
-  RasterParams P = raster_params(c, mesh, cam, T, H, W, pp);
+  RasterParams P = raster_params(c, ctx_bufs(c), mesh, cam, T, H, W, pp);
   const size_t npix = (size_t)H * W;
   if (dbg_ids) {
     P.dbg_k = dbg_k;
@@ -457,8 +525,12 @@ int forward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, con
   } else {
     P.out = (float4*)image;
   }
+  WorkQueue Q;
+  if ((rc = upload_queue(c, &P, 1, st, Q))) return rc;
+  const int kind = pp.moving ? 1 : 0;
+  const int grid = std::max(1, std::min(persistent_grid_fwd(c->num_sms, c->tile, pp.spt, kind), Q.n_work));
   if ((rc = time_begin(c, 0, st))) return rc;
-  launch_raster_fwd(P, c->tile, pp.spt, pp.moving, st);
+  launch_raster_fwd(Q, c->tile, pp.spt, kind, grid, st);
   CUDA_TRY(c, cudaGetLastError());
   if ((rc = time_end(c, 0, st))) return rc;
   c->stats.launches += 1;
@@ -470,6 +542,9 @@ int forward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, con
   }
   return MBR_OK;
 }
+
+void destroy_batch(mbr_ctx* c);
+int batch_run(mbr_ctx* c, int n, const mbr_item* items, int with_backward, cudaStream_t st);
 
 }  // namespace
 
@@ -498,7 +573,7 @@ void mbr_destroy(mbr_ctx* c) {
   if (!c) return;
   DevBuf* bufs[] = {&c->nacc, &c->pos, &c->nrm, &c->recs, &c->tables, &c->partial, &c->gslot, &c->galb, &c->gm,
                     &c->cnt64,
-                    &c->status, &c->core.counts, &c->core.offsets, &c->core.cursor, &c->core.list,
+                    &c->status, &c->queue, &c->core.counts, &c->core.offsets, &c->core.cursor, &c->core.list,
                     &c->core.scan_tmp, &c->soft.counts, &c->soft.offsets, &c->soft.cursor, &c->soft.list,
                     &c->soft.scan_tmp};
   cudaDeviceSynchronize();
@@ -506,9 +581,11 @@ void mbr_destroy(mbr_ctx* c) {
     if (b->p) cudaFree(b->p);
   if (c->host_stage) cudaFreeHost(c->host_stage);
   if (c->host_total) cudaFreeHost(c->host_total);
+  if (c->host_queue) cudaFreeHost(c->host_queue);
   for (int k = 0; k < 2; ++k)
     for (int q = 0; q < 2; ++q)
       if (c->ev[k][q]) cudaEventDestroy(c->ev[k][q]);
+  destroy_batch(c);
   delete c;
 }
 
@@ -570,7 +647,7 @@ int mbr_render_blur_backward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion*
   if (!dl_dimage || !dl_dverts) return fail(c, MBR_ERR_ARG, "null gradient buffer");
   Prepared pp;
   if ((rc = prepare(c, mesh, motion, cam, T, H, W, solver, st, true, pp))) return rc;
-  RasterParams P = raster_params(c, mesh, cam, T, H, W, pp);
+  RasterParams P = raster_params(c, ctx_bufs(c), mesh, cam, T, H, W, pp);
   const int V = mesh->V;
   const size_t gbytes = sizeof(float4) * 2 * (size_t)V * pp.n_slots;
   if ((rc = ensure(c, c->gslot, gbytes, st))) return rc;
@@ -581,8 +658,12 @@ int mbr_render_blur_backward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion*
   P.dl_dimage = (const float4*)dl_dimage;
   P.g_slot = (float4*)c->gslot.p;
   P.g_albedo = dl_dalbedo ? (float4*)c->galb.p : nullptr;
+  WorkQueue Q;
+  if ((rc = upload_queue(c, &P, 1, st, Q))) return rc;
+  const int kind = pp.moving ? 1 : 0;
+  const int grid = std::max(1, std::min(persistent_grid_bwd(c->num_sms, c->tile, pp.spt, kind), Q.n_work));
   if ((rc = time_begin(c, 1, st))) return rc;
-  launch_raster_bwd(P, c->tile, pp.spt, pp.moving, st);
+  launch_raster_bwd(Q, c->tile, pp.spt, kind, grid, st);
   CUDA_TRY(c, cudaGetLastError());
   if ((rc = time_end(c, 1, st))) return rc;
   c->stats.launches += 1 + 1 + (mesh->F > 0 ? 1 : 0);
@@ -619,25 +700,458 @@ int mbr_count_candidates(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* mot
   return MBR_OK;
 }
 
+int mbr_autotune(mbr_ctx* c, int32_t n, const mbr_item* items, int32_t with_backward, int32_t* best_tile,
+                 int32_t* best_spt, float* best_ms, void* stream) {
+  if (!c) return MBR_ERR_ARG;
+  c->err.clear();
+  if (n <= 0 || !items) return fail(c, MBR_ERR_ARG, "bad batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  bool any_fast = false;
+  for (int i = 0; i < n; ++i) any_fast |= items[i].solver == MBR_FAST;
+  const int tiles[2] = {16, 8};
+  const int spts_fast[3] = {4, 8, 16};
+  const int n_spt = any_fast ? 3 : 1;
+  const int saved_tile = c->tile, saved_spt = c->spt, saved_splits = c->splits;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(c, cudaEventCreate(&e0));
+  CUDA_TRY(c, cudaEventCreate(&e1));
+  float best = INFINITY;
+  int bt = saved_tile, bs = saved_spt, rc = MBR_OK;
+  for (int ti = 0; ti < 2 && !rc; ++ti) {
+    for (int si = 0; si < n_spt && !rc; ++si) {
+      c->tile = tiles[ti];
+      c->spt = any_fast ? spts_fast[si] : saved_spt;
+      c->splits = saved_splits;
+      // first call plans and captures; then time replays
+      if ((rc = batch_run(c, n, items, with_backward, st))) break;
+      float ms_min = INFINITY;
+      for (int r = 0; r < 3 && !rc; ++r) {
+        cudaEventRecord(e0, st);
+        rc = batch_run(c, n, items, with_backward, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms_min = std::min(ms_min, ms);
+      }
+      if (!rc && ms_min < best) {
+        best = ms_min;
+        bt = c->tile;
+        bs = c->spt;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->tile = rc ? saved_tile : bt;
+  c->spt = rc ? saved_spt : bs;
+  c->splits = saved_splits;
+  if (rc) return rc;
+  if (best_tile) *best_tile = bt;
+  if (best_spt) *best_spt = bs;
+  if (best_ms) *best_ms = best;
+  return MBR_OK;
+}
+
 int mbr_render_blur_batch(mbr_ctx* c, int32_t n, const mbr_item* items, int32_t with_backward, void* stream) {
   if (!c) return MBR_ERR_ARG;
   c->err.clear();
   if (n < 0 || (n > 0 && !items)) return fail(c, MBR_ERR_ARG, "bad batch");
+  if (n == 0) return MBR_OK;
+  return batch_run(c, n, items, with_backward, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+// ------------------------------------------------------------------ batched renders
+// mbr_render_blur_batch: every item gets its own slice of one arena; the front halves of all items
+// (normals, transform, setup, bin counts and scans) run first, one stream sync reads every bin
+// total, the fills follow, then ONE persistent raster launch covers every item's work units
+// (largest renders first), and the adjoint likewise.  The whole sequence is then captured in a
+// CUDA graph: a later call with the same structure (sizes, solvers, buffers, tuning) only rewrites
+// the pinned tables and replays the graph.  Replays bin into lists with 25% headroom; if a list
+// would overflow (the geometry moved more), the call re-plans eagerly and recaptures.
+
+struct BatchItem {
+  Prepared pp;
+  std::vector<SlotXform> xf;
+  std::vector<int2> sets;
+  std::vector<Group> groups;
+  long long nb = 0;
+  size_t o_status = 0, o_nacc = 0, o_pos = 0, o_nrm = 0, o_recs = 0, o_tab = 0, o_sets = 0, o_groups = 0;
+  size_t tab_bytes = 0, o_partial = 0, o_gslot = 0, o_galb = 0, o_gm = 0;
+  size_t o_counts[2] = {0, 0}, o_offs[2] = {0, 0}, o_tmp[2] = {0, 0}, o_cursor[2] = {0, 0};
+  size_t o_list[2] = {0, 0};
+  int cap[2] = {0, 0};
+  size_t stage_tab = 0;
+};
+
+struct BatchState {
+  std::vector<long long> sig;
+  std::vector<BatchItem> items;
+  std::vector<int> order;  // item indices, largest render first
+  DevBuf arena, lists, queue;
+  void* stage = nullptr;
+  size_t stage_cap = 0, stage_queue = 0, stage_off = 0, stage_status = 0, stage_bytes = 0;
+  size_t arena_bytes = 0, list_bytes = 0;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t capture = nullptr;  // private stream the graph is captured on (the caller's stream
+                                   // may be the legacy default stream, which cannot be captured)
+  int kind = 1;
+  int grid_fwd = 1, grid_bwd = 1;  // persistent grids, fixed by the eager run (no queries in capture)
+  bool with_backward = false;
+};
+
+void free_graph(BatchState* B) {
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  B->exec = nullptr;
+}
+
+void destroy_batch(mbr_ctx* c) {
+  if (!c->batch) return;
+  BatchState* B = c->batch;
+  free_graph(B);
+  if (B->capture) cudaStreamDestroy(B->capture);
+  DevBuf* bufs[] = {&B->arena, &B->lists, &B->queue};
+  for (DevBuf* b : bufs)
+    if (b->p) cudaFree(b->p);
+  if (B->stage) cudaFreeHost(B->stage);
+  delete B;
+  c->batch = nullptr;
+}
+
+long long fbits(float x) {
+  int32_t i;
+  std::memcpy(&i, &x, 4);
+  return i;
+}
+
+std::vector<long long> batch_signature(mbr_ctx* c, int n, const mbr_item* items, int wb) {
+  std::vector<long long> s = {n, wb, c->tile, c->spt, c->splits};
   for (int i = 0; i < n; ++i) {
     const mbr_item& it = items[i];
-    int rc = forward_impl(c, &it.mesh, &it.motion, &it.camera, it.T, it.H, it.W, it.solver, it.image, -1, nullptr,
-                          (cudaStream_t)stream);
-    if (rc) return rc;
-    if (with_backward) {
-      rc = mbr_render_blur_backward(c, &it.mesh, &it.motion, &it.camera, it.T, it.H, it.W, it.solver, it.dl_dimage,
-                                    it.dl_dverts, it.dl_dalbedo, stream);
-      if (rc) return rc;
+    const long long vals[] = {it.mesh.V, it.mesh.F, it.T, it.H, it.W, it.solver,
+                              it.solver == MBR_FAST ? num_segments(&it.motion) : 0, it.camera.time_rule,
+                              fbits(it.camera.tan_half_fov), fbits(it.camera.znear), fbits(it.camera.delta),
+                              (long long)(uintptr_t)it.mesh.verts, (long long)(uintptr_t)it.mesh.faces,
+                              (long long)(uintptr_t)it.mesh.albedo, (long long)(uintptr_t)it.image,
+                              (long long)(uintptr_t)it.dl_dimage, (long long)(uintptr_t)it.dl_dverts,
+                              (long long)(uintptr_t)it.dl_dalbedo};
+    s.insert(s.end(), std::begin(vals), std::end(vals));
+  }
+  return s;
+}
+
+size_t carve(size_t& at, size_t bytes) {
+  const size_t o = (at + 255) & ~size_t(255);
+  at = o + bytes;
+  return o;
+}
+
+// host tables of every item into the pinned stage (called on every call: motion, camera change)
+void batch_write_tables(mbr_ctx* c, const mbr_item* items, BatchState& B, bool rebuild_groups) {
+  char* h = (char*)B.stage;
+  for (size_t i = 0; i < B.items.size(); ++i) {
+    BatchItem& I = B.items[i];
+    const mbr_item& it = items[i];
+    if (rebuild_groups) {
+      Prepared pp = I.pp;
+      build_tables(c, &it.motion, &it.camera, it.T, it.solver, I.xf, I.sets, I.groups, pp);
     }
+    std::memcpy(h + I.stage_tab, I.xf.data(), sizeof(SlotXform) * I.xf.size());
+    std::memcpy(h + I.stage_tab + (I.o_sets - I.o_tab), I.sets.data(), sizeof(int2) * I.sets.size());
+    std::memcpy(h + I.stage_tab + (I.o_groups - I.o_tab), I.groups.data(), sizeof(Group) * I.groups.size());
+  }
+}
+
+// Raster parameters of every item (queue order) into the pinned stage
+void batch_write_params(mbr_ctx* c, const mbr_item* items, BatchState& B) {
+  char* h = (char*)B.stage;
+  char* A = (char*)B.arena.p;
+  char* Lb = (char*)B.lists.p;
+  RasterParams* par = (RasterParams*)(h + B.stage_queue);
+  int32_t* off = (int32_t*)(h + B.stage_off);
+  off[0] = 0;
+  for (size_t k = 0; k < B.order.size(); ++k) {
+    const int i = B.order[k];
+    const BatchItem& I = B.items[i];
+    const mbr_item& it = items[i];
+    const RasterBufs bufs{A + I.o_recs, A + I.o_nrm, {A + I.o_offs[0], A + I.o_offs[1]},
+                          {Lb + I.o_list[0], Lb + I.o_list[1]}};
+    Prepared pp = I.pp;
+    pp.d_groups = (Group*)(A + I.o_groups);
+    pp.core_cap = I.cap[0];
+    pp.soft_cap = I.cap[1];
+    RasterParams P = raster_params(c, bufs, &it.mesh, &it.camera, it.T, it.H, it.W, pp);
+    P.out = I.pp.n_split > 1 ? (float4*)(A + I.o_partial) : (float4*)it.image;
+    if (B.with_backward) {
+      P.dl_dimage = (const float4*)it.dl_dimage;
+      P.g_slot = (float4*)(A + I.o_gslot);
+      P.g_albedo = it.dl_dalbedo ? (float4*)(A + I.o_galb) : nullptr;
+    }
+    par[k] = P;
+    off[k + 1] = off[k] + P.work;
+  }
+}
+
+int batch_plan(mbr_ctx* c, int n, const mbr_item* items, int wb, cudaStream_t st, BatchState& B) {
+  int rc;
+  free_graph(&B);
+  B.items.assign(n, BatchItem());
+  B.with_backward = wb != 0;
+  bool any_fast = false, any_plain = false;
+  size_t at = 0, stage_at = 0;
+  for (int i = 0; i < n; ++i) {
+    const mbr_item& it = items[i];
+    if ((rc = validate(c, &it.mesh, &it.motion, &it.camera, it.T, it.H, it.W, it.solver))) return rc;
+    if (!it.image) return fail(c, MBR_ERR_ARG, "item %d: null image", i);
+    if (wb && (!it.dl_dimage || !it.dl_dverts)) return fail(c, MBR_ERR_ARG, "item %d: null gradient buffer", i);
+    BatchItem& I = B.items[i];
+    if ((rc = build_tables(c, &it.motion, &it.camera, it.T, it.solver, I.xf, I.sets, I.groups, I.pp))) return rc;
+    Prepared& pp = I.pp;
+    (it.solver == MBR_FAST ? any_fast : any_plain) = true;
+    const int V = it.mesh.V, F = it.mesh.F;
+    pp.tiles_x = (it.W + c->tile - 1) / c->tile;
+    pp.tiles_y = (it.H + c->tile - 1) / c->tile;
+    pp.n_tiles = pp.tiles_x * pp.tiles_y;
+    pp.r = (float)std::sqrt((double)it.camera.delta * (double)kSoftCutoff);
+    int ns = c->splits;
+    if (ns <= 0) ns = (2 * c->num_sms + pp.n_tiles - 1) / pp.n_tiles;  // batches have many items: fewer splits
+    pp.n_split = std::max(1, std::min(ns, pp.G));
+    I.nb = (long long)pp.G * pp.n_tiles;
+    if (I.nb > (1LL << 30)) return fail(c, MBR_ERR_ARG, "item %d: too many bins", i);
+    I.o_status = carve(at, sizeof(int32_t));
+    I.o_nacc = carve(at, sizeof(float) * 3 * V);
+    I.o_pos = carve(at, sizeof(float4) * (size_t)pp.n_slots * V);
+    I.o_nrm = carve(at, sizeof(float4) * (size_t)pp.n_slots * V);
+    I.o_recs = carve(at, sizeof(TriRec) * (size_t)pp.n_sets * std::max(F, 1));
+    I.o_tab = carve(at, sizeof(SlotXform) * I.xf.size());
+    I.o_sets = carve(at, sizeof(int2) * I.sets.size());
+    I.o_groups = carve(at, sizeof(Group) * I.groups.size());
+    I.tab_bytes = I.o_groups + sizeof(Group) * I.groups.size() - I.o_tab;
+    for (int q = 0; q < 2; ++q) {
+      I.o_counts[q] = carve(at, sizeof(int32_t) * (size_t)I.nb);
+      I.o_offs[q] = carve(at, sizeof(int32_t) * (size_t)(I.nb + 1));
+      I.o_tmp[q] = carve(at, sizeof(int32_t) * scan_temp_ints((int)I.nb));
+      I.o_cursor[q] = carve(at, sizeof(int32_t) * (size_t)I.nb);
+    }
+    if (pp.n_split > 1) I.o_partial = carve(at, sizeof(float4) * (size_t)it.H * it.W * pp.n_split);
+    if (wb) {
+      I.o_gslot = carve(at, sizeof(float4) * 2 * (size_t)V * pp.n_slots);
+      I.o_galb = carve(at, sizeof(float4) * V);
+      I.o_gm = carve(at, sizeof(float) * 3 * V);
+    }
+    I.stage_tab = carve(stage_at, I.tab_bytes);
+  }
+  B.kind = any_fast && any_plain ? 2 : (any_fast ? 1 : 0);
+  B.order.resize(n);
+  for (int i = 0; i < n; ++i) B.order[i] = i;
+  std::stable_sort(B.order.begin(), B.order.end(), [&](int a, int b) {
+    const double ca = (double)items[a].H * items[a].W * items[a].T, cb = (double)items[b].H * items[b].W * items[b].T;
+    return ca > cb;
+  });
+  B.stage_queue = carve(stage_at, sizeof(RasterParams) * n);
+  B.stage_off = carve(stage_at, sizeof(int32_t) * (n + 1));
+  B.stage_status = carve(stage_at, sizeof(int32_t) * 4 * n);
+  B.stage_bytes = stage_at;
+  B.arena_bytes = at;
+  if ((rc = ensure(c, B.arena, at, st))) return rc;
+  if ((rc = ensure(c, B.queue, B.stage_off - B.stage_queue + sizeof(int32_t) * (n + 1) + 512, st))) return rc;
+  if (stage_at > B.stage_cap) {
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    if (B.stage) cudaFreeHost(B.stage);
+    B.stage = nullptr;
+    B.stage_cap = 0;
+    if (cudaMallocHost(&B.stage, stage_at + stage_at / 4) != cudaSuccess)
+      return fail(c, MBR_ERR_OOM, "cudaMallocHost(%zu) failed", stage_at);
+    B.stage_cap = stage_at + stage_at / 4;
   }
   return MBR_OK;
 }
 
-}  // extern "C"
+// Issue the batch on st.  sizing: count bins, sync and size the lists (eager, not capturable);
+// otherwise the lists keep the plan's capacities and the fills are bound-checked.
+int batch_enqueue(mbr_ctx* c, const mbr_item* items, BatchState& B, cudaStream_t st, bool sizing) {
+  int rc;
+  char* A = (char*)B.arena.p;
+  const int n = (int)B.items.size();
+  for (int i = 0; i < n; ++i) {
+    const BatchItem& I = B.items[i];
+    CUDA_TRY(c, cudaMemcpyAsync(A + I.o_tab, (char*)B.stage + I.stage_tab, I.tab_bytes, cudaMemcpyHostToDevice, st));
+  }
+  for (int i = 0; i < n; ++i) {
+    const BatchItem& I = B.items[i];
+    const mbr_item& it = items[i];
+    const Prepared& pp = I.pp;
+    const int V = it.mesh.V, F = it.mesh.F;
+    int* d_status = (int*)(A + I.o_status);
+    CUDA_TRY(c, cudaMemsetAsync(d_status, 0, sizeof(int32_t), st));
+    CUDA_TRY(c, cudaMemsetAsync(A + I.o_nacc, 0, sizeof(float) * 3 * V, st));
+    launch_face_normals(it.mesh.verts, it.mesh.faces, F, V, (float*)(A + I.o_nacc), d_status, st);
+    launch_xform(it.mesh.verts, (const float*)(A + I.o_nacc), V, (const SlotXform*)(A + I.o_tab), pp.n_slots,
+                 it.camera.tan_half_fov, (float4*)(A + I.o_pos), (float4*)(A + I.o_nrm), st);
+    launch_setup((const float4*)(A + I.o_pos), it.mesh.faces, F, V, (const int2*)(A + I.o_sets), pp.n_sets,
+                 it.camera.znear, (TriRec*)(A + I.o_recs), st);
+    const float margins[2] = {kCoreMargin, pp.r + kCoreMargin};
+    for (int q = 0; q < 2; ++q) {
+      CUDA_TRY(c, cudaMemsetAsync(A + I.o_counts[q], 0, sizeof(int32_t) * (size_t)I.nb, st));
+      launch_bin(false, (const TriRec*)(A + I.o_recs), F, (const Group*)(A + I.o_groups), pp.G, it.W, it.H, c->tile,
+                 c->tile, pp.tiles_x, pp.n_tiles, margins[q], (int32_t*)(A + I.o_counts[q]), nullptr, nullptr, 0,
+                 d_status, st);
+      launch_scan((const int32_t*)(A + I.o_counts[q]), (int)I.nb, (int32_t*)(A + I.o_offs[q]),
+                  (int32_t*)(A + I.o_tmp[q]), st);
+    }
+    CUDA_TRY(c, cudaGetLastError());
+  }
+  int32_t* hs = (int32_t*)((char*)B.stage + B.stage_status);
+  if (sizing) {
+    for (int i = 0; i < n; ++i) {
+      const BatchItem& I = B.items[i];
+      for (int q = 0; q < 2; ++q)
+        CUDA_TRY(c, cudaMemcpyAsync(hs + 4 * i + q, A + I.o_offs[q] + sizeof(int32_t) * I.nb, sizeof(int32_t),
+                                    cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(c, cudaMemcpyAsync(hs + 4 * i + 2, A + I.o_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    size_t lat = 0;
+    for (int i = 0; i < n; ++i) {
+      BatchItem& I = B.items[i];
+      if (hs[4 * i + 2] & kStatusBadFace) return fail(c, MBR_ERR_ARG, "item %d: face index outside [0, V)", i);
+      for (int q = 0; q < 2; ++q) {
+        const long long t = hs[4 * i + q];
+        if (t < 0) return fail(c, MBR_ERR_DEVICE, "item %d: bin total overflow", i);
+        I.cap[q] = (int)std::min<long long>(t + t / 4 + 4096, 0x7fffffffLL);  // headroom for replays
+        I.o_list[q] = carve(lat, sizeof(int32_t) * (size_t)I.cap[q]);
+      }
+    }
+    B.list_bytes = lat;
+    if ((rc = ensure(c, B.lists, lat, st))) return rc;
+    batch_write_params(c, items, B);  // now with the list slices and capacities
+  }
+  char* Lb = (char*)B.lists.p;
+  for (int i = 0; i < n; ++i) {
+    const BatchItem& I = B.items[i];
+    const mbr_item& it = items[i];
+    const Prepared& pp = I.pp;
+    const float margins[2] = {kCoreMargin, pp.r + kCoreMargin};
+    for (int q = 0; q < 2; ++q) {
+      CUDA_TRY(c, cudaMemcpyAsync(A + I.o_cursor[q], A + I.o_offs[q], sizeof(int32_t) * (size_t)I.nb,
+                                  cudaMemcpyDeviceToDevice, st));
+      launch_bin(true, (const TriRec*)(A + I.o_recs), it.mesh.F, (const Group*)(A + I.o_groups), pp.G, it.W, it.H,
+                 c->tile, c->tile, pp.tiles_x, pp.n_tiles, margins[q], (int32_t*)(A + I.o_cursor[q]),
+                 (int32_t*)(Lb + I.o_list[q]), (const int32_t*)(A + I.o_offs[q]), I.cap[q], (int*)(A + I.o_status),
+                 st);
+    }
+    if (B.with_backward) {
+      CUDA_TRY(c, cudaMemsetAsync(A + I.o_gslot, 0, sizeof(float4) * 2 * (size_t)it.mesh.V * pp.n_slots, st));
+      if (it.dl_dalbedo) CUDA_TRY(c, cudaMemsetAsync(A + I.o_galb, 0, sizeof(float4) * it.mesh.V, st));
+    }
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  // work queue: parameters (written to the stage by the caller) -> device, counter zeroed
+  char* dq = (char*)B.queue.p;
+  const size_t qbytes = B.stage_off - B.stage_queue + sizeof(int32_t) * (n + 1);
+  const size_t cnt_at = (qbytes + 255) & ~size_t(255);
+  CUDA_TRY(c, cudaMemcpyAsync(dq, (char*)B.stage + B.stage_queue, qbytes, cudaMemcpyHostToDevice, st));
+  WorkQueue Q;
+  Q.items = (const RasterParams*)dq;
+  Q.item_off = (const int32_t*)(dq + (B.stage_off - B.stage_queue));
+  Q.n_items = n;
+  Q.n_work = ((int32_t*)((char*)B.stage + B.stage_off))[n];
+  Q.counter = (int32_t*)(dq + cnt_at);
+  const int spt = std::max(1, std::min(kMaxSpt, c->spt));
+  if (sizing) {
+    B.grid_fwd = std::max(1, std::min(persistent_grid_fwd(c->num_sms, c->tile, spt, B.kind), Q.n_work));
+    B.grid_bwd = std::max(1, std::min(persistent_grid_bwd(c->num_sms, c->tile, spt, B.kind), Q.n_work));
+  }
+  CUDA_TRY(c, cudaMemsetAsync(Q.counter, 0, sizeof(int32_t), st));
+  launch_raster_fwd(Q, c->tile, spt, B.kind, B.grid_fwd, st);
+  CUDA_TRY(c, cudaGetLastError());
+  for (int i = 0; i < n; ++i) {
+    const BatchItem& I = B.items[i];
+    if (I.pp.n_split > 1)
+      launch_finalize((const float4*)(A + I.o_partial), I.pp.n_split, (size_t)items[i].H * items[i].W,
+                      (float)(1.0 / items[i].T), (float4*)items[i].image, st);
+  }
+  c->stats.launches += 1;
+  if (B.with_backward) {
+    CUDA_TRY(c, cudaMemsetAsync(Q.counter, 0, sizeof(int32_t), st));
+    launch_raster_bwd(Q, c->tile, spt, B.kind, B.grid_bwd, st);
+    CUDA_TRY(c, cudaGetLastError());
+    c->stats.launches += 1;
+    for (int i = 0; i < n; ++i) {
+      const BatchItem& I = B.items[i];
+      const mbr_item& it = items[i];
+      launch_slot_chain(it.mesh.verts, (const float*)(A + I.o_nacc), it.mesh.V, (const SlotXform*)(A + I.o_tab),
+                        I.pp.n_slots, it.camera.tan_half_fov, (const float4*)(A + I.o_gslot),
+                        (const float4*)(A + I.o_galb), it.dl_dverts, (float*)(A + I.o_gm), it.dl_dalbedo, st);
+      launch_normals_bwd(it.mesh.verts, it.mesh.faces, it.mesh.F, it.mesh.V, (const float*)(A + I.o_gm),
+                         it.dl_dverts, st);
+    }
+    CUDA_TRY(c, cudaGetLastError());
+  }
+  // statuses back to the stage (overflow detection after a replay)
+  for (int i = 0; i < n; ++i)
+    CUDA_TRY(c, cudaMemcpyAsync(hs + 4 * i + 3, A + B.items[i].o_status, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                st));
+  return MBR_OK;
+}
+
+int batch_check(mbr_ctx* c, const BatchState& B) {
+  const int32_t* hs = (const int32_t*)((char*)B.stage + B.stage_status);
+  for (size_t i = 0; i < B.items.size(); ++i) {
+    if (hs[4 * i + 3] & kStatusBadFace) return fail(c, MBR_ERR_ARG, "item %zu: face index outside [0, V)", i);
+    if (hs[4 * i + 3] & kStatusBinOverflow) return -1;  // lists too small: re-plan
+  }
+  return MBR_OK;
+}
+
+int batch_run(mbr_ctx* c, int n, const mbr_item* items, int wb, cudaStream_t st) {
+  int rc;
+  if (!c->batch) c->batch = new (std::nothrow) BatchState();
+  if (!c->batch) return fail(c, MBR_ERR_OOM, "batch state");
+  BatchState& B = *c->batch;
+  std::vector<long long> sig = batch_signature(c, n, items, wb);
+  if (B.exec && sig == B.sig) {
+    // replay: refresh the pinned tables and parameters, launch the graph, check for overflow
+    batch_write_tables(c, items, B, true);
+    batch_write_params(c, items, B);
+    CUDA_TRY(c, cudaGraphLaunch(B.exec, st));
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    rc = batch_check(c, B);
+    if (rc == MBR_OK) return MBR_OK;
+    if (rc != -1) return rc;
+  }
+  // plan, run eagerly (sizes the bin lists), then capture the same sequence for later calls
+  if ((rc = batch_plan(c, n, items, wb, st, B))) return rc;
+  batch_write_tables(c, items, B, false);
+  if ((rc = batch_enqueue(c, items, B, st, true))) return rc;
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  if ((rc = batch_check(c, B))) return rc == -1 ? fail(c, MBR_ERR_DEVICE, "bin lists overflowed") : rc;
+  B.sig = sig;
+  // capture for replays (same sequence, lists at their planned capacities) on the private stream
+  if (!B.capture) CUDA_TRY(c, cudaStreamCreateWithFlags(&B.capture, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  CUDA_TRY(c, cudaStreamBeginCapture(B.capture, cudaStreamCaptureModeThreadLocal));
+  rc = batch_enqueue(c, items, B, B.capture, false);
+  cudaError_t ce = cudaStreamEndCapture(B.capture, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (ce != cudaSuccess) return fail(c, MBR_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+  ce = cudaGraphInstantiate(&B.exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ce != cudaSuccess) {
+    B.exec = nullptr;
+    return fail(c, MBR_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+  }
+  return MBR_OK;
+}
+
+}  // namespace
 
 // ------------------------------------------------------------------ allocation-free forward render
 // mbr_render_blur_noalloc: the forward pipeline of mbr_render_blur, with every scratch buffer
@@ -736,7 +1250,7 @@ int noalloc_forward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, 
   for (int q = 0; q < 2; ++q) {
     CUDA_TRY(c, cudaMemsetAsync(counts[q], 0, sizeof(int32_t) * (size_t)nb, st));
     launch_bin(false, recs, F, d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles, margins[q], counts[q], nullptr,
-               nullptr, d_status, st);
+               nullptr, 0, d_status, st);
     launch_scan(counts[q], (int)nb, offs[q], tmp[q], st);
     CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaMemcpyAsync(host + q, offs[q] + nb, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -753,21 +1267,39 @@ int noalloc_forward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, 
   for (int q = 0; q < 2; ++q) {
     CUDA_TRY(c, cudaMemcpyAsync(cursor[q], offs[q], sizeof(int32_t) * (size_t)nb, cudaMemcpyDeviceToDevice, st));
     launch_bin(true, recs, F, d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles, margins[q], cursor[q], list[q],
-               offs[q], d_status, st);
+               offs[q], host[q], d_status, st);
   }
   CUDA_TRY(c, cudaGetLastError());
 
   // raster, writing the caller's image directly (one split, no partial sums)
-  c->recs.p = recs;
-  c->nrm.p = nrm;
-  c->core.offsets.p = offs[0];
-  c->core.list.p = list[0];
-  c->soft.offsets.p = offs[1];
-  c->soft.list.p = list[1];
-  RasterParams P = raster_params(c, mesh, cam, T, H, W, pp);
+  pp.core_cap = host[0];
+  pp.soft_cap = host[1];
+  const RasterBufs bufs{recs, nrm, {offs[0], offs[1]}, {list[0], list[1]}};
+  RasterParams P = raster_params(c, bufs, mesh, cam, T, H, W, pp);
   P.out = (float4*)image;
-  launch_raster_fwd(P, tw, pp.spt, pp.moving, st);
+  RasterParams* d_par = (RasterParams*)A.take(sizeof(RasterParams));
+  int32_t* d_off = (int32_t*)A.take(sizeof(int32_t) * 2);
+  int32_t* d_cnt = (int32_t*)A.take(sizeof(int32_t));
+  if (!d_par || !d_off || !d_cnt)
+    return fail(c, MBR_ERR_ARG, "render needs more than the %zu MiB static scratch; use mbr_render_blur",
+                kStaticScratchBytes >> 20);
+  const int32_t off[2] = {0, P.work};
+  CUDA_TRY(c, cudaMemcpyAsync(d_par, &P, sizeof(RasterParams), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(c, cudaMemcpyAsync(d_off, off, sizeof(off), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(c, cudaMemsetAsync(d_cnt, 0, sizeof(int32_t), st));
+  WorkQueue Q;
+  Q.items = d_par;
+  Q.item_off = d_off;
+  Q.n_items = 1;
+  Q.n_work = P.work;
+  Q.counter = d_cnt;
+  const int kind = pp.moving ? 1 : 0;
+  int sms = 1;
+  CUDA_TRY(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = std::max(1, std::min(persistent_grid_fwd(sms, tw, pp.spt, kind), Q.n_work));
+  launch_raster_fwd(Q, tw, pp.spt, kind, grid, st);
   CUDA_TRY(c, cudaGetLastError());
+  // (copies from pageable host memory are staged before cudaMemcpyAsync returns)
   return MBR_OK;
 }
 

@@ -57,19 +57,20 @@ __device__ __forceinline__ void rel_vertices(const float4* r, const PixelSetup<M
 template <int SPT>
 struct BwdSoftProduct {
   float prod[SPT];
-  int nzero[SPT];
+  uint32_t nzero;  // 2 bits per sample: vanishing factors 0, 1, or 2 = "two or more"
   float inv_delta;
   __device__ __forceinline__ void begin() {}
   template <typename PS>
   __device__ __forceinline__ void term(const float4*, const PS&, const EdgeVals&, const SoftGeom& sg, int i, float,
                                        int) {
     const float f = -expm1f(-sg.d * inv_delta);
+    if (f > kTinyFactor) {
 #pragma unroll
-    for (int q = 0; q < SPT; ++q)
-      if (q == i) {
-        if (f > kTinyFactor) prod[q] *= f;
-        else nzero[q] += 1;
-      }
+      for (int q = 0; q < SPT; ++q)
+        if (q == i) prod[q] *= f;
+    } else if (((nzero >> (2 * i)) & 3u) < 2u) {
+      nzero += 1u << (2 * i);
+    }
   }
   __device__ __forceinline__ void end(int) {}
 };
@@ -80,7 +81,7 @@ struct BwdSoftProduct {
 template <int SPT, bool MOVING>
 struct BwdSoftGrad {
   float prod[SPT];
-  int nzero[SPT];
+  uint32_t nzero;
   float ga, inv_delta;
   const int32_t* faces;
   float4* gslot_a;
@@ -99,10 +100,10 @@ struct BwdSoftGrad {
     const float f = -expm1f(-sg.d * inv_delta);
     const float A = __expf(-sg.d * inv_delta);
     float pr = 1.f;
-    int nz = 0;
+    const int nz = (nzero >> (2 * i)) & 3u;
 #pragma unroll
     for (int q = 0; q < SPT; ++q)
-      if (q == i) { pr = prod[q]; nz = nzero[q]; }
+      if (q == i) pr = prod[q];
     float excl;
     if (nz == 0) excl = pr / f;
     else excl = (nz == 1 && f <= kTinyFactor) ? pr : 0.f;
@@ -370,17 +371,17 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
   }
 }
 
+// One work item of the adjoint: the 8 x 4 pixel block wb of tile `tile`, groups of `split`.
 template <int TW, int TH, int SPT, bool MOVING>
-__global__ void __launch_bounds__(TW * TH) raster_bwd_kernel(RasterParams P) {
+__device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile, int split, int wb) {
   const int n_tiles = P.tiles_x * P.tiles_y;
-  const int tile = blockIdx.x % n_tiles, split = blockIdx.x / n_tiles;
   const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
   int px, py;
-  PixelMap<TW, TH>::pixel(tx, ty, px, py);
+  PixelMap<TW, TH>::pixel(tx, ty, wb, px, py);
   const bool in_img = px < P.W && py < P.H;
   const float u = (2.f * px + 1.f) / P.W - 1.f;
   const float v = 1.f - (2.f * py + 1.f) / P.H;
-  const TileBox tb = PixelMap<TW, TH>::warp_box(tx, ty, P.W, P.H);
+  const TileBox tb = PixelMap<TW, TH>::warp_box(tx, ty, wb, P.W, P.H);
   const int g_begin = (int)((long long)P.G * split / P.n_split);
   const int g_end = (int)((long long)P.G * (split + 1) / P.n_split);
   float4 G4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -389,7 +390,7 @@ __global__ void __launch_bounds__(TW * TH) raster_bwd_kernel(RasterParams P) {
 
   for (int g = g_begin; g < g_end; ++g) {
     const Group* grp = P.groups + g;
-    GroupRegs<SPT> gq;
+    GroupRegs gq;
     gq.load(grp);
     const int n = gq.n;
     const TriRec* recs_set = P.recs + (size_t)gq.rec_set * P.F;
@@ -398,24 +399,27 @@ __global__ void __launch_bounds__(TW * TH) raster_bwd_kernel(RasterParams P) {
     float4* gslot_b = P.g_slot + (size_t)gq.slot_b * P.V * 2;
     float bestk[SPT];
     int bestf[SPT];
-    pass_winners<SPT, MOVING>(grp, n, gq.tau, recs_set, P.core.faces, P.core.off[bi], P.core.off[bi + 1], tb, in_img,
-                              u, v, bestk, bestf);
+    int cb, ce, sb, se;
+    P.core.range(bi, cb, ce);
+    P.soft.range(bi, sb, se);
+    pass_winners<SPT, MOVING>(grp, n, recs_set, P.core.faces, cb, ce, tb, in_img, u, v, bestk, bestf);
     uint32_t uncov = 0;
 #pragma unroll
     for (int i = 0; i < SPT; ++i)
       if (i < n && bestf[i] < 0) uncov |= 1u << i;
-    const int sb = P.soft.off[bi], se = P.soft.off[bi + 1];
     const bool active = in_img && ga != 0.f;
     if (se > sb && __any_sync(0xffffffffu, active && uncov != 0)) {
       BwdSoftProduct<SPT> p2;
 #pragma unroll
-      for (int i = 0; i < SPT; ++i) { p2.prod[i] = 1.f; p2.nzero[i] = 0; }
+      for (int i = 0; i < SPT; ++i) p2.prod[i] = 1.f;
+      p2.nzero = 0u;
       p2.inv_delta = P.inv_delta;
       for_soft_terms<SPT, MOVING>(grp, n, gq.xbits, recs_set, P.soft.faces, sb, se, tb, active, u, v, uncov, P.r,
                                   P.r2, p2);
       BwdSoftGrad<SPT, MOVING> p3;
 #pragma unroll
-      for (int i = 0; i < SPT; ++i) { p3.prod[i] = p2.prod[i]; p3.nzero[i] = p2.nzero[i]; }
+      for (int i = 0; i < SPT; ++i) p3.prod[i] = p2.prod[i];
+      p3.nzero = p2.nzero;
       p3.ga = ga;
       p3.inv_delta = P.inv_delta;
       p3.faces = P.faces;
@@ -430,16 +434,28 @@ __global__ void __launch_bounds__(TW * TH) raster_bwd_kernel(RasterParams P) {
 #pragma unroll 1
     for (int i = 0; i < n; ++i) {
       int f = -1;
-      float tau = 0.f;
 #pragma unroll
       for (int q = 0; q < SPT; ++q)
-        if (q == i) {
-          f = bestf[q];
-          tau = gq.tau[q];
-        }
+        if (q == i) f = bestf[q];
+      const float tau = MOVING ? __ldg(gq.tau + i) : 0.f;
       const bool has = in_img && f >= 0;
       covered_adjoint<MOVING>(P, recs_set, gq.slot_a, gq.slot_b, has, has ? f : 0, tau, u, v, gr, gg, gb);
     }
+  }
+}
+
+// Persistent adjoint raster: KIND 0 = plain solver only, 1 = fast solver only, 2 = mixed batch.
+template <int TW, int TH, int SPT, int KIND>
+__global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 4 : 2) raster_bwd_persistent(WorkQueue Q) {
+  __shared__ RasterParams sp;
+  __shared__ int s_claim[1];
+  int cur = -1, tile = 0, split = 0, wb = 0;
+  while (next_unit<TW, TH>(Q, sp, s_claim, cur, tile, split, wb)) {
+    if (tile >= sp.tiles_x * sp.tiles_y) continue;
+    if (KIND == 0 || (KIND == 2 && !sp.moving))
+      raster_bwd_block<TW, TH, 1, false>(sp, tile, split, wb);
+    else
+      raster_bwd_block<TW, TH, SPT, true>(sp, tile, split, wb);
   }
 }
 
@@ -527,26 +543,54 @@ __global__ void normals_bwd_kernel(const float* __restrict__ verts, const int32_
   atomicAdd(g_verts + 3 * a + 2, -(bz + cz));
 }
 
-template <int TW, int TH>
-static void launch_raster_bwd_tile(const RasterParams& P, int spt, bool moving, unsigned blocks, cudaStream_t st) {
-  if (!moving) {
-    raster_bwd_kernel<TW, TH, 1, false><<<blocks, TW * TH, 0, st>>>(P);
-  } else if (spt <= 4) {
-    raster_bwd_kernel<TW, TH, 4, true><<<blocks, TW * TH, 0, st>>>(P);
-  } else if (spt <= 8) {
-    raster_bwd_kernel<TW, TH, 8, true><<<blocks, TW * TH, 0, st>>>(P);
-  } else {
-    raster_bwd_kernel<TW, TH, 16, true><<<blocks, TW * TH, 0, st>>>(P);
-  }
+template <int TW, int TH, int KIND>
+static void launch_bwd_spt(const WorkQueue& Q, int spt, int grid, cudaStream_t st) {
+  if (spt <= 4)
+    raster_bwd_persistent<TW, TH, 4, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
+  else if (spt <= 8)
+    raster_bwd_persistent<TW, TH, 8, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
+  else
+    raster_bwd_persistent<TW, TH, 16, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
 }
 
-void launch_raster_bwd(const RasterParams& P, int tile, int spt, bool moving, cudaStream_t st) {
-  const unsigned blocks = (unsigned)(P.tiles_x * P.tiles_y * P.n_split);
-  if (!blocks) return;
-  if (tile == 8)
-    launch_raster_bwd_tile<8, 8>(P, spt, moving, blocks, st);
+template <int TW, int TH>
+static void launch_bwd_tile(const WorkQueue& Q, int spt, int kind, int grid, cudaStream_t st) {
+  if (kind == 0)
+    raster_bwd_persistent<TW, TH, 1, 0><<<grid, kPersistentThreads, 0, st>>>(Q);
+  else if (kind == 1)
+    launch_bwd_spt<TW, TH, 1>(Q, spt, grid, st);
   else
-    launch_raster_bwd_tile<16, 16>(P, spt, moving, blocks, st);
+    launch_bwd_spt<TW, TH, 2>(Q, spt, grid, st);
+}
+
+void launch_raster_bwd(const WorkQueue& Q, int tile, int spt, int kind, int grid, cudaStream_t st) {
+  if (Q.n_work <= 0) return;
+  if (tile == 8)
+    launch_bwd_tile<8, 8>(Q, spt, kind, grid, st);
+  else
+    launch_bwd_tile<16, 16>(Q, spt, kind, grid, st);
+}
+
+template <typename K>
+static int occupancy_of(K kernel) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kPersistentThreads, 0) != cudaSuccess) n = 1;
+  return n < 1 ? 1 : n;
+}
+
+template <int TW, int TH>
+static int occ_bwd(int spt, int kind) {
+  if (kind == 0) return occupancy_of(raster_bwd_persistent<TW, TH, 1, 0>);
+  const int sp = spt <= 4 ? 4 : (spt <= 8 ? 8 : 16);
+  if (kind == 1)
+    return sp == 4 ? occupancy_of(raster_bwd_persistent<TW, TH, 4, 1>)
+                   : sp == 8 ? occupancy_of(raster_bwd_persistent<TW, TH, 8, 1>) : occupancy_of(raster_bwd_persistent<TW, TH, 16, 1>);
+  return sp == 4 ? occupancy_of(raster_bwd_persistent<TW, TH, 4, 2>)
+                 : sp == 8 ? occupancy_of(raster_bwd_persistent<TW, TH, 8, 2>) : occupancy_of(raster_bwd_persistent<TW, TH, 16, 2>);
+}
+
+int persistent_grid_bwd(int num_sms, int tile, int spt, int kind) {
+  return num_sms * (tile == 8 ? occ_bwd<8, 8>(spt, kind) : occ_bwd<16, 16>(spt, kind));
 }
 
 void launch_slot_chain(const float* verts, const float* nacc, int V, const SlotXform* xf, int n_slots, float th,

@@ -159,7 +159,7 @@ template <bool FILL>
 __global__ void bin_kernel(const TriRec* __restrict__ recs, int F, const Group* __restrict__ groups,
                            int G, int W, int H, int tw, int th, int tiles_x, int n_tiles, float r,
                            int32_t* __restrict__ counts_or_cursor, int32_t* __restrict__ list,
-                           const int32_t* __restrict__ bin_end, int* __restrict__ status) {
+                           const int32_t* __restrict__ bin_end, int list_cap, int* __restrict__ status) {
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (size_t)G * F) return;
   const int g = (int)(idx / F), f = (int)(idx - (size_t)g * F);
@@ -179,7 +179,7 @@ __global__ void bin_kernel(const TriRec* __restrict__ recs, int F, const Group* 
       if (FILL) {
         // the fill pass revisits exactly the counted (group, face, tile) triples; the check
         // only guards the list against a mismatch
-        if (slot < bin_end[(size_t)g * n_tiles + b + 1]) list[slot] = f;
+        if (slot < bin_end[(size_t)g * n_tiles + b + 1] && slot < list_cap) list[slot] = f;
         else atomicOr(status, kStatusBinOverflow);
       }
     }
@@ -280,32 +280,34 @@ struct FwdSoftProduct {
   __device__ __forceinline__ void end(int) {}
 };
 
+// One work item: the 8 x 4 pixel block wb of tile `tile`, sample groups of split `split`.
 template <int TW, int TH, int SPT, bool MOVING>
-__global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(RasterParams P) {
+__device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile, int split, int wb) {
   const int n_tiles = P.tiles_x * P.tiles_y;
-  const int tile = blockIdx.x % n_tiles, split = blockIdx.x / n_tiles;
   const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
   int px, py;
-  PixelMap<TW, TH>::pixel(tx, ty, px, py);
+  PixelMap<TW, TH>::pixel(tx, ty, wb, px, py);
   const bool in_img = px < P.W && py < P.H;
   const float u = (2.f * px + 1.f) / P.W - 1.f;
   const float v = 1.f - (2.f * py + 1.f) / P.H;
-  const TileBox tb = PixelMap<TW, TH>::warp_box(tx, ty, P.W, P.H);
+  const TileBox tb = PixelMap<TW, TH>::warp_box(tx, ty, wb, P.W, P.H);
   const int g_begin = (int)((long long)P.G * split / P.n_split);
   const int g_end = (int)((long long)P.G * (split + 1) / P.n_split);
   float acc_r = 0.f, acc_g = 0.f, acc_b = 0.f, acc_a = 0.f;
 
   for (int g = g_begin; g < g_end; ++g) {
     const Group* grp = P.groups + g;
-    GroupRegs<SPT> gr;
+    GroupRegs gr;
     gr.load(grp);
     const int n = gr.n;
     const TriRec* recs_set = P.recs + (size_t)gr.rec_set * P.F;
     const size_t bi = (size_t)g * n_tiles + tile;
     float bestk[SPT];
     int bestf[SPT];
-    pass_winners<SPT, MOVING>(grp, n, gr.tau, recs_set, P.core.faces, P.core.off[bi], P.core.off[bi + 1], tb, in_img,
-                              u, v, bestk, bestf);
+    int cb, ce, sb, se;
+    P.core.range(bi, cb, ce);
+    P.soft.range(bi, sb, se);
+    pass_winners<SPT, MOVING>(grp, n, recs_set, P.core.faces, cb, ce, tb, in_img, u, v, bestk, bestf);
     uint32_t uncov = 0;
 #pragma unroll
     for (int i = 0; i < SPT; ++i)
@@ -314,7 +316,6 @@ __global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(RasterParams P) {
 #pragma unroll
     for (int i = 0; i < SPT; ++i) soft.prod[i] = 1.f;
     soft.inv_delta = P.inv_delta;
-    const int sb = P.soft.off[bi], se = P.soft.off[bi + 1];
     if (se > sb && __any_sync(0xffffffffu, in_img && uncov != 0))
       for_soft_terms<SPT, MOVING>(grp, n, gr.xbits, recs_set, P.soft.faces, sb, se, tb, in_img, u, v, uncov, P.r,
                                   P.r2, soft);
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(RasterParams P) {
           const int f = bestf[i];
           if (P.dbg_ids && gr.k0 + i == P.dbg_k) P.dbg_ids[(size_t)py * P.W + px] = f;
           if (f >= 0) {
-            const float tau = gr.tau[i];
+            const float tau = MOVING ? __ldg(gr.tau + i) : 0.f;
             float4 r[kRecF4];
             load_record<MOVING>(recs_set + f, r, false, false);
             const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
@@ -372,6 +373,21 @@ __global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(RasterParams P) {
       P.out[o] = make_float4(acc_r * P.inv_T, acc_g * P.inv_T, acc_b * P.inv_T, acc_a * P.inv_T);
     else
       P.out[(size_t)split * P.H * P.W + o] = make_float4(acc_r, acc_g, acc_b, acc_a);
+  }
+}
+
+// Persistent forward raster: KIND 0 = plain solver only, 1 = fast solver only, 2 = mixed batch.
+template <int TW, int TH, int SPT, int KIND>
+__global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 4 : 2) raster_fwd_persistent(WorkQueue Q) {
+  __shared__ RasterParams sp;
+  __shared__ int s_claim[1];
+  int cur = -1, tile = 0, split = 0, wb = 0;
+  while (next_unit<TW, TH>(Q, sp, s_claim, cur, tile, split, wb)) {
+    if (tile >= sp.tiles_x * sp.tiles_y) continue;
+    if (KIND == 0 || (KIND == 2 && !sp.moving))
+      raster_fwd_block<TW, TH, 1, false>(sp, tile, split, wb);
+    else
+      raster_fwd_block<TW, TH, SPT, true>(sp, tile, split, wb);
   }
 }
 
@@ -429,16 +445,16 @@ void launch_setup(const float4* pos, const int32_t* faces, int F, int V, const i
 
 void launch_bin(bool fill, const TriRec* recs, int F, const Group* groups, int G, int W, int H, int tw, int th,
                 int tiles_x, int n_tiles, float r, int32_t* counts_or_cursor, int32_t* list,
-                const int32_t* bin_off, int* status, cudaStream_t st) {
+                const int32_t* bin_off, int list_cap, int* status, cudaStream_t st) {
   const size_t n = (size_t)G * F;
   if (!n) return;
   const unsigned blocks = (unsigned)((n + 255) / 256);
   if (fill)
     bin_kernel<true><<<blocks, 256, 0, st>>>(recs, F, groups, G, W, H, tw, th, tiles_x, n_tiles, r, counts_or_cursor,
-                                             list, bin_off, status);
+                                             list, bin_off, list_cap, status);
   else
     bin_kernel<false><<<blocks, 256, 0, st>>>(recs, F, groups, G, W, H, tw, th, tiles_x, n_tiles, r, counts_or_cursor,
-                                              list, bin_off, status);
+                                              list, bin_off, list_cap, status);
 }
 
 size_t scan_temp_ints(int n) { return (size_t)(n + kScanBlock - 1) / kScanBlock + 1; }
@@ -454,26 +470,54 @@ void launch_scan(const int32_t* in, int n, int32_t* out, int32_t* temp, cudaStre
   scan_apply_kernel<<<nb, kScanThreads, 0, st>>>(in, n, temp, out);
 }
 
-template <int TW, int TH>
-static void launch_raster_fwd_tile(const RasterParams& P, int spt, bool moving, unsigned blocks, cudaStream_t st) {
-  if (!moving) {
-    raster_fwd_kernel<TW, TH, 1, false><<<blocks, TW * TH, 0, st>>>(P);
-  } else if (spt <= 4) {
-    raster_fwd_kernel<TW, TH, 4, true><<<blocks, TW * TH, 0, st>>>(P);
-  } else if (spt <= 8) {
-    raster_fwd_kernel<TW, TH, 8, true><<<blocks, TW * TH, 0, st>>>(P);
-  } else {
-    raster_fwd_kernel<TW, TH, 16, true><<<blocks, TW * TH, 0, st>>>(P);
-  }
+template <int TW, int TH, int KIND>
+static void launch_fwd_spt(const WorkQueue& Q, int spt, int grid, cudaStream_t st) {
+  if (spt <= 4)
+    raster_fwd_persistent<TW, TH, 4, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
+  else if (spt <= 8)
+    raster_fwd_persistent<TW, TH, 8, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
+  else
+    raster_fwd_persistent<TW, TH, 16, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
 }
 
-void launch_raster_fwd(const RasterParams& P, int tile, int spt, bool moving, cudaStream_t st) {
-  const unsigned blocks = (unsigned)(P.tiles_x * P.tiles_y * P.n_split);
-  if (!blocks) return;
-  if (tile == 8)
-    launch_raster_fwd_tile<8, 8>(P, spt, moving, blocks, st);
+template <int TW, int TH>
+static void launch_fwd_tile(const WorkQueue& Q, int spt, int kind, int grid, cudaStream_t st) {
+  if (kind == 0)
+    raster_fwd_persistent<TW, TH, 1, 0><<<grid, kPersistentThreads, 0, st>>>(Q);
+  else if (kind == 1)
+    launch_fwd_spt<TW, TH, 1>(Q, spt, grid, st);
   else
-    launch_raster_fwd_tile<16, 16>(P, spt, moving, blocks, st);
+    launch_fwd_spt<TW, TH, 2>(Q, spt, grid, st);
+}
+
+template <typename K>
+static int occupancy_of(K kernel) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kPersistentThreads, 0) != cudaSuccess) n = 1;
+  return n < 1 ? 1 : n;
+}
+
+template <int TW, int TH>
+static int occ_fwd(int spt, int kind) {
+  if (kind == 0) return occupancy_of(raster_fwd_persistent<TW, TH, 1, 0>);
+  const int sp = spt <= 4 ? 4 : (spt <= 8 ? 8 : 16);
+  if (kind == 1)
+    return sp == 4 ? occupancy_of(raster_fwd_persistent<TW, TH, 4, 1>)
+                   : sp == 8 ? occupancy_of(raster_fwd_persistent<TW, TH, 8, 1>) : occupancy_of(raster_fwd_persistent<TW, TH, 16, 1>);
+  return sp == 4 ? occupancy_of(raster_fwd_persistent<TW, TH, 4, 2>)
+                 : sp == 8 ? occupancy_of(raster_fwd_persistent<TW, TH, 8, 2>) : occupancy_of(raster_fwd_persistent<TW, TH, 16, 2>);
+}
+
+int persistent_grid_fwd(int num_sms, int tile, int spt, int kind) {
+  return num_sms * (tile == 8 ? occ_fwd<8, 8>(spt, kind) : occ_fwd<16, 16>(spt, kind));
+}
+
+void launch_raster_fwd(const WorkQueue& Q, int tile, int spt, int kind, int grid, cudaStream_t st) {
+  if (Q.n_work <= 0) return;
+  if (tile == 8)
+    launch_fwd_tile<8, 8>(Q, spt, kind, grid, st);
+  else
+    launch_fwd_tile<16, 16>(Q, spt, kind, grid, st);
 }
 
 void launch_finalize(const float4* partial, int n_split, size_t npix, float inv_T, float4* image, cudaStream_t st) {

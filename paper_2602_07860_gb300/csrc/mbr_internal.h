@@ -9,6 +9,7 @@
 namespace mbr {
 
 struct RasterParams;
+struct WorkQueue;
 
 void launch_face_normals(const float* verts, const int32_t* faces, int F, int V, float* nacc, int* status,
                          cudaStream_t st);
@@ -18,15 +19,18 @@ void launch_setup(const float4* pos, const int32_t* faces, int F, int V, const i
                   float znear, TriRec* recs, cudaStream_t st);
 void launch_bin(bool fill, const TriRec* recs, int F, const Group* groups, int G, int W, int H, int tw, int th,
                 int tiles_x, int n_tiles, float r, int32_t* counts_or_cursor, int32_t* list,
-                const int32_t* bin_off, int* status, cudaStream_t st);
+                const int32_t* bin_off, int list_cap, int* status, cudaStream_t st);
 size_t scan_temp_ints(int n);
 void launch_scan(const int32_t* in, int n, int32_t* out, int32_t* temp, cudaStream_t st);
-void launch_raster_fwd(const RasterParams& P, int tile, int spt, bool moving, cudaStream_t st);
+// persistent raster launches; kind 0 plain only, 1 fast only, 2 mixed
+void launch_raster_fwd(const WorkQueue& Q, int tile, int spt, int kind, int grid, cudaStream_t st);
+int persistent_grid_fwd(int num_sms, int tile, int spt, int kind);
+int persistent_grid_bwd(int num_sms, int tile, int spt, int kind);
 void launch_finalize(const float4* partial, int n_split, size_t npix, float inv_T, float4* image, cudaStream_t st);
 void launch_count(const TriRec* recs, int F, const Group* groups, int G, int W, int H, float r,
                   unsigned long long* out, cudaStream_t st);
 
-void launch_raster_bwd(const RasterParams& P, int tile, int spt, bool moving, cudaStream_t st);
+void launch_raster_bwd(const WorkQueue& Q, int tile, int spt, int kind, int grid, cudaStream_t st);
 void launch_slot_chain(const float* verts, const float* nacc, int V, const SlotXform* xf, int n_slots, float th,
                        const float4* g_slot, const float4* g_alb4, float* g_verts, float* g_m, float* g_albedo,
                        cudaStream_t st);

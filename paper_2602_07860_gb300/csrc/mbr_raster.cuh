@@ -26,10 +26,16 @@ constexpr int kR_O = 0, kR_E2 = 1, kR_Z = 2, kR_BB = 3, kR_DBB = 4, kR_D = 5, kR
 // cannot change the product of Eq. back: the soft radius is sqrt(delta * 25 ln 2).
 constexpr float kSoftCutoff = 17.328679514f;  // 25 ln 2
 constexpr float kCoreMargin = 1e-5f;  // NDC slack of the undilated boxes (covers FP32 rounding)
+constexpr int kPersistentThreads = 256;  // threads of a persistent raster CTA (8 warps)
 
 struct BinLists {
   const int32_t* off;    // [G * n_tiles + 1]
   const int32_t* faces;  // CSR face lists
+  int32_t cap;           // entries allocated in faces (a replayed plan may count more: clamped)
+  __device__ __forceinline__ void range(size_t b, int& beg, int& end) const {
+    beg = min(off[b], cap);
+    end = min(off[b + 1], cap);
+  }
 };
 
 struct RasterParams {
@@ -47,6 +53,8 @@ struct RasterParams {
   float4* out;               // image (n_split == 1, scaled) or partial sums [n_split][H*W]
   int32_t dbg_k;             // sub-frame whose winners are written to dbg_ids (or -1)
   int32_t* dbg_ids;
+  int32_t moving;            // 1: fast solver (segment records), 0: plain solver (static records)
+  int32_t work;              // work items of this render: tiles * n_split * warp blocks per tile
   // adjoint only
   const float4* dl_dimage;   // [H*W]
   float4* g_slot;            // [slots][V][2]: (dx, dy, dnx, dny), (dnz, 0, 0, 0) of the slot states
@@ -170,19 +178,19 @@ struct TileBox {
   bool empty;
 };
 
-// Warp w of a TW x TH tile owns the 8 x 4 pixel block (w % (TW/8), w / (TW/8)); lane l is pixel
-// (l % 8, l / 8) of that block.
+// Warp block b of a TW x TH tile is the 8 x 4 pixel block (b % (TW/8), b / (TW/8)); lane l is
+// pixel (l % 8, l / 8) of that block.
 template <int TW, int TH>
 struct PixelMap {
   static_assert(TW % 8 == 0 && TH % 4 == 0, "tile must be a multiple of 8 x 4 pixels");
-  static __device__ __forceinline__ void pixel(int tx, int ty, int& px, int& py) {
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    px = tx * TW + (w % (TW / 8)) * 8 + (l & 7);
-    py = ty * TH + (w / (TW / 8)) * 4 + (l >> 3);
+  static constexpr int kBlocks = (TW / 8) * (TH / 4);
+  static __device__ __forceinline__ void pixel(int tx, int ty, int wb, int& px, int& py) {
+    const int l = threadIdx.x & 31;
+    px = tx * TW + (wb % (TW / 8)) * 8 + (l & 7);
+    py = ty * TH + (wb / (TW / 8)) * 4 + (l >> 3);
   }
-  static __device__ __forceinline__ TileBox warp_box(int tx, int ty, int W, int H) {
-    const int w = threadIdx.x >> 5;
-    const int x0 = tx * TW + (w % (TW / 8)) * 8, y0 = ty * TH + (w / (TW / 8)) * 4;
+  static __device__ __forceinline__ TileBox warp_box(int tx, int ty, int wb, int W, int H) {
+    const int x0 = tx * TW + (wb % (TW / 8)) * 8, y0 = ty * TH + (wb / (TW / 8)) * 4;
     const int x1 = min(W, x0 + 8) - 1, y1 = min(H, y0 + 4) - 1;
     TileBox t;
     t.empty = x0 >= W || y0 >= H;
@@ -287,8 +295,8 @@ __device__ __forceinline__ void for_warp_candidates(const TriRec* recs_set, cons
 
 // pass 1: z-test winners of the group's samples for this pixel (warp-collective)
 template <int SPT, bool MOVING>
-__device__ __forceinline__ void pass_winners(const Group* grp, int n, const float (&taus)[SPT],
-                                             const TriRec* recs_set, const int32_t* list, int beg, int end,
+__device__ __forceinline__ void pass_winners(const Group* grp, int n, const TriRec* recs_set, const int32_t* list,
+                                             int beg, int end,
                                              const TileBox& tb, bool in_img, float u, float v, float (&bestk)[SPT],
                                              int (&bestf)[SPT]) {
 #pragma unroll
@@ -305,7 +313,7 @@ __device__ __forceinline__ void pass_winners(const Group* grp, int n, const floa
 #pragma unroll
     for (int i = 0; i < SPT; ++i) {
       if (mask & (1u << i)) {
-        const float tau = taus[i];
+        const float tau = MOVING ? __ldg(&grp->tau[i]) : 0.f;
         const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
         if (covers(e)) {
           const float key = inv_depth<MOVING>(r, e, tau);
@@ -354,12 +362,68 @@ __device__ __forceinline__ void for_soft_terms(const Group* grp, int n, uint32_t
   });
 }
 
+// Persistent scheduling: the CTAs of a grid of (SM count x resident CTAs) take work units from an
+// atomic counter until none is left.  A unit is one split of the sample groups over a 256-pixel
+// patch of one render (one 16 x 16 tile, or four 8 x 8 tiles); the CTA's 8 warps take one 8 x 4
+// block each, so a tile's records are shared in the SM's L1.  Renders are ordered by the host
+// (largest first); item_off[i] is the first unit of render i.
+struct WorkQueue {
+  const RasterParams* items;  // [n_items]
+  const int32_t* item_off;    // [n_items + 1]
+  int32_t n_items, n_work;
+  int32_t* counter;           // zeroed before the launch
+};
+
+template <int TW, int TH>
+struct UnitMap {
+  static constexpr int kBlocks = PixelMap<TW, TH>::kBlocks;       // warp blocks per tile
+  static constexpr int kTilesPerUnit = 8 / kBlocks;                // tiles per 8-warp unit
+  static_assert(kBlocks * kTilesPerUnit == 8, "a unit must be 8 warp blocks");
+  static __host__ __device__ __forceinline__ int units(int n_tiles, int n_split) {
+    return n_split * ((n_tiles + kTilesPerUnit - 1) / kTilesPerUnit);
+  }
+};
+
+// Claim the next unit for this CTA (block-collective).  On success the CTA's render parameters
+// are in sp and (tile, split, wb) is this warp's part of the unit (tile may be past the last
+// tile for a ragged unit: the caller skips it).
+template <int TW, int TH>
+__device__ __forceinline__ bool next_unit(const WorkQueue& Q, RasterParams& sp, int* s_claim, int& cur_item,
+                                          int& tile, int& split, int& wb) {
+  __syncthreads();  // every warp is done with the previous unit (sp, s_claim)
+  if (threadIdx.x == 0) s_claim[0] = atomicAdd(Q.counter, 1);
+  __syncthreads();
+  const int w = s_claim[0];
+  if (w >= Q.n_work) return false;
+  int lo = 0, hi = Q.n_items - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(Q.item_off + mid) <= w) lo = mid;
+    else hi = mid - 1;
+  }
+  if (lo != cur_item) {  // uniform across the CTA
+    const int* src = reinterpret_cast<const int*>(Q.items + lo);
+    int* dst = reinterpret_cast<int*>(&sp);
+    for (int q = threadIdx.x; q < (int)(sizeof(RasterParams) / 4); q += blockDim.x) dst[q] = __ldg(src + q);
+    __syncthreads();
+    cur_item = lo;
+  }
+  using M = UnitMap<TW, TH>;
+  const int n_tiles = sp.tiles_x * sp.tiles_y;
+  const int per_split = (n_tiles + M::kTilesPerUnit - 1) / M::kTilesPerUnit;
+  const int r = w - __ldg(Q.item_off + lo);
+  const int warp = threadIdx.x >> 5;
+  split = r / per_split;
+  tile = (r % per_split) * M::kTilesPerUnit + warp / M::kBlocks;
+  wb = warp % M::kBlocks;
+  return true;
+}
+
 // per-group values every thread keeps in registers
-template <int SPT>
 struct GroupRegs {
   int n, rec_set, slot_a, slot_b, k0;
   uint32_t xbits;
-  float tau[SPT];
+  const float* tau;  // sample times of the group (read through L1 when needed)
   __device__ __forceinline__ void load(const Group* g) {
     n = __ldg(&g->n);
     rec_set = __ldg(&g->rec_set);
@@ -367,8 +431,7 @@ struct GroupRegs {
     slot_b = __ldg(&g->slot_b);
     k0 = __ldg(&g->k0);
     xbits = __ldg(&g->xbits);
-#pragma unroll
-    for (int i = 0; i < SPT; ++i) tau[i] = i < n ? __ldg(&g->tau[i]) : 0.f;
+    tau = g->tau;
   }
 };
 

@@ -179,11 +179,8 @@ class Context:
                                                 W, _lib.SOLVERS[solver], ctypes.byref(out), _stream()))
         return out.value
 
-    def render_batch(self, items, with_backward=False):
-        """items: list of dicts(verts, faces, albedo, motion, camera, T, H, W, solver, image,
-        [dl_dimage, dl_dverts, dl_dalbedo]) with preallocated CUDA tensors."""
+    def _items(self, items, with_backward):
         arr = (MbrItem * len(items))()
-        keep = []
         for i, it in enumerate(items):
             a = arr[i]
             a.mesh = self._mesh(it["verts"], it["faces"], it["albedo"])
@@ -196,8 +193,22 @@ class Context:
                 a.dl_dimage = it["dl_dimage"].data_ptr()
                 a.dl_dverts = it["dl_dverts"].data_ptr()
                 a.dl_dalbedo = it["dl_dalbedo"].data_ptr() if it.get("dl_dalbedo") is not None else 0
-            keep.append(it)
+        return arr
+
+    def render_batch(self, items, with_backward=False):
+        """items: list of dicts(verts, faces, albedo, motion, camera, T, H, W, solver, image,
+        [dl_dimage, dl_dverts, dl_dalbedo]) with preallocated CUDA tensors (see include/mbr.h)."""
+        arr = self._items(items, with_backward)
         self._raise(self.L.mbr_render_blur_batch(self.h, len(items), arr, int(bool(with_backward)), _stream()))
+
+    def autotune(self, items, with_backward=False):
+        """Pick the fastest tile shape / sub-frames per thread for this batch; returns
+        (tile, spt, ms) and keeps the choice on the context."""
+        arr = self._items(items, with_backward)
+        t, sp, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+        self._raise(self.L.mbr_autotune(self.h, len(items), arr, int(bool(with_backward)), ctypes.byref(t),
+                                        ctypes.byref(sp), ctypes.byref(ms), _stream()))
+        return t.value, sp.value, ms.value
 
 
 _default_ctx = {}
