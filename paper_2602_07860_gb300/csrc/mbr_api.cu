@@ -3,7 +3,7 @@
 // Per call: validate arguments -> time map (Secs. 3.2-3.3, exact integer arithmetic) -> per-slot
 // motion + camera matrices (double precision, one 3x4 per slot time) -> kernels on the caller's
 // stream: normals, transform, triangle setup, tile binning (count, scan, one stream sync to
-// size the face lists, fill), raster, finalize.  Backward reruns the same front half and the
+// size the face lists, fill), unit cost order, raster.  Backward reruns the same front half and the
 // adjoint raster, then chains slot gradients to vertices.
 #include <algorithm>
 #include <cmath>
@@ -43,7 +43,7 @@ struct mbr_ctx {
   // tuning
   int tile = 16, spt = 8, splits = 0;
   // scratch
-  DevBuf nacc, pos, nrm, recs, tables, partial, gslot, galb, gm, cnt64, status;
+  DevBuf nacc, pos, nrm, recs, tables, partial, gslot, galb, gm, cnt64, status, order;
   BinSet core, soft;  // undilated bins (coverage) and r_soft-dilated bins (soft coverage)
   void* host_stage = nullptr;
   size_t host_stage_cap = 0;
@@ -245,7 +245,22 @@ struct Prepared {
   Group* d_groups = nullptr;
   float r = 0.f;
   int core_cap = 0, soft_cap = 0;  // bin list capacities
+  int n_units = 0;                  // raster work units: patches x n_split
+  int32_t* d_order = nullptr;       // their visiting order
 };
+
+// units of a render: 256-pixel patches x group splits
+int patches_of(int tile, int n_tiles) {
+  return tile == 8 ? UnitMap<8, 8>::patches(n_tiles) : UnitMap<16, 16>::patches(n_tiles);
+}
+
+// Group splits: enough units (about 64 per SM) for the largest-first order to balance the SMs;
+// more splits add one float4 atomic per pixel and split in the forward.
+int choose_splits(const mbr_ctx* c, int G, int n_patches) {
+  int ns = c->splits;
+  if (ns <= 0) ns = (int)std::min<long long>(G, (64LL * c->num_sms + n_patches - 1) / std::max(1, n_patches));
+  return std::max(1, std::min(ns, std::max(G, 1)));
+}
 
 int build_tables(mbr_ctx* c, const mbr_motion* motion, const mbr_camera* cam, int T, int solver,
                  std::vector<SlotXform>& xf, std::vector<int2>& sets, std::vector<Group>& groups, Prepared& pp) {
@@ -345,8 +360,7 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
   if ((rc = ensure(c, c->pos, sizeof(float4) * (size_t)pp.n_slots * V, st))) return rc;
   if ((rc = ensure(c, c->nrm, sizeof(float4) * (size_t)pp.n_slots * V, st))) return rc;
   if ((rc = ensure(c, c->recs, sizeof(TriRec) * (size_t)pp.n_sets * std::max(F, 1), st))) return rc;
-  if ((rc = ensure(c, c->status, sizeof(int32_t), st))) return rc;
-  int* d_status = (int*)c->status.p;
+  int* d_status = (int*)c->status.p;  // [0] this call, [1] raster launches (sticky until read)
   CUDA_TRY(c, cudaMemsetAsync(d_status, 0, sizeof(int32_t), st));
   CUDA_TRY(c, cudaMemsetAsync(c->nacc.p, 0, sizeof(float) * 3 * V, st));
   launch_face_normals(mesh->verts, mesh->faces, F, V, (float*)c->nacc.p, d_status, st);
@@ -363,6 +377,7 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
     if (c->host_total[1] & kStatusBadFace) return fail(c, MBR_ERR_ARG, "face index outside [0, V)");
     return MBR_OK;
   }
+  CUDA_TRY(c, cudaMemcpyAsync(c->host_total + 3, d_status + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
 
   // a3 binning: core and soft bins: count -> scan (both) -> one sync for the totals -> fill
   const int tw = c->tile, th = c->tile;
@@ -389,6 +404,10 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
   CUDA_TRY(c, cudaMemcpyAsync(c->host_total + 1, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(c, cudaStreamSynchronize(st));
   if (c->host_total[1] & kStatusBadFace) return fail(c, MBR_ERR_ARG, "face index outside [0, V)");
+  if (c->host_total[3] & kStatusSpin) {
+    CUDA_TRY(c, cudaMemsetAsync(d_status + 1, 0, sizeof(int32_t), st));
+    return fail(c, MBR_ERR_TIMEOUT, "a raster launch of an earlier call gave up a bounded wait (its output is incomplete)");
+  }
   long long totals[2] = {c->host_total[0], c->host_total[2]};
   for (int q = 0; q < 2; ++q) {
     BinSet& bs = *sets2[q];
@@ -406,14 +425,18 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
   c->stats.bin_entries = totals[0] + totals[1];
   pp.core_cap = (int)totals[0];
   pp.soft_cap = (int)totals[1];
-  // work split over sub-frame groups so that small images still fill the SMs
-  int ns = c->splits;
-  if (ns <= 0) ns = (8 * c->num_sms + pp.n_tiles - 1) / pp.n_tiles;
-  pp.n_split = std::max(1, std::min(ns, pp.G));
+  // work units: patches x group splits, visited largest estimate first
+  const int n_patches = patches_of(tw, pp.n_tiles);
+  pp.n_split = choose_splits(c, pp.G, n_patches);
+  pp.n_units = n_patches * pp.n_split;
+  if ((rc = ensure(c, c->order, sizeof(int32_t) * (pp.n_units + unit_order_ints(pp.n_units)), st))) return rc;
+  pp.d_order = (int32_t*)c->order.p;
+  launch_unit_order((const int32_t*)c->core.offsets.p, (const int32_t*)c->soft.offsets.p, pp.G, pp.n_tiles, tw,
+                    pp.n_split, pp.n_units, pp.d_order, pp.d_order + pp.n_units, st);
+  CUDA_TRY(c, cudaGetLastError());
+  c->stats.launches += 3;
   return MBR_OK;
 }
-
-int render_work(int tile, int tiles, int n_split);
 
 // device buffers one render's raster reads (the context's own, a batch slice or the static scratch)
 struct RasterBufs {
@@ -465,13 +488,9 @@ RasterParams raster_params(const mbr_ctx* c, const RasterBufs& b, const mbr_mesh
   P.inv_T = (float)(1.0 / T);
   P.dbg_k = -1;
   P.moving = pp.moving ? 1 : 0;
-  P.work = render_work(c->tile, pp.n_tiles, pp.n_split);
+  P.work = pp.n_units;
+  P.order = pp.d_order;
   return P;
-}
-
-// work units of one render (see UnitMap)
-int render_work(int tile, int tiles, int n_split) {
-  return tile == 8 ? UnitMap<8, 8>::units(tiles, n_split) : UnitMap<16, 16>::units(tiles, n_split);
 }
 
 // Upload the params of the renders and their work offsets; the queue's counter is zeroed on st.
@@ -503,6 +522,7 @@ int upload_queue(mbr_ctx* c, const RasterParams* items, int n, cudaStream_t st, 
   Q.n_items = n;
   Q.n_work = off[n];
   Q.counter = (int32_t*)(d + cnt_at);
+  Q.status = (int32_t*)c->status.p + 1;
   return MBR_OK;
 }
 
@@ -519,12 +539,13 @@ int forward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, con
     P.dbg_k = dbg_k;
     P.dbg_ids = dbg_ids;
   }
-  if (pp.n_split > 1 || !image) {
-    if ((rc = ensure(c, c->partial, sizeof(float4) * npix * pp.n_split, st))) return rc;
+  if (!image) {  // winner ids only: the colours go to scratch
+    if ((rc = ensure(c, c->partial, sizeof(float4) * npix, st))) return rc;
     P.out = (float4*)c->partial.p;
   } else {
     P.out = (float4*)image;
   }
+  if (pp.n_split > 1) CUDA_TRY(c, cudaMemsetAsync(P.out, 0, sizeof(float4) * npix, st));  // splits accumulate
   WorkQueue Q;
   if ((rc = upload_queue(c, &P, 1, st, Q))) return rc;
   const int kind = pp.moving ? 1 : 0;
@@ -535,11 +556,6 @@ int forward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, con
   if ((rc = time_end(c, 0, st))) return rc;
   c->stats.launches += 1;
   c->stats.n_split = pp.n_split;
-  if (pp.n_split > 1 && image) {
-    launch_finalize((const float4*)c->partial.p, pp.n_split, npix, P.inv_T, (float4*)image, st);
-    CUDA_TRY(c, cudaGetLastError());
-    c->stats.launches += 1;
-  }
   return MBR_OK;
 }
 
@@ -565,6 +581,13 @@ int mbr_create(mbr_ctx** out) {
     delete c;
     return MBR_ERR_OOM;
   }
+  if (cudaMalloc(&c->status.p, 256) != cudaSuccess || cudaMemset(c->status.p, 0, 256) != cudaSuccess) {
+    if (c->status.p) cudaFree(c->status.p);
+    cudaFreeHost(c->host_total);
+    delete c;
+    return MBR_ERR_OOM;
+  }
+  c->status.cap = 256;
   *out = c;
   return MBR_OK;
 }
@@ -572,7 +595,7 @@ int mbr_create(mbr_ctx** out) {
 void mbr_destroy(mbr_ctx* c) {
   if (!c) return;
   DevBuf* bufs[] = {&c->nacc, &c->pos, &c->nrm, &c->recs, &c->tables, &c->partial, &c->gslot, &c->galb, &c->gm,
-                    &c->cnt64,
+                    &c->cnt64, &c->order,
                     &c->status, &c->queue, &c->core.counts, &c->core.offsets, &c->core.cursor, &c->core.list,
                     &c->core.scan_tmp, &c->soft.counts, &c->soft.offsets, &c->soft.cursor, &c->soft.list,
                     &c->soft.scan_tmp};
@@ -781,7 +804,7 @@ struct BatchItem {
   std::vector<Group> groups;
   long long nb = 0;
   size_t o_status = 0, o_nacc = 0, o_pos = 0, o_nrm = 0, o_recs = 0, o_tab = 0, o_sets = 0, o_groups = 0;
-  size_t tab_bytes = 0, o_partial = 0, o_gslot = 0, o_galb = 0, o_gm = 0;
+  size_t tab_bytes = 0, o_order = 0, o_gslot = 0, o_galb = 0, o_gm = 0;
   size_t o_counts[2] = {0, 0}, o_offs[2] = {0, 0}, o_tmp[2] = {0, 0}, o_cursor[2] = {0, 0};
   size_t o_list[2] = {0, 0};
   int cap[2] = {0, 0};
@@ -882,10 +905,11 @@ void batch_write_params(mbr_ctx* c, const mbr_item* items, BatchState& B) {
                           {Lb + I.o_list[0], Lb + I.o_list[1]}};
     Prepared pp = I.pp;
     pp.d_groups = (Group*)(A + I.o_groups);
+    pp.d_order = (int32_t*)(A + I.o_order);
     pp.core_cap = I.cap[0];
     pp.soft_cap = I.cap[1];
     RasterParams P = raster_params(c, bufs, &it.mesh, &it.camera, it.T, it.H, it.W, pp);
-    P.out = I.pp.n_split > 1 ? (float4*)(A + I.o_partial) : (float4*)it.image;
+    P.out = (float4*)it.image;
     if (B.with_backward) {
       P.dl_dimage = (const float4*)it.dl_dimage;
       P.g_slot = (float4*)(A + I.o_gslot);
@@ -917,9 +941,8 @@ int batch_plan(mbr_ctx* c, int n, const mbr_item* items, int wb, cudaStream_t st
     pp.tiles_y = (it.H + c->tile - 1) / c->tile;
     pp.n_tiles = pp.tiles_x * pp.tiles_y;
     pp.r = (float)std::sqrt((double)it.camera.delta * (double)kSoftCutoff);
-    int ns = c->splits;
-    if (ns <= 0) ns = (2 * c->num_sms + pp.n_tiles - 1) / pp.n_tiles;  // batches have many items: fewer splits
-    pp.n_split = std::max(1, std::min(ns, pp.G));
+    pp.n_split = choose_splits(c, pp.G, patches_of(c->tile, pp.n_tiles));
+    pp.n_units = patches_of(c->tile, pp.n_tiles) * pp.n_split;
     I.nb = (long long)pp.G * pp.n_tiles;
     if (I.nb > (1LL << 30)) return fail(c, MBR_ERR_ARG, "item %d: too many bins", i);
     I.o_status = carve(at, sizeof(int32_t));
@@ -937,7 +960,7 @@ int batch_plan(mbr_ctx* c, int n, const mbr_item* items, int wb, cudaStream_t st
       I.o_tmp[q] = carve(at, sizeof(int32_t) * scan_temp_ints((int)I.nb));
       I.o_cursor[q] = carve(at, sizeof(int32_t) * (size_t)I.nb);
     }
-    if (pp.n_split > 1) I.o_partial = carve(at, sizeof(float4) * (size_t)it.H * it.W * pp.n_split);
+    I.o_order = carve(at, sizeof(int32_t) * (pp.n_units + unit_order_ints(pp.n_units)));
     if (wb) {
       I.o_gslot = carve(at, sizeof(float4) * 2 * (size_t)V * pp.n_slots);
       I.o_galb = carve(at, sizeof(float4) * V);
@@ -1044,6 +1067,10 @@ int batch_enqueue(mbr_ctx* c, const mbr_item* items, BatchState& B, cudaStream_t
                  (int32_t*)(Lb + I.o_list[q]), (const int32_t*)(A + I.o_offs[q]), I.cap[q], (int*)(A + I.o_status),
                  st);
     }
+    int32_t* order = (int32_t*)(A + I.o_order);
+    launch_unit_order((const int32_t*)(A + I.o_offs[0]), (const int32_t*)(A + I.o_offs[1]), pp.G, pp.n_tiles, c->tile,
+                      pp.n_split, pp.n_units, order, order + pp.n_units, st);
+    if (pp.n_split > 1) CUDA_TRY(c, cudaMemsetAsync(it.image, 0, sizeof(float4) * (size_t)it.H * it.W, st));
     if (B.with_backward) {
       CUDA_TRY(c, cudaMemsetAsync(A + I.o_gslot, 0, sizeof(float4) * 2 * (size_t)it.mesh.V * pp.n_slots, st));
       if (it.dl_dalbedo) CUDA_TRY(c, cudaMemsetAsync(A + I.o_galb, 0, sizeof(float4) * it.mesh.V, st));
@@ -1061,6 +1088,7 @@ int batch_enqueue(mbr_ctx* c, const mbr_item* items, BatchState& B, cudaStream_t
   Q.n_items = n;
   Q.n_work = ((int32_t*)((char*)B.stage + B.stage_off))[n];
   Q.counter = (int32_t*)(dq + cnt_at);
+  Q.status = (int32_t*)(A + B.items[0].o_status);
   const int spt = std::max(1, std::min(kMaxSpt, c->spt));
   if (sizing) {
     B.grid_fwd = std::max(1, std::min(persistent_grid_fwd(c->num_sms, c->tile, spt, B.kind), Q.n_work));
@@ -1069,12 +1097,6 @@ int batch_enqueue(mbr_ctx* c, const mbr_item* items, BatchState& B, cudaStream_t
   CUDA_TRY(c, cudaMemsetAsync(Q.counter, 0, sizeof(int32_t), st));
   launch_raster_fwd(Q, c->tile, spt, B.kind, B.grid_fwd, st);
   CUDA_TRY(c, cudaGetLastError());
-  for (int i = 0; i < n; ++i) {
-    const BatchItem& I = B.items[i];
-    if (I.pp.n_split > 1)
-      launch_finalize((const float4*)(A + I.o_partial), I.pp.n_split, (size_t)items[i].H * items[i].W,
-                      (float)(1.0 / items[i].T), (float4*)items[i].image, st);
-  }
   c->stats.launches += 1;
   if (B.with_backward) {
     CUDA_TRY(c, cudaMemsetAsync(Q.counter, 0, sizeof(int32_t), st));
@@ -1103,6 +1125,7 @@ int batch_check(mbr_ctx* c, const BatchState& B) {
   const int32_t* hs = (const int32_t*)((char*)B.stage + B.stage_status);
   for (size_t i = 0; i < B.items.size(); ++i) {
     if (hs[4 * i + 3] & kStatusBadFace) return fail(c, MBR_ERR_ARG, "item %zu: face index outside [0, V)", i);
+    if (hs[4 * i + 3] & kStatusSpin) return fail(c, MBR_ERR_TIMEOUT, "a raster launch gave up a bounded wait");
     if (hs[4 * i + 3] & kStatusBinOverflow) return -1;  // lists too small: re-plan
   }
   return MBR_OK;
@@ -1207,7 +1230,9 @@ int noalloc_forward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, 
   pp.tiles_x = (W + tw - 1) / tw;
   pp.tiles_y = (H + th - 1) / th;
   pp.n_tiles = pp.tiles_x * pp.tiles_y;
-  pp.n_split = 1;
+  CUDA_TRY(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
+  pp.n_split = choose_splits(c, pp.G, patches_of(tw, pp.n_tiles));
+  pp.n_units = patches_of(tw, pp.n_tiles) * pp.n_split;
   pp.r = (float)std::sqrt((double)cam->delta * (double)kSoftCutoff);
   const long long nb = (long long)pp.G * pp.n_tiles;
 
@@ -1271,18 +1296,22 @@ int noalloc_forward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, 
   }
   CUDA_TRY(c, cudaGetLastError());
 
-  // raster, writing the caller's image directly (one split, no partial sums)
+  // unit order, then the raster into the caller's image (accumulated when the groups are split)
   pp.core_cap = host[0];
   pp.soft_cap = host[1];
-  const RasterBufs bufs{recs, nrm, {offs[0], offs[1]}, {list[0], list[1]}};
-  RasterParams P = raster_params(c, bufs, mesh, cam, T, H, W, pp);
-  P.out = (float4*)image;
   RasterParams* d_par = (RasterParams*)A.take(sizeof(RasterParams));
   int32_t* d_off = (int32_t*)A.take(sizeof(int32_t) * 2);
   int32_t* d_cnt = (int32_t*)A.take(sizeof(int32_t));
-  if (!d_par || !d_off || !d_cnt)
+  pp.d_order = (int32_t*)A.take(sizeof(int32_t) * (pp.n_units + unit_order_ints(pp.n_units)));
+  if (!d_par || !d_off || !d_cnt || !pp.d_order)
     return fail(c, MBR_ERR_ARG, "render needs more than the %zu MiB static scratch; use mbr_render_blur",
                 kStaticScratchBytes >> 20);
+  launch_unit_order(offs[0], offs[1], pp.G, pp.n_tiles, tw, pp.n_split, pp.n_units, pp.d_order,
+                    pp.d_order + pp.n_units, st);
+  const RasterBufs bufs{recs, nrm, {offs[0], offs[1]}, {list[0], list[1]}};
+  RasterParams P = raster_params(c, bufs, mesh, cam, T, H, W, pp);
+  P.out = (float4*)image;
+  if (pp.n_split > 1) CUDA_TRY(c, cudaMemsetAsync(image, 0, sizeof(float4) * (size_t)H * W, st));
   const int32_t off[2] = {0, P.work};
   CUDA_TRY(c, cudaMemcpyAsync(d_par, &P, sizeof(RasterParams), cudaMemcpyHostToDevice, st));
   CUDA_TRY(c, cudaMemcpyAsync(d_off, off, sizeof(off), cudaMemcpyHostToDevice, st));
@@ -1293,10 +1322,9 @@ int noalloc_forward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, 
   Q.n_items = 1;
   Q.n_work = P.work;
   Q.counter = d_cnt;
+  Q.status = d_status;
   const int kind = pp.moving ? 1 : 0;
-  int sms = 1;
-  CUDA_TRY(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int grid = std::max(1, std::min(persistent_grid_fwd(sms, tw, pp.spt, kind), Q.n_work));
+  const int grid = std::max(1, std::min(persistent_grid_fwd(c->num_sms, tw, pp.spt, kind), Q.n_work));
   launch_raster_fwd(Q, tw, pp.spt, kind, grid, st);
   CUDA_TRY(c, cudaGetLastError());
   // (copies from pageable host memory are staged before cudaMemcpyAsync returns)

@@ -1,6 +1,6 @@
 // mbr_backward.cu -- adjoint kernels of the sm_103a motion-blurred renderer (a9).
 //
-//   raster_bwd_kernel  recomputes passes 1-2 of the forward per sample (nothing is stored),
+//   raster_bwd_persistent recomputes passes 1-2 of the forward per sample (nothing is stored),
 //                      then back-propagates dL/dimage through shading (Eq. fore + Lambert),
 //                      the barycentric edge functions, and the soft-coverage product
 //                      (Eqs. probability-function .. back, exclusive products) into gradients on
@@ -447,15 +447,17 @@ __device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile
 // Persistent adjoint raster: KIND 0 = plain solver only, 1 = fast solver only, 2 = mixed batch.
 template <int TW, int TH, int SPT, int KIND>
 __global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 4 : 2) raster_bwd_persistent(WorkQueue Q) {
-  __shared__ RasterParams sp;
-  __shared__ int s_claim[1];
+  __shared__ CtaQueue cq;
+  __shared__ RasterParams sp[kPersistentThreads / 32];
+  cq.init();
+  RasterParams& P = sp[threadIdx.x >> 5];
   int cur = -1, tile = 0, split = 0, wb = 0;
-  while (next_unit<TW, TH>(Q, sp, s_claim, cur, tile, split, wb)) {
-    if (tile >= sp.tiles_x * sp.tiles_y) continue;
-    if (KIND == 0 || (KIND == 2 && !sp.moving))
-      raster_bwd_block<TW, TH, 1, false>(sp, tile, split, wb);
+  while (warp_next<TW, TH>(Q, cq, P, cur, tile, split, wb)) {
+    if (tile >= P.tiles_x * P.tiles_y) continue;
+    if (KIND == 0 || (KIND == 2 && !P.moving))
+      raster_bwd_block<TW, TH, 1, false>(P, tile, split, wb);
     else
-      raster_bwd_block<TW, TH, SPT, true>(sp, tile, split, wb);
+      raster_bwd_block<TW, TH, SPT, true>(P, tile, split, wb);
   }
 }
 

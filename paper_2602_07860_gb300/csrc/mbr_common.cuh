@@ -48,6 +48,7 @@ constexpr uint32_t kFlagCulled = 1u;  // a vertex at camera z <= znear: skipped 
 // device status word bits (read back by the host after the binning sync)
 constexpr int kStatusBadFace = 1;       // a face index outside [0, V)
 constexpr int kStatusBinOverflow = 2;   // fill pass disagreed with the count pass
+constexpr int kStatusSpin = 4;          // a raster CTA gave up a bounded wait (result incomplete)
 
 struct Group {
   int32_t rec_set;     // record set of the group's samples

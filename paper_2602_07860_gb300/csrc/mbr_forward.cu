@@ -5,9 +5,10 @@
 //   setup_kernel         a4 setup: per (record set, face) local-frame coefficients (TriRec)
 //   bin_kernel<FILL>     a3: per (group, face) swept r_soft-dilated bounding box -> tile bins
 //   scan kernels         exclusive scan of the bin counts (CSR offsets)
-//   raster_fwd_kernel    a4-a8: barycentric solve, coverage, z-test, soft alpha, shading,
-//                        temporal average, one float4 store per pixel
-//   finalize_kernel      sums the per-split partial images
+//   raster_fwd_persistent a4-a8: barycentric solve, coverage, z-test, soft alpha, shading,
+//                        temporal average; one float4 store per pixel (or one float4 atomic
+//                        add per pixel and group split)
+//   unit_*_kernel        visiting order of the raster's work units (largest estimate first)
 //   count_kernel         N_cand (measurement)
 #include <cstdint>
 
@@ -369,38 +370,89 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
   }
   if (in_img) {
     const size_t o = (size_t)py * P.W + px;
-    if (P.n_split == 1)
-      P.out[o] = make_float4(acc_r * P.inv_T, acc_g * P.inv_T, acc_b * P.inv_T, acc_a * P.inv_T);
-    else
-      P.out[(size_t)split * P.H * P.W + o] = make_float4(acc_r, acc_g, acc_b, acc_a);
+    const float4 val = make_float4(acc_r * P.inv_T, acc_g * P.inv_T, acc_b * P.inv_T, acc_a * P.inv_T);
+    if (P.n_split == 1) P.out[o] = val;
+    else atomicAdd(P.out + o, val);  // the image was zeroed; splits add their share of the mean
   }
 }
 
 // Persistent forward raster: KIND 0 = plain solver only, 1 = fast solver only, 2 = mixed batch.
 template <int TW, int TH, int SPT, int KIND>
 __global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 4 : 2) raster_fwd_persistent(WorkQueue Q) {
-  __shared__ RasterParams sp;
-  __shared__ int s_claim[1];
+  __shared__ CtaQueue cq;
+  __shared__ RasterParams sp[kPersistentThreads / 32];
+  cq.init();
+  RasterParams& P = sp[threadIdx.x >> 5];
   int cur = -1, tile = 0, split = 0, wb = 0;
-  while (next_unit<TW, TH>(Q, sp, s_claim, cur, tile, split, wb)) {
-    if (tile >= sp.tiles_x * sp.tiles_y) continue;
-    if (KIND == 0 || (KIND == 2 && !sp.moving))
-      raster_fwd_block<TW, TH, 1, false>(sp, tile, split, wb);
+  while (warp_next<TW, TH>(Q, cq, P, cur, tile, split, wb)) {
+    if (tile >= P.tiles_x * P.tiles_y) continue;
+    if (KIND == 0 || (KIND == 2 && !P.moving))
+      raster_fwd_block<TW, TH, 1, false>(P, tile, split, wb);
     else
-      raster_fwd_block<TW, TH, SPT, true>(sp, tile, split, wb);
+      raster_fwd_block<TW, TH, SPT, true>(P, tile, split, wb);
   }
 }
 
-__global__ void finalize_kernel(const float4* __restrict__ partial, int n_split, size_t npix, float inv_T,
-                                float4* __restrict__ image) {
-  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= npix) return;
-  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int q = 0; q < n_split; ++q) {
-    const float4 x = partial[(size_t)q * npix + p];
-    s.x += x.x; s.y += x.y; s.z += x.z; s.w += x.w;
+// ---------------------------------------------------------------- unit cost order (LPT)
+// Estimated work of a unit: its bin entries over the split's groups and the patch's tiles, the
+// soft entries weighted x2 (a soft term costs more than a coverage test).  Units are bucketed by
+// half-octaves of the estimate and visited from the largest bucket down.
+constexpr int kOrderBuckets = 64;
+
+__device__ __forceinline__ int unit_bucket(const int32_t* __restrict__ core_off, const int32_t* __restrict__ soft_off,
+                                           int G, int n_tiles, int tpu, int n_patches, int n_split, int u) {
+  const int split = u / n_patches, patch = u - split * n_patches;
+  const int g0 = (int)((long long)G * split / n_split), g1 = (int)((long long)G * (split + 1) / n_split);
+  long long cost = 0;
+  for (int g = g0; g < g1; ++g)
+    for (int q = 0; q < tpu; ++q) {
+      const int t = patch * tpu + q;
+      if (t >= n_tiles) break;
+      const size_t b = (size_t)g * n_tiles + t;
+      cost += (long long)(core_off[b + 1] - core_off[b]) + 2LL * (soft_off[b + 1] - soft_off[b]);
+    }
+  if (cost <= 0) return 0;
+  const int lg = 63 - __clzll(cost);                          // floor(log2(cost))
+  const int half = lg > 0 ? (int)((cost >> (lg - 1)) & 1) : 0;  // next bit: upper half-octave
+  return min(kOrderBuckets - 1, 1 + 2 * lg + half);
+}
+
+__global__ void unit_hist_kernel(const int32_t* __restrict__ core_off, const int32_t* __restrict__ soft_off, int G,
+                                 int n_tiles, int tpu, int n_patches, int n_split, int n_units,
+                                 int32_t* __restrict__ bucket, int32_t* __restrict__ hist) {
+  __shared__ int s_hist[kOrderBuckets];
+  if (threadIdx.x < kOrderBuckets) s_hist[threadIdx.x] = 0;
+  __syncthreads();
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < n_units) {
+    const int k = unit_bucket(core_off, soft_off, G, n_tiles, tpu, n_patches, n_split, u);
+    bucket[u] = k;
+    atomicAdd(&s_hist[k], 1);
   }
-  image[p] = make_float4(s.x * inv_T, s.y * inv_T, s.z * inv_T, s.w * inv_T);
+  __syncthreads();
+  if (threadIdx.x < kOrderBuckets && s_hist[threadIdx.x]) atomicAdd(hist + threadIdx.x, s_hist[threadIdx.x]);
+}
+
+// one warp: bucket start offsets, largest bucket first (hist becomes the cursor array)
+__global__ void unit_scan_kernel(int32_t* __restrict__ hist) {
+  const int lane = threadIdx.x;
+  // lane l owns buckets 63 - 2l and 62 - 2l (descending order)
+  const int a = hist[kOrderBuckets - 1 - 2 * lane], b = hist[kOrderBuckets - 2 - 2 * lane];
+  int incl = a + b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int ex = incl - a - b;
+  hist[kOrderBuckets - 1 - 2 * lane] = ex;
+  hist[kOrderBuckets - 2 - 2 * lane] = ex + a;
+}
+
+__global__ void unit_scatter_kernel(const int32_t* __restrict__ bucket, int n_units, int32_t* __restrict__ cursor,
+                                    int32_t* __restrict__ order) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < n_units) order[atomicAdd(cursor + bucket[u], 1)] = u;
 }
 
 // ---------------------------------------------------------------- N_cand (measurement)
@@ -520,8 +572,21 @@ void launch_raster_fwd(const WorkQueue& Q, int tile, int spt, int kind, int grid
     launch_fwd_tile<16, 16>(Q, spt, kind, grid, st);
 }
 
-void launch_finalize(const float4* partial, int n_split, size_t npix, float inv_T, float4* image, cudaStream_t st) {
-  if (npix) finalize_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, st>>>(partial, n_split, npix, inv_T, image);
+size_t unit_order_ints(int n_units) { return (size_t)2 * n_units + kOrderBuckets; }
+
+void launch_unit_order(const int32_t* core_off, const int32_t* soft_off, int G, int n_tiles, int tile, int n_split,
+                       int n_units, int32_t* order, int32_t* scratch, cudaStream_t st) {
+  if (n_units <= 0) return;
+  const int tpu = tile == 8 ? UnitMap<8, 8>::kTilesPerUnit : UnitMap<16, 16>::kTilesPerUnit;
+  const int n_patches = (n_tiles + tpu - 1) / tpu;
+  int32_t* bucket = scratch;
+  int32_t* hist = scratch + n_units;
+  cudaMemsetAsync(hist, 0, sizeof(int32_t) * kOrderBuckets, st);
+  const unsigned blocks = (unsigned)((n_units + 255) / 256);
+  unit_hist_kernel<<<blocks, 256, 0, st>>>(core_off, soft_off, G, n_tiles, tpu, n_patches, n_split, n_units, bucket,
+                                           hist);
+  unit_scan_kernel<<<1, 32, 0, st>>>(hist);
+  unit_scatter_kernel<<<blocks, 256, 0, st>>>(bucket, n_units, hist, order);
 }
 
 void launch_count(const TriRec* recs, int F, const Group* groups, int G, int W, int H, float r,

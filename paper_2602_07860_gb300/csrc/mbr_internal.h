@@ -26,7 +26,11 @@ void launch_scan(const int32_t* in, int n, int32_t* out, int32_t* temp, cudaStre
 void launch_raster_fwd(const WorkQueue& Q, int tile, int spt, int kind, int grid, cudaStream_t st);
 int persistent_grid_fwd(int num_sms, int tile, int spt, int kind);
 int persistent_grid_bwd(int num_sms, int tile, int spt, int kind);
-void launch_finalize(const float4* partial, int n_split, size_t npix, float inv_T, float4* image, cudaStream_t st);
+// LPT visiting order of a render's units (patch x group split) from its bin offsets; scratch holds
+// unit_order_ints(n_units) ints
+size_t unit_order_ints(int n_units);
+void launch_unit_order(const int32_t* core_off, const int32_t* soft_off, int G, int n_tiles, int tile, int n_split,
+                       int n_units, int32_t* order, int32_t* scratch, cudaStream_t st);
 void launch_count(const TriRec* recs, int F, const Group* groups, int G, int W, int H, float r,
                   unsigned long long* out, cudaStream_t st);
 

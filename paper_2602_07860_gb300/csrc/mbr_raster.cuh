@@ -50,11 +50,12 @@ struct RasterParams {
   float r, r2, inv_delta, delta;
   float lx, ly, lz, ka, kd;
   float inv_T;
-  float4* out;               // image (n_split == 1, scaled) or partial sums [n_split][H*W]
+  float4* out;               // image: stored (n_split == 1) or accumulated with atomics (zeroed first)
   int32_t dbg_k;             // sub-frame whose winners are written to dbg_ids (or -1)
   int32_t* dbg_ids;
   int32_t moving;            // 1: fast solver (segment records), 0: plain solver (static records)
-  int32_t work;              // work items of this render: tiles * n_split * warp blocks per tile
+  int32_t work;              // units of this render: patches * n_split
+  const int32_t* order;      // [work] unit visiting order (largest estimated work first), or null
   // adjoint only
   const float4* dl_dimage;   // [H*W]
   float4* g_slot;            // [slots][V][2]: (dx, dy, dnx, dny), (dnz, 0, 0, 0) of the slot states
@@ -362,60 +363,123 @@ __device__ __forceinline__ void for_soft_terms(const Group* grp, int n, uint32_t
   });
 }
 
-// Persistent scheduling: the CTAs of a grid of (SM count x resident CTAs) take work units from an
-// atomic counter until none is left.  A unit is one split of the sample groups over a 256-pixel
-// patch of one render (one 16 x 16 tile, or four 8 x 8 tiles); the CTA's 8 warps take one 8 x 4
-// block each, so a tile's records are shared in the SM's L1.  Renders are ordered by the host
-// (largest first); item_off[i] is the first unit of render i.
+// Persistent scheduling.  A unit is one split of the sample groups (a contiguous range of
+// groups) over a 256-pixel patch of one render (one 16 x 16 tile, or four 8 x 8 tiles); it has
+// 8 warp blocks of 8 x 4 pixels.  The CTAs of a grid of (SM count x resident CTAs) take units
+// from a global atomic counter; inside a CTA the 8 blocks of a unit go to whichever warps ask
+// next, through a CTA-local ticket ring in shared memory, so a warp never waits for the slow
+// blocks of its unit and the blocks of one unit still share the SM's L1.  Each render's units
+// are visited in its cost order (largest estimated work first, from the bin sizes), so the
+// expensive silhouette patches do not form a tail.  Renders are ordered by the host (largest
+// first); item_off[i] is the first unit of render i.
 struct WorkQueue {
   const RasterParams* items;  // [n_items]
-  const int32_t* item_off;    // [n_items + 1]
-  int32_t n_items, n_work;
+  const int32_t* item_off;    // [n_items + 1] unit offsets
+  int32_t n_items, n_work;    // n_work = total units
   int32_t* counter;           // zeroed before the launch
+  int32_t* status;            // device status word (kStatusSpin if a wait gave up)
 };
+
+constexpr int kBlocksPerUnit = 8;
+constexpr int kRing = 4;              // units a CTA may have in flight
+constexpr int kSpinLimit = 1 << 22;   // bounded waits (x ~64 ns): far beyond any real wait
 
 template <int TW, int TH>
 struct UnitMap {
   static constexpr int kBlocks = PixelMap<TW, TH>::kBlocks;       // warp blocks per tile
-  static constexpr int kTilesPerUnit = 8 / kBlocks;                // tiles per 8-warp unit
-  static_assert(kBlocks * kTilesPerUnit == 8, "a unit must be 8 warp blocks");
-  static __host__ __device__ __forceinline__ int units(int n_tiles, int n_split) {
-    return n_split * ((n_tiles + kTilesPerUnit - 1) / kTilesPerUnit);
+  static constexpr int kTilesPerUnit = kBlocksPerUnit / kBlocks;  // tiles per unit (patch)
+  static_assert(kBlocks * kTilesPerUnit == kBlocksPerUnit, "a unit must be 8 warp blocks");
+  static __host__ __device__ __forceinline__ int patches(int n_tiles) {
+    return (n_tiles + kTilesPerUnit - 1) / kTilesPerUnit;
   }
 };
 
-// Claim the next unit for this CTA (block-collective).  On success the CTA's render parameters
-// are in sp and (tile, split, wb) is this warp's part of the unit (tile may be past the last
-// tile for a ragged unit: the caller skips it).
+// CTA-local hand-out of the blocks of globally claimed units (shared memory).  Ticket t is block
+// t % 8 of the CTA's local unit L = t / 8; the warp holding block 0 claims the global unit and
+// publishes it in ring slot L % kRing; a slot is reused only after its 8 tickets have read it.
+struct CtaQueue {
+  int tick;
+  int unit[kRing];
+  int ready[kRing];  // L + 1 once unit[] holds local unit L
+  int used[kRing];   // tickets that have read the slot (cumulative)
+  __device__ __forceinline__ void init() {
+    if (threadIdx.x == 0) {
+      tick = 0;
+      for (int q = 0; q < kRing; ++q) unit[q] = ready[q] = used[q] = 0;
+    }
+    __syncthreads();
+  }
+};
+
+__device__ __forceinline__ int ld_volatile(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+
+// Next block for this warp (warp-collective).  On success (tile, split, wb) is the block and P
+// (this warp's shared copy of the render parameters) is current.  Returns false when the queue
+// is exhausted or a bounded wait gave up (status word set; the caller exits).
 template <int TW, int TH>
-__device__ __forceinline__ bool next_unit(const WorkQueue& Q, RasterParams& sp, int* s_claim, int& cur_item,
+__device__ __forceinline__ bool warp_next(const WorkQueue& Q, CtaQueue& cq, RasterParams& P, int& cur_item,
                                           int& tile, int& split, int& wb) {
-  __syncthreads();  // every warp is done with the previous unit (sp, s_claim)
-  if (threadIdx.x == 0) s_claim[0] = atomicAdd(Q.counter, 1);
-  __syncthreads();
-  const int w = s_claim[0];
-  if (w >= Q.n_work) return false;
+  const int lane = threadIdx.x & 31;
+  int g = 0, b = 0;
+  if (lane == 0) {
+    const int t = atomicAdd(&cq.tick, 1);
+    const int L = t / kBlocksPerUnit, slot = L % kRing;
+    b = t % kBlocksPerUnit;
+    bool ok = true;
+    if (b == 0) {
+      int it = 0;
+      const int need = kBlocksPerUnit * (L / kRing);  // readers of the slot's previous units
+      while (ld_volatile(&cq.used[slot]) < need) {
+        if (++it > kSpinLimit) { ok = false; break; }
+        __nanosleep(64);
+      }
+      __threadfence_block();
+      if (ok) {
+        cq.unit[slot] = atomicAdd(Q.counter, 1);
+        __threadfence_block();
+        *reinterpret_cast<volatile int*>(&cq.ready[slot]) = L + 1;
+      }
+    } else {
+      int it = 0;
+      while (ld_volatile(&cq.ready[slot]) != L + 1) {
+        if (++it > kSpinLimit) { ok = false; break; }
+        __nanosleep(64);
+      }
+      __threadfence_block();
+    }
+    if (ok) {
+      g = ld_volatile(&cq.unit[slot]);
+      atomicAdd(&cq.used[slot], 1);
+    } else {
+      atomicOr(Q.status, kStatusSpin);
+      g = Q.n_work;
+    }
+  }
+  g = __shfl_sync(0xffffffffu, g, 0);
+  b = __shfl_sync(0xffffffffu, b, 0);
+  if (g >= Q.n_work) return false;
   int lo = 0, hi = Q.n_items - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(Q.item_off + mid) <= w) lo = mid;
+    if (__ldg(Q.item_off + mid) <= g) lo = mid;
     else hi = mid - 1;
   }
-  if (lo != cur_item) {  // uniform across the CTA
+  if (lo != cur_item) {  // uniform across the warp
+    __syncwarp();
     const int* src = reinterpret_cast<const int*>(Q.items + lo);
-    int* dst = reinterpret_cast<int*>(&sp);
-    for (int q = threadIdx.x; q < (int)(sizeof(RasterParams) / 4); q += blockDim.x) dst[q] = __ldg(src + q);
-    __syncthreads();
+    int* dst = reinterpret_cast<int*>(&P);
+    for (int q = lane; q < (int)(sizeof(RasterParams) / 4); q += 32) dst[q] = __ldg(src + q);
+    __syncwarp();
     cur_item = lo;
   }
   using M = UnitMap<TW, TH>;
-  const int n_tiles = sp.tiles_x * sp.tiles_y;
-  const int per_split = (n_tiles + M::kTilesPerUnit - 1) / M::kTilesPerUnit;
-  const int r = w - __ldg(Q.item_off + lo);
-  const int warp = threadIdx.x >> 5;
-  split = r / per_split;
-  tile = (r % per_split) * M::kTilesPerUnit + warp / M::kBlocks;
-  wb = warp % M::kBlocks;
+  const int n_tiles = P.tiles_x * P.tiles_y;
+  const int n_patches = M::patches(n_tiles);
+  int u = g - __ldg(Q.item_off + lo);
+  if (P.order) u = __ldg(P.order + u);
+  split = u / n_patches;
+  tile = (u - split * n_patches) * M::kTilesPerUnit + b / M::kBlocks;
+  wb = b % M::kBlocks;
   return true;
 }
 
