@@ -183,6 +183,8 @@ def main():
         return float(t.item())
 
     ctx = mbr.Context()
+    ctx_spt = 2  # sub-frames per group of the fast solver (the autotuner's pick for this workload)
+    ctx.set_tuning(16, ctx_spt, 0)
     sc = scenes.config2()
     T, H, W = sc["T"], sc["H"], sc["W"]
     v, f, a = mbr.mesh_tensors(sc)
@@ -222,27 +224,44 @@ def main():
     ms_per_step = total_ms / args.steps
     value = world * n_samples * args.steps / (total_ms / 1e3)
 
-    # ---- roofline of the dominant raster kernel (FP32 ALU bound)
+    # ---- roofline of the dominant raster kernel (FP32 ALU bound); work units counted by the GPU
+    # path itself (mbr_count_work), flops per unit from the formulas (roofline.py)
     fwd_ms = st["raster_fwd_ms"] / max(1, st["raster_fwd_count"])
     bwd_ms = st["raster_bwd_ms"] / max(1, st["raster_bwd_count"])
-    n_cand = ctx.count_candidates(v, f, a, mo, ca, T, H, W, "fast")
     num_sms = torch.cuda.get_device_properties(local).multi_processor_count
     peak = roofline.fp32_peak_tflops(num_sms)
-    if bwd_ms >= fwd_ms:
-        kern, kms, flops = "raster_bwd_kernel", bwd_ms, roofline.bwd_flops(n_cand, n_samples)
-    else:
-        kern, kms, flops = "raster_fwd_kernel", fwd_ms, roofline.fwd_flops(n_cand, n_samples)
-    achieved = flops / (kms / 1e3) / 1e12
+
+    def kernel_roofs(solver, f_ms, b_ms):
+        d = ctx.count_work(v, f, a, mo, ca, T, H, W, solver, detail=True)
+        n_box, n_soft, n_cov = d["n_box"], d["n_soft"], d["n_cov"]
+        fw = roofline.fwd_flops(solver, n_box, n_soft, n_cov, n_samples)
+        bw = roofline.bwd_flops(solver, n_box, n_soft, n_cov, n_samples)
+        units = dict(d, n_sample=n_samples)
+        return fw, bw, units, fw / (f_ms / 1e3) / 1e12, bw / (b_ms / 1e3) / 1e12
+
+    fwf, bwf, units, fwd_tf, bwd_tf = kernel_roofs("fast", fwd_ms, bwd_ms)
+    backward_dominant = bwd_ms >= fwd_ms
+    kern = "raster_bwd_persistent" if backward_dominant else "raster_fwd_persistent"
+    achieved = bwd_tf if backward_dominant else fwd_tf
     roof = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": None,
-            "peak_note": f"{num_sms} SMs x 128 FP32 lanes x 2 x 2070 MHz (derived, not measured)",
-            "work": f"N_cand={n_cand} x {roofline.FLOPS_PER_CAND} + samples={n_samples} x "
-                    f"{roofline.FLOPS_PER_SAMPLE if kern == 'raster_fwd_kernel' else roofline.FLOPS_PER_SAMPLE + roofline.FLOPS_PER_SAMPLE_BWD} flops",
-            "kernel_ms": kms, "raster_fwd_ms": fwd_ms, "raster_bwd_ms": bwd_ms}
+            "peak_note": f"{num_sms} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived from unit counts "
+                         "and the maximum SM clock; no measured FP32 peak)",
+            "work": roofline.describe("fast", units["n_box"], units["n_soft"], units["n_cov"], n_samples,
+                                      backward_dominant),
+            "flops_per_launch": bwf if backward_dominant else fwf,
+            "kernel_ms": bwd_ms if backward_dominant else fwd_ms, "raster_fwd_ms": fwd_ms, "raster_bwd_ms": bwd_ms,
+            "fwd_frac": fwd_tf / peak, "bwd_frac": bwd_tf / peak, "units": units}
 
     # ---- plain per-sub-frame solver and forward-only numbers on the same GPU
     k2 = max(3, args.steps // 2)
+    ctx.set_profiling(True)
     plain_fb = max_over_ranks(timed("plain", True, k2, 2)) / k2
+    pst = ctx.stats()
+    ctx.set_profiling(False)
+    p_fwd = pst["raster_fwd_ms"] / max(1, pst["raster_fwd_count"])
+    p_bwd = pst["raster_bwd_ms"] / max(1, pst["raster_bwd_count"])
+    _, _, p_units, p_fwd_tf, p_bwd_tf = kernel_roofs("plain", p_fwd, p_bwd)
     fast_f = max_over_ranks(timed("fast", False, k2, 2)) / k2
     plain_f = max_over_ranks(timed("plain", False, k2, 2)) / k2
     extras = {
@@ -253,6 +272,9 @@ def main():
         "plain_fwd_ms": plain_f, "plain_fwd_samples_per_s": world * n_samples / (plain_f / 1e3),
         "speedup_fast_over_plain_fwdbwd": plain_fb / ms_per_step,
         "speedup_fast_over_plain_fwd": plain_f / fast_f,
+        "plain_raster_fwd_ms": p_fwd, "plain_raster_bwd_ms": p_bwd,
+        "plain_fwd_frac": p_fwd_tf / peak, "plain_bwd_frac": p_bwd_tf / peak, "plain_units": p_units,
+        "tuning": {"tile": 16, "spt": ctx_spt, "splits": "auto"},
         "paper_context": "paper: up to 4.57x fwd+grad speedup vs SoftRas on one RTX 4090 (different workload)",
     }
 

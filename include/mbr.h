@@ -131,7 +131,7 @@ int mbr_render_blur_batch(mbr_ctx* ctx, int32_t n, const mbr_item* items, int32_
                           void* cuda_stream);
 
 /* Autotuner: times mbr_render_blur_batch on these items for every candidate tile shape (16x16,
- * 8x8 pixels) and, when a fast-solver item is present, sub-frames per thread (4, 8, 16), keeps
+ * 8x8 pixels) and, when a fast-solver item is present, sub-frames per group (1, 2, 4, 8), keeps
  * the fastest on the context (as mbr_set_tuning would) and reports it.  Any out pointer may be
  * NULL.  The items are rendered several times (their outputs are overwritten). */
 int mbr_autotune(mbr_ctx* ctx, int32_t n, const mbr_item* items, int32_t with_backward,
@@ -151,8 +151,25 @@ int mbr_count_candidates(mbr_ctx* ctx, const mbr_mesh* mesh, const mbr_motion* m
                          const mbr_camera* camera, int32_t T, int32_t H, int32_t W,
                          int32_t solver, int64_t* out, void* cuda_stream);
 
+/* Measurement hook: the units of the raster's work model for one forward render, counted by the
+ * GPU path's own (FP32) decisions.  out[0] = N_cand (as mbr_count_candidates); out[1] = N_soft,
+ * the soft-coverage factors 1 - exp(-d/delta) of uncovered samples that enter the products of
+ * Eqs. probability-function .. back (those with exp(-d/delta) > 2^-25; smaller ones leave the
+ * single-precision product unchanged); out[2] = covered samples.  Efficiency of the raster's
+ * passes: out[3] = soft distance evaluations (per pixel and sample), out[4] = warp steps over
+ * live soft candidates, out[5] = coverage tests (per pixel and sample), out[6] = warp steps over
+ * live coverage candidates; out[7] = N_box, the triples whose undilated bounding box contains
+ * the pixel centre (the coverage tests a binned rasteriser cannot avoid).  It runs the forward raster in its counting build
+ * (16 x 16 tiles, slower than mbr_render_blur) and, if image is not NULL, writes the image as
+ * mbr_render_blur does.  out is a HOST int64[8]; the call synchronises the stream.  Errors as
+ * mbr_render_blur. */
+int mbr_count_work(mbr_ctx* ctx, const mbr_mesh* mesh, const mbr_motion* motion, const mbr_camera* camera,
+                   int32_t T, int32_t H, int32_t W, int32_t solver, float* image, int64_t* out,
+                   void* cuda_stream);
+
 /* Tuning knobs (autotuner): tile edge in pixels (8 or 16), sub-frames per thread for the fast
- * solver (1..16), and the number of sub-frame groups split across CTAs (0 = automatic). */
+ * solver (1..16, default 2), and the number of sub-frame group splits of the raster work units
+ * (0 = automatic: about 64 units per SM). */
 int mbr_set_tuning(mbr_ctx* ctx, int32_t tile, int32_t spt, int32_t splits);
 
 /* Measurement counters of a context. */

@@ -23,7 +23,7 @@ from .build import build, library_path
 
 MODES = {"exact": 0, "linear": 1, "fast": 2}
 SOFT_ALL = 1
-CNT_CAND, CNT_COVERED, CNT_AMBIG, CNT_HASH, CNT_SOFT = 0, 1, 2, 3, 4
+CNT_CAND, CNT_COVERED, CNT_AMBIG, CNT_HASH, CNT_SOFT, CNT_SOFT32 = 0, 1, 2, 3, 4, 5
 AMB_COVER, AMB_DEPTH, AMB_DEGEN, AMB_REGION, AMB_CLAMP, AMB_LAMBERT, AMB_COND = 1, 2, 4, 8, 16, 32, 64
 AMB_IMAGE = AMB_COVER | AMB_DEPTH | AMB_DEGEN | AMB_REGION  # flags that can change a pixel value
 

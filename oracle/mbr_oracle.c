@@ -36,6 +36,7 @@ enum { AMB_COVER = 1, AMB_DEPTH = 2, AMB_DEGEN = 4, AMB_REGION = 8, AMB_CLAMP = 
  * estimate exceeds 1e-4 (a tenth of the gradient tolerance). */
 #define EPS32 5.96e-8
 #define COND_LIMIT 1e-4
+#define SOFT32_MIN 2.98023223876953125e-8  /* 2^-25: 1 - A rounds to 1 in single precision below */
 #define ETA_CLAMP 1e-5     /* gradient-only flag: closest-feature switch within this relative d^2 */
 #define ETA_LAMBERT 1e-5   /* gradient-only flag: |n.l| below this (Lambert clamp switches)     */
 
@@ -386,7 +387,7 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
     double l = sqrt(Ld[0] * Ld[0] + Ld[1] * Ld[1] + Ld[2] * Ld[2]);
     for (int i = 0; i < 3; ++i) Ld[i] /= l;
   }
-  int64_t n_cand = 0, n_cov = 0, n_amb = 0, n_soft = 0;
+  int64_t n_cand = 0, n_cov = 0, n_amb = 0, n_soft = 0, n_soft32 = 0;
   uint64_t hash = 1469598103934665603ULL;
 
   double* nrm = (double*)malloc(sizeof(double) * 3 * V);
@@ -400,6 +401,7 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
   int32_t* bestf = (int32_t*)malloc(sizeof(int32_t) * (npix + 1));
   uint8_t* amb = (uint8_t*)malloc(npix + 1);
   uint8_t* samb = (uint8_t*)malloc(npix + 1); /* flags of soft terms: count only if uncovered */
+  int32_t* nsoft32 = (int32_t*)malloc(sizeof(int32_t) * (npix + 1)); /* terms above 2^-25, per sample */
   double* gcur = backward ? (double*)calloc(5 * (size_t)V, sizeof(double)) : NULL;
   double* gslot = backward ? (double*)calloc(5 * (size_t)V * (S + 1), sizeof(double)) : NULL;
   double* gnb = backward ? (double*)calloc(3 * (size_t)V, sizeof(double)) : NULL;
@@ -442,6 +444,7 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
       prod[p] = 1.0;
       amb[p] = 0;
       samb[p] = 0;
+      nsoft32[p] = 0;
     }
     L.n = 0;
 
@@ -580,6 +583,7 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
               double fv = -expm1(-d / s->delta);
               prod[p] *= fv;
               ++n_soft;
+              if (A > SOFT32_MIN) ++nsoft32[p];
               if (backward) {
                 soft_entry se = {(int32_t)p, f, fv, A, d};
                 if (!push_entry(&L, se)) goto fail;
@@ -600,6 +604,7 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
       if (winners) winners[(size_t)k * npix + p] = f;
       if (ambig) ambig[(size_t)k * npix + p] = amb[p];
       hash = fnv(hash, (int64_t)k * 1000003 + (int64_t)p * 31 + f);
+      if (f < 0) n_soft32 += nsoft32[p];
       if (f >= 0) {
         ++n_cov;
         const int32_t* id = s->faces + 3 * f;
@@ -794,14 +799,15 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
     cnt[ORC_CNT_AMBIG] = n_amb;
     cnt[ORC_CNT_HASH] = (int64_t)hash;
     cnt[ORC_CNT_SOFT] = n_soft;
+    cnt[ORC_CNT_SOFT32] = n_soft32;
   }
   free(nrm); free(cur); free(key0); free(key1); free(bestk); free(secondk); free(bestw);
-  free(prod); free(bestf); free(amb); free(samb); free(gcur); free(gslot); free(gnb); free(pstart);
+  free(prod); free(bestf); free(amb); free(samb); free(nsoft32); free(gcur); free(gslot); free(gnb); free(pstart);
   free(sorted); free(L.e);
   return 0;
 fail:
   free(nrm); free(cur); free(key0); free(key1); free(bestk); free(secondk); free(bestw);
-  free(prod); free(bestf); free(amb); free(samb); free(gcur); free(gslot); free(gnb); free(pstart);
+  free(prod); free(bestf); free(amb); free(samb); free(nsoft32); free(gcur); free(gslot); free(gnb); free(pstart);
   free(sorted); free(L.e);
   return -1;
 }

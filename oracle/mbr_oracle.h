@@ -49,6 +49,8 @@ enum {
   ORC_CNT_AMBIG = 2,      /* samples flagged ambiguous for FP32 comparison                        */
   ORC_CNT_HASH = 3,       /* 64-bit hash of every discrete decision                               */
   ORC_CNT_SOFT = 4,       /* soft-coverage terms that entered a product                          */
+  ORC_CNT_SOFT32 = 5,     /* of those, terms of uncovered samples with exp(-d/delta) > 2^-25: the
+                             ones that can change a single-precision product (work measure)      */
   ORC_CNT_N = 8
 };
 

@@ -16,7 +16,7 @@ MBR_TIME_PAPER, MBR_TIME_MIDPOINT = 0, 1
 SOLVERS = {"plain": MBR_PLAIN, "fast": MBR_FAST}
 
 EXPORTS = ["mbr_create", "mbr_destroy", "mbr_render_blur", "mbr_render_blur_backward", "mbr_render_blur_batch",
-           "mbr_debug_winners", "mbr_count_candidates", "mbr_set_tuning", "mbr_set_profiling", "mbr_get_stats",
+           "mbr_debug_winners", "mbr_count_candidates", "mbr_count_work", "mbr_set_tuning", "mbr_set_profiling", "mbr_get_stats",
            "mbr_render_blur_noalloc", "mbr_autotune", "mbr_last_error"]
 
 
@@ -84,6 +84,8 @@ def load(build_if_missing=True):
     L.mbr_debug_winners.restype = c_int32
     L.mbr_count_candidates.argtypes = common + [P(c_int64), c_void_p]
     L.mbr_count_candidates.restype = c_int32
+    L.mbr_count_work.argtypes = common + [c_void_p, P(c_int64), c_void_p]
+    L.mbr_count_work.restype = c_int32
     L.mbr_render_blur_batch.argtypes = [c_void_p, c_int32, P(MbrItem), c_int32, c_void_p]
     L.mbr_render_blur_batch.restype = c_int32
     L.mbr_autotune.argtypes = [c_void_p, c_int32, P(MbrItem), c_int32, P(c_int32), P(c_int32), P(c_float), c_void_p]

@@ -41,7 +41,7 @@ struct mbr_ctx {
   int num_sms = 1;
   std::string err;
   // tuning
-  int tile = 16, spt = 8, splits = 0;
+  int tile = 16, spt = 2, splits = 0;
   // scratch
   DevBuf nacc, pos, nrm, recs, tables, partial, gslot, galb, gm, cnt64, status, order;
   BinSet core, soft;  // undilated bins (coverage) and r_soft-dilated bins (soft coverage)
@@ -723,6 +723,50 @@ int mbr_count_candidates(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* mot
   return MBR_OK;
 }
 
+int mbr_count_work(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mbr_camera* cam, int32_t T,
+                   int32_t H, int32_t W, int32_t solver, float* image, int64_t* out, void* stream) {
+  if (!c) return MBR_ERR_ARG;
+  c->err.clear();
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = validate(c, mesh, motion, cam, T, H, W, solver);
+  if (rc) return rc;
+  if (!out) return fail(c, MBR_ERR_ARG, "null out");
+  const int saved_tile = c->tile;
+  c->tile = 16;  // the counting build exists for 16 x 16 tiles
+  Prepared pp;
+  rc = prepare(c, mesh, motion, cam, T, H, W, solver, st, true, pp);
+  c->tile = saved_tile;
+  if (rc) return rc;
+  RasterParams P = raster_params(c, ctx_bufs(c), mesh, cam, T, H, W, pp);
+  const size_t npix = (size_t)H * W;
+  if (!image) {
+    if ((rc = ensure(c, c->partial, sizeof(float4) * npix, st))) return rc;
+    P.out = (float4*)c->partial.p;
+  } else {
+    P.out = (float4*)image;
+  }
+  if (pp.n_split > 1) CUDA_TRY(c, cudaMemsetAsync(P.out, 0, sizeof(float4) * npix, st));
+  if ((rc = ensure(c, c->cnt64, sizeof(unsigned long long) * 8, st))) return rc;
+  unsigned long long* d_cnt = (unsigned long long*)c->cnt64.p;
+  CUDA_TRY(c, cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * 8, st));
+  P.counts = d_cnt + 1;  // [1..6]
+  const float r_count = (float)std::sqrt((double)cam->delta * std::log(1e12));
+  launch_count((const TriRec*)c->recs.p, mesh->F, pp.d_groups, pp.G, W, H, r_count, d_cnt, st);
+  launch_count((const TriRec*)c->recs.p, mesh->F, pp.d_groups, pp.G, W, H, 0.f, d_cnt + 7, st);  // N_box
+  WorkQueue Q;
+  if ((rc = upload_queue(c, &P, 1, st, Q))) return rc;
+  const int kind = pp.moving ? 1 : 0;
+  launch_raster_count(Q, pp.spt, kind,
+                      std::max(1, std::min(persistent_grid_fwd(c->num_sms, 16, pp.spt, kind), Q.n_work)), st);
+  CUDA_TRY(c, cudaGetLastError());
+  c->stats.launches += 2;
+  unsigned long long h[8];
+  CUDA_TRY(c, cudaMemcpyAsync(h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  for (int q = 0; q < 8; ++q) out[q] = (int64_t)h[q];
+  return MBR_OK;
+}
+
 int mbr_autotune(mbr_ctx* c, int32_t n, const mbr_item* items, int32_t with_backward, int32_t* best_tile,
                  int32_t* best_spt, float* best_ms, void* stream) {
   if (!c) return MBR_ERR_ARG;
@@ -732,8 +776,8 @@ int mbr_autotune(mbr_ctx* c, int32_t n, const mbr_item* items, int32_t with_back
   bool any_fast = false;
   for (int i = 0; i < n; ++i) any_fast |= items[i].solver == MBR_FAST;
   const int tiles[2] = {16, 8};
-  const int spts_fast[3] = {4, 8, 16};
-  const int n_spt = any_fast ? 3 : 1;
+  const int spts_fast[4] = {1, 2, 4, 8};
+  const int n_spt = any_fast ? 4 : 1;
   const int saved_tile = c->tile, saved_spt = c->spt, saved_splits = c->splits;
   cudaEvent_t e0, e1;
   CUDA_TRY(c, cudaEventCreate(&e0));

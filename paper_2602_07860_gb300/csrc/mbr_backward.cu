@@ -60,6 +60,7 @@ struct BwdSoftProduct {
   uint32_t nzero;  // 2 bits per sample: vanishing factors 0, 1, or 2 = "two or more"
   float inv_delta;
   __device__ __forceinline__ void begin() {}
+  __device__ __forceinline__ void eval() {}
   template <typename PS>
   __device__ __forceinline__ void term(const float4*, const PS&, const EdgeVals&, const SoftGeom& sg, int i, float,
                                        int) {
@@ -94,6 +95,7 @@ struct BwdSoftGrad {
     for (int q = 0; q < 3; ++q) gax[q] = gay[q] = gbx[q] = gby[q] = 0.f;
     any = false;
   }
+  __device__ __forceinline__ void eval() {}
 
   __device__ __forceinline__ void term(const float4* r, const PixelSetup<MOVING>& ps, const EdgeVals& e,
                                        const SoftGeom& sg, int i, float tau, int X) {

@@ -265,11 +265,17 @@ __global__ void scan_apply_kernel(const int32_t* __restrict__ in, int n, const i
 }
 
 // ---------------------------------------------------------------- a4-a8: forward raster
-template <int SPT>
+template <int SPT, bool COUNT>
 struct FwdSoftProduct {
   float prod[SPT];
   float inv_delta;
-  __device__ __forceinline__ void begin() {}
+  uint32_t n_terms, n_eval, n_iter;  // COUNT: terms in the product, distance evaluations, warp steps
+  __device__ __forceinline__ void begin() {
+    if (COUNT && (threadIdx.x & 31) == 0) ++n_iter;
+  }
+  __device__ __forceinline__ void eval() {
+    if (COUNT) ++n_eval;
+  }
   template <typename PS>
   __device__ __forceinline__ void term(const float4*, const PS&, const EdgeVals&, const SoftGeom& sg, int i, float,
                                        int) {
@@ -277,12 +283,14 @@ struct FwdSoftProduct {
 #pragma unroll
     for (int q = 0; q < SPT; ++q)
       if (q == i) prod[q] *= f;
+    if (COUNT) ++n_terms;
   }
   __device__ __forceinline__ void end(int) {}
 };
 
 // One work item: the 8 x 4 pixel block wb of tile `tile`, sample groups of split `split`.
-template <int TW, int TH, int SPT, bool MOVING>
+// COUNT (measurement build only): also count soft terms and covered samples into P.counts.
+template <int TW, int TH, int SPT, bool MOVING, bool COUNT = false>
 __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile, int split, int wb) {
   const int n_tiles = P.tiles_x * P.tiles_y;
   const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
@@ -295,6 +303,8 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
   const int g_begin = (int)((long long)P.G * split / P.n_split);
   const int g_end = (int)((long long)P.G * (split + 1) / P.n_split);
   float acc_r = 0.f, acc_g = 0.f, acc_b = 0.f, acc_a = 0.f;
+  uint32_t n_soft = 0, n_cov = 0, n_seval = 0, n_siter = 0;
+  uint32_t ccnt[2] = {0u, 0u};
 
   for (int g = g_begin; g < g_end; ++g) {
     const Group* grp = P.groups + g;
@@ -308,18 +318,27 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
     int cb, ce, sb, se;
     P.core.range(bi, cb, ce);
     P.soft.range(bi, sb, se);
-    pass_winners<SPT, MOVING>(grp, n, recs_set, P.core.faces, cb, ce, tb, in_img, u, v, bestk, bestf);
+    pass_winners<SPT, MOVING, COUNT>(grp, n, recs_set, P.core.faces, cb, ce, tb, in_img, u, v, bestk, bestf, ccnt);
     uint32_t uncov = 0;
 #pragma unroll
     for (int i = 0; i < SPT; ++i)
       if (i < n && bestf[i] < 0) uncov |= 1u << i;
-    FwdSoftProduct<SPT> soft;
+    FwdSoftProduct<SPT, COUNT> soft;
 #pragma unroll
     for (int i = 0; i < SPT; ++i) soft.prod[i] = 1.f;
     soft.inv_delta = P.inv_delta;
+    soft.n_terms = soft.n_eval = soft.n_iter = 0;
     if (se > sb && __any_sync(0xffffffffu, in_img && uncov != 0))
       for_soft_terms<SPT, MOVING>(grp, n, gr.xbits, recs_set, P.soft.faces, sb, se, tb, in_img, u, v, uncov, P.r,
                                   P.r2, soft);
+    if (COUNT) {
+      n_seval += soft.n_eval;
+      n_siter += soft.n_iter;
+      if (in_img) {
+        n_soft += soft.n_terms;
+        n_cov += (uint32_t)n - (uint32_t)__popc(uncov);
+      }
+    }
 
     // ---- shading of the winners (Eq. fore + Lambert) and temporal accumulation (Sec. 3.3)
     if (in_img) {
@@ -374,6 +393,20 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
     if (P.n_split == 1) P.out[o] = val;
     else atomicAdd(P.out + o, val);  // the image was zeroed; splits add their share of the mean
   }
+  if (COUNT) {
+    // [soft terms, covered samples, soft evaluations, soft warp steps, coverage tests, core warp steps]
+    unsigned long long c[6] = {n_soft, n_cov, n_seval, n_siter, ccnt[0], ccnt[1]};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c[q] += __shfl_xor_sync(0xffffffffu, c[q], o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+      for (int q = 0; q < 6; ++q)
+        if (c[q]) atomicAdd(P.counts + q, c[q]);
+    }
+  }
 }
 
 // Persistent forward raster: KIND 0 = plain solver only, 1 = fast solver only, 2 = mixed batch.
@@ -390,6 +423,23 @@ __global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 4 : 2) raster_
       raster_fwd_block<TW, TH, 1, false>(P, tile, split, wb);
     else
       raster_fwd_block<TW, TH, SPT, true>(P, tile, split, wb);
+  }
+}
+
+// Measurement build of the forward (16 x 16 tiles): the same raster, counting into P.counts.
+template <int SPT, int KIND>
+__global__ void __launch_bounds__(kPersistentThreads, 2) raster_fwd_count(WorkQueue Q) {
+  __shared__ CtaQueue cq;
+  __shared__ RasterParams sp[kPersistentThreads / 32];
+  cq.init();
+  RasterParams& P = sp[threadIdx.x >> 5];
+  int cur = -1, tile = 0, split = 0, wb = 0;
+  while (warp_next<16, 16>(Q, cq, P, cur, tile, split, wb)) {
+    if (tile >= P.tiles_x * P.tiles_y) continue;
+    if (KIND == 0)
+      raster_fwd_block<16, 16, 1, false, true>(P, tile, split, wb);
+    else
+      raster_fwd_block<16, 16, SPT, true, true>(P, tile, split, wb);
   }
 }
 
@@ -587,6 +637,14 @@ void launch_unit_order(const int32_t* core_off, const int32_t* soft_off, int G, 
                                            hist);
   unit_scan_kernel<<<1, 32, 0, st>>>(hist);
   unit_scatter_kernel<<<blocks, 256, 0, st>>>(bucket, n_units, hist, order);
+}
+
+void launch_raster_count(const WorkQueue& Q, int spt, int kind, int grid, cudaStream_t st) {
+  if (Q.n_work <= 0) return;
+  if (kind == 0) raster_fwd_count<1, 0><<<grid, kPersistentThreads, 0, st>>>(Q);
+  else if (spt <= 4) raster_fwd_count<4, 1><<<grid, kPersistentThreads, 0, st>>>(Q);
+  else if (spt <= 8) raster_fwd_count<8, 1><<<grid, kPersistentThreads, 0, st>>>(Q);
+  else raster_fwd_count<16, 1><<<grid, kPersistentThreads, 0, st>>>(Q);
 }
 
 void launch_count(const TriRec* recs, int F, const Group* groups, int G, int W, int H, float r,

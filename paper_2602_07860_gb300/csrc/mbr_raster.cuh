@@ -56,6 +56,7 @@ struct RasterParams {
   int32_t moving;            // 1: fast solver (segment records), 0: plain solver (static records)
   int32_t work;              // units of this render: patches * n_split
   const int32_t* order;      // [work] unit visiting order (largest estimated work first), or null
+  unsigned long long* counts;  // measurement build only: [soft terms, covered samples]
   // adjoint only
   const float4* dl_dimage;   // [H*W]
   float4* g_slot;            // [slots][V][2]: (dx, dy, dnx, dny), (dnz, 0, 0, 0) of the slot states
@@ -294,12 +295,13 @@ __device__ __forceinline__ void for_warp_candidates(const TriRec* recs_set, cons
   }
 }
 
-// pass 1: z-test winners of the group's samples for this pixel (warp-collective)
-template <int SPT, bool MOVING>
+// pass 1: z-test winners of the group's samples for this pixel (warp-collective).  COUNT
+// (measurement build): cnt[0] += coverage tests of this lane, cnt[1] += candidate steps of the warp.
+template <int SPT, bool MOVING, bool COUNT = false>
 __device__ __forceinline__ void pass_winners(const Group* grp, int n, const TriRec* recs_set, const int32_t* list,
                                              int beg, int end,
                                              const TileBox& tb, bool in_img, float u, float v, float (&bestk)[SPT],
-                                             int (&bestf)[SPT]) {
+                                             int (&bestf)[SPT], uint32_t* cnt = nullptr) {
 #pragma unroll
   for (int i = 0; i < SPT; ++i) {
     bestk[i] = -INFINITY;
@@ -307,7 +309,9 @@ __device__ __forceinline__ void pass_winners(const Group* grp, int n, const TriR
   }
   for_warp_candidates<MOVING>(recs_set, list, beg, end, grp, n, tb, kCoreMargin, 0xffffffffu,
                               [&](int face, const TriRec* src, uint32_t mask, const float4& box) {
+    if (COUNT && (threadIdx.x & 31) == 0) ++cnt[1];
     if (!in_img || !in_box(box, u, v)) return;
+    if (COUNT) cnt[0] += __popc(mask & ((1u << n) - 1u));
     float4 r[kRecF4];
     load_record<MOVING>(src, r, true, false);
     const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
@@ -330,7 +334,8 @@ __device__ __forceinline__ void pass_winners(const Group* grp, int n, const TriR
 
 // Visit every soft-coverage term of the uncovered samples (uncov bit i) of this pixel:
 // fn.term(r, ps, e, sg, i, tau, X) for each (candidate, sample) with d <= r^2, bracketed by
-// fn.begin() and fn.end(face) per candidate.  Warp-collective: begin/end run on every lane.
+// fn.begin() and fn.end(face) per candidate; fn.eval() before each distance evaluation.
+// Warp-collective: begin/end run on every lane.
 template <int SPT, bool MOVING, typename Fn>
 __device__ __forceinline__ void for_soft_terms(const Group* grp, int n, uint32_t xbits, const TriRec* recs_set,
                                                const int32_t* list, int beg, int end, const TileBox& tb,
@@ -355,6 +360,7 @@ __device__ __forceinline__ void for_soft_terms(const Group* grp, int n, uint32_t
         const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
         if (fabsf(e.D) <= kDetMin) continue;
         const int X = (xbits >> i) & 1u;
+        fn.eval();
         const SoftGeom sg = soft_geom<MOVING>(r, ps, e, tau, X);
         if (sg.d <= r2) fn.term(r, ps, e, sg, i, tau, X);
       }

@@ -136,7 +136,7 @@ class Context:
         self._raise(self.L.mbr_get_stats(self.h, ctypes.byref(st)))
         return {k: getattr(st, k) for k, _ in st._fields_}
 
-    def set_tuning(self, tile=16, spt=8, splits=0):
+    def set_tuning(self, tile=16, spt=2, splits=0):
         self._raise(self.L.mbr_set_tuning(self.h, int(tile), int(spt), int(splits)))
 
     def render_blur(self, verts, faces, albedo, motion: Motion, camera: Camera, T, H, W, solver="fast", out=None):
@@ -178,6 +178,23 @@ class Context:
         self._raise(self.L.mbr_count_candidates(self.h, ctypes.byref(m), ctypes.byref(mo), ctypes.byref(ca), T, H,
                                                 W, _lib.SOLVERS[solver], ctypes.byref(out), _stream()))
         return out.value
+
+    def count_work(self, verts, faces, albedo, motion, camera, T, H, W, solver="fast", out=None, detail=False):
+        """(N_box, N_soft, N_covered) of one forward render (see include/mbr.h, mbr_count_work);
+        also renders into ``out`` when given.  detail=True returns the dict of all eight counters."""
+        m = self._mesh(verts, faces, albedo)
+        if out is not None:
+            _check(out, torch.float32, (H, W, 4), "image")
+        res = (ctypes.c_int64 * 8)()
+        mo, ca = motion.c(), camera.c()
+        self._raise(self.L.mbr_count_work(self.h, ctypes.byref(m), ctypes.byref(mo), ctypes.byref(ca), T, H, W,
+                                          _lib.SOLVERS[solver],
+                                          ctypes.c_void_p(out.data_ptr() if out is not None else 0), res,
+                                          _stream()))
+        keys = ("n_cand", "n_soft", "n_cov", "soft_evals", "soft_warp_steps", "cov_tests", "cov_warp_steps", "n_box")
+        if detail:
+            return {k: int(res[i]) for i, k in enumerate(keys)}
+        return int(res[7]), int(res[1]), int(res[2])
 
     def _items(self, items, with_backward):
         arr = (MbrItem * len(items))()

@@ -1,39 +1,67 @@
 """Algorithmic work model of the raster kernels (FP32 CUDA-core bound; no tensor-core work).
 
-Units (counted by ``Context.count_candidates`` and from the workload sizes):
-  N_cand   (pixel, sub-frame, triangle) triples whose triangle's bounding box at that sub-frame,
-           dilated by sqrt(delta ln 1e12), contains the pixel centre -- the "barycentric weights
-           for every pixel w.r.t. the relevant triangles, for every frame" of Sec. 3.1.
+Units, counted by the GPU path's own single-precision decisions (``Context.count_work``, pinned
+to the oracle's counters by the tests):
+  N_box    (pixel, sub-frame, triangle) triples whose triangle's (undilated) bounding box at that
+           sub-frame contains the pixel centre: the barycentric solves of Sec. 3.1 that decide
+           coverage, which any binned rasteriser has to do.  (N_cand, the same with boxes dilated
+           by sqrt(delta ln 1e12), about 20x larger here, is what a solver without binning or
+           without the covered/uncovered split evaluates; it is reported, not credited.)
+  N_soft   soft-coverage factors 1 - exp(-d/delta) of uncovered samples that can change the
+           single-precision product of Eq. back (exp(-d/delta) > 2^-25).
+  N_cov    covered samples (shaded by Eq. fore + Lambert).
   N_sample H * W * T pixel x sub-frame samples.
 
-Per-unit flops (an FMA counts 2), fixed once from the formulas, not from compiled code:
-  FLOPS_PER_CAND = 12   barycentric solve + coverage of one triple with the per-(triangle, frame)
-                        part of adj(F) hoisted: three edge functions a u + b v + c, 2 FMA each.
-  FLOPS_PER_SAMPLE = 60 shading of the sample's winner: w = N / D (1 div + 3 mul), albedo and
-                        normal interpolation (18 FMA), normalisation (3 FMA + rsqrt + 3 mul),
-                        n.l (3 FMA), Lambert and accumulation (~8).
-  FLOPS_PER_SAMPLE_BWD = 110  adjoint of the shading (~70) and of w = N / D through the edge
-                        functions to the vertex positions (~40).
-The soft-coverage term (about 45 flops + exp per uncovered triple within the soft radius) is not
-counted, so the model is a lower bound of the useful work.
+Per-unit flops (an FMA counts 2, a MUFU op 1), fixed once from the formulas, not from compiled
+code.  "plain" is the per-sub-frame solve, "fast" the quadratic-rational solver of
+Eq. time-dependent2 and the keyframe closest point of Eqs. euc-dist-approx-1..3:
+  CAND    coverage test of one N_box triple.  plain: q0 = p - v0 (2), N1, N2 = cross products with
+          the hoisted edges (6), N0 = D - N1 - N2 (2), sign tests (2) = 12.  fast: the three
+          quadratics N1(tau), N2(tau), D(tau) by Horner from the per-(pixel, segment)
+          coefficients (12), N0 (2), sign tests (2) = 16.
+  SOFT    one soft factor.  plain: closest point of the triangle by three clamped edge
+          projections (3 x 13 = 39), exponent argument, exp, 1 - e, product (4), q0 (2) = 45.
+          fast: w(tau) = N / D (Horner 12, rcp + 2 mul 3), p' = F(X) w (6), closest point in
+          F(X) (39), F(tau) w* - p with the lerped edges (20), d (3), exp and product (4) = 87.
+  COV     shading of a covered sample: w = N / D (4), albedo (18), normal (18; fast also lerps
+          the keyframe normals, not counted), normalisation (10), n.l and Lambert (8),
+          accumulation (2) = 60.
+  SAMPLE  alpha accumulation of any sample (4).
+Adjoint (the forward quantities are recomputed, not stored):
+  SOFT_BWD  the soft product pass (SOFT) plus the gradient pass (SOFT again and the derivative
+            of d through the closest point to the vertex coordinates: plain 30, fast 90) --
+            plain 120, fast 264.
+  COV_BWD   recomputed shading (60) plus its adjoint through w = N / D and the edge functions to
+            the vertex coordinates, normals and albedo (110) = 170.
+The z-test of covering candidates and the binning are not counted, so the model is a lower bound
+of the arithmetic the method needs.
 
 Peak: 152 SMs x 128 FP32 lanes x 2 flops x 2.070 GHz (maximum SM clock) = 80.6 TFLOP/s.
 """
 
-FLOPS_PER_CAND = 12
-FLOPS_PER_SAMPLE = 60
-FLOPS_PER_SAMPLE_BWD = 110
+FLOPS = {
+    "plain": dict(cand=12, soft=45, cov=60, sample=4, soft_bwd=120, cov_bwd=170),
+    "fast": dict(cand=16, soft=87, cov=60, sample=4, soft_bwd=264, cov_bwd=170),
+}
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 
 
-def fwd_flops(n_cand, n_sample):
-    return FLOPS_PER_CAND * n_cand + FLOPS_PER_SAMPLE * n_sample
+def fwd_flops(solver, n_box, n_soft, n_cov, n_sample):
+    k = FLOPS[solver]
+    return k["cand"] * n_box + k["soft"] * n_soft + k["cov"] * n_cov + k["sample"] * n_sample
 
 
-def bwd_flops(n_cand, n_sample):
-    # the adjoint recomputes coverage and shading, then back-propagates per sample
-    return FLOPS_PER_CAND * n_cand + (FLOPS_PER_SAMPLE + FLOPS_PER_SAMPLE_BWD) * n_sample
+def bwd_flops(solver, n_box, n_soft, n_cov, n_sample):
+    k = FLOPS[solver]
+    return k["cand"] * n_box + k["soft_bwd"] * n_soft + k["cov_bwd"] * n_cov + k["sample"] * n_sample
+
+
+def describe(solver, n_box, n_soft, n_cov, n_sample, backward):
+    k = FLOPS[solver]
+    s, c = ("soft_bwd", "cov_bwd") if backward else ("soft", "cov")
+    return (f"N_box={n_box} x {k['cand']} + N_soft={n_soft} x {k[s]} + N_cov={n_cov} x {k[c]} + "
+            f"N_sample={n_sample} x {k['sample']} flops ({solver} solver)")
 
 
 def fp32_peak_tflops(num_sms, mhz=SM_MAX_MHZ):

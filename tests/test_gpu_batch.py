@@ -92,11 +92,11 @@ def test_batch_replans_when_bins_overflow(ctx):
 def test_autotune_picks_a_candidate_and_keeps_results(ctx):
     items = _items(_specs()[:3], True)
     tile, spt, ms = ctx.autotune(items, True)
-    assert tile in (8, 16) and spt in (4, 8, 16) and math.isfinite(ms) and ms > 0
+    assert tile in (8, 16) and spt in (1, 2, 4, 8) and math.isfinite(ms) and ms > 0
     ctx.render_batch(items, True)
     torch.cuda.synchronize()
     _check(ctx, items, True)
-    ctx.set_tuning(16, 8, 0)
+    ctx.set_tuning(16, 2, 0)
 
 
 def test_single_renders_after_a_batch_keep_their_buffers():

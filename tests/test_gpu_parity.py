@@ -75,16 +75,16 @@ def test_tuning_variants_agree(ctx, tile, spt):
         g = gpu_render(ctx, sc, "fast")
         assert np.max(np.abs(g - ref)) < 2e-6
     finally:
-        ctx.set_tuning(16, 8, 0)
+        ctx.set_tuning(16, 2, 0)
 
 
 def test_splits_agree(ctx):
     sc = scenes.small_scene("rotate", subdiv=2, T=24, H=40, W=40)
     imgs = []
     for splits in (1, 3, 24):
-        ctx.set_tuning(16, 8, splits)
+        ctx.set_tuning(16, 2, splits)
         imgs.append(gpu_render(ctx, sc, "plain"))
-    ctx.set_tuning(16, 8, 0)
+    ctx.set_tuning(16, 2, 0)
     assert np.max(np.abs(imgs[0] - imgs[1])) < 2e-6 and np.max(np.abs(imgs[0] - imgs[2])) < 2e-6
 
 
@@ -126,6 +126,28 @@ def test_candidate_count_matches_oracle(ctx):
         n = ctx.count_candidates(v, f, a, mo, ca, sc["T"], sc["H"], sc["W"], solver)
         ref = oracle.render(sc, ORACLE_MODE[solver])["counters"][oracle.CNT_CAND]
         assert abs(n - ref) <= 1e-3 * ref, (solver, n, ref)
+
+
+@pytest.mark.parametrize("solver", ["plain", "fast"])
+@pytest.mark.parametrize("kind", ["translate", "rotate"])
+def test_work_counts_match_oracle(ctx, kind, solver):
+    """The roofline's work units counted by the GPU path (mbr_count_work) against the oracle's
+    counters: N_cand, soft terms of uncovered samples above the single-precision cutoff, covered
+    samples.  FP32 decisions near a boundary may differ: 1e-3 relative."""
+    sc = scenes.small_scene(kind, subdiv=2, T=8, H=40, W=72)
+    v, f, a, mo, ca = gpu_inputs(sc)
+    img = torch.zeros((sc["H"], sc["W"], 4), device="cuda")
+    d = ctx.count_work(v, f, a, mo, ca, sc["T"], sc["H"], sc["W"], solver, out=img, detail=True)
+    n_cand, n_soft, n_cov = d["n_cand"], d["n_soft"], d["n_cov"]
+    assert 0 < d["n_box"] < n_cand and d["cov_tests"] >= d["n_box"] * 0.5
+    c = oracle.render(sc, ORACLE_MODE[solver])["counters"]
+    assert abs(n_cand - c[oracle.CNT_CAND]) <= 1e-3 * c[oracle.CNT_CAND], (n_cand, c[oracle.CNT_CAND])
+    assert abs(n_soft - c[oracle.CNT_SOFT32]) <= 1e-3 * c[oracle.CNT_SOFT32] + 2, (n_soft, c[oracle.CNT_SOFT32])
+    assert abs(n_cov - c[oracle.CNT_COVERED]) <= 1e-3 * c[oracle.CNT_COVERED] + 2, (n_cov, c[oracle.CNT_COVERED])
+    assert n_soft > 0 and n_cov > 0
+    # the counting build renders the same image
+    ref = gpu_render(ctx, sc, solver)
+    assert float((img - torch.as_tensor(ref, device="cuda")).abs().max()) <= 1e-5
 
 
 def test_bad_arguments_return_errors(ctx):

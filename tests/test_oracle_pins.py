@@ -297,6 +297,35 @@ def test_translating_quad_converges_to_box_filter():
     assert np.max(np.abs(img[row, :, 0] / full - prof)) < 2.0 / T
 
 
+def _seg_dist2(px, py, ax, ay, bx, by):
+    ex, ey = bx - ax, by - ay
+    t = np.clip(((px - ax) * ex + (py - ay) * ey) / (ex * ex + ey * ey), 0.0, 1.0)
+    return (px - ax - t * ex) ** 2 + (py - ay - t * ey) ** 2
+
+
+def test_soft32_counter_is_the_uncovered_terms_above_the_single_precision_cutoff():
+    """CNT_SOFT32 (the work measure of the soft term) on a static screen-aligned quad: for every
+    pixel outside the quad, each of its two triangles whose squared distance is below
+    delta 25 ln 2 (exp(-d/delta) > 2^-25) counts once per sample; pixels inside count nothing."""
+    L0, R0, B, Tp = -0.37, 0.113, -0.29, 0.41
+    T, delta = 3, 4e-3
+    sc = _quad_scene(T, 0.0, L0, R0, B, Tp)
+    sc["camera"]["delta"] = delta
+    c = oracle.render(sc, "exact")["counters"]
+    H, W = sc["H"], sc["W"]
+    u = (2 * (np.arange(W) + 0.5) / W - 1)[None, :].repeat(H, 0)
+    v = (1 - 2 * (np.arange(H) + 0.5) / H)[:, None].repeat(W, 1)
+    BL, BR, TR, TL = (L0, B), (R0, B), (R0, Tp), (L0, Tp)
+    inside = (u >= L0) & (u <= R0) & (v >= B) & (v <= Tp)
+    n = np.zeros((H, W), dtype=np.int64)
+    for tri in ((BL, TR, BR), (BL, TL, TR)):
+        d2 = np.min([_seg_dist2(u, v, *tri[q], *tri[(q + 1) % 3]) for q in range(3)], axis=0)
+        n += (d2 < delta * 25 * np.log(2)) & ~inside
+    assert c[oracle.CNT_SOFT32] == T * n.sum() > 0
+    assert c[oracle.CNT_SOFT] > c[oracle.CNT_SOFT32]  # the oracle's own truncation reaches farther
+    assert c[oracle.CNT_COVERED] == T * inside.sum()
+
+
 def test_rotation_relabel_invariance_midpoint_rule():
     """With t_k = (k + 0.5)/T, omega = 2 pi and T a multiple of n, pre-rotating the mesh by 2 pi/n
     about the motion axis permutes the sub-frames and leaves the blurred image unchanged."""
