@@ -168,7 +168,7 @@ int mbr_count_work(mbr_ctx* ctx, const mbr_mesh* mesh, const mbr_motion* motion,
                    void* cuda_stream);
 
 /* Tuning knobs (autotuner): tile edge in pixels (8 or 16), sub-frames per thread for the fast
- * solver (1..16, default 2), and the number of sub-frame group splits of the raster work units
+ * solver (1..8, default 2), and the number of sub-frame group splits of the raster work units
  * (0 = automatic: about 64 units per SM). */
 int mbr_set_tuning(mbr_ctx* ctx, int32_t tile, int32_t spt, int32_t splits);
 

@@ -52,191 +52,233 @@ __device__ __forceinline__ void rel_vertices(const float4* r, const PixelSetup<M
   ax[2] = e2x - qtx; ay[2] = e2y - qty;
 }
 
-// pass 2 of the adjoint: soft products, counting vanishing factors separately so that the
-// exclusive product prod_{l != j} (1 - A_l) never divides by a zero factor
-template <int SPT>
-struct BwdSoftProduct {
-  float prod[SPT];
-  uint32_t nzero;  // 2 bits per sample: vanishing factors 0, 1, or 2 = "two or more"
-  float inv_delta;
-  __device__ __forceinline__ void begin() {}
-  __device__ __forceinline__ void eval() {}
-  template <typename PS>
-  __device__ __forceinline__ void term(const float4*, const PS&, const EdgeVals&, const SoftGeom& sg, int i, float,
-                                       int) {
-    const float f = -expm1f(-sg.d * inv_delta);
-    if (f > kTinyFactor) {
+// Gradient of one soft factor's distance d w.r.t. the vertex positions, scaled by gd = dL/dd:
+// accumulated into the slot-a (keyframe 0 / sub-frame) and slot-b (keyframe 1) sums.
+// Plain solver: exact distance, d d / d v_i = 2 (F w* - p) w*_i (envelope).  Fast solver:
+// d = |F(tau) w* - p|^2 with w* the closest point in F(X) to p' = F(X) w(tau) (Eqs.
+// euc-dist-approx-1..3), differentiated through w*, p' and w(tau) = N / D.
+template <bool MOVING>
+__device__ __forceinline__ void soft_grad_accumulate(const float4 (&r)[kRecF4], const PixelSetup<MOVING>& ps,
+                                                     const EdgeVals& e, const SoftGeom& sg, float tau, int X,
+                                                     float gd, float (&gax)[3], float (&gay)[3], float (&gbx)[3],
+                                                     float (&gby)[3]) {
+  const float grx = 2.f * sg.rx * gd, gry = 2.f * sg.ry * gd;  // d/d(F(tau) w* - p)
+  const float ws_[3] = {sg.c.w0, sg.c.w1, sg.c.w2};
+  float gtx[3], gty[3];
 #pragma unroll
-      for (int q = 0; q < SPT; ++q)
-        if (q == i) prod[q] *= f;
-    } else if (((nzero >> (2 * i)) & 3u) < 2u) {
-      nzero += 1u << (2 * i);
+  for (int q = 0; q < 3; ++q) {
+    gtx[q] = ws_[q] * grx;
+    gty[q] = ws_[q] * gry;
+  }
+  if (MOVING) {
+    // local vertex positions at tau and at keyframe X
+    const float e1tx = fmaf(tau, r[kR_D].x, r[kR_O].z), e1ty = fmaf(tau, r[kR_D].y, r[kR_O].w);
+    const float e2tx = fmaf(tau, r[kR_D].z, r[kR_E2].x), e2ty = fmaf(tau, r[kR_D].w, r[kR_E2].y);
+    const float fx = (float)X;
+    const float e1Xx = fmaf(fx, r[kR_D].x, r[kR_O].z), e1Xy = fmaf(fx, r[kR_D].y, r[kR_O].w);
+    const float e2Xx = fmaf(fx, r[kR_D].z, r[kR_E2].x), e2Xy = fmaf(fx, r[kR_D].w, r[kR_E2].y);
+    const float Vtx[3] = {0.f, e1tx, e2tx}, Vty[3] = {0.f, e1ty, e2ty};
+    const float VXx[3] = {0.f, e1Xx, e2Xx}, VXy[3] = {0.f, e1Xy, e2Xy};
+    float gXx[3] = {0.f, 0.f, 0.f}, gXy[3] = {0.f, 0.f, 0.f};
+    float gpx = 0.f, gpy = 0.f;
+    if (sg.c.region < 3) {
+      // w*_i = 1 - t, w*_j = t, t = ((p' - V_i) . E) / |E|^2 on edge (i, j) of F(X)
+      const int ei = sg.c.ei, ej = sg.c.ej;
+      float gti = 0.f, gtj = 0.f, Ex = 0.f, Ey = 0.f, Rx = 0.f, Ry = 0.f;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (q == ei) {
+          gti = Vtx[q] * grx + Vty[q] * gry;
+          Rx = sg.ppx - VXx[q];
+          Ry = sg.ppy - VXy[q];
+          Ex -= VXx[q];
+          Ey -= VXy[q];
+        }
+        if (q == ej) {
+          gtj = Vtx[q] * grx + Vty[q] * gry;
+          Ex += VXx[q];
+          Ey += VXy[q];
+        }
+      }
+      const float L2 = fmaf(Ex, Ex, Ey * Ey);
+      const float gt = (gtj - gti) / L2, t = sg.c.t;
+      gpx = gt * Ex;
+      gpy = gt * Ey;
+      const float gix = gt * (-Ex - Rx + 2.f * t * Ex), giy = gt * (-Ey - Ry + 2.f * t * Ey);
+      const float gjx = gt * (Rx - 2.f * t * Ex), gjy = gt * (Ry - 2.f * t * Ey);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (q == ei) { gXx[q] += gix; gXy[q] += giy; }
+        if (q == ej) { gXx[q] += gjx; gXy[q] += gjy; }
+      }
+    }
+    // p' = F(X) w(tau)
+    const float w1 = sg.w1, w2 = sg.w2, w0 = 1.f - w1 - w2;
+    const float wv[3] = {w0, w1, w2};
+    float gw[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      gXx[q] = fmaf(wv[q], gpx, gXx[q]);
+      gXy[q] = fmaf(wv[q], gpy, gXy[q]);
+      gw[q] = VXx[q] * gpx + VXy[q] * gpy;
+    }
+    // w = N / D with D = N0 + N1 + N2
+    const float sw = wv[0] * gw[0] + wv[1] * gw[1] + wv[2] * gw[2];
+    const float invD = 1.f / e.D;
+    float ax[3], ay[3], ex[3], ey[3];
+    rel_vertices<MOVING>(r, ps, tau, ax, ay);
+    edge_backward((gw[0] - sw) * invD, (gw[1] - sw) * invD, (gw[2] - sw) * invD, ax, ay, ex, ey);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      gtx[q] += ex[q];
+      gty[q] += ey[q];
+    }
+    // F(tau) = lerp of the two keyframes; F(X) is keyframe X
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      gax[q] = fmaf(1.f - tau, gtx[q], gax[q]);
+      gay[q] = fmaf(1.f - tau, gty[q], gay[q]);
+      gbx[q] = fmaf(tau, gtx[q], gbx[q]);
+      gby[q] = fmaf(tau, gty[q], gby[q]);
+      if (X == 0) {
+        gax[q] += gXx[q];
+        gay[q] += gXy[q];
+      } else {
+        gbx[q] += gXx[q];
+        gby[q] += gXy[q];
+      }
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      gax[q] += gtx[q];
+      gay[q] += gty[q];
     }
   }
-  __device__ __forceinline__ void end(int) {}
+}
+
+// pass 2 of the adjoint: the soft products as sums of log factors per (sample, pixel), the
+// vanishing factors counted apart, so that the exclusive products prod_{l != j} (1 - A_l) of
+// pass 3 never divide by zero
+template <int SPT, bool MOVING>
+struct BwdSoftLogPairs {
+  const TriRec* recs_set;
+  const Group* grp;
+  BlockPix bp;
+  WarpScratch<SPT>* ws;
+  uint32_t xbits;
+  float m, r2, inv_delta;
+  __device__ __forceinline__ void pair(bool ok, int face, int p, uint32_t smp) {
+    if (!ok) return;
+    float u, v;
+    bp.uv(p, u, v);
+    float4 r[kRecF4];
+    load_record<MOVING>(recs_set + face, r, false, true);
+    const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
+    while (smp) {
+      const int i = __ffs(smp) - 1;
+      smp &= smp - 1u;
+      const float tau = MOVING ? __ldg(&grp->tau[i]) : 0.f;
+      EdgeVals e;
+      SoftGeom sg;
+      if (!soft_pair_term<MOVING>(r, ps, u, v, tau, (xbits >> i) & 1u, m, r2, e, sg)) continue;
+      const float f = -expm1f(-sg.d * inv_delta);
+      if (f > kTinyFactor) atomicAdd(&ws->logp[i][p], __logf(f));
+      else atomicAdd(&ws->nzero[i][p], 1);
+    }
+  }
+  __device__ __forceinline__ void batch_end(int) {}
 };
 
 // pass 3 of the adjoint: gradient of alpha = 1 - prod_j (1 - A_j) w.r.t. the vertex positions of
-// every soft candidate, accumulated per candidate over the thread's samples, warp-reduced, and
-// added to the slot gradients by one lane
+// every soft candidate.  A batch's pairs of one face sit on consecutive lanes: they are summed by
+// a segmented warp reduction and the first lane of each run adds them to the slot gradients.
 template <int SPT, bool MOVING>
-struct BwdSoftGrad {
-  float prod[SPT];
-  uint32_t nzero;
-  float ga, inv_delta;
+struct BwdSoftGradPairs {
+  const TriRec* recs_set;
+  const Group* grp;
+  BlockPix bp;
+  WarpScratch<SPT>* ws;
+  uint32_t xbits;
+  float m, r2, inv_delta;
   const int32_t* faces;
   float4* gslot_a;
   float4* gslot_b;
   float gax[3], gay[3], gbx[3], gby[3];
-  bool any;
-
-  __device__ __forceinline__ void begin() {
+  __device__ __forceinline__ void pair(bool ok, int face, int p, uint32_t smp) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) gax[q] = gay[q] = gbx[q] = gby[q] = 0.f;
-    any = false;
-  }
-  __device__ __forceinline__ void eval() {}
-
-  __device__ __forceinline__ void term(const float4* r, const PixelSetup<MOVING>& ps, const EdgeVals& e,
-                                       const SoftGeom& sg, int i, float tau, int X) {
-    const float f = -expm1f(-sg.d * inv_delta);
-    const float A = __expf(-sg.d * inv_delta);
-    float pr = 1.f;
-    const int nz = (nzero >> (2 * i)) & 3u;
-#pragma unroll
-    for (int q = 0; q < SPT; ++q)
-      if (q == i) pr = prod[q];
-    float excl;
-    if (nz == 0) excl = pr / f;
-    else excl = (nz == 1 && f <= kTinyFactor) ? pr : 0.f;
-    // alpha = 1 - prod(1 - A_l): d alpha / d d_j = -excl A_j / delta
-    const float gd = ga * excl * (-A * inv_delta);
-    if (gd == 0.f) return;
-    any = true;
-    const float grx = 2.f * sg.rx * gd, gry = 2.f * sg.ry * gd;  // d/d(F(tau) w* - p)
-    const float ws[3] = {sg.c.w0, sg.c.w1, sg.c.w2};
-    float gtx[3], gty[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) { gtx[q] = ws[q] * grx; gty[q] = ws[q] * gry; }
-    if (MOVING) {
-      // local vertex positions at tau and at keyframe X
-      const float e1tx = fmaf(tau, r[kR_D].x, r[kR_O].z), e1ty = fmaf(tau, r[kR_D].y, r[kR_O].w);
-      const float e2tx = fmaf(tau, r[kR_D].z, r[kR_E2].x), e2ty = fmaf(tau, r[kR_D].w, r[kR_E2].y);
-      const float fx = (float)X;
-      const float e1Xx = fmaf(fx, r[kR_D].x, r[kR_O].z), e1Xy = fmaf(fx, r[kR_D].y, r[kR_O].w);
-      const float e2Xx = fmaf(fx, r[kR_D].z, r[kR_E2].x), e2Xy = fmaf(fx, r[kR_D].w, r[kR_E2].y);
-      const float Vtx[3] = {0.f, e1tx, e2tx}, Vty[3] = {0.f, e1ty, e2ty};
-      const float VXx[3] = {0.f, e1Xx, e2Xx}, VXy[3] = {0.f, e1Xy, e2Xy};
-      float gXx[3] = {0.f, 0.f, 0.f}, gXy[3] = {0.f, 0.f, 0.f};
-      float gpx = 0.f, gpy = 0.f;
-      if (sg.c.region < 3) {
-        // w*_i = 1 - t, w*_j = t, t = ((p' - V_i) . E) / |E|^2 on edge (i, j) of F(X)
-        const int ei = sg.c.ei, ej = sg.c.ej;
-        float gti = 0.f, gtj = 0.f, Ex = 0.f, Ey = 0.f, Rx = 0.f, Ry = 0.f;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          if (q == ei) {
-            gti = Vtx[q] * grx + Vty[q] * gry;
-            Rx = sg.ppx - VXx[q];
-            Ry = sg.ppy - VXy[q];
-            Ex -= VXx[q];
-            Ey -= VXy[q];
-          }
-          if (q == ej) {
-            gtj = Vtx[q] * grx + Vty[q] * gry;
-            Ex += VXx[q];
-            Ey += VXy[q];
-          }
-        }
-        const float L2 = fmaf(Ex, Ex, Ey * Ey);
-        const float gt = (gtj - gti) / L2, t = sg.c.t;
-        gpx = gt * Ex;
-        gpy = gt * Ey;
-        const float gix = gt * (-Ex - Rx + 2.f * t * Ex), giy = gt * (-Ey - Ry + 2.f * t * Ey);
-        const float gjx = gt * (Rx - 2.f * t * Ex), gjy = gt * (Ry - 2.f * t * Ey);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          if (q == ei) { gXx[q] += gix; gXy[q] += giy; }
-          if (q == ej) { gXx[q] += gjx; gXy[q] += gjy; }
-        }
-      }
-      // p' = F(X) w(tau)
-      const float w1 = sg.w1, w2 = sg.w2, w0 = 1.f - w1 - w2;
-      const float wv[3] = {w0, w1, w2};
-      float gw[3];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        gXx[q] = fmaf(wv[q], gpx, gXx[q]);
-        gXy[q] = fmaf(wv[q], gpy, gXy[q]);
-        gw[q] = VXx[q] * gpx + VXy[q] * gpy;
-      }
-      // w = N / D with D = N0 + N1 + N2
-      const float sw = wv[0] * gw[0] + wv[1] * gw[1] + wv[2] * gw[2];
-      const float invD = 1.f / e.D;
-      float ax[3], ay[3], ex[3], ey[3];
-      rel_vertices<MOVING>(r, ps, tau, ax, ay);
-      edge_backward((gw[0] - sw) * invD, (gw[1] - sw) * invD, (gw[2] - sw) * invD, ax, ay, ex, ey);
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        gtx[q] += ex[q];
-        gty[q] += ey[q];
-      }
-      // F(tau) = lerp of the two keyframes; F(X) is keyframe X
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        gax[q] = fmaf(1.f - tau, gtx[q], gax[q]);
-        gay[q] = fmaf(1.f - tau, gty[q], gay[q]);
-        gbx[q] = fmaf(tau, gtx[q], gbx[q]);
-        gby[q] = fmaf(tau, gty[q], gby[q]);
-        if (X == 0) {
-          gax[q] += gXx[q];
-          gay[q] += gXy[q];
-        } else {
-          gbx[q] += gXx[q];
-          gby[q] += gXy[q];
-        }
-      }
-    } else {
-      // exact distance: d d / d v_i = 2 (F w* - p) w*_i
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        gax[q] += gtx[q];
-        gay[q] += gty[q];
-      }
+    if (!ok) return;
+    float u, v;
+    bp.uv(p, u, v);
+    float4 r[kRecF4];
+    load_record<MOVING>(recs_set + face, r, false, true);
+    const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
+    const float ga = ws->ga[p];
+    while (smp) {
+      const int i = __ffs(smp) - 1;
+      smp &= smp - 1u;
+      const float tau = MOVING ? __ldg(&grp->tau[i]) : 0.f;
+      const int X = (xbits >> i) & 1u;
+      EdgeVals e;
+      SoftGeom sg;
+      if (!soft_pair_term<MOVING>(r, ps, u, v, tau, X, m, r2, e, sg)) continue;
+      const float f = -expm1f(-sg.d * inv_delta);
+      const float A = __expf(-sg.d * inv_delta);
+      const float S = ws->logp[i][p];
+      const int nz = ws->nzero[i][p];
+      float excl;
+      if (nz == 0) excl = __expf(S - __logf(f));
+      else excl = (nz == 1 && f <= kTinyFactor) ? __expf(S) : 0.f;
+      // alpha = 1 - prod(1 - A_l): d alpha / d d_j = -excl A_j / delta
+      const float gd = ga * excl * (-A * inv_delta);
+      if (gd == 0.f) continue;
+      soft_grad_accumulate<MOVING>(r, ps, e, sg, tau, X, gd, gax, gay, gbx, gby);
     }
   }
-
-  __device__ __forceinline__ void end(int face) {
-    const uint32_t am = __ballot_sync(0xffffffffu, any);
-    if (!am) return;
-    if (__popc(am) == 1) {
+  __device__ __forceinline__ void batch_end(int face) {
+    const int lane = threadIdx.x & 31;
+    bool mine = false;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) mine |= gax[q] != 0.f || gay[q] != 0.f || (MOVING && (gbx[q] != 0.f || gby[q] != 0.f));
+    if (!__any_sync(kFullMask, mine)) return;
+    const int prev = __shfl_up_sync(kFullMask, face, 1);
+    const bool head = face >= 0 && (lane == 0 || prev != face);
+    const uint32_t heads = __ballot_sync(kFullMask, head);
+    const uint32_t above = lane == 31 ? 0u : (heads & (kFullMask << (lane + 1)));
+    const int seg_end = above ? __ffs(above) - 1 : 32;
+    constexpr int NV = MOVING ? 12 : 6;
+    float vals[NV];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      vals[2 * q] = gax[q];
+      vals[2 * q + 1] = gay[q];
+      if (MOVING) {
+        vals[6 + 2 * q] = gbx[q];
+        vals[6 + 2 * q + 1] = gby[q];
+      }
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const float y = __shfl_down_sync(kFullMask, vals[q], o);
+        if (lane + o < seg_end) vals[q] += y;
+      }
+    }
+    if (head) {
+      bool any = false;
+#pragma unroll
+      for (int q = 0; q < NV; ++q) any |= vals[q] != 0.f;
       if (any) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           const int vid = __ldg(faces + 3 * face + q);
-          atomicAdd(reinterpret_cast<float2*>(gslot_a + (size_t)vid * 2), make_float2(gax[q], gay[q]));
+          atomicAdd(reinterpret_cast<float2*>(gslot_a + (size_t)vid * 2), make_float2(vals[2 * q], vals[2 * q + 1]));
           if (MOVING)
-            atomicAdd(reinterpret_cast<float2*>(gslot_b + (size_t)vid * 2), make_float2(gbx[q], gby[q]));
+            atomicAdd(reinterpret_cast<float2*>(gslot_b + (size_t)vid * 2),
+                      make_float2(vals[6 + 2 * q], vals[6 + 2 * q + 1]));
         }
-      }
-      return;
-    }
-    float vals[12];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      vals[2 * q] = warp_sum(gax[q]);
-      vals[2 * q + 1] = warp_sum(gay[q]);
-      vals[6 + 2 * q] = MOVING ? warp_sum(gbx[q]) : 0.f;
-      vals[7 + 2 * q] = MOVING ? warp_sum(gby[q]) : 0.f;
-    }
-    if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const int vid = __ldg(faces + 3 * face + q);
-        atomicAdd(reinterpret_cast<float2*>(gslot_a + (size_t)vid * 2), make_float2(vals[2 * q], vals[2 * q + 1]));
-        if (MOVING)
-          atomicAdd(reinterpret_cast<float2*>(gslot_b + (size_t)vid * 2),
-                    make_float2(vals[6 + 2 * q], vals[7 + 2 * q]));
       }
     }
   }
@@ -373,62 +415,95 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
   }
 }
 
-// One work item of the adjoint: the 8 x 4 pixel block wb of tile `tile`, groups of `split`.
+// One work item of the adjoint: the 8 x 4 pixel block wb of tile `tile`, groups of `split`; ws
+// is the warp's shared scratch.
 template <int TW, int TH, int SPT, bool MOVING>
-__device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile, int split, int wb) {
+__device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile, int split, int wb,
+                                                 WarpScratch<SPT>& ws) {
+  const int lane = threadIdx.x & 31;
   const int n_tiles = P.tiles_x * P.tiles_y;
   const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
   int px, py;
   PixelMap<TW, TH>::pixel(tx, ty, wb, px, py);
+  const BlockPix bp{px - (lane & 7), py - (lane >> 3), P.W, P.H};
   const bool in_img = px < P.W && py < P.H;
-  const float u = (2.f * px + 1.f) / P.W - 1.f;
-  const float v = 1.f - (2.f * py + 1.f) / P.H;
+  float u, v;
+  bp.uv(lane, u, v);
   const TileBox tb = PixelMap<TW, TH>::warp_box(tx, ty, wb, P.W, P.H);
   const int g_begin = (int)((long long)P.G * split / P.n_split);
   const int g_end = (int)((long long)P.G * (split + 1) / P.n_split);
+  const uint32_t img_mask = __ballot_sync(kFullMask, in_img);
   float4 G4 = make_float4(0.f, 0.f, 0.f, 0.f);
   if (in_img) G4 = __ldg(P.dl_dimage + (size_t)py * P.W + px);
   const float gr = G4.x * P.inv_T, gg = G4.y * P.inv_T, gb = G4.z * P.inv_T, ga = G4.w * P.inv_T;
+  const bool active = in_img && ga != 0.f;
 
   for (int g = g_begin; g < g_end; ++g) {
     const Group* grp = P.groups + g;
     GroupRegs gq;
     gq.load(grp);
     const int n = gq.n;
+    const uint32_t all_s = (1u << n) - 1u;
     const TriRec* recs_set = P.recs + (size_t)gq.rec_set * P.F;
     const size_t bi = (size_t)g * n_tiles + tile;
     float4* gslot_a = P.g_slot + (size_t)gq.slot_a * P.V * 2;
     float4* gslot_b = P.g_slot + (size_t)gq.slot_b * P.V * 2;
-    float bestk[SPT];
-    int bestf[SPT];
     int cb, ce, sb, se;
     P.core.range(bi, cb, ce);
     P.soft.range(bi, sb, se);
-    pass_winners<SPT, MOVING>(grp, n, recs_set, P.core.faces, cb, ce, tb, in_img, u, v, bestk, bestf);
+
+    // ---- pass 1: winners (recomputed)
+    uint32_t allowed[SPT];
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) {
+      allowed[i] = i < n ? img_mask : 0u;
+      ws.win[i][lane] = 0ull;
+    }
+    ws.pixs[lane] = in_img ? all_s : 0u;
+    ws.ga[lane] = ga;
+    __syncwarp();
+    CorePairs<SPT, MOVING, false> core{recs_set, grp, bp, &ws, 0u, 0u};
+    for_pairs<SPT, MOVING>(recs_set, P.core.faces, cb, ce, grp, n, tb, bp, kCoreMargin, allowed, all_s, ws, core);
+    int bestf[SPT];
     uint32_t uncov = 0;
 #pragma unroll
-    for (int i = 0; i < SPT; ++i)
-      if (i < n && bestf[i] < 0) uncov |= 1u << i;
-    const bool active = in_img && ga != 0.f;
-    if (se > sb && __any_sync(0xffffffffu, active && uncov != 0)) {
-      BwdSoftProduct<SPT> p2;
+    for (int i = 0; i < SPT; ++i) {
+      bestf[i] = -1;
+      if (i < n) {
+        const unsigned long long w = ws.win[i][lane];
+        if (w) bestf[i] = (int)(~(uint32_t)w);
+        else uncov |= 1u << i;
+      }
+    }
+
+    // ---- passes 2-3: soft products, then their gradients (uncovered samples with dL/dalpha)
+    const uint32_t my_s = active ? uncov : 0u;
+    const uint32_t any_s = __reduce_or_sync(kFullMask, my_s);
+    if (se > sb && any_s) {
 #pragma unroll
-      for (int i = 0; i < SPT; ++i) p2.prod[i] = 1.f;
-      p2.nzero = 0u;
-      p2.inv_delta = P.inv_delta;
-      for_soft_terms<SPT, MOVING>(grp, n, gq.xbits, recs_set, P.soft.faces, sb, se, tb, active, u, v, uncov, P.r,
-                                  P.r2, p2);
-      BwdSoftGrad<SPT, MOVING> p3;
-#pragma unroll
-      for (int i = 0; i < SPT; ++i) p3.prod[i] = p2.prod[i];
-      p3.nzero = p2.nzero;
-      p3.ga = ga;
+      for (int i = 0; i < SPT; ++i) {
+        allowed[i] = __ballot_sync(kFullMask, (my_s >> i) & 1u);
+        ws.logp[i][lane] = 0.f;
+        ws.nzero[i][lane] = 0;
+      }
+      ws.pixs[lane] = my_s;
+      __syncwarp();
+      const float m = P.r + kCoreMargin;
+      BwdSoftLogPairs<SPT, MOVING> p2{recs_set, grp, bp, &ws, gq.xbits, m, P.r2, P.inv_delta};
+      for_pairs<SPT, MOVING>(recs_set, P.soft.faces, sb, se, grp, n, tb, bp, m, allowed, any_s, ws, p2);
+      BwdSoftGradPairs<SPT, MOVING> p3;
+      p3.recs_set = recs_set;
+      p3.grp = grp;
+      p3.bp = bp;
+      p3.ws = &ws;
+      p3.xbits = gq.xbits;
+      p3.m = m;
+      p3.r2 = P.r2;
       p3.inv_delta = P.inv_delta;
       p3.faces = P.faces;
       p3.gslot_a = gslot_a;
       p3.gslot_b = gslot_b;
-      for_soft_terms<SPT, MOVING>(grp, n, gq.xbits, recs_set, P.soft.faces, sb, se, tb, active, u, v, uncov, P.r,
-                                  P.r2, p3);
+      for_pairs<SPT, MOVING>(recs_set, P.soft.faces, sb, se, grp, n, tb, bp, m, allowed, any_s, ws, p3);
     }
 
     // ---- covered samples: shading adjoint and barycentric adjoint of the winner (one copy of
@@ -443,6 +518,7 @@ __device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile
       const bool has = in_img && f >= 0;
       covered_adjoint<MOVING>(P, recs_set, gq.slot_a, gq.slot_b, has, has ? f : 0, tau, u, v, gr, gg, gb);
     }
+    __syncwarp();  // the scratch is rewritten by the next group
   }
 }
 
@@ -451,15 +527,17 @@ template <int TW, int TH, int SPT, int KIND>
 __global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 4 : 2) raster_bwd_persistent(WorkQueue Q) {
   __shared__ CtaQueue cq;
   __shared__ RasterParams sp[kPersistentThreads / 32];
+  __shared__ WarpScratch<SPT> ws[kPersistentThreads / 32];
   cq.init();
-  RasterParams& P = sp[threadIdx.x >> 5];
+  const int warp = threadIdx.x >> 5;
+  RasterParams& P = sp[warp];
   int cur = -1, tile = 0, split = 0, wb = 0;
   while (warp_next<TW, TH>(Q, cq, P, cur, tile, split, wb)) {
     if (tile >= P.tiles_x * P.tiles_y) continue;
     if (KIND == 0 || (KIND == 2 && !P.moving))
-      raster_bwd_block<TW, TH, 1, false>(P, tile, split, wb);
+      raster_bwd_block<TW, TH, 1, false>(P, tile, split, wb, *reinterpret_cast<WarpScratch<1>*>(ws + warp));
     else
-      raster_bwd_block<TW, TH, SPT, true>(P, tile, split, wb);
+      raster_bwd_block<TW, TH, SPT, true>(P, tile, split, wb, ws[warp]);
   }
 }
 
@@ -549,12 +627,12 @@ __global__ void normals_bwd_kernel(const float* __restrict__ verts, const int32_
 
 template <int TW, int TH, int KIND>
 static void launch_bwd_spt(const WorkQueue& Q, int spt, int grid, cudaStream_t st) {
-  if (spt <= 4)
+  if (spt <= 2)
+    raster_bwd_persistent<TW, TH, 2, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
+  else if (spt <= 4)
     raster_bwd_persistent<TW, TH, 4, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
-  else if (spt <= 8)
-    raster_bwd_persistent<TW, TH, 8, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
   else
-    raster_bwd_persistent<TW, TH, 16, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
+    raster_bwd_persistent<TW, TH, 8, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
 }
 
 template <int TW, int TH>
@@ -585,12 +663,12 @@ static int occupancy_of(K kernel) {
 template <int TW, int TH>
 static int occ_bwd(int spt, int kind) {
   if (kind == 0) return occupancy_of(raster_bwd_persistent<TW, TH, 1, 0>);
-  const int sp = spt <= 4 ? 4 : (spt <= 8 ? 8 : 16);
+  const int sp = spt <= 2 ? 2 : (spt <= 4 ? 4 : 8);
   if (kind == 1)
-    return sp == 4 ? occupancy_of(raster_bwd_persistent<TW, TH, 4, 1>)
-                   : sp == 8 ? occupancy_of(raster_bwd_persistent<TW, TH, 8, 1>) : occupancy_of(raster_bwd_persistent<TW, TH, 16, 1>);
-  return sp == 4 ? occupancy_of(raster_bwd_persistent<TW, TH, 4, 2>)
-                 : sp == 8 ? occupancy_of(raster_bwd_persistent<TW, TH, 8, 2>) : occupancy_of(raster_bwd_persistent<TW, TH, 16, 2>);
+    return sp == 2 ? occupancy_of(raster_bwd_persistent<TW, TH, 2, 1>)
+                   : sp == 4 ? occupancy_of(raster_bwd_persistent<TW, TH, 4, 1>) : occupancy_of(raster_bwd_persistent<TW, TH, 8, 1>);
+  return sp == 2 ? occupancy_of(raster_bwd_persistent<TW, TH, 2, 2>)
+                 : sp == 4 ? occupancy_of(raster_bwd_persistent<TW, TH, 4, 2>) : occupancy_of(raster_bwd_persistent<TW, TH, 8, 2>);
 }
 
 int persistent_grid_bwd(int num_sms, int tile, int spt, int kind) {

@@ -265,82 +265,131 @@ __global__ void scan_apply_kernel(const int32_t* __restrict__ in, int n, const i
 }
 
 // ---------------------------------------------------------------- a4-a8: forward raster
-template <int SPT, bool COUNT>
-struct FwdSoftProduct {
-  float prod[SPT];
-  float inv_delta;
-  uint32_t n_terms, n_eval, n_iter;  // COUNT: terms in the product, distance evaluations, warp steps
-  __device__ __forceinline__ void begin() {
-    if (COUNT && (threadIdx.x & 31) == 0) ++n_iter;
+// pass 2 of the forward: log soft factors log(1 - A_j), A_j = exp(-d_j / delta) (Eqs.
+// probability-function .. back), summed per (sample, pixel) in ws.logp.
+template <int SPT, bool MOVING, bool COUNT>
+struct FwdSoftPairs {
+  const TriRec* recs_set;
+  const Group* grp;
+  BlockPix bp;
+  WarpScratch<SPT>* ws;
+  uint32_t xbits;
+  float m, r2, inv_delta;
+  uint32_t n_terms, n_eval, n_batches;
+  __device__ __forceinline__ void pair(bool ok, int face, int p, uint32_t smp) {
+    if (!ok) return;
+    float u, v;
+    bp.uv(p, u, v);
+    float4 r[kRecF4];
+    load_record<MOVING>(recs_set + face, r, false, true);
+    const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
+    while (smp) {
+      const int i = __ffs(smp) - 1;
+      smp &= smp - 1u;
+      const float tau = MOVING ? __ldg(&grp->tau[i]) : 0.f;
+      if (COUNT) ++n_eval;
+      EdgeVals e;
+      SoftGeom sg;
+      if (!soft_pair_term<MOVING>(r, ps, u, v, tau, (xbits >> i) & 1u, m, r2, e, sg)) continue;
+      const float f = -expm1f(-sg.d * inv_delta);
+      atomicAdd(&ws->logp[i][p], __logf(f));
+      if (COUNT) ++n_terms;
+    }
   }
-  __device__ __forceinline__ void eval() {
-    if (COUNT) ++n_eval;
+  __device__ __forceinline__ void batch_end(int) {
+    if (COUNT && (threadIdx.x & 31) == 0) ++n_batches;
   }
-  template <typename PS>
-  __device__ __forceinline__ void term(const float4*, const PS&, const EdgeVals&, const SoftGeom& sg, int i, float,
-                                       int) {
-    const float f = -expm1f(-sg.d * inv_delta);
-#pragma unroll
-    for (int q = 0; q < SPT; ++q)
-      if (q == i) prod[q] *= f;
-    if (COUNT) ++n_terms;
-  }
-  __device__ __forceinline__ void end(int) {}
 };
 
-// One work item: the 8 x 4 pixel block wb of tile `tile`, sample groups of split `split`.
-// COUNT (measurement build only): also count soft terms and covered samples into P.counts.
+// One work item: the 8 x 4 pixel block wb of tile `tile`, sample groups of split `split`; ws is
+// the warp's shared scratch.  COUNT (measurement build only): also count soft terms, covered
+// samples and pass efficiency into P.counts.
 template <int TW, int TH, int SPT, bool MOVING, bool COUNT = false>
-__device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile, int split, int wb) {
+__device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile, int split, int wb,
+                                                 WarpScratch<SPT>& ws) {
+  const int lane = threadIdx.x & 31;
   const int n_tiles = P.tiles_x * P.tiles_y;
   const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
   int px, py;
   PixelMap<TW, TH>::pixel(tx, ty, wb, px, py);
+  const BlockPix bp{px - (lane & 7), py - (lane >> 3), P.W, P.H};
   const bool in_img = px < P.W && py < P.H;
-  const float u = (2.f * px + 1.f) / P.W - 1.f;
-  const float v = 1.f - (2.f * py + 1.f) / P.H;
+  float u, v;
+  bp.uv(lane, u, v);
   const TileBox tb = PixelMap<TW, TH>::warp_box(tx, ty, wb, P.W, P.H);
   const int g_begin = (int)((long long)P.G * split / P.n_split);
   const int g_end = (int)((long long)P.G * (split + 1) / P.n_split);
+  const uint32_t img_mask = __ballot_sync(kFullMask, in_img);
   float acc_r = 0.f, acc_g = 0.f, acc_b = 0.f, acc_a = 0.f;
-  uint32_t n_soft = 0, n_cov = 0, n_seval = 0, n_siter = 0;
-  uint32_t ccnt[2] = {0u, 0u};
+  uint32_t n_soft = 0, n_cov = 0, n_seval = 0, n_sbatch = 0, n_ctest = 0, n_cbatch = 0;
 
   for (int g = g_begin; g < g_end; ++g) {
     const Group* grp = P.groups + g;
     GroupRegs gr;
     gr.load(grp);
     const int n = gr.n;
+    const uint32_t all_s = (1u << n) - 1u;
     const TriRec* recs_set = P.recs + (size_t)gr.rec_set * P.F;
     const size_t bi = (size_t)g * n_tiles + tile;
-    float bestk[SPT];
-    int bestf[SPT];
     int cb, ce, sb, se;
     P.core.range(bi, cb, ce);
     P.soft.range(bi, sb, se);
-    pass_winners<SPT, MOVING, COUNT>(grp, n, recs_set, P.core.faces, cb, ce, tb, in_img, u, v, bestk, bestf, ccnt);
+
+    // ---- pass 1: winners
+    uint32_t allowed[SPT];
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) {
+      allowed[i] = i < n ? img_mask : 0u;
+      ws.win[i][lane] = 0ull;
+    }
+    ws.pixs[lane] = in_img ? all_s : 0u;
+    __syncwarp();
+    CorePairs<SPT, MOVING, COUNT> core{recs_set, grp, bp, &ws, 0u, 0u};
+    for_pairs<SPT, MOVING>(recs_set, P.core.faces, cb, ce, grp, n, tb, bp, kCoreMargin, allowed, all_s, ws, core);
+    int bestf[SPT];
     uint32_t uncov = 0;
 #pragma unroll
-    for (int i = 0; i < SPT; ++i)
-      if (i < n && bestf[i] < 0) uncov |= 1u << i;
-    FwdSoftProduct<SPT, COUNT> soft;
-#pragma unroll
-    for (int i = 0; i < SPT; ++i) soft.prod[i] = 1.f;
-    soft.inv_delta = P.inv_delta;
-    soft.n_terms = soft.n_eval = soft.n_iter = 0;
-    if (se > sb && __any_sync(0xffffffffu, in_img && uncov != 0))
-      for_soft_terms<SPT, MOVING>(grp, n, gr.xbits, recs_set, P.soft.faces, sb, se, tb, in_img, u, v, uncov, P.r,
-                                  P.r2, soft);
-    if (COUNT) {
-      n_seval += soft.n_eval;
-      n_siter += soft.n_iter;
-      if (in_img) {
-        n_soft += soft.n_terms;
-        n_cov += (uint32_t)n - (uint32_t)__popc(uncov);
+    for (int i = 0; i < SPT; ++i) {
+      bestf[i] = -1;
+      if (i < n) {
+        const unsigned long long w = ws.win[i][lane];
+        if (w) bestf[i] = (int)(~(uint32_t)w);
+        else uncov |= 1u << i;
       }
     }
 
-    // ---- shading of the winners (Eq. fore + Lambert) and temporal accumulation (Sec. 3.3)
+    // ---- pass 2: soft coverage of the uncovered samples
+    float prod[SPT];
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) prod[i] = 1.f;
+    const uint32_t my_s = in_img ? uncov : 0u;
+    const uint32_t any_s = __reduce_or_sync(kFullMask, my_s);
+    FwdSoftPairs<SPT, MOVING, COUNT> soft{recs_set, grp, bp, &ws, gr.xbits, P.r + kCoreMargin, P.r2, P.inv_delta,
+                                          0u, 0u, 0u};
+    if (se > sb && any_s) {
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) {
+        allowed[i] = __ballot_sync(kFullMask, (my_s >> i) & 1u);
+        ws.logp[i][lane] = 0.f;
+      }
+      ws.pixs[lane] = my_s;
+      __syncwarp();
+      for_pairs<SPT, MOVING>(recs_set, P.soft.faces, sb, se, grp, n, tb, bp, P.r + kCoreMargin, allowed, any_s, ws,
+                             soft);
+#pragma unroll
+      for (int i = 0; i < SPT; ++i)
+        if ((my_s >> i) & 1u) prod[i] = __expf(ws.logp[i][lane]);
+    }
+    if (COUNT) {
+      n_ctest += core.n_tests;
+      n_cbatch += core.n_batches;
+      n_seval += soft.n_eval;
+      n_sbatch += soft.n_batches;
+      n_soft += soft.n_terms;
+      if (in_img) n_cov += (uint32_t)n - (uint32_t)__popc(uncov);
+    }
+
+    // ---- shading of the winners (Eq. fore + Lambert) and temporal accumulation (Sec. 3.2)
     if (in_img) {
 #pragma unroll
       for (int i = 0; i < SPT; ++i) {
@@ -381,11 +430,12 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
             acc_b = fmaf(cb, shade, acc_b);
             acc_a += 1.f;
           } else {
-            acc_a += 1.f - soft.prod[i];
+            acc_a += 1.f - prod[i];
           }
         }
       }
     }
+    __syncwarp();  // the scratch is rewritten by the next group
   }
   if (in_img) {
     const size_t o = (size_t)py * P.W + px;
@@ -394,14 +444,14 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
     else atomicAdd(P.out + o, val);  // the image was zeroed; splits add their share of the mean
   }
   if (COUNT) {
-    // [soft terms, covered samples, soft evaluations, soft warp steps, coverage tests, core warp steps]
-    unsigned long long c[6] = {n_soft, n_cov, n_seval, n_siter, ccnt[0], ccnt[1]};
+    // [soft terms, covered samples, soft evaluations, soft pair batches, coverage tests, core pair batches]
+    unsigned long long c[6] = {n_soft, n_cov, n_seval, n_sbatch, n_ctest, n_cbatch};
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) c[q] += __shfl_xor_sync(0xffffffffu, c[q], o);
+      for (int o = 16; o > 0; o >>= 1) c[q] += __shfl_xor_sync(kFullMask, c[q], o);
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
 #pragma unroll
       for (int q = 0; q < 6; ++q)
         if (c[q]) atomicAdd(P.counts + q, c[q]);
@@ -414,15 +464,17 @@ template <int TW, int TH, int SPT, int KIND>
 __global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 4 : 2) raster_fwd_persistent(WorkQueue Q) {
   __shared__ CtaQueue cq;
   __shared__ RasterParams sp[kPersistentThreads / 32];
+  __shared__ WarpScratch<SPT> ws[kPersistentThreads / 32];
   cq.init();
-  RasterParams& P = sp[threadIdx.x >> 5];
+  const int warp = threadIdx.x >> 5;
+  RasterParams& P = sp[warp];
   int cur = -1, tile = 0, split = 0, wb = 0;
   while (warp_next<TW, TH>(Q, cq, P, cur, tile, split, wb)) {
     if (tile >= P.tiles_x * P.tiles_y) continue;
     if (KIND == 0 || (KIND == 2 && !P.moving))
-      raster_fwd_block<TW, TH, 1, false>(P, tile, split, wb);
+      raster_fwd_block<TW, TH, 1, false>(P, tile, split, wb, *reinterpret_cast<WarpScratch<1>*>(ws + warp));
     else
-      raster_fwd_block<TW, TH, SPT, true>(P, tile, split, wb);
+      raster_fwd_block<TW, TH, SPT, true>(P, tile, split, wb, ws[warp]);
   }
 }
 
@@ -431,15 +483,17 @@ template <int SPT, int KIND>
 __global__ void __launch_bounds__(kPersistentThreads, 2) raster_fwd_count(WorkQueue Q) {
   __shared__ CtaQueue cq;
   __shared__ RasterParams sp[kPersistentThreads / 32];
+  __shared__ WarpScratch<SPT> ws[kPersistentThreads / 32];
   cq.init();
-  RasterParams& P = sp[threadIdx.x >> 5];
+  const int warp = threadIdx.x >> 5;
+  RasterParams& P = sp[warp];
   int cur = -1, tile = 0, split = 0, wb = 0;
   while (warp_next<16, 16>(Q, cq, P, cur, tile, split, wb)) {
     if (tile >= P.tiles_x * P.tiles_y) continue;
     if (KIND == 0)
-      raster_fwd_block<16, 16, 1, false, true>(P, tile, split, wb);
+      raster_fwd_block<16, 16, 1, false, true>(P, tile, split, wb, *reinterpret_cast<WarpScratch<1>*>(ws + warp));
     else
-      raster_fwd_block<16, 16, SPT, true, true>(P, tile, split, wb);
+      raster_fwd_block<16, 16, SPT, true, true>(P, tile, split, wb, ws[warp]);
   }
 }
 
@@ -574,12 +628,12 @@ void launch_scan(const int32_t* in, int n, int32_t* out, int32_t* temp, cudaStre
 
 template <int TW, int TH, int KIND>
 static void launch_fwd_spt(const WorkQueue& Q, int spt, int grid, cudaStream_t st) {
-  if (spt <= 4)
+  if (spt <= 2)
+    raster_fwd_persistent<TW, TH, 2, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
+  else if (spt <= 4)
     raster_fwd_persistent<TW, TH, 4, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
-  else if (spt <= 8)
-    raster_fwd_persistent<TW, TH, 8, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
   else
-    raster_fwd_persistent<TW, TH, 16, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
+    raster_fwd_persistent<TW, TH, 8, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
 }
 
 template <int TW, int TH>
@@ -602,12 +656,12 @@ static int occupancy_of(K kernel) {
 template <int TW, int TH>
 static int occ_fwd(int spt, int kind) {
   if (kind == 0) return occupancy_of(raster_fwd_persistent<TW, TH, 1, 0>);
-  const int sp = spt <= 4 ? 4 : (spt <= 8 ? 8 : 16);
+  const int sp = spt <= 2 ? 2 : (spt <= 4 ? 4 : 8);
   if (kind == 1)
-    return sp == 4 ? occupancy_of(raster_fwd_persistent<TW, TH, 4, 1>)
-                   : sp == 8 ? occupancy_of(raster_fwd_persistent<TW, TH, 8, 1>) : occupancy_of(raster_fwd_persistent<TW, TH, 16, 1>);
-  return sp == 4 ? occupancy_of(raster_fwd_persistent<TW, TH, 4, 2>)
-                 : sp == 8 ? occupancy_of(raster_fwd_persistent<TW, TH, 8, 2>) : occupancy_of(raster_fwd_persistent<TW, TH, 16, 2>);
+    return sp == 2 ? occupancy_of(raster_fwd_persistent<TW, TH, 2, 1>)
+                   : sp == 4 ? occupancy_of(raster_fwd_persistent<TW, TH, 4, 1>) : occupancy_of(raster_fwd_persistent<TW, TH, 8, 1>);
+  return sp == 2 ? occupancy_of(raster_fwd_persistent<TW, TH, 2, 2>)
+                 : sp == 4 ? occupancy_of(raster_fwd_persistent<TW, TH, 4, 2>) : occupancy_of(raster_fwd_persistent<TW, TH, 8, 2>);
 }
 
 int persistent_grid_fwd(int num_sms, int tile, int spt, int kind) {
@@ -642,9 +696,9 @@ void launch_unit_order(const int32_t* core_off, const int32_t* soft_off, int G, 
 void launch_raster_count(const WorkQueue& Q, int spt, int kind, int grid, cudaStream_t st) {
   if (Q.n_work <= 0) return;
   if (kind == 0) raster_fwd_count<1, 0><<<grid, kPersistentThreads, 0, st>>>(Q);
+  else if (spt <= 2) raster_fwd_count<2, 1><<<grid, kPersistentThreads, 0, st>>>(Q);
   else if (spt <= 4) raster_fwd_count<4, 1><<<grid, kPersistentThreads, 0, st>>>(Q);
-  else if (spt <= 8) raster_fwd_count<8, 1><<<grid, kPersistentThreads, 0, st>>>(Q);
-  else raster_fwd_count<16, 1><<<grid, kPersistentThreads, 0, st>>>(Q);
+  else raster_fwd_count<8, 1><<<grid, kPersistentThreads, 0, st>>>(Q);
 }
 
 void launch_count(const TriRec* recs, int F, const Group* groups, int G, int W, int H, float r,

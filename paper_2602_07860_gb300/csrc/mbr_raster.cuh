@@ -267,106 +267,178 @@ __device__ __forceinline__ float4 shfl_box(const float4& b, int src) {
                      __shfl_sync(0xffffffffu, b.z, src), __shfl_sync(0xffffffffu, b.w, src));
 }
 
-// Walk a bin list 32 candidates at a time: each lane derives one candidate's meta-data, a ballot
-// keeps the candidates that touch the warp's rectangle, and the warp visits them in order with
-// fn(face, rec, mask, box).  Warp-collective: every lane of the warp must call it.
-template <bool MOVING, typename Fn>
-__device__ __forceinline__ void for_warp_candidates(const TriRec* recs_set, const int32_t* list, int beg, int end,
-                                                    const Group* grp, int n, const TileBox& tb, float m,
-                                                    uint32_t samples, Fn&& fn) {
+// ---------------------------------------------------------------- compacted pair passes
+// A warp owns an 8 x 4 pixel block (lane p = pixel (p % 8, p / 8)).  Rather than evaluating a
+// candidate triangle on all 32 lanes when it touches a few of them, a pass walks its bin list
+// 32 candidates at a time in two steps:
+//   generation  lane j takes candidate j: its samples whose box meets the warp's rectangle, and
+//               the block pixels its box can touch that take part in the pass; a warp scan lays
+//               the (candidate, pixel) pairs out in candidate order;
+//   processing  the pairs go to the 32 lanes in order, so every lane evaluates a distinct pair.
+// Results per (sample, pixel) meet in the warp's shared scratch through shared-memory atomics:
+// the z-test winner as a 64-bit max of (inverse-depth bits, ~face), the soft product as a sum
+// of log factors (vanishing factors counted apart for the adjoint).
+
+constexpr uint32_t kFullMask = 0xffffffffu;
+
+// Per-warp shared scratch of the passes.
+template <int SPT>
+struct WarpScratch {
+  unsigned long long win[SPT][32];  // z-test winner of (sample, pixel): key bits << 32 | ~face, 0 = none
+  float logp[SPT][32];              // sum of log(1 - A_j) over the soft factors that do not vanish
+  int nzero[SPT][32];               // adjoint: vanishing soft factors
+  uint32_t pixs[32];                // samples each pixel takes part in, this pass
+  float ga[32];                     // adjoint: dL/dalpha / T of each pixel
+  int face[32];                     // current chunk of 32 candidates: face ids,
+  uint32_t pmask[32];               //   block pixels each may touch,
+  uint32_t smask[32];               //   samples each may touch,
+  int prefix[33];                   //   pair offsets
+};
+
+// Pixel geometry of a warp block.
+struct BlockPix {
+  int x0, y0, W, H;
+  // NDC centre of block pixel p (the same arithmetic for the owning lane and any other lane)
+  __device__ __forceinline__ void uv(int p, float& u, float& v) const {
+    const int px = x0 + (p & 7), py = y0 + (p >> 3);
+    u = (2.f * px + 1.f) / W - 1.f;
+    v = 1.f - (2.f * py + 1.f) / H;
+  }
+};
+
+// Block pixels whose centres lie in box (xmin, xmax, ymin, ymax).  The boxes are dilated by at
+// least kCoreMargin, far above the rounding of this arithmetic, so no pixel inside the
+// undilated region is lost.
+__device__ __forceinline__ uint32_t box_pixel_mask(const float4& b, const BlockPix& bp) {
+  const float hw = 0.5f * bp.W, hh = 0.5f * bp.H;
+  const float c0 = fminf(fmaxf(ceilf(fmaf(b.x + 1.f, hw, -0.5f)) - bp.x0, -1.f), 8.f);
+  const float c1 = fminf(fmaxf(floorf(fmaf(b.y + 1.f, hw, -0.5f)) - bp.x0, -1.f), 8.f);
+  const float r0 = fminf(fmaxf(ceilf(fmaf(1.f - b.w, hh, -0.5f)) - bp.y0, -1.f), 4.f);
+  const float r1 = fminf(fmaxf(floorf(fmaf(1.f - b.z, hh, -0.5f)) - bp.y0, -1.f), 4.f);
+  const int ic0 = max((int)c0, 0), ic1 = min((int)c1, 7), ir0 = max((int)r0, 0), ir1 = min((int)r1, 3);
+  if (ic0 > ic1 || ir0 > ir1) return 0u;
+  const uint32_t xm = (0xffu >> (7 - ic1)) & (0xffu << ic0);
+  const uint32_t rb = (0xfu >> (3 - ir1)) & (0xfu << ir0);
+  const uint32_t spread = (rb & 1u) | ((rb & 2u) << 7) | ((rb & 4u) << 14) | ((rb & 8u) << 21);
+  return xm * spread;
+}
+
+// position of the r-th (0-based) set bit of m; r < popc(m)
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int r) {
+  int pos = 0, c;
+  c = __popc(m & 0xffffu); if (r >= c) { r -= c; m >>= 16; pos += 16; }
+  c = __popc(m & 0xffu);   if (r >= c) { r -= c; m >>= 8;  pos += 8; }
+  c = __popc(m & 0xfu);    if (r >= c) { r -= c; m >>= 4;  pos += 4; }
+  c = __popc(m & 0x3u);    if (r >= c) { r -= c; m >>= 2;  pos += 2; }
+  c = (int)(m & 1u);       if (r >= c) { pos += 1; }
+  return pos;
+}
+
+// Walk a bin list (warp-collective): fn.pair(ok, face, p, samples) on every lane for each
+// batch of 32 pairs (ok false on lanes without a pair), then fn.batch_end(face or -1).
+// allowed[i] = pixels taking part for sample i; any_samples = OR of their samples.
+template <int SPT, bool MOVING, typename Fn>
+__device__ __forceinline__ void for_pairs(const TriRec* recs_set, const int32_t* list, int beg, int end,
+                                          const Group* grp, int n, const TileBox& tb, const BlockPix& bp, float m,
+                                          const uint32_t (&allowed)[SPT], uint32_t any_samples, WarpScratch<SPT>& ws,
+                                          Fn&& fn) {
+  const int lane = threadIdx.x & 31;
   for (int c0 = beg; c0 < end; c0 += 32) {
-    const int j = c0 + (int)(threadIdx.x & 31);
+    const int j = c0 + lane;
     int f = 0;
-    uint32_t mask = 0;
-    float4 box = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
+    uint32_t sm = 0, pm = 0;
     if (j < end && !tb.empty) {
       f = __ldg(list + j);
-      mask = candidate_meta<MOVING>(recs_set + f, grp, n, tb, m, box) & samples;
+      float4 box;
+      sm = candidate_meta<MOVING>(recs_set + f, grp, n, tb, m, box) & any_samples;
+      if (sm) {
+        uint32_t al = 0;
+#pragma unroll
+        for (int i = 0; i < SPT; ++i)
+          if (sm & (1u << i)) al |= allowed[i];
+        pm = box_pixel_mask(box, bp) & al;
+      }
     }
-    uint32_t live = __ballot_sync(0xffffffffu, mask != 0);
-    while (live) {
-      const int src = __ffs(live) - 1;
-      live &= live - 1;
-      const int fj = __shfl_sync(0xffffffffu, f, src);
-      const uint32_t mj = __shfl_sync(0xffffffffu, mask, src);
-      const float4 bj = shfl_box(box, src);
-      fn(fj, recs_set + fj, mj, bj);
+    int incl = __popc(pm);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFullMask, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(kFullMask, incl, 31);
+    if (total == 0) continue;
+    __syncwarp();  // the previous chunk's pairs are read
+    ws.face[lane] = f;
+    ws.pmask[lane] = pm;
+    ws.smask[lane] = sm;
+    ws.prefix[lane + 1] = incl;
+    if (lane == 0) ws.prefix[0] = 0;
+    __syncwarp();
+    for (int b = 0; b < total; b += 32) {
+      const int k = b + lane;
+      int face = -1, p = 0;
+      uint32_t smp = 0;
+      if (k < total) {
+        int jj = 0;  // last candidate whose first pair is at or before k
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+          if (ws.prefix[jj + step] <= k) jj += step;
+        p = nth_set_bit(ws.pmask[jj], k - ws.prefix[jj]);
+        face = ws.face[jj];
+        smp = ws.smask[jj] & ws.pixs[p];
+      }
+      fn.pair(smp != 0u, face, p, smp);
+      fn.batch_end(face);
     }
   }
+  __syncwarp();
 }
 
-// pass 1: z-test winners of the group's samples for this pixel (warp-collective).  COUNT
-// (measurement build): cnt[0] += coverage tests of this lane, cnt[1] += candidate steps of the warp.
-template <int SPT, bool MOVING, bool COUNT = false>
-__device__ __forceinline__ void pass_winners(const Group* grp, int n, const TriRec* recs_set, const int32_t* list,
-                                             int beg, int end,
-                                             const TileBox& tb, bool in_img, float u, float v, float (&bestk)[SPT],
-                                             int (&bestf)[SPT], uint32_t* cnt = nullptr) {
-#pragma unroll
-  for (int i = 0; i < SPT; ++i) {
-    bestk[i] = -INFINITY;
-    bestf[i] = -1;
-  }
-  for_warp_candidates<MOVING>(recs_set, list, beg, end, grp, n, tb, kCoreMargin, 0xffffffffu,
-                              [&](int face, const TriRec* src, uint32_t mask, const float4& box) {
-    if (COUNT && (threadIdx.x & 31) == 0) ++cnt[1];
-    if (!in_img || !in_box(box, u, v)) return;
-    if (COUNT) cnt[0] += __popc(mask & ((1u << n) - 1u));
+// pass 1: z-test winners (Sec. 3.1: coverage by the edge functions of Eq. time-dependent2, then
+// the perspective-correct depth; ties to the smaller face id) into ws.win.  COUNT: tests, batches.
+template <int SPT, bool MOVING, bool COUNT>
+struct CorePairs {
+  const TriRec* recs_set;
+  const Group* grp;
+  BlockPix bp;
+  WarpScratch<SPT>* ws;
+  uint32_t n_tests, n_batches;
+  __device__ __forceinline__ void pair(bool ok, int face, int p, uint32_t smp) {
+    if (!ok) return;
+    float u, v;
+    bp.uv(p, u, v);
     float4 r[kRecF4];
-    load_record<MOVING>(src, r, true, false);
+    load_record<MOVING>(recs_set + face, r, true, false);
     const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
-#pragma unroll
-    for (int i = 0; i < SPT; ++i) {
-      if (mask & (1u << i)) {
-        const float tau = MOVING ? __ldg(&grp->tau[i]) : 0.f;
-        const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
-        if (covers(e)) {
-          const float key = inv_depth<MOVING>(r, e, tau);
-          if (key > bestk[i] || (key == bestk[i] && face < bestf[i])) {
-            bestk[i] = key;
-            bestf[i] = face;
-          }
-        }
+    if (COUNT) n_tests += __popc(smp);
+    while (smp) {
+      const int i = __ffs(smp) - 1;
+      smp &= smp - 1u;
+      const float tau = MOVING ? __ldg(&grp->tau[i]) : 0.f;
+      const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
+      if (covers(e)) {
+        const float key = fmaxf(inv_depth<MOVING>(r, e, tau), 1e-30f);  // > 0 for covered samples
+        const unsigned long long packed =
+            ((unsigned long long)__float_as_uint(key) << 32) | (unsigned long long)(~(uint32_t)face);
+        atomicMax(&ws->win[i][p], packed);
       }
     }
-  });
-}
+  }
+  __device__ __forceinline__ void batch_end(int) {
+    if (COUNT && (threadIdx.x & 31) == 0) ++n_batches;
+  }
+};
 
-// Visit every soft-coverage term of the uncovered samples (uncov bit i) of this pixel:
-// fn.term(r, ps, e, sg, i, tau, X) for each (candidate, sample) with d <= r^2, bracketed by
-// fn.begin() and fn.end(face) per candidate; fn.eval() before each distance evaluation.
-// Warp-collective: begin/end run on every lane.
-template <int SPT, bool MOVING, typename Fn>
-__device__ __forceinline__ void for_soft_terms(const Group* grp, int n, uint32_t xbits, const TriRec* recs_set,
-                                               const int32_t* list, int beg, int end, const TileBox& tb,
-                                               bool active, float u, float v, uint32_t uncov, float r_soft, float r2,
-                                               Fn&& fn) {
-  const float m = r_soft + kCoreMargin;
-  const uint32_t warp_uncov = __reduce_or_sync(0xffffffffu, active ? uncov : 0u);
-  for_warp_candidates<MOVING>(recs_set, list, beg, end, grp, n, tb, m, warp_uncov,
-                              [&](int face, const TriRec* src, uint32_t mask_all, const float4& box) {
-    uint32_t mask = active ? (mask_all & uncov) : 0u;
-    fn.begin();
-    if (mask && in_box(box, u, v)) {
-      float4 r[kRecF4];
-      load_record<MOVING>(src, r, false, true);
-      const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
-      // one copy of the (large) soft-term code: walk the set sample bits
-      while (mask) {
-        const int i = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const float tau = MOVING ? __ldg(&grp->tau[i]) : 0.f;
-        if (MOVING && !in_box_at(r, tau, m, u, v)) continue;
-        const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
-        if (fabsf(e.D) <= kDetMin) continue;
-        const int X = (xbits >> i) & 1u;
-        fn.eval();
-        const SoftGeom sg = soft_geom<MOVING>(r, ps, e, tau, X);
-        if (sg.d <= r2) fn.term(r, ps, e, sg, i, tau, X);
-      }
-    }
-    fn.end(face);
-  });
+// Soft-coverage geometry of one pair and sample: false if the factor is outside the cutoff.
+template <bool MOVING>
+__device__ __forceinline__ bool soft_pair_term(const float4 (&r)[kRecF4], const PixelSetup<MOVING>& ps, float u,
+                                               float v, float tau, int X, float m, float r2, EdgeVals& e,
+                                               SoftGeom& sg) {
+  if (MOVING && !in_box_at(r, tau, m, u, v)) return false;
+  e = edge_vals<MOVING>(r, ps, tau);
+  if (fabsf(e.D) <= kDetMin) return false;
+  sg = soft_geom<MOVING>(r, ps, e, tau, X);
+  return sg.d <= r2;
 }
 
 // Persistent scheduling.  A unit is one split of the sample groups (a contiguous range of
