@@ -170,8 +170,7 @@ struct BwdSoftLogPairs {
   float m, r2, inv_delta;
   __device__ __forceinline__ void pair(bool ok, int face, int p, uint32_t smp) {
     if (!ok) return;
-    float u, v;
-    bp.uv(p, u, v);
+    const float u = ws->pu[p], v = ws->pv[p];
     float4 r[kRecF4];
     load_record<MOVING>(recs_set + face, r, false, true);
     const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
@@ -182,7 +181,8 @@ struct BwdSoftLogPairs {
       EdgeVals e;
       SoftGeom sg;
       if (!soft_pair_term<MOVING>(r, ps, u, v, tau, (xbits >> i) & 1u, m, r2, e, sg)) continue;
-      const float f = -expm1f(-sg.d * inv_delta);
+      float A;
+      const float f = soft_factor(sg.d, inv_delta, A);
       if (f > kTinyFactor) atomicAdd(&ws->logp[i][p], __logf(f));
       else atomicAdd(&ws->nzero[i][p], 1);
     }
@@ -209,8 +209,7 @@ struct BwdSoftGradPairs {
 #pragma unroll
     for (int q = 0; q < 3; ++q) gax[q] = gay[q] = gbx[q] = gby[q] = 0.f;
     if (!ok) return;
-    float u, v;
-    bp.uv(p, u, v);
+    const float u = ws->pu[p], v = ws->pv[p];
     float4 r[kRecF4];
     load_record<MOVING>(recs_set + face, r, false, true);
     const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
@@ -223,8 +222,8 @@ struct BwdSoftGradPairs {
       EdgeVals e;
       SoftGeom sg;
       if (!soft_pair_term<MOVING>(r, ps, u, v, tau, X, m, r2, e, sg)) continue;
-      const float f = -expm1f(-sg.d * inv_delta);
-      const float A = __expf(-sg.d * inv_delta);
+      float A;
+      const float f = soft_factor(sg.d, inv_delta, A);
       const float S = ws->logp[i][p];
       const int nz = ws->nzero[i][p];
       float excl;
@@ -429,6 +428,8 @@ __device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile
   const bool in_img = px < P.W && py < P.H;
   float u, v;
   bp.uv(lane, u, v);
+  ws.pu[lane] = u;
+  ws.pv[lane] = v;
   const TileBox tb = PixelMap<TW, TH>::warp_box(tx, ty, wb, P.W, P.H);
   const int g_begin = (int)((long long)P.G * split / P.n_split);
   const int g_end = (int)((long long)P.G * (split + 1) / P.n_split);

@@ -278,8 +278,7 @@ struct FwdSoftPairs {
   uint32_t n_terms, n_eval, n_batches;
   __device__ __forceinline__ void pair(bool ok, int face, int p, uint32_t smp) {
     if (!ok) return;
-    float u, v;
-    bp.uv(p, u, v);
+    const float u = ws->pu[p], v = ws->pv[p];
     float4 r[kRecF4];
     load_record<MOVING>(recs_set + face, r, false, true);
     const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
@@ -291,7 +290,8 @@ struct FwdSoftPairs {
       EdgeVals e;
       SoftGeom sg;
       if (!soft_pair_term<MOVING>(r, ps, u, v, tau, (xbits >> i) & 1u, m, r2, e, sg)) continue;
-      const float f = -expm1f(-sg.d * inv_delta);
+      float A;
+      const float f = soft_factor(sg.d, inv_delta, A);
       atomicAdd(&ws->logp[i][p], __logf(f));
       if (COUNT) ++n_terms;
     }
@@ -316,6 +316,8 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
   const bool in_img = px < P.W && py < P.H;
   float u, v;
   bp.uv(lane, u, v);
+  ws.pu[lane] = u;
+  ws.pv[lane] = v;
   const TileBox tb = PixelMap<TW, TH>::warp_box(tx, ty, wb, P.W, P.H);
   const int g_begin = (int)((long long)P.G * split / P.n_split);
   const int g_end = (int)((long long)P.G * (split + 1) / P.n_split);

@@ -288,6 +288,7 @@ struct WarpScratch {
   float logp[SPT][32];              // sum of log(1 - A_j) over the soft factors that do not vanish
   int nzero[SPT][32];               // adjoint: vanishing soft factors
   uint32_t pixs[32];                // samples each pixel takes part in, this pass
+  float pu[32], pv[32];             // NDC centre of each pixel (written by its own lane)
   float ga[32];                     // adjoint: dL/dalpha / T of each pixel
   int face[32];                     // current chunk of 32 candidates: face ids,
   uint32_t pmask[32];               //   block pixels each may touch,
@@ -298,13 +299,23 @@ struct WarpScratch {
 // Pixel geometry of a warp block.
 struct BlockPix {
   int x0, y0, W, H;
-  // NDC centre of block pixel p (the same arithmetic for the owning lane and any other lane)
+  // NDC centre of block pixel p (computed by the owning lane; other lanes read it from the
+  // warp's scratch, so every lane sees the same values)
   __device__ __forceinline__ void uv(int p, float& u, float& v) const {
     const int px = x0 + (p & 7), py = y0 + (p >> 3);
     u = (2.f * px + 1.f) / W - 1.f;
     v = 1.f - (2.f * py + 1.f) / H;
   }
 };
+
+// Soft-coverage factor 1 - A, A = exp(-d / delta) (Eq. probability-function).  A is computed
+// with the fast exponential: its relative error (~1e-6) changes alpha = 1 - prod(1 - A_j) by at
+// most about that much in absolute terms, because each factor's absolute error passes through
+// the product scaled by the other factors (all <= 1).
+__device__ __forceinline__ float soft_factor(float d, float inv_delta, float& A) {
+  A = __expf(-d * inv_delta);
+  return 1.f - A;
+}
 
 // Block pixels whose centres lie in box (xmin, xmax, ymin, ymax).  The boxes are dilated by at
 // least kCoreMargin, far above the rounding of this arithmetic, so no pixel inside the
@@ -405,8 +416,7 @@ struct CorePairs {
   uint32_t n_tests, n_batches;
   __device__ __forceinline__ void pair(bool ok, int face, int p, uint32_t smp) {
     if (!ok) return;
-    float u, v;
-    bp.uv(p, u, v);
+    const float u = ws->pu[p], v = ws->pv[p];
     float4 r[kRecF4];
     load_record<MOVING>(recs_set + face, r, true, false);
     const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
