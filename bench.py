@@ -145,6 +145,65 @@ def cpu_baseline():
                       f"all 64 sub-frames, single thread, {dt:.1f} s"}
 
 
+def extra_workloads(mbr, scenes, torch, np, world):
+    """Context lines for the other workloads (same metric; not the headline): an 8-view shape-recovery
+    iteration (c3), a 32-object batch (c4) and the 1024^2 / 100k-face / T=256 render (c5)."""
+    from paper_2602_07860_gb300.recovery import ViewBatch
+    out = {}
+
+    def timeit(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps * 1e3
+
+    # c3: one iteration of the recovery loop's renders (8 views, forward + adjoint, batched)
+    views_sc, template = scenes.config3()
+    s0 = views_sc[0]
+    dev = "cuda"
+    tv = torch.as_tensor(np.asarray(template, np.float32), device=dev).contiguous()
+    tf = torch.as_tensor(np.asarray(s0["faces"], np.int32), device=dev).contiguous()
+    ta = torch.as_tensor(np.asarray(s0["albedo"], np.float32), device=dev).contiguous()
+    views = [(mbr.motion_from_dict(s["motion"]), mbr.camera_from_dict(s["camera"])) for s in views_sc]
+    vb = ViewBatch(tv, tf, ta, views, s0["T"], s0["H"], s0["W"], "fast")
+    g = torch.randn((len(views), s0["H"], s0["W"], 4), device=dev, generator=torch.Generator(dev).manual_seed(5))
+    ms = timeit(lambda: (vb.forward(), vb.backward(g)), 5)
+    n = len(views) * s0["H"] * s0["W"] * s0["T"]
+    out["c3_recovery_iteration"] = {"ms": ms, "samples_per_s": world * n / (ms / 1e3), "views": len(views),
+                                    "workload": "8 views (4 translations, 4 rotations), 2562 v, T=64, 256x256"}
+    # c4: 32 objects of mixed size in one batched forward + adjoint
+    items, n = [], 0
+    ctx = mbr.Context()
+    for s in scenes.config4():
+        vv, ff, aa = mbr.mesh_tensors(s)
+        n += s["H"] * s["W"] * s["T"]
+        items.append(dict(verts=vv, faces=ff, albedo=aa, motion=mbr.motion_from_dict(s["motion"]),
+                          camera=mbr.camera_from_dict(s["camera"]), T=s["T"], H=s["H"], W=s["W"], solver="fast",
+                          image=torch.zeros((s["H"], s["W"], 4), device=dev),
+                          dl_dimage=torch.ones((s["H"], s["W"], 4), device=dev),
+                          dl_dverts=torch.zeros_like(vv), dl_dalbedo=torch.zeros_like(aa)))
+    ms = timeit(lambda: ctx.render_batch(items, True), 3)
+    out["c4_batch_32_objects"] = {"ms": ms, "samples_per_s": world * n / (ms / 1e3), "samples": n,
+                                  "workload": "32 objects, subdiv 2-5, T in {16..256}, 128-512 px, one graph replay"}
+    # c5: the large render, both solvers
+    s = scenes.config5()
+    vv, ff, aa = mbr.mesh_tensors(s)
+    mo, ca = mbr.motion_from_dict(s["motion"]), mbr.camera_from_dict(s["camera"])
+    T, H, W = s["T"], s["H"], s["W"]
+    G5 = torch.ones((H, W, 4), device=dev)
+    ctx5 = mbr.Context()
+    c5 = {"workload": f"surface of revolution {ff.shape[0]} faces, 8 turns, T=256, 1024x1024, 96 segments"}
+    for solver in ("fast", "plain"):
+        ms = timeit(lambda: (ctx5.render_blur(vv, ff, aa, mo, ca, T, H, W, solver),
+                             ctx5.render_blur_backward(vv, ff, aa, mo, ca, T, H, W, G5, solver)), 2)
+        c5[solver] = {"fwdbwd_ms": ms, "samples_per_s": world * H * W * T / (ms / 1e3)}
+    out["c5_large"] = c5
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -152,6 +211,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mbr", choices=["mbr", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-workloads", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -183,13 +243,16 @@ def main():
         return float(t.item())
 
     ctx = mbr.Context()
-    ctx_spt = 2  # sub-frames per group of the fast solver (the autotuner's pick for this workload)
-    ctx.set_tuning(16, ctx_spt, 0)
     sc = scenes.config2()
     T, H, W = sc["T"], sc["H"], sc["W"]
     v, f, a = mbr.mesh_tensors(sc)
     mo, ca = mbr.motion_from_dict(sc["motion"]), mbr.camera_from_dict(sc["camera"])
     G = torch.as_tensor(np.random.default_rng(11).normal(size=(H, W, 4)).astype(np.float32), device="cuda")
+    # tile shape and sub-frames per group from the library's autotuner (untimed), kept on ctx
+    tune_item = dict(verts=v, faces=f, albedo=a, motion=mo, camera=ca, T=T, H=H, W=W, solver="fast",
+                     image=torch.zeros((H, W, 4), device="cuda"), dl_dimage=G, dl_dverts=torch.zeros_like(v),
+                     dl_dalbedo=torch.zeros_like(a))
+    tile, ctx_spt, _ = ctx.autotune([tune_item], True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     n_samples = H * W * T
 
@@ -274,7 +337,7 @@ def main():
         "speedup_fast_over_plain_fwd": plain_f / fast_f,
         "plain_raster_fwd_ms": p_fwd, "plain_raster_bwd_ms": p_bwd,
         "plain_fwd_frac": p_fwd_tf / peak, "plain_bwd_frac": p_bwd_tf / peak, "plain_units": p_units,
-        "tuning": {"tile": 16, "spt": ctx_spt, "splits": "auto"},
+        "tuning": {"tile": tile, "spt": ctx_spt, "splits": "auto", "chosen_by": "mbr_autotune"},
         "paper_context": "paper: up to 4.57x fwd+grad speedup vs SoftRas on one RTX 4090 (different workload)",
     }
 
@@ -309,6 +372,9 @@ def main():
     d2h = sum(t.numel() * t.element_size() for t in (out_img, out_gv, out_ga))
     e2e = {"value": world * n_samples * k2 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s / k2}
+
+    if not args.no_extra_workloads:
+        extras.update(extra_workloads(mbr, scenes, torch, np, world))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
