@@ -131,7 +131,7 @@ int mbr_render_blur_batch(mbr_ctx* ctx, int32_t n, const mbr_item* items, int32_
                           void* cuda_stream);
 
 /* Autotuner: times mbr_render_blur_batch on these items for every candidate tile shape (16x16,
- * 8x8 pixels) and, when a fast-solver item is present, sub-frames per group (1, 2, 4, 8), keeps
+ * 8x8 pixels) and, when a fast-solver item is present, sub-frames per group (1, 2, 4), keeps
  * the fastest on the context (as mbr_set_tuning would) and reports it.  Any out pointer may be
  * NULL.  The items are rendered several times (their outputs are overwritten). */
 int mbr_autotune(mbr_ctx* ctx, int32_t n, const mbr_item* items, int32_t with_backward,
@@ -168,7 +168,7 @@ int mbr_count_work(mbr_ctx* ctx, const mbr_mesh* mesh, const mbr_motion* motion,
                    void* cuda_stream);
 
 /* Tuning knobs (autotuner): tile edge in pixels (8 or 16), sub-frames per thread for the fast
- * solver (1..8, default 2), and the number of sub-frame group splits of the raster work units
+ * solver (1..4, default 2), and the number of sub-frame group splits of the raster work units
  * (0 = automatic: about 64 units per SM). */
 int mbr_set_tuning(mbr_ctx* ctx, int32_t tile, int32_t spt, int32_t splits);
 

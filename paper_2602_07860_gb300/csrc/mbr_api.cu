@@ -776,8 +776,8 @@ int mbr_autotune(mbr_ctx* c, int32_t n, const mbr_item* items, int32_t with_back
   bool any_fast = false;
   for (int i = 0; i < n; ++i) any_fast |= items[i].solver == MBR_FAST;
   const int tiles[2] = {16, 8};
-  const int spts_fast[4] = {1, 2, 4, 8};
-  const int n_spt = any_fast ? 4 : 1;
+  const int spts_fast[3] = {1, 2, 4};
+  const int n_spt = any_fast ? 3 : 1;
   const int saved_tile = c->tile, saved_spt = c->spt, saved_splits = c->splits;
   cudaEvent_t e0, e1;
   CUDA_TRY(c, cudaEventCreate(&e0));

@@ -257,12 +257,13 @@ struct BwdSoftGradPairs {
         vals[6 + 2 * q + 1] = gby[q];
       }
     }
-#pragma unroll
+#pragma unroll 1
     for (int o = 1; o < 32; o <<= 1) {
+      const bool take = lane + o < seg_end;
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
         const float y = __shfl_down_sync(kFullMask, vals[q], o);
-        if (lane + o < seg_end) vals[q] += y;
+        if (take) vals[q] += y;
       }
     }
     if (head) {
@@ -389,15 +390,34 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
   const int fl = __shfl_sync(0xffffffffu, f, leader);
   const bool uniform = __all_sync(0xffffffffu, !has || f == fl) && __popc(hmask) > 1;
   if (uniform) {
+    // one butterfly over all contributions; the offsets loop stays rolled to keep the adjoint's
+    // code small (the kernel is bound by instruction fetch, not by these few instructions)
+    constexpr int NV = MOVING ? 39 : 24;
+    float x[NV];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      ca[q] = make_float4(warp_sum(ca[q].x), warp_sum(ca[q].y), warp_sum(ca[q].z), warp_sum(ca[q].w));
-      ca_z[q] = warp_sum(ca_z[q]);
+      x[5 * q] = ca[q].x; x[5 * q + 1] = ca[q].y; x[5 * q + 2] = ca[q].z; x[5 * q + 3] = ca[q].w;
+      x[5 * q + 4] = ca_z[q];
+      x[15 + 3 * q] = cal[q].x; x[16 + 3 * q] = cal[q].y; x[17 + 3 * q] = cal[q].z;
       if (MOVING) {
-        cb[q] = make_float4(warp_sum(cb[q].x), warp_sum(cb[q].y), warp_sum(cb[q].z), warp_sum(cb[q].w));
-        cb_z[q] = warp_sum(cb_z[q]);
+        x[24 + 5 * q] = cb[q].x; x[25 + 5 * q] = cb[q].y; x[26 + 5 * q] = cb[q].z; x[27 + 5 * q] = cb[q].w;
+        x[28 + 5 * q] = cb_z[q];
       }
-      if (P.g_albedo) cal[q] = make_float4(warp_sum(cal[q].x), warp_sum(cal[q].y), warp_sum(cal[q].z), 0.f);
+    }
+#pragma unroll 1
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) x[k] += __shfl_xor_sync(0xffffffffu, x[k], o);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      ca[q] = make_float4(x[5 * q], x[5 * q + 1], x[5 * q + 2], x[5 * q + 3]);
+      ca_z[q] = x[5 * q + 4];
+      cal[q] = make_float4(x[15 + 3 * q], x[16 + 3 * q], x[17 + 3 * q], 0.f);
+      if (MOVING) {
+        cb[q] = make_float4(x[24 + 5 * q], x[25 + 5 * q], x[26 + 5 * q], x[27 + 5 * q]);
+        cb_z[q] = x[28 + 5 * q];
+      }
     }
   }
   if (uniform ? lane == leader : has) {
@@ -630,10 +650,8 @@ template <int TW, int TH, int KIND>
 static void launch_bwd_spt(const WorkQueue& Q, int spt, int grid, cudaStream_t st) {
   if (spt <= 2)
     raster_bwd_persistent<TW, TH, 2, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
-  else if (spt <= 4)
-    raster_bwd_persistent<TW, TH, 4, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
   else
-    raster_bwd_persistent<TW, TH, 8, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
+    raster_bwd_persistent<TW, TH, 4, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
 }
 
 template <int TW, int TH>
@@ -664,12 +682,9 @@ static int occupancy_of(K kernel) {
 template <int TW, int TH>
 static int occ_bwd(int spt, int kind) {
   if (kind == 0) return occupancy_of(raster_bwd_persistent<TW, TH, 1, 0>);
-  const int sp = spt <= 2 ? 2 : (spt <= 4 ? 4 : 8);
   if (kind == 1)
-    return sp == 2 ? occupancy_of(raster_bwd_persistent<TW, TH, 2, 1>)
-                   : sp == 4 ? occupancy_of(raster_bwd_persistent<TW, TH, 4, 1>) : occupancy_of(raster_bwd_persistent<TW, TH, 8, 1>);
-  return sp == 2 ? occupancy_of(raster_bwd_persistent<TW, TH, 2, 2>)
-                 : sp == 4 ? occupancy_of(raster_bwd_persistent<TW, TH, 4, 2>) : occupancy_of(raster_bwd_persistent<TW, TH, 8, 2>);
+    return spt <= 2 ? occupancy_of(raster_bwd_persistent<TW, TH, 2, 1>) : occupancy_of(raster_bwd_persistent<TW, TH, 4, 1>);
+  return spt <= 2 ? occupancy_of(raster_bwd_persistent<TW, TH, 2, 2>) : occupancy_of(raster_bwd_persistent<TW, TH, 4, 2>);
 }
 
 int persistent_grid_bwd(int num_sms, int tile, int spt, int kind) {

@@ -15,7 +15,7 @@
 
 namespace mbr {
 
-constexpr int kMaxSpt = 8;            // samples per group (max)
+constexpr int kMaxSpt = 4;            // samples per group (max)
 constexpr float kDetMin = 1e-10f;     // |det F| at or below: triangle skipped at that sample
 constexpr int kRecF4 = 11;            // float4s per triangle record
 constexpr int kRecF4Static = 4;       // float4s a static (plain-solver) record needs

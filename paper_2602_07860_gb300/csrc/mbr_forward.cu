@@ -632,10 +632,8 @@ template <int TW, int TH, int KIND>
 static void launch_fwd_spt(const WorkQueue& Q, int spt, int grid, cudaStream_t st) {
   if (spt <= 2)
     raster_fwd_persistent<TW, TH, 2, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
-  else if (spt <= 4)
-    raster_fwd_persistent<TW, TH, 4, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
   else
-    raster_fwd_persistent<TW, TH, 8, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
+    raster_fwd_persistent<TW, TH, 4, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
 }
 
 template <int TW, int TH>
@@ -658,12 +656,9 @@ static int occupancy_of(K kernel) {
 template <int TW, int TH>
 static int occ_fwd(int spt, int kind) {
   if (kind == 0) return occupancy_of(raster_fwd_persistent<TW, TH, 1, 0>);
-  const int sp = spt <= 2 ? 2 : (spt <= 4 ? 4 : 8);
   if (kind == 1)
-    return sp == 2 ? occupancy_of(raster_fwd_persistent<TW, TH, 2, 1>)
-                   : sp == 4 ? occupancy_of(raster_fwd_persistent<TW, TH, 4, 1>) : occupancy_of(raster_fwd_persistent<TW, TH, 8, 1>);
-  return sp == 2 ? occupancy_of(raster_fwd_persistent<TW, TH, 2, 2>)
-                 : sp == 4 ? occupancy_of(raster_fwd_persistent<TW, TH, 4, 2>) : occupancy_of(raster_fwd_persistent<TW, TH, 8, 2>);
+    return spt <= 2 ? occupancy_of(raster_fwd_persistent<TW, TH, 2, 1>) : occupancy_of(raster_fwd_persistent<TW, TH, 4, 1>);
+  return spt <= 2 ? occupancy_of(raster_fwd_persistent<TW, TH, 2, 2>) : occupancy_of(raster_fwd_persistent<TW, TH, 4, 2>);
 }
 
 int persistent_grid_fwd(int num_sms, int tile, int spt, int kind) {
@@ -699,8 +694,7 @@ void launch_raster_count(const WorkQueue& Q, int spt, int kind, int grid, cudaSt
   if (Q.n_work <= 0) return;
   if (kind == 0) raster_fwd_count<1, 0><<<grid, kPersistentThreads, 0, st>>>(Q);
   else if (spt <= 2) raster_fwd_count<2, 1><<<grid, kPersistentThreads, 0, st>>>(Q);
-  else if (spt <= 4) raster_fwd_count<4, 1><<<grid, kPersistentThreads, 0, st>>>(Q);
-  else raster_fwd_count<8, 1><<<grid, kPersistentThreads, 0, st>>>(Q);
+  else raster_fwd_count<4, 1><<<grid, kPersistentThreads, 0, st>>>(Q);
 }
 
 void launch_count(const TriRec* recs, int F, const Group* groups, int G, int W, int H, float r,

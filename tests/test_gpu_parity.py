@@ -64,7 +64,7 @@ def test_winner_ids_bit_exact(ctx, solver):
         assert (ids >= 0).sum() > 50
 
 
-@pytest.mark.parametrize("tile,spt", [(16, 8), (8, 4), (16, 1), (8, 2)])
+@pytest.mark.parametrize("tile,spt", [(16, 4), (8, 4), (16, 1), (8, 2)])
 def test_tuning_variants_agree(ctx, tile, spt):
     sc = scenes.small_scene("rotate", subdiv=2, T=20, H=45, W=61)
     ref = gpu_render(ctx, sc, "fast")
