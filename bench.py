@@ -198,7 +198,7 @@ def extra_workloads(mbr, scenes, torch, np, world):
     c5 = {"workload": f"surface of revolution {ff.shape[0]} faces, 8 turns, T=256, 1024x1024, 96 segments"}
     for solver in ("fast", "plain"):
         ms = timeit(lambda: (ctx5.render_blur(vv, ff, aa, mo, ca, T, H, W, solver),
-                             ctx5.render_blur_backward(vv, ff, aa, mo, ca, T, H, W, G5, solver)), 2)
+                             ctx5.render_blur_backward(vv, ff, aa, mo, ca, T, H, W, G5, solver, reuse_forward=True)), 2)
         c5[solver] = {"fwdbwd_ms": ms, "samples_per_s": world * H * W * T / (ms / 1e3)}
     out["c5_large"] = c5
     return out
@@ -257,9 +257,10 @@ def main():
     n_samples = H * W * T
 
     def step(solver, bwd=True):
+        # forward, then the adjoint as the autograd path runs it (reusing the forward's front half)
         ctx.render_blur(v, f, a, mo, ca, T, H, W, solver)
         if bwd:
-            ctx.render_blur_backward(v, f, a, mo, ca, T, H, W, G, solver)
+            ctx.render_blur_backward(v, f, a, mo, ca, T, H, W, G, solver, reuse_forward=True)
 
     def timed(solver, bwd, steps, warmup):
         for _ in range(warmup):
@@ -354,7 +355,7 @@ def main():
         da.copy_(ha, non_blocking=True)
         dG.copy_(hG, non_blocking=True)
         img = ctx.render_blur(dv, df, da, mo, ca, T, H, W, "fast")
-        gv, ga = ctx.render_blur_backward(dv, df, da, mo, ca, T, H, W, dG, "fast")
+        gv, ga = ctx.render_blur_backward(dv, df, da, mo, ca, T, H, W, dG, "fast", reuse_forward=True)
         out_img.copy_(img, non_blocking=True)
         out_gv.copy_(gv, non_blocking=True)
         out_ga.copy_(ga, non_blocking=True)
@@ -385,6 +386,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "solver": "fast", "l2": "flushed between steps (256 MiB write)",
+                           "step": "mbr_render_blur + mbr_render_blur_backward_reuse (the autograd path)",
                            "parallelism": f"{world} independent replica(s)"},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
                 "cpu_baseline": cpu, "extras": extras}

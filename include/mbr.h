@@ -116,6 +116,20 @@ int mbr_render_blur_backward(mbr_ctx* ctx, const mbr_mesh* mesh, const mbr_motio
                              int32_t solver, const float* dl_dimage, float* dl_dverts,
                              float* dl_dalbedo, void* cuda_stream);
 
+/* The adjoint of the immediately preceding mbr_render_blur on the same context: like
+ * mbr_render_blur_backward (same arguments, same results), but when no other call has used the
+ * context since that forward and every argument equals the forward's (the same mesh pointers and
+ * sizes, motion, camera, T, H, W, solver and tuning), the forward's front half -- vertex states,
+ * triangle records, tile bins, unit order -- is reused instead of recomputed, which also saves
+ * the binning's stream synchronisation.  Otherwise it recomputes, exactly as
+ * mbr_render_blur_backward.  The CALLER guarantees that the contents of verts, faces and albedo
+ * have not changed since the forward (the library compares pointers, not contents); PyTorch's
+ * saved-tensor version check gives that guarantee to the autograd path. */
+int mbr_render_blur_backward_reuse(mbr_ctx* ctx, const mbr_mesh* mesh, const mbr_motion* motion,
+                                   const mbr_camera* camera, int32_t T, int32_t H, int32_t W, int32_t solver,
+                                   const float* dl_dimage, float* dl_dverts, float* dl_dalbedo,
+                                   void* cuda_stream);
+
 /* Render n independent items (objects, motions, solvers, sub-frame counts and resolutions may
  * differ), forward and, if with_backward != 0, the adjoint too.  The front halves of all items run
  * first, one stream sync sizes every item's tile lists, then a single persistent raster launch
@@ -182,6 +196,7 @@ typedef struct {
   int64_t raster_bwd_count;  /* adjoint raster launches timed                                  */
   int32_t n_split;           /* sub-frame group splits of the last raster launch                */
   int32_t groups;            /* sample groups of the last call                                   */
+  int64_t reused;            /* adjoint calls that reused the forward's front half (cumulative)  */
 } mbr_stats;
 
 /* Switch CUDA-event timing of the raster kernels on (1, and reset the sums) or off (0).  Events

@@ -15,7 +15,8 @@ MBR_TRANSLATE, MBR_ROTATE = 0, 1
 MBR_TIME_PAPER, MBR_TIME_MIDPOINT = 0, 1
 SOLVERS = {"plain": MBR_PLAIN, "fast": MBR_FAST}
 
-EXPORTS = ["mbr_create", "mbr_destroy", "mbr_render_blur", "mbr_render_blur_backward", "mbr_render_blur_batch",
+EXPORTS = ["mbr_create", "mbr_destroy", "mbr_render_blur", "mbr_render_blur_backward",
+           "mbr_render_blur_backward_reuse", "mbr_render_blur_batch",
            "mbr_debug_winners", "mbr_count_candidates", "mbr_count_work", "mbr_set_tuning", "mbr_set_profiling", "mbr_get_stats",
            "mbr_render_blur_noalloc", "mbr_autotune", "mbr_last_error"]
 
@@ -43,7 +44,7 @@ class MbrItem(ctypes.Structure):
 class MbrStats(ctypes.Structure):
     _fields_ = [("launches", c_int64), ("bin_entries", c_int64), ("raster_fwd_ms", ctypes.c_double),
                 ("raster_bwd_ms", ctypes.c_double), ("raster_fwd_count", c_int64), ("raster_bwd_count", c_int64),
-                ("n_split", c_int32), ("groups", c_int32)]
+                ("n_split", c_int32), ("groups", c_int32), ("reused", c_int64)]
 
 
 class MbrError(RuntimeError):
@@ -80,6 +81,8 @@ def load(build_if_missing=True):
     L.mbr_render_blur.restype = c_int32
     L.mbr_render_blur_backward.argtypes = common + [c_void_p, c_void_p, c_void_p, c_void_p]
     L.mbr_render_blur_backward.restype = c_int32
+    L.mbr_render_blur_backward_reuse.argtypes = common + [c_void_p, c_void_p, c_void_p, c_void_p]
+    L.mbr_render_blur_backward_reuse.restype = c_int32
     L.mbr_debug_winners.argtypes = common + [c_int32, c_void_p, c_void_p]
     L.mbr_debug_winners.restype = c_int32
     L.mbr_count_candidates.argtypes = common + [P(c_int64), c_void_p]

@@ -33,6 +33,16 @@ struct BinSet {
 };
 
 struct BatchState;  // batched renders (defined with mbr_render_blur_batch)
+struct Prepared;    // front half of one render (defined below)
+
+// arguments of the last mbr_render_blur, whose front half the adjoint may reuse
+struct LastForward {
+  bool valid = false;
+  mbr_mesh mesh;
+  mbr_motion motion;
+  mbr_camera cam;
+  int T = 0, H = 0, W = 0, solver = 0, tile = 0, spt = 0, splits = 0;
+};
 
 }  // namespace
 
@@ -53,8 +63,12 @@ struct mbr_ctx {
   DevBuf queue;
   void* host_queue = nullptr;
   size_t host_queue_cap = 0;
+  cudaEvent_t queue_copied = nullptr;  // recorded after each copy out of host_queue
   // batch plans (mbr_render_blur_batch): arena per plan, captured graph, pinned staging
   BatchState* batch = nullptr;
+  // the last forward's front half (records, bins, unit order, normals stay in the buffers above)
+  LastForward last;
+  Prepared* last_pp = nullptr;
   // measurement: one event pair per raster kind (0 forward, 1 adjoint), harvested lazily
   bool profiling = false;
   cudaEvent_t ev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -332,6 +346,7 @@ int build_tables(mbr_ctx* c, const mbr_motion* motion, const mbr_camera* cam, in
 // the triangle setup.
 int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mbr_camera* cam, int T, int H,
             int W, int solver, cudaStream_t st, bool do_bins, Prepared& pp) {
+  c->last.valid = false;  // the buffers are about to be rewritten
   std::vector<SlotXform> xf;
   std::vector<int2> sets;
   std::vector<Group> groups;
@@ -500,6 +515,9 @@ int upload_queue(mbr_ctx* c, const RasterParams* items, int n, cudaStream_t st, 
   const size_t total = cnt_at + 256;
   int rc;
   if ((rc = ensure(c, c->queue, total, st))) return rc;
+  // the previous copy out of the pinned staging buffer may still be queued (a reused front half
+  // skips the binning sync): wait for it before rewriting the buffer
+  if (c->queue_copied) CUDA_TRY(c, cudaEventSynchronize(c->queue_copied));
   if (total > c->host_queue_cap) {
     CUDA_TRY(c, cudaStreamSynchronize(st));
     if (c->host_queue) cudaFreeHost(c->host_queue);
@@ -516,6 +534,8 @@ int upload_queue(mbr_ctx* c, const RasterParams* items, int n, cudaStream_t st, 
   for (int i = 0; i < n; ++i) off[i + 1] = off[i] + items[i].work;
   char* d = (char*)c->queue.p;
   CUDA_TRY(c, cudaMemcpyAsync(d, h, cnt_at, cudaMemcpyHostToDevice, st));
+  if (!c->queue_copied) CUDA_TRY(c, cudaEventCreateWithFlags(&c->queue_copied, cudaEventDisableTiming));
+  CUDA_TRY(c, cudaEventRecord(c->queue_copied, st));
   CUDA_TRY(c, cudaMemsetAsync(d + cnt_at, 0, sizeof(int32_t), st));
   Q.items = (const RasterParams*)d;
   Q.item_off = (const int32_t*)(d + off_at);
@@ -556,6 +576,87 @@ int forward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, con
   if ((rc = time_end(c, 0, st))) return rc;
   c->stats.launches += 1;
   c->stats.n_split = pp.n_split;
+  if (image && !dbg_ids) {
+    if (!c->last_pp) c->last_pp = new (std::nothrow) Prepared();
+    if (c->last_pp) {
+      *c->last_pp = pp;
+      LastForward& L = c->last;
+      L.mesh = *mesh;
+      L.motion = *motion;
+      L.cam = *cam;
+      L.T = T; L.H = H; L.W = W; L.solver = solver;
+      L.tile = c->tile; L.spt = c->spt; L.splits = c->splits;
+      L.valid = true;
+    }
+  }
+  return MBR_OK;
+}
+
+// field-by-field equality (padding bytes of the caller's structs are not compared)
+bool same_motion(const mbr_motion& a, const mbr_motion& b) {
+  for (int i = 0; i < 3; ++i)
+    if (a.offset[i] != b.offset[i] || a.dir[i] != b.dir[i] || a.axis[i] != b.axis[i]) return false;
+  return a.kind == b.kind && a.segments == b.segments && a.omega == b.omega;
+}
+
+bool same_camera(const mbr_camera& a, const mbr_camera& b) {
+  for (int i = 0; i < 12; ++i)
+    if (a.view[i] != b.view[i]) return false;
+  for (int i = 0; i < 3; ++i)
+    if (a.light_dir[i] != b.light_dir[i]) return false;
+  return a.tan_half_fov == b.tan_half_fov && a.znear == b.znear && a.k_ambient == b.k_ambient &&
+         a.k_diffuse == b.k_diffuse && a.delta == b.delta && a.time_rule == b.time_rule;
+}
+
+bool matches_last_forward(const mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mbr_camera* cam,
+                          int T, int H, int W, int solver) {
+  const LastForward& L = c->last;
+  return L.valid && c->last_pp && L.mesh.V == mesh->V && L.mesh.F == mesh->F && L.mesh.verts == mesh->verts &&
+         L.mesh.faces == mesh->faces && L.mesh.albedo == mesh->albedo && same_motion(L.motion, *motion) &&
+         same_camera(L.cam, *cam) && L.T == T && L.H == H && L.W == W && L.solver == solver && L.tile == c->tile &&
+         L.spt == c->spt && L.splits == c->splits;
+}
+
+// the adjoint (a9): front half (recomputed, or the last forward's when reuse is allowed and it
+// matches), adjoint raster, slot -> vertex chain, normals adjoint
+int backward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mbr_camera* cam, int T, int H,
+                  int W, int solver, const float* dl_dimage, float* dl_dverts, float* dl_dalbedo, cudaStream_t st,
+                  bool reuse) {
+  int rc = validate(c, mesh, motion, cam, T, H, W, solver);
+  if (rc) return rc;
+  if (!dl_dimage || !dl_dverts) return fail(c, MBR_ERR_ARG, "null gradient buffer");
+  Prepared pp;
+  if (reuse && matches_last_forward(c, mesh, motion, cam, T, H, W, solver)) {
+    pp = *c->last_pp;
+    c->stats.reused += 1;
+  } else if ((rc = prepare(c, mesh, motion, cam, T, H, W, solver, st, true, pp))) {
+    return rc;
+  }
+  RasterParams P = raster_params(c, ctx_bufs(c), mesh, cam, T, H, W, pp);
+  const int V = mesh->V;
+  const size_t gbytes = sizeof(float4) * 2 * (size_t)V * pp.n_slots;
+  if ((rc = ensure(c, c->gslot, gbytes, st))) return rc;
+  if ((rc = ensure(c, c->gm, sizeof(float) * 3 * V, st))) return rc;
+  if ((rc = ensure(c, c->galb, sizeof(float4) * V, st))) return rc;
+  CUDA_TRY(c, cudaMemsetAsync(c->gslot.p, 0, gbytes, st));
+  if (dl_dalbedo) CUDA_TRY(c, cudaMemsetAsync(c->galb.p, 0, sizeof(float4) * V, st));
+  P.dl_dimage = (const float4*)dl_dimage;
+  P.g_slot = (float4*)c->gslot.p;
+  P.g_albedo = dl_dalbedo ? (float4*)c->galb.p : nullptr;
+  WorkQueue Q;
+  if ((rc = upload_queue(c, &P, 1, st, Q))) return rc;
+  const int kind = pp.moving ? 1 : 0;
+  const int grid = std::max(1, std::min(persistent_grid_bwd(c->num_sms, c->tile, pp.spt, kind), Q.n_work));
+  if ((rc = time_begin(c, 1, st))) return rc;
+  launch_raster_bwd(Q, c->tile, pp.spt, kind, grid, st);
+  CUDA_TRY(c, cudaGetLastError());
+  if ((rc = time_end(c, 1, st))) return rc;
+  c->stats.launches += 1 + 1 + (mesh->F > 0 ? 1 : 0);
+  c->stats.n_split = pp.n_split;
+  launch_slot_chain(mesh->verts, (const float*)c->nacc.p, V, pp.d_xf, pp.n_slots, cam->tan_half_fov,
+                    (const float4*)c->gslot.p, (const float4*)c->galb.p, dl_dverts, (float*)c->gm.p, dl_dalbedo, st);
+  launch_normals_bwd(mesh->verts, mesh->faces, mesh->F, V, (const float*)c->gm.p, dl_dverts, st);
+  CUDA_TRY(c, cudaGetLastError());
   return MBR_OK;
 }
 
@@ -609,6 +710,8 @@ void mbr_destroy(mbr_ctx* c) {
     for (int q = 0; q < 2; ++q)
       if (c->ev[k][q]) cudaEventDestroy(c->ev[k][q]);
   destroy_batch(c);
+  delete c->last_pp;
+  if (c->queue_copied) cudaEventDestroy(c->queue_copied);
   delete c;
 }
 
@@ -664,38 +767,17 @@ int mbr_render_blur_backward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion*
                              float* dl_dverts, float* dl_dalbedo, void* stream) {
   if (!c) return MBR_ERR_ARG;
   c->err.clear();
-  cudaStream_t st = (cudaStream_t)stream;
-  int rc = validate(c, mesh, motion, cam, T, H, W, solver);
-  if (rc) return rc;
-  if (!dl_dimage || !dl_dverts) return fail(c, MBR_ERR_ARG, "null gradient buffer");
-  Prepared pp;
-  if ((rc = prepare(c, mesh, motion, cam, T, H, W, solver, st, true, pp))) return rc;
-  RasterParams P = raster_params(c, ctx_bufs(c), mesh, cam, T, H, W, pp);
-  const int V = mesh->V;
-  const size_t gbytes = sizeof(float4) * 2 * (size_t)V * pp.n_slots;
-  if ((rc = ensure(c, c->gslot, gbytes, st))) return rc;
-  if ((rc = ensure(c, c->gm, sizeof(float) * 3 * V, st))) return rc;
-  if ((rc = ensure(c, c->galb, sizeof(float4) * V, st))) return rc;
-  CUDA_TRY(c, cudaMemsetAsync(c->gslot.p, 0, gbytes, st));
-  if (dl_dalbedo) CUDA_TRY(c, cudaMemsetAsync(c->galb.p, 0, sizeof(float4) * V, st));
-  P.dl_dimage = (const float4*)dl_dimage;
-  P.g_slot = (float4*)c->gslot.p;
-  P.g_albedo = dl_dalbedo ? (float4*)c->galb.p : nullptr;
-  WorkQueue Q;
-  if ((rc = upload_queue(c, &P, 1, st, Q))) return rc;
-  const int kind = pp.moving ? 1 : 0;
-  const int grid = std::max(1, std::min(persistent_grid_bwd(c->num_sms, c->tile, pp.spt, kind), Q.n_work));
-  if ((rc = time_begin(c, 1, st))) return rc;
-  launch_raster_bwd(Q, c->tile, pp.spt, kind, grid, st);
-  CUDA_TRY(c, cudaGetLastError());
-  if ((rc = time_end(c, 1, st))) return rc;
-  c->stats.launches += 1 + 1 + (mesh->F > 0 ? 1 : 0);
-  c->stats.n_split = pp.n_split;
-  launch_slot_chain(mesh->verts, (const float*)c->nacc.p, V, pp.d_xf, pp.n_slots, cam->tan_half_fov,
-                    (const float4*)c->gslot.p, (const float4*)c->galb.p, dl_dverts, (float*)c->gm.p, dl_dalbedo, st);
-  launch_normals_bwd(mesh->verts, mesh->faces, mesh->F, V, (const float*)c->gm.p, dl_dverts, st);
-  CUDA_TRY(c, cudaGetLastError());
-  return MBR_OK;
+  return backward_impl(c, mesh, motion, cam, T, H, W, solver, dl_dimage, dl_dverts, dl_dalbedo,
+                       (cudaStream_t)stream, false);
+}
+
+int mbr_render_blur_backward_reuse(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion,
+                                   const mbr_camera* cam, int32_t T, int32_t H, int32_t W, int32_t solver,
+                                   const float* dl_dimage, float* dl_dverts, float* dl_dalbedo, void* stream) {
+  if (!c) return MBR_ERR_ARG;
+  c->err.clear();
+  return backward_impl(c, mesh, motion, cam, T, H, W, solver, dl_dimage, dl_dverts, dl_dalbedo,
+                       (cudaStream_t)stream, true);
 }
 
 int mbr_count_candidates(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mbr_camera* cam,

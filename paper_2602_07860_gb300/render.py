@@ -150,13 +150,17 @@ class Context:
         return out
 
     def render_blur_backward(self, verts, faces, albedo, motion, camera, T, H, W, dl_dimage, solver="fast",
-                             want_albedo=True):
+                             want_albedo=True, reuse_forward=False):
+        """dL/dverts (and dL/dalbedo) for dL/dimage.  reuse_forward=True: the adjoint of the
+        immediately preceding render_blur on this context with the same arguments and unchanged
+        tensor contents (mbr_render_blur_backward_reuse)."""
         m = self._mesh(verts, faces, albedo)
         _check(dl_dimage, torch.float32, (H, W, 4), "dl_dimage")
         gv = torch.empty_like(verts)
         ga = torch.empty_like(albedo) if want_albedo else None
         mo, ca = motion.c(), camera.c()
-        self._raise(self.L.mbr_render_blur_backward(
+        fn = self.L.mbr_render_blur_backward_reuse if reuse_forward else self.L.mbr_render_blur_backward
+        self._raise(fn(
             self.h, ctypes.byref(m), ctypes.byref(mo), ctypes.byref(ca), T, H, W, _lib.SOLVERS[solver],
             ctypes.c_void_p(dl_dimage.data_ptr()), ctypes.c_void_p(gv.data_ptr()),
             ctypes.c_void_p(ga.data_ptr() if ga is not None else 0), _stream()))
@@ -255,8 +259,10 @@ class RenderBlur(torch.autograd.Function):
     def backward(ctx, g):
         verts, albedo, faces = ctx.saved_tensors
         motion, camera, T, H, W, solver, rctx = ctx.args
+        # autograd's saved-tensor version check guarantees verts/albedo/faces are unchanged since the
+        # forward, so the adjoint may reuse the forward's front half if nothing else ran in between
         gv, ga = rctx.render_blur_backward(verts, faces, albedo, motion, camera, T, H, W, g.contiguous(), solver,
-                                           want_albedo=ctx.needs_input_grad[1])
+                                           want_albedo=ctx.needs_input_grad[1], reuse_forward=True)
         return gv, ga, None, None, None, None, None, None, None, None
 
 

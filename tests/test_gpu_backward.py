@@ -105,3 +105,43 @@ def test_full_size_rotation_gradient_window(ctx, x0, y0):
         assert np.linalg.norm(gv - gv_o) <= 1e-3 * np.linalg.norm(gv_o)
         err = np.linalg.norm(gv - gv_o, axis=1)
         assert np.all(err <= 1e-3 * nv_o + 1e-4 * nv_o.max()), (solver, float(err.max()), float(nv_o.max()))
+
+
+@pytest.mark.parametrize("solver", ["fast", "plain"])
+def test_adjoint_reusing_the_forward_front_half(ctx, solver):
+    """mbr_render_blur_backward_reuse right after the forward reuses its front half (counted in
+    the stats) and equals the recomputing adjoint; with another call in between it recomputes and
+    is still right."""
+    sc = scenes.small_scene("rotate", subdiv=2, T=12, H=48, W=56, seed=9)
+    other = scenes.small_scene("translate", subdiv=2, T=8, H=40, W=40, seed=10)
+    v, f, a, mo, ca = gpu_inputs(sc)
+    v2, f2, a2, mo2, ca2 = gpu_inputs(other)
+    g = torch.randn((sc["H"], sc["W"], 4), device="cuda", generator=torch.Generator("cuda").manual_seed(2))
+    T, H, W = sc["T"], sc["H"], sc["W"]
+    ref_v, ref_a = ctx.render_blur_backward(v, f, a, mo, ca, T, H, W, g, solver)
+    s0 = ctx.stats()["reused"]
+    ctx.render_blur(v, f, a, mo, ca, T, H, W, solver)
+    gv, ga = ctx.render_blur_backward(v, f, a, mo, ca, T, H, W, g, solver, reuse_forward=True)
+    torch.cuda.synchronize()
+    assert ctx.stats()["reused"] == s0 + 1
+    scale = float(ref_v.abs().max())
+    assert float((gv - ref_v).abs().max()) <= 1e-5 * scale
+    assert float((ga - ref_a).abs().max()) <= 1e-5 * float(ref_a.abs().max())
+    # another render in between: the adjoint must recompute (no reuse) and still be right
+    ctx.render_blur(v, f, a, mo, ca, T, H, W, solver)
+    ctx.render_blur(v2, f2, a2, mo2, ca2, other["T"], other["H"], other["W"], solver)
+    gv2, _ = ctx.render_blur_backward(v, f, a, mo, ca, T, H, W, g, solver, reuse_forward=True)
+    torch.cuda.synchronize()
+    assert ctx.stats()["reused"] == s0 + 1
+    assert float((gv2 - ref_v).abs().max()) <= 1e-5 * scale
+    # a changed camera is a different render: no reuse
+    ctx.render_blur(v, f, a, mo, ca, T, H, W, solver)
+    ca_moved = mbr_camera_with_delta(ca, 2e-4)
+    ctx.render_blur_backward(v, f, a, mo, ca_moved, T, H, W, g, solver, reuse_forward=True)
+    torch.cuda.synchronize()
+    assert ctx.stats()["reused"] == s0 + 1
+
+
+def mbr_camera_with_delta(ca, delta):
+    import dataclasses
+    return dataclasses.replace(ca, delta=delta)
