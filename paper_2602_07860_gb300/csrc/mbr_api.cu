@@ -53,7 +53,7 @@ struct mbr_ctx {
   // tuning
   int tile = 16, spt = 2, splits = 0;
   // scratch
-  DevBuf nacc, pos, nrm, recs, tables, partial, gslot, galb, gm, cnt64, status, order;
+  DevBuf nacc, pos, nrm, recs, tables, partial, gslot, galb, gm, cnt64, status, order, bstate;
   BinSet core, soft;  // undilated bins (coverage) and r_soft-dilated bins (soft coverage)
   void* host_stage = nullptr;
   size_t host_stage_cap = 0;
@@ -643,6 +643,11 @@ int backward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, co
   P.dl_dimage = (const float4*)dl_dimage;
   P.g_slot = (float4*)c->gslot.p;
   P.g_albedo = dl_dalbedo ? (float4*)c->galb.p : nullptr;
+  // per-sample state between the two adjoint kernels: log soft product (float) + status (byte)
+  const size_t ns = (size_t)T * H * W;
+  if ((rc = ensure(c, c->bstate, ns * 5 + 256, st))) return rc;
+  P.s_logp = (float*)c->bstate.p;
+  P.s_stat = (uint8_t*)c->bstate.p + ns * 4;
   WorkQueue Q;
   if ((rc = upload_queue(c, &P, 1, st, Q))) return rc;
   const int kind = pp.moving ? 1 : 0;
@@ -696,7 +701,7 @@ int mbr_create(mbr_ctx** out) {
 void mbr_destroy(mbr_ctx* c) {
   if (!c) return;
   DevBuf* bufs[] = {&c->nacc, &c->pos, &c->nrm, &c->recs, &c->tables, &c->partial, &c->gslot, &c->galb, &c->gm,
-                    &c->cnt64, &c->order,
+                    &c->cnt64, &c->order, &c->bstate,
                     &c->status, &c->queue, &c->core.counts, &c->core.offsets, &c->core.cursor, &c->core.list,
                     &c->core.scan_tmp, &c->soft.counts, &c->soft.offsets, &c->soft.cursor, &c->soft.list,
                     &c->soft.scan_tmp};
@@ -930,7 +935,7 @@ struct BatchItem {
   std::vector<Group> groups;
   long long nb = 0;
   size_t o_status = 0, o_nacc = 0, o_pos = 0, o_nrm = 0, o_recs = 0, o_tab = 0, o_sets = 0, o_groups = 0;
-  size_t tab_bytes = 0, o_order = 0, o_gslot = 0, o_galb = 0, o_gm = 0;
+  size_t tab_bytes = 0, o_order = 0, o_gslot = 0, o_galb = 0, o_gm = 0, o_bstate = 0;
   size_t o_counts[2] = {0, 0}, o_offs[2] = {0, 0}, o_tmp[2] = {0, 0}, o_cursor[2] = {0, 0};
   size_t o_list[2] = {0, 0};
   int cap[2] = {0, 0};
@@ -1040,6 +1045,8 @@ void batch_write_params(mbr_ctx* c, const mbr_item* items, BatchState& B) {
       P.dl_dimage = (const float4*)it.dl_dimage;
       P.g_slot = (float4*)(A + I.o_gslot);
       P.g_albedo = it.dl_dalbedo ? (float4*)(A + I.o_galb) : nullptr;
+      P.s_logp = (float*)(A + I.o_bstate);
+      P.s_stat = (uint8_t*)(A + I.o_bstate) + (size_t)it.T * it.H * it.W * 4;
     }
     par[k] = P;
     off[k + 1] = off[k] + P.work;
@@ -1091,6 +1098,7 @@ int batch_plan(mbr_ctx* c, int n, const mbr_item* items, int wb, cudaStream_t st
       I.o_gslot = carve(at, sizeof(float4) * 2 * (size_t)V * pp.n_slots);
       I.o_galb = carve(at, sizeof(float4) * V);
       I.o_gm = carve(at, sizeof(float) * 3 * V);
+      I.o_bstate = carve(at, (size_t)it.T * it.H * it.W * 5);
     }
     I.stage_tab = carve(stage_at, I.tab_bytes);
   }

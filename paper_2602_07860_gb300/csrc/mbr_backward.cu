@@ -1,6 +1,6 @@
 // mbr_backward.cu -- adjoint kernels of the sm_103a motion-blurred renderer (a9).
 //
-//   raster_bwd_persistent recomputes passes 1-2 of the forward per sample (nothing is stored),
+//   raster_bwd_persistent recomputes passes 1-2 of the forward per sample, in two phases (below),
 //                      then back-propagates dL/dimage through shading (Eq. fore + Lambert),
 //                      the barycentric edge functions, and the soft-coverage product
 //                      (Eqs. probability-function .. back, exclusive products) into gradients on
@@ -9,6 +9,7 @@
 //   slot_chain_kernel  slot-state gradients -> base vertex gradients through projection, camera
 //                      and motion; base-normal gradient -> area-weighted-normal gradient
 //   normals_bwd_kernel adjoint of the face cross products of the vertex normals (a0)
+#include <algorithm>
 #include <cstdint>
 
 #include "mbr_internal.h"
@@ -434,41 +435,67 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
   }
 }
 
-// One work item of the adjoint: the 8 x 4 pixel block wb of tile `tile`, groups of `split`; ws
-// is the warp's shared scratch.
-template <int TW, int TH, int SPT, bool MOVING>
-__device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile, int split, int wb,
-                                                 WarpScratch<SPT>& ws) {
-  const int lane = threadIdx.x & 31;
-  const int n_tiles = P.tiles_x * P.tiles_y;
-  const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
-  int px, py;
-  PixelMap<TW, TH>::pixel(tx, ty, wb, px, py);
-  const BlockPix bp{px - (lane & 7), py - (lane >> 3), P.W, P.H};
-  const bool in_img = px < P.W && py < P.H;
-  float u, v;
-  bp.uv(lane, u, v);
-  ws.pu[lane] = u;
-  ws.pv[lane] = v;
-  const TileBox tb = PixelMap<TW, TH>::warp_box(tx, ty, wb, P.W, P.H);
-  const int g_begin = (int)((long long)P.G * split / P.n_split);
-  const int g_end = (int)((long long)P.G * (split + 1) / P.n_split);
-  const uint32_t img_mask = __ballot_sync(kFullMask, in_img);
-  float4 G4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (in_img) G4 = __ldg(P.dl_dimage + (size_t)py * P.W + px);
-  const float gr = G4.x * P.inv_T, gg = G4.y * P.inv_T, gb = G4.z * P.inv_T, ga = G4.w * P.inv_T;
-  const bool active = in_img && ga != 0.f;
+// The adjoint raster runs as two kernels over the same work units, so that each has a small hot
+// code footprint (one kernel with all passes is bound by instruction fetch):
+//   phase 0  pass 1 (winners), pass 2 (soft products of the uncovered samples that carry
+//            dL/dalpha) and the covered-sample adjoint; stores, per sample, the log soft product
+//            and a status byte (inactive, or the count of vanishing factors);
+//   phase 1  pass 3 (soft-factor gradients) from that state.
+// Everything is recomputed from the mesh in the backward; nothing is kept from the forward.
+constexpr uint8_t kStatInactive = 0xff;  // covered, outside the image, or no dL/dalpha
 
-  for (int g = g_begin; g < g_end; ++g) {
+struct BwdBlock {
+  int lane, n_tiles, px, py;
+  BlockPix bp;
+  bool in_img;
+  float u, v;
+  TileBox tb;
+  int g_begin, g_end;
+  float gr, gg, gb, ga;
+};
+
+template <int TW, int TH>
+__device__ __forceinline__ BwdBlock bwd_block_setup(const RasterParams& P, int tile, int split, int wb) {
+  BwdBlock B;
+  B.lane = threadIdx.x & 31;
+  B.n_tiles = P.tiles_x * P.tiles_y;
+  const int tx = tile % P.tiles_x, ty = tile / P.tiles_x;
+  PixelMap<TW, TH>::pixel(tx, ty, wb, B.px, B.py);
+  B.bp = BlockPix{B.px - (B.lane & 7), B.py - (B.lane >> 3), P.W, P.H};
+  B.in_img = B.px < P.W && B.py < P.H;
+  B.bp.uv(B.lane, B.u, B.v);
+  B.tb = PixelMap<TW, TH>::warp_box(tx, ty, wb, P.W, P.H);
+  B.g_begin = (int)((long long)P.G * split / P.n_split);
+  B.g_end = (int)((long long)P.G * (split + 1) / P.n_split);
+  float4 G4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (B.in_img) G4 = __ldg(P.dl_dimage + (size_t)B.py * P.W + B.px);
+  B.gr = G4.x * P.inv_T;
+  B.gg = G4.y * P.inv_T;
+  B.gb = G4.z * P.inv_T;
+  B.ga = G4.w * P.inv_T;
+  return B;
+}
+
+// phase 0 on one 8 x 4 block and its split of the sample groups
+template <int TW, int TH, int SPT, bool MOVING>
+__device__ __forceinline__ void raster_bwd_state_block(const RasterParams& P, int tile, int split, int wb,
+                                                       WarpScratch<SPT>& ws) {
+  const BwdBlock B = bwd_block_setup<TW, TH>(P, tile, split, wb);
+  const int lane = B.lane;
+  ws.pu[lane] = B.u;
+  ws.pv[lane] = B.v;
+  const uint32_t img_mask = __ballot_sync(kFullMask, B.in_img);
+  const bool active = B.in_img && B.ga != 0.f;
+  const size_t plane = (size_t)P.H * P.W, pix = (size_t)B.py * P.W + B.px;
+
+  for (int g = B.g_begin; g < B.g_end; ++g) {
     const Group* grp = P.groups + g;
     GroupRegs gq;
     gq.load(grp);
     const int n = gq.n;
     const uint32_t all_s = (1u << n) - 1u;
     const TriRec* recs_set = P.recs + (size_t)gq.rec_set * P.F;
-    const size_t bi = (size_t)g * n_tiles + tile;
-    float4* gslot_a = P.g_slot + (size_t)gq.slot_a * P.V * 2;
-    float4* gslot_b = P.g_slot + (size_t)gq.slot_b * P.V * 2;
+    const size_t bi = (size_t)g * B.n_tiles + tile;
     int cb, ce, sb, se;
     P.core.range(bi, cb, ce);
     P.soft.range(bi, sb, se);
@@ -479,12 +506,13 @@ __device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile
     for (int i = 0; i < SPT; ++i) {
       allowed[i] = i < n ? img_mask : 0u;
       ws.win[i][lane] = 0ull;
+      ws.logp[i][lane] = 0.f;
+      ws.nzero[i][lane] = 0;
     }
-    ws.pixs[lane] = in_img ? all_s : 0u;
-    ws.ga[lane] = ga;
+    ws.pixs[lane] = B.in_img ? all_s : 0u;
     __syncwarp();
-    CorePairs<SPT, MOVING, false> core{recs_set, grp, bp, &ws, 0u, 0u};
-    for_pairs<SPT, MOVING>(recs_set, P.core.faces, cb, ce, grp, n, tb, bp, kCoreMargin, allowed, all_s, ws, core);
+    CorePairs<SPT, MOVING, false> core{recs_set, grp, B.bp, &ws, 0u, 0u};
+    for_pairs<SPT, MOVING>(recs_set, P.core.faces, cb, ce, grp, n, B.tb, B.bp, kCoreMargin, allowed, all_s, ws, core);
     int bestf[SPT];
     uint32_t uncov = 0;
 #pragma unroll
@@ -497,38 +525,31 @@ __device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile
       }
     }
 
-    // ---- passes 2-3: soft products, then their gradients (uncovered samples with dL/dalpha)
+    // ---- pass 2: soft products of the uncovered samples with dL/dalpha
     const uint32_t my_s = active ? uncov : 0u;
     const uint32_t any_s = __reduce_or_sync(kFullMask, my_s);
     if (se > sb && any_s) {
 #pragma unroll
-      for (int i = 0; i < SPT; ++i) {
-        allowed[i] = __ballot_sync(kFullMask, (my_s >> i) & 1u);
-        ws.logp[i][lane] = 0.f;
-        ws.nzero[i][lane] = 0;
-      }
+      for (int i = 0; i < SPT; ++i) allowed[i] = __ballot_sync(kFullMask, (my_s >> i) & 1u);
       ws.pixs[lane] = my_s;
       __syncwarp();
       const float m = P.r + kCoreMargin;
-      BwdSoftLogPairs<SPT, MOVING> p2{recs_set, grp, bp, &ws, gq.xbits, m, P.r2, P.inv_delta};
-      for_pairs<SPT, MOVING>(recs_set, P.soft.faces, sb, se, grp, n, tb, bp, m, allowed, any_s, ws, p2);
-      BwdSoftGradPairs<SPT, MOVING> p3;
-      p3.recs_set = recs_set;
-      p3.grp = grp;
-      p3.bp = bp;
-      p3.ws = &ws;
-      p3.xbits = gq.xbits;
-      p3.m = m;
-      p3.r2 = P.r2;
-      p3.inv_delta = P.inv_delta;
-      p3.faces = P.faces;
-      p3.gslot_a = gslot_a;
-      p3.gslot_b = gslot_b;
-      for_pairs<SPT, MOVING>(recs_set, P.soft.faces, sb, se, grp, n, tb, bp, m, allowed, any_s, ws, p3);
+      BwdSoftLogPairs<SPT, MOVING> p2{recs_set, grp, B.bp, &ws, gq.xbits, m, P.r2, P.inv_delta};
+      for_pairs<SPT, MOVING>(recs_set, P.soft.faces, sb, se, grp, n, B.tb, B.bp, m, allowed, any_s, ws, p2);
+    }
+    if (B.in_img) {
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) {
+        if (i < n) {
+          const size_t o = (size_t)(gq.k0 + i) * plane + pix;
+          const bool soft = (my_s >> i) & 1u;
+          P.s_stat[o] = soft ? (uint8_t)min(ws.nzero[i][lane], 2) : kStatInactive;
+          P.s_logp[o] = soft ? ws.logp[i][lane] : 0.f;
+        }
+      }
     }
 
-    // ---- covered samples: shading adjoint and barycentric adjoint of the winner (one copy of
-    // the code, looping over the group's samples)
+    // ---- covered samples: shading adjoint and barycentric adjoint of the winner
 #pragma unroll 1
     for (int i = 0; i < n; ++i) {
       int f = -1;
@@ -536,15 +557,77 @@ __device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile
       for (int q = 0; q < SPT; ++q)
         if (q == i) f = bestf[q];
       const float tau = MOVING ? __ldg(gq.tau + i) : 0.f;
-      const bool has = in_img && f >= 0;
-      covered_adjoint<MOVING>(P, recs_set, gq.slot_a, gq.slot_b, has, has ? f : 0, tau, u, v, gr, gg, gb);
+      const bool has = B.in_img && f >= 0;
+      covered_adjoint<MOVING>(P, recs_set, gq.slot_a, gq.slot_b, has, has ? f : 0, tau, B.u, B.v, B.gr, B.gg, B.gb);
     }
     __syncwarp();  // the scratch is rewritten by the next group
   }
 }
 
-// Persistent adjoint raster: KIND 0 = plain solver only, 1 = fast solver only, 2 = mixed batch.
-template <int TW, int TH, int SPT, int KIND>
+// phase 1 on one 8 x 4 block: soft-factor gradients of the uncovered samples, from phase 0's state
+template <int TW, int TH, int SPT, bool MOVING>
+__device__ __forceinline__ void raster_bwd_soft_block(const RasterParams& P, int tile, int split, int wb,
+                                                      WarpScratch<SPT>& ws) {
+  const BwdBlock B = bwd_block_setup<TW, TH>(P, tile, split, wb);
+  const int lane = B.lane;
+  ws.pu[lane] = B.u;
+  ws.pv[lane] = B.v;
+  ws.ga[lane] = B.ga;
+  const size_t plane = (size_t)P.H * P.W, pix = (size_t)B.py * P.W + B.px;
+
+  for (int g = B.g_begin; g < B.g_end; ++g) {
+    const Group* grp = P.groups + g;
+    GroupRegs gq;
+    gq.load(grp);
+    const int n = gq.n;
+    const size_t bi = (size_t)g * B.n_tiles + tile;
+    int sb, se;
+    P.soft.range(bi, sb, se);
+    uint32_t my_s = 0u;
+    if (B.in_img) {
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) {
+        if (i < n) {
+          const size_t o = (size_t)(gq.k0 + i) * plane + pix;
+          const uint8_t st = __ldg(P.s_stat + o);
+          if (st != kStatInactive) {
+            my_s |= 1u << i;
+            ws.nzero[i][lane] = st;
+            ws.logp[i][lane] = __ldg(P.s_logp + o);
+          }
+        }
+      }
+    }
+    const uint32_t any_s = __reduce_or_sync(kFullMask, my_s);
+    if (se > sb && any_s) {
+      const TriRec* recs_set = P.recs + (size_t)gq.rec_set * P.F;
+      uint32_t allowed[SPT];
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) allowed[i] = __ballot_sync(kFullMask, (my_s >> i) & 1u);
+      ws.pixs[lane] = my_s;
+      __syncwarp();
+      const float m = P.r + kCoreMargin;
+      BwdSoftGradPairs<SPT, MOVING> p3;
+      p3.recs_set = recs_set;
+      p3.grp = grp;
+      p3.bp = B.bp;
+      p3.ws = &ws;
+      p3.xbits = gq.xbits;
+      p3.m = m;
+      p3.r2 = P.r2;
+      p3.inv_delta = P.inv_delta;
+      p3.faces = P.faces;
+      p3.gslot_a = P.g_slot + (size_t)gq.slot_a * P.V * 2;
+      p3.gslot_b = P.g_slot + (size_t)gq.slot_b * P.V * 2;
+      for_pairs<SPT, MOVING>(recs_set, P.soft.faces, sb, se, grp, n, B.tb, B.bp, m, allowed, any_s, ws, p3);
+    }
+    __syncwarp();
+  }
+}
+
+// Persistent adjoint raster, phase PHASE (see above): KIND 0 = plain solver only, 1 = fast solver
+// only, 2 = mixed batch.
+template <int TW, int TH, int SPT, int KIND, int PHASE>
 __global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 4 : 2) raster_bwd_persistent(WorkQueue Q) {
   __shared__ CtaQueue cq;
   __shared__ RasterParams sp[kPersistentThreads / 32];
@@ -555,10 +638,14 @@ __global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 4 : 2) raster_
   int cur = -1, tile = 0, split = 0, wb = 0;
   while (warp_next<TW, TH>(Q, cq, P, cur, tile, split, wb)) {
     if (tile >= P.tiles_x * P.tiles_y) continue;
-    if (KIND == 0 || (KIND == 2 && !P.moving))
-      raster_bwd_block<TW, TH, 1, false>(P, tile, split, wb, *reinterpret_cast<WarpScratch<1>*>(ws + warp));
-    else
-      raster_bwd_block<TW, TH, SPT, true>(P, tile, split, wb, ws[warp]);
+    if (KIND == 0 || (KIND == 2 && !P.moving)) {
+      WarpScratch<1>& w1 = *reinterpret_cast<WarpScratch<1>*>(ws + warp);
+      if (PHASE == 0) raster_bwd_state_block<TW, TH, 1, false>(P, tile, split, wb, w1);
+      else raster_bwd_soft_block<TW, TH, 1, false>(P, tile, split, wb, w1);
+    } else {
+      if (PHASE == 0) raster_bwd_state_block<TW, TH, SPT, true>(P, tile, split, wb, ws[warp]);
+      else raster_bwd_soft_block<TW, TH, SPT, true>(P, tile, split, wb, ws[warp]);
+    }
   }
 }
 
@@ -646,30 +733,32 @@ __global__ void normals_bwd_kernel(const float* __restrict__ verts, const int32_
   atomicAdd(g_verts + 3 * a + 2, -(bz + cz));
 }
 
-template <int TW, int TH, int KIND>
+template <int TW, int TH, int KIND, int PHASE>
 static void launch_bwd_spt(const WorkQueue& Q, int spt, int grid, cudaStream_t st) {
   if (spt <= 2)
-    raster_bwd_persistent<TW, TH, 2, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
+    raster_bwd_persistent<TW, TH, 2, KIND, PHASE><<<grid, kPersistentThreads, 0, st>>>(Q);
   else
-    raster_bwd_persistent<TW, TH, 4, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
+    raster_bwd_persistent<TW, TH, 4, KIND, PHASE><<<grid, kPersistentThreads, 0, st>>>(Q);
 }
 
-template <int TW, int TH>
+template <int TW, int TH, int PHASE>
 static void launch_bwd_tile(const WorkQueue& Q, int spt, int kind, int grid, cudaStream_t st) {
   if (kind == 0)
-    raster_bwd_persistent<TW, TH, 1, 0><<<grid, kPersistentThreads, 0, st>>>(Q);
+    raster_bwd_persistent<TW, TH, 1, 0, PHASE><<<grid, kPersistentThreads, 0, st>>>(Q);
   else if (kind == 1)
-    launch_bwd_spt<TW, TH, 1>(Q, spt, grid, st);
+    launch_bwd_spt<TW, TH, 1, PHASE>(Q, spt, grid, st);
   else
-    launch_bwd_spt<TW, TH, 2>(Q, spt, grid, st);
+    launch_bwd_spt<TW, TH, 2, PHASE>(Q, spt, grid, st);
 }
 
+// both phases; the queue's counter is re-armed between them (stream order)
 void launch_raster_bwd(const WorkQueue& Q, int tile, int spt, int kind, int grid, cudaStream_t st) {
   if (Q.n_work <= 0) return;
-  if (tile == 8)
-    launch_bwd_tile<8, 8>(Q, spt, kind, grid, st);
-  else
-    launch_bwd_tile<16, 16>(Q, spt, kind, grid, st);
+  if (tile == 8) launch_bwd_tile<8, 8, 0>(Q, spt, kind, grid, st);
+  else launch_bwd_tile<16, 16, 0>(Q, spt, kind, grid, st);
+  cudaMemsetAsync(Q.counter, 0, sizeof(int32_t), st);
+  if (tile == 8) launch_bwd_tile<8, 8, 1>(Q, spt, kind, grid, st);
+  else launch_bwd_tile<16, 16, 1>(Q, spt, kind, grid, st);
 }
 
 template <typename K>
@@ -679,12 +768,20 @@ static int occupancy_of(K kernel) {
   return n < 1 ? 1 : n;
 }
 
+template <int TW, int TH, int PHASE>
+static int occ_bwd_phase(int spt, int kind) {
+  if (kind == 0) return occupancy_of(raster_bwd_persistent<TW, TH, 1, 0, PHASE>);
+  if (kind == 1)
+    return spt <= 2 ? occupancy_of(raster_bwd_persistent<TW, TH, 2, 1, PHASE>)
+                    : occupancy_of(raster_bwd_persistent<TW, TH, 4, 1, PHASE>);
+  return spt <= 2 ? occupancy_of(raster_bwd_persistent<TW, TH, 2, 2, PHASE>)
+                  : occupancy_of(raster_bwd_persistent<TW, TH, 4, 2, PHASE>);
+}
+
+// one grid serves both phases: the smaller occupancy of the two
 template <int TW, int TH>
 static int occ_bwd(int spt, int kind) {
-  if (kind == 0) return occupancy_of(raster_bwd_persistent<TW, TH, 1, 0>);
-  if (kind == 1)
-    return spt <= 2 ? occupancy_of(raster_bwd_persistent<TW, TH, 2, 1>) : occupancy_of(raster_bwd_persistent<TW, TH, 4, 1>);
-  return spt <= 2 ? occupancy_of(raster_bwd_persistent<TW, TH, 2, 2>) : occupancy_of(raster_bwd_persistent<TW, TH, 4, 2>);
+  return std::min(occ_bwd_phase<TW, TH, 0>(spt, kind), occ_bwd_phase<TW, TH, 1>(spt, kind));
 }
 
 int persistent_grid_bwd(int num_sms, int tile, int spt, int kind) {

@@ -61,6 +61,8 @@ struct RasterParams {
   const float4* dl_dimage;   // [H*W]
   float4* g_slot;            // [slots][V][2]: (dx, dy, dnx, dny), (dnz, 0, 0, 0) of the slot states
   float4* g_albedo;          // [V] (dr, dg, db, 0), or null
+  float* s_logp;             // [T][H][W] adjoint state between its two kernels: log soft product,
+  uint8_t* s_stat;           //   and status: kStatCovered, or the count of vanishing factors
 };
 
 // Edge-function values of one candidate at one sample (local frame; see TriRec).
