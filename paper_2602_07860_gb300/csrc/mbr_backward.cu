@@ -628,7 +628,7 @@ __device__ __forceinline__ void raster_bwd_soft_block(const RasterParams& P, int
 // Persistent adjoint raster, phase PHASE (see above): KIND 0 = plain solver only, 1 = fast solver
 // only, 2 = mixed batch.
 template <int TW, int TH, int SPT, int KIND, int PHASE>
-__global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 4 : 2) raster_bwd_persistent(WorkQueue Q) {
+__global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 3 : 2) raster_bwd_persistent(WorkQueue Q) {
   __shared__ CtaQueue cq;
   __shared__ RasterParams sp[kPersistentThreads / 32];
   __shared__ WarpScratch<SPT> ws[kPersistentThreads / 32];
