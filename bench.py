@@ -35,6 +35,10 @@ WORKLOAD = ("rotation: icosphere subdiv 4 + SH degree 6 (2562 v, 5120 f), one tu
             "T=64, 256x256, 12 segments; step = forward + adjoint")
 CPU_WINDOW = (64, 64, 128, 128)   # bounded oracle sample for the CPU baseline (~15 s)
 REF_WINDOW = (120, 120, 16, 16)   # per-step oracle sample of the reference arm
+# DRAM bytes (read + write) per launch from the ncu captures summarised in profiles/ (tiles 8x8,
+# spt 1, this workload); to be refreshed (or set to None) whenever the kernels change
+NCU_DRAM_BYTES = {"raster_bwd_persistent": 77.0e6,  # both phases of one adjoint
+                  "raster_fwd_persistent": 18.1e6}
 
 
 def _dist_env():
@@ -212,6 +216,8 @@ def main():
     ap.add_argument("--impl", default="mbr", choices=["mbr", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra-workloads", action="store_true")
+    ap.add_argument("--tile", type=int, default=0, help="fixed tile edge (with --spt): skip the autotuner")
+    ap.add_argument("--spt", type=int, default=0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -252,7 +258,11 @@ def main():
     tune_item = dict(verts=v, faces=f, albedo=a, motion=mo, camera=ca, T=T, H=H, W=W, solver="fast",
                      image=torch.zeros((H, W, 4), device="cuda"), dl_dimage=G, dl_dverts=torch.zeros_like(v),
                      dl_dalbedo=torch.zeros_like(a))
-    tile, ctx_spt, _ = ctx.autotune([tune_item], True)
+    if args.tile and args.spt:
+        tile, ctx_spt = args.tile, args.spt
+        ctx.set_tuning(tile, ctx_spt, 0)
+    else:
+        tile, ctx_spt, _ = ctx.autotune([tune_item], True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     n_samples = H * W * T
 
@@ -307,8 +317,10 @@ def main():
     backward_dominant = bwd_ms >= fwd_ms
     kern = "raster_bwd_persistent" if backward_dominant else "raster_fwd_persistent"
     achieved = bwd_tf if backward_dominant else fwd_tf
+    traffic = NCU_DRAM_BYTES.get(kern) if (tile, ctx_spt) == (8, 1) else None
     roof = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": traffic,
+            "traffic_note": "DRAM bytes per launch from ncu (profiles/), tiles 8x8 / spt 1",
             "peak_note": f"{num_sms} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived from unit counts "
                          "and the maximum SM clock; no measured FP32 peak)",
             "work": roofline.describe("fast", units["n_box"], units["n_soft"], units["n_cov"], n_samples,
@@ -338,7 +350,8 @@ def main():
         "speedup_fast_over_plain_fwd": plain_f / fast_f,
         "plain_raster_fwd_ms": p_fwd, "plain_raster_bwd_ms": p_bwd,
         "plain_fwd_frac": p_fwd_tf / peak, "plain_bwd_frac": p_bwd_tf / peak, "plain_units": p_units,
-        "tuning": {"tile": tile, "spt": ctx_spt, "splits": "auto", "chosen_by": "mbr_autotune"},
+        "tuning": {"tile": tile, "spt": ctx_spt, "splits": "auto",
+                   "chosen_by": "command line" if (args.tile and args.spt) else "mbr_autotune"},
         "paper_context": "paper: up to 4.57x fwd+grad speedup vs SoftRas on one RTX 4090 (different workload)",
     }
 
