@@ -186,6 +186,61 @@ __global__ void bin_kernel(const TriRec* __restrict__ recs, int F, const Group* 
     }
 }
 
+// Two-level variant (images of up to kSmemBinTiles tiles): a CTA takes 256 faces of ONE group
+// (grid.y = group) and counts its (tile, face) entries in a shared-memory histogram over the
+// tiles; the count pass adds the histogram to the global counts, the fill pass reserves one
+// range per (CTA, tile) in the global cursors and places its entries with shared-memory atomics.
+// Global atomics fall from one per entry to one per (CTA, tile) touched.
+constexpr int kSmemBinTiles = 4096;
+
+template <bool FILL>
+__global__ void bin_smem_kernel(const TriRec* __restrict__ recs, int F, const Group* __restrict__ groups, int W,
+                                int H, int tw, int th, int tiles_x, int n_tiles, float r,
+                                int32_t* __restrict__ counts_or_cursor, int32_t* __restrict__ list,
+                                const int32_t* __restrict__ bin_end, int list_cap, int* __restrict__ status) {
+  extern __shared__ int sh[];  // [n_tiles]
+  const int g = blockIdx.y;
+  for (int i = threadIdx.x; i < n_tiles; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  bool have = false;
+  int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+  if (f < F) {
+    const Group& gr = groups[g];
+    const TriRec& rec = recs[(size_t)gr.rec_set * F + f];
+    if (!(__float_as_uint(rec.f4[kR_Z].w) & kFlagCulled)) {
+      float xmin, xmax, ymin, ymax;
+      swept_bbox(rec, gr.tau_lo, gr.tau_hi, xmin, xmax, ymin, ymax);
+      int i0, i1, j0, j1;
+      if (pixel_range(xmin - r, xmax + r, ymin - r, ymax + r, W, H, i0, i1, j0, j1)) {
+        have = true;
+        tx0 = i0 / tw; tx1 = i1 / tw; ty0 = j0 / th; ty1 = j1 / th;
+      }
+    }
+  }
+  if (have)
+    for (int ty = ty0; ty <= ty1; ++ty)
+      for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&sh[ty * tiles_x + tx], 1);
+  __syncthreads();
+  int32_t* base = counts_or_cursor + (size_t)g * n_tiles;
+  if (!FILL) {
+    for (int i = threadIdx.x; i < n_tiles; i += blockDim.x)
+      if (sh[i]) atomicAdd(base + i, sh[i]);
+    return;
+  }
+  for (int i = threadIdx.x; i < n_tiles; i += blockDim.x)
+    if (sh[i]) sh[i] = atomicAdd(base + i, sh[i]);  // first slot of this CTA's range
+  __syncthreads();
+  if (have)
+    for (int ty = ty0; ty <= ty1; ++ty)
+      for (int tx = tx0; tx <= tx1; ++tx) {
+        const int b = ty * tiles_x + tx;
+        const int slot = atomicAdd(&sh[b], 1);
+        if (slot < bin_end[(size_t)g * n_tiles + b + 1] && slot < list_cap) list[slot] = f;
+        else atomicOr(status, kStatusBinOverflow);
+      }
+}
+
 // ---------------------------------------------------------------- exclusive scan (CSR offsets)
 constexpr int kScanThreads = 1024, kScanPer = 4, kScanBlock = kScanThreads * kScanPer;
 
@@ -606,6 +661,17 @@ void launch_bin(bool fill, const TriRec* recs, int F, const Group* groups, int G
                 const int32_t* bin_off, int list_cap, int* status, cudaStream_t st) {
   const size_t n = (size_t)G * F;
   if (!n) return;
+  if (n_tiles <= kSmemBinTiles && G <= 65535) {
+    const dim3 grid((unsigned)((F + 255) / 256), (unsigned)G);
+    const size_t smem = sizeof(int) * (size_t)n_tiles;
+    if (fill)
+      bin_smem_kernel<true><<<grid, 256, smem, st>>>(recs, F, groups, W, H, tw, th, tiles_x, n_tiles, r,
+                                                     counts_or_cursor, list, bin_off, list_cap, status);
+    else
+      bin_smem_kernel<false><<<grid, 256, smem, st>>>(recs, F, groups, W, H, tw, th, tiles_x, n_tiles, r,
+                                                      counts_or_cursor, list, bin_off, list_cap, status);
+    return;
+  }
   const unsigned blocks = (unsigned)((n + 255) / 256);
   if (fill)
     bin_kernel<true><<<blocks, 256, 0, st>>>(recs, F, groups, G, W, H, tw, th, tiles_x, n_tiles, r, counts_or_cursor,
