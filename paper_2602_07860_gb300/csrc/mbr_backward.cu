@@ -650,15 +650,17 @@ __global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 3 : 2) raster_
 }
 
 // ---------------------------------------------------------------- slot gradients -> vertices
-// one thread per vertex, looping over slots (no atomics); writes dL/dv and dL/dm (m = normal sum)
+// one warp per vertex, lanes over slots (no atomics); writes dL/dv and dL/dm (m = normal sum)
 __global__ void slot_chain_kernel(const float* __restrict__ verts, const float* __restrict__ nacc, int V,
                                   const SlotXform* __restrict__ xf, int n_slots, float th,
                                   const float4* __restrict__ g_slot, const float4* __restrict__ g_alb4,
                                   float* __restrict__ g_verts, float* __restrict__ g_m,
                                   float* __restrict__ g_albedo) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= V) return;
-  if (g_albedo) {
+  // one warp per vertex: lanes take the slots, then a warp sum (V is small, slots are many)
+  const int v = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (v >= V) return;  // warp-uniform
+  if (g_albedo && lane == 0) {
     const float4 a = g_alb4[v];
     g_albedo[3 * v] = a.x;
     g_albedo[3 * v + 1] = a.y;
@@ -666,7 +668,7 @@ __global__ void slot_chain_kernel(const float* __restrict__ verts, const float* 
   }
   const float px = verts[3 * v], py = verts[3 * v + 1], pz = verts[3 * v + 2];
   float gvx = 0.f, gvy = 0.f, gvz = 0.f, gnx = 0.f, gny = 0.f, gnz = 0.f;
-  for (int s = 0; s < n_slots; ++s) {
+  for (int s = lane; s < n_slots; s += 32) {
     const float4 ga = g_slot[((size_t)s * V + v) * 2];
     const float g0 = ga.x, g1 = ga.y, g2 = ga.z, g3 = ga.w, g4 = g_slot[((size_t)s * V + v) * 2 + 1].x;
     if (g0 == 0.f && g1 == 0.f && g2 == 0.f && g3 == 0.f && g4 == 0.f) continue;
@@ -686,6 +688,13 @@ __global__ void slot_chain_kernel(const float* __restrict__ verts, const float* 
     gny += R[1] * g2 + R[4] * g3 + R[7] * g4;
     gnz += R[2] * g2 + R[5] * g3 + R[8] * g4;
   }
+  gvx = warp_sum(gvx);
+  gvy = warp_sum(gvy);
+  gvz = warp_sum(gvz);
+  gnx = warp_sum(gnx);
+  gny = warp_sum(gny);
+  gnz = warp_sum(gnz);
+  if (lane != 0) return;
   g_verts[3 * v] = gvx;
   g_verts[3 * v + 1] = gvy;
   g_verts[3 * v + 2] = gvz;
@@ -792,7 +801,7 @@ void launch_slot_chain(const float* verts, const float* nacc, int V, const SlotX
                        const float4* g_slot, const float4* g_alb4, float* g_verts, float* g_m, float* g_albedo,
                        cudaStream_t st) {
   if (V > 0)
-    slot_chain_kernel<<<(V + 255) / 256, 256, 0, st>>>(verts, nacc, V, xf, n_slots, th, g_slot, g_alb4, g_verts, g_m,
+    slot_chain_kernel<<<(unsigned)(((size_t)V * 32 + 255) / 256), 256, 0, st>>>(verts, nacc, V, xf, n_slots, th, g_slot, g_alb4, g_verts, g_m,
                                                        g_albedo);
 }
 
