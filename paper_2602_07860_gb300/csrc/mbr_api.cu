@@ -402,15 +402,20 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
   const long long nb = (long long)pp.G * pp.n_tiles;
   if (nb > (1LL << 30)) return fail(c, MBR_ERR_ARG, "too many (group, tile) bins: %lld", nb);
   BinSet* sets2[2] = {&c->core, &c->soft};
-  const float margins[2] = {kCoreMargin, pp.r + kCoreMargin};
+  const float r_core = kCoreMargin, r_soft = pp.r + kCoreMargin;
+  BinTargets bt{};
   for (int q = 0; q < 2; ++q) {
     BinSet& bs = *sets2[q];
     if ((rc = ensure(c, bs.counts, sizeof(int32_t) * (size_t)nb, st))) return rc;
     if ((rc = ensure(c, bs.offsets, sizeof(int32_t) * (size_t)(nb + 1), st))) return rc;
     if ((rc = ensure(c, bs.scan_tmp, sizeof(int32_t) * scan_temp_ints((int)nb), st))) return rc;
     CUDA_TRY(c, cudaMemsetAsync(bs.counts.p, 0, sizeof(int32_t) * (size_t)nb, st));
-    launch_bin(false, (const TriRec*)c->recs.p, F, pp.d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles,
-               margins[q], (int32_t*)bs.counts.p, nullptr, nullptr, 0, d_status, st);
+    bt.counts_or_cursor[q] = (int32_t*)bs.counts.p;
+  }
+  launch_bin(false, (const TriRec*)c->recs.p, F, pp.d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles, r_core,
+             r_soft, bt, d_status, st);
+  for (int q = 0; q < 2; ++q) {
+    BinSet& bs = *sets2[q];
     launch_scan((const int32_t*)bs.counts.p, (int)nb, (int32_t*)bs.offsets.p, (int32_t*)bs.scan_tmp.p, st);
     CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaMemcpyAsync(c->host_total + 2 * q, (int32_t*)bs.offsets.p + nb, sizeof(int32_t),
@@ -431,12 +436,15 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
     if ((rc = ensure(c, bs.cursor, sizeof(int32_t) * (size_t)nb, st))) return rc;
     CUDA_TRY(c, cudaMemcpyAsync(bs.cursor.p, bs.offsets.p, sizeof(int32_t) * (size_t)nb, cudaMemcpyDeviceToDevice,
                                 st));
-    launch_bin(true, (const TriRec*)c->recs.p, F, pp.d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles,
-               margins[q], (int32_t*)bs.cursor.p, (int32_t*)bs.list.p, (const int32_t*)bs.offsets.p, (int)totals[q],
-             d_status, st);
-    CUDA_TRY(c, cudaGetLastError());
+    bt.counts_or_cursor[q] = (int32_t*)bs.cursor.p;
+    bt.list[q] = (int32_t*)bs.list.p;
+    bt.off[q] = (const int32_t*)bs.offsets.p;
+    bt.cap[q] = (int)totals[q];
   }
-  c->stats.launches += 2 * ((F > 0 ? 2 : 0) + 3);
+  launch_bin(true, (const TriRec*)c->recs.p, F, pp.d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles, r_core,
+             r_soft, bt, d_status, st);
+  CUDA_TRY(c, cudaGetLastError());
+  c->stats.launches += (F > 0 ? 2 : 0) + 2 * 3;
   c->stats.bin_entries = totals[0] + totals[1];
   pp.core_cap = (int)totals[0];
   pp.soft_cap = (int)totals[1];
@@ -1151,15 +1159,16 @@ int batch_enqueue(mbr_ctx* c, const mbr_item* items, BatchState& B, cudaStream_t
                  it.camera.tan_half_fov, (float4*)(A + I.o_pos), (float4*)(A + I.o_nrm), st);
     launch_setup((const float4*)(A + I.o_pos), it.mesh.faces, F, V, (const int2*)(A + I.o_sets), pp.n_sets,
                  it.camera.znear, (TriRec*)(A + I.o_recs), st);
-    const float margins[2] = {kCoreMargin, pp.r + kCoreMargin};
+    BinTargets bt{};
     for (int q = 0; q < 2; ++q) {
       CUDA_TRY(c, cudaMemsetAsync(A + I.o_counts[q], 0, sizeof(int32_t) * (size_t)I.nb, st));
-      launch_bin(false, (const TriRec*)(A + I.o_recs), F, (const Group*)(A + I.o_groups), pp.G, it.W, it.H, c->tile,
-                 c->tile, pp.tiles_x, pp.n_tiles, margins[q], (int32_t*)(A + I.o_counts[q]), nullptr, nullptr, 0,
-                 d_status, st);
+      bt.counts_or_cursor[q] = (int32_t*)(A + I.o_counts[q]);
+    }
+    launch_bin(false, (const TriRec*)(A + I.o_recs), F, (const Group*)(A + I.o_groups), pp.G, it.W, it.H, c->tile,
+               c->tile, pp.tiles_x, pp.n_tiles, kCoreMargin, pp.r + kCoreMargin, bt, d_status, st);
+    for (int q = 0; q < 2; ++q)
       launch_scan((const int32_t*)(A + I.o_counts[q]), (int)I.nb, (int32_t*)(A + I.o_offs[q]),
                   (int32_t*)(A + I.o_tmp[q]), st);
-    }
     CUDA_TRY(c, cudaGetLastError());
   }
   int32_t* hs = (int32_t*)((char*)B.stage + B.stage_status);
@@ -1192,15 +1201,18 @@ int batch_enqueue(mbr_ctx* c, const mbr_item* items, BatchState& B, cudaStream_t
     const BatchItem& I = B.items[i];
     const mbr_item& it = items[i];
     const Prepared& pp = I.pp;
-    const float margins[2] = {kCoreMargin, pp.r + kCoreMargin};
+    BinTargets bt{};
     for (int q = 0; q < 2; ++q) {
       CUDA_TRY(c, cudaMemcpyAsync(A + I.o_cursor[q], A + I.o_offs[q], sizeof(int32_t) * (size_t)I.nb,
                                   cudaMemcpyDeviceToDevice, st));
-      launch_bin(true, (const TriRec*)(A + I.o_recs), it.mesh.F, (const Group*)(A + I.o_groups), pp.G, it.W, it.H,
-                 c->tile, c->tile, pp.tiles_x, pp.n_tiles, margins[q], (int32_t*)(A + I.o_cursor[q]),
-                 (int32_t*)(Lb + I.o_list[q]), (const int32_t*)(A + I.o_offs[q]), I.cap[q], (int*)(A + I.o_status),
-                 st);
+      bt.counts_or_cursor[q] = (int32_t*)(A + I.o_cursor[q]);
+      bt.list[q] = (int32_t*)(Lb + I.o_list[q]);
+      bt.off[q] = (const int32_t*)(A + I.o_offs[q]);
+      bt.cap[q] = I.cap[q];
     }
+    launch_bin(true, (const TriRec*)(A + I.o_recs), it.mesh.F, (const Group*)(A + I.o_groups), pp.G, it.W, it.H,
+               c->tile, c->tile, pp.tiles_x, pp.n_tiles, kCoreMargin, pp.r + kCoreMargin, bt, (int*)(A + I.o_status),
+               st);
     int32_t* order = (int32_t*)(A + I.o_order);
     launch_unit_order((const int32_t*)(A + I.o_offs[0]), (const int32_t*)(A + I.o_offs[1]), pp.G, pp.n_tiles, c->tile,
                       pp.n_split, pp.n_units, order, order + pp.n_units, st);
@@ -1404,12 +1416,15 @@ int noalloc_forward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, 
   launch_face_normals(mesh->verts, mesh->faces, F, V, nacc, d_status, st);
   launch_xform(mesh->verts, nacc, V, d_xf, pp.n_slots, cam->tan_half_fov, pos, nrm, st);
   launch_setup(pos, mesh->faces, F, V, d_sets, pp.n_sets, cam->znear, recs, st);
-  const float margins[2] = {kCoreMargin, pp.r + kCoreMargin};
   int32_t host[3] = {0, 0, 0};
+  BinTargets bt{};
   for (int q = 0; q < 2; ++q) {
     CUDA_TRY(c, cudaMemsetAsync(counts[q], 0, sizeof(int32_t) * (size_t)nb, st));
-    launch_bin(false, recs, F, d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles, margins[q], counts[q], nullptr,
-               nullptr, 0, d_status, st);
+    bt.counts_or_cursor[q] = counts[q];
+  }
+  launch_bin(false, recs, F, d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles, kCoreMargin, pp.r + kCoreMargin,
+             bt, d_status, st);
+  for (int q = 0; q < 2; ++q) {
     launch_scan(counts[q], (int)nb, offs[q], tmp[q], st);
     CUDA_TRY(c, cudaGetLastError());
     CUDA_TRY(c, cudaMemcpyAsync(host + q, offs[q] + nb, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -1425,9 +1440,13 @@ int noalloc_forward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, 
   }
   for (int q = 0; q < 2; ++q) {
     CUDA_TRY(c, cudaMemcpyAsync(cursor[q], offs[q], sizeof(int32_t) * (size_t)nb, cudaMemcpyDeviceToDevice, st));
-    launch_bin(true, recs, F, d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles, margins[q], cursor[q], list[q],
-               offs[q], host[q], d_status, st);
+    bt.counts_or_cursor[q] = cursor[q];
+    bt.list[q] = list[q];
+    bt.off[q] = offs[q];
+    bt.cap[q] = host[q];
   }
+  launch_bin(true, recs, F, d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles, kCoreMargin, pp.r + kCoreMargin, bt,
+             d_status, st);
   CUDA_TRY(c, cudaGetLastError());
 
   // unit order, then the raster into the caller's image (accumulated when the groups are split)

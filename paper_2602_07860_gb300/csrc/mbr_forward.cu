@@ -3,7 +3,7 @@
 //   face_normals_kernel  a0: area-weighted vertex normals (face cross products, atomics)
 //   xform_kernel         a1: motion + camera + projection of every vertex at every slot time
 //   setup_kernel         a4 setup: per (record set, face) local-frame coefficients (TriRec)
-//   bin_kernel<FILL>     a3: per (group, face) swept r_soft-dilated bounding box -> tile bins
+//   bin_*kernel<FILL>    a3: per (group, face) swept bounding box -> core and soft tile bins
 //   scan kernels         exclusive scan of the bin counts (CSR offsets)
 //   raster_fwd_persistent a4-a8: barycentric solve, coverage, z-test, soft alpha, shading,
 //                        temporal average; one float4 store per pixel (or one float4 atomic
@@ -156,11 +156,23 @@ __device__ __forceinline__ bool pixel_range(float xmin, float xmax, float ymin, 
 }
 
 // ---------------------------------------------------------------- a3: tile binning
+// One pass computes both bin sets of a render (core: undilated swept box; soft: dilated by
+// r_soft) from one swept box per (group, face).  Count pass: per-(group, tile) counts; fill pass:
+// face ids into the CSR lists through the cursors (a copy of the offsets).
+
+// tile range of one dilated box; false if it covers no pixel centre
+__device__ __forceinline__ bool tile_range(float xmin, float xmax, float ymin, float ymax, float r, int W, int H,
+                                           int tw, int th, int& tx0, int& tx1, int& ty0, int& ty1) {
+  int i0, i1, j0, j1;
+  if (!pixel_range(xmin - r, xmax + r, ymin - r, ymax + r, W, H, i0, i1, j0, j1)) return false;
+  tx0 = i0 / tw; tx1 = i1 / tw; ty0 = j0 / th; ty1 = j1 / th;
+  return true;
+}
+
 template <bool FILL>
-__global__ void bin_kernel(const TriRec* __restrict__ recs, int F, const Group* __restrict__ groups,
-                           int G, int W, int H, int tw, int th, int tiles_x, int n_tiles, float r,
-                           int32_t* __restrict__ counts_or_cursor, int32_t* __restrict__ list,
-                           const int32_t* __restrict__ bin_end, int list_cap, int* __restrict__ status) {
+__global__ void bin_kernel(const TriRec* __restrict__ recs, int F, const Group* __restrict__ groups, int G, int W,
+                           int H, int tw, int th, int tiles_x, int n_tiles, float r_core, float r_soft, BinTargets t,
+                           int* __restrict__ status) {
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (size_t)G * F) return;
   const int g = (int)(idx / F), f = (int)(idx - (size_t)g * F);
@@ -169,76 +181,81 @@ __global__ void bin_kernel(const TriRec* __restrict__ recs, int F, const Group* 
   if (__float_as_uint(rec.f4[kR_Z].w) & kFlagCulled) return;
   float xmin, xmax, ymin, ymax;
   swept_bbox(rec, gr.tau_lo, gr.tau_hi, xmin, xmax, ymin, ymax);
-  int i0, i1, j0, j1;
-  if (!pixel_range(xmin - r, xmax + r, ymin - r, ymax + r, W, H, i0, i1, j0, j1)) return;
-  const int tx0 = i0 / tw, tx1 = i1 / tw, ty0 = j0 / th, ty1 = j1 / th;
-  int32_t* base = counts_or_cursor + (size_t)g * n_tiles;
-  for (int ty = ty0; ty <= ty1; ++ty)
-    for (int tx = tx0; tx <= tx1; ++tx) {
-      const int b = ty * tiles_x + tx;
-      const int slot = atomicAdd(base + b, 1);
-      if (FILL) {
-        // the fill pass revisits exactly the counted (group, face, tile) triples; the check
-        // only guards the list against a mismatch
-        if (slot < bin_end[(size_t)g * n_tiles + b + 1] && slot < list_cap) list[slot] = f;
-        else atomicOr(status, kStatusBinOverflow);
+  const float rr[2] = {r_core, r_soft};
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    int tx0, tx1, ty0, ty1;
+    if (!tile_range(xmin, xmax, ymin, ymax, rr[q], W, H, tw, th, tx0, tx1, ty0, ty1)) continue;
+    int32_t* base = t.counts_or_cursor[q] + (size_t)g * n_tiles;
+    for (int ty = ty0; ty <= ty1; ++ty)
+      for (int tx = tx0; tx <= tx1; ++tx) {
+        const int b = ty * tiles_x + tx;
+        const int slot = atomicAdd(base + b, 1);
+        if (FILL) {
+          // the fill pass revisits exactly the counted triples; the check only guards the list
+          if (slot < t.off[q][(size_t)g * n_tiles + b + 1] && slot < t.cap[q]) t.list[q][slot] = f;
+          else atomicOr(status, kStatusBinOverflow);
+        }
       }
-    }
+  }
 }
 
 // Two-level variant (images of up to kSmemBinTiles tiles): a CTA takes 256 faces of ONE group
-// (grid.y = group) and counts its (tile, face) entries in a shared-memory histogram over the
-// tiles; the count pass adds the histogram to the global counts, the fill pass reserves one
-// range per (CTA, tile) in the global cursors and places its entries with shared-memory atomics.
-// Global atomics fall from one per entry to one per (CTA, tile) touched.
+// (grid.y = group) and counts its (tile, face) entries in shared-memory histograms over the
+// tiles (one per bin set); the count pass adds them to the global counts, the fill pass reserves
+// one range per (CTA, tile) in the global cursors and places its entries with shared-memory
+// atomics.  Global atomics fall from one per entry to one per (CTA, tile) touched.
 constexpr int kSmemBinTiles = 4096;
 
 template <bool FILL>
 __global__ void bin_smem_kernel(const TriRec* __restrict__ recs, int F, const Group* __restrict__ groups, int W,
-                                int H, int tw, int th, int tiles_x, int n_tiles, float r,
-                                int32_t* __restrict__ counts_or_cursor, int32_t* __restrict__ list,
-                                const int32_t* __restrict__ bin_end, int list_cap, int* __restrict__ status) {
-  extern __shared__ int sh[];  // [n_tiles]
+                                int H, int tw, int th, int tiles_x, int n_tiles, float r_core, float r_soft,
+                                BinTargets t, int* __restrict__ status) {
+  extern __shared__ int sh[];  // [2][n_tiles]
   const int g = blockIdx.y;
-  for (int i = threadIdx.x; i < n_tiles; i += blockDim.x) sh[i] = 0;
+  for (int i = threadIdx.x; i < 2 * n_tiles; i += blockDim.x) sh[i] = 0;
   __syncthreads();
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  bool have = false;
-  int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+  bool have[2] = {false, false};
+  int tx0[2], tx1[2], ty0[2], ty1[2];
   if (f < F) {
     const Group& gr = groups[g];
     const TriRec& rec = recs[(size_t)gr.rec_set * F + f];
     if (!(__float_as_uint(rec.f4[kR_Z].w) & kFlagCulled)) {
       float xmin, xmax, ymin, ymax;
       swept_bbox(rec, gr.tau_lo, gr.tau_hi, xmin, xmax, ymin, ymax);
-      int i0, i1, j0, j1;
-      if (pixel_range(xmin - r, xmax + r, ymin - r, ymax + r, W, H, i0, i1, j0, j1)) {
-        have = true;
-        tx0 = i0 / tw; tx1 = i1 / tw; ty0 = j0 / th; ty1 = j1 / th;
-      }
+      have[0] = tile_range(xmin, xmax, ymin, ymax, r_core, W, H, tw, th, tx0[0], tx1[0], ty0[0], ty1[0]);
+      have[1] = tile_range(xmin, xmax, ymin, ymax, r_soft, W, H, tw, th, tx0[1], tx1[1], ty0[1], ty1[1]);
     }
   }
-  if (have)
-    for (int ty = ty0; ty <= ty1; ++ty)
-      for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&sh[ty * tiles_x + tx], 1);
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+    if (have[q])
+      for (int ty = ty0[q]; ty <= ty1[q]; ++ty)
+        for (int tx = tx0[q]; tx <= tx1[q]; ++tx) atomicAdd(&sh[q * n_tiles + ty * tiles_x + tx], 1);
   __syncthreads();
-  int32_t* base = counts_or_cursor + (size_t)g * n_tiles;
   if (!FILL) {
-    for (int i = threadIdx.x; i < n_tiles; i += blockDim.x)
-      if (sh[i]) atomicAdd(base + i, sh[i]);
+    for (int i = threadIdx.x; i < 2 * n_tiles; i += blockDim.x) {
+      const int q = i >= n_tiles, b = i - q * n_tiles;
+      if (sh[i]) atomicAdd(t.counts_or_cursor[q] + (size_t)g * n_tiles + b, sh[i]);
+    }
     return;
   }
-  for (int i = threadIdx.x; i < n_tiles; i += blockDim.x)
-    if (sh[i]) sh[i] = atomicAdd(base + i, sh[i]);  // first slot of this CTA's range
+  for (int i = threadIdx.x; i < 2 * n_tiles; i += blockDim.x) {
+    const int q = i >= n_tiles, b = i - q * n_tiles;
+    if (sh[i]) sh[i] = atomicAdd(t.counts_or_cursor[q] + (size_t)g * n_tiles + b, sh[i]);  // first slot of the range
+  }
   __syncthreads();
-  if (have)
-    for (int ty = ty0; ty <= ty1; ++ty)
-      for (int tx = tx0; tx <= tx1; ++tx) {
-        const int b = ty * tiles_x + tx;
-        const int slot = atomicAdd(&sh[b], 1);
-        if (slot < bin_end[(size_t)g * n_tiles + b + 1] && slot < list_cap) list[slot] = f;
-        else atomicOr(status, kStatusBinOverflow);
-      }
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+    if (have[q])
+      for (int ty = ty0[q]; ty <= ty1[q]; ++ty)
+        for (int tx = tx0[q]; tx <= tx1[q]; ++tx) {
+          const int b = ty * tiles_x + tx;
+          const int slot = atomicAdd(&sh[q * n_tiles + b], 1);
+          if (slot < t.off[q][(size_t)g * n_tiles + b + 1] && slot < t.cap[q]) t.list[q][slot] = f;
+          else atomicOr(status, kStatusBinOverflow);
+        }
 }
 
 // ---------------------------------------------------------------- exclusive scan (CSR offsets)
@@ -657,28 +674,28 @@ void launch_setup(const float4* pos, const int32_t* faces, int F, int V, const i
 }
 
 void launch_bin(bool fill, const TriRec* recs, int F, const Group* groups, int G, int W, int H, int tw, int th,
-                int tiles_x, int n_tiles, float r, int32_t* counts_or_cursor, int32_t* list,
-                const int32_t* bin_off, int list_cap, int* status, cudaStream_t st) {
+                int tiles_x, int n_tiles, float r_core, float r_soft, const BinTargets& t, int* status,
+                cudaStream_t st) {
   const size_t n = (size_t)G * F;
   if (!n) return;
   if (n_tiles <= kSmemBinTiles && G <= 65535) {
     const dim3 grid((unsigned)((F + 255) / 256), (unsigned)G);
-    const size_t smem = sizeof(int) * (size_t)n_tiles;
+    const size_t smem = sizeof(int) * 2 * (size_t)n_tiles;
     if (fill)
-      bin_smem_kernel<true><<<grid, 256, smem, st>>>(recs, F, groups, W, H, tw, th, tiles_x, n_tiles, r,
-                                                     counts_or_cursor, list, bin_off, list_cap, status);
+      bin_smem_kernel<true><<<grid, 256, smem, st>>>(recs, F, groups, W, H, tw, th, tiles_x, n_tiles, r_core, r_soft,
+                                                     t, status);
     else
-      bin_smem_kernel<false><<<grid, 256, smem, st>>>(recs, F, groups, W, H, tw, th, tiles_x, n_tiles, r,
-                                                      counts_or_cursor, list, bin_off, list_cap, status);
+      bin_smem_kernel<false><<<grid, 256, smem, st>>>(recs, F, groups, W, H, tw, th, tiles_x, n_tiles, r_core, r_soft,
+                                                      t, status);
     return;
   }
   const unsigned blocks = (unsigned)((n + 255) / 256);
   if (fill)
-    bin_kernel<true><<<blocks, 256, 0, st>>>(recs, F, groups, G, W, H, tw, th, tiles_x, n_tiles, r, counts_or_cursor,
-                                             list, bin_off, list_cap, status);
+    bin_kernel<true><<<blocks, 256, 0, st>>>(recs, F, groups, G, W, H, tw, th, tiles_x, n_tiles, r_core, r_soft, t,
+                                             status);
   else
-    bin_kernel<false><<<blocks, 256, 0, st>>>(recs, F, groups, G, W, H, tw, th, tiles_x, n_tiles, r, counts_or_cursor,
-                                              list, bin_off, list_cap, status);
+    bin_kernel<false><<<blocks, 256, 0, st>>>(recs, F, groups, G, W, H, tw, th, tiles_x, n_tiles, r_core, r_soft, t,
+                                              status);
 }
 
 size_t scan_temp_ints(int n) { return (size_t)(n + kScanBlock - 1) / kScanBlock + 1; }

@@ -17,9 +17,16 @@ void launch_xform(const float* verts, const float* nacc, int V, const SlotXform*
                   float4* pos, float4* nrm, cudaStream_t st);
 void launch_setup(const float4* pos, const int32_t* faces, int F, int V, const int2* set_slots, int n_sets,
                   float znear, TriRec* recs, cudaStream_t st);
+// both bin sets of a render: [0] core (undilated), [1] soft (dilated by r_soft)
+struct BinTargets {
+  int32_t* counts_or_cursor[2];  // count pass: zeroed counts; fill pass: cursors (copies of the offsets)
+  int32_t* list[2];              // fill pass: CSR face lists
+  const int32_t* off[2];         // fill pass: CSR offsets
+  int cap[2];                    // fill pass: list capacities
+};
 void launch_bin(bool fill, const TriRec* recs, int F, const Group* groups, int G, int W, int H, int tw, int th,
-                int tiles_x, int n_tiles, float r, int32_t* counts_or_cursor, int32_t* list,
-                const int32_t* bin_off, int list_cap, int* status, cudaStream_t st);
+                int tiles_x, int n_tiles, float r_core, float r_soft, const BinTargets& t, int* status,
+                cudaStream_t st);
 size_t scan_temp_ints(int n);
 void launch_scan(const int32_t* in, int n, int32_t* out, int32_t* temp, cudaStream_t st);
 // persistent raster launches; kind 0 plain only, 1 fast only, 2 mixed
