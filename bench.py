@@ -205,6 +205,26 @@ def extra_workloads(mbr, scenes, torch, np, world):
                              ctx5.render_blur_backward(vv, ff, aa, mo, ca, T, H, W, G5, solver, reuse_forward=True)), 2)
         c5[solver] = {"fwdbwd_ms": ms, "samples_per_s": world * H * W * T / (ms / 1e3)}
     out["c5_large"] = c5
+    # segmentation analysis on the benchmark workload: linear segments of the fast solver vs the
+    # exact per-sub-frame render (plain): time and image error
+    import dataclasses
+    s2 = scenes.config2()
+    v2, f2, a2 = mbr.mesh_tensors(s2)
+    mo2, ca2 = mbr.motion_from_dict(s2["motion"]), mbr.camera_from_dict(s2["camera"])
+    T2, H2, W2 = s2["T"], s2["H"], s2["W"]
+    G2 = torch.ones((H2, W2, 4), device=dev)
+    ctx2 = mbr.Context()
+    exact = ctx2.render_blur(v2, f2, a2, mo2, ca2, T2, H2, W2, "plain").clone()
+    sweep = {}
+    for S in (6, 12, 24, 48):
+        m = dataclasses.replace(mo2, segments=S)
+        img = ctx2.render_blur(v2, f2, a2, m, ca2, T2, H2, W2, "fast")
+        err = (img - exact).abs()
+        ms = timeit(lambda: (ctx2.render_blur(v2, f2, a2, m, ca2, T2, H2, W2, "fast"),
+                             ctx2.render_blur_backward(v2, f2, a2, m, ca2, T2, H2, W2, G2, "fast",
+                                                       reuse_forward=True)), 5)
+        sweep[str(S)] = {"fwdbwd_ms": ms, "mean_abs_err_vs_exact": float(err.mean()), "max_abs_err_vs_exact": float(err.max())}
+    out["segment_sweep"] = sweep
     return out
 
 

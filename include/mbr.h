@@ -51,6 +51,7 @@ extern "C" {
 
 #define MBR_TRANSLATE 0
 #define MBR_ROTATE 1
+#define MBR_PARABOLIC 2
 
 #define MBR_TIME_PAPER 0    /* t_k = k/(T-1), T = 1 -> 0.5 (Sec. 3.2)  */
 #define MBR_TIME_MIDPOINT 1 /* t_k = (k + 0.5)/T                        */
@@ -68,10 +69,17 @@ typedef struct {
 /* Rigid motion over the exposure, t in [0, 1] (Sec. "Motion Parameters"). */
 typedef struct {
   int32_t kind;     /* MBR_TRANSLATE: P(t) = v + offset + t dir
-                       MBR_ROTATE:    P(t) = R(omega t) v, right-handed about unit(axis)   */
+                       MBR_ROTATE:    P(t) = R(omega t) v, right-handed about unit(axis)
+                       MBR_PARABOLIC: P(t) = R(omega t) v + offset + t dir + t^2 acc, the
+                                      combined rotation and parabolic translation of the
+                                      appendix's parabolic recovery (there: omega = pi about
+                                      +y, offset (0.5, -0.5, 0.5), dir (-1, 4, -1),
+                                      acc (0, -4, 0))                                      */
   int32_t segments; /* fast solver's linear segments; 0 = 1 (translation) or
-                       ceil(12 |omega| / 2 pi) (rotation; 12 per turn, Sec. 3.3)           */
+                       ceil(12 |omega| / 2 pi), at least 1 (rotation and parabolic; 12 per
+                       turn, Sec. 3.3)                                                     */
   float offset[3], dir[3], axis[3], omega;
+  float acc[3];     /* MBR_PARABOLIC only: quadratic term of the translation              */
 } mbr_motion;
 
 /* Camera, shading and soft-coverage parameters. */

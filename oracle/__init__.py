@@ -34,6 +34,7 @@ class OrcScene(ctypes.Structure):
         ("verts", POINTER(c_double)), ("faces", POINTER(c_int32)), ("albedo", POINTER(c_double)),
         ("motion_kind", c_int32), ("segments", c_int32),
         ("offset", c_double * 3), ("dir", c_double * 3), ("axis", c_double * 3), ("omega", c_double),
+        ("acc", c_double * 3),
         ("view", c_double * 12), ("tan_half_fov", c_double), ("znear", c_double),
         ("light_dir", c_double * 3), ("k_ambient", c_double), ("k_diffuse", c_double),
         ("delta", c_double), ("time_rule", c_int32), ("T", c_int32), ("H", c_int32), ("W", c_int32),
@@ -87,12 +88,13 @@ class _Scene:
         s.verts = _ptr(self.verts, c_double)
         s.faces = _ptr(self.faces, c_int32)
         s.albedo = _ptr(self.albedo, c_double)
-        s.motion_kind = 0 if m["kind"] == "translate" else 1
+        s.motion_kind = {"translate": 0, "rotate": 1, "parabolic": 2}[m["kind"]]
         s.segments = int(m.get("segments", 0))
         s.offset[:] = [float(x) for x in m["offset"]]
         s.dir[:] = [float(x) for x in m["dir"]]
         s.axis[:] = [float(x) for x in m["axis"]]
         s.omega = float(m["omega"])
+        s.acc[:] = [float(x) for x in m.get("acc", (0.0, 0.0, 0.0))]
         s.view[:] = [float(x) for x in np.asarray(c["view"]).reshape(-1)]
         s.tan_half_fov = float(c["tan_half_fov"])
         s.znear = float(c["znear"])

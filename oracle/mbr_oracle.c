@@ -111,17 +111,24 @@ static int32_t sample_key_x(const orc_scene* s, int32_t k) {
 
 /* ------------------------------------------------------------------ motion + camera */
 
-/* Motion parameters (scene settings): translation v + offset + t dir; rotation R(omega t) v. */
+/* Motion parameters (scene settings): translation v + offset + t dir; rotation R(omega t) v;
+ * the parabolic recovery's motion: the vertex rotated by R(omega t), then translated by a
+ * quadratic in t, offset + t dir + t^2 acc (the appendix writes it in s = 0.5 - t). */
 static void place(const orc_scene* s, double t, const double p[3], double out[3]) {
   if (s->motion_kind == 0) {
     for (int i = 0; i < 3; ++i) out[i] = p[i] + s->offset[i] + t * s->dir[i];
-  } else {
+  } else if (s->motion_kind == 1) {
     rotate_vec(s->axis, s->omega * t, p, out);
+  } else {
+    double r[3];
+    if (s->omega != 0.0) rotate_vec(s->axis, s->omega * t, p, r);
+    else { r[0] = p[0]; r[1] = p[1]; r[2] = p[2]; }
+    for (int i = 0; i < 3; ++i) out[i] = r[i] + s->offset[i] + t * s->dir[i] + t * t * s->acc[i];
   }
 }
 
 static void orient(const orc_scene* s, double t, const double n[3], double out[3]) {
-  if (s->motion_kind == 0) {
+  if (s->motion_kind == 0 || (s->motion_kind == 2 && s->omega == 0.0)) {
     out[0] = n[0]; out[1] = n[1]; out[2] = n[2];
   } else {
     rotate_vec(s->axis, s->omega * t, n, out);
@@ -310,8 +317,8 @@ static void chain_state(const orc_scene* s, double t, const double* gst, double*
     double dP[3];
     for (int i = 0; i < 3; ++i) dP[i] = m[i] * dxc + m[4 + i] * dyc + m[8 + i] * dzc;
     double dv[3], dn[3];
-    if (s->motion_kind == 0) {
-      memcpy(dv, dP, sizeof(dP));
+    if (s->motion_kind == 0 || (s->motion_kind == 2 && s->omega == 0.0)) {
+      memcpy(dv, dP, sizeof(dP)); /* translations do not depend on v: d P / d v = identity */
       dn[0] = g[2]; dn[1] = g[3]; dn[2] = g[4];
     } else {
       rotate_vec_T(s->axis, s->omega * t, dP, dv);

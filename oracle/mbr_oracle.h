@@ -28,9 +28,13 @@ typedef struct {
   const double* verts;    /* [V,3] base vertex positions (world)                         */
   const int32_t* faces;   /* [F,3] vertex indices                                          */
   const double* albedo;   /* [V,3] per-vertex colour                                       */
-  int32_t motion_kind;    /* 0: P(t) = v + offset + t*dir ; 1: P(t) = R(omega*t, axis) v   */
+  int32_t motion_kind;    /* 0: P(t) = v + offset + t*dir ; 1: P(t) = R(omega*t, axis) v ;
+                             2: P(t) = R(omega*t, axis) v + offset + t*dir + t^2*acc (the
+                             rotation plus parabolic translation of the appendix's parabolic
+                             recovery)                                                        */
   int32_t segments;       /* linear segments of the fast solver; 0 = default rule          */
   double offset[3], dir[3], axis[3], omega;
+  double acc[3];          /* kind 2: quadratic translation term                             */
   double view[12];        /* 3x4 world->camera, camera +z forward                          */
   double tan_half_fov, znear;
   double light_dir[3];    /* direction towards the light, world space (normalised here)    */

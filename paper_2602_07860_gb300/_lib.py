@@ -11,7 +11,7 @@ from . import build as _build
 
 MBR_OK, MBR_ERR_ARG, MBR_ERR_CUDA, MBR_ERR_OOM, MBR_ERR_TIMEOUT, MBR_ERR_DEVICE = range(6)
 MBR_PLAIN, MBR_FAST = 0, 1
-MBR_TRANSLATE, MBR_ROTATE = 0, 1
+MBR_TRANSLATE, MBR_ROTATE, MBR_PARABOLIC = 0, 1, 2
 MBR_TIME_PAPER, MBR_TIME_MIDPOINT = 0, 1
 SOLVERS = {"plain": MBR_PLAIN, "fast": MBR_FAST}
 
@@ -27,7 +27,7 @@ class MbrMesh(ctypes.Structure):
 
 class MbrMotion(ctypes.Structure):
     _fields_ = [("kind", c_int32), ("segments", c_int32), ("offset", c_float * 3), ("dir", c_float * 3),
-                ("axis", c_float * 3), ("omega", c_float)]
+                ("axis", c_float * 3), ("omega", c_float), ("acc", c_float * 3)]
 
 
 class MbrCamera(ctypes.Structure):

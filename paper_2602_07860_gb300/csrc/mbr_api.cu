@@ -169,8 +169,12 @@ SlotXform slot_xform(const mbr_motion* m, const mbr_camera* cam, double t) {
   } else {
     double k[3] = {m->axis[0], m->axis[1], m->axis[2]};
     const double n = std::sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
-    for (double& x : k) x /= n;
-    rotation(k, (double)m->omega * t, Rm);
+    if (n > 0) {
+      for (double& x : k) x /= n;
+      rotation(k, (double)m->omega * t, Rm);
+    }
+    if (m->kind == MBR_PARABOLIC)
+      for (int i = 0; i < 3; ++i) b[i] = (double)m->offset[i] + t * (double)m->dir[i] + t * t * (double)m->acc[i];
   }
   SlotXform x;
   std::memset(&x, 0, sizeof(x));
@@ -195,10 +199,10 @@ int validate(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const m
   if (T < 1 || T > (1 << 20)) return fail(c, MBR_ERR_ARG, "bad T=%d", T);
   if (H < 1 || W < 1 || H > 16384 || W > 16384) return fail(c, MBR_ERR_ARG, "bad image size %dx%d", H, W);
   if (solver != MBR_PLAIN && solver != MBR_FAST) return fail(c, MBR_ERR_ARG, "bad solver %d", solver);
-  if (motion->kind != MBR_TRANSLATE && motion->kind != MBR_ROTATE)
+  if (motion->kind != MBR_TRANSLATE && motion->kind != MBR_ROTATE && motion->kind != MBR_PARABOLIC)
     return fail(c, MBR_ERR_ARG, "bad motion kind %d", motion->kind);
   if (motion->segments < 0 || motion->segments > 1000000) return fail(c, MBR_ERR_ARG, "bad segments");
-  if (motion->kind == MBR_ROTATE &&
+  if ((motion->kind == MBR_ROTATE || (motion->kind == MBR_PARABOLIC && motion->omega != 0.f)) &&
       !(motion->axis[0] * motion->axis[0] + motion->axis[1] * motion->axis[1] + motion->axis[2] * motion->axis[2] > 0.f))
     return fail(c, MBR_ERR_ARG, "zero rotation axis");
   if (!(cam->tan_half_fov > 0.f) || !(cam->delta > 0.f)) return fail(c, MBR_ERR_ARG, "bad camera fov/delta");
@@ -604,6 +608,8 @@ int forward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, con
 bool same_motion(const mbr_motion& a, const mbr_motion& b) {
   for (int i = 0; i < 3; ++i)
     if (a.offset[i] != b.offset[i] || a.dir[i] != b.dir[i] || a.axis[i] != b.axis[i]) return false;
+  for (int i = 0; i < 3; ++i)
+    if (a.acc[i] != b.acc[i]) return false;
   return a.kind == b.kind && a.segments == b.segments && a.omega == b.omega;
 }
 

@@ -14,23 +14,28 @@ from . import _lib
 from ._lib import MbrCamera, MbrError, MbrItem, MbrMesh, MbrMotion
 
 
+_KINDS = {"translate": _lib.MBR_TRANSLATE, "rotate": _lib.MBR_ROTATE, "parabolic": _lib.MBR_PARABOLIC}
+
+
 @dataclass
 class Motion:
-    kind: str = "translate"          # 'translate' | 'rotate'
+    kind: str = "translate"          # 'translate' | 'rotate' | 'parabolic' (see include/mbr.h)
     offset: tuple = (0.0, 0.0, 0.0)
     dir: tuple = (0.0, 0.0, 0.0)
     axis: tuple = (0.0, 1.0, 0.0)
     omega: float = 0.0
     segments: int = 0
+    acc: tuple = (0.0, 0.0, 0.0)     # parabolic: quadratic term of the translation
 
     def c(self):
         m = MbrMotion()
-        m.kind = _lib.MBR_TRANSLATE if self.kind == "translate" else _lib.MBR_ROTATE
+        m.kind = _KINDS[self.kind]
         m.segments = int(self.segments)
         m.offset[:] = [float(x) for x in self.offset]
         m.dir[:] = [float(x) for x in self.dir]
         m.axis[:] = [float(x) for x in self.axis]
         m.omega = float(self.omega)
+        m.acc[:] = [float(x) for x in self.acc]
         return m
 
 
@@ -60,7 +65,8 @@ class Camera:
 
 def motion_from_dict(m):
     return Motion(kind=m["kind"], offset=tuple(m["offset"]), dir=tuple(m["dir"]), axis=tuple(m["axis"]),
-                  omega=float(m["omega"]), segments=int(m.get("segments", 0)))
+                  omega=float(m["omega"]), segments=int(m.get("segments", 0)),
+                  acc=tuple(m.get("acc", (0.0, 0.0, 0.0))))
 
 
 def camera_from_dict(c):

@@ -272,6 +272,17 @@ def rotate(axis, omega, segments=0):
                 omega=float(omega), segments=segments)
 
 
+def parabolic(axis=(0.0, 1.0, 0.0), omega=math.pi, offset=(0.5, -0.5, 0.5), dir=(-1.0, 4.0, -1.0),
+              acc=(0.0, -4.0, 0.0), segments=0):
+    """Rotation R(omega t) about unit(axis) plus the translation offset + t dir + t^2 acc.  The
+    defaults are the appendix's parabolic trajectory: a half turn about +y and
+    T(t) = (s, -4 s^2 + 0.5, s) with s = 0.5 - t."""
+    a = np.asarray(axis, dtype=np.float64)
+    return dict(kind="parabolic", offset=np.asarray(offset, np.float64), dir=np.asarray(dir, np.float64),
+                axis=a / np.linalg.norm(a), omega=float(omega), segments=int(segments),
+                acc=np.asarray(acc, np.float64))
+
+
 def scene(verts, faces, albedo, motion, cam, T, H, W):
     return dict(verts=np.ascontiguousarray(verts, dtype=np.float64),
                 faces=np.ascontiguousarray(faces, dtype=np.int32),
@@ -369,6 +380,8 @@ def small_scene(kind="rotate", subdiv=2, T=8, H=40, W=72, seed=MASTER_SEED + 100
     alb = random_albedo(len(v), rng)
     if kind == "rotate":
         mot = rotate(random_unit(rng), omega, segments)
+    elif kind == "parabolic":
+        mot = parabolic(segments=segments)
     else:
         mot = translate(d, segments=segments)
     cam = camera(look_at(orbit_eye(4.0, eye[0], eye[1])), fov_deg=fov, time_rule=time_rule)

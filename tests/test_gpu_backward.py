@@ -51,6 +51,8 @@ GRAD_SCENES = {
     "rotate_wide_soft": lambda: dict(scenes.small_scene("rotate", subdiv=1, T=6, H=32, W=40),
                                      camera=dict(scenes.small_scene("rotate", subdiv=1)["camera"], delta=2e-3)),
     "c1": lambda: scenes.config1(),
+    "parabolic": lambda: dict(scenes.small_scene("parabolic", subdiv=2, T=10, H=40, W=48),
+                              camera=scenes.camera(scenes.look_at(scenes.orbit_eye(5.0, 0, 10.0)))),
 }
 
 

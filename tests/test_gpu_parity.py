@@ -43,6 +43,9 @@ SCENES = {
     "rotate_fast_spin_S_gt_T": lambda: scenes.small_scene("rotate", subdiv=2, T=5, H=36, W=36, omega=6 * math.pi),
     "subdiv4_sh_96x80": lambda: scenes.config2(T=16, H=80, W=96),
     "single_subframe": lambda: scenes.small_scene("rotate", subdiv=2, T=1, H=33, W=47),
+    # the appendix's combined rotation and parabolic translation (6 segments for the half turn)
+    "parabolic_appendix": lambda: dict(scenes.small_scene("parabolic", subdiv=2, T=16, H=48, W=64),
+                                       camera=scenes.camera(scenes.look_at(scenes.orbit_eye(5.0, 0, 10.0)))),
 }
 
 
@@ -164,3 +167,19 @@ def test_bad_arguments_return_errors(ctx):
         ctx.set_tuning(12, 8, 0)
     # the context stays usable after errors
     assert np.isfinite(gpu_render(ctx, sc, "fast")).all()
+
+
+def test_segment_count_convergence(ctx):
+    """Segmentation analysis: the fast solver linearises the rotation per segment, so its image
+    approaches the exact per-sub-frame render as segments go 6 -> 12 -> 24 -> 48 (one turn)."""
+    import dataclasses
+    sc = scenes.config2(T=48, H=96, W=96)
+    v, f, a, mo, ca = gpu_inputs(sc)
+    exact = ctx.render_blur(v, f, a, mo, ca, sc["T"], sc["H"], sc["W"], "plain")
+    errs = []
+    for S in (6, 12, 24, 48):
+        img = ctx.render_blur(v, f, a, dataclasses.replace(mo, segments=S), ca, sc["T"], sc["H"], sc["W"], "fast")
+        errs.append(float((img - exact).abs().mean()))
+    torch.cuda.synchronize()
+    assert all(errs[i + 1] < errs[i] for i in range(3)), errs
+    assert errs[-1] < 0.25 * errs[0], errs

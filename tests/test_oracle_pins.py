@@ -480,3 +480,54 @@ def test_brute_force_tiny_mesh(mode):
     b = _brute_force(sc, mode)
     assert np.max(np.abs(a - b)) < 1e-9
     assert a[..., 3].max() > 0.5 and (a[..., 3] > 0).mean() < 1.0
+
+
+def _with_motion(sc, motion):
+    return dict(sc, motion=motion)
+
+
+@pytest.mark.parametrize("mode", ["exact", "linear", "fast"])
+def test_parabolic_motion_reduces_to_translation_and_rotation(mode):
+    """The parabolic kind with no rotation and no quadratic term is the translation kind, and with
+    no translation it is the rotation kind: identical images, bit for bit."""
+    sc = scenes.small_scene("translate", subdiv=2, T=6, H=24, W=32, d=(0.7, 0.2, 0.3))
+    m = sc["motion"]
+    par = scenes.parabolic(axis=(0.0, 1.0, 0.0), omega=0.0, offset=m["offset"], dir=m["dir"], acc=(0.0, 0.0, 0.0))
+    a = oracle.render(sc, mode)["rgba"]
+    b = oracle.render(_with_motion(sc, par), mode)["rgba"]
+    assert np.array_equal(a, b)
+    scr = scenes.small_scene("rotate", subdiv=2, T=6, H=24, W=32)
+    mr = scr["motion"]
+    par = scenes.parabolic(axis=mr["axis"], omega=mr["omega"], offset=(0, 0, 0), dir=(0, 0, 0), acc=(0, 0, 0))
+    a = oracle.render(scr, mode)["rgba"]
+    b = oracle.render(_with_motion(scr, par), mode)["rgba"]
+    assert np.array_equal(a, b)
+
+
+def test_parabolic_trajectory_is_quadratic():
+    """With omega = 0 a vertex moves on a quadratic: its camera-space position has a constant second
+    difference 2 acc h^2 (the camera is an affine map), and a zero one for acc = 0."""
+    sc = scenes.small_scene("translate", subdiv=1, T=4, H=16, W=16)
+    cam = sc["camera"]
+    R = np.asarray(cam["view"]).reshape(3, 4)[:, :3]
+    acc = np.array([0.3, -4.0, 0.2])
+    par = scenes.parabolic(omega=0.0, offset=(0.1, 0.2, 0.0), dir=(-1.0, 4.0, -1.0), acc=acc)
+    s = _with_motion(sc, par)
+    th = cam["tan_half_fov"]
+
+    def camera_pos(t):
+        st = oracle.vertex_state(s, t)  # ndc x, ndc y, camera z
+        z = st[:, 2]
+        return np.stack([st[:, 0] * z * th, st[:, 1] * z * th, z], 1)
+
+    h = 0.125
+    for t in (0.25, 0.5, 0.75):
+        d2 = camera_pos(t + h) - 2 * camera_pos(t) + camera_pos(t - h)
+        assert np.allclose(d2, (R @ (2 * acc * h * h))[None, :], atol=1e-9)
+    # the appendix's trajectory: T(t) = (s, -4 s^2 + 0.5, s), s = 0.5 - t, peaks at t = 0.5
+    pap = scenes.parabolic(omega=0.0)
+    s2 = _with_motion(sc, pap)
+    p = {t: oracle.vertex_state(s2, t) for t in (0.0, 0.5, 1.0)}
+    disp = lambda t: (lambda st: np.stack([st[:, 0] * st[:, 2] * th, st[:, 1] * st[:, 2] * th, st[:, 2]], 1))(p[t])
+    up = disp(0.5) - 0.5 * (disp(0.0) + disp(1.0))
+    assert np.allclose(up, (R @ np.array([0.0, 1.0, 0.0]))[None, :], atol=1e-9)  # +1 in world y at mid-exposure
