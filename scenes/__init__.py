@@ -199,6 +199,31 @@ def surface_of_revolution(n_theta: int, n_rings: int, rng: np.random.Generator, 
     return v, _orient_outward_centroid(v, f)
 
 
+def uv_sphere(n_theta: int = 50, n_inner: int = 27):
+    """Unit UV sphere: n_inner rings of n_theta vertices between two poles, quads split in two and
+    polar fans.  The defaults give 1352 vertices and 2700 faces, the size of the template mesh of
+    the translational recovery experiment."""
+    ys = np.cos(np.linspace(0.0, math.pi, n_inner + 2))[1:-1]
+    rs = np.sqrt(np.maximum(0.0, 1.0 - ys ** 2))
+    th = np.arange(n_theta) * (2 * math.pi / n_theta)
+    ring = np.stack([rs[:, None] * np.cos(th)[None, :], np.broadcast_to(ys[:, None], (n_inner, n_theta)),
+                     -rs[:, None] * np.sin(th)[None, :]], axis=-1)
+    verts = np.concatenate([ring.reshape(-1, 3), [[0.0, 1.0, 0.0], [0.0, -1.0, 0.0]]], 0)
+    north, south = n_inner * n_theta, n_inner * n_theta + 1
+    faces = []
+    for i in range(n_inner - 1):
+        for j in range(n_theta):
+            a, b = i * n_theta + j, i * n_theta + (j + 1) % n_theta
+            c, d = a + n_theta, b + n_theta
+            faces += [[a, c, b], [b, c, d]]
+    for j in range(n_theta):
+        faces.append([north, j, (j + 1) % n_theta])
+        last = (n_inner - 1) * n_theta
+        faces.append([south, last + (j + 1) % n_theta, last + j])
+    f = np.asarray(faces, dtype=np.int32)
+    return verts, _orient_outward_centroid(verts, f)
+
+
 def _orient_outward_centroid(v, f):
     """Orient faces away from the y axis point at the face's height (surfaces of revolution)."""
     a, b, c = v[f[:, 0]], v[f[:, 1]], v[f[:, 2]]
