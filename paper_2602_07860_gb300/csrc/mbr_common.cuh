@@ -3,7 +3,7 @@
 // Data layout in HBM (per call, owned by the context):
 //   slot_pos[slot][V]  float4 (ndc x, ndc y, camera z, 0)   -- vertex state at a slot time
 //   slot_nrm[slot][V]  float4 (world normal xyz, 0)
-//   recs[set][F]       TriRec (7 x float4)                    -- per (record set, face) setup
+//   recs[set][F]       TriRec (11 x float4)                   -- per (record set, face) setup
 //   groups[G]          Group                                  -- samples sharing a record set
 //   bins               CSR over (group, tile): face ids       -- tile binning
 // A "slot" is a time at which vertices are placed exactly: the S+1 keyframes s/S of the fast
@@ -18,7 +18,6 @@ namespace mbr {
 constexpr int kMaxSpt = 4;            // samples per group (max)
 constexpr float kDetMin = 1e-10f;     // |det F| at or below: triangle skipped at that sample
 constexpr int kRecF4 = 11;            // float4s per triangle record
-constexpr int kRecF4Static = 4;       // float4s a static (plain-solver) record needs
 
 // Per (record set, face) triangle record.  Local frame: origin o = v0 at the set's first
 // keyframe; e1 = v1 - v0, e2 = v2 - v0 at that keyframe; d1, d2 = change of e1, e2 over the

@@ -4,11 +4,13 @@
 //   xform_kernel         a1: motion + camera + projection of every vertex at every slot time
 //   setup_kernel         a4 setup: per (record set, face) local-frame coefficients (TriRec)
 //   bin_*kernel<FILL>    a3: per (group, face) swept bounding box -> core and soft tile bins
+//                        (shared-memory histograms per CTA of one group, or global atomics)
 //   scan kernels         exclusive scan of the bin counts (CSR offsets)
 //   raster_fwd_persistent a4-a8: barycentric solve, coverage, z-test, soft alpha, shading,
 //                        temporal average; one float4 store per pixel (or one float4 atomic
 //                        add per pixel and group split)
 //   unit_*_kernel        visiting order of the raster's work units (largest estimate first)
+//   raster_fwd_count     work counters of the raster passes (measurement)
 //   count_kernel         N_cand (measurement)
 #include <cstdint>
 

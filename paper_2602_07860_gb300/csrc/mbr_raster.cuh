@@ -1,19 +1,21 @@
-// mbr_raster.cuh -- per-candidate arithmetic and the shared passes of the tiled raster kernels
-// (forward and adjoint).
+// mbr_raster.cuh -- per-candidate arithmetic, the pair passes and the work scheduling shared by
+// the persistent raster kernels (forward and adjoint).
 //
-// One CTA owns a TW x TH pixel tile (one pixel per thread) and a contiguous range of sample
-// groups; each warp owns an 8 x 4 pixel block of the tile and walks the tile's bin lists on its
-// own (no block-wide barriers inside a group).  For each group:
-//   pass 1  the tile's "core" candidates (swept bounding box, no soft dilation), 32 at a time:
-//           each lane marks which of the group's samples of one candidate can touch the warp's
-//           block and a pixel-reject box; a ballot keeps the live candidates and the warp
-//           evaluates them: edge functions of Eq. time-dependent2, coverage, perspective-correct
-//           z-test (Sec. 3.1).  Samples live in registers (SPT of them).
-//   pass 2  only if some pixel of the warp has an uncovered sample: the r_soft-dilated list,
-//           walked the same way, multiplies the soft-coverage factors 1 - exp(-d/delta)
-//           (Eqs. probability-function .. back) of the uncovered samples.
-// The forward then shades the winners (Eq. fore + Lambert) and accumulates; the adjoint adds a
-// third pass for the soft-term gradients.
+// Work units are (256-pixel patch, split of the sample groups); CTAs draw them from a cost-ordered
+// queue and hand them to their warps through a small shared-memory ring, and each warp owns an
+// 8 x 4 pixel block of a tile (no block-wide barriers inside a unit).  For each sample group
+// (SPT samples that share a record set) a warp walks the tile's bin lists in "pair passes":
+//   1. lanes over candidates: each lane tests one face of the list for the group's samples
+//      (swept boxes, pixel-reject box) and builds, as bit masks, which (pixel, sample) pairs of
+//      the block it can touch;
+//   2. a warp prefix scan over the pair counts;
+//   3. lanes over pairs: each lane evaluates one (candidate, pixel, sample) pair.
+// The core pass (swept bounding box, no soft dilation) evaluates the edge functions of
+// Eq. time-dependent2, coverage and the perspective-correct z-test (Sec. 3.1) and keeps the winner
+// per (pixel, sample) with a 64-bit atomicMax in shared memory.  The soft pass (r_soft-dilated
+// list, uncovered samples only) sums log(1 - exp(-d/delta)) of Eqs. probability-function .. back.
+// The forward shades the winners (Eq. fore + Lambert) and accumulates; the adjoint reruns both
+// passes and adds one for the soft-term gradients.
 #pragma once
 #include "mbr_common.cuh"
 

@@ -36,3 +36,18 @@ def test_laplacian_of_rigid_translation_is_zero_and_edges_of_closed_mesh():
     bump[0] += 0.1
     assert float(laplacian_delta_loss(bump, V, e)) > 0
     assert edge_opposites(F).shape[1] == 3 * f.shape[0] // 2  # closed: every edge has two faces
+
+
+def test_laplacian_of_one_moved_vertex_on_a_tetrahedron():
+    """Every vertex of a tetrahedron has the other three as neighbours.  Moving vertex 0 by e gives
+    Laplacians e at vertex 0 and -e/3 at the others: |e|^2 (1 + 3/9) in total."""
+    from paper_2602_07860_gb300.recovery import edge_index, laplacian_delta_loss
+    V = torch.tensor([[1., 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], dtype=torch.float64)
+    F = torch.tensor([[0, 1, 2], [0, 3, 1], [0, 2, 3], [1, 3, 2]])
+    e = edge_index(F, 4)
+    assert e.shape == (2, 12)
+    moved = V.clone()
+    step = torch.tensor([0.2, -0.1, 0.3], dtype=torch.float64)
+    moved[0] += step
+    expect = float((step * step).sum()) * (1.0 + 3.0 / 9.0)
+    assert abs(float(laplacian_delta_loss(moved, V, e)) - expect) < 1e-14
