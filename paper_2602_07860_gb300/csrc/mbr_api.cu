@@ -558,8 +558,10 @@ int upload_queue(mbr_ctx* c, const RasterParams* items, int n, cudaStream_t st, 
   return MBR_OK;
 }
 
+// pp_out (optional) receives the front half of this render
 int forward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mbr_camera* cam, int T, int H,
-                 int W, int solver, float* image, int dbg_k, int32_t* dbg_ids, cudaStream_t st) {
+                 int W, int solver, float* image, int dbg_k, int32_t* dbg_ids, cudaStream_t st,
+                 Prepared* pp_out = nullptr) {
   int rc = validate(c, mesh, motion, cam, T, H, W, solver);
   if (rc) return rc;
   if (!image && !dbg_ids) return fail(c, MBR_ERR_ARG, "null image");
@@ -576,6 +578,11 @@ int forward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, con
     P.out = (float4*)c->partial.p;
   } else {
     P.out = (float4*)image;
+    // per-sample state for a following adjoint: winner or log soft product (4 B) + status (1 B)
+    const size_t ns = (size_t)T * npix;
+    if ((rc = ensure(c, c->bstate, ns * 5 + 256, st))) return rc;
+    P.s_val = (float*)c->bstate.p;
+    P.s_stat = (uint8_t*)c->bstate.p + ns * 4;
   }
   if (pp.n_split > 1) CUDA_TRY(c, cudaMemsetAsync(P.out, 0, sizeof(float4) * npix, st));  // splits accumulate
   WorkQueue Q;
@@ -588,6 +595,7 @@ int forward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, con
   if ((rc = time_end(c, 0, st))) return rc;
   c->stats.launches += 1;
   c->stats.n_split = pp.n_split;
+  if (pp_out) *pp_out = pp;
   if (image && !dbg_ids) {
     if (!c->last_pp) c->last_pp = new (std::nothrow) Prepared();
     if (c->last_pp) {
@@ -631,8 +639,9 @@ bool matches_last_forward(const mbr_ctx* c, const mbr_mesh* mesh, const mbr_moti
          L.spt == c->spt && L.splits == c->splits;
 }
 
-// the adjoint (a9): front half (recomputed, or the last forward's when reuse is allowed and it
-// matches), adjoint raster, slot -> vertex chain, normals adjoint
+// the adjoint (a9): front half and forward raster state (the last forward's when reuse is allowed
+// and it matches, else recomputed: the forward raster runs again into scratch), adjoint raster,
+// slot -> vertex chain, normals adjoint
 int backward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mbr_camera* cam, int T, int H,
                   int W, int solver, const float* dl_dimage, float* dl_dverts, float* dl_dalbedo, cudaStream_t st,
                   bool reuse) {
@@ -643,8 +652,12 @@ int backward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, co
   if (reuse && matches_last_forward(c, mesh, motion, cam, T, H, W, solver)) {
     pp = *c->last_pp;
     c->stats.reused += 1;
-  } else if ((rc = prepare(c, mesh, motion, cam, T, H, W, solver, st, true, pp))) {
-    return rc;
+  } else {
+    // the forward raster writes the per-sample state (its image goes to scratch)
+    if ((rc = ensure(c, c->partial, sizeof(float4) * (size_t)H * W, st))) return rc;
+    if ((rc = forward_impl(c, mesh, motion, cam, T, H, W, solver, (float*)c->partial.p, -1, nullptr, st, &pp)))
+      return rc;
+    c->last.valid = false;  // the scratch image is not the caller's
   }
   RasterParams P = raster_params(c, ctx_bufs(c), mesh, cam, T, H, W, pp);
   const int V = mesh->V;
@@ -657,10 +670,9 @@ int backward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, co
   P.dl_dimage = (const float4*)dl_dimage;
   P.g_slot = (float4*)c->gslot.p;
   P.g_albedo = dl_dalbedo ? (float4*)c->galb.p : nullptr;
-  // per-sample state between the two adjoint kernels: log soft product (float) + status (byte)
+  // the forward raster's per-sample state
   const size_t ns = (size_t)T * H * W;
-  if ((rc = ensure(c, c->bstate, ns * 5 + 256, st))) return rc;
-  P.s_logp = (float*)c->bstate.p;
+  P.s_val = (float*)c->bstate.p;
   P.s_stat = (uint8_t*)c->bstate.p + ns * 4;
   WorkQueue Q;
   if ((rc = upload_queue(c, &P, 1, st, Q))) return rc;
@@ -1055,11 +1067,11 @@ void batch_write_params(mbr_ctx* c, const mbr_item* items, BatchState& B) {
     pp.soft_cap = I.cap[1];
     RasterParams P = raster_params(c, bufs, &it.mesh, &it.camera, it.T, it.H, it.W, pp);
     P.out = (float4*)it.image;
-    if (B.with_backward) {
+    if (B.with_backward) {  // the forward launch writes the per-sample state, the adjoint reads it
       P.dl_dimage = (const float4*)it.dl_dimage;
       P.g_slot = (float4*)(A + I.o_gslot);
       P.g_albedo = it.dl_dalbedo ? (float4*)(A + I.o_galb) : nullptr;
-      P.s_logp = (float*)(A + I.o_bstate);
+      P.s_val = (float*)(A + I.o_bstate);
       P.s_stat = (uint8_t*)(A + I.o_bstate) + (size_t)it.T * it.H * it.W * 4;
     }
     par[k] = P;

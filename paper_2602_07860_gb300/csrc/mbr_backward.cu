@@ -1,11 +1,12 @@
 // mbr_backward.cu -- adjoint kernels of the sm_103a motion-blurred renderer (a9).
 //
-//   raster_bwd_persistent recomputes passes 1-2 of the forward per sample, in two phases (below),
-//                      then back-propagates dL/dimage through shading (Eq. fore + Lambert),
-//                      the barycentric edge functions, and the soft-coverage product
-//                      (Eqs. probability-function .. back, exclusive products) into gradients on
-//                      the slot vertex states (ndc x, y and world normal); soft-term gradients
-//                      are warp-reduced per candidate before the atomics
+//   raster_bwd_persistent back-propagates dL/dimage, in two phases (below), from the forward
+//                      raster's per-sample state: through shading (Eq. fore + Lambert) and the
+//                      barycentric edge functions of the stored winners, and through the
+//                      soft-coverage product (Eqs. probability-function .. back, exclusive
+//                      products) of the uncovered samples, into gradients on the slot vertex
+//                      states (ndc x, y and world normal); soft-term gradients are warp-reduced
+//                      per candidate before the atomics
 //   slot_chain_kernel  slot-state gradients -> base vertex gradients through projection, camera
 //                      and motion; base-normal gradient -> area-weighted-normal gradient
 //   normals_bwd_kernel adjoint of the face cross products of the vertex normals (a0)
@@ -16,8 +17,6 @@
 #include "mbr_raster.cuh"
 
 namespace mbr {
-
-constexpr float kTinyFactor = 1e-30f;
 
 __device__ __forceinline__ float warp_sum(float x) {
 #pragma unroll
@@ -157,39 +156,6 @@ __device__ __forceinline__ void soft_grad_accumulate(const float4 (&r)[kRecF4], 
     }
   }
 }
-
-// pass 2 of the adjoint: the soft products as sums of log factors per (sample, pixel), the
-// vanishing factors counted apart, so that the exclusive products prod_{l != j} (1 - A_l) of
-// pass 3 never divide by zero
-template <int SPT, bool MOVING>
-struct BwdSoftLogPairs {
-  const TriRec* recs_set;
-  const Group* grp;
-  BlockPix bp;
-  WarpScratch<SPT>* ws;
-  uint32_t xbits;
-  float m, r2, inv_delta;
-  __device__ __forceinline__ void pair(bool ok, int face, int p, uint32_t smp) {
-    if (!ok) return;
-    const float u = ws->pu[p], v = ws->pv[p];
-    float4 r[kRecF4];
-    load_record<MOVING>(recs_set + face, r, false, true);
-    const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
-    while (smp) {
-      const int i = __ffs(smp) - 1;
-      smp &= smp - 1u;
-      const float tau = MOVING ? __ldg(&grp->tau[i]) : 0.f;
-      EdgeVals e;
-      SoftGeom sg;
-      if (!soft_pair_term<MOVING>(r, ps, u, v, tau, (xbits >> i) & 1u, m, r2, e, sg)) continue;
-      float A;
-      const float f = soft_factor(sg.d, inv_delta, A);
-      if (f > kTinyFactor) atomicAdd(&ws->logp[i][p], __logf(f));
-      else atomicAdd(&ws->nzero[i][p], 1);
-    }
-  }
-  __device__ __forceinline__ void batch_end(int) {}
-};
 
 // pass 3 of the adjoint: gradient of alpha = 1 - prod_j (1 - A_j) w.r.t. the vertex positions of
 // every soft candidate.  A batch's pairs of one face sit on consecutive lanes: they are summed by
@@ -435,15 +401,12 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
   }
 }
 
-// The adjoint raster runs as two kernels over the same work units, so that each has a small hot
-// code footprint (one kernel with all passes is bound by instruction fetch):
-//   phase 0  pass 1 (winners), pass 2 (soft products of the uncovered samples that carry
-//            dL/dalpha) and the covered-sample adjoint; stores, per sample, the log soft product
-//            and a status byte (inactive, or the count of vanishing factors);
-//   phase 1  pass 3 (soft-factor gradients) from that state.
-// Everything is recomputed from the mesh in the backward; nothing is kept from the forward.
-constexpr uint8_t kStatInactive = 0xff;  // covered, outside the image, or no dL/dalpha
-
+// The adjoint raster reads the per-sample state of the forward raster (winner face of a covered
+// sample; log soft product and vanishing-factor count of an uncovered one) and runs as two
+// kernels over the forward's work units:
+//   phase 0  covered samples: shading adjoint and barycentric adjoint of the stored winner;
+//   phase 1  uncovered samples with dL/dalpha: soft-factor gradients (pass 3).
+// Neither repeats the forward's coverage or soft-product passes.
 struct BwdBlock {
   int lane, n_tiles, px, py;
   BlockPix bp;
@@ -477,98 +440,37 @@ __device__ __forceinline__ BwdBlock bwd_block_setup(const RasterParams& P, int t
 }
 
 // phase 0 on one 8 x 4 block and its split of the sample groups
-template <int TW, int TH, int SPT, bool MOVING>
-__device__ __forceinline__ void raster_bwd_state_block(const RasterParams& P, int tile, int split, int wb,
-                                                       WarpScratch<SPT>& ws) {
+template <int TW, int TH, bool MOVING>
+__device__ __forceinline__ void raster_bwd_covered_block(const RasterParams& P, int tile, int split, int wb) {
   const BwdBlock B = bwd_block_setup<TW, TH>(P, tile, split, wb);
-  const int lane = B.lane;
-  ws.pu[lane] = B.u;
-  ws.pv[lane] = B.v;
-  const uint32_t img_mask = __ballot_sync(kFullMask, B.in_img);
-  const bool active = B.in_img && B.ga != 0.f;
+  const bool rgb = B.gr != 0.f || B.gg != 0.f || B.gb != 0.f;
+  if (!__any_sync(kFullMask, B.in_img && rgb)) return;  // no colour gradient on this block
   const size_t plane = (size_t)P.H * P.W, pix = (size_t)B.py * P.W + B.px;
-
   for (int g = B.g_begin; g < B.g_end; ++g) {
-    const Group* grp = P.groups + g;
     GroupRegs gq;
-    gq.load(grp);
-    const int n = gq.n;
-    const uint32_t all_s = (1u << n) - 1u;
+    gq.load(P.groups + g);
     const TriRec* recs_set = P.recs + (size_t)gq.rec_set * P.F;
-    const size_t bi = (size_t)g * B.n_tiles + tile;
-    int cb, ce, sb, se;
-    P.core.range(bi, cb, ce);
-    P.soft.range(bi, sb, se);
-
-    // ---- pass 1: winners (recomputed)
-    uint32_t allowed[SPT];
-#pragma unroll
-    for (int i = 0; i < SPT; ++i) {
-      allowed[i] = i < n ? img_mask : 0u;
-      ws.win[i][lane] = 0ull;
-      ws.logp[i][lane] = 0.f;
-      ws.nzero[i][lane] = 0;
-    }
-    ws.pixs[lane] = B.in_img ? all_s : 0u;
-    __syncwarp();
-    CorePairs<SPT, MOVING, false> core{recs_set, grp, B.bp, &ws, 0u, 0u};
-    for_pairs<SPT, MOVING>(recs_set, P.core.faces, cb, ce, grp, n, B.tb, B.bp, kCoreMargin, allowed, all_s, ws, core);
-    int bestf[SPT];
-    uint32_t uncov = 0;
-#pragma unroll
-    for (int i = 0; i < SPT; ++i) {
-      bestf[i] = -1;
-      if (i < n) {
-        const unsigned long long w = ws.win[i][lane];
-        if (w) bestf[i] = (int)(~(uint32_t)w);
-        else uncov |= 1u << i;
-      }
-    }
-
-    // ---- pass 2: soft products of the uncovered samples with dL/dalpha
-    const uint32_t my_s = active ? uncov : 0u;
-    const uint32_t any_s = __reduce_or_sync(kFullMask, my_s);
-    if (se > sb && any_s) {
-#pragma unroll
-      for (int i = 0; i < SPT; ++i) allowed[i] = __ballot_sync(kFullMask, (my_s >> i) & 1u);
-      ws.pixs[lane] = my_s;
-      __syncwarp();
-      const float m = P.r + kCoreMargin;
-      BwdSoftLogPairs<SPT, MOVING> p2{recs_set, grp, B.bp, &ws, gq.xbits, m, P.r2, P.inv_delta};
-      for_pairs<SPT, MOVING>(recs_set, P.soft.faces, sb, se, grp, n, B.tb, B.bp, m, allowed, any_s, ws, p2);
-    }
-    if (B.in_img) {
-#pragma unroll
-      for (int i = 0; i < SPT; ++i) {
-        if (i < n) {
-          const size_t o = (size_t)(gq.k0 + i) * plane + pix;
-          const bool soft = (my_s >> i) & 1u;
-          P.s_stat[o] = soft ? (uint8_t)min(ws.nzero[i][lane], 2) : kStatInactive;
-          P.s_logp[o] = soft ? ws.logp[i][lane] : 0.f;
-        }
-      }
-    }
-
-    // ---- covered samples: shading adjoint and barycentric adjoint of the winner
 #pragma unroll 1
-    for (int i = 0; i < n; ++i) {
+    for (int i = 0; i < gq.n; ++i) {
       int f = -1;
-#pragma unroll
-      for (int q = 0; q < SPT; ++q)
-        if (q == i) f = bestf[q];
+      if (B.in_img && rgb) {
+        const size_t o = (size_t)(gq.k0 + i) * plane + pix;
+        if (__ldg(P.s_stat + o) == kStatCovered) f = __float_as_int(__ldg(P.s_val + o));
+      }
       const float tau = MOVING ? __ldg(gq.tau + i) : 0.f;
-      const bool has = B.in_img && f >= 0;
+      const bool has = f >= 0;
       covered_adjoint<MOVING>(P, recs_set, gq.slot_a, gq.slot_b, has, has ? f : 0, tau, B.u, B.v, B.gr, B.gg, B.gb);
     }
-    __syncwarp();  // the scratch is rewritten by the next group
   }
 }
 
-// phase 1 on one 8 x 4 block: soft-factor gradients of the uncovered samples, from phase 0's state
+// phase 1 on one 8 x 4 block: soft-factor gradients of the uncovered samples
 template <int TW, int TH, int SPT, bool MOVING>
 __device__ __forceinline__ void raster_bwd_soft_block(const RasterParams& P, int tile, int split, int wb,
                                                       WarpScratch<SPT>& ws) {
   const BwdBlock B = bwd_block_setup<TW, TH>(P, tile, split, wb);
+  const bool active = B.in_img && B.ga != 0.f;
+  if (!__any_sync(kFullMask, active)) return;  // no alpha gradient on this block
   const int lane = B.lane;
   ws.pu[lane] = B.u;
   ws.pv[lane] = B.v;
@@ -584,16 +486,16 @@ __device__ __forceinline__ void raster_bwd_soft_block(const RasterParams& P, int
     int sb, se;
     P.soft.range(bi, sb, se);
     uint32_t my_s = 0u;
-    if (B.in_img) {
+    if (active) {
 #pragma unroll
       for (int i = 0; i < SPT; ++i) {
         if (i < n) {
           const size_t o = (size_t)(gq.k0 + i) * plane + pix;
           const uint8_t st = __ldg(P.s_stat + o);
-          if (st != kStatInactive) {
+          if (st != kStatCovered) {
             my_s |= 1u << i;
             ws.nzero[i][lane] = st;
-            ws.logp[i][lane] = __ldg(P.s_logp + o);
+            ws.logp[i][lane] = __ldg(P.s_val + o);
           }
         }
       }
@@ -628,23 +530,26 @@ __device__ __forceinline__ void raster_bwd_soft_block(const RasterParams& P, int
 // Persistent adjoint raster, phase PHASE (see above): KIND 0 = plain solver only, 1 = fast solver
 // only, 2 = mixed batch.
 template <int TW, int TH, int SPT, int KIND, int PHASE>
-__global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 3 : 2) raster_bwd_persistent(WorkQueue Q) {
+__global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 4 : 2) raster_bwd_persistent(WorkQueue Q) {
   __shared__ CtaQueue cq;
   __shared__ RasterParams sp[kPersistentThreads / 32];
-  __shared__ WarpScratch<SPT> ws[kPersistentThreads / 32];
+  constexpr int kScratch = PHASE == 0 ? 1 : kPersistentThreads / 32;  // phase 0 needs no pair scratch
+  __shared__ WarpScratch<SPT> ws[kScratch];
   cq.init();
   const int warp = threadIdx.x >> 5;
   RasterParams& P = sp[warp];
   int cur = -1, tile = 0, split = 0, wb = 0;
   while (warp_next<TW, TH>(Q, cq, P, cur, tile, split, wb)) {
     if (tile >= P.tiles_x * P.tiles_y) continue;
-    if (KIND == 0 || (KIND == 2 && !P.moving)) {
-      WarpScratch<1>& w1 = *reinterpret_cast<WarpScratch<1>*>(ws + warp);
-      if (PHASE == 0) raster_bwd_state_block<TW, TH, 1, false>(P, tile, split, wb, w1);
-      else raster_bwd_soft_block<TW, TH, 1, false>(P, tile, split, wb, w1);
+    const bool moving = KIND == 1 || (KIND == 2 && P.moving);
+    if constexpr (PHASE == 0) {
+      if (moving) raster_bwd_covered_block<TW, TH, true>(P, tile, split, wb);
+      else raster_bwd_covered_block<TW, TH, false>(P, tile, split, wb);
     } else {
-      if (PHASE == 0) raster_bwd_state_block<TW, TH, SPT, true>(P, tile, split, wb, ws[warp]);
-      else raster_bwd_soft_block<TW, TH, SPT, true>(P, tile, split, wb, ws[warp]);
+      if (!moving)
+        raster_bwd_soft_block<TW, TH, 1, false>(P, tile, split, wb, *reinterpret_cast<WarpScratch<1>*>(ws + warp));
+      else
+        raster_bwd_soft_block<TW, TH, SPT, true>(P, tile, split, wb, ws[warp]);
     }
   }
 }

@@ -340,7 +340,8 @@ __global__ void scan_apply_kernel(const int32_t* __restrict__ in, int n, const i
 
 // ---------------------------------------------------------------- a4-a8: forward raster
 // pass 2 of the forward: log soft factors log(1 - A_j), A_j = exp(-d_j / delta) (Eqs.
-// probability-function .. back), summed per (sample, pixel) in ws.logp.
+// probability-function .. back), summed per (sample, pixel) in ws.logp; vanishing factors are
+// counted in ws.nzero instead (the product is then 0).
 template <int SPT, bool MOVING, bool COUNT>
 struct FwdSoftPairs {
   const TriRec* recs_set;
@@ -366,7 +367,8 @@ struct FwdSoftPairs {
       if (!soft_pair_term<MOVING>(r, ps, u, v, tau, (xbits >> i) & 1u, m, r2, e, sg)) continue;
       float A;
       const float f = soft_factor(sg.d, inv_delta, A);
-      atomicAdd(&ws->logp[i][p], __logf(f));
+      if (f > kTinyFactor) atomicAdd(&ws->logp[i][p], __logf(f));
+      else atomicAdd(&ws->nzero[i][p], 1);
       if (COUNT) ++n_terms;
     }
   }
@@ -435,9 +437,13 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
     }
 
     // ---- pass 2: soft coverage of the uncovered samples
-    float prod[SPT];
+    float logp[SPT];
+    int nzero[SPT];
 #pragma unroll
-    for (int i = 0; i < SPT; ++i) prod[i] = 1.f;
+    for (int i = 0; i < SPT; ++i) {
+      logp[i] = 0.f;
+      nzero[i] = 0;
+    }
     const uint32_t my_s = in_img ? uncov : 0u;
     const uint32_t any_s = __reduce_or_sync(kFullMask, my_s);
     FwdSoftPairs<SPT, MOVING, COUNT> soft{recs_set, grp, bp, &ws, gr.xbits, P.r + kCoreMargin, P.r2, P.inv_delta,
@@ -447,14 +453,17 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
       for (int i = 0; i < SPT; ++i) {
         allowed[i] = __ballot_sync(kFullMask, (my_s >> i) & 1u);
         ws.logp[i][lane] = 0.f;
+        ws.nzero[i][lane] = 0;
       }
       ws.pixs[lane] = my_s;
       __syncwarp();
       for_pairs<SPT, MOVING>(recs_set, P.soft.faces, sb, se, grp, n, tb, bp, P.r + kCoreMargin, allowed, any_s, ws,
                              soft);
 #pragma unroll
-      for (int i = 0; i < SPT; ++i)
-        if ((my_s >> i) & 1u) prod[i] = __expf(ws.logp[i][lane]);
+      for (int i = 0; i < SPT; ++i) {
+        logp[i] = ws.logp[i][lane];
+        nzero[i] = ws.nzero[i][lane];
+      }
     }
     if (COUNT) {
       n_ctest += core.n_tests;
@@ -471,6 +480,11 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
       for (int i = 0; i < SPT; ++i) {
         if (i < n) {
           const int f = bestf[i];
+          if (P.s_stat) {  // the adjoint's per-sample state
+            const size_t o = (size_t)(gr.k0 + i) * ((size_t)P.H * P.W) + (size_t)py * P.W + px;
+            P.s_stat[o] = f >= 0 ? kStatCovered : (uint8_t)min(nzero[i], 2);
+            P.s_val[o] = f >= 0 ? __int_as_float(f) : logp[i];
+          }
           if (P.dbg_ids && gr.k0 + i == P.dbg_k) P.dbg_ids[(size_t)py * P.W + px] = f;
           if (f >= 0) {
             const float tau = MOVING ? __ldg(gr.tau + i) : 0.f;
@@ -506,7 +520,7 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
             acc_b = fmaf(cb, shade, acc_b);
             acc_a += 1.f;
           } else {
-            acc_a += 1.f - prod[i];
+            acc_a += nzero[i] ? 1.f : 1.f - __expf(logp[i]);
           }
         }
       }

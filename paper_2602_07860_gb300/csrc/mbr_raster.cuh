@@ -63,9 +63,15 @@ struct RasterParams {
   const float4* dl_dimage;   // [H*W]
   float4* g_slot;            // [slots][V][2]: (dx, dy, dnx, dny), (dnz, 0, 0, 0) of the slot states
   float4* g_albedo;          // [V] (dr, dg, db, 0), or null
-  float* s_logp;             // [T][H][W] adjoint state between its two kernels: log soft product,
-  uint8_t* s_stat;           //   and status: kStatCovered, or the count of vanishing factors
+  // per-sample raster state, written by the forward (when s_stat is set) and read by the adjoint
+  float* s_val;              // [T][H][W] covered: winner face id (int bits); else log soft product
+  uint8_t* s_stat;           // [T][H][W] kStatCovered, or the count of vanishing soft factors (<= 2)
 };
+
+constexpr uint8_t kStatCovered = 0xff;
+// A soft factor 1 - A at or below this is "vanishing": it is counted, not summed as a log, so
+// that the adjoint's exclusive products prod_{l != j} (1 - A_l) never divide by zero.
+constexpr float kTinyFactor = 1e-30f;
 
 // Edge-function values of one candidate at one sample (local frame; see TriRec).
 struct EdgeVals {
@@ -290,7 +296,7 @@ template <int SPT>
 struct WarpScratch {
   unsigned long long win[SPT][32];  // z-test winner of (sample, pixel): key bits << 32 | ~face, 0 = none
   float logp[SPT][32];              // sum of log(1 - A_j) over the soft factors that do not vanish
-  int nzero[SPT][32];               // adjoint: vanishing soft factors
+  int nzero[SPT][32];               // vanishing soft factors
   uint32_t pixs[32];                // samples each pixel takes part in, this pass
   float pu[32], pv[32];             // NDC centre of each pixel (written by its own lane)
   float ga[32];                     // adjoint: dL/dalpha / T of each pixel

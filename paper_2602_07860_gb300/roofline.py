@@ -27,10 +27,11 @@ Eq. time-dependent2 and the keyframe closest point of Eqs. euc-dist-approx-1..3:
           the keyframe normals, not counted), normalisation (10), n.l and Lambert (8),
           accumulation (2) = 60.
   SAMPLE  alpha accumulation of any sample (4).
-Adjoint (the forward quantities are recomputed, not stored):
-  SOFT_BWD  the soft product pass (SOFT) plus the gradient pass (SOFT again and the derivative
-            of d through the closest point to the vertex coordinates: plain 30, fast 90) --
-            plain 120, fast 264.
+Adjoint (the forward raster stores, per sample, the winner face or the log soft product and the
+count of vanishing factors; the adjoint reads them and does not repeat the coverage tests):
+  SOFT_BWD  the soft factor recomputed (SOFT: d and the closest point are needed again) and the
+            derivative of d through the closest point to the vertex coordinates (plain 30,
+            fast 90) -- plain 75, fast 177.
   COV_BWD   recomputed shading (60) plus its adjoint through w = N / D and the edge functions to
             the vertex coordinates, normals and albedo (110) = 170.
 The z-test of covering candidates and the binning are not counted, so the model is a lower bound
@@ -40,8 +41,8 @@ Peak: 152 SMs x 128 FP32 lanes x 2 flops x 2.070 GHz (maximum SM clock) = 80.6 T
 """
 
 FLOPS = {
-    "plain": dict(cand=12, soft=45, cov=60, sample=4, soft_bwd=120, cov_bwd=170),
-    "fast": dict(cand=16, soft=87, cov=60, sample=4, soft_bwd=264, cov_bwd=170),
+    "plain": dict(cand=12, soft=45, cov=60, sample=4, soft_bwd=75, cov_bwd=170),
+    "fast": dict(cand=16, soft=87, cov=60, sample=4, soft_bwd=177, cov_bwd=170),
 }
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
@@ -53,14 +54,16 @@ def fwd_flops(solver, n_box, n_soft, n_cov, n_sample):
 
 
 def bwd_flops(solver, n_box, n_soft, n_cov, n_sample):
+    """n_box is accepted for symmetry with fwd_flops; the adjoint does no coverage tests."""
     k = FLOPS[solver]
-    return k["cand"] * n_box + k["soft_bwd"] * n_soft + k["cov_bwd"] * n_cov + k["sample"] * n_sample
+    return k["soft_bwd"] * n_soft + k["cov_bwd"] * n_cov + k["sample"] * n_sample
 
 
 def describe(solver, n_box, n_soft, n_cov, n_sample, backward):
     k = FLOPS[solver]
     s, c = ("soft_bwd", "cov_bwd") if backward else ("soft", "cov")
-    return (f"N_box={n_box} x {k['cand']} + N_soft={n_soft} x {k[s]} + N_cov={n_cov} x {k[c]} + "
+    box = "" if backward else f"N_box={n_box} x {k['cand']} + "
+    return (f"{box}N_soft={n_soft} x {k[s]} + N_cov={n_cov} x {k[c]} + "
             f"N_sample={n_sample} x {k['sample']} flops ({solver} solver)")
 
 
