@@ -264,8 +264,21 @@ struct Prepared {
   float r = 0.f;
   int core_cap = 0, soft_cap = 0;  // bin list capacities
   int n_units = 0;                  // raster work units: patches x n_split
-  int32_t* d_order = nullptr;       // their visiting order
+  int32_t* d_order = nullptr;       // their visiting order (estimate from the bins)
+  int32_t* d_order_bwd = nullptr;   // the adjoint's visiting order (from the forward's measured cost)
+  int32_t* d_cost = nullptr;        // the forward's measured adjoint cost per unit
+  int32_t* d_order_tmp = nullptr;   // scratch of the order kernels
 };
+
+// order buffer of a render: order | adjoint order | cost | scratch
+size_t order_buffer_ints(int n_units) { return (size_t)3 * n_units + unit_order_ints(n_units); }
+
+void carve_orders(int32_t* base, Prepared& pp) {
+  pp.d_order = base;
+  pp.d_order_bwd = base + pp.n_units;
+  pp.d_cost = base + 2 * (size_t)pp.n_units;
+  pp.d_order_tmp = base + 3 * (size_t)pp.n_units;
+}
 
 // units of a render: 256-pixel patches x group splits
 int patches_of(int tile, int n_tiles) {
@@ -456,10 +469,10 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
   const int n_patches = patches_of(tw, pp.n_tiles);
   pp.n_split = choose_splits(c, pp.G, n_patches);
   pp.n_units = n_patches * pp.n_split;
-  if ((rc = ensure(c, c->order, sizeof(int32_t) * (pp.n_units + unit_order_ints(pp.n_units)), st))) return rc;
-  pp.d_order = (int32_t*)c->order.p;
+  if ((rc = ensure(c, c->order, sizeof(int32_t) * order_buffer_ints(pp.n_units), st))) return rc;
+  carve_orders((int32_t*)c->order.p, pp);
   launch_unit_order((const int32_t*)c->core.offsets.p, (const int32_t*)c->soft.offsets.p, pp.G, pp.n_tiles, tw,
-                    pp.n_split, pp.n_units, pp.d_order, pp.d_order + pp.n_units, st);
+                    pp.n_split, pp.n_units, pp.d_order, pp.d_order_tmp, st);
   CUDA_TRY(c, cudaGetLastError());
   c->stats.launches += 3;
   return MBR_OK;
@@ -583,6 +596,8 @@ int forward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, con
     if ((rc = ensure(c, c->bstate, ns * 5 + 256, st))) return rc;
     P.s_val = (float*)c->bstate.p;
     P.s_stat = (uint8_t*)c->bstate.p + ns * 4;
+    P.unit_cost = pp.d_cost;  // and its cost per unit, for the adjoint's visiting order
+    CUDA_TRY(c, cudaMemsetAsync(pp.d_cost, 0, sizeof(int32_t) * pp.n_units, st));
   }
   if (pp.n_split > 1) CUDA_TRY(c, cudaMemsetAsync(P.out, 0, sizeof(float4) * npix, st));  // splits accumulate
   WorkQueue Q;
@@ -670,10 +685,12 @@ int backward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, co
   P.dl_dimage = (const float4*)dl_dimage;
   P.g_slot = (float4*)c->gslot.p;
   P.g_albedo = dl_dalbedo ? (float4*)c->galb.p : nullptr;
-  // the forward raster's per-sample state
+  // the forward raster's per-sample state, and the units in the order of its measured cost
   const size_t ns = (size_t)T * H * W;
   P.s_val = (float*)c->bstate.p;
   P.s_stat = (uint8_t*)c->bstate.p + ns * 4;
+  launch_unit_order_measured(pp.d_cost, pp.n_units, pp.d_order_bwd, pp.d_order_tmp, st);
+  P.order = pp.d_order_bwd;
   WorkQueue Q;
   if ((rc = upload_queue(c, &P, 1, st, Q))) return rc;
   const int kind = pp.moving ? 1 : 0;
@@ -682,7 +699,7 @@ int backward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, co
   launch_raster_bwd(Q, c->tile, pp.spt, kind, grid, st);
   CUDA_TRY(c, cudaGetLastError());
   if ((rc = time_end(c, 1, st))) return rc;
-  c->stats.launches += 1 + 1 + (mesh->F > 0 ? 1 : 0);
+  c->stats.launches += 3 + 1 + 1 + (mesh->F > 0 ? 1 : 0);  // order, raster, slot chain, normals
   c->stats.n_split = pp.n_split;
   launch_slot_chain(mesh->verts, (const float*)c->nacc.p, V, pp.d_xf, pp.n_slots, cam->tan_half_fov,
                     (const float4*)c->gslot.p, (const float4*)c->galb.p, dl_dverts, (float*)c->gm.p, dl_dalbedo, st);
@@ -1062,7 +1079,7 @@ void batch_write_params(mbr_ctx* c, const mbr_item* items, BatchState& B) {
                           {Lb + I.o_list[0], Lb + I.o_list[1]}};
     Prepared pp = I.pp;
     pp.d_groups = (Group*)(A + I.o_groups);
-    pp.d_order = (int32_t*)(A + I.o_order);
+    carve_orders((int32_t*)(A + I.o_order), pp);
     pp.core_cap = I.cap[0];
     pp.soft_cap = I.cap[1];
     RasterParams P = raster_params(c, bufs, &it.mesh, &it.camera, it.T, it.H, it.W, pp);
@@ -1073,6 +1090,7 @@ void batch_write_params(mbr_ctx* c, const mbr_item* items, BatchState& B) {
       P.g_albedo = it.dl_dalbedo ? (float4*)(A + I.o_galb) : nullptr;
       P.s_val = (float*)(A + I.o_bstate);
       P.s_stat = (uint8_t*)(A + I.o_bstate) + (size_t)it.T * it.H * it.W * 4;
+      P.unit_cost = pp.d_cost;
     }
     par[k] = P;
     off[k + 1] = off[k] + P.work;
@@ -1119,7 +1137,7 @@ int batch_plan(mbr_ctx* c, int n, const mbr_item* items, int wb, cudaStream_t st
       I.o_tmp[q] = carve(at, sizeof(int32_t) * scan_temp_ints((int)I.nb));
       I.o_cursor[q] = carve(at, sizeof(int32_t) * (size_t)I.nb);
     }
-    I.o_order = carve(at, sizeof(int32_t) * (pp.n_units + unit_order_ints(pp.n_units)));
+    I.o_order = carve(at, sizeof(int32_t) * order_buffer_ints(pp.n_units));
     if (wb) {
       I.o_gslot = carve(at, sizeof(float4) * 2 * (size_t)V * pp.n_slots);
       I.o_galb = carve(at, sizeof(float4) * V);
@@ -1231,11 +1249,13 @@ int batch_enqueue(mbr_ctx* c, const mbr_item* items, BatchState& B, cudaStream_t
     launch_bin(true, (const TriRec*)(A + I.o_recs), it.mesh.F, (const Group*)(A + I.o_groups), pp.G, it.W, it.H,
                c->tile, c->tile, pp.tiles_x, pp.n_tiles, kCoreMargin, pp.r + kCoreMargin, bt, (int*)(A + I.o_status),
                st);
-    int32_t* order = (int32_t*)(A + I.o_order);
+    Prepared po = pp;
+    carve_orders((int32_t*)(A + I.o_order), po);
     launch_unit_order((const int32_t*)(A + I.o_offs[0]), (const int32_t*)(A + I.o_offs[1]), pp.G, pp.n_tiles, c->tile,
-                      pp.n_split, pp.n_units, order, order + pp.n_units, st);
+                      pp.n_split, pp.n_units, po.d_order, po.d_order_tmp, st);
     if (pp.n_split > 1) CUDA_TRY(c, cudaMemsetAsync(it.image, 0, sizeof(float4) * (size_t)it.H * it.W, st));
     if (B.with_backward) {
+      CUDA_TRY(c, cudaMemsetAsync(po.d_cost, 0, sizeof(int32_t) * pp.n_units, st));
       CUDA_TRY(c, cudaMemsetAsync(A + I.o_gslot, 0, sizeof(float4) * 2 * (size_t)it.mesh.V * pp.n_slots, st));
       if (it.dl_dalbedo) CUDA_TRY(c, cudaMemsetAsync(A + I.o_galb, 0, sizeof(float4) * it.mesh.V, st));
     }
@@ -1263,10 +1283,17 @@ int batch_enqueue(mbr_ctx* c, const mbr_item* items, BatchState& B, cudaStream_t
   CUDA_TRY(c, cudaGetLastError());
   c->stats.launches += 1;
   if (B.with_backward) {
+    // the adjoint visits each item's units in the order of the forward's measured cost: the
+    // order array the launches share is rewritten in place
+    for (int i = 0; i < n; ++i) {
+      Prepared po = B.items[i].pp;
+      carve_orders((int32_t*)(A + B.items[i].o_order), po);
+      launch_unit_order_measured(po.d_cost, po.n_units, po.d_order, po.d_order_tmp, st);
+    }
     CUDA_TRY(c, cudaMemsetAsync(Q.counter, 0, sizeof(int32_t), st));
     launch_raster_bwd(Q, c->tile, spt, B.kind, B.grid_bwd, st);
     CUDA_TRY(c, cudaGetLastError());
-    c->stats.launches += 1;
+    c->stats.launches += 3 * n + 1;
     for (int i = 0; i < n; ++i) {
       const BatchItem& I = B.items[i];
       const mbr_item& it = items[i];

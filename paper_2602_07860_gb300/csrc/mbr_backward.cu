@@ -1,7 +1,7 @@
 // mbr_backward.cu -- adjoint kernels of the sm_103a motion-blurred renderer (a9).
 //
-//   raster_bwd_persistent back-propagates dL/dimage, in two phases (below), from the forward
-//                      raster's per-sample state: through shading (Eq. fore + Lambert) and the
+//   raster_bwd_persistent back-propagates dL/dimage from the forward raster's per-sample
+//                      state: through shading (Eq. fore + Lambert) and the
 //                      barycentric edge functions of the stored winners, and through the
 //                      soft-coverage product (Eqs. probability-function .. back, exclusive
 //                      products) of the uncovered samples, into gradients on the slot vertex
@@ -402,11 +402,11 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
 }
 
 // The adjoint raster reads the per-sample state of the forward raster (winner face of a covered
-// sample; log soft product and vanishing-factor count of an uncovered one) and runs as two
-// kernels over the forward's work units:
-//   phase 0  covered samples: shading adjoint and barycentric adjoint of the stored winner;
-//   phase 1  uncovered samples with dL/dalpha: soft-factor gradients (pass 3).
-// Neither repeats the forward's coverage or soft-product passes.
+// sample; log soft product and vanishing-factor count of an uncovered one) and does not repeat
+// the forward's coverage or soft-product passes.  Per block and sample group: the shading and
+// barycentric adjoint of the covered samples' winners, then the soft-factor gradients (pass 3)
+// of the uncovered samples that carry dL/dalpha.  Both parts run in one kernel: the covered part
+// is latency-bound (dependent loads and atomics) and fills the issue slots of the soft part.
 struct BwdBlock {
   int lane, n_tiles, px, py;
   BlockPix bp;
@@ -439,38 +439,15 @@ __device__ __forceinline__ BwdBlock bwd_block_setup(const RasterParams& P, int t
   return B;
 }
 
-// phase 0 on one 8 x 4 block and its split of the sample groups
-template <int TW, int TH, bool MOVING>
-__device__ __forceinline__ void raster_bwd_covered_block(const RasterParams& P, int tile, int split, int wb) {
-  const BwdBlock B = bwd_block_setup<TW, TH>(P, tile, split, wb);
-  const bool rgb = B.gr != 0.f || B.gg != 0.f || B.gb != 0.f;
-  if (!__any_sync(kFullMask, B.in_img && rgb)) return;  // no colour gradient on this block
-  const size_t plane = (size_t)P.H * P.W, pix = (size_t)B.py * P.W + B.px;
-  for (int g = B.g_begin; g < B.g_end; ++g) {
-    GroupRegs gq;
-    gq.load(P.groups + g);
-    const TriRec* recs_set = P.recs + (size_t)gq.rec_set * P.F;
-#pragma unroll 1
-    for (int i = 0; i < gq.n; ++i) {
-      int f = -1;
-      if (B.in_img && rgb) {
-        const size_t o = (size_t)(gq.k0 + i) * plane + pix;
-        if (__ldg(P.s_stat + o) == kStatCovered) f = __float_as_int(__ldg(P.s_val + o));
-      }
-      const float tau = MOVING ? __ldg(gq.tau + i) : 0.f;
-      const bool has = f >= 0;
-      covered_adjoint<MOVING>(P, recs_set, gq.slot_a, gq.slot_b, has, has ? f : 0, tau, B.u, B.v, B.gr, B.gg, B.gb);
-    }
-  }
-}
-
-// phase 1 on one 8 x 4 block: soft-factor gradients of the uncovered samples
+// the adjoint of one 8 x 4 block over its split of the sample groups
 template <int TW, int TH, int SPT, bool MOVING>
-__device__ __forceinline__ void raster_bwd_soft_block(const RasterParams& P, int tile, int split, int wb,
-                                                      WarpScratch<SPT>& ws) {
+__device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile, int split, int wb,
+                                                 WarpScratch<SPT>& ws) {
   const BwdBlock B = bwd_block_setup<TW, TH>(P, tile, split, wb);
-  const bool active = B.in_img && B.ga != 0.f;
-  if (!__any_sync(kFullMask, active)) return;  // no alpha gradient on this block
+  const bool rgb = B.in_img && (B.gr != 0.f || B.gg != 0.f || B.gb != 0.f);  // colour gradient
+  const bool alpha = B.in_img && B.ga != 0.f;                                // alpha gradient
+  const bool any_rgb = __any_sync(kFullMask, rgb);
+  if (!any_rgb && !__any_sync(kFullMask, alpha)) return;
   const int lane = B.lane;
   ws.pu[lane] = B.u;
   ws.pv[lane] = B.v;
@@ -482,27 +459,46 @@ __device__ __forceinline__ void raster_bwd_soft_block(const RasterParams& P, int
     GroupRegs gq;
     gq.load(grp);
     const int n = gq.n;
-    const size_t bi = (size_t)g * B.n_tiles + tile;
-    int sb, se;
-    P.soft.range(bi, sb, se);
+    const TriRec* recs_set = P.recs + (size_t)gq.rec_set * P.F;
+    // the forward's state of the group's samples at this pixel
+    int win[SPT];
     uint32_t my_s = 0u;
-    if (active) {
 #pragma unroll
-      for (int i = 0; i < SPT; ++i) {
-        if (i < n) {
-          const size_t o = (size_t)(gq.k0 + i) * plane + pix;
-          const uint8_t st = __ldg(P.s_stat + o);
-          if (st != kStatCovered) {
-            my_s |= 1u << i;
-            ws.nzero[i][lane] = st;
-            ws.logp[i][lane] = __ldg(P.s_val + o);
-          }
+    for (int i = 0; i < SPT; ++i) {
+      win[i] = -1;
+      if (i < n && B.in_img) {
+        const size_t o = (size_t)(gq.k0 + i) * plane + pix;
+        const uint8_t st = __ldg(P.s_stat + o);
+        if (st == kStatCovered) {
+          win[i] = __float_as_int(__ldg(P.s_val + o));
+        } else if (alpha) {
+          my_s |= 1u << i;
+          ws.nzero[i][lane] = st;
+          ws.logp[i][lane] = __ldg(P.s_val + o);
         }
       }
     }
+
+    // ---- covered samples: shading adjoint and barycentric adjoint of the winner
+    if (any_rgb) {
+#pragma unroll 1
+      for (int i = 0; i < n; ++i) {
+        int f = -1;
+#pragma unroll
+        for (int q = 0; q < SPT; ++q)
+          if (q == i) f = win[q];
+        const bool has = rgb && f >= 0;
+        const float tau = MOVING ? __ldg(gq.tau + i) : 0.f;
+        covered_adjoint<MOVING>(P, recs_set, gq.slot_a, gq.slot_b, has, has ? f : 0, tau, B.u, B.v, B.gr, B.gg,
+                                B.gb);
+      }
+    }
+
+    // ---- uncovered samples: soft-factor gradients (pass 3)
     const uint32_t any_s = __reduce_or_sync(kFullMask, my_s);
+    int sb, se;
+    P.soft.range((size_t)g * B.n_tiles + tile, sb, se);
     if (se > sb && any_s) {
-      const TriRec* recs_set = P.recs + (size_t)gq.rec_set * P.F;
       uint32_t allowed[SPT];
 #pragma unroll
       for (int i = 0; i < SPT; ++i) allowed[i] = __ballot_sync(kFullMask, (my_s >> i) & 1u);
@@ -523,34 +519,26 @@ __device__ __forceinline__ void raster_bwd_soft_block(const RasterParams& P, int
       p3.gslot_b = P.g_slot + (size_t)gq.slot_b * P.V * 2;
       for_pairs<SPT, MOVING>(recs_set, P.soft.faces, sb, se, grp, n, B.tb, B.bp, m, allowed, any_s, ws, p3);
     }
-    __syncwarp();
+    __syncwarp();  // the scratch is rewritten by the next group
   }
 }
 
-// Persistent adjoint raster, phase PHASE (see above): KIND 0 = plain solver only, 1 = fast solver
-// only, 2 = mixed batch.
-template <int TW, int TH, int SPT, int KIND, int PHASE>
-__global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 4 : 2) raster_bwd_persistent(WorkQueue Q) {
+// Persistent adjoint raster: KIND 0 = plain solver only, 1 = fast solver only, 2 = mixed batch.
+template <int TW, int TH, int SPT, int KIND>
+__global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 3 : 2) raster_bwd_persistent(WorkQueue Q) {
   __shared__ CtaQueue cq;
   __shared__ RasterParams sp[kPersistentThreads / 32];
-  constexpr int kScratch = PHASE == 0 ? 1 : kPersistentThreads / 32;  // phase 0 needs no pair scratch
-  __shared__ WarpScratch<SPT> ws[kScratch];
+  __shared__ WarpScratch<SPT> ws[kPersistentThreads / 32];
   cq.init();
   const int warp = threadIdx.x >> 5;
   RasterParams& P = sp[warp];
   int cur = -1, tile = 0, split = 0, wb = 0;
   while (warp_next<TW, TH>(Q, cq, P, cur, tile, split, wb)) {
     if (tile >= P.tiles_x * P.tiles_y) continue;
-    const bool moving = KIND == 1 || (KIND == 2 && P.moving);
-    if constexpr (PHASE == 0) {
-      if (moving) raster_bwd_covered_block<TW, TH, true>(P, tile, split, wb);
-      else raster_bwd_covered_block<TW, TH, false>(P, tile, split, wb);
-    } else {
-      if (!moving)
-        raster_bwd_soft_block<TW, TH, 1, false>(P, tile, split, wb, *reinterpret_cast<WarpScratch<1>*>(ws + warp));
-      else
-        raster_bwd_soft_block<TW, TH, SPT, true>(P, tile, split, wb, ws[warp]);
-    }
+    if (KIND == 0 || (KIND == 2 && !P.moving))
+      raster_bwd_block<TW, TH, 1, false>(P, tile, split, wb, *reinterpret_cast<WarpScratch<1>*>(ws + warp));
+    else
+      raster_bwd_block<TW, TH, SPT, true>(P, tile, split, wb, ws[warp]);
   }
 }
 
@@ -647,32 +635,28 @@ __global__ void normals_bwd_kernel(const float* __restrict__ verts, const int32_
   atomicAdd(g_verts + 3 * a + 2, -(bz + cz));
 }
 
-template <int TW, int TH, int KIND, int PHASE>
+template <int TW, int TH, int KIND>
 static void launch_bwd_spt(const WorkQueue& Q, int spt, int grid, cudaStream_t st) {
   if (spt <= 2)
-    raster_bwd_persistent<TW, TH, 2, KIND, PHASE><<<grid, kPersistentThreads, 0, st>>>(Q);
+    raster_bwd_persistent<TW, TH, 2, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
   else
-    raster_bwd_persistent<TW, TH, 4, KIND, PHASE><<<grid, kPersistentThreads, 0, st>>>(Q);
+    raster_bwd_persistent<TW, TH, 4, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
 }
 
-template <int TW, int TH, int PHASE>
+template <int TW, int TH>
 static void launch_bwd_tile(const WorkQueue& Q, int spt, int kind, int grid, cudaStream_t st) {
   if (kind == 0)
-    raster_bwd_persistent<TW, TH, 1, 0, PHASE><<<grid, kPersistentThreads, 0, st>>>(Q);
+    raster_bwd_persistent<TW, TH, 1, 0><<<grid, kPersistentThreads, 0, st>>>(Q);
   else if (kind == 1)
-    launch_bwd_spt<TW, TH, 1, PHASE>(Q, spt, grid, st);
+    launch_bwd_spt<TW, TH, 1>(Q, spt, grid, st);
   else
-    launch_bwd_spt<TW, TH, 2, PHASE>(Q, spt, grid, st);
+    launch_bwd_spt<TW, TH, 2>(Q, spt, grid, st);
 }
 
-// both phases; the queue's counter is re-armed between them (stream order)
 void launch_raster_bwd(const WorkQueue& Q, int tile, int spt, int kind, int grid, cudaStream_t st) {
   if (Q.n_work <= 0) return;
-  if (tile == 8) launch_bwd_tile<8, 8, 0>(Q, spt, kind, grid, st);
-  else launch_bwd_tile<16, 16, 0>(Q, spt, kind, grid, st);
-  cudaMemsetAsync(Q.counter, 0, sizeof(int32_t), st);
-  if (tile == 8) launch_bwd_tile<8, 8, 1>(Q, spt, kind, grid, st);
-  else launch_bwd_tile<16, 16, 1>(Q, spt, kind, grid, st);
+  if (tile == 8) launch_bwd_tile<8, 8>(Q, spt, kind, grid, st);
+  else launch_bwd_tile<16, 16>(Q, spt, kind, grid, st);
 }
 
 template <typename K>
@@ -682,20 +666,14 @@ static int occupancy_of(K kernel) {
   return n < 1 ? 1 : n;
 }
 
-template <int TW, int TH, int PHASE>
-static int occ_bwd_phase(int spt, int kind) {
-  if (kind == 0) return occupancy_of(raster_bwd_persistent<TW, TH, 1, 0, PHASE>);
-  if (kind == 1)
-    return spt <= 2 ? occupancy_of(raster_bwd_persistent<TW, TH, 2, 1, PHASE>)
-                    : occupancy_of(raster_bwd_persistent<TW, TH, 4, 1, PHASE>);
-  return spt <= 2 ? occupancy_of(raster_bwd_persistent<TW, TH, 2, 2, PHASE>)
-                  : occupancy_of(raster_bwd_persistent<TW, TH, 4, 2, PHASE>);
-}
-
-// one grid serves both phases: the smaller occupancy of the two
 template <int TW, int TH>
 static int occ_bwd(int spt, int kind) {
-  return std::min(occ_bwd_phase<TW, TH, 0>(spt, kind), occ_bwd_phase<TW, TH, 1>(spt, kind));
+  if (kind == 0) return occupancy_of(raster_bwd_persistent<TW, TH, 1, 0>);
+  if (kind == 1)
+    return spt <= 2 ? occupancy_of(raster_bwd_persistent<TW, TH, 2, 1>)
+                    : occupancy_of(raster_bwd_persistent<TW, TH, 4, 1>);
+  return spt <= 2 ? occupancy_of(raster_bwd_persistent<TW, TH, 2, 2>)
+                  : occupancy_of(raster_bwd_persistent<TW, TH, 4, 2>);
 }
 
 int persistent_grid_bwd(int num_sms, int tile, int spt, int kind) {

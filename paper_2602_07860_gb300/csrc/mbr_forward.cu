@@ -373,7 +373,7 @@ struct FwdSoftPairs {
     }
   }
   __device__ __forceinline__ void batch_end(int) {
-    if (COUNT && (threadIdx.x & 31) == 0) ++n_batches;
+    if ((threadIdx.x & 31) == 0) ++n_batches;  // lane 0: the adjoint's cost estimate
   }
 };
 
@@ -400,6 +400,7 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
   const uint32_t img_mask = __ballot_sync(kFullMask, in_img);
   float acc_r = 0.f, acc_g = 0.f, acc_b = 0.f, acc_a = 0.f;
   uint32_t n_soft = 0, n_cov = 0, n_seval = 0, n_sbatch = 0, n_ctest = 0, n_cbatch = 0;
+  int adj_cost = 0;  // lane 0: soft pair batches + samples with a covered pixel (the adjoint's work)
 
   for (int g = g_begin; g < g_end; ++g) {
     const Group* grp = P.groups + g;
@@ -465,6 +466,7 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
         nzero[i] = ws.nzero[i][lane];
       }
     }
+    adj_cost += (int)soft.n_batches + __popc(__reduce_or_sync(kFullMask, in_img ? (all_s & ~uncov) : 0u));
     if (COUNT) {
       n_ctest += core.n_tests;
       n_cbatch += core.n_batches;
@@ -526,6 +528,10 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
       }
     }
     __syncwarp();  // the scratch is rewritten by the next group
+  }
+  if (P.unit_cost && lane == 0 && adj_cost) {
+    const int unit = split * UnitMap<TW, TH>::patches(n_tiles) + tile / UnitMap<TW, TH>::kTilesPerUnit;
+    atomicAdd(P.unit_cost + unit, adj_cost);
   }
   if (in_img) {
     const size_t o = (size_t)py * P.W + px;
@@ -593,6 +599,14 @@ __global__ void __launch_bounds__(kPersistentThreads, 2) raster_fwd_count(WorkQu
 // half-octaves of the estimate and visited from the largest bucket down.
 constexpr int kOrderBuckets = 64;
 
+// bucket of a cost estimate: half-octaves, largest visited first
+__device__ __forceinline__ int cost_bucket(long long cost) {
+  if (cost <= 0) return 0;
+  const int lg = 63 - __clzll(cost);                          // floor(log2(cost))
+  const int half = lg > 0 ? (int)((cost >> (lg - 1)) & 1) : 0;  // next bit: upper half-octave
+  return min(kOrderBuckets - 1, 1 + 2 * lg + half);
+}
+
 __device__ __forceinline__ int unit_bucket(const int32_t* __restrict__ core_off, const int32_t* __restrict__ soft_off,
                                            int G, int n_tiles, int tpu, int n_patches, int n_split, int u) {
   const int split = u / n_patches, patch = u - split * n_patches;
@@ -605,10 +619,22 @@ __device__ __forceinline__ int unit_bucket(const int32_t* __restrict__ core_off,
       const size_t b = (size_t)g * n_tiles + t;
       cost += (long long)(core_off[b + 1] - core_off[b]) + 2LL * (soft_off[b + 1] - soft_off[b]);
     }
-  if (cost <= 0) return 0;
-  const int lg = 63 - __clzll(cost);                          // floor(log2(cost))
-  const int half = lg > 0 ? (int)((cost >> (lg - 1)) & 1) : 0;  // next bit: upper half-octave
-  return min(kOrderBuckets - 1, 1 + 2 * lg + half);
+  return cost_bucket(cost);
+}
+
+__global__ void unit_hist_cost_kernel(const int32_t* __restrict__ cost, int n_units, int32_t* __restrict__ bucket,
+                                      int32_t* __restrict__ hist) {
+  __shared__ int s_hist[kOrderBuckets];
+  if (threadIdx.x < kOrderBuckets) s_hist[threadIdx.x] = 0;
+  __syncthreads();
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < n_units) {
+    const int k = cost_bucket(cost[u]);
+    bucket[u] = k;
+    atomicAdd(&s_hist[k], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < kOrderBuckets && s_hist[threadIdx.x]) atomicAdd(hist + threadIdx.x, s_hist[threadIdx.x]);
 }
 
 __global__ void unit_hist_kernel(const int32_t* __restrict__ core_off, const int32_t* __restrict__ soft_off, int G,
@@ -785,6 +811,17 @@ void launch_unit_order(const int32_t* core_off, const int32_t* soft_off, int G, 
   const unsigned blocks = (unsigned)((n_units + 255) / 256);
   unit_hist_kernel<<<blocks, 256, 0, st>>>(core_off, soft_off, G, n_tiles, tpu, n_patches, n_split, n_units, bucket,
                                            hist);
+  unit_scan_kernel<<<1, 32, 0, st>>>(hist);
+  unit_scatter_kernel<<<blocks, 256, 0, st>>>(bucket, n_units, hist, order);
+}
+
+void launch_unit_order_measured(const int32_t* cost, int n_units, int32_t* order, int32_t* scratch, cudaStream_t st) {
+  if (n_units <= 0) return;
+  int32_t* bucket = scratch;
+  int32_t* hist = scratch + n_units;
+  cudaMemsetAsync(hist, 0, sizeof(int32_t) * kOrderBuckets, st);
+  const unsigned blocks = (unsigned)((n_units + 255) / 256);
+  unit_hist_cost_kernel<<<blocks, 256, 0, st>>>(cost, n_units, bucket, hist);
   unit_scan_kernel<<<1, 32, 0, st>>>(hist);
   unit_scatter_kernel<<<blocks, 256, 0, st>>>(bucket, n_units, hist, order);
 }

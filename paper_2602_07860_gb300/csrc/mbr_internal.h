@@ -38,6 +38,8 @@ int persistent_grid_bwd(int num_sms, int tile, int spt, int kind);
 size_t unit_order_ints(int n_units);
 void launch_unit_order(const int32_t* core_off, const int32_t* soft_off, int G, int n_tiles, int tile, int n_split,
                        int n_units, int32_t* order, int32_t* scratch, cudaStream_t st);
+// the same from a measured cost per unit (the forward raster's estimate of the adjoint's work)
+void launch_unit_order_measured(const int32_t* cost, int n_units, int32_t* order, int32_t* scratch, cudaStream_t st);
 // measurement build of the forward raster (16 x 16 tiles): counts soft terms / covered samples
 void launch_raster_count(const WorkQueue& Q, int spt, int kind, int grid, cudaStream_t st);
 void launch_count(const TriRec* recs, int F, const Group* groups, int G, int W, int H, float r,

@@ -58,6 +58,7 @@ struct RasterParams {
   int32_t moving;            // 1: fast solver (segment records), 0: plain solver (static records)
   int32_t work;              // units of this render: patches * n_split
   const int32_t* order;      // [work] unit visiting order (largest estimated work first), or null
+  int32_t* unit_cost;        // forward, if set: [work] measured adjoint work per unit (zeroed before)
   unsigned long long* counts;  // measurement build only: [soft terms, covered samples]
   // adjoint only
   const float4* dl_dimage;   // [H*W]
