@@ -29,7 +29,7 @@ struct DevBuf {
 
 // one CSR binning of (group, tile) -> face lists
 struct BinSet {
-  DevBuf counts, offsets, cursor, list, scan_tmp;
+  DevBuf offsets, list, scan_tmp;
 };
 
 struct BatchState;  // batched renders (defined with mbr_render_blur_batch)
@@ -53,7 +53,7 @@ struct mbr_ctx {
   // tuning
   int tile = 16, spt = 2, splits = 0;
   // scratch
-  DevBuf nacc, pos, nrm, recs, tables, partial, gslot, galb, gm, cnt64, status, order, bstate;
+  DevBuf nacc, pos, nrm, recs, tables, partial, gslot, galb, gm, cnt64, status, order, bstate, bin_counts;
   BinSet core, soft;  // undilated bins (coverage) and r_soft-dilated bins (soft coverage)
   void* host_stage = nullptr;
   size_t host_stage_cap = 0;
@@ -404,12 +404,11 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
   c->stats.launches += (F > 0 ? 1 : 0) + 1 + (F > 0 ? 1 : 0);
   c->stats.groups = pp.G;
   if (!do_bins) {
-    CUDA_TRY(c, cudaMemcpyAsync(c->host_total + 1, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaMemcpyAsync(c->host_total, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(c, cudaStreamSynchronize(st));
-    if (c->host_total[1] & kStatusBadFace) return fail(c, MBR_ERR_ARG, "face index outside [0, V)");
+    if (c->host_total[0] & kStatusBadFace) return fail(c, MBR_ERR_ARG, "face index outside [0, V)");
     return MBR_OK;
   }
-  CUDA_TRY(c, cudaMemcpyAsync(c->host_total + 3, d_status + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
 
   // a3 binning: core and soft bins: count -> scan (both) -> one sync for the totals -> fill
   const int tw = c->tile, th = c->tile;
@@ -420,40 +419,39 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
   if (nb > (1LL << 30)) return fail(c, MBR_ERR_ARG, "too many (group, tile) bins: %lld", nb);
   BinSet* sets2[2] = {&c->core, &c->soft};
   const float r_core = kCoreMargin, r_soft = pp.r + kCoreMargin;
+  // both count arrays in one buffer (one clear); after the scan they are the fill cursors
+  if ((rc = ensure(c, c->bin_counts, sizeof(int32_t) * 2 * (size_t)nb, st))) return rc;
+  CUDA_TRY(c, cudaMemsetAsync(c->bin_counts.p, 0, sizeof(int32_t) * 2 * (size_t)nb, st));
   BinTargets bt{};
+  ScanPair sp{};
   for (int q = 0; q < 2; ++q) {
     BinSet& bs = *sets2[q];
-    if ((rc = ensure(c, bs.counts, sizeof(int32_t) * (size_t)nb, st))) return rc;
     if ((rc = ensure(c, bs.offsets, sizeof(int32_t) * (size_t)(nb + 1), st))) return rc;
     if ((rc = ensure(c, bs.scan_tmp, sizeof(int32_t) * scan_temp_ints((int)nb), st))) return rc;
-    CUDA_TRY(c, cudaMemsetAsync(bs.counts.p, 0, sizeof(int32_t) * (size_t)nb, st));
-    bt.counts_or_cursor[q] = (int32_t*)bs.counts.p;
+    bt.counts_or_cursor[q] = (int32_t*)c->bin_counts.p + q * (size_t)nb;
+    sp.in[q] = bt.counts_or_cursor[q];
+    sp.out[q] = (int32_t*)bs.offsets.p;
+    sp.sums[q] = (int32_t*)bs.scan_tmp.p;
   }
+  sp.total = d_status + 2;  // [2] core, [3] soft list totals
+  sp.n = (int)nb;
   launch_bin(false, (const TriRec*)c->recs.p, F, pp.d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles, r_core,
              r_soft, bt, d_status, st);
-  for (int q = 0; q < 2; ++q) {
-    BinSet& bs = *sets2[q];
-    launch_scan((const int32_t*)bs.counts.p, (int)nb, (int32_t*)bs.offsets.p, (int32_t*)bs.scan_tmp.p, st);
-    CUDA_TRY(c, cudaGetLastError());
-    CUDA_TRY(c, cudaMemcpyAsync(c->host_total + 2 * q, (int32_t*)bs.offsets.p + nb, sizeof(int32_t),
-                                cudaMemcpyDeviceToHost, st));
-  }
-  CUDA_TRY(c, cudaMemcpyAsync(c->host_total + 1, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  launch_scan_pair(sp, st);
+  CUDA_TRY(c, cudaGetLastError());
+  // one read-back: [0] this call's status, [1] raster launches' status, [2], [3] list totals
+  CUDA_TRY(c, cudaMemcpyAsync(c->host_total, d_status, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(c, cudaStreamSynchronize(st));
-  if (c->host_total[1] & kStatusBadFace) return fail(c, MBR_ERR_ARG, "face index outside [0, V)");
-  if (c->host_total[3] & kStatusSpin) {
+  if (c->host_total[0] & kStatusBadFace) return fail(c, MBR_ERR_ARG, "face index outside [0, V)");
+  if (c->host_total[1] & kStatusSpin) {
     CUDA_TRY(c, cudaMemsetAsync(d_status + 1, 0, sizeof(int32_t), st));
     return fail(c, MBR_ERR_TIMEOUT, "a raster launch of an earlier call gave up a bounded wait (its output is incomplete)");
   }
-  long long totals[2] = {c->host_total[0], c->host_total[2]};
+  long long totals[2] = {c->host_total[2], c->host_total[3]};
   for (int q = 0; q < 2; ++q) {
     BinSet& bs = *sets2[q];
     if (totals[q] < 0) return fail(c, MBR_ERR_DEVICE, "bin total overflow");
     if ((rc = ensure(c, bs.list, sizeof(int32_t) * (size_t)std::max<long long>(totals[q], 1), st))) return rc;
-    if ((rc = ensure(c, bs.cursor, sizeof(int32_t) * (size_t)nb, st))) return rc;
-    CUDA_TRY(c, cudaMemcpyAsync(bs.cursor.p, bs.offsets.p, sizeof(int32_t) * (size_t)nb, cudaMemcpyDeviceToDevice,
-                                st));
-    bt.counts_or_cursor[q] = (int32_t*)bs.cursor.p;
     bt.list[q] = (int32_t*)bs.list.p;
     bt.off[q] = (const int32_t*)bs.offsets.p;
     bt.cap[q] = (int)totals[q];
@@ -461,7 +459,7 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
   launch_bin(true, (const TriRec*)c->recs.p, F, pp.d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles, r_core,
              r_soft, bt, d_status, st);
   CUDA_TRY(c, cudaGetLastError());
-  c->stats.launches += (F > 0 ? 2 : 0) + 2 * 3;
+  c->stats.launches += (F > 0 ? 2 : 0) + 3;
   c->stats.bin_entries = totals[0] + totals[1];
   pp.core_cap = (int)totals[0];
   pp.soft_cap = (int)totals[1];
@@ -472,9 +470,9 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
   if ((rc = ensure(c, c->order, sizeof(int32_t) * order_buffer_ints(pp.n_units), st))) return rc;
   carve_orders((int32_t*)c->order.p, pp);
   launch_unit_order((const int32_t*)c->core.offsets.p, (const int32_t*)c->soft.offsets.p, pp.G, pp.n_tiles, tw,
-                    pp.n_split, pp.n_units, pp.d_order, pp.d_order_tmp, st);
+                    pp.n_split, pp.n_units, pp.d_order, pp.d_order_tmp, pp.d_cost, st);
   CUDA_TRY(c, cudaGetLastError());
-  c->stats.launches += 3;
+  c->stats.launches += 1;
   return MBR_OK;
 }
 
@@ -557,11 +555,11 @@ int upload_queue(mbr_ctx* c, const RasterParams* items, int n, cudaStream_t st, 
   int32_t* off = (int32_t*)(h + off_at);
   off[0] = 0;
   for (int i = 0; i < n; ++i) off[i + 1] = off[i] + items[i].work;
+  *(int32_t*)(h + cnt_at) = 0;  // the queue's counter travels with the parameters
   char* d = (char*)c->queue.p;
-  CUDA_TRY(c, cudaMemcpyAsync(d, h, cnt_at, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(c, cudaMemcpyAsync(d, h, cnt_at + sizeof(int32_t), cudaMemcpyHostToDevice, st));
   if (!c->queue_copied) CUDA_TRY(c, cudaEventCreateWithFlags(&c->queue_copied, cudaEventDisableTiming));
   CUDA_TRY(c, cudaEventRecord(c->queue_copied, st));
-  CUDA_TRY(c, cudaMemsetAsync(d + cnt_at, 0, sizeof(int32_t), st));
   Q.items = (const RasterParams*)d;
   Q.item_off = (const int32_t*)(d + off_at);
   Q.n_items = n;
@@ -596,8 +594,7 @@ int forward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, con
     if ((rc = ensure(c, c->bstate, ns * 5 + 256, st))) return rc;
     P.s_val = (float*)c->bstate.p;
     P.s_stat = (uint8_t*)c->bstate.p + ns * 4;
-    P.unit_cost = pp.d_cost;  // and its cost per unit, for the adjoint's visiting order
-    CUDA_TRY(c, cudaMemsetAsync(pp.d_cost, 0, sizeof(int32_t) * pp.n_units, st));
+    P.unit_cost = pp.d_cost;  // and its cost per unit (cleared by the unit order), for the adjoint's order
   }
   if (pp.n_split > 1) CUDA_TRY(c, cudaMemsetAsync(P.out, 0, sizeof(float4) * npix, st));  // splits accumulate
   WorkQueue Q;
@@ -745,8 +742,8 @@ void mbr_destroy(mbr_ctx* c) {
   if (!c) return;
   DevBuf* bufs[] = {&c->nacc, &c->pos, &c->nrm, &c->recs, &c->tables, &c->partial, &c->gslot, &c->galb, &c->gm,
                     &c->cnt64, &c->order, &c->bstate,
-                    &c->status, &c->queue, &c->core.counts, &c->core.offsets, &c->core.cursor, &c->core.list,
-                    &c->core.scan_tmp, &c->soft.counts, &c->soft.offsets, &c->soft.cursor, &c->soft.list,
+                    &c->status, &c->queue, &c->bin_counts, &c->core.offsets, &c->core.list,
+                    &c->core.scan_tmp, &c->soft.offsets, &c->soft.list,
                     &c->soft.scan_tmp};
   cudaDeviceSynchronize();
   for (DevBuf* b : bufs)
@@ -979,7 +976,7 @@ struct BatchItem {
   long long nb = 0;
   size_t o_status = 0, o_nacc = 0, o_pos = 0, o_nrm = 0, o_recs = 0, o_tab = 0, o_sets = 0, o_groups = 0;
   size_t tab_bytes = 0, o_order = 0, o_gslot = 0, o_galb = 0, o_gm = 0, o_bstate = 0;
-  size_t o_counts[2] = {0, 0}, o_offs[2] = {0, 0}, o_tmp[2] = {0, 0}, o_cursor[2] = {0, 0};
+  size_t o_counts = 0, o_offs[2] = {0, 0}, o_tmp[2] = {0, 0};
   size_t o_list[2] = {0, 0};
   int cap[2] = {0, 0};
   size_t stage_tab = 0;
@@ -1122,7 +1119,7 @@ int batch_plan(mbr_ctx* c, int n, const mbr_item* items, int wb, cudaStream_t st
     pp.n_units = patches_of(c->tile, pp.n_tiles) * pp.n_split;
     I.nb = (long long)pp.G * pp.n_tiles;
     if (I.nb > (1LL << 30)) return fail(c, MBR_ERR_ARG, "item %d: too many bins", i);
-    I.o_status = carve(at, sizeof(int32_t));
+    I.o_status = carve(at, sizeof(int32_t) * 4);  // [0] status, [2], [3] list totals
     I.o_nacc = carve(at, sizeof(float) * 3 * V);
     I.o_pos = carve(at, sizeof(float4) * (size_t)pp.n_slots * V);
     I.o_nrm = carve(at, sizeof(float4) * (size_t)pp.n_slots * V);
@@ -1131,11 +1128,10 @@ int batch_plan(mbr_ctx* c, int n, const mbr_item* items, int wb, cudaStream_t st
     I.o_sets = carve(at, sizeof(int2) * I.sets.size());
     I.o_groups = carve(at, sizeof(Group) * I.groups.size());
     I.tab_bytes = I.o_groups + sizeof(Group) * I.groups.size() - I.o_tab;
+    I.o_counts = carve(at, sizeof(int32_t) * 2 * (size_t)I.nb);  // core, soft counts (then cursors)
     for (int q = 0; q < 2; ++q) {
-      I.o_counts[q] = carve(at, sizeof(int32_t) * (size_t)I.nb);
       I.o_offs[q] = carve(at, sizeof(int32_t) * (size_t)(I.nb + 1));
       I.o_tmp[q] = carve(at, sizeof(int32_t) * scan_temp_ints((int)I.nb));
-      I.o_cursor[q] = carve(at, sizeof(int32_t) * (size_t)I.nb);
     }
     I.o_order = carve(at, sizeof(int32_t) * order_buffer_ints(pp.n_units));
     if (wb) {
@@ -1196,33 +1192,34 @@ int batch_enqueue(mbr_ctx* c, const mbr_item* items, BatchState& B, cudaStream_t
     launch_setup((const float4*)(A + I.o_pos), it.mesh.faces, F, V, (const int2*)(A + I.o_sets), pp.n_sets,
                  it.camera.znear, (TriRec*)(A + I.o_recs), st);
     BinTargets bt{};
+    ScanPair sp{};
+    CUDA_TRY(c, cudaMemsetAsync(A + I.o_counts, 0, sizeof(int32_t) * 2 * (size_t)I.nb, st));
     for (int q = 0; q < 2; ++q) {
-      CUDA_TRY(c, cudaMemsetAsync(A + I.o_counts[q], 0, sizeof(int32_t) * (size_t)I.nb, st));
-      bt.counts_or_cursor[q] = (int32_t*)(A + I.o_counts[q]);
+      bt.counts_or_cursor[q] = (int32_t*)(A + I.o_counts) + q * (size_t)I.nb;
+      sp.in[q] = bt.counts_or_cursor[q];
+      sp.out[q] = (int32_t*)(A + I.o_offs[q]);
+      sp.sums[q] = (int32_t*)(A + I.o_tmp[q]);
     }
+    sp.total = d_status + 2;
+    sp.n = (int)I.nb;
     launch_bin(false, (const TriRec*)(A + I.o_recs), F, (const Group*)(A + I.o_groups), pp.G, it.W, it.H, c->tile,
                c->tile, pp.tiles_x, pp.n_tiles, kCoreMargin, pp.r + kCoreMargin, bt, d_status, st);
-    for (int q = 0; q < 2; ++q)
-      launch_scan((const int32_t*)(A + I.o_counts[q]), (int)I.nb, (int32_t*)(A + I.o_offs[q]),
-                  (int32_t*)(A + I.o_tmp[q]), st);
+    launch_scan_pair(sp, st);
     CUDA_TRY(c, cudaGetLastError());
   }
   int32_t* hs = (int32_t*)((char*)B.stage + B.stage_status);
   if (sizing) {
-    for (int i = 0; i < n; ++i) {
-      const BatchItem& I = B.items[i];
-      for (int q = 0; q < 2; ++q)
-        CUDA_TRY(c, cudaMemcpyAsync(hs + 4 * i + q, A + I.o_offs[q] + sizeof(int32_t) * I.nb, sizeof(int32_t),
-                                    cudaMemcpyDeviceToHost, st));
-      CUDA_TRY(c, cudaMemcpyAsync(hs + 4 * i + 2, A + I.o_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    }
+    // per item [0] status, [2], [3] list totals
+    for (int i = 0; i < n; ++i)
+      CUDA_TRY(c, cudaMemcpyAsync(hs + 4 * i, A + B.items[i].o_status, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost,
+                                  st));
     CUDA_TRY(c, cudaStreamSynchronize(st));
     size_t lat = 0;
     for (int i = 0; i < n; ++i) {
       BatchItem& I = B.items[i];
-      if (hs[4 * i + 2] & kStatusBadFace) return fail(c, MBR_ERR_ARG, "item %d: face index outside [0, V)", i);
+      if (hs[4 * i] & kStatusBadFace) return fail(c, MBR_ERR_ARG, "item %d: face index outside [0, V)", i);
       for (int q = 0; q < 2; ++q) {
-        const long long t = hs[4 * i + q];
+        const long long t = hs[4 * i + 2 + q];
         if (t < 0) return fail(c, MBR_ERR_DEVICE, "item %d: bin total overflow", i);
         I.cap[q] = (int)std::min<long long>(t + t / 4 + 4096, 0x7fffffffLL);  // headroom for replays
         I.o_list[q] = carve(lat, sizeof(int32_t) * (size_t)I.cap[q]);
@@ -1239,9 +1236,7 @@ int batch_enqueue(mbr_ctx* c, const mbr_item* items, BatchState& B, cudaStream_t
     const Prepared& pp = I.pp;
     BinTargets bt{};
     for (int q = 0; q < 2; ++q) {
-      CUDA_TRY(c, cudaMemcpyAsync(A + I.o_cursor[q], A + I.o_offs[q], sizeof(int32_t) * (size_t)I.nb,
-                                  cudaMemcpyDeviceToDevice, st));
-      bt.counts_or_cursor[q] = (int32_t*)(A + I.o_cursor[q]);
+      bt.counts_or_cursor[q] = (int32_t*)(A + I.o_counts) + q * (size_t)I.nb;  // zeroed by the scan
       bt.list[q] = (int32_t*)(Lb + I.o_list[q]);
       bt.off[q] = (const int32_t*)(A + I.o_offs[q]);
       bt.cap[q] = I.cap[q];
@@ -1252,10 +1247,9 @@ int batch_enqueue(mbr_ctx* c, const mbr_item* items, BatchState& B, cudaStream_t
     Prepared po = pp;
     carve_orders((int32_t*)(A + I.o_order), po);
     launch_unit_order((const int32_t*)(A + I.o_offs[0]), (const int32_t*)(A + I.o_offs[1]), pp.G, pp.n_tiles, c->tile,
-                      pp.n_split, pp.n_units, po.d_order, po.d_order_tmp, st);
+                      pp.n_split, pp.n_units, po.d_order, po.d_order_tmp, B.with_backward ? po.d_cost : nullptr, st);
     if (pp.n_split > 1) CUDA_TRY(c, cudaMemsetAsync(it.image, 0, sizeof(float4) * (size_t)it.H * it.W, st));
     if (B.with_backward) {
-      CUDA_TRY(c, cudaMemsetAsync(po.d_cost, 0, sizeof(int32_t) * pp.n_units, st));
       CUDA_TRY(c, cudaMemsetAsync(A + I.o_gslot, 0, sizeof(float4) * 2 * (size_t)it.mesh.V * pp.n_slots, st));
       if (it.dl_dalbedo) CUDA_TRY(c, cudaMemsetAsync(A + I.o_galb, 0, sizeof(float4) * it.mesh.V, st));
     }
@@ -1307,7 +1301,7 @@ int batch_enqueue(mbr_ctx* c, const mbr_item* items, BatchState& B, cudaStream_t
   }
   // statuses back to the stage (overflow detection after a replay)
   for (int i = 0; i < n; ++i)
-    CUDA_TRY(c, cudaMemcpyAsync(hs + 4 * i + 3, A + B.items[i].o_status, sizeof(int32_t), cudaMemcpyDeviceToHost,
+    CUDA_TRY(c, cudaMemcpyAsync(hs + 4 * i + 1, A + B.items[i].o_status, sizeof(int32_t), cudaMemcpyDeviceToHost,
                                 st));
   return MBR_OK;
 }
@@ -1315,9 +1309,9 @@ int batch_enqueue(mbr_ctx* c, const mbr_item* items, BatchState& B, cudaStream_t
 int batch_check(mbr_ctx* c, const BatchState& B) {
   const int32_t* hs = (const int32_t*)((char*)B.stage + B.stage_status);
   for (size_t i = 0; i < B.items.size(); ++i) {
-    if (hs[4 * i + 3] & kStatusBadFace) return fail(c, MBR_ERR_ARG, "item %zu: face index outside [0, V)", i);
-    if (hs[4 * i + 3] & kStatusSpin) return fail(c, MBR_ERR_TIMEOUT, "a raster launch gave up a bounded wait");
-    if (hs[4 * i + 3] & kStatusBinOverflow) return -1;  // lists too small: re-plan
+    if (hs[4 * i + 1] & kStatusBadFace) return fail(c, MBR_ERR_ARG, "item %zu: face index outside [0, V)", i);
+    if (hs[4 * i + 1] & kStatusSpin) return fail(c, MBR_ERR_TIMEOUT, "a raster launch gave up a bounded wait");
+    if (hs[4 * i + 1] & kStatusBinOverflow) return -1;  // lists too small: re-plan
   }
   return MBR_OK;
 }
@@ -1429,7 +1423,7 @@ int noalloc_forward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, 
 
   // fixed part of the arena
   Arena A{(char*)base, kStaticScratchBytes, 0};
-  int* d_status = (int*)A.take(sizeof(int32_t));
+  int* d_status = (int*)A.take(sizeof(int32_t) * 4);  // [0] status, [2], [3] list totals
   float* nacc = (float*)A.take(sizeof(float) * 3 * (size_t)V);
   float4* pos = (float4*)A.take(sizeof(float4) * (size_t)pp.n_slots * V);
   float4* nrm = (float4*)A.take(sizeof(float4) * (size_t)pp.n_slots * V);
@@ -1437,15 +1431,14 @@ int noalloc_forward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, 
   SlotXform* d_xf = (SlotXform*)A.take(sizeof(SlotXform) * xf.size());
   int2* d_sets = (int2*)A.take(sizeof(int2) * sets.size());
   Group* d_groups = (Group*)A.take(sizeof(Group) * groups.size());
-  int32_t *counts[2], *offs[2], *tmp[2], *cursor[2], *list[2];
+  int32_t *offs[2], *tmp[2], *list[2];
+  int32_t* counts = (int32_t*)A.take(sizeof(int32_t) * 2 * (size_t)nb);  // core, soft counts (then cursors)
   for (int q = 0; q < 2; ++q) {
-    counts[q] = (int32_t*)A.take(sizeof(int32_t) * (size_t)nb);
     offs[q] = (int32_t*)A.take(sizeof(int32_t) * (size_t)(nb + 1));
     tmp[q] = (int32_t*)A.take(sizeof(int32_t) * scan_temp_ints((int)nb));
-    cursor[q] = (int32_t*)A.take(sizeof(int32_t) * (size_t)nb);
   }
-  if (!d_status || !nacc || !pos || !nrm || !recs || !d_xf || !d_sets || !d_groups || !counts[1] || !offs[1] ||
-      !tmp[1] || !cursor[1] || nb > (1LL << 30))
+  if (!d_status || !nacc || !pos || !nrm || !recs || !d_xf || !d_sets || !d_groups || !counts || !offs[1] ||
+      !tmp[1] || nb > (1LL << 30))
     return fail(c, MBR_ERR_ARG,
                 "render needs more than the %zu MiB static scratch (V=%d F=%d T=%d %dx%d); use mbr_render_blur",
                 kStaticScratchBytes >> 20, V, F, T, W, H);
@@ -1461,22 +1454,26 @@ int noalloc_forward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, 
   launch_face_normals(mesh->verts, mesh->faces, F, V, nacc, d_status, st);
   launch_xform(mesh->verts, nacc, V, d_xf, pp.n_slots, cam->tan_half_fov, pos, nrm, st);
   launch_setup(pos, mesh->faces, F, V, d_sets, pp.n_sets, cam->znear, recs, st);
-  int32_t host[3] = {0, 0, 0};
+  int32_t status4[4] = {0, 0, 0, 0};  // pageable: the copy below is synchronised before it is read
   BinTargets bt{};
+  ScanPair sp{};
+  CUDA_TRY(c, cudaMemsetAsync(counts, 0, sizeof(int32_t) * 2 * (size_t)nb, st));
   for (int q = 0; q < 2; ++q) {
-    CUDA_TRY(c, cudaMemsetAsync(counts[q], 0, sizeof(int32_t) * (size_t)nb, st));
-    bt.counts_or_cursor[q] = counts[q];
+    bt.counts_or_cursor[q] = counts + q * (size_t)nb;
+    sp.in[q] = bt.counts_or_cursor[q];
+    sp.out[q] = offs[q];
+    sp.sums[q] = tmp[q];
   }
+  sp.total = d_status + 2;
+  sp.n = (int)nb;
   launch_bin(false, recs, F, d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles, kCoreMargin, pp.r + kCoreMargin,
              bt, d_status, st);
-  for (int q = 0; q < 2; ++q) {
-    launch_scan(counts[q], (int)nb, offs[q], tmp[q], st);
-    CUDA_TRY(c, cudaGetLastError());
-    CUDA_TRY(c, cudaMemcpyAsync(host + q, offs[q] + nb, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  }
-  CUDA_TRY(c, cudaMemcpyAsync(host + 2, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  launch_scan_pair(sp, st);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaMemcpyAsync(status4, d_status, sizeof(status4), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(c, cudaStreamSynchronize(st));
-  if (host[2] & kStatusBadFace) return fail(c, MBR_ERR_ARG, "face index outside [0, V)");
+  if (status4[0] & kStatusBadFace) return fail(c, MBR_ERR_ARG, "face index outside [0, V)");
+  const int32_t host[2] = {status4[2], status4[3]};
   for (int q = 0; q < 2; ++q) {
     list[q] = (int32_t*)A.take(sizeof(int32_t) * (size_t)std::max(host[q], 1));
     if (host[q] < 0 || !list[q])
@@ -1484,8 +1481,6 @@ int noalloc_forward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, 
                   host[0], host[1], kStaticScratchBytes >> 20);
   }
   for (int q = 0; q < 2; ++q) {
-    CUDA_TRY(c, cudaMemcpyAsync(cursor[q], offs[q], sizeof(int32_t) * (size_t)nb, cudaMemcpyDeviceToDevice, st));
-    bt.counts_or_cursor[q] = cursor[q];
     bt.list[q] = list[q];
     bt.off[q] = offs[q];
     bt.cap[q] = host[q];
@@ -1505,7 +1500,7 @@ int noalloc_forward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, 
     return fail(c, MBR_ERR_ARG, "render needs more than the %zu MiB static scratch; use mbr_render_blur",
                 kStaticScratchBytes >> 20);
   launch_unit_order(offs[0], offs[1], pp.G, pp.n_tiles, tw, pp.n_split, pp.n_units, pp.d_order,
-                    pp.d_order + pp.n_units, st);
+                    pp.d_order + pp.n_units, nullptr, st);
   const RasterBufs bufs{recs, nrm, {offs[0], offs[1]}, {list[0], list[1]}};
   RasterParams P = raster_params(c, bufs, mesh, cam, T, H, W, pp);
   P.out = (float4*)image;

@@ -192,8 +192,9 @@ __global__ void bin_kernel(const TriRec* __restrict__ recs, int F, const Group* 
     for (int ty = ty0; ty <= ty1; ++ty)
       for (int tx = tx0; tx <= tx1; ++tx) {
         const int b = ty * tiles_x + tx;
-        const int slot = atomicAdd(base + b, 1);
+        const int k = atomicAdd(base + b, 1);
         if (FILL) {
+          const int slot = t.off[q][(size_t)g * n_tiles + b] + k;
           // the fill pass revisits exactly the counted triples; the check only guards the list
           if (slot < t.off[q][(size_t)g * n_tiles + b + 1] && slot < t.cap[q]) t.list[q][slot] = f;
           else atomicOr(status, kStatusBinOverflow);
@@ -245,7 +246,8 @@ __global__ void bin_smem_kernel(const TriRec* __restrict__ recs, int F, const Gr
   }
   for (int i = threadIdx.x; i < 2 * n_tiles; i += blockDim.x) {
     const int q = i >= n_tiles, b = i - q * n_tiles;
-    if (sh[i]) sh[i] = atomicAdd(t.counts_or_cursor[q] + (size_t)g * n_tiles + b, sh[i]);  // first slot of the range
+    const size_t gb = (size_t)g * n_tiles + b;
+    if (sh[i]) sh[i] = t.off[q][gb] + atomicAdd(t.counts_or_cursor[q] + gb, sh[i]);  // first slot of the range
   }
   __syncthreads();
 #pragma unroll
@@ -291,20 +293,25 @@ __device__ __forceinline__ int block_exclusive_scan(int x, int* s_warp, int& tot
   return r;
 }
 
-__global__ void scan_reduce_kernel(const int32_t* __restrict__ in, int n, int32_t* __restrict__ sums) {
+// The core and soft count arrays are scanned together (grid.y = array).  The apply pass zeroes
+// the counts after reading them: they are the fill pass's cursors (slot = offset + cursor).
+__global__ void scan_reduce_kernel(ScanPair sp) {
   __shared__ int s_warp[33];
+  const int q = blockIdx.y, n = sp.n;
+  const int32_t* in = sp.in[q];
   const size_t base = (size_t)blockIdx.x * kScanBlock + (size_t)threadIdx.x * kScanPer;
   int x = 0;
 #pragma unroll
-  for (int q = 0; q < kScanPer; ++q)
-    if (base + q < (size_t)n) x += in[base + q];
+  for (int k = 0; k < kScanPer; ++k)
+    if (base + k < (size_t)n) x += in[base + k];
   int total;
   block_exclusive_scan(x, s_warp, total);
-  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+  if (threadIdx.x == 0) sp.sums[q][blockIdx.x] = total;
 }
 
-__global__ void scan_sums_kernel(int32_t* __restrict__ sums, int nb) {
+__global__ void scan_sums_kernel(ScanPair sp, int nb) {
   __shared__ int s_warp[33];
+  int32_t* sums = sp.sums[blockIdx.y];
   int carry = 0;
   for (int c = 0; c < nb; c += kScanThreads) {
     const int i = c + threadIdx.x;
@@ -317,25 +324,34 @@ __global__ void scan_sums_kernel(int32_t* __restrict__ sums, int nb) {
   if (threadIdx.x == 0) sums[nb] = carry;
 }
 
-__global__ void scan_apply_kernel(const int32_t* __restrict__ in, int n, const int32_t* __restrict__ sums,
-                                  int32_t* __restrict__ out) {
+__global__ void scan_apply_kernel(ScanPair sp) {
   __shared__ int s_warp[33];
+  const int q = blockIdx.y, n = sp.n;
+  int32_t* in = sp.in[q];
+  int32_t* out = sp.out[q];
+  const int32_t* sums = sp.sums[q];
   const size_t base = (size_t)blockIdx.x * kScanBlock + (size_t)threadIdx.x * kScanPer;
   int v[kScanPer];
   int x = 0;
 #pragma unroll
-  for (int q = 0; q < kScanPer; ++q) {
-    v[q] = base + q < (size_t)n ? in[base + q] : 0;
-    x += v[q];
+  for (int k = 0; k < kScanPer; ++k) {
+    v[k] = base + k < (size_t)n ? in[base + k] : 0;
+    x += v[k];
   }
   int total;
   int ex = block_exclusive_scan(x, s_warp, total) + sums[blockIdx.x];
 #pragma unroll
-  for (int q = 0; q < kScanPer; ++q) {
-    if (base + q < (size_t)n) out[base + q] = ex;
-    ex += v[q];
+  for (int k = 0; k < kScanPer; ++k) {
+    if (base + k < (size_t)n) {
+      out[base + k] = ex;
+      in[base + k] = 0;
+    }
+    ex += v[k];
   }
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = sums[gridDim.x];
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+    out[n] = sums[gridDim.x];
+    if (sp.total) sp.total[q] = sums[gridDim.x];
+  }
 }
 
 // ---------------------------------------------------------------- a4-a8: forward raster
@@ -622,57 +638,42 @@ __device__ __forceinline__ int unit_bucket(const int32_t* __restrict__ core_off,
   return cost_bucket(cost);
 }
 
-__global__ void unit_hist_cost_kernel(const int32_t* __restrict__ cost, int n_units, int32_t* __restrict__ bucket,
-                                      int32_t* __restrict__ hist) {
+// One CTA: bucket every unit by its cost (from the bins, or measured when cost_in is set), count
+// the buckets in shared memory, scan them largest first, scatter the units.  cost_zero (if set)
+// is cleared on the way (the forward raster accumulates its measured costs there).
+constexpr int kOrderThreads = 1024;
+
+__global__ void __launch_bounds__(kOrderThreads) unit_order_kernel(
+    const int32_t* __restrict__ core_off, const int32_t* __restrict__ soft_off, int G, int n_tiles, int tpu,
+    int n_patches, int n_split, const int32_t* __restrict__ cost_in, int32_t* __restrict__ cost_zero, int n_units,
+    int32_t* __restrict__ bucket, int32_t* __restrict__ order) {
   __shared__ int s_hist[kOrderBuckets];
   if (threadIdx.x < kOrderBuckets) s_hist[threadIdx.x] = 0;
   __syncthreads();
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u < n_units) {
-    const int k = cost_bucket(cost[u]);
+  for (int u = threadIdx.x; u < n_units; u += kOrderThreads) {
+    const int k = cost_in ? cost_bucket(cost_in[u])
+                          : unit_bucket(core_off, soft_off, G, n_tiles, tpu, n_patches, n_split, u);
     bucket[u] = k;
     atomicAdd(&s_hist[k], 1);
+    if (cost_zero) cost_zero[u] = 0;
   }
   __syncthreads();
-  if (threadIdx.x < kOrderBuckets && s_hist[threadIdx.x]) atomicAdd(hist + threadIdx.x, s_hist[threadIdx.x]);
-}
-
-__global__ void unit_hist_kernel(const int32_t* __restrict__ core_off, const int32_t* __restrict__ soft_off, int G,
-                                 int n_tiles, int tpu, int n_patches, int n_split, int n_units,
-                                 int32_t* __restrict__ bucket, int32_t* __restrict__ hist) {
-  __shared__ int s_hist[kOrderBuckets];
-  if (threadIdx.x < kOrderBuckets) s_hist[threadIdx.x] = 0;
-  __syncthreads();
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u < n_units) {
-    const int k = unit_bucket(core_off, soft_off, G, n_tiles, tpu, n_patches, n_split, u);
-    bucket[u] = k;
-    atomicAdd(&s_hist[k], 1);
-  }
-  __syncthreads();
-  if (threadIdx.x < kOrderBuckets && s_hist[threadIdx.x]) atomicAdd(hist + threadIdx.x, s_hist[threadIdx.x]);
-}
-
-// one warp: bucket start offsets, largest bucket first (hist becomes the cursor array)
-__global__ void unit_scan_kernel(int32_t* __restrict__ hist) {
-  const int lane = threadIdx.x;
-  // lane l owns buckets 63 - 2l and 62 - 2l (descending order)
-  const int a = hist[kOrderBuckets - 1 - 2 * lane], b = hist[kOrderBuckets - 2 - 2 * lane];
-  int incl = a + b;
+  if (threadIdx.x < 32) {
+    // lane l owns buckets 63 - 2l and 62 - 2l (descending order)
+    const int lane = threadIdx.x;
+    const int a = s_hist[kOrderBuckets - 1 - 2 * lane], b = s_hist[kOrderBuckets - 2 - 2 * lane];
+    int incl = a + b;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int ex = incl - a - b;
+    s_hist[kOrderBuckets - 1 - 2 * lane] = ex;
+    s_hist[kOrderBuckets - 2 - 2 * lane] = ex + a;
   }
-  const int ex = incl - a - b;
-  hist[kOrderBuckets - 1 - 2 * lane] = ex;
-  hist[kOrderBuckets - 2 - 2 * lane] = ex + a;
-}
-
-__global__ void unit_scatter_kernel(const int32_t* __restrict__ bucket, int n_units, int32_t* __restrict__ cursor,
-                                    int32_t* __restrict__ order) {
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u < n_units) order[atomicAdd(cursor + bucket[u], 1)] = u;
+  __syncthreads();
+  for (int u = threadIdx.x; u < n_units; u += kOrderThreads) order[atomicAdd(&s_hist[bucket[u]], 1)] = u;
 }
 
 // ---------------------------------------------------------------- N_cand (measurement)
@@ -742,15 +743,12 @@ void launch_bin(bool fill, const TriRec* recs, int F, const Group* groups, int G
 
 size_t scan_temp_ints(int n) { return (size_t)(n + kScanBlock - 1) / kScanBlock + 1; }
 
-void launch_scan(const int32_t* in, int n, int32_t* out, int32_t* temp, cudaStream_t st) {
-  const int nb = (n + kScanBlock - 1) / kScanBlock;
-  if (nb == 0) {
-    cudaMemsetAsync(out, 0, sizeof(int32_t), st);
-    return;
-  }
-  scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(in, n, temp);
-  scan_sums_kernel<<<1, kScanThreads, 0, st>>>(temp, nb);
-  scan_apply_kernel<<<nb, kScanThreads, 0, st>>>(in, n, temp, out);
+void launch_scan_pair(const ScanPair& sp, cudaStream_t st) {
+  const int nb = (sp.n + kScanBlock - 1) / kScanBlock;
+  if (nb == 0) return;  // callers only scan non-empty bin arrays
+  scan_reduce_kernel<<<dim3(nb, 2), kScanThreads, 0, st>>>(sp);
+  scan_sums_kernel<<<dim3(1, 2), kScanThreads, 0, st>>>(sp, nb);
+  scan_apply_kernel<<<dim3(nb, 2), kScanThreads, 0, st>>>(sp);
 }
 
 template <int TW, int TH, int KIND>
@@ -798,32 +796,21 @@ void launch_raster_fwd(const WorkQueue& Q, int tile, int spt, int kind, int grid
     launch_fwd_tile<16, 16>(Q, spt, kind, grid, st);
 }
 
-size_t unit_order_ints(int n_units) { return (size_t)2 * n_units + kOrderBuckets; }
+size_t unit_order_ints(int n_units) { return (size_t)n_units; }
 
 void launch_unit_order(const int32_t* core_off, const int32_t* soft_off, int G, int n_tiles, int tile, int n_split,
-                       int n_units, int32_t* order, int32_t* scratch, cudaStream_t st) {
+                       int n_units, int32_t* order, int32_t* scratch, int32_t* cost_zero, cudaStream_t st) {
   if (n_units <= 0) return;
   const int tpu = tile == 8 ? UnitMap<8, 8>::kTilesPerUnit : UnitMap<16, 16>::kTilesPerUnit;
   const int n_patches = (n_tiles + tpu - 1) / tpu;
-  int32_t* bucket = scratch;
-  int32_t* hist = scratch + n_units;
-  cudaMemsetAsync(hist, 0, sizeof(int32_t) * kOrderBuckets, st);
-  const unsigned blocks = (unsigned)((n_units + 255) / 256);
-  unit_hist_kernel<<<blocks, 256, 0, st>>>(core_off, soft_off, G, n_tiles, tpu, n_patches, n_split, n_units, bucket,
-                                           hist);
-  unit_scan_kernel<<<1, 32, 0, st>>>(hist);
-  unit_scatter_kernel<<<blocks, 256, 0, st>>>(bucket, n_units, hist, order);
+  unit_order_kernel<<<1, kOrderThreads, 0, st>>>(core_off, soft_off, G, n_tiles, tpu, n_patches, n_split, nullptr,
+                                                 cost_zero, n_units, scratch, order);
 }
 
 void launch_unit_order_measured(const int32_t* cost, int n_units, int32_t* order, int32_t* scratch, cudaStream_t st) {
   if (n_units <= 0) return;
-  int32_t* bucket = scratch;
-  int32_t* hist = scratch + n_units;
-  cudaMemsetAsync(hist, 0, sizeof(int32_t) * kOrderBuckets, st);
-  const unsigned blocks = (unsigned)((n_units + 255) / 256);
-  unit_hist_cost_kernel<<<blocks, 256, 0, st>>>(cost, n_units, bucket, hist);
-  unit_scan_kernel<<<1, 32, 0, st>>>(hist);
-  unit_scatter_kernel<<<blocks, 256, 0, st>>>(bucket, n_units, hist, order);
+  unit_order_kernel<<<1, kOrderThreads, 0, st>>>(nullptr, nullptr, 0, 0, 1, 1, 1, cost, nullptr, n_units, scratch,
+                                                 order);
 }
 
 void launch_raster_count(const WorkQueue& Q, int spt, int kind, int grid, cudaStream_t st) {

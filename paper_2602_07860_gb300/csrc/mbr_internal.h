@@ -19,7 +19,7 @@ void launch_setup(const float4* pos, const int32_t* faces, int F, int V, const i
                   float znear, TriRec* recs, cudaStream_t st);
 // both bin sets of a render: [0] core (undilated), [1] soft (dilated by r_soft)
 struct BinTargets {
-  int32_t* counts_or_cursor[2];  // count pass: zeroed counts; fill pass: cursors (copies of the offsets)
+  int32_t* counts_or_cursor[2];  // count pass: zeroed counts; fill pass: zeroed cursors (slot = offset + cursor)
   int32_t* list[2];              // fill pass: CSR face lists
   const int32_t* off[2];         // fill pass: CSR offsets
   int cap[2];                    // fill pass: list capacities
@@ -27,17 +27,26 @@ struct BinTargets {
 void launch_bin(bool fill, const TriRec* recs, int F, const Group* groups, int G, int W, int H, int tw, int th,
                 int tiles_x, int n_tiles, float r_core, float r_soft, const BinTargets& t, int* status,
                 cudaStream_t st);
+// exclusive scans of the core and soft bin counts in one set of launches; the counts are zeroed
+// (they become the fill pass's cursors) and total[q] (if set) receives out[q][n]
+struct ScanPair {
+  int32_t* in[2];    // [n] counts
+  int32_t* out[2];   // [n + 1] offsets
+  int32_t* sums[2];  // [scan_temp_ints(n)] scratch
+  int32_t* total;    // [2] or null
+  int n;
+};
 size_t scan_temp_ints(int n);
-void launch_scan(const int32_t* in, int n, int32_t* out, int32_t* temp, cudaStream_t st);
+void launch_scan_pair(const ScanPair& sp, cudaStream_t st);
 // persistent raster launches; kind 0 plain only, 1 fast only, 2 mixed
 void launch_raster_fwd(const WorkQueue& Q, int tile, int spt, int kind, int grid, cudaStream_t st);
 int persistent_grid_fwd(int num_sms, int tile, int spt, int kind);
 int persistent_grid_bwd(int num_sms, int tile, int spt, int kind);
-// LPT visiting order of a render's units (patch x group split) from its bin offsets; scratch holds
-// unit_order_ints(n_units) ints
+// LPT visiting order of a render's units (patch x group split) from its bin offsets (one launch);
+// scratch holds unit_order_ints(n_units) ints; cost_zero (if set, [n_units]) is cleared
 size_t unit_order_ints(int n_units);
 void launch_unit_order(const int32_t* core_off, const int32_t* soft_off, int G, int n_tiles, int tile, int n_split,
-                       int n_units, int32_t* order, int32_t* scratch, cudaStream_t st);
+                       int n_units, int32_t* order, int32_t* scratch, int32_t* cost_zero, cudaStream_t st);
 // the same from a measured cost per unit (the forward raster's estimate of the adjoint's work)
 void launch_unit_order_measured(const int32_t* cost, int n_units, int32_t* order, int32_t* scratch, cudaStream_t st);
 // measurement build of the forward raster (16 x 16 tiles): counts soft terms / covered samples

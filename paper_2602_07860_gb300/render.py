@@ -250,7 +250,9 @@ def default_context():
 
 class RenderBlur(torch.autograd.Function):
     """image = render_blur(verts, albedo); backward gives dL/dverts and dL/dalbedo through the
-    library's adjoint kernels (sub-frame state recomputed, not stored)."""
+    library's adjoint kernels.  The adjoint recomputes every sub-frame quantity (barycentrics,
+    distances, closest points, shading) per sample; the forward keeps only, per sample, the winner
+    face or the aggregate log soft product, and its front half (records, bins)."""
 
     @staticmethod
     def forward(ctx, verts, albedo, faces, motion, camera, T, H, W, solver, rctx):
