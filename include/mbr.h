@@ -55,6 +55,9 @@ extern "C" {
 
 #define MBR_TIME_PAPER 0    /* t_k = k/(T-1), T = 1 -> 0.5 (Sec. 3.2)  */
 #define MBR_TIME_MIDPOINT 1 /* t_k = (k + 0.5)/T                        */
+/* soft-coverage probability of a background pixel at squared distance d from a triangle */
+#define MBR_PROB_EXP 0      /* A = exp(-d/delta), the paper's choice (App. "Implementation Details") */
+#define MBR_PROB_SIGMOID 1  /* A = sigmoid(-d/delta), the original SoftRas map the appendix replaces */
 
 typedef struct mbr_ctx mbr_ctx;
 
@@ -91,6 +94,7 @@ typedef struct {
   float k_ambient, k_diffuse; /* I = c (k_ambient + k_diffuse max(0, n.l))                   */
   float delta;          /* soft-coverage temperature of Eq. probability-function (1e-4)      */
   int32_t time_rule;    /* MBR_TIME_PAPER or MBR_TIME_MIDPOINT                                */
+  int32_t prob;         /* MBR_PROB_EXP or MBR_PROB_SIGMOID                                   */
 } mbr_camera;
 
 /* One render of a batch (device pointers; see mbr_render_blur_batch). */

@@ -12,7 +12,10 @@
  *   - a triangle is skipped at a sample when |det F| <= 1e-10 or any vertex has camera
  *     z <= znear (exact modes: at t; keyframe modes: at either keyframe of the segment);
  *   - foreground samples have alpha 1 and Lambertian colour; background samples are black with
- *     alpha 1 - prod_j (1 - exp(-d_j / delta)) over triangles with d_j <= delta ln 1e12;
+ *     alpha 1 - prod_j (1 - A_j) over triangles with d_j <= delta ln 1e12, A_j = exp(-d_j / delta)
+ *     (the paper's map) or sigmoid(-d_j / delta) (the SoftRas map it replaces, App.
+ *     "Implementation Details"); the sigmoid is below the exponential, so the truncation bound
+ *     holds for both;
  *   - the closest point lies on the triangle (sum of weights 1), found by the appendix's three
  *     clamped edge projections; the fast mode searches F(X) (X = 0 if tau <= 0.5 else 1) around
  *     F(X) w(tau) and measures d at F(tau) w* (Eqs. euc-dist-approx-2/3).
@@ -101,6 +104,21 @@ void orc_sample_time(const orc_scene* s, int32_t k, int32_t* seg, double* t, dou
 }
 
 /* keyframe X of Eq. euc-dist-approx-2: 0 if tau <= 0.5 else 1, decided on the exact fraction */
+/* soft-coverage probability A (Eq. probability-function) of squared distance d, its factor
+ * 1 - A (computed without cancellation) and dA/dd */
+static double soft_prob(const orc_scene* s, double d, double* one_minus, double* dA_dd) {
+  const double x = d / s->delta, e = exp(-x);
+  if (s->prob == 1) {
+    const double A = e / (1.0 + e);
+    *one_minus = 1.0 / (1.0 + e);
+    *dA_dd = -A * *one_minus / s->delta;
+    return A;
+  }
+  *one_minus = -expm1(-x);
+  *dA_dd = -e / s->delta;
+  return e;
+}
+
 static int32_t sample_key_x(const orc_scene* s, int32_t k) {
   int64_t S = orc_num_segments(s), num, den;
   time_fraction(s, k, &num, &den);
@@ -283,7 +301,7 @@ double orc_closest_point(const double tri[6], double px, double py, double w[3],
 
 /* ------------------------------------------------------------------ renderer */
 
-typedef struct { int32_t p, f; double fval, A, d; } soft_entry;
+typedef struct { int32_t p, f; double fval, dA, d; } soft_entry;  /* dA = dA/dd */
 
 typedef struct {
   soft_entry* e;
@@ -560,7 +578,8 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
                 double ax = c.w_second[0] * tri[0] + c.w_second[1] * tri[2] + c.w_second[2] * tri[4];
                 double ay = c.w_second[0] * tri[1] + c.w_second[1] * tri[3] + c.w_second[2] * tri[5];
                 double d_alt = (u - ax) * (u - ax) + (v - ay) * (v - ay);
-                if (fmin(d, d_alt) <= r2 && fabs(exp(-d / s->delta) - exp(-d_alt / s->delta)) > 1e-6)
+                double om, dA;
+                if (fmin(d, d_alt) <= r2 && fabs(soft_prob(s, d, &om, &dA) - soft_prob(s, d_alt, &om, &dA)) > 1e-6)
                   samb[p] |= AMB_REGION;
               }
             } else {
@@ -586,13 +605,13 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
             }
             hash = fnv(fnv(fnv(hash, k * 7919 + 1), (int64_t)p * 104729 + f), c.region * 2 + include);
             if (include) {
-              double A = exp(-d / s->delta);
-              double fv = -expm1(-d / s->delta);
+              double fv, dA;
+              soft_prob(s, d, &fv, &dA);
               prod[p] *= fv;
               ++n_soft;
-              if (A > SOFT32_MIN) ++nsoft32[p];
+              if (exp(-d / s->delta) > SOFT32_MIN) ++nsoft32[p];  /* inside the single-precision radius */
               if (backward) {
-                soft_entry se = {(int32_t)p, f, fv, A, d};
+                soft_entry se = {(int32_t)p, f, fv, dA, d};
                 if (!push_entry(&L, se)) goto fail;
               }
             }
@@ -698,8 +717,8 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
           const soft_entry* se = sorted + qq;
           double excl = pre[qq - b] * suffix;
           suffix *= se->fval;
-          /* alpha = 1 - prod(1 - A_j): dalpha/dA_j = prod_{l != j}(1 - A_l); dA/dd = -A/delta */
-          double gd = ga * excl * (-se->A / s->delta);
+          /* alpha = 1 - prod(1 - A_j): dalpha/dA_j = prod_{l != j}(1 - A_l) */
+          double gd = ga * excl * se->dA;
           const int32_t* id = s->faces + 3 * se->f;
           int32_t i = (int32_t)(p % w) + x0, j = (int32_t)(p / w) + y0;
           double u = 2.0 * (i + 0.5) / s->W - 1.0, v = 1.0 - 2.0 * (j + 0.5) / s->H;

@@ -40,6 +40,9 @@ typedef struct {
   double light_dir[3];    /* direction towards the light, world space (normalised here)    */
   double k_ambient, k_diffuse, delta;
   int32_t time_rule;      /* 0: t_k = k/(T-1) (T=1: 0.5) ; 1: t_k = (k+0.5)/T             */
+  int32_t prob;           /* soft-coverage probability of Eq. probability-function: 0 exp(-d/delta)
+                             (the paper's), 1 sigmoid(-d/delta) (SoftRas's, App. "Implementation
+                             Details")                                                        */
   int32_t T, H, W;
 } orc_scene;
 

@@ -168,6 +168,7 @@ struct BwdSoftGradPairs {
   WarpScratch<SPT>* ws;
   uint32_t xbits;
   float m, r2, inv_delta;
+  int prob;
   const int32_t* faces;
   float4* gslot_a;
   float4* gslot_b;
@@ -189,15 +190,15 @@ struct BwdSoftGradPairs {
       EdgeVals e;
       SoftGeom sg;
       if (!soft_pair_term<MOVING>(r, ps, u, v, tau, X, m, r2, e, sg)) continue;
-      float A;
-      const float f = soft_factor(sg.d, inv_delta, A);
+      float A, dA;
+      const float f = soft_factor(sg.d, inv_delta, prob, A, dA);
       const float S = ws->logp[i][p];
       const int nz = ws->nzero[i][p];
       float excl;
       if (nz == 0) excl = __expf(S - __logf(f));
       else excl = (nz == 1 && f <= kTinyFactor) ? __expf(S) : 0.f;
-      // alpha = 1 - prod(1 - A_l): d alpha / d d_j = -excl A_j / delta
-      const float gd = ga * excl * (-A * inv_delta);
+      // alpha = 1 - prod(1 - A_l): d alpha / d d_j = excl dA_j/dd
+      const float gd = ga * excl * dA;
       if (gd == 0.f) continue;
       soft_grad_accumulate<MOVING>(r, ps, e, sg, tau, X, gd, gax, gay, gbx, gby);
     }
@@ -514,6 +515,7 @@ __device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile
       p3.m = m;
       p3.r2 = P.r2;
       p3.inv_delta = P.inv_delta;
+      p3.prob = P.prob;
       p3.faces = P.faces;
       p3.gslot_a = P.g_slot + (size_t)gq.slot_a * P.V * 2;
       p3.gslot_b = P.g_slot + (size_t)gq.slot_b * P.V * 2;

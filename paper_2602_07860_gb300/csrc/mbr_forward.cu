@@ -366,6 +366,7 @@ struct FwdSoftPairs {
   WarpScratch<SPT>* ws;
   uint32_t xbits;
   float m, r2, inv_delta;
+  int prob;
   uint32_t n_terms, n_eval, n_batches;
   __device__ __forceinline__ void pair(bool ok, int face, int p, uint32_t smp) {
     if (!ok) return;
@@ -381,8 +382,8 @@ struct FwdSoftPairs {
       EdgeVals e;
       SoftGeom sg;
       if (!soft_pair_term<MOVING>(r, ps, u, v, tau, (xbits >> i) & 1u, m, r2, e, sg)) continue;
-      float A;
-      const float f = soft_factor(sg.d, inv_delta, A);
+      float A, dA;
+      const float f = soft_factor(sg.d, inv_delta, prob, A, dA);
       if (f > kTinyFactor) atomicAdd(&ws->logp[i][p], __logf(f));
       else atomicAdd(&ws->nzero[i][p], 1);
       if (COUNT) ++n_terms;
@@ -464,7 +465,7 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
     const uint32_t my_s = in_img ? uncov : 0u;
     const uint32_t any_s = __reduce_or_sync(kFullMask, my_s);
     FwdSoftPairs<SPT, MOVING, COUNT> soft{recs_set, grp, bp, &ws, gr.xbits, P.r + kCoreMargin, P.r2, P.inv_delta,
-                                          0u, 0u, 0u};
+                                          P.prob, 0u, 0u, 0u};
     if (se > sb && any_s) {
 #pragma unroll
       for (int i = 0; i < SPT; ++i) {

@@ -50,6 +50,7 @@ struct RasterParams {
   int32_t F, V, G;
   int32_t H, W, tiles_x, tiles_y, n_split;
   float r, r2, inv_delta, delta;
+  int32_t prob;              // soft-coverage map: 0 exp(-d/delta), 1 sigmoid(-d/delta)
   float lx, ly, lz, ka, kd;
   float inv_T;
   float4* out;               // image: stored (n_split == 1) or accumulated with atomics (zeroed first)
@@ -319,13 +320,25 @@ struct BlockPix {
   }
 };
 
-// Soft-coverage factor 1 - A, A = exp(-d / delta) (Eq. probability-function).  A is computed
-// with the fast exponential: its relative error (~1e-6) changes alpha = 1 - prod(1 - A_j) by at
-// most about that much in absolute terms, because each factor's absolute error passes through
-// the product scaled by the other factors (all <= 1).
-__device__ __forceinline__ float soft_factor(float d, float inv_delta, float& A) {
-  A = __expf(-d * inv_delta);
-  return 1.f - A;
+// Soft-coverage probability A of a triangle at squared distance d (Eq. probability-function)
+// and the factor 1 - A it contributes; dA_dd receives dA/dd.  prob 0: A = exp(-d/delta) (the
+// paper's map); 1: A = sigmoid(-d/delta) = E / (1 + E) with E = exp(-d/delta) (the SoftRas map
+// the paper replaces), so 1 - A = 1 / (1 + E) and dA/dd = -A (1 - A) / delta.  E comes from the
+// fast exponential: its relative error (~1e-6) changes alpha = 1 - prod(1 - A_j) by at most
+// about that much in absolute terms, because each factor's absolute error passes through the
+// product scaled by the other factors (all <= 1).  The sigmoid is below the exponential, so the
+// 2^-25 cutoff of the soft radius holds for both maps.
+__device__ __forceinline__ float soft_factor(float d, float inv_delta, int prob, float& A, float& dA_dd) {
+  const float E = __expf(-d * inv_delta);
+  if (prob == 0) {
+    A = E;
+    dA_dd = -E * inv_delta;
+    return 1.f - E;
+  }
+  const float f = 1.f / (1.f + E);
+  A = E * f;
+  dA_dd = -A * f * inv_delta;
+  return f;
 }
 
 // Block pixels whose centres lie in box (xmin, xmax, ymin, ymax).  The boxes are dilated by at

@@ -49,6 +49,7 @@ class Camera:
     k_diffuse: float = 0.7
     delta: float = 1e-4
     time_rule: str = "paper"         # 'paper' | 'midpoint'
+    prob: str = "exp"                # soft-coverage map: 'exp' (the paper's) | 'sigmoid' (SoftRas)
 
     def c(self):
         c = MbrCamera()
@@ -60,6 +61,7 @@ class Camera:
         c.k_diffuse = float(self.k_diffuse)
         c.delta = float(self.delta)
         c.time_rule = _lib.MBR_TIME_PAPER if self.time_rule == "paper" else _lib.MBR_TIME_MIDPOINT
+        c.prob = {"exp": _lib.MBR_PROB_EXP, "sigmoid": _lib.MBR_PROB_SIGMOID}[self.prob]
         return c
 
 
@@ -72,7 +74,7 @@ def motion_from_dict(m):
 def camera_from_dict(c):
     return Camera(view=tuple(np.asarray(c["view"]).reshape(-1)), tan_half_fov=c["tan_half_fov"], znear=c["znear"],
                   light_dir=tuple(c["light_dir"]), k_ambient=c["k_ambient"], k_diffuse=c["k_diffuse"],
-                  delta=c["delta"], time_rule=c.get("time_rule", "paper"))
+                  delta=c["delta"], time_rule=c.get("time_rule", "paper"), prob=c.get("prob", "exp"))
 
 
 def mesh_tensors(scene, device="cuda"):

@@ -53,6 +53,8 @@ GRAD_SCENES = {
     "c1": lambda: scenes.config1(),
     "parabolic": lambda: dict(scenes.small_scene("parabolic", subdiv=2, T=10, H=40, W=48),
                               camera=scenes.camera(scenes.look_at(scenes.orbit_eye(5.0, 0, 10.0)))),
+    "rotate_sigmoid_prob": lambda: dict(scenes.small_scene("rotate", subdiv=1, T=6, H=32, W=40),
+                                        camera=scenes.camera(scenes.look_at((0, 0, -4)), delta=2e-3, prob="sigmoid")),
 }
 
 

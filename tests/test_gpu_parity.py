@@ -46,6 +46,9 @@ SCENES = {
     # the appendix's combined rotation and parabolic translation (6 segments for the half turn)
     "parabolic_appendix": lambda: dict(scenes.small_scene("parabolic", subdiv=2, T=16, H=48, W=64),
                                        camera=scenes.camera(scenes.look_at(scenes.orbit_eye(5.0, 0, 10.0)))),
+    # the SoftRas probability map the paper replaces (sigmoid instead of exp), with a wide delta
+    "rotate_sigmoid_prob": lambda: dict(scenes.small_scene("rotate", subdiv=2, T=8, H=40, W=56),
+                                        camera=scenes.camera(scenes.look_at((0, 0, -4)), delta=2e-3, prob="sigmoid")),
 }
 
 

@@ -326,6 +326,34 @@ def test_soft32_counter_is_the_uncovered_terms_above_the_single_precision_cutoff
     assert c[oracle.CNT_COVERED] == T * inside.sum()
 
 
+@pytest.mark.parametrize("prob", ["exp", "sigmoid"])
+def test_static_quad_soft_alpha_closed_form(prob):
+    """Static screen-aligned quad (two triangles): a pixel inside has alpha 1; a pixel outside has
+    alpha = 1 - prod over the two triangles of (1 - A(d)), d the squared distance to the triangle
+    (the minimum over its edges), A(d) = exp(-d/delta) or sigmoid(-d/delta), terms beyond
+    delta ln 1e12 dropped (Eqs. probability-function and back)."""
+    L0, R0, B, Tp = -0.37, 0.113, -0.29, 0.41
+    T, delta = 2, 4e-3
+    sc = _quad_scene(T, 0.0, L0, R0, B, Tp)
+    sc["camera"] = dict(sc["camera"], delta=delta, prob=prob)
+    a = oracle.render(sc, "exact")["rgba"][..., 3]
+    H, W = sc["H"], sc["W"]
+    u = (2 * (np.arange(W) + 0.5) / W - 1)[None, :].repeat(H, 0)
+    v = (1 - 2 * (np.arange(H) + 0.5) / H)[:, None].repeat(W, 1)
+    BL, BR, TR, TL = (L0, B), (R0, B), (R0, Tp), (L0, Tp)
+    inside = (u >= L0) & (u <= R0) & (v >= B) & (v <= Tp)
+    keep = np.ones((H, W))
+    for tri in ((BL, TR, BR), (BL, TL, TR)):
+        d2 = np.min([_seg_dist2(u, v, *tri[q], *tri[(q + 1) % 3]) for q in range(3)], axis=0)
+        x = d2 / delta
+        A = np.exp(-x) if prob == "exp" else 1.0 / (1.0 + np.exp(x))
+        keep *= np.where(d2 <= delta * np.log(1e12), 1.0 - A, 1.0)
+    expect = np.where(inside, 1.0, 1.0 - keep)
+    assert np.max(np.abs(a - expect)) < 1e-12
+    if prob == "sigmoid":  # at the quad's edge the SoftRas map gives 1/2 per triangle
+        assert np.all(expect[~inside] < 0.75 + 1e-12)
+
+
 def test_rotation_relabel_invariance_midpoint_rule():
     """With t_k = (k + 0.5)/T, omega = 2 pi and T a multiple of n, pre-rotating the mesh by 2 pi/n
     about the motion axis permutes the sub-frames and leaves the blurred image unchanged."""
