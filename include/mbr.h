@@ -58,6 +58,9 @@ extern "C" {
 /* soft-coverage probability of a background pixel at squared distance d from a triangle */
 #define MBR_PROB_EXP 0      /* A = exp(-d/delta), the paper's choice (App. "Implementation Details") */
 #define MBR_PROB_SIGMOID 1  /* A = sigmoid(-d/delta), the original SoftRas map the appendix replaces */
+/* attribute (albedo, normal) interpolation of a covered sample */
+#define MBR_INTERP_SCREEN 0       /* screen-space barycentrics w (Eq. fore)                          */
+#define MBR_INTERP_PERSPECTIVE 1  /* perspective-correct (w_i / z_i) / sum_j (w_j / z_j), z camera depth */
 
 typedef struct mbr_ctx mbr_ctx;
 
@@ -95,6 +98,7 @@ typedef struct {
   float delta;          /* soft-coverage temperature of Eq. probability-function (1e-4)      */
   int32_t time_rule;    /* MBR_TIME_PAPER or MBR_TIME_MIDPOINT                                */
   int32_t prob;         /* MBR_PROB_EXP or MBR_PROB_SIGMOID                                   */
+  int32_t interp;       /* MBR_INTERP_SCREEN or MBR_INTERP_PERSPECTIVE                        */
 } mbr_camera;
 
 /* One render of a batch (device pointers; see mbr_render_blur_batch). */

@@ -37,8 +37,8 @@ class OrcScene(ctypes.Structure):
         ("acc", c_double * 3),
         ("view", c_double * 12), ("tan_half_fov", c_double), ("znear", c_double),
         ("light_dir", c_double * 3), ("k_ambient", c_double), ("k_diffuse", c_double),
-        ("delta", c_double), ("time_rule", c_int32), ("prob", c_int32), ("T", c_int32), ("H", c_int32),
-        ("W", c_int32),
+        ("delta", c_double), ("time_rule", c_int32), ("prob", c_int32), ("interp", c_int32),
+        ("T", c_int32), ("H", c_int32), ("W", c_int32),
     ]
 
 
@@ -105,6 +105,7 @@ class _Scene:
         s.delta = float(c["delta"])
         s.time_rule = 0 if c.get("time_rule", "paper") == "paper" else 1
         s.prob = {"exp": 0, "sigmoid": 1}[c.get("prob", "exp")]
+        s.interp = {"screen": 0, "perspective": 1}[c.get("interp", "screen")]
         s.T, s.H, s.W = int(sc["T"]), int(sc["H"]), int(sc["W"])
         self.s = s
 

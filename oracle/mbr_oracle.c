@@ -325,13 +325,13 @@ static void chain_state(const orc_scene* s, double t, const double* gst, double*
   double th = s->tan_half_fov;
   const double* m = s->view;
   for (int32_t v = 0; v < s->V; ++v) {
-    const double* g = gst + 5 * v;
-    if (g[0] == 0 && g[1] == 0 && g[2] == 0 && g[3] == 0 && g[4] == 0) continue;
+    const double* g = gst + 6 * v;  /* x, y, nx, ny, nz, camera z */
+    if (g[0] == 0 && g[1] == 0 && g[2] == 0 && g[3] == 0 && g[4] == 0 && g[5] == 0) continue;
     double P[3], cam[3], x, y, z;
     place(s, t, s->verts + 3 * v, P);
     project(s, P, &x, &y, &z, cam);
     double dxc = g[0] / (z * th), dyc = g[1] / (z * th);
-    double dzc = -(g[0] * x + g[1] * y) / z;
+    double dzc = g[5] - (g[0] * x + g[1] * y) / z;
     double dP[3];
     for (int i = 0; i < 3; ++i) dP[i] = m[i] * dxc + m[4 + i] * dyc + m[8 + i] * dzc;
     double dv[3], dn[3];
@@ -427,8 +427,8 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
   uint8_t* amb = (uint8_t*)malloc(npix + 1);
   uint8_t* samb = (uint8_t*)malloc(npix + 1); /* flags of soft terms: count only if uncovered */
   int32_t* nsoft32 = (int32_t*)malloc(sizeof(int32_t) * (npix + 1)); /* terms above 2^-25, per sample */
-  double* gcur = backward ? (double*)calloc(5 * (size_t)V, sizeof(double)) : NULL;
-  double* gslot = backward ? (double*)calloc(5 * (size_t)V * (S + 1), sizeof(double)) : NULL;
+  double* gcur = backward ? (double*)calloc(6 * (size_t)V, sizeof(double)) : NULL;
+  double* gslot = backward ? (double*)calloc(6 * (size_t)V * (S + 1), sizeof(double)) : NULL;
   double* gnb = backward ? (double*)calloc(3 * (size_t)V, sizeof(double)) : NULL;
   size_t* pstart = backward ? (size_t*)malloc(sizeof(size_t) * (npix + 2)) : NULL;
   soft_entry* sorted = NULL;
@@ -635,11 +635,21 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
         ++n_cov;
         const int32_t* id = s->faces + 3 * f;
         const double* wb = bestw + 3 * p;
+        /* attribute weights: the screen-space barycentrics (Eq. fore) or the perspective-correct
+         * aw_i = (w_i / z_i) / S, S = sum_j w_j / z_j, z the vertices' camera depths */
+        double aw[3], zc[3], S_w = 0.0;
+        for (int q = 0; q < 3; ++q) {
+          zc[q] = cur[6 * id[q] + 2];
+          aw[q] = wb[q];
+          S_w += wb[q] / zc[q];
+        }
+        if (s->interp == 1)
+          for (int q = 0; q < 3; ++q) aw[q] = wb[q] / zc[q] / S_w;
         double col[3] = {0, 0, 0}, nn[3] = {0, 0, 0};
         for (int q = 0; q < 3; ++q)
           for (int c = 0; c < 3; ++c) {
-            col[c] += wb[q] * s->albedo[3 * id[q] + c];
-            nn[c] += wb[q] * cur[6 * id[q] + 3 + c];
+            col[c] += aw[q] * s->albedo[3 * id[q] + c];
+            nn[c] += aw[q] * cur[6 * id[q] + 3 + c];
           }
         double len = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
         double dot = len > 0 ? (nn[0] * Ld[0] + nn[1] * Ld[1] + nn[2] * Ld[2]) / len : 0.0;
@@ -659,7 +669,7 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
           }
           for (int q = 0; q < 3; ++q)
             for (int c = 0; c < 3; ++c) {
-              if (galb) galb[3 * id[q] + c] += wb[q] * gcol[c];
+              if (galb) galb[3 * id[q] + c] += aw[q] * gcol[c];
               gw[q] += s->albedo[3 * id[q] + c] * gcol[c];
             }
           if (len > 0 && dot > 0) {
@@ -671,9 +681,17 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
             for (int c = 0; c < 3; ++c) gnn[c] = (gnh[c] - nh[c] * ng) / len;
             for (int q = 0; q < 3; ++q)
               for (int c = 0; c < 3; ++c) {
-                gcur[5 * id[q] + 2 + c] += wb[q] * gnn[c];
+                gcur[6 * id[q] + 2 + c] += aw[q] * gnn[c];
                 gw[q] += cur[6 * id[q] + 3 + c] * gnn[c];
               }
+          }
+          if (s->interp == 1) {
+            /* gw holds dL/daw: dL/dw_k = (gw_k - sum_i gw_i aw_i) / (z_k S), dL/dz_k = -(w_k / z_k) dL/dw_k */
+            double sa = aw[0] * gw[0] + aw[1] * gw[1] + aw[2] * gw[2];
+            for (int q = 0; q < 3; ++q) {
+              gw[q] = (gw[q] - sa) / (zc[q] * S_w);
+              gcur[6 * id[q] + 5] += -(wb[q] / zc[q]) * gw[q];
+            }
           }
           double tri[6], y[3];
           for (int q = 0; q < 3; ++q) {
@@ -682,8 +700,8 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
           }
           solve_transposed(tri, gw, y);
           for (int q = 0; q < 3; ++q) {
-            gcur[5 * id[q]] += -y[0] * wb[q];
-            gcur[5 * id[q] + 1] += -y[1] * wb[q];
+            gcur[6 * id[q]] += -y[0] * wb[q];
+            gcur[6 * id[q] + 1] += -y[1] * wb[q];
           }
         }
       } else if (rgba) {
@@ -734,8 +752,8 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
             double qx = c.w[0] * tri[0] + c.w[1] * tri[2] + c.w[2] * tri[4];
             double qy = c.w[0] * tri[1] + c.w[1] * tri[3] + c.w[2] * tri[5];
             for (int q = 0; q < 3; ++q) {
-              gcur[5 * id[q]] += gd * -2.0 * (u - qx) * c.w[q];
-              gcur[5 * id[q] + 1] += gd * -2.0 * (v - qy) * c.w[q];
+              gcur[6 * id[q]] += gd * -2.0 * (u - qx) * c.w[q];
+              gcur[6 * id[q] + 1] += gd * -2.0 * (v - qy) * c.w[q];
             }
           } else {
             double wb[3], trX[6];
@@ -754,13 +772,13 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
             double gqx = -2.0 * (u - qx) * gd, gqy = -2.0 * (v - qy) * gd;
             double gws[3];
             for (int q = 0; q < 3; ++q) {
-              gcur[5 * id[q]] += c.w[q] * gqx;
-              gcur[5 * id[q] + 1] += c.w[q] * gqy;
+              gcur[6 * id[q]] += c.w[q] * gqx;
+              gcur[6 * id[q] + 1] += c.w[q] * gqy;
               gws[q] = tri[2 * q] * gqx + tri[2 * q + 1] * gqy;
             }
             /* w* = (1-t) e_i + t e_j with t = ((p' - v_i).e)/|e|^2 when t is interior */
             double gpx = 0, gpy = 0;
-            double* gX = gslot + 5 * (size_t)V * (seg + X);
+            double* gX = gslot + 6 * (size_t)V * (seg + X);
             if (c.region < 3) {
               int ii = c.ei, jj = c.ej;
               double ex = trX[2 * jj] - trX[2 * ii], ey = trX[2 * jj + 1] - trX[2 * ii + 1];
@@ -769,24 +787,24 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
               double gt = gws[jj] - gws[ii], tt = c.t;
               gpx = gt * ex / L2;
               gpy = gt * ey / L2;
-              gX[5 * id[ii]] += gt * (-ex - rx + 2.0 * tt * ex) / L2;
-              gX[5 * id[ii] + 1] += gt * (-ey - ry + 2.0 * tt * ey) / L2;
-              gX[5 * id[jj]] += gt * (rx - 2.0 * tt * ex) / L2;
-              gX[5 * id[jj] + 1] += gt * (ry - 2.0 * tt * ey) / L2;
+              gX[6 * id[ii]] += gt * (-ex - rx + 2.0 * tt * ex) / L2;
+              gX[6 * id[ii] + 1] += gt * (-ey - ry + 2.0 * tt * ey) / L2;
+              gX[6 * id[jj]] += gt * (rx - 2.0 * tt * ex) / L2;
+              gX[6 * id[jj] + 1] += gt * (ry - 2.0 * tt * ey) / L2;
             }
             /* p' = F(X) w */
             double gw[3];
             for (int q = 0; q < 3; ++q) {
-              gX[5 * id[q]] += wb[q] * gpx;
-              gX[5 * id[q] + 1] += wb[q] * gpy;
+              gX[6 * id[q]] += wb[q] * gpx;
+              gX[6 * id[q] + 1] += wb[q] * gpy;
               gw[q] = trX[2 * q] * gpx + trX[2 * q + 1] * gpy;
             }
             /* w = F(tau)^-1 p */
             double y[3];
             solve_transposed(tri, gw, y);
             for (int q = 0; q < 3; ++q) {
-              gcur[5 * id[q]] += -y[0] * wb[q];
-              gcur[5 * id[q] + 1] += -y[1] * wb[q];
+              gcur[6 * id[q]] += -y[0] * wb[q];
+              gcur[6 * id[q] + 1] += -y[1] * wb[q];
             }
           }
         }
@@ -799,14 +817,14 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
       if (mode == ORC_PLAIN_EXACT) {
         chain_state(s, t, gcur, gverts, gnb);
       } else {
-        double* g0 = gslot + 5 * (size_t)V * seg;
-        double* g1 = gslot + 5 * (size_t)V * (seg + 1);
-        for (size_t q = 0; q < 5 * (size_t)V; ++q) {
+        double* g0 = gslot + 6 * (size_t)V * seg;
+        double* g1 = gslot + 6 * (size_t)V * (seg + 1);
+        for (size_t q = 0; q < 6 * (size_t)V; ++q) {
           g0[q] += (1.0 - tau) * gcur[q];
           g1[q] += tau * gcur[q];
         }
       }
-      memset(gcur, 0, sizeof(double) * 5 * V);
+      memset(gcur, 0, sizeof(double) * 6 * V);
     }
   }
 
@@ -815,7 +833,7 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
   if (backward) {
     if (mode != ORC_PLAIN_EXACT)
       for (int32_t sg = 0; sg <= S; ++sg)
-        chain_state(s, (double)sg / S, gslot + 5 * (size_t)V * sg, gverts, gnb);
+        chain_state(s, (double)sg / S, gslot + 6 * (size_t)V * sg, gverts, gnb);
     normals_backward(s, gnb, gverts);
   }
   if (cnt) {

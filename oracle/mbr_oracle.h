@@ -43,6 +43,8 @@ typedef struct {
   int32_t prob;           /* soft-coverage probability of Eq. probability-function: 0 exp(-d/delta)
                              (the paper's), 1 sigmoid(-d/delta) (SoftRas's, App. "Implementation
                              Details")                                                        */
+  int32_t interp;         /* attribute weights of a covered sample: 0 screen-space w (Eq. fore),
+                             1 perspective-correct (w_i / z_i) / sum_j (w_j / z_j)             */
   int32_t T, H, W;
 } orc_scene;
 

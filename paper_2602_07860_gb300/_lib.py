@@ -14,6 +14,7 @@ MBR_PLAIN, MBR_FAST = 0, 1
 MBR_TRANSLATE, MBR_ROTATE, MBR_PARABOLIC = 0, 1, 2
 MBR_TIME_PAPER, MBR_TIME_MIDPOINT = 0, 1
 MBR_PROB_EXP, MBR_PROB_SIGMOID = 0, 1
+MBR_INTERP_SCREEN, MBR_INTERP_PERSPECTIVE = 0, 1
 SOLVERS = {"plain": MBR_PLAIN, "fast": MBR_FAST}
 
 EXPORTS = ["mbr_create", "mbr_destroy", "mbr_render_blur", "mbr_render_blur_backward",
@@ -34,7 +35,7 @@ class MbrMotion(ctypes.Structure):
 class MbrCamera(ctypes.Structure):
     _fields_ = [("view", c_float * 12), ("tan_half_fov", c_float), ("znear", c_float), ("light_dir", c_float * 3),
                 ("k_ambient", c_float), ("k_diffuse", c_float), ("delta", c_float), ("time_rule", c_int32),
-                ("prob", c_int32)]
+                ("prob", c_int32), ("interp", c_int32)]
 
 
 class MbrItem(ctypes.Structure):

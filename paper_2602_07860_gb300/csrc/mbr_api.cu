@@ -207,6 +207,8 @@ int validate(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const m
     return fail(c, MBR_ERR_ARG, "zero rotation axis");
   if (!(cam->tan_half_fov > 0.f) || !(cam->delta > 0.f)) return fail(c, MBR_ERR_ARG, "bad camera fov/delta");
   if (cam->prob != MBR_PROB_EXP && cam->prob != MBR_PROB_SIGMOID) return fail(c, MBR_ERR_ARG, "bad probability map");
+  if (cam->interp != MBR_INTERP_SCREEN && cam->interp != MBR_INTERP_PERSPECTIVE)
+    return fail(c, MBR_ERR_ARG, "bad attribute interpolation");
   if (cam->time_rule != MBR_TIME_PAPER && cam->time_rule != MBR_TIME_MIDPOINT)
     return fail(c, MBR_ERR_ARG, "bad time rule");
   const long long T_ = T;
@@ -517,6 +519,7 @@ RasterParams raster_params(const mbr_ctx* c, const RasterBufs& b, const mbr_mesh
   P.delta = cam->delta;
   P.inv_delta = 1.0f / cam->delta;
   P.prob = cam->prob;
+  P.persp = cam->interp == MBR_INTERP_PERSPECTIVE ? 1 : 0;
   double L[3] = {cam->light_dir[0], cam->light_dir[1], cam->light_dir[2]};
   const double ln = std::sqrt(L[0] * L[0] + L[1] * L[1] + L[2] * L[2]);
   if (ln > 0) for (double& x : L) x /= ln;
@@ -641,7 +644,8 @@ bool same_camera(const mbr_camera& a, const mbr_camera& b) {
   for (int i = 0; i < 3; ++i)
     if (a.light_dir[i] != b.light_dir[i]) return false;
   return a.tan_half_fov == b.tan_half_fov && a.znear == b.znear && a.k_ambient == b.k_ambient &&
-         a.k_diffuse == b.k_diffuse && a.delta == b.delta && a.time_rule == b.time_rule && a.prob == b.prob;
+         a.k_diffuse == b.k_diffuse && a.delta == b.delta && a.time_rule == b.time_rule && a.prob == b.prob &&
+         a.interp == b.interp;
 }
 
 bool matches_last_forward(const mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mbr_camera* cam,

@@ -261,22 +261,25 @@ template <bool MOVING>
 __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const TriRec* recs_set, int slot_a, int slot_b,
                                                 bool has, int f, float tau, float u, float v, float gr, float gg,
                                                 float gb) {
-  // per-vertex contributions: slot a (dx, dy, dnx, dny | dnz), slot b (same), albedo (r, g, b)
+  // per-vertex contributions: slot a (dx, dy, dnx, dny | dnz, dz), slot b (same), albedo (r, g, b)
   float4 ca[3], cb[3], cal[3];
-  float ca_z[3], cb_z[3];
+  float ca_z[3], cb_z[3], ca_dz[3], cb_dz[3];
   int vid[3] = {0, 0, 0};
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     ca[q] = cb[q] = cal[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    ca_z[q] = cb_z[q] = 0.f;
+    ca_z[q] = cb_z[q] = ca_dz[q] = cb_dz[q] = 0.f;
   }
   if (has) {
     float4 r[kRecF4];
-    load_record<MOVING>(recs_set + f, r, false, false);
+    load_record<MOVING>(recs_set + f, r, P.persp != 0, false);
     const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
     const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
     const float invD = 1.0f / e.D;
-    const float w[3] = {e.N0 * invD, e.N1 * invD, e.N2 * invD};
+    const float wb[3] = {e.N0 * invD, e.N1 * invD, e.N2 * invD};  // screen-space barycentrics
+    float w[3], iz[3], z[3] = {1.f, 1.f, 1.f};                     // attribute weights
+    if (P.persp) depths_at<MOVING>(r, tau, z);
+    attribute_weights(P.persp != 0, wb, z, w, iz);
     float al[3][3], nv[3][3];
     float cr = 0.f, cg = 0.f, cbl = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
 #pragma unroll
@@ -332,8 +335,20 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
         }
       }
     }
+    // attribute weights -> screen barycentrics (and vertex depths, perspective-correct weights
+    // a_i = (w_i / z_i) / S: dL/dw_k = (g_k - sum_i g_i a_i) / (z_k S), dL/dz_k = -(w_k / z_k) dL/dw_k)
+    if (P.persp) {
+      const float sa = w[0] * gw[0] + w[1] * gw[1] + w[2] * gw[2];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        gw[q] = (gw[q] - sa) * iz[q];
+        const float gz = -(wb[q] / z[q]) * gw[q];
+        ca_dz[q] = MOVING ? (1.f - tau) * gz : gz;
+        if (MOVING) cb_dz[q] = tau * gz;
+      }
+    }
     // w = N / D -> vertex positions at tau
-    const float sw = w[0] * gw[0] + w[1] * gw[1] + w[2] * gw[2];
+    const float sw = wb[0] * gw[0] + wb[1] * gw[1] + wb[2] * gw[2];
     float ax[3], ay[3], ex[3], ey[3];
     rel_vertices<MOVING>(r, ps, tau, ax, ay);
     edge_backward((gw[0] - sw) * invD, (gw[1] - sw) * invD, (gw[2] - sw) * invD, ax, ay, ex, ey);
@@ -360,7 +375,8 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
   if (uniform) {
     // one butterfly over all contributions; the offsets loop stays rolled to keep the adjoint's
     // code small (the kernel is bound by instruction fetch, not by these few instructions)
-    constexpr int NV = MOVING ? 39 : 24;
+    constexpr int kDzA = MOVING ? 39 : 24, kDzB = 42;  // slot depth gradients
+    constexpr int NV = MOVING ? 45 : 27;
     float x[NV];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -370,7 +386,9 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
       if (MOVING) {
         x[24 + 5 * q] = cb[q].x; x[25 + 5 * q] = cb[q].y; x[26 + 5 * q] = cb[q].z; x[27 + 5 * q] = cb[q].w;
         x[28 + 5 * q] = cb_z[q];
+        x[kDzB + q] = cb_dz[q];
       }
+      x[kDzA + q] = ca_dz[q];
     }
 #pragma unroll 1
     for (int o = 16; o > 0; o >>= 1) {
@@ -385,17 +403,19 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
       if (MOVING) {
         cb[q] = make_float4(x[24 + 5 * q], x[25 + 5 * q], x[26 + 5 * q], x[27 + 5 * q]);
         cb_z[q] = x[28 + 5 * q];
+        cb_dz[q] = x[kDzB + q];
       }
+      ca_dz[q] = x[kDzA + q];
     }
   }
   if (uniform ? lane == leader : has) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       atomicAdd(ga_ + (size_t)vid[q] * 2, ca[q]);
-      atomicAdd(reinterpret_cast<float*>(ga_ + (size_t)vid[q] * 2 + 1), ca_z[q]);
+      atomicAdd(reinterpret_cast<float2*>(ga_ + (size_t)vid[q] * 2 + 1), make_float2(ca_z[q], ca_dz[q]));
       if (MOVING) {
         atomicAdd(gb_ + (size_t)vid[q] * 2, cb[q]);
-        atomicAdd(reinterpret_cast<float*>(gb_ + (size_t)vid[q] * 2 + 1), cb_z[q]);
+        atomicAdd(reinterpret_cast<float2*>(gb_ + (size_t)vid[q] * 2 + 1), make_float2(cb_z[q], cb_dz[q]));
       }
       if (P.g_albedo) atomicAdd(P.g_albedo + vid[q], cal[q]);
     }
@@ -565,8 +585,9 @@ __global__ void slot_chain_kernel(const float* __restrict__ verts, const float* 
   float gvx = 0.f, gvy = 0.f, gvz = 0.f, gnx = 0.f, gny = 0.f, gnz = 0.f;
   for (int s = lane; s < n_slots; s += 32) {
     const float4 ga = g_slot[((size_t)s * V + v) * 2];
-    const float g0 = ga.x, g1 = ga.y, g2 = ga.z, g3 = ga.w, g4 = g_slot[((size_t)s * V + v) * 2 + 1].x;
-    if (g0 == 0.f && g1 == 0.f && g2 == 0.f && g3 == 0.f && g4 == 0.f) continue;
+    const float4 gz4 = g_slot[((size_t)s * V + v) * 2 + 1];
+    const float g0 = ga.x, g1 = ga.y, g2 = ga.z, g3 = ga.w, g4 = gz4.x, g5 = gz4.y;
+    if (g0 == 0.f && g1 == 0.f && g2 == 0.f && g3 == 0.f && g4 == 0.f && g5 == 0.f) continue;
     const float* A = xf[s].A;
     const float* R = xf[s].R;
     const float xc = fmaf(A[0], px, fmaf(A[1], py, fmaf(A[2], pz, A[3])));
@@ -575,7 +596,7 @@ __global__ void slot_chain_kernel(const float* __restrict__ verts, const float* 
     const float den = zc * th;
     // x = xc / (zc th), y = yc / (zc th)
     const float dxc = g0 / den, dyc = g1 / den;
-    const float dzc = -(g0 * xc + g1 * yc) / (den * zc);
+    const float dzc = g5 - (g0 * xc + g1 * yc) / (den * zc);  // camera z: direct (depth) + projection
     gvx += A[0] * dxc + A[4] * dyc + A[8] * dzc;
     gvy += A[1] * dxc + A[5] * dyc + A[9] * dzc;
     gvz += A[2] * dxc + A[6] * dyc + A[10] * dzc;

@@ -508,11 +508,14 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
           if (f >= 0) {
             const float tau = MOVING ? __ldg(gr.tau + i) : 0.f;
             float4 r[kRecF4];
-            load_record<MOVING>(recs_set + f, r, false, false);
+            load_record<MOVING>(recs_set + f, r, P.persp != 0, false);
             const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
             const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
             const float invD = 1.0f / e.D;
-            const float w[3] = {e.N0 * invD, e.N1 * invD, e.N2 * invD};
+            const float wb[3] = {e.N0 * invD, e.N1 * invD, e.N2 * invD};
+            float w[3], iz[3], z[3] = {1.f, 1.f, 1.f};
+            if (P.persp) depths_at<MOVING>(r, tau, z);
+            attribute_weights(P.persp != 0, wb, z, w, iz);
             float cr = 0.f, cg = 0.f, cb = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
 #pragma unroll
             for (int q = 0; q < 3; ++q) {

@@ -51,6 +51,7 @@ struct RasterParams {
   int32_t H, W, tiles_x, tiles_y, n_split;
   float r, r2, inv_delta, delta;
   int32_t prob;              // soft-coverage map: 0 exp(-d/delta), 1 sigmoid(-d/delta)
+  int32_t persp;             // attribute weights: 0 screen-space w (Eq. fore), 1 perspective-correct
   float lx, ly, lz, ka, kd;
   float inv_T;
   float4* out;               // image: stored (n_split == 1) or accumulated with atomics (zeroed first)
@@ -63,7 +64,7 @@ struct RasterParams {
   unsigned long long* counts;  // measurement build only: [soft terms, covered samples]
   // adjoint only
   const float4* dl_dimage;   // [H*W]
-  float4* g_slot;            // [slots][V][2]: (dx, dy, dnx, dny), (dnz, 0, 0, 0) of the slot states
+  float4* g_slot;            // [slots][V][2]: (dx, dy, dnx, dny), (dnz, dz, 0, 0) of the slot states
   float4* g_albedo;          // [V] (dr, dg, db, 0), or null
   // per-sample raster state, written by the forward (when s_stat is set) and read by the adjoint
   float* s_val;              // [T][H][W] covered: winner face id (int bits); else log soft product
@@ -123,6 +124,46 @@ __device__ __forceinline__ bool covers(const EdgeVals& e) {
   const bool pos = e.N0 >= 0.f && e.N1 >= 0.f && e.N2 >= 0.f;
   const bool neg = e.N0 <= 0.f && e.N1 <= 0.f && e.N2 <= 0.f;
   return (pos || neg) && fabsf(e.D) > kDetMin;
+}
+
+// Camera depths of the record's vertices at tau (keyframe lerp for the fast solver).
+template <bool MOVING>
+__device__ __forceinline__ void depths_at(const float4* r, float tau, float z[3]) {
+  z[0] = r[kR_Z].x;
+  z[1] = r[kR_Z].y;
+  z[2] = r[kR_Z].z;
+  if (MOVING) {
+    z[0] = fmaf(tau, r[kR_DZ].x, z[0]);
+    z[1] = fmaf(tau, r[kR_DZ].y, z[1]);
+    z[2] = fmaf(tau, r[kR_DZ].z, z[2]);
+  }
+}
+
+// Attribute weights of a covered sample from its screen-space barycentrics w: w itself (Eq. fore
+// interpolates in screen space), or, with persp, the perspective-correct weights
+// (w_i / z_i) / sum_j (w_j / z_j); iz receives 1 / (z_i sum_j w_j / z_j) for the adjoint.
+__device__ __forceinline__ void attribute_weights(bool persp, const float w[3], const float z[3], float a[3],
+                                                  float iz[3]) {
+  if (!persp) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      a[q] = w[q];
+      iz[q] = 0.f;
+    }
+    return;
+  }
+  float s = 0.f, wz[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    wz[q] = w[q] / z[q];
+    s += wz[q];
+  }
+  const float is = 1.f / s;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    a[q] = wz[q] * is;
+    iz[q] = is / z[q];
+  }
 }
 
 // Perspective-correct inverse depth sum_i w_i / z_i(tau): larger is nearer.

@@ -50,6 +50,7 @@ class Camera:
     delta: float = 1e-4
     time_rule: str = "paper"         # 'paper' | 'midpoint'
     prob: str = "exp"                # soft-coverage map: 'exp' (the paper's) | 'sigmoid' (SoftRas)
+    interp: str = "screen"           # attribute weights: 'screen' (Eq. fore) | 'perspective'
 
     def c(self):
         c = MbrCamera()
@@ -62,6 +63,7 @@ class Camera:
         c.delta = float(self.delta)
         c.time_rule = _lib.MBR_TIME_PAPER if self.time_rule == "paper" else _lib.MBR_TIME_MIDPOINT
         c.prob = {"exp": _lib.MBR_PROB_EXP, "sigmoid": _lib.MBR_PROB_SIGMOID}[self.prob]
+        c.interp = {"screen": _lib.MBR_INTERP_SCREEN, "perspective": _lib.MBR_INTERP_PERSPECTIVE}[self.interp]
         return c
 
 
@@ -74,7 +76,8 @@ def motion_from_dict(m):
 def camera_from_dict(c):
     return Camera(view=tuple(np.asarray(c["view"]).reshape(-1)), tan_half_fov=c["tan_half_fov"], znear=c["znear"],
                   light_dir=tuple(c["light_dir"]), k_ambient=c["k_ambient"], k_diffuse=c["k_diffuse"],
-                  delta=c["delta"], time_rule=c.get("time_rule", "paper"), prob=c.get("prob", "exp"))
+                  delta=c["delta"], time_rule=c.get("time_rule", "paper"), prob=c.get("prob", "exp"),
+                  interp=c.get("interp", "screen"))
 
 
 def mesh_tensors(scene, device="cuda"):

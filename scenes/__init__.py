@@ -278,10 +278,10 @@ def orbit_eye(dist, azimuth_deg, elevation_deg):
     return (dist * math.cos(e) * math.sin(a), dist * math.sin(e), -dist * math.cos(e) * math.cos(a))
 
 
-def camera(view, fov_deg=40.0, time_rule="paper", delta=DELTA, prob="exp"):
+def camera(view, fov_deg=40.0, time_rule="paper", delta=DELTA, prob="exp", interp="screen"):
     return dict(view=np.asarray(view, dtype=np.float64), tan_half_fov=math.tan(math.radians(fov_deg) / 2),
                 znear=ZNEAR, light_dir=np.array(LIGHT_DIR, dtype=np.float64), k_ambient=K_AMBIENT,
-                k_diffuse=K_DIFFUSE, delta=delta, time_rule=time_rule, prob=prob)
+                k_diffuse=K_DIFFUSE, delta=delta, time_rule=time_rule, prob=prob, interp=interp)
 
 
 def translate(d, offset=None, segments=0):

@@ -49,6 +49,10 @@ SCENES = {
     # the SoftRas probability map the paper replaces (sigmoid instead of exp), with a wide delta
     "rotate_sigmoid_prob": lambda: dict(scenes.small_scene("rotate", subdiv=2, T=8, H=40, W=56),
                                         camera=scenes.camera(scenes.look_at((0, 0, -4)), delta=2e-3, prob="sigmoid")),
+    # perspective-correct attribute weights, camera close to the mesh (strong depth variation)
+    "translate_perspective_attrs": lambda: dict(
+        scenes.small_scene("translate", subdiv=2, T=10, H=44, W=60, d=(0.8, -0.2, 1.0)),
+        camera=scenes.camera(scenes.look_at((0.4, 0.3, -2.6)), fov_deg=60.0, interp="perspective")),
 }
 
 

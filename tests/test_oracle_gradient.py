@@ -13,19 +13,21 @@ def _loss(sc, G, mode, **kw):
     return float(np.sum(r["rgba"] * G)), int(r["counters"][oracle.CNT_HASH])
 
 
-def _scene(kind, delta, prob="exp"):
+def _scene(kind, delta, prob="exp", interp="screen"):
     sc = scenes.small_scene(kind, subdiv=1, T=4, H=22, W=26, lmax=3, sigma=0.08, d=(0.9, 0.2, 0.4))
-    sc["camera"] = dict(sc["camera"], delta=delta, prob=prob)
+    sc["camera"] = dict(sc["camera"], delta=delta, prob=prob, interp=interp)
     return sc
 
 
-@pytest.mark.parametrize("mode,kind,delta,prob",
-                         [(m, k, d, "exp") for m in ("exact", "linear", "fast") for k in ("rotate", "translate")
-                          for d in (1e-4, 2e-3)] +
-                         [(m, k, 2e-3, "sigmoid") for m in ("exact", "fast") for k in ("rotate", "translate")])
-def test_adjoint_matches_central_differences(mode, kind, delta, prob):
-    """prob 'sigmoid' is the SoftRas probability map (dA/dd = -A (1 - A) / delta)."""
-    sc = _scene(kind, delta, prob)
+@pytest.mark.parametrize("mode,kind,delta,prob,interp",
+                         [(m, k, d, "exp", "screen") for m in ("exact", "linear", "fast")
+                          for k in ("rotate", "translate") for d in (1e-4, 2e-3)] +
+                         [(m, k, 2e-3, "sigmoid", "screen") for m in ("exact", "fast") for k in ("rotate", "translate")] +
+                         [(m, k, 1e-4, "exp", "perspective") for m in ("exact", "fast") for k in ("rotate", "translate")])
+def test_adjoint_matches_central_differences(mode, kind, delta, prob, interp):
+    """prob 'sigmoid' is the SoftRas probability map (dA/dd = -A (1 - A) / delta); interp
+    'perspective' the perspective-correct attribute weights (gradients also reach the depths)."""
+    sc = _scene(kind, delta, prob, interp)
     rng = np.random.default_rng(17)
     G = rng.normal(size=(sc["H"], sc["W"], 4))
     gv, ga, _ = oracle.render_backward(sc, G, mode)

@@ -354,6 +354,48 @@ def test_static_quad_soft_alpha_closed_form(prob):
         assert np.all(expect[~inside] < 0.75 + 1e-12)
 
 
+def test_perspective_correct_attributes_are_affine_in_world_space():
+    """A static triangle tilted in depth, albedo an affine function of world position: with
+    perspective-correct weights every covered pixel shows shade x (alpha . P + beta) at the 3D
+    point P where the pixel's ray meets the triangle's plane, the defining property of
+    perspective-correct interpolation; screen-space weights (Eq. fore) miss it."""
+    tri = np.array([[-1.3, -1.0, -0.9], [1.4, -0.8, 1.1], [0.1, 1.3, 0.3]])
+    alpha = np.array([[0.20, -0.10, 0.15], [0.05, 0.12, -0.08], [-0.11, 0.04, 0.10]])
+    beta = np.array([0.5, 0.45, 0.55])
+    alb = tri @ alpha.T + beta
+    view = scenes.look_at((0.0, 0.0, -4.0))
+    sc = scenes.scene(tri, np.array([[0, 1, 2]], dtype=np.int32), alb,
+                      scenes.translate((0.0, 0.0, 0.0), offset=(0.0, 0.0, 0.0)),
+                      scenes.camera(view, interp="perspective"), 1, 36, 44)
+    out = oracle.render(sc, "exact", ambig=True)
+    rgba, amb = out["rgba"], out["ambig"][0]
+    R, tvec = view[:, :3], view[:, 3]
+    th = sc["camera"]["tan_half_fov"]
+    cam = tri @ R.T + tvec                      # camera-space vertices
+    nrm = np.cross(cam[1] - cam[0], cam[2] - cam[0])
+    n_world = np.cross(tri[1] - tri[0], tri[2] - tri[0])
+    n_world /= np.linalg.norm(n_world)
+    L = np.asarray(scenes.LIGHT_DIR) / np.linalg.norm(scenes.LIGHT_DIR)
+    shade = scenes.K_AMBIENT + scenes.K_DIFFUSE * max(0.0, float(n_world @ L))
+    H, W = sc["H"], sc["W"]
+    checked, worst_screen = 0, 0.0
+    screen = oracle.render(dict(sc, camera=dict(sc["camera"], interp="screen")), "exact")["rgba"]
+    for j in range(H):
+        for i in range(W):
+            if rgba[j, i, 3] < 1.0 or amb[j, i]:
+                continue  # not covered, or within rounding of an edge
+            u, v = 2 * (i + 0.5) / W - 1, 1 - 2 * (j + 0.5) / H
+            ray = np.array([u * th, v * th, 1.0])
+            s_hit = (nrm @ cam[0]) / (nrm @ ray)
+            P = R.T @ (s_hit * ray - tvec)        # back to world space
+            expect = shade * (alpha @ P + beta)
+            assert np.max(np.abs(rgba[j, i, :3] - expect)) < 1e-12, (i, j)
+            worst_screen = max(worst_screen, float(np.max(np.abs(screen[j, i, :3] - expect))))
+            checked += 1
+    assert checked > 200
+    assert worst_screen > 1e-3  # the screen-space weights are not perspective-correct here
+
+
 def test_rotation_relabel_invariance_midpoint_rule():
     """With t_k = (k + 0.5)/T, omega = 2 pi and T a multiple of n, pre-rotating the mesh by 2 pi/n
     about the motion axis permutes the sub-frames and leaves the blurred image unchanged."""
