@@ -64,12 +64,19 @@ extern "C" {
 
 typedef struct mbr_ctx mbr_ctx;
 
-/* Triangle mesh (device pointers). */
+/* Triangle mesh (device pointers).  The vertex attribute c_i of Eq. fore is the per-vertex
+ * colour, or, when texture is set, a texture coordinate: the colour of a covered sample is then
+ * the texture sampled bilinearly (clamp to edge, texel centres at (k + 0.5) / size) at the
+ * interpolated (u, v); u runs along the texture's width, v along its rows. */
 typedef struct {
   int32_t V, F;
-  const float* verts;   /* [V,3] base vertex positions, world units                    */
-  const int32_t* faces; /* [F,3] vertex indices in [0, V)                               */
-  const float* albedo;  /* [V,3] per-vertex colour (the c_i of Eq. fore)                */
+  const float* verts;    /* [V,3] base vertex positions, world units                    */
+  const int32_t* faces;  /* [F,3] vertex indices in [0, V)                               */
+  const float* albedo;   /* [V,3] per-vertex colour (unused when textured)              */
+  const float* uv;       /* [V,2] texture coordinates (required when textured), or null */
+  const float* texture;  /* [tex_h, tex_w, 3] RGB texels, or null (per-vertex colour)   */
+  int32_t tex_h, tex_w;
+  float* dl_dtexture;    /* adjoint only: [tex_h, tex_w, 3] texel gradients, overwritten; or null */
 } mbr_mesh;
 
 /* Rigid motion over the exposure, t in [0, 1] (Sec. "Motion Parameters"). */

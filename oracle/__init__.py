@@ -25,6 +25,7 @@ MODES = {"exact": 0, "linear": 1, "fast": 2}
 SOFT_ALL = 1
 CNT_CAND, CNT_COVERED, CNT_AMBIG, CNT_HASH, CNT_SOFT, CNT_SOFT32 = 0, 1, 2, 3, 4, 5
 AMB_COVER, AMB_DEPTH, AMB_DEGEN, AMB_REGION, AMB_CLAMP, AMB_LAMBERT, AMB_COND = 1, 2, 4, 8, 16, 32, 64
+AMB_TEXCELL = 128  # gradient only: a textured sample near a texel-centre line (the bilinear slope jumps)
 AMB_IMAGE = AMB_COVER | AMB_DEPTH | AMB_DEGEN | AMB_REGION  # flags that can change a pixel value
 
 
@@ -32,6 +33,8 @@ class OrcScene(ctypes.Structure):
     _fields_ = [
         ("V", c_int32), ("F", c_int32),
         ("verts", POINTER(c_double)), ("faces", POINTER(c_int32)), ("albedo", POINTER(c_double)),
+        ("uv", POINTER(c_double)), ("texture", POINTER(c_double)), ("tex_h", c_int32), ("tex_w", c_int32),
+        ("dl_dtexture", POINTER(c_double)),
         ("motion_kind", c_int32), ("segments", c_int32),
         ("offset", c_double * 3), ("dir", c_double * 3), ("axis", c_double * 3), ("omega", c_double),
         ("acc", c_double * 3),
@@ -83,11 +86,20 @@ class _Scene:
         self.verts = np.ascontiguousarray(sc["verts"], dtype=np.float64)
         self.faces = np.ascontiguousarray(sc["faces"], dtype=np.int32)
         self.albedo = np.ascontiguousarray(sc["albedo"], dtype=np.float64)
+        tex = sc.get("texture")
+        self.uv = np.ascontiguousarray(sc["uv"], dtype=np.float64) if tex is not None else None
+        self.texture = np.ascontiguousarray(tex, dtype=np.float64) if tex is not None else None
+        self.gtex = np.zeros_like(self.texture) if tex is not None else None
         m, c = sc["motion"], sc["camera"]
         s = OrcScene()
         s.V, s.F = len(self.verts), len(self.faces)
         s.verts = _ptr(self.verts, c_double)
         s.faces = _ptr(self.faces, c_int32)
+        if tex is not None:
+            s.uv = _ptr(self.uv, c_double)
+            s.texture = _ptr(self.texture, c_double)
+            s.tex_h, s.tex_w = self.texture.shape[0], self.texture.shape[1]
+            s.dl_dtexture = _ptr(self.gtex, c_double)
         s.albedo = _ptr(self.albedo, c_double)
         s.motion_kind = {"translate": 0, "rotate": 1, "parabolic": 2}[m["kind"]]
         s.segments = int(m.get("segments", 0))
@@ -176,8 +188,10 @@ def render(sc, mode="fast", window=None, soft_all=False, winners=False, ambig=Fa
     return dict(rgba=rgba, winners=win, ambig=amb, counters=cnt)
 
 
-def render_backward(sc, dl_drgba, mode="fast", window=None, soft_all=False):
-    """(dL/dverts [V,3], dL/dalbedo [V,3], counters) for the loss gradient ``dl_drgba`` [h,w,4]."""
+def render_backward(sc, dl_drgba, mode="fast", window=None, soft_all=False, texture_grad=None):
+    """(dL/dverts [V,3], dL/dalbedo [V,3], counters) for the loss gradient ``dl_drgba`` [h,w,4].
+    For a textured scene, ``texture_grad`` (an array shaped like the texture) receives
+    dL/dtexture."""
     S = _Scene(sc)
     x0, y0, w, h = window if window is not None else (0, 0, S.s.W, S.s.H)
     g = np.ascontiguousarray(dl_drgba, dtype=np.float64).reshape(h, w, 4)
@@ -189,4 +203,6 @@ def render_backward(sc, dl_drgba, mode="fast", window=None, soft_all=False):
                                    _ptr(cnt, c_int64))
     if rc != 0:
         raise RuntimeError(f"orc_render_backward failed ({rc})")
+    if texture_grad is not None:
+        texture_grad[...] = S.gtex
     return gv, ga, cnt

@@ -33,7 +33,8 @@
 #define ETA_DET 1e-5       /* ambiguity: |det F| <= D_MIN + ETA_DET * (longest edge)^2          */
 #define ETA_REGION 1e-6    /* ambiguity: fast-mode closest-edge tie (relative)                   */
 
-enum { AMB_COVER = 1, AMB_DEPTH = 2, AMB_DEGEN = 4, AMB_REGION = 8, AMB_CLAMP = 16, AMB_LAMBERT = 32, AMB_COND = 64 };
+enum { AMB_COVER = 1, AMB_DEPTH = 2, AMB_DEGEN = 4, AMB_REGION = 8, AMB_CLAMP = 16, AMB_LAMBERT = 32, AMB_COND = 64,
+       AMB_TEXCELL = 128 };
 /* gradient-only flag: single-precision conditioning.  The FP32 relative error of a gradient term
  * that passes through w = F^-1 p grows like eps32 (Lmax^2 / |det F|) max(1, |w|); flag when that
  * estimate exceeds 1e-4 (a tenth of the gradient tolerance). */
@@ -42,6 +43,7 @@ enum { AMB_COVER = 1, AMB_DEPTH = 2, AMB_DEGEN = 4, AMB_REGION = 8, AMB_CLAMP = 
 #define SOFT32_MIN 2.98023223876953125e-8  /* 2^-25: 1 - A rounds to 1 in single precision below */
 #define ETA_CLAMP 1e-5     /* gradient-only flag: closest-feature switch within this relative d^2 */
 #define ETA_LAMBERT 1e-5   /* gradient-only flag: |n.l| below this (Lambert clamp switches)     */
+#define ETA_TEXCELL 2e-4   /* gradient-only flag: texel-space coordinate this near a texel centre line */
 
 /* ------------------------------------------------------------------ small helpers */
 
@@ -104,6 +106,35 @@ void orc_sample_time(const orc_scene* s, int32_t k, int32_t* seg, double* t, dou
 }
 
 /* keyframe X of Eq. euc-dist-approx-2: 0 if tau <= 0.5 else 1, decided on the exact fraction */
+/* Bilinear texture sample at (u, v) (clamp to edge; texel centres at (k + 0.5) / size; u along
+ * the width, v along the rows): colour c[3], the four taps (texel index, weight), dc/du and
+ * dc/dv (zero across a clamped border), and the cell (x0, y0) for the decision hash. */
+typedef struct { int64_t idx[4]; double wt[4]; int64_t cell; double edge; } tex_taps;  /* edge: distance of
+  the texel-space coordinates to the nearest texel-centre line, where the bilinear slope jumps */
+
+static void tex_sample(const orc_scene* s, double u, double v, double c[3], double dcdu[3], double dcdv[3],
+                       tex_taps* t) {
+  const int32_t w = s->tex_w, h = s->tex_h;
+  double X = u * w - 0.5, Y = v * h - 0.5;
+  X = fmin(fmax(X, -1.0), (double)w);
+  Y = fmin(fmax(Y, -1.0), (double)h);
+  const double x0f = floor(X), y0f = floor(Y), fx = X - x0f, fy = Y - y0f;
+  const int64_t x0 = (int64_t)x0f, y0 = (int64_t)y0f;
+  const int64_t xa = x0 < 0 ? 0 : (x0 > w - 1 ? w - 1 : x0), xb = x0 + 1 < 0 ? 0 : (x0 + 1 > w - 1 ? w - 1 : x0 + 1);
+  const int64_t ya = y0 < 0 ? 0 : (y0 > h - 1 ? h - 1 : y0), yb = y0 + 1 < 0 ? 0 : (y0 + 1 > h - 1 ? h - 1 : y0 + 1);
+  t->idx[0] = ya * w + xa; t->idx[1] = ya * w + xb; t->idx[2] = yb * w + xa; t->idx[3] = yb * w + xb;
+  t->wt[0] = (1 - fx) * (1 - fy); t->wt[1] = fx * (1 - fy); t->wt[2] = (1 - fx) * fy; t->wt[3] = fx * fy;
+  t->cell = (x0 + 2) * 100003 + (y0 + 2);
+  t->edge = fmin(fabs(X - nearbyint(X)), fabs(Y - nearbyint(Y)));
+  for (int k = 0; k < 3; ++k) {
+    const double t00 = s->texture[3 * t->idx[0] + k], t10 = s->texture[3 * t->idx[1] + k];
+    const double t01 = s->texture[3 * t->idx[2] + k], t11 = s->texture[3 * t->idx[3] + k];
+    c[k] = t->wt[0] * t00 + t->wt[1] * t10 + t->wt[2] * t01 + t->wt[3] * t11;
+    dcdu[k] = w * ((1 - fy) * (t10 - t00) + fy * (t11 - t01));
+    dcdv[k] = h * ((1 - fx) * (t01 - t00) + fx * (t11 - t10));
+  }
+}
+
 /* soft-coverage probability A (Eq. probability-function) of squared distance d, its factor
  * 1 - A (computed without cancellation) and dA/dd */
 static double soft_prob(const orc_scene* s, double d, double* one_minus, double* dA_dd) {
@@ -400,7 +431,8 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
                        int32_t w, int32_t h, double* rgba, int32_t* winners, uint8_t* ambig,
                        int64_t* cnt, const double* dl, double* gverts, double* galb) {
   if (!s || s->V <= 0 || s->F < 0 || s->T <= 0 || s->H <= 0 || s->W <= 0 || w < 0 || h < 0 ||
-      x0 < 0 || y0 < 0 || x0 + w > s->W || y0 + h > s->H || mode < 0 || mode > 2)
+      x0 < 0 || y0 < 0 || x0 + w > s->W || y0 + h > s->H || mode < 0 || mode > 2 ||
+      (s->texture && (!s->uv || s->tex_h < 1 || s->tex_w < 1)))
     return -1;
   const int32_t V = s->V, F = s->F, T = s->T, S = orc_num_segments(s);
   const size_t npix = (size_t)w * (size_t)h;
@@ -628,7 +660,6 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
       if (f < 0) amb[p] |= samb[p];
       if (amb[p]) ++n_amb;
       if (winners) winners[(size_t)k * npix + p] = f;
-      if (ambig) ambig[(size_t)k * npix + p] = amb[p];
       hash = fnv(hash, (int64_t)k * 1000003 + (int64_t)p * 31 + f);
       if (f < 0) n_soft32 += nsoft32[p];
       if (f >= 0) {
@@ -648,9 +679,21 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
         double col[3] = {0, 0, 0}, nn[3] = {0, 0, 0};
         for (int q = 0; q < 3; ++q)
           for (int c = 0; c < 3; ++c) {
-            col[c] += aw[q] * s->albedo[3 * id[q] + c];
+            if (!s->texture) col[c] += aw[q] * s->albedo[3 * id[q] + c];
             nn[c] += aw[q] * cur[6 * id[q] + 3 + c];
           }
+        /* textured: the vertex attribute is uv_i (Eq. fore) and the colour its texture sample */
+        double tuv[2] = {0, 0}, dcdu[3] = {0, 0, 0}, dcdv[3] = {0, 0, 0};
+        tex_taps taps;
+        if (s->texture) {
+          for (int q = 0; q < 3; ++q) {
+            tuv[0] += aw[q] * s->uv[2 * id[q]];
+            tuv[1] += aw[q] * s->uv[2 * id[q] + 1];
+          }
+          tex_sample(s, tuv[0], tuv[1], col, dcdu, dcdv, &taps);
+          hash = fnv(hash, taps.cell);
+          if (taps.edge < ETA_TEXCELL * fmax(1.0, fmax(s->tex_w, s->tex_h) / 64.0)) amb[p] |= AMB_TEXCELL;
+        }
         double len = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
         double dot = len > 0 ? (nn[0] * Ld[0] + nn[1] * Ld[1] + nn[2] * Ld[2]) / len : 0.0;
         double shade = s->k_ambient + s->k_diffuse * (dot > 0 ? dot : 0.0);
@@ -667,11 +710,24 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
             gcol[c] = G[c] / T * shade;
             gshade += G[c] / T * col[c];
           }
-          for (int q = 0; q < 3; ++q)
+          if (s->texture) {
+            /* c = texture(sum_q aw_q uv_q): dL/daw_q = uv_q . (dL/du, dL/dv); texels by the taps */
+            double gu = 0, gv = 0;
             for (int c = 0; c < 3; ++c) {
-              if (galb) galb[3 * id[q] + c] += aw[q] * gcol[c];
-              gw[q] += s->albedo[3 * id[q] + c] * gcol[c];
+              gu += dcdu[c] * gcol[c];
+              gv += dcdv[c] * gcol[c];
             }
+            for (int q = 0; q < 3; ++q) gw[q] += s->uv[2 * id[q]] * gu + s->uv[2 * id[q] + 1] * gv;
+            if (s->dl_dtexture)
+              for (int k = 0; k < 4; ++k)
+                for (int c = 0; c < 3; ++c) s->dl_dtexture[3 * taps.idx[k] + c] += taps.wt[k] * gcol[c];
+          } else {
+            for (int q = 0; q < 3; ++q)
+              for (int c = 0; c < 3; ++c) {
+                if (galb) galb[3 * id[q] + c] += aw[q] * gcol[c];
+                gw[q] += s->albedo[3 * id[q] + c] * gcol[c];
+              }
+          }
           if (len > 0 && dot > 0) {
             double nh[3] = {nn[0] / len, nn[1] / len, nn[2] / len};
             double gnh[3] = {s->k_diffuse * gshade * Ld[0], s->k_diffuse * gshade * Ld[1],
@@ -707,6 +763,7 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
       } else if (rgba) {
         rgba[4 * p + 3] += 1.0 - prod[p];
       }
+      if (ambig) ambig[(size_t)k * npix + p] = amb[p];  /* after shading: Lambert, texel-cell flags */
     }
 
     /* ---- soft-coverage adjoint for uncovered samples: exclusive products per pixel */

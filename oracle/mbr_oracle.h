@@ -27,7 +27,15 @@ typedef struct {
   int32_t V, F;
   const double* verts;    /* [V,3] base vertex positions (world)                         */
   const int32_t* faces;   /* [F,3] vertex indices                                          */
-  const double* albedo;   /* [V,3] per-vertex colour                                       */
+  const double* albedo;   /* [V,3] per-vertex colour (unused when textured)               */
+  const double* uv;       /* [V,2] texture coordinates, or NULL                            */
+  const double* texture;  /* [tex_h, tex_w, 3] RGB texels, or NULL: when set, the vertex
+                             attribute c_i of Eq. fore is uv_i and the sample colour is the
+                             texture sampled bilinearly (clamp to edge, texel centres at
+                             (k + 0.5) / size, u along the width, v along the rows)         */
+  int32_t tex_h, tex_w;
+  double* dl_dtexture;    /* orc_render_backward: [tex_h, tex_w, 3] texel gradients
+                             (accumulated; the caller zeroes it), or NULL                   */
   int32_t motion_kind;    /* 0: P(t) = v + offset + t*dir ; 1: P(t) = R(omega*t, axis) v ;
                              2: P(t) = R(omega*t, axis) v + offset + t*dir + t^2*acc (the
                              rotation plus parabolic translation of the appendix's parabolic
@@ -86,7 +94,9 @@ double orc_closest_point(const double tri[6], double px, double py, double w[3],
  *                      change a pixel); 16 fast-mode closest-feature switch (edge interior vs
  *                      vertex, or a near tie), 32 Lambert clamp, 64 single-precision
  *                      conditioning eps32 Lmax^2/|det F| max(1,|w|) > 1e-4 of a term through
- *                      w = F^-1 p (these three only change gradients); may be NULL
+ *                      w = F^-1 p, 128 a textured sample within 2e-4 texels of a texel-centre
+ *                      line (where the bilinear slope jumps) (these four only change
+ *                      gradients); may be NULL
  *   counters [ORC_CNT_N]
  * returns 0, or -1 on bad arguments / allocation failure. */
 int32_t orc_render(const orc_scene* s, int32_t mode, int32_t flags, int32_t x0, int32_t y0,

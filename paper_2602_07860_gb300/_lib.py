@@ -24,7 +24,9 @@ EXPORTS = ["mbr_create", "mbr_destroy", "mbr_render_blur", "mbr_render_blur_back
 
 
 class MbrMesh(ctypes.Structure):
-    _fields_ = [("V", c_int32), ("F", c_int32), ("verts", c_void_p), ("faces", c_void_p), ("albedo", c_void_p)]
+    _fields_ = [("V", c_int32), ("F", c_int32), ("verts", c_void_p), ("faces", c_void_p), ("albedo", c_void_p),
+                ("uv", c_void_p), ("texture", c_void_p), ("tex_h", c_int32), ("tex_w", c_int32),
+                ("dl_dtexture", c_void_p)]
 
 
 class MbrMotion(ctypes.Structure):

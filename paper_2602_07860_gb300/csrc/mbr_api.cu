@@ -196,6 +196,8 @@ int validate(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const m
   if (mesh->V < 1 || mesh->F < 0) return fail(c, MBR_ERR_ARG, "bad mesh sizes V=%d F=%d", mesh->V, mesh->F);
   if (!mesh->verts || !mesh->albedo || (mesh->F > 0 && !mesh->faces))
     return fail(c, MBR_ERR_ARG, "null mesh buffer");
+  if (mesh->texture && (!mesh->uv || mesh->tex_h < 1 || mesh->tex_w < 1 || mesh->tex_h > 65536 || mesh->tex_w > 65536))
+    return fail(c, MBR_ERR_ARG, "a texture needs uv coordinates and a size in [1, 65536]");
   if (T < 1 || T > (1 << 20)) return fail(c, MBR_ERR_ARG, "bad T=%d", T);
   if (H < 1 || W < 1 || H > 16384 || W > 16384) return fail(c, MBR_ERR_ARG, "bad image size %dx%d", H, W);
   if (solver != MBR_PLAIN && solver != MBR_FAST) return fail(c, MBR_ERR_ARG, "bad solver %d", solver);
@@ -506,6 +508,12 @@ RasterParams raster_params(const mbr_ctx* c, const RasterBufs& b, const mbr_mesh
   P.slot_nrm = (const float4*)b.nrm;
   P.faces = mesh->faces;
   P.albedo = mesh->albedo;
+  if (mesh->texture) {
+    P.uv = mesh->uv;
+    P.tex = mesh->texture;
+    P.tex_w = mesh->tex_w;
+    P.tex_h = mesh->tex_h;
+  }
   P.F = mesh->F;
   P.V = mesh->V;
   P.G = pp.G;
@@ -652,7 +660,9 @@ bool matches_last_forward(const mbr_ctx* c, const mbr_mesh* mesh, const mbr_moti
                           int T, int H, int W, int solver) {
   const LastForward& L = c->last;
   return L.valid && c->last_pp && L.mesh.V == mesh->V && L.mesh.F == mesh->F && L.mesh.verts == mesh->verts &&
-         L.mesh.faces == mesh->faces && L.mesh.albedo == mesh->albedo && same_motion(L.motion, *motion) &&
+         L.mesh.faces == mesh->faces && L.mesh.albedo == mesh->albedo && L.mesh.uv == mesh->uv &&
+         L.mesh.texture == mesh->texture && L.mesh.tex_h == mesh->tex_h && L.mesh.tex_w == mesh->tex_w &&
+         same_motion(L.motion, *motion) &&
          same_camera(L.cam, *cam) && L.T == T && L.H == H && L.W == W && L.solver == solver && L.tile == c->tile &&
          L.spt == c->spt && L.splits == c->splits;
 }
@@ -688,6 +698,10 @@ int backward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, co
   P.dl_dimage = (const float4*)dl_dimage;
   P.g_slot = (float4*)c->gslot.p;
   P.g_albedo = dl_dalbedo ? (float4*)c->galb.p : nullptr;
+  if (mesh->texture && mesh->dl_dtexture) {
+    CUDA_TRY(c, cudaMemsetAsync(mesh->dl_dtexture, 0, sizeof(float) * 3 * (size_t)mesh->tex_h * mesh->tex_w, st));
+    P.g_tex = mesh->dl_dtexture;
+  }
   // the forward raster's per-sample state, and the units in the order of its measured cost
   const size_t ns = (size_t)T * H * W;
   P.s_val = (float*)c->bstate.p;
@@ -1038,7 +1052,8 @@ std::vector<long long> batch_signature(mbr_ctx* c, int n, const mbr_item* items,
                               (long long)(uintptr_t)it.mesh.verts, (long long)(uintptr_t)it.mesh.faces,
                               (long long)(uintptr_t)it.mesh.albedo, (long long)(uintptr_t)it.image,
                               (long long)(uintptr_t)it.dl_dimage, (long long)(uintptr_t)it.dl_dverts,
-                              (long long)(uintptr_t)it.dl_dalbedo};
+                              (long long)(uintptr_t)it.dl_dalbedo, (long long)(uintptr_t)it.mesh.dl_dtexture,
+                              (long long)(uintptr_t)it.mesh.texture, it.mesh.tex_h, it.mesh.tex_w};
     s.insert(s.end(), std::begin(vals), std::end(vals));
   }
   return s;
@@ -1091,6 +1106,7 @@ void batch_write_params(mbr_ctx* c, const mbr_item* items, BatchState& B) {
       P.dl_dimage = (const float4*)it.dl_dimage;
       P.g_slot = (float4*)(A + I.o_gslot);
       P.g_albedo = it.dl_dalbedo ? (float4*)(A + I.o_galb) : nullptr;
+      if (it.mesh.texture) P.g_tex = it.mesh.dl_dtexture;
       P.s_val = (float*)(A + I.o_bstate);
       P.s_stat = (uint8_t*)(A + I.o_bstate) + (size_t)it.T * it.H * it.W * 4;
       P.unit_cost = pp.d_cost;
@@ -1258,6 +1274,9 @@ int batch_enqueue(mbr_ctx* c, const mbr_item* items, BatchState& B, cudaStream_t
     if (B.with_backward) {
       CUDA_TRY(c, cudaMemsetAsync(A + I.o_gslot, 0, sizeof(float4) * 2 * (size_t)it.mesh.V * pp.n_slots, st));
       if (it.dl_dalbedo) CUDA_TRY(c, cudaMemsetAsync(A + I.o_galb, 0, sizeof(float4) * it.mesh.V, st));
+      if (it.mesh.texture && it.mesh.dl_dtexture)
+        CUDA_TRY(c, cudaMemsetAsync(it.mesh.dl_dtexture, 0, sizeof(float) * 3 * (size_t)it.mesh.tex_h * it.mesh.tex_w,
+                                    st));
     }
   }
   CUDA_TRY(c, cudaGetLastError());

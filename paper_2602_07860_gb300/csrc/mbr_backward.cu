@@ -280,14 +280,21 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
     float w[3], iz[3], z[3] = {1.f, 1.f, 1.f};                     // attribute weights
     if (P.persp) depths_at<MOVING>(r, tau, z);
     attribute_weights(P.persp != 0, wb, z, w, iz);
+    const bool textured = P.tex != nullptr;  // vertex attribute: a texture coordinate (Eq. fore)
     float al[3][3], nv[3][3];
     float cr = 0.f, cg = 0.f, cbl = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       vid[q] = __ldg(P.faces + 3 * f + q);
-      al[q][0] = __ldg(P.albedo + 3 * vid[q]);
-      al[q][1] = __ldg(P.albedo + 3 * vid[q] + 1);
-      al[q][2] = __ldg(P.albedo + 3 * vid[q] + 2);
+      if (textured) {
+        al[q][0] = __ldg(P.uv + 2 * vid[q]);
+        al[q][1] = __ldg(P.uv + 2 * vid[q] + 1);
+        al[q][2] = 0.f;
+      } else {
+        al[q][0] = __ldg(P.albedo + 3 * vid[q]);
+        al[q][1] = __ldg(P.albedo + 3 * vid[q] + 1);
+        al[q][2] = __ldg(P.albedo + 3 * vid[q] + 2);
+      }
       float4 na = __ldg(P.slot_nrm + (size_t)slot_a * P.V + vid[q]);
       if (MOVING) {
         const float4 nb = __ldg(P.slot_nrm + (size_t)slot_b * P.V + vid[q]);
@@ -303,6 +310,15 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
       ny = fmaf(w[q], na.y, ny);
       nz = fmaf(w[q], na.z, nz);
     }
+    float du[3] = {0.f, 0.f, 0.f}, dv[3] = {0.f, 0.f, 0.f};
+    TexTap tap;
+    if (textured) {  // cr.. held the interpolated (u, v)
+      float c[3];
+      tap = tex_lookup(P.tex, P.tex_w, P.tex_h, cr, cg, c, du, dv);
+      cr = c[0];
+      cg = c[1];
+      cbl = c[2];
+    }
     const float len = sqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
     const float dot = len > 0.f ? fmaf(nx, P.lx, fmaf(ny, P.ly, nz * P.lz)) / len : 0.f;
     const float shade = fmaf(P.kd, fmaxf(dot, 0.f), P.ka);
@@ -310,10 +326,28 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
     const float gcr = gr * shade, gcg = gg * shade, gcb = gb * shade;
     const float gshade = gr * cr + gg * cg + gb * cbl;
     float gw[3];
+    if (textured) {
+      // c = texture(sum_q w_q uv_q): dL/dw_q = uv_q . (dL/du, dL/dv); texel gradients by the taps
+      const float gu = du[0] * gcr + du[1] * gcg + du[2] * gcb, gv = dv[0] * gcr + dv[1] * gcg + dv[2] * gcb;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      gw[q] = al[q][0] * gcr + al[q][1] * gcg + al[q][2] * gcb;
-      cal[q] = make_float4(w[q] * gcr, w[q] * gcg, w[q] * gcb, 0.f);
+      for (int q = 0; q < 3; ++q) {
+        gw[q] = al[q][0] * gu + al[q][1] * gv;
+        cal[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      if (P.g_tex) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          atomicAdd(P.g_tex + 3 * tap.idx[k], tap.wt[k] * gcr);
+          atomicAdd(P.g_tex + 3 * tap.idx[k] + 1, tap.wt[k] * gcg);
+          atomicAdd(P.g_tex + 3 * tap.idx[k] + 2, tap.wt[k] * gcb);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        gw[q] = al[q][0] * gcr + al[q][1] * gcg + al[q][2] * gcb;
+        cal[q] = make_float4(w[q] * gcr, w[q] * gcg, w[q] * gcb, 0.f);
+      }
     }
     if (len > 0.f && dot > 0.f) {
       const float il = 1.f / len;
@@ -417,7 +451,7 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
         atomicAdd(gb_ + (size_t)vid[q] * 2, cb[q]);
         atomicAdd(reinterpret_cast<float2*>(gb_ + (size_t)vid[q] * 2 + 1), make_float2(cb_z[q], cb_dz[q]));
       }
-      if (P.g_albedo) atomicAdd(P.g_albedo + vid[q], cal[q]);
+      if (P.g_albedo && !P.tex) atomicAdd(P.g_albedo + vid[q], cal[q]);
     }
   }
 }

@@ -516,13 +516,19 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
             float w[3], iz[3], z[3] = {1.f, 1.f, 1.f};
             if (P.persp) depths_at<MOVING>(r, tau, z);
             attribute_weights(P.persp != 0, wb, z, w, iz);
-            float cr = 0.f, cg = 0.f, cb = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
+            float cr = 0.f, cg = 0.f, cb = 0.f, nx = 0.f, ny = 0.f, nz = 0.f, tu = 0.f, tv = 0.f;
+            const bool textured = P.tex != nullptr;
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
               const int vid = __ldg(P.faces + 3 * f + q);
-              cr = fmaf(w[q], __ldg(P.albedo + 3 * vid), cr);
-              cg = fmaf(w[q], __ldg(P.albedo + 3 * vid + 1), cg);
-              cb = fmaf(w[q], __ldg(P.albedo + 3 * vid + 2), cb);
+              if (textured) {  // the vertex attribute is a texture coordinate (Eq. fore)
+                tu = fmaf(w[q], __ldg(P.uv + 2 * vid), tu);
+                tv = fmaf(w[q], __ldg(P.uv + 2 * vid + 1), tv);
+              } else {
+                cr = fmaf(w[q], __ldg(P.albedo + 3 * vid), cr);
+                cg = fmaf(w[q], __ldg(P.albedo + 3 * vid + 1), cg);
+                cb = fmaf(w[q], __ldg(P.albedo + 3 * vid + 2), cb);
+              }
               float4 na = __ldg(P.slot_nrm + (size_t)gr.slot_a * P.V + vid);
               if (MOVING) {
                 const float4 nb = __ldg(P.slot_nrm + (size_t)gr.slot_b * P.V + vid);
@@ -533,6 +539,13 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
               nx = fmaf(w[q], na.x, nx);
               ny = fmaf(w[q], na.y, ny);
               nz = fmaf(w[q], na.z, nz);
+            }
+            if (textured) {
+              float c[3], du[3], dv[3];
+              tex_lookup(P.tex, P.tex_w, P.tex_h, tu, tv, c, du, dv);
+              cr = c[0];
+              cg = c[1];
+              cb = c[2];
             }
             const float len = sqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
             const float dot = len > 0.f ? fmaf(nx, P.lx, fmaf(ny, P.ly, nz * P.lz)) / len : 0.f;

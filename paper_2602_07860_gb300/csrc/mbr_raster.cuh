@@ -47,6 +47,10 @@ struct RasterParams {
   const float4* slot_nrm;    // [slots][V]
   const int32_t* faces;      // [F,3]
   const float* albedo;       // [V,3]
+  const float* uv;           // [V,2] texture coordinates, or null (textured when uv and tex are set)
+  const float* tex;          // [tex_h][tex_w][3] RGB texels, or null
+  int32_t tex_w, tex_h;
+  float* g_tex;              // adjoint: [tex_h][tex_w][3] texel gradients (zeroed), or null
   int32_t F, V, G;
   int32_t H, W, tiles_x, tiles_y, n_split;
   float r, r2, inv_delta, delta;
@@ -124,6 +128,42 @@ __device__ __forceinline__ bool covers(const EdgeVals& e) {
   const bool pos = e.N0 >= 0.f && e.N1 >= 0.f && e.N2 >= 0.f;
   const bool neg = e.N0 <= 0.f && e.N1 <= 0.f && e.N2 <= 0.f;
   return (pos || neg) && fabsf(e.D) > kDetMin;
+}
+
+// Bilinear texture lookup at (u, v) in [0, 1]^2 (u along the width, v along the rows; texel
+// centres at (k + 0.5) / size; clamp-to-edge addressing).  Returns the colour, the four taps and
+// their weights, and dc/du, dc/dv for the adjoint (zero across a clamped border).
+struct TexTap {
+  int idx[4];   // texel indices (x + y w): (x0, y0), (x1, y0), (x0, y1), (x1, y1)
+  float wt[4];  // bilinear weights
+};
+
+__device__ __forceinline__ TexTap tex_lookup(const float* __restrict__ tex, int w, int h, float u, float v,
+                                             float c[3], float dcdu[3], float dcdv[3]) {
+  const float X = fminf(fmaxf(u * w - 0.5f, -1.f), (float)w), Y = fminf(fmaxf(v * h - 0.5f, -1.f), (float)h);
+  const float x0f = floorf(X), y0f = floorf(Y);
+  const float fx = X - x0f, fy = Y - y0f;
+  const int x0 = (int)x0f, y0 = (int)y0f;
+  const int xa = min(max(x0, 0), w - 1), xb = min(max(x0 + 1, 0), w - 1);
+  const int ya = min(max(y0, 0), h - 1), yb = min(max(y0 + 1, 0), h - 1);
+  TexTap t;
+  t.idx[0] = ya * w + xa;
+  t.idx[1] = ya * w + xb;
+  t.idx[2] = yb * w + xa;
+  t.idx[3] = yb * w + xb;
+  t.wt[0] = (1.f - fx) * (1.f - fy);
+  t.wt[1] = fx * (1.f - fy);
+  t.wt[2] = (1.f - fx) * fy;
+  t.wt[3] = fx * fy;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float t00 = __ldg(tex + 3 * t.idx[0] + k), t10 = __ldg(tex + 3 * t.idx[1] + k);
+    const float t01 = __ldg(tex + 3 * t.idx[2] + k), t11 = __ldg(tex + 3 * t.idx[3] + k);
+    c[k] = t.wt[0] * t00 + t.wt[1] * t10 + t.wt[2] * t01 + t.wt[3] * t11;
+    dcdu[k] = w * ((1.f - fy) * (t10 - t00) + fy * (t11 - t01));
+    dcdv[k] = h * ((1.f - fx) * (t01 - t00) + fx * (t11 - t10));
+  }
+  return t;
 }
 
 // Camera depths of the record's vertices at tau (keyframe lerp for the fast solver).

@@ -129,7 +129,7 @@ class Context:
             raise MbrError(rc, self.L.mbr_last_error(self.h).decode())
 
     @staticmethod
-    def _mesh(verts, faces, albedo):
+    def _mesh(verts, faces, albedo, uv=None, texture=None, dl_dtexture=None):
         V, F = verts.shape[0], faces.shape[0]
         _check(verts, torch.float32, (V, 3), "verts")
         _check(faces, torch.int32, (F, 3), "faces")
@@ -137,6 +137,16 @@ class Context:
         m = MbrMesh()
         m.V, m.F = V, F
         m.verts, m.faces, m.albedo = verts.data_ptr(), faces.data_ptr(), albedo.data_ptr()
+        if texture is not None:  # textured: the vertex attribute is uv, the colour a texture sample
+            if uv is None or texture.dim() != 3:
+                raise ValueError("a texture [th, tw, 3] needs uv [V, 2]")
+            _check(uv, torch.float32, (V, 2), "uv")
+            _check(texture, torch.float32, (texture.shape[0], texture.shape[1], 3), "texture")
+            m.uv, m.texture = uv.data_ptr(), texture.data_ptr()
+            m.tex_h, m.tex_w = texture.shape[0], texture.shape[1]
+            if dl_dtexture is not None:
+                _check(dl_dtexture, torch.float32, tuple(texture.shape), "dl_dtexture")
+                m.dl_dtexture = dl_dtexture.data_ptr()
         return m
 
     def set_profiling(self, on=True):
@@ -150,8 +160,11 @@ class Context:
     def set_tuning(self, tile=16, spt=2, splits=0):
         self._raise(self.L.mbr_set_tuning(self.h, int(tile), int(spt), int(splits)))
 
-    def render_blur(self, verts, faces, albedo, motion: Motion, camera: Camera, T, H, W, solver="fast", out=None):
-        m = self._mesh(verts, faces, albedo)
+    def render_blur(self, verts, faces, albedo, motion: Motion, camera: Camera, T, H, W, solver="fast", out=None,
+                    uv=None, texture=None):
+        """[H, W, 4] blurred RGBA.  With ``texture`` [th, tw, 3] and ``uv`` [V, 2] the colours are
+        texture samples at the interpolated uv (albedo unused)."""
+        m = self._mesh(verts, faces, albedo, uv, texture)
         if out is None:
             out = torch.empty((H, W, 4), dtype=torch.float32, device=verts.device)
         _check(out, torch.float32, (H, W, 4), "image")
@@ -161,11 +174,13 @@ class Context:
         return out
 
     def render_blur_backward(self, verts, faces, albedo, motion, camera, T, H, W, dl_dimage, solver="fast",
-                             want_albedo=True, reuse_forward=False):
-        """dL/dverts (and dL/dalbedo) for dL/dimage.  reuse_forward=True: the adjoint of the
-        immediately preceding render_blur on this context with the same arguments and unchanged
-        tensor contents (mbr_render_blur_backward_reuse)."""
-        m = self._mesh(verts, faces, albedo)
+                             want_albedo=True, reuse_forward=False, uv=None, texture=None):
+        """dL/dverts (and dL/dalbedo) for dL/dimage; textured (``uv``, ``texture`` given):
+        (dL/dverts, dL/dalbedo, dL/dtexture).  reuse_forward=True: the adjoint of the immediately
+        preceding render_blur on this context with the same arguments and unchanged tensor
+        contents (mbr_render_blur_backward_reuse)."""
+        gt = torch.empty_like(texture) if texture is not None else None
+        m = self._mesh(verts, faces, albedo, uv, texture, gt)
         _check(dl_dimage, torch.float32, (H, W, 4), "dl_dimage")
         gv = torch.empty_like(verts)
         ga = torch.empty_like(albedo) if want_albedo else None
@@ -175,7 +190,7 @@ class Context:
             self.h, ctypes.byref(m), ctypes.byref(mo), ctypes.byref(ca), T, H, W, _lib.SOLVERS[solver],
             ctypes.c_void_p(dl_dimage.data_ptr()), ctypes.c_void_p(gv.data_ptr()),
             ctypes.c_void_p(ga.data_ptr() if ga is not None else 0), _stream()))
-        return gv, ga
+        return (gv, ga, gt) if texture is not None else (gv, ga)
 
     def debug_winners(self, verts, faces, albedo, motion, camera, T, H, W, k, solver="fast"):
         m = self._mesh(verts, faces, albedo)
@@ -215,7 +230,8 @@ class Context:
         arr = (MbrItem * len(items))()
         for i, it in enumerate(items):
             a = arr[i]
-            a.mesh = self._mesh(it["verts"], it["faces"], it["albedo"])
+            a.mesh = self._mesh(it["verts"], it["faces"], it["albedo"], it.get("uv"), it.get("texture"),
+                                it.get("dl_dtexture") if with_backward else None)
             a.motion = it["motion"].c()
             a.camera = it["camera"].c()
             a.T, a.H, a.W = it["T"], it["H"], it["W"]
@@ -229,7 +245,8 @@ class Context:
 
     def render_batch(self, items, with_backward=False):
         """items: list of dicts(verts, faces, albedo, motion, camera, T, H, W, solver, image,
-        [dl_dimage, dl_dverts, dl_dalbedo]) with preallocated CUDA tensors (see include/mbr.h)."""
+        [uv, texture], [dl_dimage, dl_dverts, dl_dalbedo, dl_dtexture]) with preallocated CUDA
+        tensors (see include/mbr.h)."""
         arr = self._items(items, with_backward)
         self._raise(self.L.mbr_render_blur_batch(self.h, len(items), arr, int(bool(with_backward)), _stream()))
 

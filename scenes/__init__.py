@@ -308,6 +308,35 @@ def parabolic(axis=(0.0, 1.0, 0.0), omega=math.pi, offset=(0.5, -0.5, 0.5), dir=
                 acc=np.asarray(acc, np.float64))
 
 
+def spherical_uv(verts):
+    """Per-vertex texture coordinates from the direction of each vertex: u = longitude / 2 pi,
+    v = colatitude / pi (a seam where the longitude wraps)."""
+    v = np.asarray(verts, dtype=np.float64)
+    r = np.linalg.norm(v, axis=1)
+    u = 0.5 + np.arctan2(v[:, 2], v[:, 0]) / (2 * math.pi)
+    w = np.arccos(np.clip(v[:, 1] / np.maximum(r, 1e-12), -1.0, 1.0)) / math.pi
+    return np.stack([u, w], axis=1)
+
+
+def smooth_texture(th, tw, rng, terms=4):
+    """RGB texture [th, tw, 3] in [0.1, 0.9]: a few random low-frequency sinusoids per channel."""
+    ys, xs = np.meshgrid(np.arange(th) / th, np.arange(tw) / tw, indexing="ij")
+    tex = np.full((th, tw, 3), 0.5)
+    for c in range(3):
+        for _ in range(terms):
+            fx, fy = rng.integers(1, 4, size=2)
+            ph = rng.uniform(0, 2 * math.pi)
+            tex[..., c] += 0.1 * np.sin(2 * math.pi * (fx * xs + fy * ys) + ph)
+    return np.clip(tex, 0.1, 0.9)
+
+
+def textured(sc, th=16, tw=24, seed=MASTER_SEED + 300):
+    """The scene with spherical per-vertex uv and a smooth random texture (colours come from the
+    texture instead of the per-vertex albedo)."""
+    rng = np.random.default_rng(seed)
+    return dict(sc, uv=spherical_uv(sc["verts"]), texture=smooth_texture(th, tw, rng))
+
+
 def scene(verts, faces, albedo, motion, cam, T, H, W):
     return dict(verts=np.ascontiguousarray(verts, dtype=np.float64),
                 faces=np.ascontiguousarray(faces, dtype=np.int32),

@@ -601,3 +601,89 @@ def test_parabolic_trajectory_is_quadratic():
     disp = lambda t: (lambda st: np.stack([st[:, 0] * st[:, 2] * th, st[:, 1] * st[:, 2] * th, st[:, 2]], 1))(p[t])
     up = disp(0.5) - 0.5 * (disp(0.0) + disp(1.0))
     assert np.allclose(up, (R @ np.array([0.0, 1.0, 0.0]))[None, :], atol=1e-9)  # +1 in world y at mid-exposure
+
+
+# ----------------------------------------------------------------------------- textures
+
+def _textured_quad(tex, T=1, D=0.0, L0=-0.55, R0=0.45, B=-0.4, Tp=0.52, H=30, W=40, uv_box=(0.0, 1.0, 0.0, 1.0)):
+    """Static (or translating) screen-aligned quad whose corners carry uv = the corners of
+    ``uv_box`` (u0, u1, v0, v1): u grows to the right, v grows downwards on screen."""
+    sc = _quad_scene(T, D, L0, R0, B, Tp, H=H, W=W)
+    u0, u1, v0, v1 = uv_box
+    # quad corners: 0 = (L0, B), 1 = (R0, B), 2 = (R0, Tp), 3 = (L0, Tp)
+    sc["uv"] = np.array([[u0, v1], [u1, v1], [u1, v0], [u0, v0]], float)
+    sc["texture"] = np.asarray(tex, float)
+    return sc
+
+
+def test_texture_affine_in_texel_space_is_reproduced():
+    """A texture whose texels are an affine function of their indices (value a + b x + c y at
+    texel (x, y)) is reproduced exactly by the bilinear lookup between texel centres, and the
+    uv of a screen-aligned quad is affine in screen space: every covered pixel shows
+    shade x (a + b X + c Y), X = u tw - 1/2, Y = v th - 1/2 (clamped to the texel-centre range)."""
+    th, tw = 6, 9
+    ys, xs = np.meshgrid(np.arange(th), np.arange(tw), indexing="ij")
+    coef = np.array([[0.30, 0.05, 0.02], [0.55, -0.03, 0.04], [0.20, 0.02, 0.06]])
+    tex = np.stack([c[0] + c[1] * xs + c[2] * ys for c in coef], axis=-1)
+    L0, R0, B, Tp = -0.55, 0.45, -0.4, 0.52
+    sc = _textured_quad(tex, L0=L0, R0=R0, B=B, Tp=Tp)
+    out = oracle.render(sc, "exact", winners=True, ambig=True)
+    rgba = out["rgba"]
+    covered = (out["winners"][0] >= 0) & (out["ambig"][0] == 0)
+    H, W = sc["H"], sc["W"]
+    n = np.array([0.0, 0.0, 1.0])
+    L = np.asarray(scenes.LIGHT_DIR) / np.linalg.norm(scenes.LIGHT_DIR)
+    shades = [scenes.K_AMBIENT + scenes.K_DIFFUSE * max(0.0, s * float(n @ L)) for s in (1.0, -1.0)]
+    checked = 0
+    for j in range(H):
+        for i in range(W):
+            if not covered[j, i]:
+                continue
+            x, y = 2 * (i + 0.5) / W - 1, 1 - 2 * (j + 0.5) / H
+            u = (x - L0) / (R0 - L0)
+            v = (Tp - y) / (Tp - B)
+            X = np.clip(u * tw - 0.5, 0, tw - 1)
+            Y = np.clip(v * th - 0.5, 0, th - 1)
+            val = coef[:, 0] + coef[:, 1] * X + coef[:, 2] * Y
+            err = min(np.max(np.abs(rgba[j, i, :3] - sh * val)) for sh in shades)
+            assert err < 1e-12, (i, j, err)
+            checked += 1
+    assert checked > 200
+
+
+def test_texture_gradient_is_exact_and_vertex_gradient_matches_differences():
+    """L is linear in the texels: dL/dtexture equals the change of L for a unit texel step.  The
+    vertex gradient through uv interpolation and the texture slope matches central differences
+    (skipping steps that move a sample across a texel cell, part of the decision hash)."""
+    rng = np.random.default_rng(5)
+    th, tw = 5, 7
+    tex = rng.uniform(0.1, 0.9, size=(th, tw, 3))
+    sc = _textured_quad(tex, T=4, D=0.3, uv_box=(0.1, 0.85, 0.05, 0.9))
+    G = rng.normal(size=(sc["H"], sc["W"], 4))
+    gt = np.zeros_like(tex)
+    gv, _, _ = oracle.render_backward(sc, G, "exact", texture_grad=gt)
+
+    def loss(s):
+        r = oracle.render(s, "exact")
+        return float(np.sum(r["rgba"] * G)), int(r["counters"][oracle.CNT_HASH])
+
+    l0, h0 = loss(sc)
+    for (y, x, c) in [(0, 0, 0), (2, 3, 1), (4, 6, 2), (1, 5, 0)]:
+        t2 = tex.copy()
+        t2[y, x, c] += 1.0
+        l1, _ = loss(dict(sc, texture=t2))
+        assert abs((l1 - l0) - gt[y, x, c]) < 1e-9 * max(1.0, abs(gt[y, x, c]))
+    h = 1e-6
+    checked = 0
+    for v in range(4):
+        for c in range(2):
+            p, m = dict(sc, verts=sc["verts"].copy()), dict(sc, verts=sc["verts"].copy())
+            p["verts"][v, c] += h
+            m["verts"][v, c] -= h
+            (lp, hp), (lm, hm) = loss(p), loss(m)
+            if hp != h0 or hm != h0:
+                continue
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - gv[v, c]) <= 1e-5 * abs(fd) + 1e-7 * np.max(np.abs(gv)), (v, c, fd, gv[v, c])
+            checked += 1
+    assert checked >= 4
