@@ -285,6 +285,16 @@ void carve_orders(int32_t* base, Prepared& pp) {
   pp.d_order_tmp = base + 3 * (size_t)pp.n_units;
 }
 
+// a render that uses a variant (texture colours, perspective-correct weights, sigmoid map) runs
+// the raster kernels compiled with them; the paper's default path runs kernels without their code
+bool uses_variants(const mbr_mesh* mesh, const mbr_camera* cam) {
+  return mesh->texture != nullptr || cam->interp != MBR_INTERP_SCREEN || cam->prob != MBR_PROB_EXP;
+}
+
+int raster_kind(const Prepared& pp, const mbr_mesh* mesh, const mbr_camera* cam) {
+  return (pp.moving ? 1 : 0) | (uses_variants(mesh, cam) ? kKindExt : 0);
+}
+
 // units of a render: 256-pixel patches x group splits
 int patches_of(int tile, int n_tiles) {
   return tile == 8 ? UnitMap<8, 8>::patches(n_tiles) : UnitMap<16, 16>::patches(n_tiles);
@@ -612,7 +622,7 @@ int forward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, con
   if (pp.n_split > 1) CUDA_TRY(c, cudaMemsetAsync(P.out, 0, sizeof(float4) * npix, st));  // splits accumulate
   WorkQueue Q;
   if ((rc = upload_queue(c, &P, 1, st, Q))) return rc;
-  const int kind = pp.moving ? 1 : 0;
+  const int kind = raster_kind(pp, mesh, cam);
   const int grid = std::max(1, std::min(persistent_grid_fwd(c->num_sms, c->tile, pp.spt, kind), Q.n_work));
   if ((rc = time_begin(c, 0, st))) return rc;
   launch_raster_fwd(Q, c->tile, pp.spt, kind, grid, st);
@@ -710,7 +720,7 @@ int backward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, co
   P.order = pp.d_order_bwd;
   WorkQueue Q;
   if ((rc = upload_queue(c, &P, 1, st, Q))) return rc;
-  const int kind = pp.moving ? 1 : 0;
+  const int kind = raster_kind(pp, mesh, cam);
   const int grid = std::max(1, std::min(persistent_grid_bwd(c->num_sms, c->tile, pp.spt, kind), Q.n_work));
   if ((rc = time_begin(c, 1, st))) return rc;
   launch_raster_bwd(Q, c->tile, pp.spt, kind, grid, st);
@@ -1121,7 +1131,7 @@ int batch_plan(mbr_ctx* c, int n, const mbr_item* items, int wb, cudaStream_t st
   free_graph(&B);
   B.items.assign(n, BatchItem());
   B.with_backward = wb != 0;
-  bool any_fast = false, any_plain = false;
+  bool any_fast = false, any_plain = false, any_ext = false;
   size_t at = 0, stage_at = 0;
   for (int i = 0; i < n; ++i) {
     const mbr_item& it = items[i];
@@ -1132,6 +1142,7 @@ int batch_plan(mbr_ctx* c, int n, const mbr_item* items, int wb, cudaStream_t st
     if ((rc = build_tables(c, &it.motion, &it.camera, it.T, it.solver, I.xf, I.sets, I.groups, I.pp))) return rc;
     Prepared& pp = I.pp;
     (it.solver == MBR_FAST ? any_fast : any_plain) = true;
+    any_ext = any_ext || uses_variants(&it.mesh, &it.camera);
     const int V = it.mesh.V, F = it.mesh.F;
     pp.tiles_x = (it.W + c->tile - 1) / c->tile;
     pp.tiles_y = (it.H + c->tile - 1) / c->tile;
@@ -1164,7 +1175,7 @@ int batch_plan(mbr_ctx* c, int n, const mbr_item* items, int wb, cudaStream_t st
     }
     I.stage_tab = carve(stage_at, I.tab_bytes);
   }
-  B.kind = any_fast && any_plain ? 2 : (any_fast ? 1 : 0);
+  B.kind = (any_fast && any_plain ? 2 : (any_fast ? 1 : 0)) | (any_ext ? kKindExt : 0);
   B.order.resize(n);
   for (int i = 0; i < n; ++i) B.order[i] = i;
   std::stable_sort(B.order.begin(), B.order.end(), [&](int a, int b) {
@@ -1541,7 +1552,7 @@ int noalloc_forward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, 
   Q.n_work = P.work;
   Q.counter = d_cnt;
   Q.status = d_status;
-  const int kind = pp.moving ? 1 : 0;
+  const int kind = raster_kind(pp, mesh, cam);
   const int grid = std::max(1, std::min(persistent_grid_fwd(c->num_sms, tw, pp.spt, kind), Q.n_work));
   launch_raster_fwd(Q, tw, pp.spt, kind, grid, st);
   CUDA_TRY(c, cudaGetLastError());

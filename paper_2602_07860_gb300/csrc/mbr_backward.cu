@@ -256,8 +256,9 @@ struct BwdSoftGradPairs {
 // functions to the slot states of the winner's vertices.  Lanes that share a winner face are
 // reduced together (one leader adds them), so each distinct face of the warp costs one set of
 // vector atomics.  Warp-collective: every lane calls it; lanes without a covered sample pass
-// has = false.
-template <bool MOVING>
+// has = false.  EXT: texture colours and perspective-correct weights are honoured (see
+// raster_fwd_block); without it they are compiled out.
+template <bool MOVING, bool EXT>
 __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const TriRec* recs_set, int slot_a, int slot_b,
                                                 bool has, int f, float tau, float u, float v, float gr, float gg,
                                                 float gb) {
@@ -271,16 +272,17 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
     ca_z[q] = cb_z[q] = ca_dz[q] = cb_dz[q] = 0.f;
   }
   if (has) {
+    const bool persp = EXT && P.persp != 0;
+    const bool textured = EXT && P.tex != nullptr;  // vertex attribute: a texture coordinate (Eq. fore)
     float4 r[kRecF4];
-    load_record<MOVING>(recs_set + f, r, P.persp != 0, false);
+    load_record<MOVING>(recs_set + f, r, persp, false);
     const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
     const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
     const float invD = 1.0f / e.D;
     const float wb[3] = {e.N0 * invD, e.N1 * invD, e.N2 * invD};  // screen-space barycentrics
     float w[3], iz[3], z[3] = {1.f, 1.f, 1.f};                     // attribute weights
-    if (P.persp) depths_at<MOVING>(r, tau, z);
-    attribute_weights(P.persp != 0, wb, z, w, iz);
-    const bool textured = P.tex != nullptr;  // vertex attribute: a texture coordinate (Eq. fore)
+    if (persp) depths_at<MOVING>(r, tau, z);
+    attribute_weights(persp, wb, z, w, iz);
     float al[3][3], nv[3][3];
     float cr = 0.f, cg = 0.f, cbl = 0.f, nx = 0.f, ny = 0.f, nz = 0.f;
 #pragma unroll
@@ -371,7 +373,7 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
     }
     // attribute weights -> screen barycentrics (and vertex depths, perspective-correct weights
     // a_i = (w_i / z_i) / S: dL/dw_k = (g_k - sum_i g_i a_i) / (z_k S), dL/dz_k = -(w_k / z_k) dL/dw_k)
-    if (P.persp) {
+    if (persp) {
       const float sa = w[0] * gw[0] + w[1] * gw[1] + w[2] * gw[2];
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
@@ -409,8 +411,8 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
   if (uniform) {
     // one butterfly over all contributions; the offsets loop stays rolled to keep the adjoint's
     // code small (the kernel is bound by instruction fetch, not by these few instructions)
-    constexpr int kDzA = MOVING ? 39 : 24, kDzB = 42;  // slot depth gradients
-    constexpr int NV = MOVING ? 45 : 27;
+    constexpr int kDzA = MOVING ? 39 : 24, kDzB = 42;  // slot depth gradients (EXT only)
+    constexpr int NV = EXT ? (MOVING ? 45 : 27) : (MOVING ? 39 : 24);
     float x[NV];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -420,9 +422,9 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
       if (MOVING) {
         x[24 + 5 * q] = cb[q].x; x[25 + 5 * q] = cb[q].y; x[26 + 5 * q] = cb[q].z; x[27 + 5 * q] = cb[q].w;
         x[28 + 5 * q] = cb_z[q];
-        x[kDzB + q] = cb_dz[q];
+        if (EXT) x[kDzB + q] = cb_dz[q];
       }
-      x[kDzA + q] = ca_dz[q];
+      if (EXT) x[kDzA + q] = ca_dz[q];
     }
 #pragma unroll 1
     for (int o = 16; o > 0; o >>= 1) {
@@ -437,9 +439,9 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
       if (MOVING) {
         cb[q] = make_float4(x[24 + 5 * q], x[25 + 5 * q], x[26 + 5 * q], x[27 + 5 * q]);
         cb_z[q] = x[28 + 5 * q];
-        cb_dz[q] = x[kDzB + q];
+        if (EXT) cb_dz[q] = x[kDzB + q];
       }
-      ca_dz[q] = x[kDzA + q];
+      if (EXT) ca_dz[q] = x[kDzA + q];
     }
   }
   if (uniform ? lane == leader : has) {
@@ -451,7 +453,7 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
         atomicAdd(gb_ + (size_t)vid[q] * 2, cb[q]);
         atomicAdd(reinterpret_cast<float2*>(gb_ + (size_t)vid[q] * 2 + 1), make_float2(cb_z[q], cb_dz[q]));
       }
-      if (P.g_albedo && !P.tex) atomicAdd(P.g_albedo + vid[q], cal[q]);
+      if (P.g_albedo && !(EXT && P.tex)) atomicAdd(P.g_albedo + vid[q], cal[q]);
     }
   }
 }
@@ -494,8 +496,8 @@ __device__ __forceinline__ BwdBlock bwd_block_setup(const RasterParams& P, int t
   return B;
 }
 
-// the adjoint of one 8 x 4 block over its split of the sample groups
-template <int TW, int TH, int SPT, bool MOVING>
+// the adjoint of one 8 x 4 block over its split of the sample groups (EXT: see covered_adjoint)
+template <int TW, int TH, int SPT, bool MOVING, bool EXT>
 __device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile, int split, int wb,
                                                  WarpScratch<SPT>& ws) {
   const BwdBlock B = bwd_block_setup<TW, TH>(P, tile, split, wb);
@@ -544,8 +546,8 @@ __device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile
           if (q == i) f = win[q];
         const bool has = rgb && f >= 0;
         const float tau = MOVING ? __ldg(gq.tau + i) : 0.f;
-        covered_adjoint<MOVING>(P, recs_set, gq.slot_a, gq.slot_b, has, has ? f : 0, tau, B.u, B.v, B.gr, B.gg,
-                                B.gb);
+        covered_adjoint<MOVING, EXT>(P, recs_set, gq.slot_a, gq.slot_b, has, has ? f : 0, tau, B.u, B.v, B.gr,
+                                     B.gg, B.gb);
       }
     }
 
@@ -569,7 +571,7 @@ __device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile
       p3.m = m;
       p3.r2 = P.r2;
       p3.inv_delta = P.inv_delta;
-      p3.prob = P.prob;
+      p3.prob = EXT ? P.prob : 0;
       p3.faces = P.faces;
       p3.gslot_a = P.g_slot + (size_t)gq.slot_a * P.V * 2;
       p3.gslot_b = P.g_slot + (size_t)gq.slot_b * P.V * 2;
@@ -579,8 +581,9 @@ __device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile
   }
 }
 
-// Persistent adjoint raster: KIND 0 = plain solver only, 1 = fast solver only, 2 = mixed batch.
-template <int TW, int TH, int SPT, int KIND>
+// Persistent adjoint raster: KIND 0 = plain solver only, 1 = fast solver only, 2 = mixed batch;
+// EXT: with the variants.
+template <int TW, int TH, int SPT, int KIND, bool EXT>
 __global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 3 : 2) raster_bwd_persistent(WorkQueue Q) {
   __shared__ CtaQueue cq;
   __shared__ RasterParams sp[kPersistentThreads / 32];
@@ -592,9 +595,9 @@ __global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 3 : 2) raster_
   while (warp_next<TW, TH>(Q, cq, P, cur, tile, split, wb)) {
     if (tile >= P.tiles_x * P.tiles_y) continue;
     if (KIND == 0 || (KIND == 2 && !P.moving))
-      raster_bwd_block<TW, TH, 1, false>(P, tile, split, wb, *reinterpret_cast<WarpScratch<1>*>(ws + warp));
+      raster_bwd_block<TW, TH, 1, false, EXT>(P, tile, split, wb, *reinterpret_cast<WarpScratch<1>*>(ws + warp));
     else
-      raster_bwd_block<TW, TH, SPT, true>(P, tile, split, wb, ws[warp]);
+      raster_bwd_block<TW, TH, SPT, true, EXT>(P, tile, split, wb, ws[warp]);
   }
 }
 
@@ -692,28 +695,34 @@ __global__ void normals_bwd_kernel(const float* __restrict__ verts, const int32_
   atomicAdd(g_verts + 3 * a + 2, -(bz + cz));
 }
 
-template <int TW, int TH, int KIND>
+template <int TW, int TH, int KIND, bool EXT>
 static void launch_bwd_spt(const WorkQueue& Q, int spt, int grid, cudaStream_t st) {
   if (spt <= 2)
-    raster_bwd_persistent<TW, TH, 2, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
+    raster_bwd_persistent<TW, TH, 2, KIND, EXT><<<grid, kPersistentThreads, 0, st>>>(Q);
   else
-    raster_bwd_persistent<TW, TH, 4, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
+    raster_bwd_persistent<TW, TH, 4, KIND, EXT><<<grid, kPersistentThreads, 0, st>>>(Q);
 }
 
-template <int TW, int TH>
+template <int TW, int TH, bool EXT>
 static void launch_bwd_tile(const WorkQueue& Q, int spt, int kind, int grid, cudaStream_t st) {
   if (kind == 0)
-    raster_bwd_persistent<TW, TH, 1, 0><<<grid, kPersistentThreads, 0, st>>>(Q);
+    raster_bwd_persistent<TW, TH, 1, 0, EXT><<<grid, kPersistentThreads, 0, st>>>(Q);
   else if (kind == 1)
-    launch_bwd_spt<TW, TH, 1>(Q, spt, grid, st);
+    launch_bwd_spt<TW, TH, 1, EXT>(Q, spt, grid, st);
   else
-    launch_bwd_spt<TW, TH, 2>(Q, spt, grid, st);
+    launch_bwd_spt<TW, TH, 2, EXT>(Q, spt, grid, st);
 }
 
 void launch_raster_bwd(const WorkQueue& Q, int tile, int spt, int kind, int grid, cudaStream_t st) {
   if (Q.n_work <= 0) return;
-  if (tile == 8) launch_bwd_tile<8, 8>(Q, spt, kind, grid, st);
-  else launch_bwd_tile<16, 16>(Q, spt, kind, grid, st);
+  const int k = kind & kKindMask;
+  if (kind & kKindExt) {
+    if (tile == 8) launch_bwd_tile<8, 8, true>(Q, spt, k, grid, st);
+    else launch_bwd_tile<16, 16, true>(Q, spt, k, grid, st);
+  } else {
+    if (tile == 8) launch_bwd_tile<8, 8, false>(Q, spt, k, grid, st);
+    else launch_bwd_tile<16, 16, false>(Q, spt, k, grid, st);
+  }
 }
 
 template <typename K>
@@ -723,18 +732,22 @@ static int occupancy_of(K kernel) {
   return n < 1 ? 1 : n;
 }
 
-template <int TW, int TH>
+template <int TW, int TH, bool EXT>
 static int occ_bwd(int spt, int kind) {
-  if (kind == 0) return occupancy_of(raster_bwd_persistent<TW, TH, 1, 0>);
+  if (kind == 0) return occupancy_of(raster_bwd_persistent<TW, TH, 1, 0, EXT>);
   if (kind == 1)
-    return spt <= 2 ? occupancy_of(raster_bwd_persistent<TW, TH, 2, 1>)
-                    : occupancy_of(raster_bwd_persistent<TW, TH, 4, 1>);
-  return spt <= 2 ? occupancy_of(raster_bwd_persistent<TW, TH, 2, 2>)
-                  : occupancy_of(raster_bwd_persistent<TW, TH, 4, 2>);
+    return spt <= 2 ? occupancy_of(raster_bwd_persistent<TW, TH, 2, 1, EXT>)
+                    : occupancy_of(raster_bwd_persistent<TW, TH, 4, 1, EXT>);
+  return spt <= 2 ? occupancy_of(raster_bwd_persistent<TW, TH, 2, 2, EXT>)
+                  : occupancy_of(raster_bwd_persistent<TW, TH, 4, 2, EXT>);
 }
 
 int persistent_grid_bwd(int num_sms, int tile, int spt, int kind) {
-  return num_sms * (tile == 8 ? occ_bwd<8, 8>(spt, kind) : occ_bwd<16, 16>(spt, kind));
+  const int k = kind & kKindMask;
+  int occ;
+  if (kind & kKindExt) occ = tile == 8 ? occ_bwd<8, 8, true>(spt, k) : occ_bwd<16, 16, true>(spt, k);
+  else occ = tile == 8 ? occ_bwd<8, 8, false>(spt, k) : occ_bwd<16, 16, false>(spt, k);
+  return num_sms * occ;
 }
 
 void launch_slot_chain(const float* verts, const float* nacc, int V, const SlotXform* xf, int n_slots, float th,

@@ -396,8 +396,10 @@ struct FwdSoftPairs {
 
 // One work item: the 8 x 4 pixel block wb of tile `tile`, sample groups of split `split`; ws is
 // the warp's shared scratch.  COUNT (measurement build only): also count soft terms, covered
-// samples and pass efficiency into P.counts.
-template <int TW, int TH, int SPT, bool MOVING, bool COUNT = false>
+// samples and pass efficiency into P.counts.  EXT: the variants (texture colours,
+// perspective-correct weights, sigmoid probability) are honoured; without it they are compiled
+// out, so the paper's default path carries none of their code.
+template <int TW, int TH, int SPT, bool MOVING, bool COUNT = false, bool EXT = false>
 __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile, int split, int wb,
                                                  WarpScratch<SPT>& ws) {
   const int lane = threadIdx.x & 31;
@@ -465,7 +467,7 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
     const uint32_t my_s = in_img ? uncov : 0u;
     const uint32_t any_s = __reduce_or_sync(kFullMask, my_s);
     FwdSoftPairs<SPT, MOVING, COUNT> soft{recs_set, grp, bp, &ws, gr.xbits, P.r + kCoreMargin, P.r2, P.inv_delta,
-                                          P.prob, 0u, 0u, 0u};
+                                          EXT ? P.prob : 0, 0u, 0u, 0u};
     if (se > sb && any_s) {
 #pragma unroll
       for (int i = 0; i < SPT; ++i) {
@@ -507,17 +509,17 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
           if (P.dbg_ids && gr.k0 + i == P.dbg_k) P.dbg_ids[(size_t)py * P.W + px] = f;
           if (f >= 0) {
             const float tau = MOVING ? __ldg(gr.tau + i) : 0.f;
+            const bool persp = EXT && P.persp != 0, textured = EXT && P.tex != nullptr;
             float4 r[kRecF4];
-            load_record<MOVING>(recs_set + f, r, P.persp != 0, false);
+            load_record<MOVING>(recs_set + f, r, persp, false);
             const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
             const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
             const float invD = 1.0f / e.D;
             const float wb[3] = {e.N0 * invD, e.N1 * invD, e.N2 * invD};
             float w[3], iz[3], z[3] = {1.f, 1.f, 1.f};
-            if (P.persp) depths_at<MOVING>(r, tau, z);
-            attribute_weights(P.persp != 0, wb, z, w, iz);
+            if (persp) depths_at<MOVING>(r, tau, z);
+            attribute_weights(persp, wb, z, w, iz);
             float cr = 0.f, cg = 0.f, cb = 0.f, nx = 0.f, ny = 0.f, nz = 0.f, tu = 0.f, tv = 0.f;
-            const bool textured = P.tex != nullptr;
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
               const int vid = __ldg(P.faces + 3 * f + q);
@@ -588,8 +590,9 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
   }
 }
 
-// Persistent forward raster: KIND 0 = plain solver only, 1 = fast solver only, 2 = mixed batch.
-template <int TW, int TH, int SPT, int KIND>
+// Persistent forward raster: KIND 0 = plain solver only, 1 = fast solver only, 2 = mixed batch;
+// EXT: with the variants (see raster_fwd_block).
+template <int TW, int TH, int SPT, int KIND, bool EXT>
 __global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 3 : 2) raster_fwd_persistent(WorkQueue Q) {
   __shared__ CtaQueue cq;
   __shared__ RasterParams sp[kPersistentThreads / 32];
@@ -601,9 +604,9 @@ __global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 3 : 2) raster_
   while (warp_next<TW, TH>(Q, cq, P, cur, tile, split, wb)) {
     if (tile >= P.tiles_x * P.tiles_y) continue;
     if (KIND == 0 || (KIND == 2 && !P.moving))
-      raster_fwd_block<TW, TH, 1, false>(P, tile, split, wb, *reinterpret_cast<WarpScratch<1>*>(ws + warp));
+      raster_fwd_block<TW, TH, 1, false, false, EXT>(P, tile, split, wb, *reinterpret_cast<WarpScratch<1>*>(ws + warp));
     else
-      raster_fwd_block<TW, TH, SPT, true>(P, tile, split, wb, ws[warp]);
+      raster_fwd_block<TW, TH, SPT, true, false, EXT>(P, tile, split, wb, ws[warp]);
   }
 }
 
@@ -768,22 +771,22 @@ void launch_scan_pair(const ScanPair& sp, cudaStream_t st) {
   scan_apply_kernel<<<dim3(nb, 2), kScanThreads, 0, st>>>(sp);
 }
 
-template <int TW, int TH, int KIND>
+template <int TW, int TH, int KIND, bool EXT>
 static void launch_fwd_spt(const WorkQueue& Q, int spt, int grid, cudaStream_t st) {
   if (spt <= 2)
-    raster_fwd_persistent<TW, TH, 2, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
+    raster_fwd_persistent<TW, TH, 2, KIND, EXT><<<grid, kPersistentThreads, 0, st>>>(Q);
   else
-    raster_fwd_persistent<TW, TH, 4, KIND><<<grid, kPersistentThreads, 0, st>>>(Q);
+    raster_fwd_persistent<TW, TH, 4, KIND, EXT><<<grid, kPersistentThreads, 0, st>>>(Q);
 }
 
-template <int TW, int TH>
+template <int TW, int TH, bool EXT>
 static void launch_fwd_tile(const WorkQueue& Q, int spt, int kind, int grid, cudaStream_t st) {
   if (kind == 0)
-    raster_fwd_persistent<TW, TH, 1, 0><<<grid, kPersistentThreads, 0, st>>>(Q);
+    raster_fwd_persistent<TW, TH, 1, 0, EXT><<<grid, kPersistentThreads, 0, st>>>(Q);
   else if (kind == 1)
-    launch_fwd_spt<TW, TH, 1>(Q, spt, grid, st);
+    launch_fwd_spt<TW, TH, 1, EXT>(Q, spt, grid, st);
   else
-    launch_fwd_spt<TW, TH, 2>(Q, spt, grid, st);
+    launch_fwd_spt<TW, TH, 2, EXT>(Q, spt, grid, st);
 }
 
 template <typename K>
@@ -793,24 +796,35 @@ static int occupancy_of(K kernel) {
   return n < 1 ? 1 : n;
 }
 
-template <int TW, int TH>
+template <int TW, int TH, bool EXT>
 static int occ_fwd(int spt, int kind) {
-  if (kind == 0) return occupancy_of(raster_fwd_persistent<TW, TH, 1, 0>);
+  if (kind == 0) return occupancy_of(raster_fwd_persistent<TW, TH, 1, 0, EXT>);
   if (kind == 1)
-    return spt <= 2 ? occupancy_of(raster_fwd_persistent<TW, TH, 2, 1>) : occupancy_of(raster_fwd_persistent<TW, TH, 4, 1>);
-  return spt <= 2 ? occupancy_of(raster_fwd_persistent<TW, TH, 2, 2>) : occupancy_of(raster_fwd_persistent<TW, TH, 4, 2>);
+    return spt <= 2 ? occupancy_of(raster_fwd_persistent<TW, TH, 2, 1, EXT>)
+                    : occupancy_of(raster_fwd_persistent<TW, TH, 4, 1, EXT>);
+  return spt <= 2 ? occupancy_of(raster_fwd_persistent<TW, TH, 2, 2, EXT>)
+                  : occupancy_of(raster_fwd_persistent<TW, TH, 4, 2, EXT>);
 }
 
+// kind: kKindPlain / kKindFast / kKindMixed, plus kKindExt for the variant kernels
 int persistent_grid_fwd(int num_sms, int tile, int spt, int kind) {
-  return num_sms * (tile == 8 ? occ_fwd<8, 8>(spt, kind) : occ_fwd<16, 16>(spt, kind));
+  const int k = kind & kKindMask;
+  int occ;
+  if (kind & kKindExt) occ = tile == 8 ? occ_fwd<8, 8, true>(spt, k) : occ_fwd<16, 16, true>(spt, k);
+  else occ = tile == 8 ? occ_fwd<8, 8, false>(spt, k) : occ_fwd<16, 16, false>(spt, k);
+  return num_sms * occ;
 }
 
 void launch_raster_fwd(const WorkQueue& Q, int tile, int spt, int kind, int grid, cudaStream_t st) {
   if (Q.n_work <= 0) return;
-  if (tile == 8)
-    launch_fwd_tile<8, 8>(Q, spt, kind, grid, st);
-  else
-    launch_fwd_tile<16, 16>(Q, spt, kind, grid, st);
+  const int k = kind & kKindMask;
+  if (kind & kKindExt) {
+    if (tile == 8) launch_fwd_tile<8, 8, true>(Q, spt, k, grid, st);
+    else launch_fwd_tile<16, 16, true>(Q, spt, k, grid, st);
+  } else {
+    if (tile == 8) launch_fwd_tile<8, 8, false>(Q, spt, k, grid, st);
+    else launch_fwd_tile<16, 16, false>(Q, spt, k, grid, st);
+  }
 }
 
 size_t unit_order_ints(int n_units) { return (size_t)n_units; }
@@ -832,7 +846,7 @@ void launch_unit_order_measured(const int32_t* cost, int n_units, int32_t* order
 
 void launch_raster_count(const WorkQueue& Q, int spt, int kind, int grid, cudaStream_t st) {
   if (Q.n_work <= 0) return;
-  if (kind == 0) raster_fwd_count<1, 0><<<grid, kPersistentThreads, 0, st>>>(Q);
+  if ((kind & kKindMask) == 0) raster_fwd_count<1, 0><<<grid, kPersistentThreads, 0, st>>>(Q);
   else if (spt <= 2) raster_fwd_count<2, 1><<<grid, kPersistentThreads, 0, st>>>(Q);
   else raster_fwd_count<4, 1><<<grid, kPersistentThreads, 0, st>>>(Q);
 }

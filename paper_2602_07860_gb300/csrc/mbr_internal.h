@@ -38,7 +38,9 @@ struct ScanPair {
 };
 size_t scan_temp_ints(int n);
 void launch_scan_pair(const ScanPair& sp, cudaStream_t st);
-// persistent raster launches; kind 0 plain only, 1 fast only, 2 mixed
+// persistent raster launches; kind 0 plain only, 1 fast only, 2 mixed, plus kKindExt for the
+// kernels with the variants (texture colours, perspective-correct weights, sigmoid probability)
+constexpr int kKindMask = 3, kKindExt = 4;
 void launch_raster_fwd(const WorkQueue& Q, int tile, int spt, int kind, int grid, cudaStream_t st);
 int persistent_grid_fwd(int num_sms, int tile, int spt, int kind);
 int persistent_grid_bwd(int num_sms, int tile, int spt, int kind);
