@@ -34,6 +34,11 @@ struct BinSet {
 
 struct BatchState;  // batched renders (defined with mbr_render_blur_batch)
 struct Prepared;    // front half of one render (defined below)
+struct FwdCostKey {  // unit layout whose measured forward costs the order buffer holds
+  bool valid = false;
+  int n_units = 0, G = 0, n_tiles = 0, n_split = 0, tile = 0;
+  const void* buf = nullptr;
+};
 
 // arguments of the last mbr_render_blur, whose front half the adjoint may reuse
 struct LastForward {
@@ -54,6 +59,7 @@ struct mbr_ctx {
   int tile = 16, spt = 2, splits = 0;
   // scratch
   DevBuf nacc, pos, nrm, recs, tables, partial, gslot, galb, gm, cnt64, status, order, bstate, bin_counts;
+  FwdCostKey fcost;  // unit layout of the last forward whose per-unit cost is in the order buffer
   BinSet core, soft;  // undilated bins (coverage) and r_soft-dilated bins (soft coverage)
   void* host_stage = nullptr;
   size_t host_stage_cap = 0;
@@ -272,17 +278,19 @@ struct Prepared {
   int32_t* d_order = nullptr;       // their visiting order (estimate from the bins)
   int32_t* d_order_bwd = nullptr;   // the adjoint's visiting order (from the forward's measured cost)
   int32_t* d_cost = nullptr;        // the forward's measured adjoint cost per unit
+  int32_t* d_fcost = nullptr;       // the forward's measured own cost per unit
   int32_t* d_order_tmp = nullptr;   // scratch of the order kernels
 };
 
-// order buffer of a render: order | adjoint order | cost | scratch
-size_t order_buffer_ints(int n_units) { return (size_t)3 * n_units + unit_order_ints(n_units); }
+// order buffer of a render: order | adjoint order | adjoint cost | forward cost | scratch
+size_t order_buffer_ints(int n_units) { return (size_t)4 * n_units + unit_order_ints(n_units); }
 
 void carve_orders(int32_t* base, Prepared& pp) {
   pp.d_order = base;
   pp.d_order_bwd = base + pp.n_units;
   pp.d_cost = base + 2 * (size_t)pp.n_units;
-  pp.d_order_tmp = base + 3 * (size_t)pp.n_units;
+  pp.d_fcost = base + 3 * (size_t)pp.n_units;
+  pp.d_order_tmp = base + 4 * (size_t)pp.n_units;
 }
 
 // a render that uses a variant (texture colours, perspective-correct weights, sigmoid map) runs
@@ -484,8 +492,17 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
   pp.n_units = n_patches * pp.n_split;
   if ((rc = ensure(c, c->order, sizeof(int32_t) * order_buffer_ints(pp.n_units), st))) return rc;
   carve_orders((int32_t*)c->order.p, pp);
-  launch_unit_order((const int32_t*)c->core.offsets.p, (const int32_t*)c->soft.offsets.p, pp.G, pp.n_tiles, tw,
-                    pp.n_split, pp.n_units, pp.d_order, pp.d_order_tmp, pp.d_cost, st);
+  // The previous forward of the same unit layout measured each unit's work: visit the units in
+  // that order (an optimisation loop's geometry moves little between calls); otherwise estimate
+  // from the bin sizes.  Either way both cost arrays are cleared for this render's measurements.
+  const FwdCostKey& K = c->fcost;
+  if (K.valid && K.buf == c->order.p && K.n_units == pp.n_units && K.G == pp.G && K.n_tiles == pp.n_tiles &&
+      K.n_split == pp.n_split && K.tile == tw)
+    launch_unit_order_measured(pp.d_fcost, pp.n_units, pp.d_order, pp.d_order_tmp, pp.d_fcost, pp.d_cost, st);
+  else
+    launch_unit_order((const int32_t*)c->core.offsets.p, (const int32_t*)c->soft.offsets.p, pp.G, pp.n_tiles, tw,
+                      pp.n_split, pp.n_units, pp.d_order, pp.d_order_tmp, pp.d_cost, pp.d_fcost, st);
+  c->fcost.valid = false;  // until this render's forward has measured
   CUDA_TRY(c, cudaGetLastError());
   c->stats.launches += 1;
   return MBR_OK;
@@ -618,6 +635,7 @@ int forward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, con
     P.s_val = (float*)c->bstate.p;
     P.s_stat = (uint8_t*)c->bstate.p + ns * 4;
     P.unit_cost = pp.d_cost;  // and its cost per unit (cleared by the unit order), for the adjoint's order
+    P.fwd_cost = pp.d_fcost;  // and its own, for the next forward's order
   }
   if (pp.n_split > 1) CUDA_TRY(c, cudaMemsetAsync(P.out, 0, sizeof(float4) * npix, st));  // splits accumulate
   WorkQueue Q;
@@ -631,6 +649,7 @@ int forward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, con
   c->stats.launches += 1;
   c->stats.n_split = pp.n_split;
   if (pp_out) *pp_out = pp;
+  if (P.fwd_cost) c->fcost = FwdCostKey{true, pp.n_units, pp.G, pp.n_tiles, pp.n_split, c->tile, c->order.p};
   if (image && !dbg_ids) {
     if (!c->last_pp) c->last_pp = new (std::nothrow) Prepared();
     if (c->last_pp) {
@@ -716,7 +735,7 @@ int backward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, co
   const size_t ns = (size_t)T * H * W;
   P.s_val = (float*)c->bstate.p;
   P.s_stat = (uint8_t*)c->bstate.p + ns * 4;
-  launch_unit_order_measured(pp.d_cost, pp.n_units, pp.d_order_bwd, pp.d_order_tmp, st);
+  launch_unit_order_measured(pp.d_cost, pp.n_units, pp.d_order_bwd, pp.d_order_tmp, nullptr, nullptr, st);
   P.order = pp.d_order_bwd;
   WorkQueue Q;
   if ((rc = upload_queue(c, &P, 1, st, Q))) return rc;
@@ -1280,7 +1299,8 @@ int batch_enqueue(mbr_ctx* c, const mbr_item* items, BatchState& B, cudaStream_t
     Prepared po = pp;
     carve_orders((int32_t*)(A + I.o_order), po);
     launch_unit_order((const int32_t*)(A + I.o_offs[0]), (const int32_t*)(A + I.o_offs[1]), pp.G, pp.n_tiles, c->tile,
-                      pp.n_split, pp.n_units, po.d_order, po.d_order_tmp, B.with_backward ? po.d_cost : nullptr, st);
+                      pp.n_split, pp.n_units, po.d_order, po.d_order_tmp, B.with_backward ? po.d_cost : nullptr,
+                      nullptr, st);
     if (pp.n_split > 1) CUDA_TRY(c, cudaMemsetAsync(it.image, 0, sizeof(float4) * (size_t)it.H * it.W, st));
     if (B.with_backward) {
       CUDA_TRY(c, cudaMemsetAsync(A + I.o_gslot, 0, sizeof(float4) * 2 * (size_t)it.mesh.V * pp.n_slots, st));
@@ -1318,7 +1338,7 @@ int batch_enqueue(mbr_ctx* c, const mbr_item* items, BatchState& B, cudaStream_t
     for (int i = 0; i < n; ++i) {
       Prepared po = B.items[i].pp;
       carve_orders((int32_t*)(A + B.items[i].o_order), po);
-      launch_unit_order_measured(po.d_cost, po.n_units, po.d_order, po.d_order_tmp, st);
+      launch_unit_order_measured(po.d_cost, po.n_units, po.d_order, po.d_order_tmp, nullptr, nullptr, st);
     }
     CUDA_TRY(c, cudaMemsetAsync(Q.counter, 0, sizeof(int32_t), st));
     launch_raster_bwd(Q, c->tile, spt, B.kind, B.grid_bwd, st);
@@ -1536,7 +1556,7 @@ int noalloc_forward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, 
     return fail(c, MBR_ERR_ARG, "render needs more than the %zu MiB static scratch; use mbr_render_blur",
                 kStaticScratchBytes >> 20);
   launch_unit_order(offs[0], offs[1], pp.G, pp.n_tiles, tw, pp.n_split, pp.n_units, pp.d_order,
-                    pp.d_order + pp.n_units, nullptr, st);
+                    pp.d_order + pp.n_units, nullptr, nullptr, st);
   const RasterBufs bufs{recs, nrm, {offs[0], offs[1]}, {list[0], list[1]}};
   RasterParams P = raster_params(c, bufs, mesh, cam, T, H, W, pp);
   P.out = (float4*)image;

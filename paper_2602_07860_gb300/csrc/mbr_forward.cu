@@ -420,6 +420,7 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
   float acc_r = 0.f, acc_g = 0.f, acc_b = 0.f, acc_a = 0.f;
   uint32_t n_soft = 0, n_cov = 0, n_seval = 0, n_sbatch = 0, n_ctest = 0, n_cbatch = 0;
   int adj_cost = 0;  // lane 0: soft pair batches + samples with a covered pixel (the adjoint's work)
+  int fwd_cost = 0;  // lane 0: core and soft pair batches (this kernel's work)
 
   for (int g = g_begin; g < g_end; ++g) {
     const Group* grp = P.groups + g;
@@ -486,6 +487,7 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
       }
     }
     adj_cost += (int)soft.n_batches + __popc(__reduce_or_sync(kFullMask, in_img ? (all_s & ~uncov) : 0u));
+    fwd_cost += (int)(core.n_batches + soft.n_batches) + 1;
     if (COUNT) {
       n_ctest += core.n_tests;
       n_cbatch += core.n_batches;
@@ -564,9 +566,10 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
     }
     __syncwarp();  // the scratch is rewritten by the next group
   }
-  if (P.unit_cost && lane == 0 && adj_cost) {
+  if (lane == 0 && (P.unit_cost || P.fwd_cost)) {
     const int unit = split * UnitMap<TW, TH>::patches(n_tiles) + tile / UnitMap<TW, TH>::kTilesPerUnit;
-    atomicAdd(P.unit_cost + unit, adj_cost);
+    if (P.unit_cost && adj_cost) atomicAdd(P.unit_cost + unit, adj_cost);
+    if (P.fwd_cost && fwd_cost) atomicAdd(P.fwd_cost + unit, fwd_cost);
   }
   if (in_img) {
     const size_t o = (size_t)py * P.W + px;
@@ -659,13 +662,14 @@ __device__ __forceinline__ int unit_bucket(const int32_t* __restrict__ core_off,
 }
 
 // One CTA: bucket every unit by its cost (from the bins, or measured when cost_in is set), count
-// the buckets in shared memory, scan them largest first, scatter the units.  cost_zero (if set)
-// is cleared on the way (the forward raster accumulates its measured costs there).
+// the buckets in shared memory, scan them largest first, scatter the units.  cost_zero and
+// cost_zero2 (if set) are cleared on the way (the forward raster accumulates its measured costs
+// there); cost_zero may be cost_in.
 constexpr int kOrderThreads = 1024;
 
 __global__ void __launch_bounds__(kOrderThreads) unit_order_kernel(
     const int32_t* __restrict__ core_off, const int32_t* __restrict__ soft_off, int G, int n_tiles, int tpu,
-    int n_patches, int n_split, const int32_t* __restrict__ cost_in, int32_t* __restrict__ cost_zero, int n_units,
+    int n_patches, int n_split, const int32_t* cost_in, int32_t* cost_zero, int32_t* cost_zero2, int n_units,
     int32_t* __restrict__ bucket, int32_t* __restrict__ order) {
   __shared__ int s_hist[kOrderBuckets];
   if (threadIdx.x < kOrderBuckets) s_hist[threadIdx.x] = 0;
@@ -675,7 +679,8 @@ __global__ void __launch_bounds__(kOrderThreads) unit_order_kernel(
                           : unit_bucket(core_off, soft_off, G, n_tiles, tpu, n_patches, n_split, u);
     bucket[u] = k;
     atomicAdd(&s_hist[k], 1);
-    if (cost_zero) cost_zero[u] = 0;
+    if (cost_zero) cost_zero[u] = 0;  // may be cost_in: this thread has read it
+    if (cost_zero2) cost_zero2[u] = 0;
   }
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -830,18 +835,20 @@ void launch_raster_fwd(const WorkQueue& Q, int tile, int spt, int kind, int grid
 size_t unit_order_ints(int n_units) { return (size_t)n_units; }
 
 void launch_unit_order(const int32_t* core_off, const int32_t* soft_off, int G, int n_tiles, int tile, int n_split,
-                       int n_units, int32_t* order, int32_t* scratch, int32_t* cost_zero, cudaStream_t st) {
+                       int n_units, int32_t* order, int32_t* scratch, int32_t* cost_zero, int32_t* cost_zero2,
+                       cudaStream_t st) {
   if (n_units <= 0) return;
   const int tpu = tile == 8 ? UnitMap<8, 8>::kTilesPerUnit : UnitMap<16, 16>::kTilesPerUnit;
   const int n_patches = (n_tiles + tpu - 1) / tpu;
   unit_order_kernel<<<1, kOrderThreads, 0, st>>>(core_off, soft_off, G, n_tiles, tpu, n_patches, n_split, nullptr,
-                                                 cost_zero, n_units, scratch, order);
+                                                 cost_zero, cost_zero2, n_units, scratch, order);
 }
 
-void launch_unit_order_measured(const int32_t* cost, int n_units, int32_t* order, int32_t* scratch, cudaStream_t st) {
+void launch_unit_order_measured(const int32_t* cost, int n_units, int32_t* order, int32_t* scratch,
+                                int32_t* cost_zero, int32_t* cost_zero2, cudaStream_t st) {
   if (n_units <= 0) return;
-  unit_order_kernel<<<1, kOrderThreads, 0, st>>>(nullptr, nullptr, 0, 0, 1, 1, 1, cost, nullptr, n_units, scratch,
-                                                 order);
+  unit_order_kernel<<<1, kOrderThreads, 0, st>>>(nullptr, nullptr, 0, 0, 1, 1, 1, cost, cost_zero, cost_zero2,
+                                                 n_units, scratch, order);
 }
 
 void launch_raster_count(const WorkQueue& Q, int spt, int kind, int grid, cudaStream_t st) {

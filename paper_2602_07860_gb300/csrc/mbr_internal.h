@@ -45,12 +45,16 @@ void launch_raster_fwd(const WorkQueue& Q, int tile, int spt, int kind, int grid
 int persistent_grid_fwd(int num_sms, int tile, int spt, int kind);
 int persistent_grid_bwd(int num_sms, int tile, int spt, int kind);
 // LPT visiting order of a render's units (patch x group split) from its bin offsets (one launch);
-// scratch holds unit_order_ints(n_units) ints; cost_zero (if set, [n_units]) is cleared
+// scratch holds unit_order_ints(n_units) ints; cost_zero, cost_zero2 (if set, [n_units]) are
+// cleared
 size_t unit_order_ints(int n_units);
 void launch_unit_order(const int32_t* core_off, const int32_t* soft_off, int G, int n_tiles, int tile, int n_split,
-                       int n_units, int32_t* order, int32_t* scratch, int32_t* cost_zero, cudaStream_t st);
-// the same from a measured cost per unit (the forward raster's estimate of the adjoint's work)
-void launch_unit_order_measured(const int32_t* cost, int n_units, int32_t* order, int32_t* scratch, cudaStream_t st);
+                       int n_units, int32_t* order, int32_t* scratch, int32_t* cost_zero, int32_t* cost_zero2,
+                       cudaStream_t st);
+// the same from a measured cost per unit (a raster's own measurement); cost_zero (may be cost)
+// and cost_zero2 (if set) are cleared after reading
+void launch_unit_order_measured(const int32_t* cost, int n_units, int32_t* order, int32_t* scratch,
+                                int32_t* cost_zero, int32_t* cost_zero2, cudaStream_t st);
 // measurement build of the forward raster (16 x 16 tiles): counts soft terms / covered samples
 void launch_raster_count(const WorkQueue& Q, int spt, int kind, int grid, cudaStream_t st);
 void launch_count(const TriRec* recs, int F, const Group* groups, int G, int W, int H, float r,
