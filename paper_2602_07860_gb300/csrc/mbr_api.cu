@@ -1131,6 +1131,7 @@ void batch_write_params(mbr_ctx* c, const mbr_item* items, BatchState& B) {
     pp.soft_cap = I.cap[1];
     RasterParams P = raster_params(c, bufs, &it.mesh, &it.camera, it.T, it.H, it.W, pp);
     P.out = (float4*)it.image;
+    P.fwd_cost = pp.d_fcost;  // the forward measures its per-unit work for the next replay's order
     if (B.with_backward) {  // the forward launch writes the per-sample state, the adjoint reads it
       P.dl_dimage = (const float4*)it.dl_dimage;
       P.g_slot = (float4*)(A + I.o_gslot);
@@ -1298,9 +1299,13 @@ int batch_enqueue(mbr_ctx* c, const mbr_item* items, BatchState& B, cudaStream_t
                st);
     Prepared po = pp;
     carve_orders((int32_t*)(A + I.o_order), po);
-    launch_unit_order((const int32_t*)(A + I.o_offs[0]), (const int32_t*)(A + I.o_offs[1]), pp.G, pp.n_tiles, c->tile,
-                      pp.n_split, pp.n_units, po.d_order, po.d_order_tmp, B.with_backward ? po.d_cost : nullptr,
-                      nullptr, st);
+    // the sizing run orders the units by the bin estimate; the captured replays by the previous
+    // run's measured forward cost (same plan, so the same unit layout)
+    if (sizing)
+      launch_unit_order((const int32_t*)(A + I.o_offs[0]), (const int32_t*)(A + I.o_offs[1]), pp.G, pp.n_tiles,
+                        c->tile, pp.n_split, pp.n_units, po.d_order, po.d_order_tmp, po.d_cost, po.d_fcost, st);
+    else
+      launch_unit_order_measured(po.d_fcost, pp.n_units, po.d_order, po.d_order_tmp, po.d_fcost, po.d_cost, st);
     if (pp.n_split > 1) CUDA_TRY(c, cudaMemsetAsync(it.image, 0, sizeof(float4) * (size_t)it.H * it.W, st));
     if (B.with_backward) {
       CUDA_TRY(c, cudaMemsetAsync(A + I.o_gslot, 0, sizeof(float4) * 2 * (size_t)it.mesh.V * pp.n_slots, st));

@@ -420,7 +420,7 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
   float acc_r = 0.f, acc_g = 0.f, acc_b = 0.f, acc_a = 0.f;
   uint32_t n_soft = 0, n_cov = 0, n_seval = 0, n_sbatch = 0, n_ctest = 0, n_cbatch = 0;
   int adj_cost = 0;  // lane 0: soft pair batches + samples with a covered pixel (the adjoint's work)
-  int fwd_cost = 0;  // lane 0: core and soft pair batches (this kernel's work)
+  const long long t_start = clock64();  // this block's own time is the forward's cost measure
 
   for (int g = g_begin; g < g_end; ++g) {
     const Group* grp = P.groups + g;
@@ -487,7 +487,6 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
       }
     }
     adj_cost += (int)soft.n_batches + __popc(__reduce_or_sync(kFullMask, in_img ? (all_s & ~uncov) : 0u));
-    fwd_cost += (int)(core.n_batches + soft.n_batches) + 1;
     if (COUNT) {
       n_ctest += core.n_tests;
       n_cbatch += core.n_batches;
@@ -569,7 +568,9 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
   if (lane == 0 && (P.unit_cost || P.fwd_cost)) {
     const int unit = split * UnitMap<TW, TH>::patches(n_tiles) + tile / UnitMap<TW, TH>::kTilesPerUnit;
     if (P.unit_cost && adj_cost) atomicAdd(P.unit_cost + unit, adj_cost);
-    if (P.fwd_cost && fwd_cost) atomicAdd(P.fwd_cost + unit, fwd_cost);
+    // SM cycles / 64 spent on the block (a unit's 8 blocks sum to far below 2^31)
+    const int cyc = (int)min((clock64() - t_start) >> 6, (long long)(1 << 24));
+    if (P.fwd_cost && cyc > 0) atomicAdd(P.fwd_cost + unit, cyc);
   }
   if (in_img) {
     const size_t o = (size_t)py * P.W + px;

@@ -65,7 +65,7 @@ struct RasterParams {
   int32_t work;              // units of this render: patches * n_split
   const int32_t* order;      // [work] unit visiting order (largest estimated work first), or null
   int32_t* unit_cost;        // forward, if set: [work] measured adjoint work per unit (zeroed before)
-  int32_t* fwd_cost;         // forward, if set: [work] measured forward work per unit (zeroed before)
+  int32_t* fwd_cost;         // forward, if set: [work] its own time per unit, SM cycles / 64 (zeroed before)
   unsigned long long* counts;  // measurement build only: [soft terms, covered samples]
   // adjoint only
   const float4* dl_dimage;   // [H*W]
@@ -541,7 +541,7 @@ struct CorePairs {
     }
   }
   __device__ __forceinline__ void batch_end(int) {
-    if ((threadIdx.x & 31) == 0) ++n_batches;  // lane 0: the forward's cost measure
+    if (COUNT && (threadIdx.x & 31) == 0) ++n_batches;
   }
 };
 
