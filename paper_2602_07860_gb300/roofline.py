@@ -23,17 +23,27 @@ Eq. time-dependent2 and the keyframe closest point of Eqs. euc-dist-approx-1..3:
           projections (3 x 13 = 39), exponent argument, exp, 1 - e, product (4), q0 (2) = 45.
           fast: w(tau) = N / D (Horner 12, rcp + 2 mul 3), p' = F(X) w (6), closest point in
           F(X) (39), F(tau) w* - p with the lerped edges (20), d (3), exp and product (4) = 87.
-  COV     shading of a covered sample: w = N / D (4), albedo (18), normal (18; fast also lerps
-          the keyframe normals, not counted), normalisation (10), n.l and Lambert (8),
-          accumulation (2) = 60.
+  COV     shading of a covered sample: w = N / D (4), albedo (18), normal (18), normalisation
+          (10), n.l and Lambert (8), accumulation (2) = 60; fast also lerps the three keyframe
+          normals to tau (18) = 78.
   SAMPLE  alpha accumulation of any sample (4).
 Adjoint (the forward raster stores, per sample, the winner face or the log soft product and the
 count of vanishing factors; the adjoint reads them and does not repeat the coverage tests):
-  SOFT_BWD  the soft factor recomputed (SOFT: d and the closest point are needed again) and the
-            derivative of d through the closest point to the vertex coordinates (plain 30,
-            fast 90) -- plain 75, fast 177.
-  COV_BWD   recomputed shading (60) plus its adjoint through w = N / D and the edge functions to
-            the vertex coordinates, normals and albedo (110) = 170.
+  SOFT_BWD  the soft factor recomputed (SOFT: d and the closest point are needed again), the
+            exclusive product exp(S - log f) and dA/dd (5), and the derivative of d to the
+            vertex coordinates.  plain (Danskin: the closest point moves along the surface):
+            g_r = 2 gd r (3), w*_i g_r to three vertices (6) = 9; total 45 + 5 + 9 = 59.
+            fast, d = |F(tau) w* - p|^2 with w* the closest point in F(X) of p' = F(X) w(tau):
+            g_r (3), w*_i g_r (6), the edge parameter t of w* and its partials to p' and the two
+            keyframe-X edge vertices (37), p' = F(X) w to the keyframe-X vertices and to w (23),
+            w = N / D quotient rule (11), N = cross products to the vertices at tau, with the
+            relative vertices (44), and the keyframe lerp of tau back to the two segment slots
+            plus the keyframe-X terms (42) = 166; total 87 + 5 + 166 = 258.
+  COV_BWD   recomputed shading (COV) plus its adjoint: I = c shade (8), albedo / colour weights
+            (24), Lambert through the normalised normal (22), normal weights and slot normals
+            (24 fast, 12 plain), w = N / D (11), relative vertices (26 fast, 6 plain), edge
+            functions to the vertices (18), keyframe lerp to the slots (24 fast only) -- adjoint
+            fast 157, plain 101; total fast 78 + 157 = 235, plain 60 + 101 = 161.
 The z-test of covering candidates and the binning are not counted, so the model is a lower bound
 of the arithmetic the method needs.
 
@@ -41,8 +51,8 @@ Peak: 152 SMs x 128 FP32 lanes x 2 flops x 2.070 GHz (maximum SM clock) = 80.6 T
 """
 
 FLOPS = {
-    "plain": dict(cand=12, soft=45, cov=60, sample=4, soft_bwd=75, cov_bwd=170),
-    "fast": dict(cand=16, soft=87, cov=60, sample=4, soft_bwd=177, cov_bwd=170),
+    "plain": dict(cand=12, soft=45, cov=60, sample=4, soft_bwd=59, cov_bwd=161),
+    "fast": dict(cand=16, soft=87, cov=78, sample=4, soft_bwd=258, cov_bwd=235),
 }
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
