@@ -44,6 +44,48 @@ def _dist_env():
     return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+class Replicas:
+    """Bookkeeping of an N-process run: one independent replica of the whole step per GPU, no
+    data-path collective.  The barrier brackets the timed region and each rank's elapsed time is
+    reduced with MAX, so the whole-job throughput is N x (units of one replica) / (slowest rank's
+    time).  ``backend`` is "nccl" for the GPU run (tensors on ``device``) and "gloo" on CPU."""
+
+    def __init__(self, world, rank, backend=None, device="cpu"):
+        self.world, self.rank, self.device = world, rank, device
+        self.dist = None
+        if world > 1:
+            import torch.distributed as dist
+            if backend == "nccl":
+                dist.init_process_group("nccl", device_id=device)
+            else:
+                dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self, sync=None):
+        if self.dist is not None:
+            self.dist.barrier()
+        if sync is not None:
+            sync()
+
+    def max(self, x):
+        if self.dist is None:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def job_rate(self, units_per_replica, seconds):
+        """Whole-job throughput: all replicas' units over the slowest rank's time."""
+        return self.world * units_per_replica / seconds
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.barrier()
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
 def _clock_sampler():
     try:
         f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
@@ -278,22 +320,12 @@ def main():
 
     world, rank, local = _dist_env()
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    reps = Replicas(world, rank, "nccl", torch.device("cuda", local))
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
+        reps.barrier(torch.cuda.synchronize)
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    max_over_ranks = reps.max
 
     ctx = mbr.Context()
     sc = scenes.config2()
@@ -343,7 +375,7 @@ def main():
     launches = (st["launches"] - l0) * args.steps // (args.steps + args.warmup)
     total_ms = max_over_ranks(total_ms)
     ms_per_step = total_ms / args.steps
-    value = world * n_samples * args.steps / (total_ms / 1e3)
+    value = reps.job_rate(n_samples * args.steps, total_ms / 1e3)
 
     # ---- roofline of the dominant raster kernel (FP32 ALU bound); work units counted by the GPU
     # path itself (mbr_count_work), flops per unit from the formulas (roofline.py)
@@ -451,9 +483,7 @@ def main():
                 "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof,
                 "cpu_baseline": cpu, "extras": extras}
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
+    reps.close()
     return 0
 
 
