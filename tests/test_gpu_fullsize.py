@@ -75,3 +75,42 @@ def test_batch_items_windows():
         r = oracle.render(s, ORACLE_MODE[items[i]["solver"]], window=(x0, y0, w, h), ambig=True)
         max_clean, frac, excess = compare_images(g[y0:y0 + h, x0:x0 + w], r["rgba"], r["ambig"], s["T"])
         assert max_clean <= TOL and excess <= 0.0, (i, items[i]["solver"], max_clean, excess, frac)
+
+
+def test_more_than_2_31_samples_per_render():
+    """T x H x W = 520 x 2048 x 2048 > 2^31 samples (the per-sample raster state alone is 10.9 GB):
+    sample and pixel indices are 64-bit.  Silhouette windows of the image match the oracle, and the
+    adjoint (reusing the forward's state, whose late sub-frames sit beyond index 2^31) matches the
+    oracle's for a loss restricted to one window."""
+    import paper_2602_07860_gb300 as mbr
+    sc = scenes.small_scene("translate", subdiv=2, T=520, H=2048, W=2048, d=(0.6, 0.2, 0.0))
+    assert sc["T"] * sc["H"] * sc["W"] > 2 ** 31
+    ctx = mbr.Context()
+    v, f, a = mbr.mesh_tensors(sc)
+    mo, ca = mbr.motion_from_dict(sc["motion"]), mbr.camera_from_dict(sc["camera"])
+    T, H, W = sc["T"], sc["H"], sc["W"]
+    img = ctx.render_blur(v, f, a, mo, ca, T, H, W, "fast")
+    wins = _silhouette_windows(sc)
+    g = {}
+    for (x0, y0, w, h) in wins:
+        g[(x0, y0)] = img[y0:y0 + h, x0:x0 + w].cpu().double().numpy()
+    for win in wins:
+        x0, y0, w, h = win
+        r = oracle.render(sc, "fast", window=win, ambig=True)
+        max_clean, frac, excess = compare_images(g[(x0, y0)], r["rgba"], r["ambig"], T)
+        assert max_clean <= TOL and excess <= 0.0, (win, max_clean, excess, frac)
+        assert r["rgba"][..., 3].max() > 0.05
+    # adjoint for a loss on the first window only
+    x0, y0, w, h = wins[0]
+    r = oracle.render(sc, "fast", window=wins[0], ambig=True)
+    Gw = np.random.default_rng(2).normal(size=(h, w, 4))
+    Gw[(r["ambig"] != 0).any(0)] = 0.0
+    gv_o, _, _ = oracle.render_backward(sc, Gw, "fast", window=wins[0])
+    G = torch.zeros((H, W, 4), device="cuda")
+    G[y0:y0 + h, x0:x0 + w] = torch.as_tensor(Gw, dtype=torch.float32, device="cuda")
+    gv, _ = ctx.render_blur_backward(v, f, a, mo, ca, T, H, W, G, "fast", reuse_forward=True)
+    assert ctx.stats()["reused"] >= 1
+    gv = gv.cpu().double().numpy()
+    nv = np.linalg.norm(gv_o, axis=1)
+    err = np.linalg.norm(gv - gv_o, axis=1)
+    assert nv.max() > 0 and np.all(err <= 1e-3 * nv + 1e-4 * nv.max()), float((err / (nv + 1e-30)).max())
