@@ -37,7 +37,7 @@ CPU_WINDOW = (64, 64, 128, 128)   # bounded oracle sample for the CPU baseline (
 REF_WINDOW = (120, 120, 16, 16)   # per-step oracle sample of the reference arm
 # DRAM bytes (read + write) per launch from the ncu captures summarised in profiles/ (tiles 8x8,
 # spt 1, this workload); to be refreshed (or set to None) whenever the kernels change
-NCU_DRAM_BYTES = {"raster_bwd_persistent": 34.87e6, "raster_fwd_persistent": 18.14e6}
+NCU_DRAM_BYTES = {"raster_bwd_persistent": 34.89e6, "raster_fwd_persistent": 18.18e6}
 
 
 def _dist_env():

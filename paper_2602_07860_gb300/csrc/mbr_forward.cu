@@ -675,27 +675,18 @@ __global__ void __launch_bounds__(kOrderThreads) unit_order_kernel(
   __shared__ int s_hist[kOrderBuckets];
   if (threadIdx.x < kOrderBuckets) s_hist[threadIdx.x] = 0;
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const unsigned below = (1u << lane) - 1u;
-  // lanes of a warp that share a bucket add their count once (warp-aggregated shared atomics:
-  // most units fall into a few buckets)
-  for (int u0 = 0; u0 < n_units; u0 += kOrderThreads) {
-    const int u = u0 + threadIdx.x;
-    const bool ok = u < n_units;
-    const unsigned act = __ballot_sync(0xffffffffu, ok);
-    if (ok) {
-      const int k = cost_in ? cost_bucket(cost_in[u])
-                            : unit_bucket(core_off, soft_off, G, n_tiles, tpu, n_patches, n_split, u);
-      bucket[u] = k;
-      if (cost_zero) cost_zero[u] = 0;  // may be cost_in: this thread has read it
-      if (cost_zero2) cost_zero2[u] = 0;
-      const unsigned peers = __match_any_sync(act, k);
-      if (lane == __ffs(peers) - 1) atomicAdd(&s_hist[k], __popc(peers));
-    }
+  for (int u = threadIdx.x; u < n_units; u += kOrderThreads) {
+    const int k = cost_in ? cost_bucket(cost_in[u])
+                          : unit_bucket(core_off, soft_off, G, n_tiles, tpu, n_patches, n_split, u);
+    bucket[u] = k;
+    atomicAdd(&s_hist[k], 1);
+    if (cost_zero) cost_zero[u] = 0;  // may be cost_in: this thread has read it
+    if (cost_zero2) cost_zero2[u] = 0;
   }
   __syncthreads();
   if (threadIdx.x < 32) {
     // lane l owns buckets 63 - 2l and 62 - 2l (descending order)
+    const int lane = threadIdx.x;
     const int a = s_hist[kOrderBuckets - 1 - 2 * lane], b = s_hist[kOrderBuckets - 2 - 2 * lane];
     int incl = a + b;
 #pragma unroll
@@ -708,20 +699,7 @@ __global__ void __launch_bounds__(kOrderThreads) unit_order_kernel(
     s_hist[kOrderBuckets - 2 - 2 * lane] = ex + a;
   }
   __syncthreads();
-  for (int u0 = 0; u0 < n_units; u0 += kOrderThreads) {
-    const int u = u0 + threadIdx.x;
-    const bool ok = u < n_units;
-    const unsigned act = __ballot_sync(0xffffffffu, ok);
-    if (ok) {
-      const int k = bucket[u];
-      const unsigned peers = __match_any_sync(act, k);
-      const int leader = __ffs(peers) - 1;
-      int base = 0;
-      if (lane == leader) base = atomicAdd(&s_hist[k], __popc(peers));
-      base = __shfl_sync(peers, base, leader);
-      order[base + __popc(peers & below)] = u;
-    }
-  }
+  for (int u = threadIdx.x; u < n_units; u += kOrderThreads) order[atomicAdd(&s_hist[bucket[u]], 1)] = u;
 }
 
 // ---------------------------------------------------------------- N_cand (measurement)
