@@ -131,9 +131,13 @@ int mbr_render_blur(mbr_ctx* ctx, const mbr_mesh* mesh, const mbr_motion* motion
                     float* image, void* cuda_stream);
 
 /* Adjoint of mbr_render_blur ("Gradient Computation", Sec. 3.3): given dL/dimage [H,W,4],
- * writes dL/dverts [V,3] (overwritten) and, if non-NULL, dL/dalbedo [V,3].  The forward state
- * of every sample is recomputed, not stored.  Discrete choices (coverage, z-test winner,
- * closest-point region, Lambert clamp) carry no gradient. */
+ * writes dL/dverts [V,3] (overwritten) and, if non-NULL, dL/dalbedo [V,3] (and, for a textured
+ * mesh with dl_dtexture set, the texel gradients).  It runs the forward raster first (into
+ * context scratch), which leaves per sample the winner face, or the log soft product and the
+ * count of vanishing factors; the adjoint kernel reads that and recomputes every sub-frame
+ * quantity it differentiates (barycentrics, depths, distances, closest points, shading).
+ * Discrete choices (coverage, z-test winner, closest-point region, Lambert clamp) carry no
+ * gradient. */
 int mbr_render_blur_backward(mbr_ctx* ctx, const mbr_mesh* mesh, const mbr_motion* motion,
                              const mbr_camera* camera, int32_t T, int32_t H, int32_t W,
                              int32_t solver, const float* dl_dimage, float* dl_dverts,
@@ -143,9 +147,9 @@ int mbr_render_blur_backward(mbr_ctx* ctx, const mbr_mesh* mesh, const mbr_motio
  * mbr_render_blur_backward (same arguments, same results), but when no other call has used the
  * context since that forward and every argument equals the forward's (the same mesh pointers and
  * sizes, motion, camera, T, H, W, solver and tuning), the forward's front half -- vertex states,
- * triangle records, tile bins, unit order -- is reused instead of recomputed, which also saves
- * the binning's stream synchronisation.  Otherwise it recomputes, exactly as
- * mbr_render_blur_backward.  The CALLER guarantees that the contents of verts, faces and albedo
+ * triangle records, tile bins, unit costs -- and its per-sample raster state are reused, which
+ * saves the front half, its stream synchronisation and the forward raster.  Otherwise it runs
+ * them, exactly as mbr_render_blur_backward.  The CALLER guarantees that the contents of verts, faces and albedo
  * have not changed since the forward (the library compares pointers, not contents); PyTorch's
  * saved-tensor version check gives that guarantee to the autograd path. */
 int mbr_render_blur_backward_reuse(mbr_ctx* ctx, const mbr_mesh* mesh, const mbr_motion* motion,
