@@ -36,8 +36,9 @@ WORKLOAD = ("rotation: icosphere subdiv 4 + SH degree 6 (2562 v, 5120 f), one tu
 CPU_WINDOW = (64, 64, 128, 128)   # bounded oracle sample for the CPU baseline (~15 s)
 REF_WINDOW = (120, 120, 16, 16)   # per-step oracle sample of the reference arm
 # DRAM bytes (read + write) per launch from the ncu captures summarised in profiles/ (tiles 8x8,
-# spt 1, this workload); to be refreshed (or set to None) whenever the kernels change
-NCU_DRAM_BYTES = {"raster_bwd_persistent": 34.89e6, "raster_fwd_persistent": 18.18e6}
+# this workload), by (kernel, sub-frames per thread); to be refreshed whenever the kernels change
+NCU_DRAM_BYTES = {("raster_bwd_persistent", 1): 34.89e6, ("raster_fwd_persistent", 1): 18.18e6,
+                  ("raster_bwd_persistent", 2): 33.99e6, ("raster_fwd_persistent", 2): 16.90e6}
 
 
 def _dist_env():
@@ -396,10 +397,10 @@ def main():
     backward_dominant = bwd_ms >= fwd_ms
     kern = "raster_bwd_persistent" if backward_dominant else "raster_fwd_persistent"
     achieved = bwd_tf if backward_dominant else fwd_tf
-    traffic = NCU_DRAM_BYTES.get(kern) if (tile, ctx_spt) == (8, 1) else None
+    traffic = NCU_DRAM_BYTES.get((kern, ctx_spt)) if tile == 8 else None
     roof = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
-            "traffic_note": "DRAM bytes per launch from ncu (profiles/), tiles 8x8 / spt 1",
+            "traffic_note": f"DRAM bytes per launch from ncu (profiles/), tiles 8x8, spt {ctx_spt}",
             "peak_note": f"{num_sms} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived from unit counts "
                          "and the maximum SM clock; no measured FP32 peak)",
             "work": roofline.describe("fast", units["n_box"], units["n_soft"], units["n_cov"], n_samples,
