@@ -33,8 +33,8 @@ METRIC = "pixel x sub-frame samples/s, fast solver forward+backward"
 UNIT = "samples/s"
 WORKLOAD = ("rotation: icosphere subdiv 4 + SH degree 6 (2562 v, 5120 f), one turn about a seeded axis, "
             "T=64, 256x256, 12 segments; step = forward + adjoint")
-CPU_WINDOW = (64, 64, 128, 128)   # bounded oracle sample for the CPU baseline (~15 s)
-REF_WINDOW = (120, 120, 16, 16)   # per-step oracle sample of the reference arm
+CPU_WINDOW = (64, 64, 128, 128)   # bounded oracle sample for the CPU baseline (~20 s on one core)
+REF_WINDOW = (96, 96, 64, 64)     # per-step oracle sample of the reference arm (all host cores)
 # DRAM bytes (read + write) per launch from the ncu captures summarised in profiles/ (tiles 8x8,
 # this workload), by (kernel, sub-frames per thread); to be refreshed whenever the kernels change
 NCU_DRAM_BYTES = {("raster_bwd_persistent", 1): 34.89e6, ("raster_fwd_persistent", 1): 18.18e6,
@@ -134,61 +134,92 @@ def _peaks():
         return {}
 
 
-def run_reference(args):
-    """Reference arm: the FP64 oracle (as it stands) on the host cores, each step a bounded window
-    of the same workload, forward + backward of the fast solver's definition."""
-    world, rank, _ = _dist_env()
-    if rank != 0:
-        return 0
+def _oracle_strip(job):
+    """One worker's share of an oracle timing: fast-mode forward + backward of rows [r0, r1) of the
+    window (x0, y0, w, h) of the rotation workload.  The loss gradient is the same seeded array for
+    any split, so the strips together do exactly the window's work."""
+    x0, y0, w, h, r0, r1 = job
     import numpy as np
 
     import oracle
     import scenes
-    oracle.build()
     sc = scenes.config2()
+    G = np.random.default_rng(7).normal(size=(h, w, 4))[r0:r1]
+    win = (x0, y0 + r0, w, r1 - r0)
+    t = time.perf_counter()
+    oracle.render(sc, "fast", window=win)
+    oracle.render_backward(sc, G, "fast", window=win)
+    return time.perf_counter() - t
+
+
+class OraclePool:
+    """The FP64 oracle, as it stands, on all host cores: one single-threaded worker process per
+    core (started with spawn, before any GPU work of this process), a window split into row
+    strips across them."""
+
+    def __init__(self, cores=None):
+        import multiprocessing as mp
+        import oracle
+        oracle.build()
+        self.cores = cores or os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        self.pool.map(_oracle_strip, [(0, 0, 1, 1, 0, 1)] * self.cores)  # import and load in every worker
+
+    def run(self, window):
+        x0, y0, w, h = window
+        n = min(self.cores, h)
+        cuts = [round(h * i / n) for i in range(n + 1)]
+        t = time.perf_counter()
+        self.pool.map(_oracle_strip, [(x0, y0, w, h, cuts[i], cuts[i + 1]) for i in range(n)])
+        return time.perf_counter() - t
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle (as it stands) on the host cores, each step a bounded window
+    of the same workload, forward + backward of the fast solver's definition, split across one
+    worker process per core."""
+    world, rank, _ = _dist_env()
+    if rank != 0:
+        return 0
+    import scenes
+    pool = OraclePool()
+    T = scenes.config2()["T"]
     x0, y0, w, h = REF_WINDOW
-    G = np.random.default_rng(7).normal(size=(h, w, 4))
-
-    def step():
-        oracle.render(sc, "fast", window=REF_WINDOW)
-        oracle.render_backward(sc, G, "fast", window=REF_WINDOW)
-
     for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    dt = time.perf_counter() - t0
-    samples = w * h * sc["T"] * args.steps
+        pool.run(REF_WINDOW)
+    dt = sum(pool.run(REF_WINDOW) for _ in range(args.steps))
+    pool.close()
+    samples = w * h * T * args.steps
     value = samples / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": f"{w}x{h} pixel window at ({x0},{y0}) per step",
-                       "parallelism": "single host thread"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{w}x{h} window x 64 sub-frames per step"},
+                       "parallelism": f"{pool.cores} host processes (one per core), row strips of the window"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+                             "sample": f"{w}x{h} window x {T} sub-frames per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def cpu_baseline():
-    import numpy as np
-
-    import oracle
+def cpu_baseline(pool):
+    """The oracle on the host cores: a window of the workload on every core (row strips), and the
+    same window on one core."""
     import scenes
-    oracle.build()
-    sc = scenes.config2()
+    T = scenes.config2()["T"]
     x0, y0, w, h = CPU_WINDOW
-    G = np.random.default_rng(7).normal(size=(h, w, 4))
-    t0 = time.perf_counter()
-    oracle.render(sc, "fast", window=CPU_WINDOW)
-    oracle.render_backward(sc, G, "fast", window=CPU_WINDOW)
-    dt = time.perf_counter() - t0
-    return {"value": w * h * sc["T"] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    dt_all = pool.run(CPU_WINDOW)
+    dt_one = _oracle_strip((x0, y0, w, h, 0, h))
+    n = w * h * T
+    return {"value": n / dt_all, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
             "sample": f"fast-mode forward+backward of a {w}x{h} window at ({x0},{y0}) of the same workload, "
-                      f"all 64 sub-frames, single thread, {dt:.1f} s"}
+                      f"all {T} sub-frames, {pool.cores} worker processes (row strips), {dt_all:.1f} s",
+            "single_core": {"value": n / dt_one, "cores": 1, "seconds": dt_one}}
 
 
 def extra_workloads(mbr, scenes, torch, np, world):
@@ -311,6 +342,9 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    world, rank, _ = _dist_env()
+    # the oracle's worker processes start before this process touches the GPU
+    cpu_pool = OraclePool() if rank == 0 and world == 1 and not args.no_cpu_baseline else None
 
     import numpy as np
     import torch
@@ -471,8 +505,9 @@ def main():
         extras.update(extra_workloads(mbr, scenes, torch, np, world))
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline()
+    if cpu_pool is not None:
+        cpu = cpu_baseline(cpu_pool)
+        cpu_pool.close()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
