@@ -101,7 +101,7 @@ __device__ __forceinline__ void soft_grad_accumulate(const float4 (&r)[kRecF4], 
         }
       }
       const float L2 = fmaf(Ex, Ex, Ey * Ey);
-      const float gt = (gtj - gti) / L2, t = sg.c.t;
+      const float gt = __fdividef(gtj - gti, L2), t = sg.c.t;
       gpx = gt * Ex;
       gpy = gt * Ey;
       const float gix = gt * (-Ex - Rx + 2.f * t * Ex), giy = gt * (-Ey - Ry + 2.f * t * Ey);
@@ -124,7 +124,7 @@ __device__ __forceinline__ void soft_grad_accumulate(const float4 (&r)[kRecF4], 
     }
     // w = N / D with D = N0 + N1 + N2
     const float sw = wv[0] * gw[0] + wv[1] * gw[1] + wv[2] * gw[2];
-    const float invD = 1.f / e.D;
+    const float invD = __fdividef(1.f, e.D);
     float ax[3], ay[3], ex[3], ey[3];
     rel_vertices<MOVING>(r, ps, tau, ax, ay);
     edge_backward((gw[0] - sw) * invD, (gw[1] - sw) * invD, (gw[2] - sw) * invD, ax, ay, ex, ey);
@@ -278,7 +278,7 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
     load_record<MOVING>(recs_set + f, r, persp, false);
     const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
     const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
-    const float invD = 1.0f / e.D;
+    const float invD = __fdividef(1.0f, e.D);
     const float wb[3] = {e.N0 * invD, e.N1 * invD, e.N2 * invD};  // screen-space barycentrics
     float w[3], iz[3], z[3] = {1.f, 1.f, 1.f};                     // attribute weights
     if (persp) depths_at<MOVING>(r, tau, z);
@@ -322,7 +322,7 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
       cbl = c[2];
     }
     const float len = sqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
-    const float dot = len > 0.f ? fmaf(nx, P.lx, fmaf(ny, P.ly, nz * P.lz)) / len : 0.f;
+    const float dot = len > 0.f ? __fdividef(fmaf(nx, P.lx, fmaf(ny, P.ly, nz * P.lz)), len) : 0.f;
     const float shade = fmaf(P.kd, fmaxf(dot, 0.f), P.ka);
     // I = c shade
     const float gcr = gr * shade, gcg = gg * shade, gcb = gb * shade;
@@ -352,7 +352,7 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
       }
     }
     if (len > 0.f && dot > 0.f) {
-      const float il = 1.f / len;
+      const float il = __fdividef(1.f, len);
       const float hx = nx * il, hy = ny * il, hz = nz * il;
       const float gx = P.kd * gshade * P.lx, gy = P.kd * gshade * P.ly, gz = P.kd * gshade * P.lz;
       const float hg = hx * gx + hy * gy + hz * gz;

@@ -515,7 +515,7 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
             load_record<MOVING>(recs_set + f, r, persp, false);
             const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
             const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
-            const float invD = 1.0f / e.D;
+            const float invD = __fdividef(1.0f, e.D);
             const float wb[3] = {e.N0 * invD, e.N1 * invD, e.N2 * invD};
             float w[3], iz[3], z[3] = {1.f, 1.f, 1.f};
             if (persp) depths_at<MOVING>(r, tau, z);
@@ -551,7 +551,7 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
               cb = c[2];
             }
             const float len = sqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
-            const float dot = len > 0.f ? fmaf(nx, P.lx, fmaf(ny, P.ly, nz * P.lz)) / len : 0.f;
+            const float dot = len > 0.f ? __fdividef(fmaf(nx, P.lx, fmaf(ny, P.ly, nz * P.lz)), len) : 0.f;
             const float shade = fmaf(P.kd, fmaxf(dot, 0.f), P.ka);
             acc_r = fmaf(cr, shade, acc_r);
             acc_g = fmaf(cg, shade, acc_g);

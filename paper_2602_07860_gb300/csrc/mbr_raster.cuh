@@ -238,7 +238,7 @@ __device__ __forceinline__ SoftGeom soft_geom(const float4* r, const PixelSetup<
     const float fx = (float)X;
     const float e1Xx = fmaf(fx, r[kR_D].x, r[kR_O].z), e1Xy = fmaf(fx, r[kR_D].y, r[kR_O].w);
     const float e2Xx = fmaf(fx, r[kR_D].z, r[kR_E2].x), e2Xy = fmaf(fx, r[kR_D].w, r[kR_E2].y);
-    const float invD = 1.0f / e.D;
+    const float invD = __fdividef(1.0f, e.D);
     g.w1 = e.N1 * invD;
     g.w2 = e.N2 * invD;
     g.ppx = fmaf(g.w1, e1Xx, g.w2 * e2Xx);
