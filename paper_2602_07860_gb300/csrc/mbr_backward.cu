@@ -159,7 +159,8 @@ __device__ __forceinline__ void soft_grad_accumulate(const float4 (&r)[kRecF4], 
 
 // pass 3 of the adjoint: gradient of alpha = 1 - prod_j (1 - A_j) w.r.t. the vertex positions of
 // every soft candidate.  A batch's pairs of one face sit on consecutive lanes: they are summed by
-// a segmented warp reduction and the first lane of each run adds them to the slot gradients.
+// a segmented warp reduction (as many halving steps as the batch's longest run needs) and the
+// first lane of each run adds them to the slot gradients.
 template <int SPT, bool MOVING>
 struct BwdSoftGradPairs {
   const TriRec* recs_set;
@@ -214,6 +215,9 @@ struct BwdSoftGradPairs {
     const uint32_t heads = __ballot_sync(kFullMask, head);
     const uint32_t above = lane == 31 ? 0u : (heads & (kFullMask << (lane + 1)));
     const int seg_end = above ? __ffs(above) - 1 : 32;
+    // lanes without a pair (face < 0) trail the batch: a run ends at the last lane with a pair
+    const int n_valid = __popc(__ballot_sync(kFullMask, face >= 0));
+    const int longest = __reduce_max_sync(kFullMask, head ? min(seg_end, n_valid) - lane : 0);
     constexpr int NV = MOVING ? 12 : 6;
     float vals[NV];
 #pragma unroll
@@ -226,7 +230,7 @@ struct BwdSoftGradPairs {
       }
     }
 #pragma unroll 1
-    for (int o = 1; o < 32; o <<= 1) {
+    for (int o = 1; o < longest; o <<= 1) {
       const bool take = lane + o < seg_end;
 #pragma unroll
       for (int q = 0; q < NV; ++q) {

@@ -5,9 +5,24 @@ import torch
 
 import oracle
 import paper_2602_07860_gb300 as mbr
+import scenes
 
 ORACLE_MODE = {"plain": "exact", "fast": "fast"}
 TOL = 1e-4  # absolute, intensities in [0, 1]
+
+
+def degenerate_scene():
+    """A rotating sphere plus three degenerate faces: a repeated vertex and three collinear
+    vertices (both zero area), and a duplicate of face 5 (exact depth ties)."""
+    sc = scenes.small_scene("rotate", subdiv=3, T=8, H=40, W=52)
+    v, f, a = sc["verts"], sc["faces"], sc["albedo"]
+    mid = 0.5 * (v[f[0, 0]] + v[f[0, 1]])  # a vertex on the first face's first edge
+    m = len(v)
+    extra = np.array([[f[0, 0], f[0, 0], f[0, 1]],
+                      [f[0, 0], m, f[0, 1]],
+                      f[5]], dtype=np.int32)
+    return dict(sc, verts=np.vstack([v, mid[None, :]]), albedo=np.vstack([a, a[:1]]),
+                faces=np.vstack([f, extra]).astype(np.int32))
 
 
 def gpu_inputs(sc):

@@ -8,7 +8,7 @@ import torch
 
 import oracle
 import scenes
-from gpu_util import ORACLE_MODE, gpu_inputs
+from gpu_util import ORACLE_MODE, degenerate_scene, gpu_inputs
 
 pytestmark = pytest.mark.gpu
 
@@ -56,6 +56,8 @@ GRAD_SCENES = {
     "rotate_sigmoid_prob": lambda: dict(scenes.small_scene("rotate", subdiv=1, T=6, H=32, W=40),
                                         camera=scenes.camera(scenes.look_at((0, 0, -4)), delta=2e-3, prob="sigmoid")),
     "static_zero_motion": lambda: scenes.small_scene("translate", subdiv=2, T=6, H=36, W=44, d=(0.0, 0.0, 0.0)),
+    # zero-area faces and a duplicated face (the oracle flags the exact depth ties as ambiguous)
+    "degenerate_faces": degenerate_scene,
     "rotate_perspective_attrs": lambda: dict(
         scenes.small_scene("rotate", subdiv=2, T=8, H=40, W=48),
         camera=scenes.camera(scenes.look_at((0.4, 0.3, -2.6)), fov_deg=60.0, interp="perspective")),

@@ -13,7 +13,7 @@ import torch
 
 import oracle
 import scenes
-from gpu_util import ORACLE_MODE, TOL, compare_images, gpu_inputs, gpu_render
+from gpu_util import ORACLE_MODE, TOL, compare_images, degenerate_scene, gpu_inputs, gpu_render
 
 pytestmark = pytest.mark.gpu
 
@@ -35,19 +35,6 @@ def _check(ctx, sc, solver, max_flag_frac=0.05):
     return r, g
 
 
-def _degenerate_scene():
-    sc = scenes.small_scene("rotate", subdiv=3, T=8, H=40, W=52)
-    v, f, a = sc["verts"], sc["faces"], sc["albedo"]
-    mid = 0.5 * (v[f[0, 0]] + v[f[0, 1]])  # a vertex on the first face's first edge
-    v2 = np.vstack([v, mid[None, :]])
-    a2 = np.vstack([a, a[:1]])
-    m = len(v)
-    extra = np.array([[f[0, 0], f[0, 0], f[0, 1]],     # repeated vertex: zero area
-                      [f[0, 0], m, f[0, 1]],           # collinear vertices: zero area
-                      f[5]], dtype=np.int32)           # duplicate of face 5
-    return dict(sc, verts=v2, albedo=a2, faces=np.vstack([f, extra]).astype(np.int32))
-
-
 SCENES = {
     "c1_translate_64": lambda: scenes.config1(),
     "rotate_ragged_72x40": lambda: scenes.small_scene("rotate", subdiv=2, T=8, H=40, W=72),
@@ -66,7 +53,7 @@ SCENES = {
     "static_zero_motion": lambda: scenes.small_scene("translate", subdiv=2, T=6, H=36, W=44, d=(0.0, 0.0, 0.0)),
     # degenerate input: zero-area faces (a repeated vertex, three collinear vertices) and a
     # duplicated face (exact depth ties, resolved to the smaller id)
-    "degenerate_faces": lambda: _degenerate_scene(),
+    "degenerate_faces": degenerate_scene,
     # soft band far below a pixel (delta 1e-6) and far above it (delta 1e-2)
     "rotate_tiny_delta": lambda: dict(scenes.small_scene("rotate", subdiv=2, T=6, H=40, W=48),
                                       camera=scenes.camera(scenes.look_at((0, 0, -4)), delta=1e-6)),
