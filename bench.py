@@ -37,8 +37,8 @@ CPU_WINDOW = (64, 64, 128, 128)   # bounded oracle sample for the CPU baseline (
 REF_WINDOW = (96, 96, 64, 64)     # per-step oracle sample of the reference arm (all host cores)
 # DRAM bytes (read + write) per launch from the ncu captures summarised in profiles/ (tiles 8x8,
 # this workload), by (kernel, sub-frames per thread); to be refreshed whenever the kernels change
-NCU_DRAM_BYTES = {("raster_bwd_persistent", 1): 34.88e6, ("raster_fwd_persistent", 1): 18.18e6,
-                  ("raster_bwd_persistent", 2): 34.09e6, ("raster_fwd_persistent", 2): 16.90e6}
+NCU_DRAM_BYTES = {("raster_bwd_persistent", 1): 34.93e6, ("raster_fwd_persistent", 1): 18.18e6,
+                  ("raster_bwd_persistent", 2): 33.98e6, ("raster_fwd_persistent", 2): 16.90e6}
 
 
 def _dist_env():

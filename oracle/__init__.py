@@ -22,7 +22,7 @@ import numpy as np
 from .build import build, library_path
 
 MODES = {"exact": 0, "linear": 1, "fast": 2}
-SOFT_ALL = 1
+SOFT_ALL, SOFT32 = 1, 2
 CNT_CAND, CNT_COVERED, CNT_AMBIG, CNT_HASH, CNT_SOFT, CNT_SOFT32 = 0, 1, 2, 3, 4, 5
 AMB_COVER, AMB_DEPTH, AMB_DEGEN, AMB_REGION, AMB_CLAMP, AMB_LAMBERT, AMB_COND = 1, 2, 4, 8, 16, 32, 64
 AMB_TEXCELL = 128  # gradient only: a textured sample near a texel-centre line (the bilinear slope jumps)
@@ -168,8 +168,14 @@ def closest_point(tri, px, py):
     return d2, w, reg.value
 
 
-def render(sc, mode="fast", window=None, soft_all=False, winners=False, ambig=False):
-    """Blurred RGBA image of ``sc`` (or of ``window`` = (x0, y0, w, h)).
+def _flags(soft_all, soft32):
+    return (SOFT_ALL if soft_all else 0) | (SOFT32 if soft32 else 0)
+
+
+def render(sc, mode="fast", window=None, soft_all=False, winners=False, ambig=False, soft32=False):
+    """Blurred RGBA image of ``sc`` (or of ``window`` = (x0, y0, w, h)).  ``soft_all``: no soft
+    truncation; ``soft32``: truncation at the single-precision cutoff (factors with
+    exp(-d/delta) <= 2^-25 dropped) instead of d <= delta ln 1e12.
 
     Returns dict(rgba [h,w,4] f64, winners [T,h,w] i32 | None, ambig [T,h,w] u8 | None,
     counters [8] i64)."""
@@ -180,7 +186,7 @@ def render(sc, mode="fast", window=None, soft_all=False, winners=False, ambig=Fa
     win = np.zeros((T, h, w), dtype=np.int32) if winners else None
     amb = np.zeros((T, h, w), dtype=np.uint8) if ambig else None
     cnt = np.zeros(8, dtype=np.int64)
-    rc = lib().orc_render(S.ref, MODES[mode], SOFT_ALL if soft_all else 0, x0, y0, w, h,
+    rc = lib().orc_render(S.ref, MODES[mode], _flags(soft_all, soft32), x0, y0, w, h,
                           _ptr(rgba, c_double), _ptr(win, c_int32), _ptr(amb, c_uint8),
                           _ptr(cnt, c_int64))
     if rc != 0:
@@ -188,8 +194,9 @@ def render(sc, mode="fast", window=None, soft_all=False, winners=False, ambig=Fa
     return dict(rgba=rgba, winners=win, ambig=amb, counters=cnt)
 
 
-def render_backward(sc, dl_drgba, mode="fast", window=None, soft_all=False, texture_grad=None):
-    """(dL/dverts [V,3], dL/dalbedo [V,3], counters) for the loss gradient ``dl_drgba`` [h,w,4].
+def render_backward(sc, dl_drgba, mode="fast", window=None, soft_all=False, texture_grad=None, soft32=False):
+    """(dL/dverts [V,3], dL/dalbedo [V,3], counters) for the loss gradient ``dl_drgba`` [h,w,4]
+    (``soft_all``, ``soft32``: the truncation, as in ``render``).
     For a textured scene, ``texture_grad`` (an array shaped like the texture) receives
     dL/dtexture."""
     S = _Scene(sc)
@@ -198,7 +205,7 @@ def render_backward(sc, dl_drgba, mode="fast", window=None, soft_all=False, text
     gv = np.zeros((S.s.V, 3))
     ga = np.zeros((S.s.V, 3))
     cnt = np.zeros(8, dtype=np.int64)
-    rc = lib().orc_render_backward(S.ref, MODES[mode], SOFT_ALL if soft_all else 0, x0, y0, w, h,
+    rc = lib().orc_render_backward(S.ref, MODES[mode], _flags(soft_all, soft32), x0, y0, w, h,
                                    _ptr(g, c_double), _ptr(gv, c_double), _ptr(ga, c_double),
                                    _ptr(cnt, c_int64))
     if rc != 0:

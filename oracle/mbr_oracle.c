@@ -436,7 +436,7 @@ static int render_impl(const orc_scene* s, int32_t mode, int32_t flags, int32_t 
     return -1;
   const int32_t V = s->V, F = s->F, T = s->T, S = orc_num_segments(s);
   const size_t npix = (size_t)w * (size_t)h;
-  const double r2 = s->delta * log(1e12), r = sqrt(r2);
+  const double r2 = (flags & ORC_SOFT32) ? s->delta * 25.0 * log(2.0) : s->delta * log(1e12), r = sqrt(r2);
   const int soft_all = (flags & ORC_SOFT_ALL) != 0;
   const int backward = dl != NULL;
   double Ld[3] = {s->light_dir[0], s->light_dir[1], s->light_dir[2]};

@@ -57,7 +57,11 @@ typedef struct {
 } orc_scene;
 
 enum { ORC_PLAIN_EXACT = 0, ORC_PLAIN_LINEAR = 1, ORC_FAST_REF = 2 };
-enum { ORC_SOFT_ALL = 1 };  /* flag: no soft-coverage truncation, every triangle at every pixel */
+/* flags: ORC_SOFT_ALL no soft-coverage truncation, every triangle at every pixel; ORC_SOFT32 the
+ * single-precision truncation instead of d <= delta ln 1e12: keep a factor only while
+ * exp(-d/delta) > 2^-25, i.e. d < delta 25 ln 2 (below it 1 - A rounds to 1 in single precision,
+ * so an FP32 product cannot see the factor; the adjoint of that product has no term for it) */
+enum { ORC_SOFT_ALL = 1, ORC_SOFT32 = 2 };
 
 /* counters[] written by orc_render / orc_render_backward */
 enum {

@@ -1,5 +1,7 @@
 """CUDA adjoint (mbr_render_blur_backward) vs the oracle's FP64 adjoint, which is itself pinned
-to central finite differences.  dL/dimage is zeroed on pixels whose samples the oracle flags as
+to central finite differences.  The oracle runs with the kernels' single-precision soft truncation
+(soft32: factors with exp(-d/delta) <= 2^-25 dropped, the ones an FP32 product cannot see), so
+both sides differentiate the same function.  dL/dimage is zeroed on pixels whose samples the oracle flags as
 ambiguous for FP32 (any flag, including the gradient-only ones), so both sides differentiate the
 same discrete choices.  Bound: per-vertex |g_gpu - g_oracle|_2 <= 1e-3 |g_oracle|_2 + 1e-6 max."""
 import numpy as np
@@ -21,11 +23,11 @@ def ctx():
 
 def _grad_check(ctx, sc, solver, seed=0, rel=1e-3):
     mode = ORACLE_MODE[solver]
-    r = oracle.render(sc, mode, ambig=True)
+    r = oracle.render(sc, mode, ambig=True, soft32=True)
     rng = np.random.default_rng(seed)
     G = rng.normal(size=(sc["H"], sc["W"], 4))
     G[(r["ambig"] != 0).any(0)] = 0.0
-    gv_o, ga_o, _ = oracle.render_backward(sc, G, mode)
+    gv_o, ga_o, _ = oracle.render_backward(sc, G, mode, soft32=True)
     v, f, a, mo, ca = gpu_inputs(sc)
     gv, ga = ctx.render_blur_backward(v, f, a, mo, ca, sc["T"], sc["H"], sc["W"],
                                       torch.as_tensor(G, dtype=torch.float32, device="cuda"), solver)
@@ -58,6 +60,9 @@ GRAD_SCENES = {
     "static_zero_motion": lambda: scenes.small_scene("translate", subdiv=2, T=6, H=36, W=44, d=(0.0, 0.0, 0.0)),
     # zero-area faces and a duplicated face (the oracle flags the exact depth ties as ambiguous)
     "degenerate_faces": degenerate_scene,
+    # one-pixel-wide images: every tile is ragged
+    "strip_1x37": lambda: scenes.small_scene("rotate", subdiv=2, T=8, H=1, W=37),
+    "strip_41x1": lambda: scenes.small_scene("rotate", subdiv=2, T=8, H=41, W=1),
     "rotate_perspective_attrs": lambda: dict(
         scenes.small_scene("rotate", subdiv=2, T=8, H=40, W=48),
         camera=scenes.camera(scenes.look_at((0.4, 0.3, -2.6)), fov_deg=60.0, interp="perspective")),
@@ -68,6 +73,23 @@ GRAD_SCENES = {
 @pytest.mark.parametrize("name", sorted(GRAD_SCENES))
 def test_adjoint_matches_oracle(ctx, name, solver):
     _grad_check(ctx, GRAD_SCENES[name](), solver)
+
+
+@pytest.mark.parametrize("solver", ["plain", "fast"])
+def test_adjoint_is_zero_without_visible_geometry_or_loss(ctx, solver):
+    """No faces, a mesh far outside the view, or a zero dL/dimage: both gradients are exactly zero
+    (and the buffers the call overwrites hold no stale values)."""
+    sc = scenes.small_scene("translate", subdiv=1, T=4, H=20, W=24)
+    G = torch.randn((sc["H"], sc["W"], 4), device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+    cases = [(dict(sc, faces=np.zeros((0, 3), dtype=np.int32)), G),
+             (dict(sc, verts=sc["verts"] + np.array([50.0, 0.0, 0.0])), G),
+             (sc, torch.zeros_like(G))]
+    for case, g in cases:
+        v, f, a, mo, ca = gpu_inputs(case)
+        gv, ga = ctx.render_blur_backward(v, f, a, mo, ca, case["T"], case["H"], case["W"], g, solver)
+        torch.cuda.synchronize()
+        assert gv.shape == v.shape and ga.shape == a.shape
+        assert float(gv.abs().max()) == 0.0 and float(ga.abs().max()) == 0.0
 
 
 @pytest.mark.parametrize("solver", ["plain", "fast"])
@@ -99,11 +121,11 @@ def test_full_size_rotation_gradient_window(ctx, x0, y0):
     target = dict(sc, verts=sc["verts"] * 1.02)
     for solver in ("fast", "plain"):
         mode = ORACLE_MODE[solver]
-        r = oracle.render(sc, mode, window=(x0, y0, w, h), ambig=True)
-        tgt = oracle.render(target, mode, window=(x0, y0, w, h))["rgba"]
+        r = oracle.render(sc, mode, window=(x0, y0, w, h), ambig=True, soft32=True)
+        tgt = oracle.render(target, mode, window=(x0, y0, w, h), soft32=True)["rgba"]
         Gw = 2.0 * (r["rgba"] - tgt)
         Gw[(r["ambig"] != 0).any(0)] = 0.0
-        gv_o, _, _ = oracle.render_backward(sc, Gw, mode, window=(x0, y0, w, h))
+        gv_o, _, _ = oracle.render_backward(sc, Gw, mode, window=(x0, y0, w, h), soft32=True)
         G = np.zeros((sc["H"], sc["W"], 4))
         G[y0:y0 + h, x0:x0 + w] = Gw
         v, f, a, mo, ca = gpu_inputs(sc)

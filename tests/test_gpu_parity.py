@@ -35,6 +35,10 @@ def _check(ctx, sc, solver, max_flag_frac=0.05):
     return r, g
 
 
+def _off_axis(sc):
+    return dict(sc, camera=scenes.camera(scenes.look_at((0.13, 0.07, -4))))
+
+
 SCENES = {
     "c1_translate_64": lambda: scenes.config1(),
     "rotate_ragged_72x40": lambda: scenes.small_scene("rotate", subdiv=2, T=8, H=40, W=72),
@@ -59,6 +63,12 @@ SCENES = {
                                       camera=scenes.camera(scenes.look_at((0, 0, -4)), delta=1e-6)),
     "rotate_wide_delta": lambda: dict(scenes.small_scene("rotate", subdiv=1, T=4, H=32, W=40),
                                       camera=scenes.camera(scenes.look_at((0, 0, -4)), delta=1e-2)),
+    # one-pixel images and strips: every tile is ragged.  The camera looks slightly off the
+    # optical axis, so the pixel row / column does not run along the mesh's vertices and edges
+    # (on the axis most of its samples are flagged as FP32-ambiguous)
+    "pixel_1x1_off_axis": lambda: _off_axis(scenes.small_scene("rotate", subdiv=2, T=8, H=1, W=1)),
+    "strip_1x37_off_axis": lambda: _off_axis(scenes.small_scene("rotate", subdiv=2, T=8, H=1, W=37)),
+    "strip_41x1_off_axis": lambda: _off_axis(scenes.small_scene("rotate", subdiv=2, T=8, H=41, W=1)),
     # perspective-correct attribute weights, camera close to the mesh (strong depth variation)
     "translate_perspective_attrs": lambda: dict(
         scenes.small_scene("translate", subdiv=2, T=10, H=44, W=60, d=(0.8, -0.2, 1.0)),

@@ -52,12 +52,12 @@ def test_textured_forward_matches_oracle(ctx, name, solver):
 def test_textured_adjoint_matches_oracle(ctx, name, solver, rel=1e-3):
     sc = SCENES[name]()
     mode = ORACLE_MODE[solver]
-    r = oracle.render(sc, mode, ambig=True)
+    r = oracle.render(sc, mode, ambig=True, soft32=True)  # the kernels' soft truncation
     rng = np.random.default_rng(3)
     G = rng.normal(size=(sc["H"], sc["W"], 4))
     G[(r["ambig"] != 0).any(0)] = 0.0
     gt_o = np.zeros_like(np.asarray(sc["texture"], dtype=np.float64))
-    gv_o, _, _ = oracle.render_backward(sc, G, mode, texture_grad=gt_o)
+    gv_o, _, _ = oracle.render_backward(sc, G, mode, texture_grad=gt_o, soft32=True)
     v, f, a, mo, ca = gpu_inputs(sc)
     uv, tex = _tex(sc)
     gv, _, gt = ctx.render_blur_backward(v, f, a, mo, ca, sc["T"], sc["H"], sc["W"],

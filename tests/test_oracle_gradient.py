@@ -27,11 +27,21 @@ def _scene(kind, delta, prob="exp", interp="screen"):
 def test_adjoint_matches_central_differences(mode, kind, delta, prob, interp):
     """prob 'sigmoid' is the SoftRas probability map (dA/dd = -A (1 - A) / delta); interp
     'perspective' the perspective-correct attribute weights (gradients also reach the depths)."""
-    sc = _scene(kind, delta, prob, interp)
+    _fd_check(_scene(kind, delta, prob, interp), mode)
+
+
+@pytest.mark.parametrize("mode,kind", [("exact", "rotate"), ("fast", "rotate"), ("fast", "translate")])
+def test_single_precision_truncated_adjoint_matches_central_differences(mode, kind):
+    """With soft32 (factors with exp(-d/delta) <= 2^-25 dropped, the kernels' truncation) the
+    adjoint is still the exact derivative of the truncated forward."""
+    _fd_check(_scene(kind, 1e-4), mode, soft32=True)
+
+
+def _fd_check(sc, mode, **kw):
     rng = np.random.default_rng(17)
     G = rng.normal(size=(sc["H"], sc["W"], 4))
-    gv, ga, _ = oracle.render_backward(sc, G, mode)
-    _, h0 = _loss(sc, G, mode)
+    gv, ga, _ = oracle.render_backward(sc, G, mode, **kw)
+    _, h0 = _loss(sc, G, mode, **kw)
     h = 1e-6
     V = len(sc["verts"])
     coords = [(int(v), int(c)) for v, c in zip(rng.integers(0, V, 40), rng.integers(0, 3, 40))]
@@ -42,8 +52,8 @@ def test_adjoint_matches_central_differences(mode, kind, delta, prob, interp):
         minus = dict(sc, verts=sc["verts"].copy())
         plus["verts"][v, c] += h
         minus["verts"][v, c] -= h
-        lp, hp = _loss(plus, G, mode)
-        lm, hm = _loss(minus, G, mode)
+        lp, hp = _loss(plus, G, mode, **kw)
+        lm, hm = _loss(minus, G, mode, **kw)
         if hp != h0 or hm != h0:
             continue  # a discrete choice changed inside [-h, h]
         fd = (lp - lm) / (2 * h)
@@ -54,8 +64,8 @@ def test_adjoint_matches_central_differences(mode, kind, delta, prob, interp):
     for v, c in coords[:10]:
         plus = dict(sc, albedo=sc["albedo"].copy())
         plus["albedo"][v, c] += 1.0
-        lp, _ = _loss(plus, G, mode)
-        l0, _ = _loss(sc, G, mode)
+        lp, _ = _loss(plus, G, mode, **kw)
+        l0, _ = _loss(sc, G, mode, **kw)
         assert abs((lp - l0) - ga[v, c]) < 1e-9 * max(1.0, abs(ga[v, c]))
 
 

@@ -448,6 +448,23 @@ def test_soft_truncation_bound():
         assert np.max(np.abs(a - b)) <= len(sc["faces"]) * 1e-12 + 1e-15
 
 
+def test_single_precision_truncation():
+    """soft32 keeps exactly the soft factors above 2^-25: covered samples and colour are untouched
+    (RGB identical), alpha moves by at most F 2^-25, every term the single-precision counter sees
+    is kept, and no term beyond it is."""
+    sc = scenes.small_scene("rotate", subdiv=1, T=4, H=20, W=26)
+    for mode in ("exact", "fast"):
+        a = oracle.render(sc, mode)
+        b = oracle.render(sc, mode, soft32=True)
+        assert np.array_equal(a["rgba"][..., :3], b["rgba"][..., :3])
+        gap = np.max(np.abs(a["rgba"][..., 3] - b["rgba"][..., 3]))
+        assert 0.0 < gap <= len(sc["faces"]) * 2.0 ** -25
+        ca, cb = a["counters"], b["counters"]
+        assert cb[oracle.CNT_SOFT32] == ca[oracle.CNT_SOFT32]
+        assert cb[oracle.CNT_SOFT32] <= cb[oracle.CNT_SOFT] < ca[oracle.CNT_SOFT]
+        assert cb[oracle.CNT_COVERED] == ca[oracle.CNT_COVERED]
+
+
 # ----------------------------------------------------------------------------- brute force
 
 def _seg_min_ternary(a, b, p, iters=100):
