@@ -17,6 +17,7 @@ Under torchrun (N > 1) every rank renders its own replica (no collective on the 
 timing is the max over ranks and the value is the aggregate.
 """
 import argparse
+import datetime
 import json
 import math
 import os
@@ -35,6 +36,13 @@ WORKLOAD = ("rotation: icosphere subdiv 4 + SH degree 6 (2562 v, 5120 f), one tu
             "T=64, 256x256, 12 segments; step = forward + adjoint")
 CPU_WINDOW = (64, 64, 128, 128)   # bounded oracle sample for the CPU baseline (~20 s on one core)
 REF_WINDOW = (96, 96, 64, 64)     # per-step oracle sample of the reference arm (all host cores)
+
+
+def ref_window(steps):
+    """The reference arm's per-step window: REF_WINDOW up to 200 steps, fewer rows beyond (at least
+    16), so that a long --steps run still ends within a few minutes."""
+    x0, y0, w, h = REF_WINDOW
+    return (x0, y0, w, h if steps <= 200 else max(16, h * 200 // steps))
 # DRAM bytes (read + write) per launch from the ncu captures summarised in profiles/ (tiles 8x8,
 # this workload), by (kernel, sub-frames per thread); to be refreshed whenever the kernels change
 NCU_DRAM_BYTES = {("raster_bwd_persistent", 1): 34.93e6, ("raster_fwd_persistent", 1): 18.18e6,
@@ -88,19 +96,34 @@ class Replicas:
 
 
 def _clock_sampler():
+    """nvidia-smi sampling the clocks and throttle reasons every 200 ms into a temporary file;
+    returns once the first sample is written (or after 5 s), so that the timed region that follows
+    is covered from its start."""
     try:
         f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-             "clocks_event_reasons.sw_power_cap")
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
                              stdout=f, stderr=subprocess.DEVNULL)
+        t_end = time.time() + 5.0
+        while time.time() < t_end and p.poll() is None and os.path.getsize(f.name) == 0:
+            time.sleep(0.02)
         return p, f.name
     except Exception:
         return None, None
 
 
-def _clock_summary(proc, path, index):
+def _sample_time(stamp):
+    try:
+        return datetime.datetime.strptime(stamp, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+    except ValueError:
+        return None
+
+
+def _clock_summary(proc, path, index, t0=None, t1=None):
+    """Median SM clock, maximum SM clock and the throttle reasons seen by the samples taken between
+    t0 and t1 (time.time() around the timed region); all samples if none falls inside."""
     if proc is None:
         return None
     proc.terminate()
@@ -112,19 +135,23 @@ def _clock_summary(proc, path, index):
     try:
         for line in open(path):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9 and parts[0] == str(index):
+            if len(parts) >= 10 and parts[1] == str(index):
                 rows.append(parts)
         os.unlink(path)
     except Exception:
         return None
     if not rows:
         return None
-    sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
-    mx = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+    inside = [r for r in rows if t0 is not None and (_sample_time(r[0]) or 0.0) >= t0 and
+              (_sample_time(r[0]) or 0.0) <= t1]
+    use = inside or rows
+    sm = [float(r[2]) for r in use if r[2].replace(".", "", 1).isdigit()]
+    mx = [float(r[3]) for r in use if r[3].replace(".", "", 1).isdigit()]
     names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-    reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+    reasons = sorted({names[i] for r in use for i in range(4) if r[6 + i].lower() == "active"})
     return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-            "reasons": reasons, "samples": len(rows)}
+            "reasons": reasons, "samples": len(use), "samples_in_timed_region": len(inside),
+            "timed_region_s": None if t0 is None else round(t1 - t0, 3)}
 
 
 def _peaks():
@@ -188,10 +215,11 @@ def run_reference(args):
     import scenes
     pool = OraclePool()
     T = scenes.config2()["T"]
-    x0, y0, w, h = REF_WINDOW
+    win = ref_window(args.steps)
+    x0, y0, w, h = win
     for _ in range(args.warmup):
-        pool.run(REF_WINDOW)
-    dt = sum(pool.run(REF_WINDOW) for _ in range(args.steps))
+        pool.run(win)
+    dt = sum(pool.run(win) for _ in range(args.steps))
     pool.close()
     samples = w * h * T * args.steps
     value = samples / dt
@@ -332,7 +360,8 @@ def extra_workloads(mbr, scenes, torch, np, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    # 600 timed steps take about 0.65 s: three or more clock samples at the sampler's 200 ms
+    ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mbr", choices=["mbr", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -386,10 +415,12 @@ def main():
         if bwd:
             ctx.render_blur_backward(v, f, a, mo, ca, T, H, W, G, solver, reuse_forward=True)
 
-    def timed(solver, bwd, steps, warmup):
+    def timed(solver, bwd, steps, warmup, t_region=None):
         for _ in range(warmup):
             step(solver, bwd)
         barrier()
+        if t_region is not None:
+            t_region[0] = time.time()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         for e0, e1 in ev:
             flush.zero_()
@@ -397,14 +428,17 @@ def main():
             step(solver, bwd)
             e1.record()
         barrier()
+        if t_region is not None:
+            t_region[1] = time.time()
         return sum(e0.elapsed_time(e1) for e0, e1 in ev)
 
     # ---- headline: fast solver forward + backward, raster kernels timed by events in the library
     l0 = ctx.stats()["launches"]
     ctx.set_profiling(True)
     proc, path = _clock_sampler() if rank == 0 else (None, None)
-    total_ms = timed("fast", True, args.steps, args.warmup)
-    clocks = _clock_summary(proc, path, local) if rank == 0 else None
+    t_region = [0.0, 0.0]
+    total_ms = timed("fast", True, args.steps, args.warmup, t_region)
+    clocks = _clock_summary(proc, path, local, *t_region) if rank == 0 else None
     st = ctx.stats()
     ctx.set_profiling(False)
     launches = (st["launches"] - l0) * args.steps // (args.steps + args.warmup)
