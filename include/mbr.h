@@ -137,7 +137,8 @@ int mbr_render_blur(mbr_ctx* ctx, const mbr_mesh* mesh, const mbr_motion* motion
  * count of vanishing factors; the adjoint kernel reads that and recomputes every sub-frame
  * quantity it differentiates (barycentrics, depths, distances, closest points, shading).
  * Discrete choices (coverage, z-test winner, closest-point region, Lambert clamp) carry no
- * gradient. */
+ * gradient.  It is the derivative of the single-precision image the forward computes: soft
+ * factors with exp(-d/delta) <= 2^-25, which leave that image unchanged, contribute nothing. */
 int mbr_render_blur_backward(mbr_ctx* ctx, const mbr_mesh* mesh, const mbr_motion* motion,
                              const mbr_camera* camera, int32_t T, int32_t H, int32_t W,
                              int32_t solver, const float* dl_dimage, float* dl_dverts,
