@@ -45,6 +45,11 @@ def ref_window(steps):
     return (x0, y0, w, h if steps <= 200 else max(16, h * 200 // steps))
 # DRAM bytes (read + write) per launch from the ncu captures summarised in profiles/ (tiles 8x8,
 # this workload), by (kernel, sub-frames per thread); to be refreshed whenever the kernels change
+# Pipe utilisation (% of active cycles) and issue-active share of the fast raster kernels at tiles
+# 8x8, from one `ncu --set full` capture each on this workload (summaries in profiles/): the
+# counter view of the roofline fraction next to the credited-flops view.
+NCU_PIPES = {"raster_bwd_persistent": {"fma": 19.7, "alu": 27.3, "xu": 4.5, "lsu": 22.2, "issue_active": 43.0},
+             "raster_fwd_persistent": {"fma": 20.0, "alu": 32.3, "xu": 8.2, "lsu": 21.7, "issue_active": 49.8}}
 NCU_DRAM_BYTES = {("raster_bwd_persistent", 1): 34.93e6, ("raster_fwd_persistent", 1): 18.18e6,
                   ("raster_bwd_persistent", 2): 33.98e6, ("raster_fwd_persistent", 2): 16.90e6}
 
@@ -475,7 +480,8 @@ def main():
                                       backward_dominant),
             "flops_per_launch": bwf if backward_dominant else fwf,
             "kernel_ms": bwd_ms if backward_dominant else fwd_ms, "raster_fwd_ms": fwd_ms, "raster_bwd_ms": bwd_ms,
-            "fwd_frac": fwd_tf / peak, "bwd_frac": bwd_tf / peak, "units": units}
+            "fwd_frac": fwd_tf / peak, "bwd_frac": bwd_tf / peak, "units": units,
+            "ncu_pipes_pct": NCU_PIPES.get(kern) if tile == 8 else None}
 
     # ---- plain per-sub-frame solver and forward-only numbers on the same GPU
     k2 = max(3, args.steps // 2)
