@@ -536,6 +536,10 @@ def main():
         torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     barrier()
+    # untimed: the overlapped read-back delivered the image of the step
+    check = ctx.render_blur(v, f, a, mo, ca, T, H, W, "fast").cpu()
+    if not torch.allclose(out_img, check, atol=1e-6, rtol=0.0):
+        raise RuntimeError("end-to-end step: the image read back differs from a fresh render")
     h2d = sum(t.numel() * t.element_size() for t in (hv, hf, ha, hG))
     d2h = sum(t.numel() * t.element_size() for t in (out_img, out_gv, out_ga))
     e2e = {"value": world * n_samples * k2 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
