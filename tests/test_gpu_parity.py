@@ -24,7 +24,17 @@ def ctx():
     return mbr.Context()
 
 
-def _check(ctx, sc, solver, max_flag_frac=0.05):
+# Fraction of pixels with an FP32-ambiguous sample (a property of the oracle's scene alone), as
+# measured per scene and solver: at most 1% everywhere except where the scene makes ties on
+# purpose or crowds edges.  The degenerate scene's duplicated face ties on every pixel it covers;
+# the 96 x 80 subdiv-4 render has about 5000 faces over 7680 pixels (plain 1.21%, fast 0.90%),
+# and the depth-moving translation gives keyframe closest-feature ties to the fast solver
+# (1.45%).  Bounds sit just above the measurement, so more flagged pixels than the scene's
+# own fail the test.
+FLAG_FRAC = {"degenerate_faces": 0.033, "subdiv4_sh_96x80": 0.0125, "translate_depth_motion": 0.015}
+
+
+def _check(ctx, sc, solver, max_flag_frac=0.01):
     r = oracle.render(sc, ORACLE_MODE[solver], ambig=True)
     g = gpu_render(ctx, sc, solver)
     assert np.isfinite(g).all()
@@ -79,7 +89,7 @@ SCENES = {
 @pytest.mark.parametrize("solver", ["plain", "fast"])
 @pytest.mark.parametrize("name", sorted(SCENES))
 def test_forward_matches_oracle(ctx, name, solver):
-    _check(ctx, SCENES[name](), solver)
+    _check(ctx, SCENES[name](), solver, FLAG_FRAC.get(name, 0.01))
 
 
 @pytest.mark.parametrize("solver", ["plain", "fast"])
@@ -101,7 +111,7 @@ def test_tuning_variants_agree(ctx, tile, spt):
     ctx.set_tuning(tile, spt, 0)
     try:
         for solver in ("fast", "plain"):
-            _check(ctx, sc, solver)
+            _check(ctx, sc, solver, 0.0125)  # measured: plain 1.17%, fast 1.24% of the pixels flagged
         g = gpu_render(ctx, sc, "fast")
         assert np.max(np.abs(g - ref)) < 2e-6
     finally:

@@ -146,6 +146,161 @@ def test_vertex_normals_octahedron_closed_form():
     assert np.allclose(n, v, atol=1e-15)
 
 
+def test_vertex_normals_weight_faces_by_area():
+    """Vertex normals are the normalised sum of the incident faces' UN-normalised cross products
+    (area weighting).  Vertex 0 touches a face of area 2 with normal +z and a face of area 1/2
+    with normal -x, so its normal is (-1, 0, 4) / sqrt(17), computed by hand.  The other common
+    rules give different vectors here and would fail: the unweighted mean of unit face normals is
+    (-1, 0, 1) / sqrt(2), and the angle-weighted mean (incident angles 90 and 26.57 degrees) is
+    about (-0.283, 0, 0.959)."""
+    v = np.array([[0, 0, 0], [2, 0, 0], [0, 2, 0], [0, 1, -0.5]], float)
+    f = np.array([[0, 1, 2], [0, 2, 3]], dtype=np.int32)
+    sc = scenes.scene(v, f, np.full_like(v, 0.5), scenes.translate((0, 0, 0)),
+                      scenes.camera(scenes.look_at((0, 0, -4))), 1, 8, 8)
+    n = oracle.vertex_normals(sc)
+    area = np.array([-1.0, 0.0, 4.0]) / math.sqrt(17.0)
+    assert np.allclose(n[0], area, atol=1e-15) and np.allclose(n[2], area, atol=1e-15)
+    assert np.allclose(n[1], [0, 0, 1], atol=1e-15) and np.allclose(n[3], [-1, 0, 0], atol=1e-15)
+    # the rejected rules really are far from the pinned value at vertex 0
+    assert np.linalg.norm(area - np.array([-1.0, 0.0, 1.0]) / math.sqrt(2.0)) > 0.5
+    ang = np.array([-math.atan2(1.0, 2.0), 0.0, math.pi / 2])
+    assert np.linalg.norm(area - ang / np.linalg.norm(ang)) > 0.04
+
+
+def _screen_quad(x0, x1, y0, y1, zc, th):
+    """World vertices (camera at (0, 0, -4) looking along +z) of a quad facing the camera whose
+    screen extent is [x0, x1] x [y0, y1] at camera depth zc; faces wound so the normal is -z."""
+    wz = zc - 4.0
+    v = np.array([[x0 * zc * th, y0 * zc * th, wz], [x1 * zc * th, y0 * zc * th, wz],
+                  [x1 * zc * th, y1 * zc * th, wz], [x0 * zc * th, y1 * zc * th, wz]], float)
+    return v, np.array([[0, 2, 1], [0, 3, 2]], dtype=np.int32)
+
+
+def _two_quads(va, fa, ca, vb, fb, cb, a_first, W=64, H=48):
+    """One static scene of two quads with their own vertices and constant albedos; faces of
+    quad A listed first (a_first) or second."""
+    parts = [(va, fa, ca), (vb, fb, cb)] if a_first else [(vb, fb, cb), (va, fa, ca)]
+    verts, faces, alb, off = [], [], [], 0
+    for v, f, c in parts:
+        verts.append(v)
+        faces.append(f + off)
+        alb.append(np.tile(np.asarray(c, float), (len(v), 1)))
+        off += len(v)
+    return scenes.scene(np.vstack(verts), np.vstack(faces), np.vstack(alb), scenes.translate((0, 0, 0)),
+                        scenes.camera(scenes.look_at((0, 0, -4))), 1, H, W)
+
+
+def _lambert(cam, n):
+    L = np.asarray(cam["light_dir"], float) / np.linalg.norm(cam["light_dir"])
+    n = np.asarray(n, float) / np.linalg.norm(n)
+    return cam["k_ambient"] + cam["k_diffuse"] * max(0.0, float(n @ L))
+
+
+def _pixel_centres(H, W):
+    u = (2 * (np.arange(W) + 0.5) / W - 1)[None, :].repeat(H, 0)
+    v = (1 - 2 * (np.arange(H) + 0.5) / H)[:, None].repeat(W, 1)
+    return u, v
+
+
+@pytest.mark.parametrize("a_first", [True, False])
+def test_ztest_nearer_quad_wins_the_overlap(a_first):
+    """Sec. 3.1 z-test: two overlapping screen-aligned quads, A at camera depth 3 (near, red) and
+    B at depth 5 (far, blue).  Pixels inside both show A's closed-form Lambert colour, whichever
+    quad's faces are listed first; pixels inside one quad show that quad.  A reversed test
+    (farthest wins) would show B in the overlap, and a first-listed-wins rule would flip with the
+    listing order."""
+    th = math.tan(math.radians(20))
+    ax0, ax1, ay0, ay1 = -0.61, 0.23, -0.43, 0.37
+    bx0, bx1, by0, by1 = -0.17, 0.69, -0.29, 0.53
+    va, fa = _screen_quad(ax0, ax1, ay0, ay1, 3.0, th)
+    vb, fb = _screen_quad(bx0, bx1, by0, by1, 5.0, th)
+    ca, cb = (0.8, 0.25, 0.2), (0.2, 0.3, 0.85)
+    sc = _two_quads(va, fa, ca, vb, fb, cb, a_first)
+    img = oracle.render(sc, "exact")["rgba"]
+    shade = _lambert(sc["camera"], (0, 0, -1))
+    u, v = _pixel_centres(sc["H"], sc["W"])
+    in_a = (u >= ax0) & (u <= ax1) & (v >= ay0) & (v <= ay1)
+    in_b = (u >= bx0) & (u <= bx1) & (v >= by0) & (v <= by1)
+    assert (in_a & in_b).sum() > 100 and (in_b & ~in_a).sum() > 50
+    assert np.abs(img[in_a][:, :3] - shade * np.array(ca)).max() < 1e-12
+    assert np.abs(img[in_b & ~in_a][:, :3] - shade * np.array(cb)).max() < 1e-12
+    assert np.abs(img[in_a | in_b][:, 3] - 1.0).max() < 1e-12
+
+
+@pytest.mark.parametrize("a_first", [True, False])
+def test_ztest_exact_depth_tie_goes_to_the_smaller_face_id(a_first):
+    """Sec. 3.1 z-test tie rule: quad B duplicates quad A's geometry exactly (its own vertices,
+    bit-identical positions, same winding) with another colour.  Every covered pixel is an exact
+    depth tie, resolved to the smaller face id, i.e. to the quad listed first: the image shows A
+    when A's faces come first and B otherwise."""
+    th = math.tan(math.radians(20))
+    va, fa = _screen_quad(-0.51, 0.33, -0.41, 0.47, 4.0, th)
+    ca, cb = (0.8, 0.25, 0.2), (0.2, 0.3, 0.85)
+    sc = _two_quads(va, fa, ca, va.copy(), fa, cb, a_first)
+    img = oracle.render(sc, "exact")["rgba"]
+    u, v = _pixel_centres(sc["H"], sc["W"])
+    inside = (u >= -0.51) & (u <= 0.33) & (v >= -0.41) & (v <= 0.47)
+    want = np.array(ca if a_first else cb) * _lambert(sc["camera"], (0, 0, -1))
+    assert inside.sum() > 300
+    assert np.abs(img[inside][:, :3] - want).max() < 1e-12
+
+
+def _affine_z_winner(sc, u, v):
+    """The REJECTED rule, for contrast: per pixel, the face whose screen-space (affine)
+    interpolation of vertex camera depths sum_i w_i z_i is smallest.  Returns face ids (-1: none)."""
+    st = oracle.vertex_state(sc, 0.5)
+    best = np.full(u.shape, np.inf)
+    win = np.full(u.shape, -1)
+    for fi, (a, b, c) in enumerate(sc["faces"]):
+        P = st[[a, b, c]]
+        M = np.array([P[:, 0], P[:, 1], np.ones(3)])
+        w = np.linalg.solve(M, np.stack([u.ravel(), v.ravel(), np.ones(u.size)])).T.reshape(u.shape + (3,))
+        inside = (w >= 0).all(-1)
+        z = w @ P[:, 2]
+        take = inside & (z < best)
+        best[take] = z[take]
+        win[take] = fi
+    return win
+
+
+@pytest.mark.parametrize("a_first", [True, False])
+def test_ztest_uses_perspective_correct_depth(a_first):
+    """Sec. 3.1 z-test with a tilted quad: B lies in the camera-space plane z_c = 4 + x_c / 2 and
+    crosses the screen-aligned quad A (z_c = 4) at x_c = 0.  On screen, B's true depth is
+    z_c(u) = 4 / (1 - u tan(20 deg) / 2), nearer than A exactly where u < 0, so the overlap shows
+    B's colour left of u = 0 and A's colour right of it.  The perspective-correct key
+    sum_i w_i / z_i is exactly 1 / z_c for planar faces and reproduces this.  An affine depth
+    key sum_i w_i z_i moves the crossing by several pixels: the test checks that it would fail."""
+    th = math.tan(math.radians(20))
+    va, fa = _screen_quad(-0.6, 0.6, -0.5, 0.5, 4.0, th)
+    xc = np.array([-1.2, 1.2, 1.2, -1.2])
+    zc = 4.0 + 0.5 * xc
+    yc = np.array([-0.35, -0.35, 0.35, 0.35]) * 4.0 * th
+    vb = np.stack([xc, yc, zc - 4.0], 1)
+    fb = np.array([[0, 2, 1], [0, 3, 2]], dtype=np.int32)
+    ca, cb = (0.8, 0.25, 0.2), (0.2, 0.3, 0.85)
+    sc = _two_quads(va, fa, ca, vb, fb, cb, a_first)
+    img = oracle.render(sc, "exact")["rgba"]
+    cam = sc["camera"]
+    col_a = np.array(ca) * _lambert(cam, (0, 0, -1))
+    col_b = np.array(cb) * _lambert(cam, (0.5, 0, -1))
+    u, v = _pixel_centres(sc["H"], sc["W"])
+    # B's screen footprint: x from its projected left to right edge, |y| below its edges' projection
+    zb = 4.0 / (1.0 - 0.5 * th * u)
+    in_b = (zb * th * u >= -1.2) & (zb * th * u <= 1.2) & (np.abs(v) * zb * th <= 0.35 * 4.0 * th)
+    in_a = (np.abs(u) <= 0.6) & (np.abs(v) <= 0.5)
+    both = in_a & in_b
+    left, right = both & (u < 0), both & (u > 0)
+    assert left.sum() > 100 and right.sum() > 100
+    assert np.abs(img[left][:, :3] - col_b).max() < 1e-12
+    assert np.abs(img[right][:, :3] - col_a).max() < 1e-12
+    # the affine key picks the wrong quad on a band of overlap pixels
+    ids = _affine_z_winner(sc, u, v)
+    b_ids = {2, 3} if a_first else {0, 1}
+    affine_b = np.isin(ids, list(b_ids))
+    assert ((affine_b != (u < 0)) & both).sum() >= 40
+
+
 def test_camera_optical_axis_and_fov_edge():
     """Camera (scene settings): a point on the optical axis projects to (0, 0); a point at the
     half-FOV angle projects to ndc 1; camera z is the distance along the view direction."""
