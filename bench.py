@@ -43,15 +43,31 @@ def ref_window(steps):
     16), so that a long --steps run still ends within a few minutes."""
     x0, y0, w, h = REF_WINDOW
     return (x0, y0, w, h if steps <= 200 else max(16, h * 200 // steps))
-# DRAM bytes (read + write) per launch from the ncu captures summarised in profiles/ (tiles 8x8,
-# this workload), by (kernel, sub-frames per thread); to be refreshed whenever the kernels change
-# Pipe utilisation (% of active cycles) and issue-active share of the fast raster kernels at tiles
-# 8x8, from one `ncu --set full` capture each on this workload (summaries in profiles/): the
-# counter view of the roofline fraction next to the credited-flops view.
-NCU_PIPES = {"raster_bwd_persistent": {"fma": 19.7, "alu": 27.3, "xu": 4.5, "lsu": 22.2, "issue_active": 43.0},
-             "raster_fwd_persistent": {"fma": 20.0, "alu": 32.3, "xu": 8.2, "lsu": 21.7, "issue_active": 49.8}}
-NCU_DRAM_BYTES = {("raster_bwd_persistent", 1): 34.93e6, ("raster_fwd_persistent", 1): 18.18e6,
-                  ("raster_bwd_persistent", 2): 33.98e6, ("raster_fwd_persistent", 2): 16.90e6}
+# Counters of the dominant raster kernels from one ncu capture each (summaries in profiles/): DRAM
+# bytes per launch and pipe utilisation (% of active cycles).  They describe the kernels as they were
+# compiled when captured: the entry is attached to the bench line only if the current kernel
+# sources hash to CAPTURED["sources"] and the run uses the captured tile / samples-per-group;
+# otherwise the line carries null.
+CAPTURED = {"sources": None, "tile": None, "spt": None, "kernels": {}}
+
+
+def kernel_sources_sha():
+    """sha256 (first 16 hex digits) of the CUDA sources the library is built from."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2602_07860_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            h.update(open(os.path.join(d, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def captured_counters(kernel, tile, spt):
+    """The captured counters of ``kernel`` if they still describe this build and configuration."""
+    if CAPTURED["sources"] != kernel_sources_sha() or (CAPTURED["tile"], CAPTURED["spt"]) != (tile, spt):
+        return None
+    return CAPTURED["kernels"].get(kernel)
 
 
 def _dist_env():
@@ -126,9 +142,10 @@ def _sample_time(stamp):
         return None
 
 
-def _clock_summary(proc, path, index, t0=None, t1=None):
+def _clock_summary(proc, path, index, t0=None, t1=None, keep_rows=False):
     """Median SM clock, maximum SM clock and the throttle reasons seen by the samples taken between
-    t0 and t1 (time.time() around the timed region); all samples if none falls inside."""
+    t0 and t1 (time.time() around the timed region); all samples if none falls inside.  With
+    keep_rows: (summary, all rows of this GPU) so that other intervals can be summarised too."""
     if proc is None:
         return None
     proc.terminate()
@@ -147,6 +164,11 @@ def _clock_summary(proc, path, index, t0=None, t1=None):
         return None
     if not rows:
         return None
+    summary = _summarise_rows(rows, t0, t1)
+    return (summary, rows) if keep_rows else summary
+
+
+def _summarise_rows(rows, t0, t1):
     inside = [r for r in rows if t0 is not None and (_sample_time(r[0]) or 0.0) >= t0 and
               (_sample_time(r[0]) or 0.0) <= t1]
     use = inside or rows
@@ -270,21 +292,48 @@ def extra_workloads(mbr, scenes, torch, np, world):
         torch.cuda.synchronize()
         return (time.perf_counter() - t0) / reps * 1e3
 
-    # c3: one iteration of the recovery loop's renders (8 views, forward + adjoint, batched)
+    # c3: the shape-recovery run to its end: 8 blurred views (4 translations, 4 rotations) of the
+    # SH-8 target, 256^2, T = 64; Adam (lr 1e-3) on the undisplaced sphere's vertices for 500
+    # iterations, L2 image loss + 0.1 Laplacian; every iteration one graph replay of the 8-view
+    # forward batch and one of the adjoint batch
+    from paper_2602_07860_gb300.recovery import recover_shape
     views_sc, template = scenes.config3()
     s0 = views_sc[0]
     dev = "cuda"
-    tv = torch.as_tensor(np.asarray(template, np.float32), device=dev).contiguous()
-    tf = torch.as_tensor(np.asarray(s0["faces"], np.int32), device=dev).contiguous()
-    ta = torch.as_tensor(np.asarray(s0["albedo"], np.float32), device=dev).contiguous()
+    tt = lambda x, dt=torch.float32: torch.as_tensor(np.asarray(x), dtype=dt, device=dev).contiguous()
+    tgt_v = tt(s0["verts"])
+    tf = tt(s0["faces"], torch.int32)
+    ta = tt(s0["albedo"])
     views = [(mbr.motion_from_dict(s["motion"]), mbr.camera_from_dict(s["camera"])) for s in views_sc]
-    vb = ViewBatch(tv, tf, ta, views, s0["T"], s0["H"], s0["W"], "fast")
+    targets = ViewBatch(tgt_v, tf, ta, views, s0["T"], s0["H"], s0["W"], "fast").forward().clone()
+    tv = tt(template)
+    vb = ViewBatch(tv.clone(), tf, ta, views, s0["T"], s0["H"], s0["W"], "fast")
     g = torch.randn((len(views), s0["H"], s0["W"], 4), device=dev, generator=torch.Generator(dev).manual_seed(5))
     ms = timeit(lambda: (vb.forward(), vb.backward(g)), 5)
     n = len(views) * s0["H"] * s0["W"] * s0["T"]
     out["c3_recovery_iteration"] = {"ms": ms, "samples_per_s": world * n / (ms / 1e3), "views": len(views),
                                     "workload": "8 views (4 translations, 4 rotations), 2562 v, T=64, 256x256"}
-    # c4: 32 objects of mixed size in one batched forward + adjoint
+    iters, marks, track = 500, (0, 100, 250, 499), {}
+
+    def on_iter(it, v, img_loss):
+        if it in marks:
+            track[it] = (float(img_loss), float((v - tgt_v).norm(dim=1).mean()))
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    v_final, hist = recover_shape(tv, tf, ta, views, targets, s0["T"], s0["H"], s0["W"], iters=iters, lr=1e-3,
+                                  lap_weight=0.1, solver="fast", on_iter=on_iter)
+    torch.cuda.synchronize()
+    run_s = time.perf_counter() - t0
+    out["c3_recovery_run"] = {
+        "iterations": iters, "seconds": run_s, "ms_per_iteration": 1e3 * run_s / iters,
+        "image_loss": {str(k): track[k][0] for k in marks},
+        "mean_vertex_distance_to_target": {str(k): track[k][1] for k in marks},
+        "final_mean_vertex_distance_to_target": float((v_final - tgt_v).norm(dim=1).mean()),
+        "workload": "8 views, 256x256, T=64, Adam lr 1e-3, L2 image loss + 0.1 Laplacian, from the undisplaced "
+                    "subdiv-4 sphere towards the SH-8 target (same topology: per-vertex distance)",
+        "includes": "renders, adjoint, loss terms, optimiser, one host read of the loss per iteration"}
+    # c4: 32 objects of mixed size in one batched forward + adjoint, tiles chosen by the autotuner
     items, n = [], 0
     ctx = mbr.Context()
     for s in scenes.config4():
@@ -295,8 +344,11 @@ def extra_workloads(mbr, scenes, torch, np, world):
                           image=torch.zeros((s["H"], s["W"], 4), device=dev),
                           dl_dimage=torch.ones((s["H"], s["W"], 4), device=dev),
                           dl_dverts=torch.zeros_like(vv), dl_dalbedo=torch.zeros_like(aa)))
+    tile4, spt4, tune_ms = ctx.autotune(items, True)
     ms = timeit(lambda: ctx.render_batch(items, True), 3)
     out["c4_batch_32_objects"] = {"ms": ms, "samples_per_s": world * n / (ms / 1e3), "samples": n,
+                                  "tuning": {"tile": tile4, "spt": spt4, "autotune_best_ms": tune_ms,
+                                             "chosen_by": "mbr_autotune"},
                                   "workload": "32 objects, subdiv 2-5, T in {16..256}, 128-512 px, one graph replay"}
     # c5: the large render, both solvers
     s = scenes.config5()
@@ -414,100 +466,163 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     n_samples = H * W * T
 
-    def step(solver, bwd=True):
-        # forward, then the adjoint as the autograd path runs it (reusing the forward's front half)
-        ctx.render_blur(v, f, a, mo, ca, T, H, W, solver)
-        if bwd:
-            ctx.render_blur_backward(v, f, a, mo, ca, T, H, W, G, solver, reuse_forward=True)
+    class Scene:
+        """Timing of one scene on ctx: forward (+ adjoint reusing the forward's front half, as the
+        autograd path runs it), L2 flushed before every timed step, CUDA events around each step;
+        the library's own events time the raster kernels."""
 
-    def timed(solver, bwd, steps, warmup, t_region=None):
-        for _ in range(warmup):
-            step(solver, bwd)
-        barrier()
-        if t_region is not None:
-            t_region[0] = time.time()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        for e0, e1 in ev:
-            flush.zero_()
-            e0.record()
-            step(solver, bwd)
-            e1.record()
-        barrier()
-        if t_region is not None:
-            t_region[1] = time.time()
-        return sum(e0.elapsed_time(e1) for e0, e1 in ev)
+        def __init__(self, scd):
+            self.sc = scd
+            self.T, self.H, self.W = scd["T"], scd["H"], scd["W"]
+            self.v, self.f, self.a = mbr.mesh_tensors(scd)
+            self.mo, self.ca = mbr.motion_from_dict(scd["motion"]), mbr.camera_from_dict(scd["camera"])
+            self.G = torch.as_tensor(np.random.default_rng(11).normal(size=(self.H, self.W, 4)).astype(np.float32),
+                                     device="cuda")
+            self.n = self.H * self.W * self.T
+
+        def step(self, solver, bwd=True):
+            ctx.render_blur(self.v, self.f, self.a, self.mo, self.ca, self.T, self.H, self.W, solver)
+            if bwd:
+                ctx.render_blur_backward(self.v, self.f, self.a, self.mo, self.ca, self.T, self.H, self.W, self.G,
+                                         solver, reuse_forward=True)
+
+        def timed(self, solver, bwd, steps, warmup, t_region=None):
+            """(total ms over the timed steps, library stats of the timed steps)"""
+            for _ in range(warmup):
+                self.step(solver, bwd)
+            barrier()
+            ctx.set_profiling(True)
+            if t_region is not None:
+                t_region[0] = time.time()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for e0, e1 in ev:
+                flush.zero_()
+                e0.record()
+                self.step(solver, bwd)
+                e1.record()
+            barrier()
+            if t_region is not None:
+                t_region[1] = time.time()
+            st_ = ctx.stats()
+            ctx.set_profiling(False)
+            return max_over_ranks(sum(e0.elapsed_time(e1) for e0, e1 in ev)), st_
+
+        def units(self, solver):
+            d = ctx.count_work(self.v, self.f, self.a, self.mo, self.ca, self.T, self.H, self.W, solver, detail=True)
+            return dict(d, n_sample=self.n)
+
+        def fracs(self, solver, st_, peak_tf):
+            """raster kernel ms, credited TFLOP/s and fraction of the measured peak, per direction"""
+            u = self.units(solver)
+            out = {"units": u}
+            for key, fl_fn, cnt in (("fwd", roofline.fwd_flops, "raster_fwd"), ("bwd", roofline.bwd_flops, "raster_bwd")):
+                if st_[cnt + "_count"]:
+                    k_ms = st_[cnt + "_ms"] / st_[cnt + "_count"]
+                    fl = fl_fn(solver, u["n_box"], u["n_soft"], u["n_cov"], self.n)
+                    tf = fl / (k_ms / 1e3) / 1e12
+                    out[key] = {"raster_ms": k_ms, "flops": fl, "tflops": tf, "frac": tf / peak_tf}
+            return out
+
+    main_scene = Scene(sc)
+    main_scene.v, main_scene.f, main_scene.a, main_scene.G = v, f, a, G
 
     # ---- headline: fast solver forward + backward, raster kernels timed by events in the library
     l0 = ctx.stats()["launches"]
-    ctx.set_profiling(True)
     proc, path = _clock_sampler() if rank == 0 else (None, None)
     t_region = [0.0, 0.0]
-    total_ms = timed("fast", True, args.steps, args.warmup, t_region)
-    clocks = _clock_summary(proc, path, local, *t_region) if rank == 0 else None
-    st = ctx.stats()
-    ctx.set_profiling(False)
-    launches = (st["launches"] - l0) * args.steps // (args.steps + args.warmup)
-    total_ms = max_over_ranks(total_ms)
+    total_ms, st = main_scene.timed("fast", True, args.steps, args.warmup, t_region)
+    launches = (ctx.stats()["launches"] - l0) * args.steps // (args.steps + args.warmup)
     ms_per_step = total_ms / args.steps
     value = reps.job_rate(n_samples * args.steps, total_ms / 1e3)
+    # ---- the roofline's denominator, measured now: FMA chains on every SM for about half a second
+    t_peak = [time.time(), 0.0]
+    peak, peak_flops, peak_ms = ctx.measure_fp32_peak(iters=20000, launches=25)
+    t_peak[1] = time.time()
+    clock_rows = _clock_summary(proc, path, local, *t_region, keep_rows=True) if rank == 0 else None
+    clocks = clock_rows[0] if clock_rows else None
+    peak_clocks = _summarise_rows(clock_rows[1], *t_peak) if clock_rows else None
+    num_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_derived = roofline.fp32_peak_tflops(num_sms)
 
     # ---- roofline of the dominant raster kernel (FP32 ALU bound); work units counted by the GPU
     # path itself (mbr_count_work), flops per unit from the formulas (roofline.py)
-    fwd_ms = st["raster_fwd_ms"] / max(1, st["raster_fwd_count"])
-    bwd_ms = st["raster_bwd_ms"] / max(1, st["raster_bwd_count"])
-    num_sms = torch.cuda.get_device_properties(local).multi_processor_count
-    peak = roofline.fp32_peak_tflops(num_sms)
-
-    def kernel_roofs(solver, f_ms, b_ms):
-        d = ctx.count_work(v, f, a, mo, ca, T, H, W, solver, detail=True)
-        n_box, n_soft, n_cov = d["n_box"], d["n_soft"], d["n_cov"]
-        fw = roofline.fwd_flops(solver, n_box, n_soft, n_cov, n_samples)
-        bw = roofline.bwd_flops(solver, n_box, n_soft, n_cov, n_samples)
-        units = dict(d, n_sample=n_samples)
-        return fw, bw, units, fw / (f_ms / 1e3) / 1e12, bw / (b_ms / 1e3) / 1e12
-
-    fwf, bwf, units, fwd_tf, bwd_tf = kernel_roofs("fast", fwd_ms, bwd_ms)
+    rf = main_scene.fracs("fast", st, peak)
+    units = rf["units"]
+    fwd_ms, bwd_ms = rf["fwd"]["raster_ms"], rf["bwd"]["raster_ms"]
     backward_dominant = bwd_ms >= fwd_ms
     kern = "raster_bwd_persistent" if backward_dominant else "raster_fwd_persistent"
-    achieved = bwd_tf if backward_dominant else fwd_tf
-    traffic = NCU_DRAM_BYTES.get((kern, ctx_spt)) if tile == 8 else None
-    roof = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic,
-            "traffic_note": f"DRAM bytes per launch from ncu (profiles/), tiles 8x8, spt {ctx_spt}",
-            "peak_note": f"{num_sms} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived from unit counts "
-                         "and the maximum SM clock; no measured FP32 peak)",
+    dom = rf["bwd"] if backward_dominant else rf["fwd"]
+    cap = captured_counters(kern, tile, ctx_spt)
+    roof = {"bound": "alu", "kernel": kern, "achieved": dom["tflops"], "peak": peak, "unit": "TFLOP/s",
+            "frac": dom["frac"], "traffic": cap["dram_bytes"] if cap else None,
+            "traffic_note": (f"ncu DRAM bytes per launch, captured on these kernel sources at tile {tile}, "
+                             f"spt {ctx_spt}" if cap else "null: no ncu capture of the current kernel sources "
+                             "in this configuration"),
+            "peak_measured": peak,
+            "peak_note": (f"measured in this run: mbr_measure_fp32_peak, FMA chains on all {num_sms} SMs, "
+                          f"{peak_flops:.3e} flops in {peak_ms:.0f} ms (CUDA events); clocks during it: "
+                          f"{peak_clocks}"),
+            "peak_derived": peak_derived, "frac_of_derived": dom["tflops"] / peak_derived,
+            "peak_derived_note": f"{num_sms} SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
             "work": roofline.describe("fast", units["n_box"], units["n_soft"], units["n_cov"], n_samples,
                                       backward_dominant),
-            "flops_per_launch": bwf if backward_dominant else fwf,
-            "kernel_ms": bwd_ms if backward_dominant else fwd_ms, "raster_fwd_ms": fwd_ms, "raster_bwd_ms": bwd_ms,
-            "fwd_frac": fwd_tf / peak, "bwd_frac": bwd_tf / peak, "units": units,
-            "ncu_pipes_pct": NCU_PIPES.get(kern) if tile == 8 else None}
+            "flops_per_launch": dom["flops"], "kernel_ms": dom["raster_ms"],
+            "raster_fwd_ms": fwd_ms, "raster_bwd_ms": bwd_ms,
+            "fwd_frac": rf["fwd"]["frac"], "bwd_frac": rf["bwd"]["frac"], "units": units,
+            "ncu_pipes_pct": cap["pipes_pct"] if cap else None, "n_split": st["n_split"], "groups": st["groups"]}
 
-    # ---- plain per-sub-frame solver and forward-only numbers on the same GPU
+    # ---- plain per-sub-frame solver and forward-only numbers on the same GPU (rotation)
     k2 = max(3, args.steps // 2)
-    ctx.set_profiling(True)
-    plain_fb = max_over_ranks(timed("plain", True, k2, 2)) / k2
-    pst = ctx.stats()
-    ctx.set_profiling(False)
-    p_fwd = pst["raster_fwd_ms"] / max(1, pst["raster_fwd_count"])
-    p_bwd = pst["raster_bwd_ms"] / max(1, pst["raster_bwd_count"])
-    _, _, p_units, p_fwd_tf, p_bwd_tf = kernel_roofs("plain", p_fwd, p_bwd)
-    fast_f = max_over_ranks(timed("fast", False, k2, 2)) / k2
-    plain_f = max_over_ranks(timed("plain", False, k2, 2)) / k2
+    plain_fb, pst = main_scene.timed("plain", True, k2, 2)
+    plain_fb /= k2
+    prf = main_scene.fracs("plain", pst, peak)
+    fast_f, fst = main_scene.timed("fast", False, k2, 2)
+    fast_f /= k2
+    plain_f, _ = main_scene.timed("plain", False, k2, 2)
+    plain_f /= k2
     extras = {
         "fast_fwdbwd_iters_per_s": 1e3 / ms_per_step,
         "plain_fwdbwd_ms": plain_fb, "plain_fwdbwd_samples_per_s": world * n_samples / (plain_fb / 1e3),
         "plain_fwdbwd_iters_per_s": 1e3 / plain_fb,
-        "fast_fwd_ms": fast_f, "fast_fwd_samples_per_s": world * n_samples / (fast_f / 1e3),
-        "plain_fwd_ms": plain_f, "plain_fwd_samples_per_s": world * n_samples / (plain_f / 1e3),
         "speedup_fast_over_plain_fwdbwd": plain_fb / ms_per_step,
-        "speedup_fast_over_plain_fwd": plain_f / fast_f,
-        "plain_raster_fwd_ms": p_fwd, "plain_raster_bwd_ms": p_bwd,
-        "plain_fwd_frac": p_fwd_tf / peak, "plain_bwd_frac": p_bwd_tf / peak, "plain_units": p_units,
+        "c2_forward_plain_vs_fast": {
+            "fast_ms": fast_f, "plain_ms": plain_f, "speedup_fast_over_plain": plain_f / fast_f,
+            "fast_samples_per_s": world * n_samples / (fast_f / 1e3),
+            "plain_samples_per_s": world * n_samples / (plain_f / 1e3),
+            "fast_raster_ms": fst["raster_fwd_ms"] / max(1, fst["raster_fwd_count"])},
+        "plain_raster_fwd_ms": prf["fwd"]["raster_ms"], "plain_raster_bwd_ms": prf["bwd"]["raster_ms"],
+        "plain_fwd_frac": prf["fwd"]["frac"], "plain_bwd_frac": prf["bwd"]["frac"], "plain_units": prf["units"],
         "tuning": {"tile": tile, "spt": ctx_spt, "splits": "auto",
                    "chosen_by": "command line" if (args.tile and args.spt) else "mbr_autotune"},
-        "paper_context": "paper: up to 4.57x fwd+grad speedup vs SoftRas on one RTX 4090 (different workload)",
+        "paper_context": "paper: up to 4.57x fwd+grad speedup vs SoftRas on one RTX 4090 (different workload, "
+                         "linear translation, Sec. 4.2)",
     }
+    # ---- the translation scene at the headline's size (the paper's speed comparison uses linear
+    # translation): same mesh, d = 1.5 perpendicular to the view, T = 64, 256^2, one segment
+    tsc = Scene(scenes.config2_translate())
+    tr = {"workload": "translation: the rotation workload's mesh moved by d = (1.5, 0, 0), T=64, 256x256, S=1"}
+    for solver in ("fast", "plain"):
+        fb_ms, fb_st = tsc.timed(solver, True, k2, 2)
+        fb_ms /= k2
+        fw_ms, fw_st = tsc.timed(solver, False, k2, 2)
+        fw_ms /= k2
+        fr = tsc.fracs(solver, fb_st, peak)
+        tr[solver] = {"fwdbwd_ms": fb_ms, "fwdbwd_samples_per_s": world * tsc.n / (fb_ms / 1e3),
+                      "fwdbwd_iters_per_s": 1e3 / fb_ms, "fwd_ms": fw_ms,
+                      "fwd_samples_per_s": world * tsc.n / (fw_ms / 1e3),
+                      "raster_fwd_ms": fr["fwd"]["raster_ms"], "raster_bwd_ms": fr["bwd"]["raster_ms"],
+                      "fwd_frac": fr["fwd"]["frac"], "bwd_frac": fr["bwd"]["frac"], "units": fr["units"]}
+    tr["speedup_fast_over_plain_fwdbwd"] = tr["plain"]["fwdbwd_ms"] / tr["fast"]["fwdbwd_ms"]
+    tr["speedup_fast_over_plain_fwd"] = tr["plain"]["fwd_ms"] / tr["fast"]["fwd_ms"]
+    extras["translate"] = tr
+    # ---- config 1 (64^2, T = 16, translation): forward only, plain vs fast
+    c1 = Scene(scenes.config1())
+    c1r = {"workload": "icosphere subdiv 2 + jitter, d = (1.5, 0, 0), T=16, 64x64, forward only"}
+    for solver in ("fast", "plain"):
+        ms1, _ = c1.timed(solver, False, k2, 2)
+        c1r[solver] = {"fwd_ms": ms1 / k2, "samples_per_s": world * c1.n / (ms1 / k2 / 1e3)}
+    c1r["speedup_fast_over_plain_fwd"] = c1r["plain"]["fwd_ms"] / c1r["fast"]["fwd_ms"]
+    extras["c1_forward"] = c1r
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
     hv, hf, ha, hG = v.cpu().pin_memory(), f.cpu().pin_memory(), a.cpu().pin_memory(), G.cpu().pin_memory()

@@ -43,7 +43,7 @@ extern "C" {
 #define MBR_ERR_ARG 1     /* invalid argument (null pointer, bad size, unsupported value)      */
 #define MBR_ERR_CUDA 2    /* a CUDA runtime call failed                                        */
 #define MBR_ERR_OOM 3     /* device allocation failed                                          */
-#define MBR_ERR_TIMEOUT 4 /* a bounded device-side wait ran out (batch scheduler)              */
+#define MBR_ERR_TIMEOUT 4 /* a bounded device-side wait of the raster gave up (output incomplete) */
 #define MBR_ERR_DEVICE 5  /* a kernel reported an error through the device status word        */
 
 #define MBR_PLAIN 0
@@ -247,12 +247,39 @@ int mbr_get_stats(mbr_ctx* ctx, mbr_stats* out);
  * return MBR_ERR_ARG with a message naming the limit; use mbr_render_blur for those.
  * All calls on a device share the array, which keeps the last call's contents (the call clears
  * what it accumulates): calls whose work overlaps on the GPU -- different streams or threads
- * without ordering between them -- race.  The call synchronises its stream once, like
- * mbr_render_blur.  Arguments are those of mbr_render_blur; err (may be NULL) receives the error
- * message of a failed call, truncated to err_len bytes including the terminating zero. */
+ * without ordering between them -- race.  Host <-> device traffic: one copy of the motion and
+ * camera tables from pageable host memory at the start (it may wait for work already queued on
+ * the stream), one stream synchronisation after binning (it reads the tile-list sizes), then one
+ * copy of the raster's parameters into the idle stream.  The raster itself is not waited for: if
+ * one of its bounded device-side waits gave up (the image is then incomplete), the NEXT call on
+ * this device returns MBR_ERR_TIMEOUT and clears the report.  Arguments are those of
+ * mbr_render_blur; err (may be NULL) receives the error message of a failed call, truncated to
+ * err_len bytes including the terminating zero. */
 int mbr_render_blur_noalloc(const mbr_mesh* mesh, const mbr_motion* motion, const mbr_camera* camera,
                             int32_t T, int32_t H, int32_t W, int32_t solver, float* image,
                             void* cuda_stream, char* err, int32_t err_len);
+
+/* Measurement hook: the FP32 CUDA-core peak of this GPU, measured.  Runs `launches` back-to-back
+ * launches of a kernel that fills every SM with independent FMA chains (`iters` x 128 FMAs per
+ * thread each), timed by CUDA events on the stream; *flops receives the FP32 operations executed
+ * (an FMA counts 2), *ms the elapsed time.  flops / ms is the roofline denominator of the
+ * renderer's ALU-bound kernels (the paper has no counterpart).  Synchronises the stream. */
+int mbr_measure_fp32_peak(mbr_ctx* ctx, int32_t iters, int32_t launches, double* flops, float* ms,
+                          void* cuda_stream);
+
+/* Test hook for the raster's bounded waits (process-wide; applies to raster launches issued after
+ * it, not to CUDA graphs captured before it).  The persistent raster CTAs hand work units to their
+ * warps through shared-memory flags; every wait on such a flag polls at most `polls` times
+ * (about 64 ns each; polls = 0 restores the default of 2^22, about 0.27 s), then sets the
+ * kernel's status word, stops taking work and returns -- the kernel never hangs.  stall = 1 makes
+ * the CTAs never publish a claimed unit, so every wait for a publication runs out after `polls`
+ * polls (the flag that nothing sets); it needs 0 < polls <= 2^20.  check_now = 1 makes
+ * mbr_render_blur, mbr_render_blur_backward(_reuse) and mbr_render_blur_noalloc synchronise their
+ * stream after the raster and return MBR_ERR_TIMEOUT from the same call; otherwise a give-up is
+ * reported by the next call on the same context (or device, for the no-alloc entry) at its
+ * binning synchronisation, and mbr_render_blur_batch reports it from the same call.  Returns
+ * MBR_ERR_ARG for invalid values. */
+int mbr_debug_wait_limit(int32_t polls, int32_t stall, int32_t check_now);
 
 /* Message of the last failed call on ctx ("" if none).  Valid until the next call. */
 const char* mbr_last_error(mbr_ctx* ctx);

@@ -20,7 +20,7 @@ SOLVERS = {"plain": MBR_PLAIN, "fast": MBR_FAST}
 EXPORTS = ["mbr_create", "mbr_destroy", "mbr_render_blur", "mbr_render_blur_backward",
            "mbr_render_blur_backward_reuse", "mbr_render_blur_batch",
            "mbr_debug_winners", "mbr_count_candidates", "mbr_count_work", "mbr_set_tuning", "mbr_set_profiling", "mbr_get_stats",
-           "mbr_render_blur_noalloc", "mbr_autotune", "mbr_last_error"]
+           "mbr_render_blur_noalloc", "mbr_autotune", "mbr_measure_fp32_peak", "mbr_debug_wait_limit", "mbr_last_error"]
 
 
 class MbrMesh(ctypes.Structure):
@@ -107,6 +107,10 @@ def load(build_if_missing=True):
     L.mbr_render_blur_noalloc.argtypes = [P(MbrMesh), P(MbrMotion), P(MbrCamera), c_int32, c_int32, c_int32,
                                           c_int32, c_void_p, c_void_p, ctypes.c_char_p, c_int32]
     L.mbr_render_blur_noalloc.restype = c_int32
+    L.mbr_measure_fp32_peak.argtypes = [c_void_p, c_int32, c_int32, P(ctypes.c_double), P(c_float), c_void_p]
+    L.mbr_measure_fp32_peak.restype = c_int32
+    L.mbr_debug_wait_limit.argtypes = [c_int32, c_int32, c_int32]
+    L.mbr_debug_wait_limit.restype = c_int32
     L.mbr_last_error.argtypes = [c_void_p]
     L.mbr_last_error.restype = ctypes.c_char_p
     _lib = L

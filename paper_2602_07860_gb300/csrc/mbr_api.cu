@@ -6,6 +6,7 @@
 // size the face lists, fill), unit cost order, raster.  Backward reruns the same front half and the
 // adjoint raster, then chains slot gradients to vertices.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -85,6 +86,15 @@ struct mbr_ctx {
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
+
+// bounded-wait test hook (mbr_debug_wait_limit): applies to raster launches issued after it is set
+std::atomic<int32_t> g_wait_polls{0}, g_wait_stall{0}, g_wait_check{0};
+
+void set_wait_fields(WorkQueue& Q) {
+  const int32_t polls = g_wait_polls.load();
+  Q.spin_limit = polls > 0 ? polls : kSpinLimit;
+  Q.stall = g_wait_stall.load() ? 1 : 0;
+}
 
 int fail(mbr_ctx* c, int code, const char* fmt, ...) {
   char buf[512];
@@ -606,6 +616,23 @@ int upload_queue(mbr_ctx* c, const RasterParams* items, int n, cudaStream_t st, 
   Q.n_work = off[n];
   Q.counter = (int32_t*)(d + cnt_at);
   Q.status = (int32_t*)c->status.p + 1;
+  set_wait_fields(Q);
+  return MBR_OK;
+}
+
+// With the wait hook's check_now set: wait for the raster just launched and report a wait that gave
+// up from this call (normally the next call's binning sync reports it).  word is the sticky status
+// word of the raster's queue; it is cleared when reported.
+int check_waits_now(mbr_ctx* c, int32_t* word, cudaStream_t st) {
+  if (!g_wait_check.load()) return MBR_OK;
+  int32_t h = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&h, word, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  if (h & kStatusSpin) {
+    CUDA_TRY(c, cudaMemsetAsync(word, 0, sizeof(int32_t), st));
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    return fail(c, MBR_ERR_TIMEOUT, "a raster launch gave up a bounded wait (its output is incomplete)");
+  }
   return MBR_OK;
 }
 
@@ -648,6 +675,7 @@ int forward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, con
   if ((rc = time_end(c, 0, st))) return rc;
   c->stats.launches += 1;
   c->stats.n_split = pp.n_split;
+  if ((rc = check_waits_now(c, Q.status, st))) return rc;
   if (pp_out) *pp_out = pp;
   if (P.fwd_cost) c->fcost = FwdCostKey{true, pp.n_units, pp.G, pp.n_tiles, pp.n_split, c->tile, c->order.p};
   if (image && !dbg_ids) {
@@ -745,6 +773,7 @@ int backward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, co
   launch_raster_bwd(Q, c->tile, pp.spt, kind, grid, st);
   CUDA_TRY(c, cudaGetLastError());
   if ((rc = time_end(c, 1, st))) return rc;
+  if ((rc = check_waits_now(c, Q.status, st))) return rc;
   c->stats.launches += 3 + 1 + 1 + (mesh->F > 0 ? 1 : 0);  // order, raster, slot chain, normals
   c->stats.n_split = pp.n_split;
   launch_slot_chain(mesh->verts, (const float*)c->nacc.p, V, pp.d_xf, pp.n_slots, cam->tan_half_fov,
@@ -828,6 +857,41 @@ int mbr_get_stats(mbr_ctx* c, mbr_stats* out) {
 }
 
 const char* mbr_last_error(mbr_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int mbr_measure_fp32_peak(mbr_ctx* c, int32_t iters, int32_t launches, double* flops, float* ms, void* stream) {
+  if (!c) return MBR_ERR_ARG;
+  c->err.clear();
+  if (iters < 1 || launches < 1 || !flops || !ms) return fail(c, MBR_ERR_ARG, "bad peak measurement arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc;
+  if ((rc = ensure(c, c->cnt64, sizeof(float) * 8 * (size_t)c->num_sms * 32, st))) return rc;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(c, cudaEventCreate(&e0));
+  CUDA_TRY(c, cudaEventCreate(&e1));
+  launch_fma_peak(c->num_sms, std::max(1, iters / 16), (float*)c->cnt64.p, st);  // warm-up
+  double total = 0.0;
+  cudaEventRecord(e0, st);
+  for (int i = 0; i < launches; ++i) total += launch_fma_peak(c->num_sms, iters, (float*)c->cnt64.p, st);
+  cudaEventRecord(e1, st);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return fail(c, MBR_ERR_CUDA, "peak measurement: %s", cudaGetErrorString(e));
+  *flops = total;
+  *ms = t;
+  return MBR_OK;
+}
+
+int mbr_debug_wait_limit(int32_t polls, int32_t stall, int32_t check_now) {
+  if (polls < 0 || (stall && polls <= 0) || (stall && polls > (1 << 20))) return MBR_ERR_ARG;
+  g_wait_polls.store(polls);
+  g_wait_stall.store(stall ? 1 : 0);
+  g_wait_check.store(check_now ? 1 : 0);
+  return MBR_OK;
+}
 
 int mbr_set_tuning(mbr_ctx* c, int32_t tile, int32_t spt, int32_t splits) {
   if (!c) return MBR_ERR_ARG;
@@ -1328,6 +1392,7 @@ int batch_enqueue(mbr_ctx* c, const mbr_item* items, BatchState& B, cudaStream_t
   Q.n_work = ((int32_t*)((char*)B.stage + B.stage_off))[n];
   Q.counter = (int32_t*)(dq + cnt_at);
   Q.status = (int32_t*)(A + B.items[0].o_status);
+  set_wait_fields(Q);
   const int spt = std::max(1, std::min(kMaxSpt, c->spt));
   if (sizing) {
     B.grid_fwd = std::max(1, std::min(persistent_grid_fwd(c->num_sms, c->tile, spt, B.kind), Q.n_work));
@@ -1476,44 +1541,53 @@ int noalloc_forward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, 
   pp.tiles_x = (W + tw - 1) / tw;
   pp.tiles_y = (H + th - 1) / th;
   pp.n_tiles = pp.tiles_x * pp.tiles_y;
+  const long long nb = (long long)pp.G * pp.n_tiles;
+  if (nb > (1LL << 30)) return fail(c, MBR_ERR_ARG, "too many (group, tile) bins: %lld", nb);
   CUDA_TRY(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
   pp.n_split = choose_splits(c, pp.G, patches_of(tw, pp.n_tiles));
   pp.n_units = patches_of(tw, pp.n_tiles) * pp.n_split;
   pp.r = (float)std::sqrt((double)cam->delta * (double)kSoftCutoff);
-  const long long nb = (long long)pp.G * pp.n_tiles;
 
-  // fixed part of the arena
+  // fixed part of the arena; the tables travel in one copy
+  const size_t xf_b = sizeof(SlotXform) * xf.size(), sets_b = sizeof(int2) * sets.size(),
+               g_b = sizeof(Group) * groups.size();
+  const size_t off_sets = (xf_b + 255) & ~size_t(255), off_g = (off_sets + sets_b + 255) & ~size_t(255);
+  const size_t tab_b = off_g + g_b;
   Arena A{(char*)base, kStaticScratchBytes, 0};
-  int* d_status = (int*)A.take(sizeof(int32_t) * 4);  // [0] status, [2], [3] list totals
+  // [0] this call's status, [1] raster waits (sticky until reported), [2], [3] list totals
+  int* d_status = (int*)A.take(sizeof(int32_t) * 4);
   float* nacc = (float*)A.take(sizeof(float) * 3 * (size_t)V);
   float4* pos = (float4*)A.take(sizeof(float4) * (size_t)pp.n_slots * V);
   float4* nrm = (float4*)A.take(sizeof(float4) * (size_t)pp.n_slots * V);
   TriRec* recs = (TriRec*)A.take(sizeof(TriRec) * (size_t)pp.n_sets * std::max(F, 1));
-  SlotXform* d_xf = (SlotXform*)A.take(sizeof(SlotXform) * xf.size());
-  int2* d_sets = (int2*)A.take(sizeof(int2) * sets.size());
-  Group* d_groups = (Group*)A.take(sizeof(Group) * groups.size());
-  int32_t *offs[2], *tmp[2], *list[2];
+  char* d_tab = (char*)A.take(tab_b);
+  int32_t *offs[2] = {nullptr, nullptr}, *tmp[2] = {nullptr, nullptr}, *list[2];
   int32_t* counts = (int32_t*)A.take(sizeof(int32_t) * 2 * (size_t)nb);  // core, soft counts (then cursors)
   for (int q = 0; q < 2; ++q) {
     offs[q] = (int32_t*)A.take(sizeof(int32_t) * (size_t)(nb + 1));
     tmp[q] = (int32_t*)A.take(sizeof(int32_t) * scan_temp_ints((int)nb));
   }
-  if (!d_status || !nacc || !pos || !nrm || !recs || !d_xf || !d_sets || !d_groups || !counts || !offs[1] ||
-      !tmp[1] || nb > (1LL << 30))
+  if (!d_status || !nacc || !pos || !nrm || !recs || !d_tab || !counts || !offs[1] || !tmp[1])
     return fail(c, MBR_ERR_ARG,
                 "render needs more than the %zu MiB static scratch (V=%d F=%d T=%d %dx%d); use mbr_render_blur",
                 kStaticScratchBytes >> 20, V, F, T, W, H);
-  pp.d_xf = d_xf;
-  pp.d_groups = d_groups;
-  CUDA_TRY(c, cudaMemcpyAsync(d_xf, xf.data(), sizeof(SlotXform) * xf.size(), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(c, cudaMemcpyAsync(d_sets, sets.data(), sizeof(int2) * sets.size(), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(c, cudaMemcpyAsync(d_groups, groups.data(), sizeof(Group) * groups.size(), cudaMemcpyHostToDevice, st));
+  pp.d_xf = (SlotXform*)d_tab;
+  const int2* d_sets = (const int2*)(d_tab + off_sets);
+  pp.d_groups = (Group*)(d_tab + off_g);
+  {
+    std::vector<char> h(tab_b, 0);
+    std::memcpy(h.data(), xf.data(), xf_b);
+    std::memcpy(h.data() + off_sets, sets.data(), sets_b);
+    std::memcpy(h.data() + off_g, groups.data(), g_b);
+    // pageable source: the copy is staged before cudaMemcpyAsync returns
+    CUDA_TRY(c, cudaMemcpyAsync(d_tab, h.data(), tab_b, cudaMemcpyHostToDevice, st));
+  }
 
-  // the array keeps the previous call's contents: clear everything that accumulates
+  // the array keeps the previous call's contents: clear everything that accumulates (not [1])
   CUDA_TRY(c, cudaMemsetAsync(d_status, 0, sizeof(int32_t), st));
   CUDA_TRY(c, cudaMemsetAsync(nacc, 0, sizeof(float) * 3 * V, st));
   launch_face_normals(mesh->verts, mesh->faces, F, V, nacc, d_status, st);
-  launch_xform(mesh->verts, nacc, V, d_xf, pp.n_slots, cam->tan_half_fov, pos, nrm, st);
+  launch_xform(mesh->verts, nacc, V, pp.d_xf, pp.n_slots, cam->tan_half_fov, pos, nrm, st);
   launch_setup(pos, mesh->faces, F, V, d_sets, pp.n_sets, cam->znear, recs, st);
   int32_t status4[4] = {0, 0, 0, 0};  // pageable: the copy below is synchronised before it is read
   BinTargets bt{};
@@ -1527,13 +1601,18 @@ int noalloc_forward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, 
   }
   sp.total = d_status + 2;
   sp.n = (int)nb;
-  launch_bin(false, recs, F, d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles, kCoreMargin, pp.r + kCoreMargin,
+  launch_bin(false, recs, F, pp.d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles, kCoreMargin, pp.r + kCoreMargin,
              bt, d_status, st);
   launch_scan_pair(sp, st);
   CUDA_TRY(c, cudaGetLastError());
   CUDA_TRY(c, cudaMemcpyAsync(status4, d_status, sizeof(status4), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(c, cudaStreamSynchronize(st));
   if (status4[0] & kStatusBadFace) return fail(c, MBR_ERR_ARG, "face index outside [0, V)");
+  if (status4[1] & kStatusSpin) {
+    CUDA_TRY(c, cudaMemsetAsync(d_status + 1, 0, sizeof(int32_t), st));
+    return fail(c, MBR_ERR_TIMEOUT,
+                "a raster launch of an earlier call gave up a bounded wait (its output is incomplete)");
+  }
   const int32_t host[2] = {status4[2], status4[3]};
   for (int q = 0; q < 2; ++q) {
     list[q] = (int32_t*)A.take(sizeof(int32_t) * (size_t)std::max(host[q], 1));
@@ -1546,43 +1625,49 @@ int noalloc_forward(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, 
     bt.off[q] = offs[q];
     bt.cap[q] = host[q];
   }
-  launch_bin(true, recs, F, d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles, kCoreMargin, pp.r + kCoreMargin, bt,
+  launch_bin(true, recs, F, pp.d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles, kCoreMargin, pp.r + kCoreMargin, bt,
              d_status, st);
   CUDA_TRY(c, cudaGetLastError());
 
   // unit order, then the raster into the caller's image (accumulated when the groups are split)
   pp.core_cap = host[0];
   pp.soft_cap = host[1];
-  RasterParams* d_par = (RasterParams*)A.take(sizeof(RasterParams));
-  int32_t* d_off = (int32_t*)A.take(sizeof(int32_t) * 2);
-  int32_t* d_cnt = (int32_t*)A.take(sizeof(int32_t));
+  struct QueueHead {  // the raster's parameters, its work offsets and the queue counter, one copy
+    RasterParams P;
+    int32_t off[2];
+    int32_t counter;
+  };
+  QueueHead* d_head = (QueueHead*)A.take(sizeof(QueueHead));
   pp.d_order = (int32_t*)A.take(sizeof(int32_t) * (pp.n_units + unit_order_ints(pp.n_units)));
-  if (!d_par || !d_off || !d_cnt || !pp.d_order)
+  if (!d_head || !pp.d_order)
     return fail(c, MBR_ERR_ARG, "render needs more than the %zu MiB static scratch; use mbr_render_blur",
                 kStaticScratchBytes >> 20);
   launch_unit_order(offs[0], offs[1], pp.G, pp.n_tiles, tw, pp.n_split, pp.n_units, pp.d_order,
                     pp.d_order + pp.n_units, nullptr, nullptr, st);
   const RasterBufs bufs{recs, nrm, {offs[0], offs[1]}, {list[0], list[1]}};
-  RasterParams P = raster_params(c, bufs, mesh, cam, T, H, W, pp);
-  P.out = (float4*)image;
+  QueueHead head;
+  std::memset(&head, 0, sizeof(head));
+  head.P = raster_params(c, bufs, mesh, cam, T, H, W, pp);
+  head.P.out = (float4*)image;
+  head.off[0] = 0;
+  head.off[1] = head.P.work;
+  head.counter = 0;
   if (pp.n_split > 1) CUDA_TRY(c, cudaMemsetAsync(image, 0, sizeof(float4) * (size_t)H * W, st));
-  const int32_t off[2] = {0, P.work};
-  CUDA_TRY(c, cudaMemcpyAsync(d_par, &P, sizeof(RasterParams), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(c, cudaMemcpyAsync(d_off, off, sizeof(off), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(c, cudaMemsetAsync(d_cnt, 0, sizeof(int32_t), st));
+  // the stream is idle after the binning sync, so this pageable copy does not wait
+  CUDA_TRY(c, cudaMemcpyAsync(d_head, &head, sizeof(head), cudaMemcpyHostToDevice, st));
   WorkQueue Q;
-  Q.items = d_par;
-  Q.item_off = d_off;
+  Q.items = &d_head->P;
+  Q.item_off = d_head->off;
   Q.n_items = 1;
-  Q.n_work = P.work;
-  Q.counter = d_cnt;
-  Q.status = d_status;
+  Q.n_work = head.P.work;
+  Q.counter = &d_head->counter;
+  Q.status = d_status + 1;  // sticky: reported by the next call's binning sync
+  set_wait_fields(Q);
   const int kind = raster_kind(pp, mesh, cam);
   const int grid = std::max(1, std::min(persistent_grid_fwd(c->num_sms, tw, pp.spt, kind), Q.n_work));
   launch_raster_fwd(Q, tw, pp.spt, kind, grid, st);
   CUDA_TRY(c, cudaGetLastError());
-  // (copies from pageable host memory are staged before cudaMemcpyAsync returns)
-  return MBR_OK;
+  return check_waits_now(c, Q.status, st);
 }
 
 }  // namespace

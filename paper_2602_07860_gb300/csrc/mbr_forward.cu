@@ -724,6 +724,30 @@ __global__ void count_kernel(const TriRec* __restrict__ recs, int F, const Group
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
+// ---------------------------------------------------------------- FP32 peak (measurement)
+// Independent FMA chains: each thread runs kChains chains of a = a * m + c, kUnroll steps per
+// iteration, so every warp has kChains independent FMAs in flight and the FMA pipe, not the
+// dependency latency, sets the rate.  m and c keep the values near 1 (no overflow, no denormals);
+// the result is stored only if it equals an impossible value, so the chains cannot be removed.
+constexpr int kPeakChains = 8, kPeakUnroll = 16, kPeakThreads = 256;
+
+__global__ void __launch_bounds__(kPeakThreads) fma_peak_kernel(int iters, float m, float c, float* sink) {
+  float a[kPeakChains];
+#pragma unroll
+  for (int q = 0; q < kPeakChains; ++q) a[q] = 1.0f + 1e-3f * (float)(threadIdx.x + q);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < kPeakUnroll; ++u) {
+#pragma unroll
+      for (int q = 0; q < kPeakChains; ++q) a[q] = fmaf(a[q], m, c);
+    }
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int q = 0; q < kPeakChains; ++q) s += a[q];
+  if (s == -1.0f) sink[blockIdx.x] = s;  // never true for these chains
+}
+
 // ---------------------------------------------------------------- launch wrappers
 void launch_face_normals(const float* verts, const int32_t* faces, int F, int V, float* nacc, int* status,
                          cudaStream_t st) {
@@ -831,6 +855,16 @@ void launch_raster_fwd(const WorkQueue& Q, int tile, int spt, int kind, int grid
     if (tile == 8) launch_fwd_tile<8, 8, false>(Q, spt, k, grid, st);
     else launch_fwd_tile<16, 16, false>(Q, spt, k, grid, st);
   }
+}
+
+double launch_fma_peak(int num_sms, int iters, float* sink, cudaStream_t st) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fma_peak_kernel, kPeakThreads, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int grid = num_sms * per_sm;
+  fma_peak_kernel<<<grid, kPeakThreads, 0, st>>>(iters, 0.999999f, 1e-6f, sink);
+  return 2.0 * kPeakChains * kPeakUnroll * (double)iters * grid * kPeakThreads;  // FMA = 2 flops
 }
 
 size_t unit_order_ints(int n_units) { return (size_t)n_units; }

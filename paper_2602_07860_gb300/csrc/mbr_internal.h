@@ -60,6 +60,9 @@ void launch_raster_count(const WorkQueue& Q, int spt, int kind, int grid, cudaSt
 void launch_count(const TriRec* recs, int F, const Group* groups, int G, int W, int H, float r,
                   unsigned long long* out, cudaStream_t st);
 
+// FP32 peak measurement: one launch of FMA chains filling every SM; returns the flops it executes
+double launch_fma_peak(int num_sms, int iters, float* sink, cudaStream_t st);
+
 void launch_raster_bwd(const WorkQueue& Q, int tile, int spt, int kind, int grid, cudaStream_t st);
 void launch_slot_chain(const float* verts, const float* nacc, int V, const SlotXform* xf, int n_slots, float th,
                        const float4* g_slot, const float4* g_alb4, float* g_verts, float* g_m, float* g_albedo,

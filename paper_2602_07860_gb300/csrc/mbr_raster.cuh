@@ -572,11 +572,15 @@ struct WorkQueue {
   int32_t n_items, n_work;    // n_work = total units
   int32_t* counter;           // zeroed before the launch
   int32_t* status;            // device status word (kStatusSpin if a wait gave up)
+  int32_t spin_limit;         // polls (x ~64 ns) before a wait gives up; kSpinLimit normally
+  int32_t stall;              // test hook: 1 = claimed units are never published, so every wait
+                              // for a publication runs into its limit (nothing faults or hangs)
 };
 
 constexpr int kBlocksPerUnit = 8;
 constexpr int kRing = 4;              // units a CTA may have in flight
-constexpr int kSpinLimit = 1 << 22;   // bounded waits (x ~64 ns): far beyond any real wait
+constexpr int kSpinLimit = 1 << 22;   // default bounded wait (x ~64 ns, about 0.27 s): far beyond any real wait
+
 
 template <int TW, int TH>
 struct UnitMap {
@@ -624,19 +628,19 @@ __device__ __forceinline__ bool warp_next(const WorkQueue& Q, CtaQueue& cq, Rast
       int it = 0;
       const int need = kBlocksPerUnit * (L / kRing);  // readers of the slot's previous units
       while (ld_volatile(&cq.used[slot]) < need) {
-        if (++it > kSpinLimit) { ok = false; break; }
+        if (++it > Q.spin_limit) { ok = false; break; }
         __nanosleep(64);
       }
       __threadfence_block();
       if (ok) {
         cq.unit[slot] = atomicAdd(Q.counter, 1);
         __threadfence_block();
-        *reinterpret_cast<volatile int*>(&cq.ready[slot]) = L + 1;
+        if (!Q.stall) *reinterpret_cast<volatile int*>(&cq.ready[slot]) = L + 1;
       }
     } else {
       int it = 0;
       while (ld_volatile(&cq.ready[slot]) != L + 1) {
-        if (++it > kSpinLimit) { ok = false; break; }
+        if (++it > Q.spin_limit) { ok = false; break; }
         __nanosleep(64);
       }
       __threadfence_block();

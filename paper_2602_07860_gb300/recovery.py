@@ -89,10 +89,12 @@ def laplacian_loss(verts, edges):
 
 
 def recover_shape(template, faces, albedo, views, targets, T, H, W, iters=500, lr=1e-3, lap_weight=0.1,
-                  solver="fast", log_every=0):
+                  solver="fast", log_every=0, on_iter=None):
     """Adam on the vertices of ``template`` [V,3] so that their blurred renders under ``views``
     (list of (Motion, Camera)) match ``targets`` [n, H, W, 4].  Loss = mean squared RGBA error
-    summed over views + lap_weight x Laplacian term.  Returns (vertices, loss history)."""
+    summed over views + lap_weight x Laplacian term.  ``on_iter(it, verts, image_loss)``, if
+    given, sees the vertices each iteration renders (before its Adam step).  Returns (vertices,
+    loss history)."""
     v = template.detach().clone().contiguous().requires_grad_(True)
     vb = ViewBatch(v, faces, albedo, views, T, H, W, solver)
     edges = edge_index(faces, v.shape[0])
@@ -103,6 +105,8 @@ def recover_shape(template, faces, albedo, views, targets, T, H, W, iters=500, l
         imgs = vb.render()
         img_loss = ((imgs - targets) ** 2).mean(dim=(1, 2, 3)).sum()
         loss = img_loss + lap_weight * laplacian_loss(v, edges)
+        if on_iter is not None:
+            on_iter(it, v.detach(), img_loss.detach())
         loss.backward()
         opt.step()
         hist.append((float(img_loss.detach()), float(loss.detach())))

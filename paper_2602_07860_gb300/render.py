@@ -157,6 +157,14 @@ class Context:
         self._raise(self.L.mbr_get_stats(self.h, ctypes.byref(st)))
         return {k: getattr(st, k) for k, _ in st._fields_}
 
+    def measure_fp32_peak(self, iters=20000, launches=10):
+        """Measured FP32 peak (TFLOP/s) and its raw figures: FMA chains on every SM, CUDA-event
+        timed (mbr_measure_fp32_peak)."""
+        fl, ms = ctypes.c_double(), ctypes.c_float()
+        self._raise(self.L.mbr_measure_fp32_peak(self.h, iters, launches, ctypes.byref(fl), ctypes.byref(ms),
+                                                 _stream()))
+        return fl.value / (ms.value * 1e-3) / 1e12, fl.value, ms.value
+
     def set_tuning(self, tile=16, spt=2, splits=0):
         self._raise(self.L.mbr_set_tuning(self.h, int(tile), int(spt), int(splits)))
 

@@ -372,6 +372,14 @@ def config2(seed=MASTER_SEED + 2, T=64, H=256, W=256):
     return scene(v, f, alb, rotate(axis, 2 * math.pi), camera(look_at(orbit_eye(4.0, 0, 0))), T, H, W)
 
 
+def config2_translate(seed=MASTER_SEED + 2, T=64, H=256, W=256):
+    """Translation counterpart of config2 (the paper times its solvers on linear translation,
+    Sec. 4.2): the same subdiv-4, SH-6 mesh and albedo, moved by d = (1.5, 0, 0) perpendicular
+    to the view axis and centred on the origin (o = -d/2); T = 64, 256x256, one linear segment."""
+    sc = config2(seed, T, H, W)
+    return dict(sc, motion=translate((1.5, 0.0, 0.0)))
+
+
 def config3(seed=MASTER_SEED + 3, T=64, H=256, W=256):
     """Shape recovery: target subdiv-4 sphere with SH displacement (degree <= 8, N(0, 0.08)); 8 blurred
     views (4 translations with |d| ~ U[0.5, 2], 4 rotations with omega ~ U[pi, 4pi]) seen from

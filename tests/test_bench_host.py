@@ -58,3 +58,20 @@ def test_reference_window_is_bounded():
     rows = [bench.ref_window(k)[3] for k in (201, 400, 600, 10**6)]
     assert rows == sorted(rows, reverse=True) and rows[0] < h and rows[-1] == 16
     assert all(bench.ref_window(k)[:3] == (x0, y0, w) for k in (1, 600, 10**6))
+
+
+def test_captured_counters_only_describe_the_captured_build():
+    """ncu counters attach to the bench line only for the kernel sources and the tile /
+    samples-per-group they were captured with."""
+    saved = dict(bench.CAPTURED)
+    try:
+        bench.CAPTURED.update(sources=bench.kernel_sources_sha(), tile=8, spt=2,
+                              kernels={"raster_bwd_persistent": {"dram_bytes": 1.0, "pipes_pct": {}}})
+        assert bench.captured_counters("raster_bwd_persistent", 8, 2) == {"dram_bytes": 1.0, "pipes_pct": {}}
+        assert bench.captured_counters("raster_bwd_persistent", 8, 1) is None
+        assert bench.captured_counters("raster_fwd_persistent", 8, 2) is None
+        bench.CAPTURED["sources"] = "0" * 16
+        assert bench.captured_counters("raster_bwd_persistent", 8, 2) is None
+    finally:
+        bench.CAPTURED.clear()
+        bench.CAPTURED.update(saved)
