@@ -71,6 +71,12 @@ def lib():
         L.orc_render_backward.argtypes = [P(OrcScene), c_int32, c_int32, c_int32, c_int32, c_int32,
                                           c_int32, P(c_double), P(c_double), P(c_double), P(c_int64)]
         L.orc_render_backward.restype = c_int32
+        L.orc_sdf_extract.argtypes = [c_int32, P(c_double), P(c_double), c_double, c_int64, c_int64, P(c_double),
+                                      P(c_int64), P(c_int32), P(c_int64)]
+        L.orc_sdf_extract.restype = c_int32
+        L.orc_sdf_extract_backward.argtypes = [c_int32, P(c_double), P(c_double), c_double, c_int64, P(c_int64),
+                                               P(c_double), P(c_double)]
+        L.orc_sdf_extract_backward.restype = c_int32
         _lib = L
     return _lib
 
@@ -213,3 +219,44 @@ def render_backward(sc, dl_drgba, mode="fast", window=None, soft_all=False, text
     if texture_grad is not None:
         texture_grad[...] = S.gtex
     return gv, ga, cnt
+
+
+def sdf_extract(sdf, lo, h):
+    """Marching-tetrahedra mesh of the zero level set of ``sdf`` [(n+1),(n+1),(n+1)] (indexed
+    [k, j, i], i.e. z, y, x) sampled at lo + h (i, j, k): (verts [V,3], vert_edges [V,2] grid
+    index pairs a < b, faces [F,3] facing s >= 0).  Vertices are in ascending (a, b) order."""
+    s = np.ascontiguousarray(sdf, dtype=np.float64)
+    n = s.shape[0] - 1
+    assert s.shape == (n + 1,) * 3
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    cnt = np.zeros(2, dtype=np.int64)
+    e = np.zeros(1, dtype=np.int64)
+    rc = lib().orc_sdf_extract(n, _ptr(s, c_double), _ptr(lo, c_double), float(h), 0, 0, None, None, None,
+                               _ptr(cnt, c_int64))
+    if rc < 0:
+        raise RuntimeError("orc_sdf_extract failed")
+    V, F = int(cnt[0]), int(cnt[1])
+    verts = np.zeros((max(V, 1), 3))
+    edges = np.zeros((max(V, 1), 2), dtype=np.int64)
+    faces = np.zeros((max(F, 1), 3), dtype=np.int32)
+    rc = lib().orc_sdf_extract(n, _ptr(s, c_double), _ptr(lo, c_double), float(h), V, F, _ptr(verts, c_double),
+                               _ptr(edges, c_int64), _ptr(faces, c_int32), _ptr(cnt, c_int64))
+    if rc != 0:
+        raise RuntimeError("orc_sdf_extract failed")
+    del e
+    return verts[:V], edges[:V], faces[:F]
+
+
+def sdf_extract_backward(sdf, lo, h, vert_edges, dl_dverts):
+    """dL/dsdf (same shape as sdf) for dL/dverts [V,3] of sdf_extract's vertices."""
+    s = np.ascontiguousarray(sdf, dtype=np.float64)
+    n = s.shape[0] - 1
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    ve = np.ascontiguousarray(vert_edges, dtype=np.int64)
+    g = np.ascontiguousarray(dl_dverts, dtype=np.float64)
+    out = np.zeros_like(s)
+    rc = lib().orc_sdf_extract_backward(n, _ptr(s, c_double), _ptr(lo, c_double), float(h), len(ve),
+                                        _ptr(ve, c_int64), _ptr(g, c_double), _ptr(out, c_double))
+    if rc != 0:
+        raise RuntimeError("orc_sdf_extract_backward failed")
+    return out

@@ -9,6 +9,7 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "mbr_oracle.c")
+SRC_SDF = os.path.join(HERE, "sdf_oracle.c")
 HDR = os.path.join(HERE, "mbr_oracle.h")
 
 
@@ -19,11 +20,11 @@ def library_path():
 def build(force=False):
     out = library_path()
     if not force and os.path.exists(out) and os.path.getmtime(out) >= max(
-            os.path.getmtime(SRC), os.path.getmtime(HDR)):
+            os.path.getmtime(SRC), os.path.getmtime(SRC_SDF), os.path.getmtime(HDR)):
         return out
     tmp = out + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-Wextra", "-Wno-unused-parameter",
-           "-o", tmp, SRC, "-lm"]
+           "-o", tmp, SRC, SRC_SDF, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out

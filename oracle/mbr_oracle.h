@@ -114,6 +114,19 @@ int32_t orc_render_backward(const orc_scene* s, int32_t mode, int32_t flags, int
                             int32_t y0, int32_t w, int32_t h, const double* dl_drgba,
                             double* dl_dverts, double* dl_dalbedo, int64_t* counters);
 
+/* SDF -> triangle mesh extraction (rotational recovery, Sec. 5), marching tetrahedra on a regular
+ * grid of n cells per axis; s [(n+1)^3] samples at lo + h (i, j, k), index (k (n+1) + j) (n+1) + i.
+ * Writes up to max_verts vertices [V,3] in ascending order of their grid edge (a, b) (a < b,
+ * vert_edges [V,2], may be NULL) and up to max_faces faces [F,3] facing the outside (s >= 0);
+ * counts[0] = V, counts[1] = F.  Returns 0, 1 if the outputs are too small (counts still set),
+ * -1 on bad arguments.  See sdf_oracle.c for the rules. */
+int32_t orc_sdf_extract(int32_t n, const double* s, const double lo[3], double h, int64_t max_verts,
+                        int64_t max_faces, double* verts, int64_t* vert_edges, int32_t* faces, int64_t* counts);
+/* adjoint of the vertex positions w.r.t. the samples (topology held fixed): dl_ds [(n+1)^3]
+ * accumulates (the caller zeroes it) */
+int32_t orc_sdf_extract_backward(int32_t n, const double* s, const double lo[3], double h, int64_t n_verts,
+                                 const int64_t* vert_edges, const double* dl_dverts, double* dl_ds);
+
 #ifdef __cplusplus
 }
 #endif
