@@ -259,6 +259,32 @@ int mbr_render_blur_noalloc(const mbr_mesh* mesh, const mbr_motion* motion, cons
                             int32_t T, int32_t H, int32_t W, int32_t solver, float* image,
                             void* cuda_stream, char* err, int32_t err_len);
 
+/* SDF -> triangle mesh (the rotational recovery of Sec. 5 optimises a signed distance field and
+ * extracts the mesh it renders from it differentiably; the paper uses FlexiCubes, this library
+ * marching tetrahedra).  sdf [(n+1)^3] DEVICE float samples at lo + h (i, j, k) (lo HOST [3]),
+ * index (k (n+1) + j) (n+1) + i, 1 <= n <= 512; a sample is inside when s < 0.  Every grid cube is
+ * split into the six tetrahedra corner 0 -> +e_a -> +e_a +e_b -> corner 7 (one per order of the
+ * axes); every tetrahedron edge whose ends differ in sign carries one vertex at the zero of the
+ * linear interpolant, p = p_a + t (p_b - p_a), t = s_a / (s_a - s_b), shared by the tetrahedra of
+ * that grid edge.  A tetrahedron with one corner alone on its side gives one triangle, two and two
+ * the quad on the crossing edges (a,c), (a,d), (b,d), (b,c) (a < b inside, c < d outside in
+ * tetrahedron order) cut along (a,c)-(b,d); every face is wound so that its normal points outside
+ * (s >= 0).  Writes the vertices [V,3] and faces [F,3] (DEVICE, caller-owned, capacities max_verts
+ * and max_faces; V <= 7 (n+1)^3 and F <= 12 n^3 always hold), and if vert_edges is not NULL the grid
+ * indices (a, b), a < b, of each vertex's edge [V,2] (needed by the adjoint).  counts (HOST [2])
+ * receives V and F; if they exceed the capacities nothing is written and MBR_ERR_ARG is returned
+ * with counts set.  The call synchronises its stream once (to read V and F). */
+int mbr_sdf_extract(mbr_ctx* ctx, int32_t n, const float* sdf, const float lo[3], float h, int32_t max_verts,
+                    int32_t max_faces, float* verts, int32_t* faces, int32_t* vert_edges, int32_t* counts,
+                    void* cuda_stream);
+
+/* Adjoint of mbr_sdf_extract's vertex positions w.r.t. the samples, the crossing topology held
+ * fixed: dL/ds_a += dL/dt (-s_b) / (s_a - s_b)^2, dL/ds_b += dL/dt s_a / (s_a - s_b)^2 with
+ * dL/dt = dL/dp . (p_b - p_a).  dl_dverts [n_verts,3] and vert_edges [n_verts,2] as returned by the
+ * extraction of the same sdf; dl_dsdf [(n+1)^3] DEVICE is overwritten.  Stream-ordered. */
+int mbr_sdf_extract_backward(mbr_ctx* ctx, int32_t n, const float* sdf, float h, int32_t n_verts,
+                             const int32_t* vert_edges, const float* dl_dverts, float* dl_dsdf, void* cuda_stream);
+
 /* Measurement hook: the FP32 CUDA-core peak of this GPU, measured.  Runs `launches` back-to-back
  * launches of a kernel that fills every SM with independent FMA chains (`iters` x 128 FMAs per
  * thread each), timed by CUDA events on the stream; *flops receives the FP32 operations executed

@@ -20,7 +20,7 @@ SOLVERS = {"plain": MBR_PLAIN, "fast": MBR_FAST}
 EXPORTS = ["mbr_create", "mbr_destroy", "mbr_render_blur", "mbr_render_blur_backward",
            "mbr_render_blur_backward_reuse", "mbr_render_blur_batch",
            "mbr_debug_winners", "mbr_count_candidates", "mbr_count_work", "mbr_set_tuning", "mbr_set_profiling", "mbr_get_stats",
-           "mbr_render_blur_noalloc", "mbr_autotune", "mbr_measure_fp32_peak", "mbr_debug_wait_limit", "mbr_last_error"]
+           "mbr_render_blur_noalloc", "mbr_autotune", "mbr_sdf_extract", "mbr_sdf_extract_backward", "mbr_measure_fp32_peak", "mbr_debug_wait_limit", "mbr_last_error"]
 
 
 class MbrMesh(ctypes.Structure):
@@ -107,6 +107,12 @@ def load(build_if_missing=True):
     L.mbr_render_blur_noalloc.argtypes = [P(MbrMesh), P(MbrMotion), P(MbrCamera), c_int32, c_int32, c_int32,
                                           c_int32, c_void_p, c_void_p, ctypes.c_char_p, c_int32]
     L.mbr_render_blur_noalloc.restype = c_int32
+    L.mbr_sdf_extract.argtypes = [c_void_p, c_int32, c_void_p, P(c_float), c_float, c_int32, c_int32, c_void_p,
+                                  c_void_p, c_void_p, P(c_int32), c_void_p]
+    L.mbr_sdf_extract.restype = c_int32
+    L.mbr_sdf_extract_backward.argtypes = [c_void_p, c_int32, c_void_p, c_float, c_int32, c_void_p, c_void_p,
+                                           c_void_p, c_void_p]
+    L.mbr_sdf_extract_backward.restype = c_int32
     L.mbr_measure_fp32_peak.argtypes = [c_void_p, c_int32, c_int32, P(ctypes.c_double), P(c_float), c_void_p]
     L.mbr_measure_fp32_peak.restype = c_int32
     L.mbr_debug_wait_limit.argtypes = [c_int32, c_int32, c_int32]

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["mbr_forward.cu", "mbr_backward.cu", "mbr_api.cu"]
+SOURCES = ["mbr_forward.cu", "mbr_backward.cu", "mbr_api.cu", "mbr_sdf.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -60,6 +60,7 @@ struct mbr_ctx {
   int tile = 16, spt = 2, splits = 0;
   // scratch
   DevBuf nacc, pos, nrm, recs, tables, partial, gslot, galb, gm, cnt64, status, order, bstate, bin_counts;
+  DevBuf sdf_cnt, sdf_off, sdf_tmp;  // SDF extraction: edge flags + triangle counts, their scans
   FwdCostKey fcost;  // unit layout of the last forward whose per-unit cost is in the order buffer
   BinSet core, soft;  // undilated bins (coverage) and r_soft-dilated bins (soft coverage)
   void* host_stage = nullptr;
@@ -801,7 +802,7 @@ int mbr_create(mbr_ctx** out) {
   }
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   if (c->num_sms < 1) c->num_sms = 1;
-  if (cudaMallocHost(&c->host_total, sizeof(int32_t) * 4) != cudaSuccess) {
+  if (cudaMallocHost(&c->host_total, sizeof(int32_t) * 16) != cudaSuccess) {
     delete c;
     return MBR_ERR_OOM;
   }
@@ -819,7 +820,7 @@ int mbr_create(mbr_ctx** out) {
 void mbr_destroy(mbr_ctx* c) {
   if (!c) return;
   DevBuf* bufs[] = {&c->nacc, &c->pos, &c->nrm, &c->recs, &c->tables, &c->partial, &c->gslot, &c->galb, &c->gm,
-                    &c->cnt64, &c->order, &c->bstate,
+                    &c->cnt64, &c->order, &c->bstate, &c->sdf_cnt, &c->sdf_off, &c->sdf_tmp,
                     &c->status, &c->queue, &c->bin_counts, &c->core.offsets, &c->core.list,
                     &c->core.scan_tmp, &c->soft.offsets, &c->soft.list,
                     &c->soft.scan_tmp};
@@ -857,6 +858,65 @@ int mbr_get_stats(mbr_ctx* c, mbr_stats* out) {
 }
 
 const char* mbr_last_error(mbr_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int mbr_sdf_extract(mbr_ctx* c, int32_t n, const float* sdf, const float lo[3], float h, int32_t max_verts,
+                    int32_t max_faces, float* verts, int32_t* faces, int32_t* vert_edges, int32_t* counts,
+                    void* stream) {
+  if (!c) return MBR_ERR_ARG;
+  c->err.clear();
+  if (n < 1 || n > 512 || !sdf || !lo || !(h > 0.f) || !counts || max_verts < 0 || max_faces < 0 ||
+      (max_verts > 0 && !verts) || (max_faces > 0 && !faces))
+    return fail(c, MBR_ERR_ARG, "bad SDF extraction arguments (n in [1, 512], h > 0, output buffers)");
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long m = (long long)n + 1, n_edges = m * m * m * 7;  // >= the tetrahedron count n^3 6
+  int rc;
+  // [0] edge flags -> vertex ids, [1] triangles per tetrahedron -> face offsets (zero-padded)
+  if ((rc = ensure(c, c->sdf_cnt, sizeof(int32_t) * 2 * (size_t)n_edges, st))) return rc;
+  if ((rc = ensure(c, c->sdf_off, sizeof(int32_t) * 2 * (size_t)(n_edges + 1), st))) return rc;
+  if ((rc = ensure(c, c->sdf_tmp, sizeof(int32_t) * 2 * scan_temp_ints((int)n_edges), st))) return rc;
+  int32_t* cnt = (int32_t*)c->sdf_cnt.p;
+  int32_t* off = (int32_t*)c->sdf_off.p;
+  int32_t* d_tot = (int32_t*)c->status.p + 8;  // [8], [9]: vertex and face totals
+  CUDA_TRY(c, cudaMemsetAsync(cnt + n_edges, 0, sizeof(int32_t) * (size_t)n_edges, st));
+  launch_sdf_count(n, sdf, cnt, cnt + n_edges, st);
+  ScanPair sp{};
+  for (int q = 0; q < 2; ++q) {
+    sp.in[q] = cnt + q * (size_t)n_edges;
+    sp.out[q] = off + q * (size_t)(n_edges + 1);
+    sp.sums[q] = (int32_t*)c->sdf_tmp.p + q * scan_temp_ints((int)n_edges);
+  }
+  sp.total = d_tot;
+  sp.n = (int)n_edges;
+  launch_scan_pair(sp, st);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaMemcpyAsync(c->host_total, d_tot, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(c, cudaStreamSynchronize(st));
+  counts[0] = c->host_total[0];
+  counts[1] = c->host_total[1];
+  if (counts[0] > max_verts || counts[1] > max_faces)
+    return fail(c, MBR_ERR_ARG, "the mesh has %d vertices and %d faces; the outputs hold %d and %d", counts[0],
+                counts[1], max_verts, max_faces);
+  launch_sdf_write(n, sdf, lo, h, off, off + n_edges + 1, verts, vert_edges, faces, st);
+  CUDA_TRY(c, cudaGetLastError());
+  c->stats.launches += 6;
+  return MBR_OK;
+}
+
+int mbr_sdf_extract_backward(mbr_ctx* c, int32_t n, const float* sdf, float h, int32_t n_verts,
+                             const int32_t* vert_edges, const float* dl_dverts, float* dl_dsdf, void* stream) {
+  if (!c) return MBR_ERR_ARG;
+  c->err.clear();
+  if (n < 1 || n > 512 || !sdf || !(h > 0.f) || n_verts < 0 || (n_verts > 0 && (!vert_edges || !dl_dverts)) ||
+      !dl_dsdf)
+    return fail(c, MBR_ERR_ARG, "bad SDF adjoint arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t m = (size_t)n + 1;
+  CUDA_TRY(c, cudaMemsetAsync(dl_dsdf, 0, sizeof(float) * m * m * m, st));
+  launch_sdf_grad(n, sdf, h, n_verts, vert_edges, dl_dverts, dl_dsdf, st);
+  CUDA_TRY(c, cudaGetLastError());
+  c->stats.launches += 1;
+  return MBR_OK;
+}
 
 int mbr_measure_fp32_peak(mbr_ctx* c, int32_t iters, int32_t launches, double* flops, float* ms, void* stream) {
   if (!c) return MBR_ERR_ARG;

@@ -70,4 +70,13 @@ void launch_slot_chain(const float* verts, const float* nacc, int V, const SlotX
 void launch_normals_bwd(const float* verts, const int32_t* faces, int F, int V, const float* g_m, float* g_verts,
                         cudaStream_t st);
 
+// SDF -> mesh (rotational recovery): per edge id (7 per grid point) a sign-change flag and per
+// tetrahedron (6 per cube) its triangle count; then, from their exclusive scans, the vertices
+// (positions, grid edges) and the oriented faces; and the adjoint dL/dverts -> dL/ds (accumulated)
+void launch_sdf_count(int n, const float* s, int32_t* edge_flag, int32_t* tet_count, cudaStream_t st);
+void launch_sdf_write(int n, const float* s, const float lo[3], float h, const int32_t* vert_off,
+                      const int32_t* face_off, float* verts, int32_t* vert_edges, int32_t* faces, cudaStream_t st);
+void launch_sdf_grad(int n, const float* s, float h, int nv, const int32_t* vert_edges, const float* dl_dverts,
+                     float* dl_ds, cudaStream_t st);
+
 }  // namespace mbr

@@ -157,6 +157,40 @@ class Context:
         self._raise(self.L.mbr_get_stats(self.h, ctypes.byref(st)))
         return {k: getattr(st, k) for k, _ in st._fields_}
 
+    def sdf_extract(self, sdf, lo, h, want_edges=True):
+        """Triangle mesh of the zero level set of ``sdf`` [(n+1)]^3 (float32, indexed [z, y, x])
+        sampled at lo + h (i, j, k) (mbr_sdf_extract): (verts [V,3], faces [F,3] int32,
+        vert_edges [V,2] int32 or None), sized to the mesh."""
+        n = sdf.shape[0] - 1
+        _check(sdf, torch.float32, (n + 1, n + 1, n + 1), "sdf")
+        lo_c = (ctypes.c_float * 3)(*[float(x) for x in lo])
+        counts = (ctypes.c_int32 * 2)()
+        # capacities that always suffice (7 edges per grid point, 12 triangles per cube), one call
+        max_v, max_f = 7 * (n + 1) ** 3, 12 * n ** 3
+        verts = torch.empty((max_v, 3), dtype=torch.float32, device=sdf.device)
+        faces = torch.empty((max_f, 3), dtype=torch.int32, device=sdf.device)
+        edges = torch.empty((max_v, 2), dtype=torch.int32, device=sdf.device) if want_edges else None
+        self._raise(self.L.mbr_sdf_extract(
+            self.h, n, ctypes.c_void_p(sdf.data_ptr()), lo_c, float(h), max_v, max_f, ctypes.c_void_p(verts.data_ptr()),
+            ctypes.c_void_p(faces.data_ptr()), ctypes.c_void_p(edges.data_ptr() if edges is not None else 0), counts,
+            _stream()))
+        V, F = counts[0], counts[1]
+        verts, faces = verts[:V], faces[:F]
+        edges = edges[:V] if edges is not None else None
+        return verts, faces, edges
+
+    def sdf_extract_backward(self, sdf, h, vert_edges, dl_dverts):
+        """dL/dsdf for dL/dverts of sdf_extract's vertices (mbr_sdf_extract_backward)."""
+        n = sdf.shape[0] - 1
+        V = vert_edges.shape[0]
+        _check(vert_edges, torch.int32, (V, 2), "vert_edges")
+        _check(dl_dverts, torch.float32, (V, 3), "dl_dverts")
+        out = torch.empty_like(sdf)
+        self._raise(self.L.mbr_sdf_extract_backward(
+            self.h, n, ctypes.c_void_p(sdf.data_ptr()), float(h), V, ctypes.c_void_p(vert_edges.data_ptr()),
+            ctypes.c_void_p(dl_dverts.data_ptr()), ctypes.c_void_p(out.data_ptr()), _stream()))
+        return out
+
     def measure_fp32_peak(self, iters=20000, launches=10):
         """Measured FP32 peak (TFLOP/s) and its raw figures: FMA chains on every SM, CUDA-event
         timed (mbr_measure_fp32_peak)."""
