@@ -435,16 +435,10 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
     P.soft.range(bi, sb, se);
 
     // ---- pass 1: winners
-    uint32_t allowed[SPT];
 #pragma unroll
-    for (int i = 0; i < SPT; ++i) {
-      allowed[i] = i < n ? img_mask : 0u;
-      ws.win[i][lane] = 0ull;
-    }
-    ws.pixs[lane] = in_img ? all_s : 0u;
+    for (int i = 0; i < SPT; ++i) ws.win[i][lane] = 0ull;
     __syncwarp();
-    CorePairs<SPT, MOVING, COUNT> core{recs_set, grp, bp, &ws, 0u, 0u};
-    for_pairs<SPT, MOVING>(recs_set, P.core.faces, cb, ce, grp, n, tb, bp, kCoreMargin, allowed, all_s, ws, core);
+    const uint32_t core_tests = core_raster<SPT, MOVING>(recs_set, P.core.faces, cb, ce, gr.tau, n, tb, bp, img_mask, ws);
     int bestf[SPT];
     uint32_t uncov = 0;
 #pragma unroll
@@ -470,6 +464,7 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
     FwdSoftPairs<SPT, MOVING, COUNT> soft{recs_set, grp, bp, &ws, gr.xbits, P.r + kCoreMargin, P.r2, P.inv_delta,
                                           EXT ? P.prob : 0, 0u, 0u, 0u};
     if (se > sb && any_s) {
+      uint32_t allowed[SPT];
 #pragma unroll
       for (int i = 0; i < SPT; ++i) {
         allowed[i] = __ballot_sync(kFullMask, (my_s >> i) & 1u);
@@ -488,8 +483,8 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
     }
     adj_cost += (int)soft.n_batches + __popc(__reduce_or_sync(kFullMask, in_img ? (all_s & ~uncov) : 0u));
     if (COUNT) {
-      n_ctest += core.n_tests;
-      n_cbatch += core.n_batches;
+      n_ctest += core_tests;
+      n_cbatch += (uint32_t)(ce - cb + 31) / 32 * ((threadIdx.x & 31) == 0);
       n_seval += soft.n_eval;
       n_sbatch += soft.n_batches;
       n_soft += soft.n_terms;

@@ -512,38 +512,76 @@ __device__ __forceinline__ void for_pairs(const TriRec* recs_set, const int32_t*
 }
 
 // pass 1: z-test winners (Sec. 3.1: coverage by the edge functions of Eq. time-dependent2, then
-// the perspective-correct depth; ties to the smaller face id) into ws.win.  COUNT: tests, batches.
-template <int SPT, bool MOVING, bool COUNT>
-struct CorePairs {
-  const TriRec* recs_set;
-  const Group* grp;
-  BlockPix bp;
-  WarpScratch<SPT>* ws;
-  uint32_t n_tests, n_batches;
-  __device__ __forceinline__ void pair(bool ok, int face, int p, uint32_t smp) {
-    if (!ok) return;
-    const float u = ws->pu[p], v = ws->pv[p];
-    float4 r[kRecF4];
-    load_record<MOVING>(recs_set + face, r, true, false);
-    const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
-    if (COUNT) n_tests += __popc(smp);
-    while (smp) {
-      const int i = __ffs(smp) - 1;
-      smp &= smp - 1u;
-      const float tau = MOVING ? __ldg(&grp->tau[i]) : 0.f;
-      const EdgeVals e = edge_vals<MOVING>(r, ps, tau);
-      if (covers(e)) {
-        const float key = fmaxf(inv_depth<MOVING>(r, e, tau), 1e-30f);  // > 0 for covered samples
-        const unsigned long long packed =
-            ((unsigned long long)__float_as_uint(key) << 32) | (unsigned long long)(~(uint32_t)face);
-        atomicMax(&ws->win[i][p], packed);
+// the perspective-correct depth; ties to the smaller face id) into ws.win.  Lanes over candidates:
+// lane j takes candidate j of the bin list and, for each sample of the group whose box at tau
+// meets the warp's block, forms the edge functions at that tau once -- for a fixed tau the
+// numerators N1, N2 and the denominator D of Eq. time-dependent2 are affine in the pixel position
+// (N1 = cross(p - o, E2(tau)) + c1 tau + a11 tau^2, N2 = cross(E1(tau), p - o) + c2 tau + a12 tau^2,
+// D = D0 + D1 tau + D2 tau^2, with E1, E2 the local edges at tau) -- together with the reciprocal
+// vertex depths and 1 / D, and then sweeps the block pixels inside that box: a coverage test is a
+// few multiply-adds and a covered pixel's depth key three more.  Returns the coverage tests.
+template <int SPT, bool MOVING>
+__device__ __forceinline__ uint32_t core_raster(const TriRec* recs_set, const int32_t* list, int beg, int end,
+                                                const float* tau_g, int n, const TileBox& tb, const BlockPix& bp,
+                                                uint32_t img_mask, WarpScratch<SPT>& ws) {
+  const int lane = threadIdx.x & 31;
+  uint32_t n_tests = 0;
+  if (tb.empty) return 0;
+  for (int c0 = beg; c0 < end; c0 += 32) {
+    const int j = c0 + lane;
+    if (j >= end) continue;
+    const int f = __ldg(list + j);
+    const TriRec* rec = recs_set + f;
+    const float4 o = __ldg(&rec->f4[kR_O]), e2 = __ldg(&rec->f4[kR_E2]), zz = __ldg(&rec->f4[kR_Z]);
+    const float4 b = __ldg(&rec->f4[kR_BB]);
+    float4 db = make_float4(0.f, 0.f, 0.f, 0.f), d = db, g = db, a = db, dz = db;
+    if (MOVING) {
+      db = __ldg(&rec->f4[kR_DBB]);
+      d = __ldg(&rec->f4[kR_D]);
+      g = __ldg(&rec->f4[kR_G]);
+      a = __ldg(&rec->f4[kR_A]);
+      dz = __ldg(&rec->f4[kR_DZ]);
+    }
+    const uint32_t key_lo = ~(uint32_t)f;
+    for (int i = 0; i < (MOVING ? n : 1); ++i) {
+      const float tau = MOVING ? __ldg(tau_g + i) : 0.f;
+      float4 bx;
+      bx.x = fmaf(tau, db.x, b.x) - kCoreMargin;
+      bx.y = fmaf(tau, db.y, b.y) + kCoreMargin;
+      bx.z = fmaf(tau, db.z, b.z) - kCoreMargin;
+      bx.w = fmaf(tau, db.w, b.w) + kCoreMargin;
+      if (bx.x > tb.u_hi || bx.y < tb.u_lo || bx.z > tb.v_hi || bx.w < tb.v_lo) continue;
+      uint32_t pm = box_pixel_mask(bx, bp) & img_mask;
+      if (!pm) continue;
+      // edge functions at tau, affine in (u, v) about the record origin
+      const float E1x = fmaf(tau, d.x, o.z), E1y = fmaf(tau, d.y, o.w);
+      const float E2x = fmaf(tau, d.z, e2.x), E2y = fmaf(tau, d.w, e2.y);
+      const float k1 = tau * fmaf(a.x, tau, g.z), k2 = tau * fmaf(a.y, tau, g.w);
+      const float D = fmaf(fmaf(a.w, tau, a.z), tau, e2.z);
+      if (!(fabsf(D) > kDetMin)) continue;
+      const float iD = __fdividef(1.0f, D);
+      const float iz0 = __fdividef(1.0f, fmaf(tau, dz.x, zz.x)), iz1 = __fdividef(1.0f, fmaf(tau, dz.y, zz.y)),
+                  iz2 = __fdividef(1.0f, fmaf(tau, dz.z, zz.z));
+      n_tests += __popc(pm);
+      while (pm) {
+        const int p = __ffs(pm) - 1;
+        pm &= pm - 1u;
+        const float qx = ws.pu[p] - o.x, qy = ws.pv[p] - o.y;
+        const float N1 = fmaf(qx, E2y, fmaf(-qy, E2x, k1));
+        const float N2 = fmaf(E1x, qy, fmaf(-E1y, qx, k2));
+        const float N0 = D - N1 - N2;
+        const bool pos = N0 >= 0.f && N1 >= 0.f && N2 >= 0.f;
+        const bool neg = N0 <= 0.f && N1 <= 0.f && N2 <= 0.f;
+        if (pos || neg) {
+          const float key = fmaxf(fmaf(N0, iz0, fmaf(N1, iz1, N2 * iz2)) * iD, 1e-30f);  // > 0 when covered
+          atomicMax(&ws.win[i][p], ((unsigned long long)__float_as_uint(key) << 32) | (unsigned long long)key_lo);
+        }
       }
     }
   }
-  __device__ __forceinline__ void batch_end(int) {
-    if (COUNT && (threadIdx.x & 31) == 0) ++n_batches;
-  }
-};
+  __syncwarp();
+  return n_tests;
+}
 
 // Soft-coverage geometry of one pair and sample: false if the factor is outside the cutoff.
 template <bool MOVING>
