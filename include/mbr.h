@@ -209,6 +209,15 @@ int mbr_count_work(mbr_ctx* ctx, const mbr_mesh* mesh, const mbr_motion* motion,
                    int32_t T, int32_t H, int32_t W, int32_t solver, float* image, int64_t* out,
                    void* cuda_stream);
 
+/* Memory of the adjoint ("Gradient Computation", Sec. 3.3).  The forward raster can keep, per
+ * pixel and sub-frame, its discrete outcome -- the winner face of a covered sample, else the log
+ * soft product and the count of vanishing factors -- 5 bytes, so that the adjoint does not repeat
+ * its coverage and soft-product passes.  It keeps them only while T x H x W x 5 bytes <= bytes
+ * (default 2^30); above that, the adjoint recomputes them per sample group from the geometry and
+ * no storage grows with T.  bytes = 0: always recompute.  Applies to every following render and
+ * batch on ctx; MBR_ERR_ARG for a negative value. */
+int mbr_set_state_budget(mbr_ctx* ctx, int64_t bytes);
+
 /* Tuning knobs (autotuner): tile edge in pixels (8 or 16), sub-frames per thread for the fast
  * solver (1..4, default 2), and the number of sub-frame group splits of the raster work units
  * (0 = automatic: about 64 units per SM). */

@@ -20,7 +20,7 @@ SOLVERS = {"plain": MBR_PLAIN, "fast": MBR_FAST}
 EXPORTS = ["mbr_create", "mbr_destroy", "mbr_render_blur", "mbr_render_blur_backward",
            "mbr_render_blur_backward_reuse", "mbr_render_blur_batch",
            "mbr_debug_winners", "mbr_count_candidates", "mbr_count_work", "mbr_set_tuning", "mbr_set_profiling", "mbr_get_stats",
-           "mbr_render_blur_noalloc", "mbr_autotune", "mbr_sdf_extract", "mbr_sdf_extract_backward", "mbr_measure_fp32_peak", "mbr_debug_wait_limit", "mbr_last_error"]
+           "mbr_render_blur_noalloc", "mbr_autotune", "mbr_set_state_budget", "mbr_sdf_extract", "mbr_sdf_extract_backward", "mbr_measure_fp32_peak", "mbr_debug_wait_limit", "mbr_last_error"]
 
 
 class MbrMesh(ctypes.Structure):
@@ -98,6 +98,8 @@ def load(build_if_missing=True):
     L.mbr_render_blur_batch.restype = c_int32
     L.mbr_autotune.argtypes = [c_void_p, c_int32, P(MbrItem), c_int32, P(c_int32), P(c_int32), P(c_float), c_void_p]
     L.mbr_autotune.restype = c_int32
+    L.mbr_set_state_budget.argtypes = [c_void_p, c_int64]
+    L.mbr_set_state_budget.restype = c_int32
     L.mbr_set_tuning.argtypes = [c_void_p, c_int32, c_int32, c_int32]
     L.mbr_set_tuning.restype = c_int32
     L.mbr_set_profiling.argtypes = [c_void_p, c_int32]

@@ -48,6 +48,7 @@ struct LastForward {
   mbr_motion motion;
   mbr_camera cam;
   int T = 0, H = 0, W = 0, solver = 0, tile = 0, spt = 0, splits = 0;
+  long long state_budget = 0;
 };
 
 }  // namespace
@@ -58,6 +59,7 @@ struct mbr_ctx {
   std::string err;
   // tuning
   int tile = 16, spt = 2, splits = 0;
+  long long state_budget = 1LL << 30;  // the forward keeps per-sample state for the adjoint up to this size
   // scratch
   DevBuf nacc, pos, nrm, recs, tables, partial, gslot, galb, gm, cnt64, status, order, bstate, bin_counts;
   DevBuf sdf_cnt, sdf_off, sdf_tmp;  // SDF extraction: edge flags + triangle counts, their scans
@@ -291,7 +293,13 @@ struct Prepared {
   int32_t* d_cost = nullptr;        // the forward's measured adjoint cost per unit
   int32_t* d_fcost = nullptr;       // the forward's measured own cost per unit
   int32_t* d_order_tmp = nullptr;   // scratch of the order kernels
+  bool stored = false;              // the forward kept the per-sample state (else the adjoint recomputes it)
 };
+
+// the forward keeps the adjoint's per-sample state (5 bytes per pixel and sub-frame) within the budget
+bool keeps_state(const mbr_ctx* c, int T, int H, int W) {
+  return (double)T * H * W * 5.0 <= (double)c->state_budget;
+}
 
 // order buffer of a render: order | adjoint order | adjoint cost | forward cost | scratch
 size_t order_buffer_ints(int n_units) { return (size_t)4 * n_units + unit_order_ints(n_units); }
@@ -657,11 +665,15 @@ int forward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, con
     P.out = (float4*)c->partial.p;
   } else {
     P.out = (float4*)image;
-    // per-sample state for a following adjoint: winner or log soft product (4 B) + status (1 B)
-    const size_t ns = (size_t)T * npix;
-    if ((rc = ensure(c, c->bstate, ns * 5 + 256, st))) return rc;
-    P.s_val = (float*)c->bstate.p;
-    P.s_stat = (uint8_t*)c->bstate.p + ns * 4;
+    // per-sample state for a following adjoint, within the budget: winner or log soft product
+    // (4 B) + status (1 B); above it the adjoint recomputes them
+    pp.stored = keeps_state(c, T, H, W);
+    if (pp.stored) {
+      const size_t ns = (size_t)T * npix;
+      if ((rc = ensure(c, c->bstate, ns * 5 + 256, st))) return rc;
+      P.s_val = (float*)c->bstate.p;
+      P.s_stat = (uint8_t*)c->bstate.p + ns * 4;
+    }
     P.unit_cost = pp.d_cost;  // and its cost per unit (cleared by the unit order), for the adjoint's order
     P.fwd_cost = pp.d_fcost;  // and its own, for the next forward's order
   }
@@ -689,6 +701,7 @@ int forward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, con
       L.cam = *cam;
       L.T = T; L.H = H; L.W = W; L.solver = solver;
       L.tile = c->tile; L.spt = c->spt; L.splits = c->splits;
+      L.state_budget = c->state_budget;
       L.valid = true;
     }
   }
@@ -722,7 +735,7 @@ bool matches_last_forward(const mbr_ctx* c, const mbr_mesh* mesh, const mbr_moti
          L.mesh.texture == mesh->texture && L.mesh.tex_h == mesh->tex_h && L.mesh.tex_w == mesh->tex_w &&
          same_motion(L.motion, *motion) &&
          same_camera(L.cam, *cam) && L.T == T && L.H == H && L.W == W && L.solver == solver && L.tile == c->tile &&
-         L.spt == c->spt && L.splits == c->splits;
+         L.spt == c->spt && L.splits == c->splits && L.state_budget == c->state_budget;
 }
 
 // the adjoint (a9): front half and forward raster state (the last forward's when reuse is allowed
@@ -760,10 +773,13 @@ int backward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, co
     CUDA_TRY(c, cudaMemsetAsync(mesh->dl_dtexture, 0, sizeof(float) * 3 * (size_t)mesh->tex_h * mesh->tex_w, st));
     P.g_tex = mesh->dl_dtexture;
   }
-  // the forward raster's per-sample state, and the units in the order of its measured cost
-  const size_t ns = (size_t)T * H * W;
-  P.s_val = (float*)c->bstate.p;
-  P.s_stat = (uint8_t*)c->bstate.p + ns * 4;
+  // the forward raster's per-sample state (if it kept it; else the adjoint recomputes it), and the
+  // units in the order of its measured cost
+  if (pp.stored) {
+    const size_t ns = (size_t)T * H * W;
+    P.s_val = (float*)c->bstate.p;
+    P.s_stat = (uint8_t*)c->bstate.p + ns * 4;
+  }
   launch_unit_order_measured(pp.d_cost, pp.n_units, pp.d_order_bwd, pp.d_order_tmp, nullptr, nullptr, st);
   P.order = pp.d_order_bwd;
   WorkQueue Q;
@@ -950,6 +966,14 @@ int mbr_debug_wait_limit(int32_t polls, int32_t stall, int32_t check_now) {
   g_wait_polls.store(polls);
   g_wait_stall.store(stall ? 1 : 0);
   g_wait_check.store(check_now ? 1 : 0);
+  return MBR_OK;
+}
+
+int mbr_set_state_budget(mbr_ctx* c, int64_t bytes) {
+  if (!c) return MBR_ERR_ARG;
+  if (bytes < 0) return fail(c, MBR_ERR_ARG, "the state budget must be >= 0 bytes");
+  c->state_budget = bytes;
+  c->last.valid = false;
   return MBR_OK;
 }
 
@@ -1196,7 +1220,7 @@ long long fbits(float x) {
 }
 
 std::vector<long long> batch_signature(mbr_ctx* c, int n, const mbr_item* items, int wb) {
-  std::vector<long long> s = {n, wb, c->tile, c->spt, c->splits};
+  std::vector<long long> s = {n, wb, c->tile, c->spt, c->splits, c->state_budget};
   for (int i = 0; i < n; ++i) {
     const mbr_item& it = items[i];
     const long long vals[] = {it.mesh.V, it.mesh.F, it.T, it.H, it.W, it.solver,
@@ -1261,8 +1285,10 @@ void batch_write_params(mbr_ctx* c, const mbr_item* items, BatchState& B) {
       P.g_slot = (float4*)(A + I.o_gslot);
       P.g_albedo = it.dl_dalbedo ? (float4*)(A + I.o_galb) : nullptr;
       if (it.mesh.texture) P.g_tex = it.mesh.dl_dtexture;
-      P.s_val = (float*)(A + I.o_bstate);
-      P.s_stat = (uint8_t*)(A + I.o_bstate) + (size_t)it.T * it.H * it.W * 4;
+      if (pp.stored) {
+        P.s_val = (float*)(A + I.o_bstate);
+        P.s_stat = (uint8_t*)(A + I.o_bstate) + (size_t)it.T * it.H * it.W * 4;
+      }
       P.unit_cost = pp.d_cost;
     }
     par[k] = P;
@@ -1315,7 +1341,8 @@ int batch_plan(mbr_ctx* c, int n, const mbr_item* items, int wb, cudaStream_t st
       I.o_gslot = carve(at, sizeof(float4) * 2 * (size_t)V * pp.n_slots);
       I.o_galb = carve(at, sizeof(float4) * V);
       I.o_gm = carve(at, sizeof(float) * 3 * V);
-      I.o_bstate = carve(at, (size_t)it.T * it.H * it.W * 5);
+      pp.stored = keeps_state(c, it.T, it.H, it.W);
+      if (pp.stored) I.o_bstate = carve(at, (size_t)it.T * it.H * it.W * 5);
     }
     I.stage_tab = carve(stage_at, I.tab_bytes);
   }

@@ -521,23 +521,61 @@ __device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile
     gq.load(grp);
     const int n = gq.n;
     const TriRec* recs_set = P.recs + (size_t)gq.rec_set * P.F;
-    // the forward's state of the group's samples at this pixel
     int win[SPT];
     uint32_t my_s = 0u;
+    int sb, se;
+    P.soft.range((size_t)g * B.n_tiles + tile, sb, se);
+    if (P.s_stat) {
+      // the forward's state of the group's samples at this pixel
 #pragma unroll
-    for (int i = 0; i < SPT; ++i) {
-      win[i] = -1;
-      if (i < n && B.in_img) {
-        const size_t o = (size_t)(gq.k0 + i) * plane + pix;
-        const uint8_t st = __ldg(P.s_stat + o);
-        if (st == kStatCovered) {
-          win[i] = __float_as_int(__ldg(P.s_val + o));
-        } else if (alpha) {
-          my_s |= 1u << i;
-          ws.nzero[i][lane] = st;
-          ws.logp[i][lane] = __ldg(P.s_val + o);
+      for (int i = 0; i < SPT; ++i) {
+        win[i] = -1;
+        if (i < n && B.in_img) {
+          const size_t o = (size_t)(gq.k0 + i) * plane + pix;
+          const uint8_t st = __ldg(P.s_stat + o);
+          if (st == kStatCovered) {
+            win[i] = __float_as_int(__ldg(P.s_val + o));
+          } else if (alpha) {
+            my_s |= 1u << i;
+            ws.nzero[i][lane] = st;
+            ws.logp[i][lane] = __ldg(P.s_val + o);
+          }
         }
       }
+    } else {
+      // state-free adjoint: recompute the group's winners and the soft products of its uncovered
+      // samples that carry dL/dalpha, exactly as the forward raster does (same passes, same order)
+      int cb, ce;
+      P.core.range((size_t)g * B.n_tiles + tile, cb, ce);
+      const uint32_t img_mask = __ballot_sync(kFullMask, B.in_img);
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) ws.win[i][lane] = 0ull;
+      __syncwarp();
+      core_raster<SPT, MOVING>(recs_set, P.core.faces, cb, ce, gq.tau, n, B.tb, B.bp, img_mask, ws);
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) {
+        win[i] = -1;
+        if (i < n && B.in_img) {
+          const unsigned long long w = ws.win[i][lane];
+          if (w) win[i] = (int)(~(uint32_t)w);
+          else if (alpha) my_s |= 1u << i;
+        }
+        ws.logp[i][lane] = 0.f;
+        ws.nzero[i][lane] = 0;
+      }
+      const uint32_t any_u = __reduce_or_sync(kFullMask, my_s);
+      if (se > sb && any_u) {
+        uint32_t allowed[SPT];
+#pragma unroll
+        for (int i = 0; i < SPT; ++i) allowed[i] = __ballot_sync(kFullMask, (my_s >> i) & 1u);
+        ws.pixs[lane] = my_s;
+        __syncwarp();
+        FwdSoftPairs<SPT, MOVING, false> sp{recs_set, grp, B.bp, &ws, gq.xbits, P.r + kCoreMargin, P.r2,
+                                            P.inv_delta, EXT ? P.prob : 0, 0u, 0u, 0u};
+        for_pairs<SPT, MOVING>(recs_set, P.soft.faces, sb, se, grp, n, B.tb, B.bp, P.r + kCoreMargin, allowed, any_u,
+                               ws, sp);
+      }
+      __syncwarp();
     }
 
     // ---- covered samples: shading adjoint and barycentric adjoint of the winner
@@ -557,8 +595,6 @@ __device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile
 
     // ---- uncovered samples: soft-factor gradients (pass 3)
     const uint32_t any_s = __reduce_or_sync(kFullMask, my_s);
-    int sb, se;
-    P.soft.range((size_t)g * B.n_tiles + tile, sb, se);
     if (se > sb && any_s) {
       uint32_t allowed[SPT];
 #pragma unroll

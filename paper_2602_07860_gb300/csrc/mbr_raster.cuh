@@ -595,6 +595,45 @@ __device__ __forceinline__ bool soft_pair_term(const float4 (&r)[kRecF4], const 
   return sg.d <= r2;
 }
 
+// pass 2 of the forward: log soft factors log(1 - A_j), A_j = exp(-d_j / delta) (Eqs.
+// probability-function .. back), summed per (sample, pixel) in ws.logp; vanishing factors are
+// counted in ws.nzero instead (the product is then 0).
+template <int SPT, bool MOVING, bool COUNT>
+struct FwdSoftPairs {
+  const TriRec* recs_set;
+  const Group* grp;
+  BlockPix bp;
+  WarpScratch<SPT>* ws;
+  uint32_t xbits;
+  float m, r2, inv_delta;
+  int prob;
+  uint32_t n_terms, n_eval, n_batches;
+  __device__ __forceinline__ void pair(bool ok, int face, int p, uint32_t smp) {
+    if (!ok) return;
+    const float u = ws->pu[p], v = ws->pv[p];
+    float4 r[kRecF4];
+    load_record<MOVING>(recs_set + face, r, false, true);
+    const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
+    while (smp) {
+      const int i = __ffs(smp) - 1;
+      smp &= smp - 1u;
+      const float tau = MOVING ? __ldg(&grp->tau[i]) : 0.f;
+      if (COUNT) ++n_eval;
+      EdgeVals e;
+      SoftGeom sg;
+      if (!soft_pair_term<MOVING>(r, ps, u, v, tau, (xbits >> i) & 1u, m, r2, e, sg)) continue;
+      float A, dA;
+      const float f = soft_factor(sg.d, inv_delta, prob, A, dA);
+      if (f > kTinyFactor) atomicAdd(&ws->logp[i][p], __logf(f));
+      else atomicAdd(&ws->nzero[i][p], 1);
+      if (COUNT) ++n_terms;
+    }
+  }
+  __device__ __forceinline__ void batch_end(int) {
+    if ((threadIdx.x & 31) == 0) ++n_batches;  // lane 0: the adjoint's cost estimate
+  }
+};
+
 // Persistent scheduling.  A unit is one split of the sample groups (a contiguous range of
 // groups) over a 256-pixel patch of one render (one 16 x 16 tile, or four 8 x 8 tiles); it has
 // 8 warp blocks of 8 x 4 pixels.  The CTAs of a grid of (SM count x resident CTAs) take units

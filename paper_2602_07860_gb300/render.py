@@ -199,6 +199,11 @@ class Context:
                                                  _stream()))
         return fl.value / (ms.value * 1e-3) / 1e12, fl.value, ms.value
 
+    def set_state_budget(self, nbytes):
+        """Per-sample forward state kept for the adjoint up to ``nbytes`` (0: the adjoint always
+        recomputes it; mbr_set_state_budget)."""
+        self._raise(self.L.mbr_set_state_budget(self.h, int(nbytes)))
+
     def set_tuning(self, tile=16, spt=2, splits=0):
         self._raise(self.L.mbr_set_tuning(self.h, int(tile), int(spt), int(splits)))
 

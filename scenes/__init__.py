@@ -433,6 +433,23 @@ def config5(seed=MASTER_SEED + 5, T=256, H=1024, W=1024):
                  camera(look_at(orbit_eye(4.0, 0, 20.0))), T, H, W)
 
 
+def config_sdf_rotation(seed=MASTER_SEED + 6, T=24, H=128, W=128, n_views=5):
+    """Rotational recovery through an SDF (the paper's rotation task): a target subdiv-4 sphere with
+    SH displacement (degree <= 4, N(0, 0.08)) spinning one turn about +y per exposure (12
+    segments), seen from ``n_views`` cameras at elevations from -40 to 40 degrees (azimuths 30
+    degrees apart), distance 4; grey albedo 0.7.  Returns the scenes (one per view) -- they share
+    the target mesh."""
+    rng = np.random.default_rng(seed)
+    v, f = sh_sphere(4, 4, 0.08, rng)
+    alb = np.full((len(v), 3), 0.7)
+    out = []
+    for i in range(n_views):
+        e = -40.0 + 80.0 * i / max(1, n_views - 1)
+        cam = camera(look_at(orbit_eye(4.0, 30.0 * i, e)))
+        out.append(scene(v, f, alb, rotate((0.0, 1.0, 0.0), 2 * math.pi), cam, T, H, W))
+    return out
+
+
 def small_scene(kind="rotate", subdiv=2, T=8, H=40, W=72, seed=MASTER_SEED + 100, lmax=4, sigma=0.05,
                 time_rule="paper", omega=2 * math.pi, segments=0, d=(1.2, 0.3, 0.0), eye=(0.0, 0.0),
                 fov=40.0):

@@ -21,6 +21,16 @@ def ctx():
     return mbr.Context()
 
 
+@pytest.fixture(scope="module")
+def ctx_free():
+    """A context whose forward keeps no per-sample state: its adjoint recomputes coverage and the
+    soft products (the state-free adjoint)."""
+    import paper_2602_07860_gb300 as mbr
+    c = mbr.Context()
+    c.set_state_budget(0)
+    return c
+
+
 def _grad_check(ctx, sc, solver, seed=0, rel=1e-3):
     mode = ORACLE_MODE[solver]
     r = oracle.render(sc, mode, ambig=True, soft32=True)
@@ -76,6 +86,42 @@ def test_adjoint_matches_oracle(ctx, name, solver):
 
 
 @pytest.mark.parametrize("solver", ["plain", "fast"])
+@pytest.mark.parametrize("name", ["rotate", "translate_depth", "c1", "degenerate_faces", "strip_1x37", "parabolic",
+                                  "rotate_perspective_attrs"])
+def test_state_free_adjoint_matches_oracle(ctx_free, name, solver):
+    _grad_check(ctx_free, GRAD_SCENES[name](), solver)
+
+
+@pytest.mark.parametrize("solver", ["plain", "fast"])
+def test_state_free_adjoint_at_T256(ctx_free, solver):
+    """T = 256 sub-frames (the large workload's count) with no stored sample state."""
+    _grad_check(ctx_free, scenes.small_scene("rotate", subdiv=2, T=256, H=32, W=40, omega=4 * np.pi), solver)
+
+
+@pytest.mark.parametrize("solver", ["plain", "fast"])
+def test_state_free_equals_stored_state(ctx, ctx_free, solver):
+    """The two adjoint modes compute the same gradients (up to the order of floating-point sums),
+    through the autograd path and through the recomputing call; a budget below one render's
+    state selects the state-free mode by itself."""
+    import paper_2602_07860_gb300 as mbr
+    sc = scenes.small_scene("rotate", subdiv=3, T=16, H=56, W=64, seed=4)
+    v, f, a, mo, ca = gpu_inputs(sc)
+    G = torch.randn((sc["H"], sc["W"], 4), device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+    T, H, W = sc["T"], sc["H"], sc["W"]
+    ref_v, ref_a = ctx.render_blur_backward(v, f, a, mo, ca, T, H, W, G, solver)
+    small = mbr.Context()
+    small.set_state_budget(T * H * W * 5 - 1)
+    for c in (ctx_free, small):
+        c.render_blur(v, f, a, mo, ca, T, H, W, solver)
+        gv, ga = c.render_blur_backward(v, f, a, mo, ca, T, H, W, G, solver, reuse_forward=True)
+        torch.cuda.synchronize()
+        assert float((gv - ref_v).abs().max()) <= 1e-4 * float(ref_v.abs().max())
+        assert float((ga - ref_a).abs().max()) <= 1e-4 * float(ref_a.abs().max())
+    with pytest.raises(Exception):
+        small.set_state_budget(-1)
+
+
+@pytest.mark.parametrize("solver", ["plain", "fast"])
 def test_adjoint_is_zero_without_visible_geometry_or_loss(ctx, solver):
     """No faces, a mesh far outside the view, or a zero dL/dimage: both gradients are exactly zero
     (and the buffers the call overwrites hold no stale values)."""
@@ -107,8 +153,9 @@ def test_autograd_function_uses_the_adjoint(ctx, solver):
     assert torch.allclose(aa.grad, ga, rtol=1e-4, atol=1e-6)
 
 
+@pytest.mark.parametrize("state_free", [False, True])
 @pytest.mark.parametrize("x0,y0", [(116, 100), (56, 88), (56, 152)])
-def test_full_size_rotation_gradient_window(ctx, x0, y0):
+def test_full_size_rotation_gradient_window(ctx, ctx_free, x0, y0, state_free):
     """Full-size rotation workload (the benchmark's) with an L2 image loss against a target (the
     same object scaled by 1.02) on a 24x24 window: GPU adjoint vs the oracle adjoint.
 
@@ -116,6 +163,7 @@ def test_full_size_rotation_gradient_window(ctx, x0, y0):
     The floor is the FP32 limit of the soft term: exp(-d / delta) with delta = 1e-4 turns the
     ~6e-8 absolute error of single-precision screen positions into ~(2 r / delta) 6e-8 ~ 6e-5
     relative error per term, which shows where a vertex's contributions nearly cancel."""
+    ctx = ctx_free if state_free else ctx
     sc = scenes.config2()
     w, h = 24, 24
     target = dict(sc, verts=sc["verts"] * 1.02)
