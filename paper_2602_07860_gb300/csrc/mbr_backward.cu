@@ -190,13 +190,38 @@ struct BwdSoftGradPairs {
       const int X = (xbits >> i) & 1u;
       EdgeVals e;
       SoftGeom sg;
-      if (!soft_pair_term<MOVING>(r, ps, u, v, tau, X, m, r2, e, sg)) continue;
+      if (MOVING) {
+        // the term exactly as the forward's soft pass evaluates it (soft_affine), then the
+        // quantities the gradient needs
+        if (!in_box_at(r, tau, m, u, v)) continue;
+        e.D = fmaf(fmaf(r[kR_A].w, tau, r[kR_A].z), tau, r[kR_E2].z);
+        if (!(fabsf(e.D) > kDetMin)) continue;
+        const SoftAffine sa = soft_affine(r[kR_O], r[kR_E2], r[kR_D], r[kR_G], r[kR_A], X ? r[kR_IL1] : r[kR_IL0], tau,
+                                          X, e.D);
+        const SoftEval ev = soft_affine_eval(sa.k, u, v);
+        if (!(ev.d <= r2)) continue;
+        sg.d = ev.d;
+        sg.c = ev.c;
+        sg.w1 = fmaf(ev.qx, sa.w1u, fmaf(ev.qy, sa.w1v, sa.w1c));
+        sg.w2 = fmaf(ev.qx, sa.w2u, fmaf(ev.qy, sa.w2v, sa.w2c));
+        sg.ppx = ev.ppx;
+        sg.ppy = ev.ppy;
+        sg.rx = ev.rx;
+        sg.ry = ev.ry;
+        e.N1 = sg.w1 * e.D;
+        e.N2 = sg.w2 * e.D;
+        e.N0 = e.D - e.N1 - e.N2;
+      } else if (!soft_pair_term<MOVING>(r, ps, u, v, tau, X, m, r2, e, sg)) {
+        continue;
+      }
       float A, dA;
       const float f = soft_factor(sg.d, inv_delta, prob, A, dA);
       const float S = ws->logp[i][p];
       const int nz = ws->nzero[i][p];
+      // the product of the other factors, each <= 1 (the bound keeps a factor that rounds to 0
+      // from turning it into infinity)
       float excl;
-      if (nz == 0) excl = __expf(S - __logf(f));
+      if (nz == 0) excl = fminf(__expf(S - __logf(f)), 1.f);
       else excl = (nz == 1 && f <= kTinyFactor) ? __expf(S) : 0.f;
       // alpha = 1 - prod(1 - A_l): d alpha / d d_j = excl dA_j/dd
       const float gd = ga * excl * dA;
@@ -500,6 +525,43 @@ __device__ __forceinline__ BwdBlock bwd_block_setup(const RasterParams& P, int t
   return B;
 }
 
+// The state-free adjoint's per-group state (the forward kept none): the group's winners and the
+// soft log products of its uncovered samples that carry dL/dalpha, recomputed by the forward's own
+// passes.  Out of line, so that the stored-state path carries none of its registers.  Writes the
+// winners to ws.wface and the soft state to ws.logp / ws.nzero; returns this pixel's uncovered
+// samples that carry dL/dalpha.
+template <int SPT, bool MOVING, bool EXT>
+__device__ __noinline__ uint32_t recompute_group_state(const RasterParams& P, const TriRec* recs_set,
+                                                       const GroupRegs& gq, int g, int tile, const BwdBlock& B,
+                                                       bool alpha, int sb, int se, WarpScratch<SPT>& ws) {
+  const int lane = threadIdx.x & 31;
+  const int n = gq.n;
+  int cb, ce;
+  P.core.range((size_t)g * B.n_tiles + tile, cb, ce);
+  float bkey[SPT];
+  int win[SPT];
+  core_raster<SPT, MOVING>(recs_set, P.core.faces, cb, ce, gq.tau, n, B.tb, B.u, B.v, B.in_img, ws, bkey, win);
+  uint32_t my_s = 0u;
+#pragma unroll
+  for (int i = 0; i < SPT; ++i) {
+    if (!(i < n && B.in_img)) win[i] = -1;
+    else if (win[i] < 0 && alpha) my_s |= 1u << i;
+    ws.wface[i][lane] = win[i];
+  }
+  float lp[SPT];
+  int nz[SPT];
+  uint32_t t0 = 0, t1 = 0;
+  soft_raster<SPT, MOVING>(recs_set, P.soft.faces, sb, se, gq.tau, gq.xbits, n, B.tb, B.u, B.v, my_s,
+                           P.r + kCoreMargin, P.r2, P.inv_delta, EXT ? P.prob : 0, ws, lp, nz, t0, t1);
+#pragma unroll
+  for (int i = 0; i < SPT; ++i) {
+    ws.logp[i][lane] = lp[i];
+    ws.nzero[i][lane] = nz[i];
+  }
+  __syncwarp();
+  return my_s;
+}
+
 // the adjoint of one 8 x 4 block over its split of the sample groups (EXT: see covered_adjoint)
 template <int TW, int TH, int SPT, bool MOVING, bool EXT>
 __device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile, int split, int wb,
@@ -545,36 +607,9 @@ __device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile
     } else {
       // state-free adjoint: recompute the group's winners and the soft products of its uncovered
       // samples that carry dL/dalpha, exactly as the forward raster does (same passes, same order)
-      int cb, ce;
-      P.core.range((size_t)g * B.n_tiles + tile, cb, ce);
-      const uint32_t img_mask = __ballot_sync(kFullMask, B.in_img);
+      my_s = recompute_group_state<SPT, MOVING, EXT>(P, recs_set, gq, g, tile, B, alpha, sb, se, ws);
 #pragma unroll
-      for (int i = 0; i < SPT; ++i) ws.win[i][lane] = 0ull;
-      __syncwarp();
-      core_raster<SPT, MOVING>(recs_set, P.core.faces, cb, ce, gq.tau, n, B.tb, B.bp, img_mask, ws);
-#pragma unroll
-      for (int i = 0; i < SPT; ++i) {
-        win[i] = -1;
-        if (i < n && B.in_img) {
-          const unsigned long long w = ws.win[i][lane];
-          if (w) win[i] = (int)(~(uint32_t)w);
-          else if (alpha) my_s |= 1u << i;
-        }
-        ws.logp[i][lane] = 0.f;
-        ws.nzero[i][lane] = 0;
-      }
-      const uint32_t any_u = __reduce_or_sync(kFullMask, my_s);
-      if (se > sb && any_u) {
-        uint32_t allowed[SPT];
-#pragma unroll
-        for (int i = 0; i < SPT; ++i) allowed[i] = __ballot_sync(kFullMask, (my_s >> i) & 1u);
-        ws.pixs[lane] = my_s;
-        __syncwarp();
-        FwdSoftPairs<SPT, MOVING, false> sp{recs_set, grp, B.bp, &ws, gq.xbits, P.r + kCoreMargin, P.r2,
-                                            P.inv_delta, EXT ? P.prob : 0, 0u, 0u, 0u};
-        for_pairs<SPT, MOVING>(recs_set, P.soft.faces, sb, se, grp, n, B.tb, B.bp, P.r + kCoreMargin, allowed, any_u,
-                               ws, sp);
-      }
+      for (int i = 0; i < SPT; ++i) win[i] = ws.wface[i][lane];
       __syncwarp();
     }
 

@@ -377,7 +377,6 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
   const TileBox tb = PixelMap<TW, TH>::warp_box(tx, ty, wb, P.W, P.H);
   const int g_begin = (int)((long long)P.G * split / P.n_split);
   const int g_end = (int)((long long)P.G * (split + 1) / P.n_split);
-  const uint32_t img_mask = __ballot_sync(kFullMask, in_img);
   float acc_r = 0.f, acc_g = 0.f, acc_b = 0.f, acc_a = 0.f;
   uint32_t n_soft = 0, n_cov = 0, n_seval = 0, n_sbatch = 0, n_ctest = 0, n_cbatch = 0;
   int adj_cost = 0;  // lane 0: soft pair batches + samples with a covered pixel (the adjoint's work)
@@ -396,59 +395,30 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
     P.soft.range(bi, sb, se);
 
     // ---- pass 1: winners
-#pragma unroll
-    for (int i = 0; i < SPT; ++i) ws.win[i][lane] = 0ull;
-    __syncwarp();
-    const uint32_t core_tests = core_raster<SPT, MOVING>(recs_set, P.core.faces, cb, ce, gr.tau, n, tb, bp, img_mask, ws);
+    float bkey[SPT];
     int bestf[SPT];
+    const uint32_t core_tests =
+        core_raster<SPT, MOVING>(recs_set, P.core.faces, cb, ce, gr.tau, n, tb, u, v, in_img, ws, bkey, bestf);
     uint32_t uncov = 0;
 #pragma unroll
-    for (int i = 0; i < SPT; ++i) {
-      bestf[i] = -1;
-      if (i < n) {
-        const unsigned long long w = ws.win[i][lane];
-        if (w) bestf[i] = (int)(~(uint32_t)w);
-        else uncov |= 1u << i;
-      }
-    }
+    for (int i = 0; i < SPT; ++i)
+      if (i < n && bestf[i] < 0) uncov |= 1u << i;
 
     // ---- pass 2: soft coverage of the uncovered samples
     float logp[SPT];
     int nzero[SPT];
-#pragma unroll
-    for (int i = 0; i < SPT; ++i) {
-      logp[i] = 0.f;
-      nzero[i] = 0;
-    }
     const uint32_t my_s = in_img ? uncov : 0u;
-    const uint32_t any_s = __reduce_or_sync(kFullMask, my_s);
-    FwdSoftPairs<SPT, MOVING, COUNT> soft{recs_set, grp, bp, &ws, gr.xbits, P.r + kCoreMargin, P.r2, P.inv_delta,
-                                          EXT ? P.prob : 0, 0u, 0u, 0u};
-    if (se > sb && any_s) {
-      uint32_t allowed[SPT];
-#pragma unroll
-      for (int i = 0; i < SPT; ++i) {
-        allowed[i] = __ballot_sync(kFullMask, (my_s >> i) & 1u);
-        ws.logp[i][lane] = 0.f;
-        ws.nzero[i][lane] = 0;
-      }
-      ws.pixs[lane] = my_s;
-      __syncwarp();
-      for_pairs<SPT, MOVING>(recs_set, P.soft.faces, sb, se, grp, n, tb, bp, P.r + kCoreMargin, allowed, any_s, ws,
-                             soft);
-#pragma unroll
-      for (int i = 0; i < SPT; ++i) {
-        logp[i] = ws.logp[i][lane];
-        nzero[i] = ws.nzero[i][lane];
-      }
-    }
-    adj_cost += (int)soft.n_batches + __popc(__reduce_or_sync(kFullMask, in_img ? (all_s & ~uncov) : 0u));
+    uint32_t s_terms = 0, s_touch = 0;
+    const uint32_t s_eval = soft_raster<SPT, MOVING>(recs_set, P.soft.faces, sb, se, gr.tau, gr.xbits, n, tb, u, v, my_s,
+                                                     P.r + kCoreMargin, P.r2, P.inv_delta, EXT ? P.prob : 0, ws, logp,
+                                                     nzero, s_terms, s_touch);
+    adj_cost += (int)s_touch + __popc(__reduce_or_sync(kFullMask, in_img ? (all_s & ~uncov) : 0u));
     if (COUNT) {
       n_ctest += core_tests;
       n_cbatch += (uint32_t)(ce - cb + 31) / 32 * ((threadIdx.x & 31) == 0);
-      n_seval += soft.n_eval;
-      n_sbatch += soft.n_batches;
-      n_soft += soft.n_terms;
+      n_seval += s_eval;
+      n_sbatch += s_touch;
+      n_soft += s_terms;
       if (in_img) n_cov += (uint32_t)n - (uint32_t)__popc(uncov);
     }
 

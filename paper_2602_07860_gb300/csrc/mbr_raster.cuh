@@ -378,8 +378,8 @@ constexpr uint32_t kFullMask = 0xffffffffu;
 // Per-warp shared scratch of the passes.
 template <int SPT>
 struct WarpScratch {
-  unsigned long long win[SPT][32];  // z-test winner of (sample, pixel): key bits << 32 | ~face, 0 = none
   float logp[SPT][32];              // sum of log(1 - A_j) over the soft factors that do not vanish
+  int wface[SPT][32];               // state-free adjoint: recomputed winner face (or -1)
   int nzero[SPT][32];               // vanishing soft factors
   uint32_t pixs[32];                // samples each pixel takes part in, this pass
   float pu[32], pv[32];             // NDC centre of each pixel (written by its own lane)
@@ -388,6 +388,7 @@ struct WarpScratch {
   uint32_t pmask[32];               //   block pixels each may touch,
   uint32_t smask[32];               //   samples each may touch,
   int prefix[33];                   //   pair offsets
+  float4 coef[32][6];               // per candidate of a chunk: its coefficients at one sample time
 };
 
 // Pixel geometry of a warp block.
@@ -512,74 +513,110 @@ __device__ __forceinline__ void for_pairs(const TriRec* recs_set, const int32_t*
 }
 
 // pass 1: z-test winners (Sec. 3.1: coverage by the edge functions of Eq. time-dependent2, then
-// the perspective-correct depth; ties to the smaller face id) into ws.win.  Lanes over candidates:
-// lane j takes candidate j of the bin list and, for each sample of the group whose box at tau
-// meets the warp's block, forms the edge functions at that tau once -- for a fixed tau the
-// numerators N1, N2 and the denominator D of Eq. time-dependent2 are affine in the pixel position
-// (N1 = cross(p - o, E2(tau)) + c1 tau + a11 tau^2, N2 = cross(E1(tau), p - o) + c2 tau + a12 tau^2,
-// D = D0 + D1 tau + D2 tau^2, with E1, E2 the local edges at tau) -- together with the reciprocal
-// vertex depths and 1 / D, and then sweeps the block pixels inside that box: a coverage test is a
-// few multiply-adds and a covered pixel's depth key three more.  Returns the coverage tests.
+// the perspective-correct depth; ties to the smaller face id).  Lanes over pixels: the bin list is
+// read 32 candidates at a time, lane j holding candidate j's record.  For each sample time tau of
+// the group the candidates whose box at tau meets the warp's block are picked by ballot, and each
+// of them forms its edge functions at tau once -- for a fixed tau the numerators N1, N2 and the
+// denominator D of Eq. time-dependent2 are affine in the pixel position (N1 = cross(p - o, E2(tau))
+// + c1 tau + a11 tau^2, N2 = cross(E1(tau), p - o) + c2 tau + a12 tau^2, D = D0 + D1 tau + D2 tau^2,
+// with E1, E2 the local edges at tau) -- together with the reciprocal vertex depths and 1 / D, into
+// the warp's shared table.  Every lane then tests its own pixel against those candidates in turn
+// (broadcast reads) and keeps the nearest covering face per sample in registers: a test is a few
+// multiply-adds, with no atomics.  bkey / bface: inverse-depth key (0: none) and face per sample.
+// Returns the coverage tests of this lane's pixel.
 template <int SPT, bool MOVING>
 __device__ __forceinline__ uint32_t core_raster(const TriRec* recs_set, const int32_t* list, int beg, int end,
-                                                const float* tau_g, int n, const TileBox& tb, const BlockPix& bp,
-                                                uint32_t img_mask, WarpScratch<SPT>& ws) {
+                                                const float* tau_g, int n, const TileBox& tb, float u, float v,
+                                                bool in_img, WarpScratch<SPT>& ws, float (&bkey)[SPT],
+                                                int (&bface)[SPT]) {
   const int lane = threadIdx.x & 31;
   uint32_t n_tests = 0;
+#pragma unroll
+  for (int i = 0; i < SPT; ++i) {
+    bkey[i] = 0.f;
+    bface[i] = -1;
+  }
   if (tb.empty) return 0;
   for (int c0 = beg; c0 < end; c0 += 32) {
     const int j = c0 + lane;
-    if (j >= end) continue;
-    const int f = __ldg(list + j);
+    const bool valid = j < end;
+    const int f = valid ? __ldg(list + j) : 0;
     const TriRec* rec = recs_set + f;
-    const float4 o = __ldg(&rec->f4[kR_O]), e2 = __ldg(&rec->f4[kR_E2]), zz = __ldg(&rec->f4[kR_Z]);
-    const float4 b = __ldg(&rec->f4[kR_BB]);
-    float4 db = make_float4(0.f, 0.f, 0.f, 0.f), d = db, g = db, a = db, dz = db;
-    if (MOVING) {
-      db = __ldg(&rec->f4[kR_DBB]);
-      d = __ldg(&rec->f4[kR_D]);
-      g = __ldg(&rec->f4[kR_G]);
-      a = __ldg(&rec->f4[kR_A]);
-      dz = __ldg(&rec->f4[kR_DZ]);
-    }
-    const uint32_t key_lo = ~(uint32_t)f;
-    for (int i = 0; i < (MOVING ? n : 1); ++i) {
-      const float tau = MOVING ? __ldg(tau_g + i) : 0.f;
-      float4 bx;
-      bx.x = fmaf(tau, db.x, b.x) - kCoreMargin;
-      bx.y = fmaf(tau, db.y, b.y) + kCoreMargin;
-      bx.z = fmaf(tau, db.z, b.z) - kCoreMargin;
-      bx.w = fmaf(tau, db.w, b.w) + kCoreMargin;
-      if (bx.x > tb.u_hi || bx.y < tb.u_lo || bx.z > tb.v_hi || bx.w < tb.v_lo) continue;
-      uint32_t pm = box_pixel_mask(bx, bp) & img_mask;
-      if (!pm) continue;
-      // edge functions at tau, affine in (u, v) about the record origin
-      const float E1x = fmaf(tau, d.x, o.z), E1y = fmaf(tau, d.y, o.w);
-      const float E2x = fmaf(tau, d.z, e2.x), E2y = fmaf(tau, d.w, e2.y);
-      const float k1 = tau * fmaf(a.x, tau, g.z), k2 = tau * fmaf(a.y, tau, g.w);
-      const float D = fmaf(fmaf(a.w, tau, a.z), tau, e2.z);
-      if (!(fabsf(D) > kDetMin)) continue;
-      const float iD = __fdividef(1.0f, D);
-      const float iz0 = __fdividef(1.0f, fmaf(tau, dz.x, zz.x)), iz1 = __fdividef(1.0f, fmaf(tau, dz.y, zz.y)),
-                  iz2 = __fdividef(1.0f, fmaf(tau, dz.z, zz.z));
-      n_tests += __popc(pm);
-      while (pm) {
-        const int p = __ffs(pm) - 1;
-        pm &= pm - 1u;
-        const float qx = ws.pu[p] - o.x, qy = ws.pv[p] - o.y;
-        const float N1 = fmaf(qx, E2y, fmaf(-qy, E2x, k1));
-        const float N2 = fmaf(E1x, qy, fmaf(-E1y, qx, k2));
-        const float N0 = D - N1 - N2;
-        const bool pos = N0 >= 0.f && N1 >= 0.f && N2 >= 0.f;
-        const bool neg = N0 <= 0.f && N1 <= 0.f && N2 <= 0.f;
-        if (pos || neg) {
-          const float key = fmaxf(fmaf(N0, iz0, fmaf(N1, iz1, N2 * iz2)) * iD, 1e-30f);  // > 0 when covered
-          atomicMax(&ws.win[i][p], ((unsigned long long)__float_as_uint(key) << 32) | (unsigned long long)key_lo);
-        }
+    // the box and the denominator's fields stay in registers; the rest is read when needed
+    float4 e2 = make_float4(0.f, 0.f, 0.f, 0.f), b = e2, db = e2, a = e2;
+    if (valid) {
+      e2 = __ldg(&rec->f4[kR_E2]);
+      b = __ldg(&rec->f4[kR_BB]);
+      if (MOVING) {
+        db = __ldg(&rec->f4[kR_DBB]);
+        a = __ldg(&rec->f4[kR_A]);
       }
     }
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) {
+      if (i >= (MOVING ? n : 1)) break;
+      const float tau = MOVING ? __ldg(tau_g + i) : 0.f;
+      // the candidate's box at tau against the block's pixel rectangle
+      const bool hit = valid && fmaf(tau, db.x, b.x) - kCoreMargin <= tb.u_hi &&
+                       fmaf(tau, db.y, b.y) + kCoreMargin >= tb.u_lo && fmaf(tau, db.z, b.z) - kCoreMargin <= tb.v_hi &&
+                       fmaf(tau, db.w, b.w) + kCoreMargin >= tb.v_lo;
+      const float D = fmaf(fmaf(a.w, tau, a.z), tau, e2.z);
+      uint32_t M = __ballot_sync(kFullMask, hit && fabsf(D) > kDetMin);
+      if (!M) continue;
+      if ((M >> lane) & 1u) {
+        const float4 o = __ldg(&rec->f4[kR_O]), zz = __ldg(&rec->f4[kR_Z]);
+        float4 d = make_float4(0.f, 0.f, 0.f, 0.f), g = d, dz = d;
+        if (MOVING) {
+          d = __ldg(&rec->f4[kR_D]);
+          g = __ldg(&rec->f4[kR_G]);
+          dz = __ldg(&rec->f4[kR_DZ]);
+        }
+        const float E1x = fmaf(tau, d.x, o.z), E1y = fmaf(tau, d.y, o.w);
+        const float E2x = fmaf(tau, d.z, e2.x), E2y = fmaf(tau, d.w, e2.y);
+        ws.coef[lane][0] = make_float4(o.x, o.y, E2y, -E2x);
+        ws.coef[lane][1] = make_float4(-E1y, E1x, tau * fmaf(a.x, tau, g.z), tau * fmaf(a.y, tau, g.w));
+        ws.coef[lane][2] = make_float4(D, __fdividef(1.0f, D), __int_as_float(f), 0.f);
+        ws.coef[lane][3] = make_float4(__fdividef(1.0f, fmaf(tau, dz.x, zz.x)), __fdividef(1.0f, fmaf(tau, dz.y, zz.y)),
+                                       __fdividef(1.0f, fmaf(tau, dz.z, zz.z)), 0.f);
+      }
+      __syncwarp();
+      if (in_img) n_tests += __popc(M);
+      while (M) {
+        // two candidates per step (independent chains; the second repeats the first when one is left)
+        const int ca = __ffs(M) - 1;
+        M &= M - 1u;
+        const int cb = M ? __ffs(M) - 1 : ca;
+        if (M) M &= M - 1u;
+        const float4 a0 = ws.coef[ca][0], a1 = ws.coef[ca][1], a2 = ws.coef[ca][2];
+        const float4 b0 = ws.coef[cb][0], b1 = ws.coef[cb][1], b2 = ws.coef[cb][2];
+        const float qxa = u - a0.x, qya = v - a0.y, qxb = u - b0.x, qyb = v - b0.y;
+        const float N1a = fmaf(qxa, a0.z, fmaf(qya, a0.w, a1.z)), N1b = fmaf(qxb, b0.z, fmaf(qyb, b0.w, b1.z));
+        const float N2a = fmaf(qxa, a1.x, fmaf(qya, a1.y, a1.w)), N2b = fmaf(qxb, b1.x, fmaf(qyb, b1.y, b1.w));
+        const float N0a = a2.x - N1a - N2a, N0b = b2.x - N1b - N2b;
+        const bool cova = (N0a >= 0.f && N1a >= 0.f && N2a >= 0.f) || (N0a <= 0.f && N1a <= 0.f && N2a <= 0.f);
+        const bool covb = (N0b >= 0.f && N1b >= 0.f && N2b >= 0.f) || (N0b <= 0.f && N1b <= 0.f && N2b <= 0.f);
+        if (cova) {
+          const float4 a3 = ws.coef[ca][3];
+          const float key = fmaxf(fmaf(N0a, a3.x, fmaf(N1a, a3.y, N2a * a3.z)) * a2.y, 1e-30f);  // > 0 when covered
+          const int face = __float_as_int(a2.z);
+          if (key > bkey[i] || (key == bkey[i] && face < bface[i])) {
+            bkey[i] = key;
+            bface[i] = face;
+          }
+        }
+        if (covb && cb != ca) {
+          const float4 b3 = ws.coef[cb][3];
+          const float key = fmaxf(fmaf(N0b, b3.x, fmaf(N1b, b3.y, N2b * b3.z)) * b2.y, 1e-30f);
+          const int face = __float_as_int(b2.z);
+          if (key > bkey[i] || (key == bkey[i] && face < bface[i])) {
+            bkey[i] = key;
+            bface[i] = face;
+          }
+        }
+      }
+      __syncwarp();  // the table is rewritten for the next sample
+    }
   }
-  __syncwarp();
   return n_tests;
 }
 
@@ -595,44 +632,161 @@ __device__ __forceinline__ bool soft_pair_term(const float4 (&r)[kRecF4], const 
   return sg.d <= r2;
 }
 
-// pass 2 of the forward: log soft factors log(1 - A_j), A_j = exp(-d_j / delta) (Eqs.
-// probability-function .. back), summed per (sample, pixel) in ws.logp; vanishing factors are
-// counted in ws.nzero instead (the product is then 0).
-template <int SPT, bool MOVING, bool COUNT>
-struct FwdSoftPairs {
-  const TriRec* recs_set;
-  const Group* grp;
-  BlockPix bp;
-  WarpScratch<SPT>* ws;
-  uint32_t xbits;
-  float m, r2, inv_delta;
-  int prob;
-  uint32_t n_terms, n_eval, n_batches;
-  __device__ __forceinline__ void pair(bool ok, int face, int p, uint32_t smp) {
-    if (!ok) return;
-    const float u = ws->pu[p], v = ws->pv[p];
-    float4 r[kRecF4];
-    load_record<MOVING>(recs_set + face, r, false, true);
-    const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
-    while (smp) {
-      const int i = __ffs(smp) - 1;
-      smp &= smp - 1u;
-      const float tau = MOVING ? __ldg(&grp->tau[i]) : 0.f;
-      if (COUNT) ++n_eval;
-      EdgeVals e;
-      SoftGeom sg;
-      if (!soft_pair_term<MOVING>(r, ps, u, v, tau, (xbits >> i) & 1u, m, r2, e, sg)) continue;
-      float A, dA;
-      const float f = soft_factor(sg.d, inv_delta, prob, A, dA);
-      if (f > kTinyFactor) atomicAdd(&ws->logp[i][p], __logf(f));
-      else atomicAdd(&ws->nzero[i][p], 1);
-      if (COUNT) ++n_terms;
+// The fast solver's soft distance as affine coefficients in q = p - o (o the record origin) at one
+// sample time tau and keyframe X (Eqs. euc-dist-approx-1..3): w(tau) = (N1, N2) / D is affine in q
+// (N1 = cross(q, E2) + c1 tau + a11 tau^2, N2 = cross(E1, q) + c2 tau + a12 tau^2 with E1, E2 the
+// local edges at tau), hence so is the transported point p' = F(X) w(tau); the closest point w* of
+// F(X) to p' (three clamped edge projections) gives d = |F(tau) w* - p|^2 with
+// F(tau) w* - p = w*_1 E1 + w*_2 E2 - (q - tau g).  The forward's soft pass and the adjoint evaluate
+// the term with these same functions, so both take the same single-precision decisions (cutoff,
+// vanishing factor).  k[0] = (o, dp'x/dq), k[1] = (p'x(0), dp'y/dq, p'y(0)), k[2] = (e1(X), e2(X)),
+// k[3] = (1/|edge(X)|^2, tau g.x), k[4] = (E1, E2), k[5] = (tau g.y); wc = the affine w1, w2.
+struct SoftAffine {
+  float4 k[6];
+  float w1u, w1v, w1c, w2u, w2v, w2c;
+};
+
+__device__ __forceinline__ SoftAffine soft_affine(const float4& o, const float4& e2, const float4& d, const float4& g,
+                                                  const float4& a, const float4& il, float tau, int X, float D) {
+  SoftAffine s;
+  const float fx = (float)X;
+  const float E1x = fmaf(tau, d.x, o.z), E1y = fmaf(tau, d.y, o.w);
+  const float E2x = fmaf(tau, d.z, e2.x), E2y = fmaf(tau, d.w, e2.y);
+  const float iD = __fdividef(1.0f, D);
+  s.w1u = E2y * iD;
+  s.w1v = -E2x * iD;
+  s.w1c = tau * fmaf(a.x, tau, g.z) * iD;
+  s.w2u = -E1y * iD;
+  s.w2v = E1x * iD;
+  s.w2c = tau * fmaf(a.y, tau, g.w) * iD;
+  const float e1Xx = fmaf(fx, d.x, o.z), e1Xy = fmaf(fx, d.y, o.w);
+  const float e2Xx = fmaf(fx, d.z, e2.x), e2Xy = fmaf(fx, d.w, e2.y);
+  s.k[0] = make_float4(o.x, o.y, fmaf(s.w1u, e1Xx, s.w2u * e2Xx), fmaf(s.w1v, e1Xx, s.w2v * e2Xx));
+  s.k[1] = make_float4(fmaf(s.w1c, e1Xx, s.w2c * e2Xx), fmaf(s.w1u, e1Xy, s.w2u * e2Xy), fmaf(s.w1v, e1Xy, s.w2v * e2Xy),
+                       fmaf(s.w1c, e1Xy, s.w2c * e2Xy));
+  s.k[2] = make_float4(e1Xx, e1Xy, e2Xx, e2Xy);
+  s.k[3] = make_float4(il.x, il.y, il.z, tau * g.x);
+  s.k[4] = make_float4(E1x, E1y, E2x, E2y);
+  s.k[5] = make_float4(tau * g.y, 0.f, 0.f, 0.f);
+  return s;
+}
+
+// The distance of the pixel (u, v) from the coefficients; outputs q, p', the closest point and
+// r = F(tau) w* - p for the adjoint.
+struct SoftEval {
+  float qx, qy, ppx, ppy, rx, ry, d;
+  Closest c;
+};
+
+__device__ __forceinline__ SoftEval soft_affine_eval(const float4 (&k)[6], float u, float v) {
+  SoftEval e;
+  e.qx = u - k[0].x;
+  e.qy = v - k[0].y;
+  e.ppx = fmaf(e.qx, k[0].z, fmaf(e.qy, k[0].w, k[1].x));
+  e.ppy = fmaf(e.qx, k[1].y, fmaf(e.qy, k[1].z, k[1].w));
+  e.c = closest_local(k[2].x, k[2].y, k[2].z, k[2].w, e.ppx, e.ppy, make_float4(k[3].x, k[3].y, k[3].z, 0.f));
+  e.rx = fmaf(e.c.w1, k[4].x, fmaf(e.c.w2, k[4].z, k[3].w - e.qx));
+  e.ry = fmaf(e.c.w1, k[4].y, fmaf(e.c.w2, k[4].w, k[5].x - e.qy));
+  e.d = fmaf(e.rx, e.rx, e.ry * e.ry);
+  return e;
+}
+
+// pass 2 of the forward: the soft factors 1 - A_j of the uncovered samples (Eqs.
+// probability-function .. back), A_j = exp(-d_j / delta), summed as logs per (sample, pixel) in
+// registers (factors that vanish are counted apart).  Lanes over pixels, as in pass 1: per sample
+// time, the candidates whose box at tau dilated by the soft radius meets the block publish their
+// distance coefficients (soft_affine for the fast solver; the plain solver's closest point of F(t)
+// to p needs the record's origin, edges and inverse edge lengths) into the warp's table, and every
+// lane that takes part (its sample is uncovered) evaluates its own pixel against each of them.
+// Only the box and the denominator's fields stay in registers across the samples; a candidate's
+// other fields are read when it publishes.  Returns this lane's distance evaluations.
+template <int SPT, bool MOVING>
+__device__ __forceinline__ uint32_t soft_raster(const TriRec* recs_set, const int32_t* list, int beg, int end,
+                                                const float* tau_g, uint32_t xbits, int n, const TileBox& tb, float u,
+                                                float v, uint32_t my_s, float m, float r2, float inv_delta, int prob,
+                                                WarpScratch<SPT>& ws, float (&logp)[SPT], int (&nzero)[SPT],
+                                                uint32_t& n_terms, uint32_t& n_touch) {
+  const int lane = threadIdx.x & 31;
+  uint32_t n_eval = 0;
+#pragma unroll
+  for (int i = 0; i < SPT; ++i) {
+    logp[i] = 0.f;
+    nzero[i] = 0;
+  }
+  const uint32_t any_s = __reduce_or_sync(kFullMask, my_s);
+  if (tb.empty || !any_s) return 0;
+  for (int c0 = beg; c0 < end; c0 += 32) {
+    const int j = c0 + lane;
+    const bool valid = j < end;
+    const int f = valid ? __ldg(list + j) : 0;
+    const TriRec* rec = recs_set + f;
+    float4 b = make_float4(0.f, 0.f, 0.f, 0.f), db = b, e2 = b, a = b;
+    if (valid) {
+      b = __ldg(&rec->f4[kR_BB]);
+      e2 = __ldg(&rec->f4[kR_E2]);
+      if (MOVING) {
+        db = __ldg(&rec->f4[kR_DBB]);
+        a = __ldg(&rec->f4[kR_A]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) {
+      if (i >= (MOVING ? n : 1)) break;
+      if (!((any_s >> i) & 1u)) continue;
+      const float tau = MOVING ? __ldg(tau_g + i) : 0.f;
+      const bool hit = valid && fmaf(tau, db.x, b.x) - m <= tb.u_hi && fmaf(tau, db.y, b.y) + m >= tb.u_lo &&
+                       fmaf(tau, db.z, b.z) - m <= tb.v_hi && fmaf(tau, db.w, b.w) + m >= tb.v_lo;
+      const float D = MOVING ? fmaf(fmaf(a.w, tau, a.z), tau, e2.z) : e2.z;
+      uint32_t M = __ballot_sync(kFullMask, hit && fabsf(D) > kDetMin);
+      if (!M) continue;
+      if ((M >> lane) & 1u) {
+        const float4 o = __ldg(&rec->f4[kR_O]);
+        if (MOVING) {
+          const int X = (xbits >> i) & 1u;
+          const SoftAffine sa = soft_affine(o, e2, __ldg(&rec->f4[kR_D]), __ldg(&rec->f4[kR_G]), a,
+                                            __ldg(&rec->f4[X ? kR_IL1 : kR_IL0]), tau, X, D);
+#pragma unroll
+          for (int q = 0; q < 6; ++q) ws.coef[lane][q] = sa.k[q];
+        } else {
+          const float4 il0 = __ldg(&rec->f4[kR_IL0]);
+          ws.coef[lane][0] = o;
+          ws.coef[lane][1] = make_float4(e2.x, e2.y, il0.x, il0.y);
+          ws.coef[lane][2] = make_float4(il0.z, 0.f, 0.f, 0.f);
+        }
+      }
+      __syncwarp();
+      const bool take = (my_s >> i) & 1u;
+      if (lane == 0) n_touch += __popc(M);
+      if (take) n_eval += __popc(M);
+      while (M) {
+        const int c = __ffs(M) - 1;
+        M &= M - 1u;
+        if (!take) continue;
+        float dd;
+        if (MOVING) {
+          float4 k[6];
+#pragma unroll
+          for (int q = 0; q < 6; ++q) k[q] = ws.coef[c][q];
+          dd = soft_affine_eval(k, u, v).d;
+        } else {
+          // the plain solver's term exactly as soft_geom forms it: closest point of (0, e1, e2) to q
+          const float4 k0 = ws.coef[c][0], k1 = ws.coef[c][1];
+          const float ilz = ws.coef[c][2].x;
+          dd = closest_local(k0.z, k0.w, k1.x, k1.y, u - k0.x, v - k0.y, make_float4(k1.z, k1.w, ilz, 0.f)).d2;
+        }
+        if (dd <= r2) {
+          float A, dA;
+          const float fct = soft_factor(dd, inv_delta, prob, A, dA);
+          if (fct > kTinyFactor) logp[i] += __logf(fct);
+          else ++nzero[i];
+          ++n_terms;
+        }
+      }
+      __syncwarp();  // the table is rewritten for the next sample
     }
   }
-  __device__ __forceinline__ void batch_end(int) {
-    if ((threadIdx.x & 31) == 0) ++n_batches;  // lane 0: the adjoint's cost estimate
-  }
-};
+  return n_eval;
+}
 
 // Persistent scheduling.  A unit is one split of the sample groups (a contiguous range of
 // groups) over a 256-pixel patch of one render (one 16 x 16 tile, or four 8 x 8 tiles); it has

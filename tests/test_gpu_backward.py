@@ -122,6 +122,28 @@ def test_state_free_equals_stored_state(ctx, ctx_free, solver):
 
 
 @pytest.mark.parametrize("solver", ["plain", "fast"])
+@pytest.mark.parametrize("state_free", [False, True])
+def test_adjoint_is_finite_where_pixels_lie_on_edges(ctx, ctx_free, solver, state_free):
+    """The undisplaced icosphere of the shape-recovery workload seen by two of its full-size views
+    (256^2, T = 64): its symmetric tessellation puts pixel centres exactly on triangle edges, where
+    an uncovered sample's soft factor 1 - exp(-d / delta) rounds to zero.  Forward and adjoint must
+    take the same single-precision decision there (a factor the forward counted as vanishing is not
+    divided out by the adjoint), so every vertex gradient is finite."""
+    import paper_2602_07860_gb300 as mbr
+    views, template = scenes.config3()
+    c = ctx_free if state_free else ctx
+    for k in (0, 7):
+        sc = dict(views[k], verts=template)
+        v, f, a, mo, ca = gpu_inputs(sc)
+        G = torch.as_tensor(np.random.default_rng(3).normal(size=(sc["H"], sc["W"], 4)).astype(np.float32),
+                            device="cuda")
+        gv, ga = c.render_blur_backward(v, f, a, mo, ca, sc["T"], sc["H"], sc["W"], G, solver)
+        torch.cuda.synchronize()
+        assert torch.isfinite(gv).all() and torch.isfinite(ga).all(), (k, solver, state_free)
+        assert float(gv.abs().max()) > 0
+
+
+@pytest.mark.parametrize("solver", ["plain", "fast"])
 def test_adjoint_is_zero_without_visible_geometry_or_loss(ctx, solver):
     """No faces, a mesh far outside the view, or a zero dL/dimage: both gradients are exactly zero
     (and the buffers the call overwrites hold no stale values)."""
