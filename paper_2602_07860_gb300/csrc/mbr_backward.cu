@@ -174,13 +174,24 @@ struct BwdSoftGradPairs {
   float4* gslot_a;
   float4* gslot_b;
   float gax[3], gay[3], gbx[3], gby[3];
-  __device__ __forceinline__ void pair(bool ok, int face, int p, uint32_t smp) {
+  __device__ __forceinline__ void pair(bool ok, int face, int p, uint32_t smp, int slot) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) gax[q] = gay[q] = gbx[q] = gby[q] = 0.f;
     if (!ok) return;
     const float u = ws->pu[p], v = ws->pv[p];
+    // the candidate's record, staged in shared memory when its chunk was laid out
     float4 r[kRecF4];
-    load_record<MOVING>(recs_set + face, r, false, true);
+    r[kR_O] = ws->coef[slot][kR_O];
+    r[kR_E2] = ws->coef[slot][kR_E2];
+    r[kR_IL0] = ws->coef[slot][kR_IL0];
+    if (MOVING) {
+      r[kR_IL1] = ws->coef[slot][kR_IL1];
+      r[kR_BB] = ws->coef[slot][kR_BB];
+      r[kR_DBB] = ws->coef[slot][kR_DBB];
+      r[kR_D] = ws->coef[slot][kR_D];
+      r[kR_G] = ws->coef[slot][kR_G];
+      r[kR_A] = ws->coef[slot][kR_A];
+    }
     const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
     const float ga = ws->ga[p];
     while (smp) {
@@ -650,7 +661,7 @@ __device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile
       p3.faces = P.faces;
       p3.gslot_a = P.g_slot + (size_t)gq.slot_a * P.V * 2;
       p3.gslot_b = P.g_slot + (size_t)gq.slot_b * P.V * 2;
-      for_pairs<SPT, MOVING>(recs_set, P.soft.faces, sb, se, grp, n, B.tb, B.bp, m, allowed, any_s, ws, p3);
+      for_pairs<SPT, MOVING, true>(recs_set, P.soft.faces, sb, se, grp, n, B.tb, B.bp, m, allowed, any_s, ws, p3);
     }
     __syncwarp();  // the scratch is rewritten by the next group
   }

@@ -388,7 +388,8 @@ struct WarpScratch {
   uint32_t pmask[32];               //   block pixels each may touch,
   uint32_t smask[32];               //   samples each may touch,
   int prefix[33];                   //   pair offsets
-  float4 coef[32][6];               // per candidate of a chunk: its coefficients at one sample time
+  float4 coef[32][kRecF4];          // per candidate of a chunk: forward passes: its coefficients at one
+                                    // sample time; adjoint pairs: its whole record
 };
 
 // Pixel geometry of a warp block.
@@ -452,10 +453,13 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int r) {
   return pos;
 }
 
-// Walk a bin list (warp-collective): fn.pair(ok, face, p, samples) on every lane for each
-// batch of 32 pairs (ok false on lanes without a pair), then fn.batch_end(face or -1).
-// allowed[i] = pixels taking part for sample i; any_samples = OR of their samples.
-template <int SPT, bool MOVING, typename Fn>
+// Walk a bin list (warp-collective): fn.pair(ok, face, p, samples, slot) on every lane for each
+// batch of 32 pairs (ok false on lanes without a pair), then fn.batch_end(face or -1).  slot is
+// the candidate's row in the chunk: with STAGE, lane j copies candidate j's record into
+// ws.coef[j] when the chunk is laid out, so that the chunk's pairs read their records from
+// shared memory instead of global memory.  allowed[i] = pixels taking part for sample i;
+// any_samples = OR of their samples.
+template <int SPT, bool MOVING, bool STAGE = false, typename Fn>
 __device__ __forceinline__ void for_pairs(const TriRec* recs_set, const int32_t* list, int beg, int end,
                                           const Group* grp, int n, const TileBox& tb, const BlockPix& bp, float m,
                                           const uint32_t (&allowed)[SPT], uint32_t any_samples, WarpScratch<SPT>& ws,
@@ -491,13 +495,18 @@ __device__ __forceinline__ void for_pairs(const TriRec* recs_set, const int32_t*
     ws.smask[lane] = sm;
     ws.prefix[lane + 1] = incl;
     if (lane == 0) ws.prefix[0] = 0;
+    if (STAGE && pm) {
+      const TriRec* rec = recs_set + f;
+#pragma unroll
+      for (int q = 0; q < kRecF4; ++q)
+        if (MOVING || q == kR_O || q == kR_E2 || q == kR_Z || q == kR_BB || q == kR_IL0) ws.coef[lane][q] = __ldg(&rec->f4[q]);
+    }
     __syncwarp();
     for (int b = 0; b < total; b += 32) {
       const int k = b + lane;
-      int face = -1, p = 0;
+      int face = -1, p = 0, jj = 0;  // jj: last candidate whose first pair is at or before k
       uint32_t smp = 0;
       if (k < total) {
-        int jj = 0;  // last candidate whose first pair is at or before k
 #pragma unroll
         for (int step = 16; step > 0; step >>= 1)
           if (ws.prefix[jj + step] <= k) jj += step;
@@ -505,7 +514,7 @@ __device__ __forceinline__ void for_pairs(const TriRec* recs_set, const int32_t*
         face = ws.face[jj];
         smp = ws.smask[jj] & ws.pixs[p];
       }
-      fn.pair(smp != 0u, face, p, smp);
+      fn.pair(smp != 0u, face, p, smp, jj);
       fn.batch_end(face);
     }
   }
