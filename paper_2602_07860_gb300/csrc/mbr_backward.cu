@@ -294,14 +294,14 @@ struct BwdSoftGradPairs {
 
 // Adjoint of one covered sample: shading (Eq. fore + Lambert) and w = N / D through the edge
 // functions to the slot states of the winner's vertices.  Lanes that share a winner face are
-// reduced together (one leader adds them), so each distinct face of the warp costs one set of
-// vector atomics.  Warp-collective: every lane calls it; lanes without a covered sample pass
+// summed in shared memory (ws_rows, one row per lane) and their lowest lane adds them, so each
+// distinct face of the warp costs one set of vector atomics.  Warp-collective: every lane calls it; lanes without a covered sample pass
 // has = false.  EXT: texture colours and perspective-correct weights are honoured (see
 // raster_fwd_block); without it they are compiled out.
 template <bool MOVING, bool EXT>
 __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const TriRec* recs_set, int slot_a, int slot_b,
                                                 bool has, int f, float tau, float u, float v, float gr, float gg,
-                                                float gb) {
+                                                float gb, float4 (*ws_rows)[12]) {
   // per-vertex contributions: slot a (dx, dy, dnx, dny | dnz, dz), slot b (same), albedo (r, g, b)
   float4 ca[3], cb[3], cal[3];
   float ca_z[3], cb_z[3], ca_dz[3], cb_dz[3];
@@ -441,18 +441,18 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
   }
   float4* ga_ = P.g_slot + (size_t)slot_a * P.V * 2;
   float4* gb_ = P.g_slot + (size_t)slot_b * P.V * 2;
-  // one reduction when every covered lane of the warp has the same winner, else per-lane adds
+  // Lanes with the same winner face add their contributions in shared memory first: the lowest
+  // lane of each group sums the group's rows and issues the face's atomics, so a face costs one
+  // set of vector atomics per warp and sample instead of one per covered lane.
   const uint32_t hmask = __ballot_sync(0xffffffffu, has);
   if (!hmask) return;
   const int lane = threadIdx.x & 31;
-  const int leader = __ffs(hmask) - 1;
-  const int fl = __shfl_sync(0xffffffffu, f, leader);
-  const bool uniform = __all_sync(0xffffffffu, !has || f == fl) && __popc(hmask) > 1;
-  if (uniform) {
-    // one butterfly over all contributions; the offsets loop stays rolled to keep the adjoint's
-    // code small (the kernel is bound by instruction fetch, not by these few instructions)
-    constexpr int kDzA = MOVING ? 39 : 24, kDzB = 42;  // slot depth gradients (EXT only)
-    constexpr int NV = EXT ? (MOVING ? 45 : 27) : (MOVING ? 39 : 24);
+  const uint32_t grp = __match_any_sync(0xffffffffu, has ? f : -1 - lane);
+  const bool lead = has && (__ffs(grp) - 1) == lane;
+  constexpr int kDzA = MOVING ? 39 : 24, kDzB = 42;  // slot depth gradients (EXT only)
+  constexpr int NV = EXT ? (MOVING ? 45 : 27) : (MOVING ? 39 : 24);
+  const bool shared_sum = __any_sync(0xffffffffu, has && __popc(grp) > 1);
+  if (shared_sum) {
     float x[NV];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -466,25 +466,37 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
       }
       if (EXT) x[kDzA + q] = ca_dz[q];
     }
-#pragma unroll 1
-    for (int o = 16; o > 0; o >>= 1) {
+    float* row = reinterpret_cast<float*>(ws_rows + lane);
+    __syncwarp();
+    if (has) {
 #pragma unroll
-      for (int k = 0; k < NV; ++k) x[k] += __shfl_xor_sync(0xffffffffu, x[k], o);
+      for (int k = 0; k < NV; ++k) row[k] = x[k];
     }
+    __syncwarp();
+    if (lead) {
+      uint32_t others = grp & (grp - 1u);
+      while (others) {
+        const float* src = reinterpret_cast<const float*>(ws_rows + (__ffs(others) - 1));
+        others &= others - 1u;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      ca[q] = make_float4(x[5 * q], x[5 * q + 1], x[5 * q + 2], x[5 * q + 3]);
-      ca_z[q] = x[5 * q + 4];
-      cal[q] = make_float4(x[15 + 3 * q], x[16 + 3 * q], x[17 + 3 * q], 0.f);
-      if (MOVING) {
-        cb[q] = make_float4(x[24 + 5 * q], x[25 + 5 * q], x[26 + 5 * q], x[27 + 5 * q]);
-        cb_z[q] = x[28 + 5 * q];
-        if (EXT) cb_dz[q] = x[kDzB + q];
+        for (int k = 0; k < NV; ++k) x[k] += src[k];
       }
-      if (EXT) ca_dz[q] = x[kDzA + q];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        ca[q] = make_float4(x[5 * q], x[5 * q + 1], x[5 * q + 2], x[5 * q + 3]);
+        ca_z[q] = x[5 * q + 4];
+        cal[q] = make_float4(x[15 + 3 * q], x[16 + 3 * q], x[17 + 3 * q], 0.f);
+        if (MOVING) {
+          cb[q] = make_float4(x[24 + 5 * q], x[25 + 5 * q], x[26 + 5 * q], x[27 + 5 * q]);
+          cb_z[q] = x[28 + 5 * q];
+          if (EXT) cb_dz[q] = x[kDzB + q];
+        }
+        if (EXT) ca_dz[q] = x[kDzA + q];
+      }
     }
+    __syncwarp();  // the rows are read before they are reused
   }
-  if (uniform ? lane == leader : has) {
+  if (lead) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       atomicAdd(ga_ + (size_t)vid[q] * 2, ca[q]);
@@ -635,7 +647,7 @@ __device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile
         const bool has = rgb && f >= 0;
         const float tau = MOVING ? __ldg(gq.tau + i) : 0.f;
         covered_adjoint<MOVING, EXT>(P, recs_set, gq.slot_a, gq.slot_b, has, has ? f : 0, tau, B.u, B.v, B.gr,
-                                     B.gg, B.gb);
+                                     B.gg, B.gb, ws.coef);
       }
     }
 

@@ -388,8 +388,9 @@ struct WarpScratch {
   uint32_t pmask[32];               //   block pixels each may touch,
   uint32_t smask[32];               //   samples each may touch,
   int prefix[33];                   //   pair offsets
-  float4 coef[32][kRecF4];          // per candidate of a chunk: forward passes: its coefficients at one
-                                    // sample time; adjoint pairs: its whole record
+  float4 coef[32][12];              // per candidate of a chunk: forward passes: its coefficients at one
+                                    // sample time; adjoint pairs: its whole record; covered adjoint: a
+                                    // lane's contributions to its winner's vertices
 };
 
 // Pixel geometry of a warp block.
