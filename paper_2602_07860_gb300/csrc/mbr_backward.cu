@@ -159,14 +159,15 @@ __device__ __forceinline__ void soft_grad_accumulate(const float4 (&r)[kRecF4], 
 
 // pass 3 of the adjoint: gradient of alpha = 1 - prod_j (1 - A_j) w.r.t. the vertex positions of
 // every soft candidate.  A batch's pairs of one face sit on consecutive lanes: they are summed by
-// a segmented warp reduction (as many halving steps as the batch's longest run needs) and the
-// first lane of each run adds them to the slot gradients.
+// a segmented warp reduction (as many halving steps as the batch's longest run needs) into the
+// face's row of the chunk in shared memory, and each face's row is added to the slot gradients
+// once, when its chunk is done.
 template <int SPT, bool MOVING>
 struct BwdSoftGradPairs {
   const TriRec* recs_set;
   const Group* grp;
   BlockPix bp;
-  WarpScratch<SPT>* ws;
+  BwdScratch<SPT>* ws;
   uint32_t xbits;
   float m, r2, inv_delta;
   int prob;
@@ -240,7 +241,16 @@ struct BwdSoftGradPairs {
       soft_grad_accumulate<MOVING>(r, ps, e, sg, tau, X, gd, gax, gay, gbx, gby);
     }
   }
-  __device__ __forceinline__ void batch_end(int face) {
+  __device__ __forceinline__ void chunk_begin() {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < (MOVING ? 12 : 6); ++k) ws->grow[lane][k] = 0.f;
+    __syncwarp();
+  }
+  // the batch's pairs of one face sit on consecutive lanes: a segmented warp sum (as many halving
+  // steps as the batch's longest run needs); the first lane of each run adds the run's total to the
+  // face's row of the chunk (one head per face and batch, so no two lanes add to one row)
+  __device__ __forceinline__ void batch_end(int face, int slot) {
     const int lane = threadIdx.x & 31;
     bool mine = false;
 #pragma unroll
@@ -275,9 +285,23 @@ struct BwdSoftGradPairs {
       }
     }
     if (head) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) ws->grow[slot][q] += vals[q];
+    }
+    __syncwarp();  // the next batch's heads read the rows
+  }
+  // candidate j's gradient summed over the chunk's batches: one set of atomics per face
+  __device__ __forceinline__ void chunk_end(int face, bool had_pairs) {
+    const int lane = threadIdx.x & 31;
+    constexpr int NV = MOVING ? 12 : 6;
+    if (had_pairs) {
+      float vals[NV];
       bool any = false;
 #pragma unroll
-      for (int q = 0; q < NV; ++q) any |= vals[q] != 0.f;
+      for (int q = 0; q < NV; ++q) {
+        vals[q] = ws->grow[lane][q];
+        any |= vals[q] != 0.f;
+      }
       if (any) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
@@ -289,6 +313,7 @@ struct BwdSoftGradPairs {
         }
       }
     }
+    __syncwarp();
   }
 };
 
@@ -298,10 +323,10 @@ struct BwdSoftGradPairs {
 // distinct face of the warp costs one set of vector atomics.  Warp-collective: every lane calls it; lanes without a covered sample pass
 // has = false.  EXT: texture colours and perspective-correct weights are honoured (see
 // raster_fwd_block); without it they are compiled out.
-template <bool MOVING, bool EXT>
+template <bool MOVING, bool EXT, int R>
 __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const TriRec* recs_set, int slot_a, int slot_b,
                                                 bool has, int f, float tau, float u, float v, float gr, float gg,
-                                                float gb, float4 (*ws_rows)[12]) {
+                                                float gb, float4 (*ws_rows)[R]) {
   // per-vertex contributions: slot a (dx, dy, dnx, dny | dnz, dz), slot b (same), albedo (r, g, b)
   float4 ca[3], cb[3], cal[3];
   float ca_z[3], cb_z[3], ca_dz[3], cb_dz[3];
@@ -451,6 +476,7 @@ __device__ __forceinline__ void covered_adjoint(const RasterParams& P, const Tri
   const bool lead = has && (__ffs(grp) - 1) == lane;
   constexpr int kDzA = MOVING ? 39 : 24, kDzB = 42;  // slot depth gradients (EXT only)
   constexpr int NV = EXT ? (MOVING ? 45 : 27) : (MOVING ? 39 : 24);
+  static_assert(NV <= 4 * R, "a lane's contributions must fit its row");
   const bool shared_sum = __any_sync(0xffffffffu, has && __popc(grp) > 1);
   if (shared_sum) {
     float x[NV];
@@ -556,7 +582,7 @@ __device__ __forceinline__ BwdBlock bwd_block_setup(const RasterParams& P, int t
 template <int SPT, bool MOVING, bool EXT>
 __device__ __noinline__ uint32_t recompute_group_state(const RasterParams& P, const TriRec* recs_set,
                                                        const GroupRegs& gq, int g, int tile, const BwdBlock& B,
-                                                       bool alpha, int sb, int se, WarpScratch<SPT>& ws) {
+                                                       bool alpha, int sb, int se, BwdScratch<SPT>& ws) {
   const int lane = threadIdx.x & 31;
   const int n = gq.n;
   int cb, ce;
@@ -588,7 +614,7 @@ __device__ __noinline__ uint32_t recompute_group_state(const RasterParams& P, co
 // the adjoint of one 8 x 4 block over its split of the sample groups (EXT: see covered_adjoint)
 template <int TW, int TH, int SPT, bool MOVING, bool EXT>
 __device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile, int split, int wb,
-                                                 WarpScratch<SPT>& ws) {
+                                                 BwdScratch<SPT>& ws) {
   const BwdBlock B = bwd_block_setup<TW, TH>(P, tile, split, wb);
   const bool rgb = B.in_img && (B.gr != 0.f || B.gg != 0.f || B.gb != 0.f);  // colour gradient
   const bool alpha = B.in_img && B.ga != 0.f;                                // alpha gradient
@@ -685,17 +711,21 @@ template <int TW, int TH, int SPT, int KIND, bool EXT>
 __global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 3 : 2) raster_bwd_persistent(WorkQueue Q) {
   __shared__ CtaQueue cq;
   __shared__ RasterParams sp[kPersistentThreads / 32];
-  __shared__ WarpScratch<SPT> ws[kPersistentThreads / 32];
+  __shared__ BwdScratch<SPT> ws[kPersistentThreads / 32];
   cq.init();
   const int warp = threadIdx.x >> 5;
   RasterParams& P = sp[warp];
   int cur = -1, tile = 0, split = 0, wb = 0;
   while (warp_next<TW, TH>(Q, cq, P, cur, tile, split, wb)) {
     if (tile >= P.tiles_x * P.tiles_y) continue;
-    if (KIND == 0 || (KIND == 2 && !P.moving))
-      raster_bwd_block<TW, TH, 1, false, EXT>(P, tile, split, wb, *reinterpret_cast<WarpScratch<1>*>(ws + warp));
-    else
-      raster_bwd_block<TW, TH, SPT, true, EXT>(P, tile, split, wb, ws[warp]);
+    if constexpr (KIND == 0) {
+      raster_bwd_block<TW, TH, 1, false, EXT>(P, tile, split, wb, ws[warp]);
+    } else {
+      if (KIND == 2 && !P.moving)
+        raster_bwd_block<TW, TH, 1, false, EXT>(P, tile, split, wb, *reinterpret_cast<BwdScratch<1>*>(ws + warp));
+      else
+        raster_bwd_block<TW, TH, SPT, true, EXT>(P, tile, split, wb, ws[warp]);
+    }
   }
 }
 

@@ -376,7 +376,7 @@ __device__ __forceinline__ float4 shfl_box(const float4& b, int src) {
 constexpr uint32_t kFullMask = 0xffffffffu;
 
 // Per-warp shared scratch of the passes.
-template <int SPT>
+template <int SPT, int ROWS = 6>
 struct WarpScratch {
   float logp[SPT][32];              // sum of log(1 - A_j) over the soft factors that do not vanish
   int wface[SPT][32];               // state-free adjoint: recomputed winner face (or -1)
@@ -388,9 +388,16 @@ struct WarpScratch {
   uint32_t pmask[32];               //   block pixels each may touch,
   uint32_t smask[32];               //   samples each may touch,
   int prefix[33];                   //   pair offsets
-  float4 coef[32][12];              // per candidate of a chunk: forward passes: its coefficients at one
-                                    // sample time; adjoint pairs: its whole record; covered adjoint: a
-                                    // lane's contributions to its winner's vertices
+  float4 coef[32][ROWS];            // per candidate of a chunk: forward passes: its coefficients at one
+                                    // sample time (6 rows); adjoint: its staged record, or a lane's
+                                    // contributions to its covered sample's winner (12 rows)
+};
+
+// The adjoint's scratch: 12-row tables and, per candidate of a chunk, its soft-term gradient summed
+// over the chunk's pair batches before one set of global atomics.
+template <int SPT>
+struct BwdScratch : WarpScratch<SPT, SPT == 1 ? 10 : 12> {  // SPT 1: the plain solver (fewer values)
+  float grow[32][SPT == 1 ? 6 : 12];
 };
 
 // Pixel geometry of a warp block.
@@ -454,16 +461,19 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int r) {
   return pos;
 }
 
-// Walk a bin list (warp-collective): fn.pair(ok, face, p, samples, slot) on every lane for each
-// batch of 32 pairs (ok false on lanes without a pair), then fn.batch_end(face or -1).  slot is
+// Walk a bin list (warp-collective): fn.chunk_begin() before each chunk of 32 candidates that has
+// pairs, fn.pair(ok, face, p, samples, slot) on every lane for each batch of 32 pairs (ok false
+// on lanes without a pair), then fn.batch_end(face or -1, slot), and fn.chunk_end(face, has
+// pairs) on lane j for candidate j at the chunk's end.  slot is
 // the candidate's row in the chunk: with STAGE, lane j copies candidate j's record into
 // ws.coef[j] when the chunk is laid out, so that the chunk's pairs read their records from
 // shared memory instead of global memory.  allowed[i] = pixels taking part for sample i;
 // any_samples = OR of their samples.
-template <int SPT, bool MOVING, bool STAGE = false, typename Fn>
+template <int SPT, bool MOVING, bool STAGE = false, int ROWS = 6, typename Fn>
 __device__ __forceinline__ void for_pairs(const TriRec* recs_set, const int32_t* list, int beg, int end,
                                           const Group* grp, int n, const TileBox& tb, const BlockPix& bp, float m,
-                                          const uint32_t (&allowed)[SPT], uint32_t any_samples, WarpScratch<SPT>& ws,
+                                          const uint32_t (&allowed)[SPT], uint32_t any_samples,
+                                          WarpScratch<SPT, ROWS>& ws,
                                           Fn&& fn) {
   const int lane = threadIdx.x & 31;
   for (int c0 = beg; c0 < end; c0 += 32) {
@@ -496,6 +506,7 @@ __device__ __forceinline__ void for_pairs(const TriRec* recs_set, const int32_t*
     ws.smask[lane] = sm;
     ws.prefix[lane + 1] = incl;
     if (lane == 0) ws.prefix[0] = 0;
+    fn.chunk_begin();
     if (STAGE && pm) {
       const TriRec* rec = recs_set + f;
 #pragma unroll
@@ -516,8 +527,9 @@ __device__ __forceinline__ void for_pairs(const TriRec* recs_set, const int32_t*
         smp = ws.smask[jj] & ws.pixs[p];
       }
       fn.pair(smp != 0u, face, p, smp, jj);
-      fn.batch_end(face);
+      fn.batch_end(face, jj);
     }
+    fn.chunk_end(f, pm != 0u);
   }
   __syncwarp();
 }
@@ -534,10 +546,10 @@ __device__ __forceinline__ void for_pairs(const TriRec* recs_set, const int32_t*
 // (broadcast reads) and keeps the nearest covering face per sample in registers: a test is a few
 // multiply-adds, with no atomics.  bkey / bface: inverse-depth key (0: none) and face per sample.
 // Returns the coverage tests of this lane's pixel.
-template <int SPT, bool MOVING>
+template <int SPT, bool MOVING, int ROWS>
 __device__ __forceinline__ uint32_t core_raster(const TriRec* recs_set, const int32_t* list, int beg, int end,
                                                 const float* tau_g, int n, const TileBox& tb, float u, float v,
-                                                bool in_img, WarpScratch<SPT>& ws, float (&bkey)[SPT],
+                                                bool in_img, WarpScratch<SPT, ROWS>& ws, float (&bkey)[SPT],
                                                 int (&bface)[SPT]) {
   const int lane = threadIdx.x & 31;
   uint32_t n_tests = 0;
@@ -710,11 +722,11 @@ __device__ __forceinline__ SoftEval soft_affine_eval(const float4 (&k)[6], float
 // lane that takes part (its sample is uncovered) evaluates its own pixel against each of them.
 // Only the box and the denominator's fields stay in registers across the samples; a candidate's
 // other fields are read when it publishes.  Returns this lane's distance evaluations.
-template <int SPT, bool MOVING>
+template <int SPT, bool MOVING, int ROWS>
 __device__ __forceinline__ uint32_t soft_raster(const TriRec* recs_set, const int32_t* list, int beg, int end,
                                                 const float* tau_g, uint32_t xbits, int n, const TileBox& tb, float u,
                                                 float v, uint32_t my_s, float m, float r2, float inv_delta, int prob,
-                                                WarpScratch<SPT>& ws, float (&logp)[SPT], int (&nzero)[SPT],
+                                                WarpScratch<SPT, ROWS>& ws, float (&logp)[SPT], int (&nzero)[SPT],
                                                 uint32_t& n_terms, uint32_t& n_touch) {
   const int lane = threadIdx.x & 31;
   uint32_t n_eval = 0;
