@@ -54,105 +54,101 @@ __device__ __forceinline__ void rel_vertices(const float4* r, const PixelSetup<M
 
 // Gradient of one soft factor's distance d w.r.t. the vertex positions, scaled by gd = dL/dd:
 // accumulated into the slot-a (keyframe 0 / sub-frame) and slot-b (keyframe 1) sums.
-// Plain solver: exact distance, d d / d v_i = 2 (F w* - p) w*_i (envelope).  Fast solver:
-// d = |F(tau) w* - p|^2 with w* the closest point in F(X) to p' = F(X) w(tau) (Eqs.
-// euc-dist-approx-1..3), differentiated through w*, p' and w(tau) = N / D.
-template <bool MOVING>
-__device__ __forceinline__ void soft_grad_accumulate(const float4 (&r)[kRecF4], const PixelSetup<MOVING>& ps,
-                                                     const EdgeVals& e, const SoftGeom& sg, float tau, int X,
-                                                     float gd, float (&gax)[3], float (&gay)[3], float (&gbx)[3],
-                                                     float (&gby)[3]) {
-  const float grx = 2.f * sg.rx * gd, gry = 2.f * sg.ry * gd;  // d/d(F(tau) w* - p)
-  const float ws_[3] = {sg.c.w0, sg.c.w1, sg.c.w2};
+// Plain solver: exact distance, d d / d v_i = 2 (F w* - p) w*_i (envelope).
+__device__ __forceinline__ void soft_grad_plain(const Closest& c, float rx, float ry, float gd, float (&gax)[3],
+                                                float (&gay)[3]) {
+  const float grx = 2.f * rx * gd, gry = 2.f * ry * gd;  // d/d(F w* - p)
+  const float ws_[3] = {c.w0, c.w1, c.w2};
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    gax[q] = fmaf(ws_[q], grx, gax[q]);
+    gay[q] = fmaf(ws_[q], gry, gay[q]);
+  }
+}
+
+// Fast solver: d = |F(tau) w* - p|^2 with w* the closest point in F(X) to p' = F(X) w(tau) (Eqs.
+// euc-dist-approx-1..3), differentiated through w*, p' and w(tau) = N / D.  k: the term's
+// coefficients at tau (soft_affine: F(X)'s edges in k[2], F(tau)'s in k[4], tau g in k[3].w and
+// k[5].x); ev: its evaluation at the pixel; (w1, w2) = w(tau); iD = 1 / D(tau).
+__device__ __forceinline__ void soft_grad_fast(const float4 (&k)[6], const SoftEval& ev, float w1, float w2, float iD,
+                                               float tau, int X, float gd, float (&gax)[3], float (&gay)[3],
+                                               float (&gbx)[3], float (&gby)[3]) {
+  const float grx = 2.f * ev.rx * gd, gry = 2.f * ev.ry * gd;  // d/d(F(tau) w* - p)
+  const float ws_[3] = {ev.c.w0, ev.c.w1, ev.c.w2};
   float gtx[3], gty[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     gtx[q] = ws_[q] * grx;
     gty[q] = ws_[q] * gry;
   }
-  if (MOVING) {
-    // local vertex positions at tau and at keyframe X
-    const float e1tx = fmaf(tau, r[kR_D].x, r[kR_O].z), e1ty = fmaf(tau, r[kR_D].y, r[kR_O].w);
-    const float e2tx = fmaf(tau, r[kR_D].z, r[kR_E2].x), e2ty = fmaf(tau, r[kR_D].w, r[kR_E2].y);
-    const float fx = (float)X;
-    const float e1Xx = fmaf(fx, r[kR_D].x, r[kR_O].z), e1Xy = fmaf(fx, r[kR_D].y, r[kR_O].w);
-    const float e2Xx = fmaf(fx, r[kR_D].z, r[kR_E2].x), e2Xy = fmaf(fx, r[kR_D].w, r[kR_E2].y);
-    const float Vtx[3] = {0.f, e1tx, e2tx}, Vty[3] = {0.f, e1ty, e2ty};
-    const float VXx[3] = {0.f, e1Xx, e2Xx}, VXy[3] = {0.f, e1Xy, e2Xy};
-    float gXx[3] = {0.f, 0.f, 0.f}, gXy[3] = {0.f, 0.f, 0.f};
-    float gpx = 0.f, gpy = 0.f;
-    if (sg.c.region < 3) {
-      // w*_i = 1 - t, w*_j = t, t = ((p' - V_i) . E) / |E|^2 on edge (i, j) of F(X)
-      const int ei = sg.c.ei, ej = sg.c.ej;
-      float gti = 0.f, gtj = 0.f, Ex = 0.f, Ey = 0.f, Rx = 0.f, Ry = 0.f;
+  // local vertex positions at tau and at keyframe X
+  const float Vtx[3] = {0.f, k[4].x, k[4].z}, Vty[3] = {0.f, k[4].y, k[4].w};
+  const float VXx[3] = {0.f, k[2].x, k[2].z}, VXy[3] = {0.f, k[2].y, k[2].w};
+  float gXx[3] = {0.f, 0.f, 0.f}, gXy[3] = {0.f, 0.f, 0.f};
+  float gpx = 0.f, gpy = 0.f;
+  if (ev.c.region < 3) {
+    // w*_i = 1 - t, w*_j = t, t = ((p' - V_i) . E) / |E|^2 on edge (i, j) of F(X)
+    const int ei = ev.c.ei, ej = ev.c.ej;
+    float gti = 0.f, gtj = 0.f, Ex = 0.f, Ey = 0.f, Rx = 0.f, Ry = 0.f;
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        if (q == ei) {
-          gti = Vtx[q] * grx + Vty[q] * gry;
-          Rx = sg.ppx - VXx[q];
-          Ry = sg.ppy - VXy[q];
-          Ex -= VXx[q];
-          Ey -= VXy[q];
-        }
-        if (q == ej) {
-          gtj = Vtx[q] * grx + Vty[q] * gry;
-          Ex += VXx[q];
-          Ey += VXy[q];
-        }
+    for (int q = 0; q < 3; ++q) {
+      if (q == ei) {
+        gti = Vtx[q] * grx + Vty[q] * gry;
+        Rx = ev.ppx - VXx[q];
+        Ry = ev.ppy - VXy[q];
+        Ex -= VXx[q];
+        Ey -= VXy[q];
       }
-      const float L2 = fmaf(Ex, Ex, Ey * Ey);
-      const float gt = __fdividef(gtj - gti, L2), t = sg.c.t;
-      gpx = gt * Ex;
-      gpy = gt * Ey;
-      const float gix = gt * (-Ex - Rx + 2.f * t * Ex), giy = gt * (-Ey - Ry + 2.f * t * Ey);
-      const float gjx = gt * (Rx - 2.f * t * Ex), gjy = gt * (Ry - 2.f * t * Ey);
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        if (q == ei) { gXx[q] += gix; gXy[q] += giy; }
-        if (q == ej) { gXx[q] += gjx; gXy[q] += gjy; }
+      if (q == ej) {
+        gtj = Vtx[q] * grx + Vty[q] * gry;
+        Ex += VXx[q];
+        Ey += VXy[q];
       }
     }
-    // p' = F(X) w(tau)
-    const float w1 = sg.w1, w2 = sg.w2, w0 = 1.f - w1 - w2;
-    const float wv[3] = {w0, w1, w2};
-    float gw[3];
+    const float L2 = fmaf(Ex, Ex, Ey * Ey);
+    const float gt = __fdividef(gtj - gti, L2), t = ev.c.t;
+    gpx = gt * Ex;
+    gpy = gt * Ey;
+    const float gix = gt * (-Ex - Rx + 2.f * t * Ex), giy = gt * (-Ey - Ry + 2.f * t * Ey);
+    const float gjx = gt * (Rx - 2.f * t * Ex), gjy = gt * (Ry - 2.f * t * Ey);
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      gXx[q] = fmaf(wv[q], gpx, gXx[q]);
-      gXy[q] = fmaf(wv[q], gpy, gXy[q]);
-      gw[q] = VXx[q] * gpx + VXy[q] * gpy;
+      if (q == ei) { gXx[q] += gix; gXy[q] += giy; }
+      if (q == ej) { gXx[q] += gjx; gXy[q] += gjy; }
     }
-    // w = N / D with D = N0 + N1 + N2
-    const float sw = wv[0] * gw[0] + wv[1] * gw[1] + wv[2] * gw[2];
-    const float invD = __fdividef(1.f, e.D);
-    float ax[3], ay[3], ex[3], ey[3];
-    rel_vertices<MOVING>(r, ps, tau, ax, ay);
-    edge_backward((gw[0] - sw) * invD, (gw[1] - sw) * invD, (gw[2] - sw) * invD, ax, ay, ex, ey);
+  }
+  // p' = F(X) w(tau)
+  const float w0 = 1.f - w1 - w2;
+  const float wv[3] = {w0, w1, w2};
+  float gw[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      gtx[q] += ex[q];
-      gty[q] += ey[q];
-    }
-    // F(tau) = lerp of the two keyframes; F(X) is keyframe X
+  for (int q = 0; q < 3; ++q) {
+    gXx[q] = fmaf(wv[q], gpx, gXx[q]);
+    gXy[q] = fmaf(wv[q], gpy, gXy[q]);
+    gw[q] = VXx[q] * gpx + VXy[q] * gpy;
+  }
+  // w = N / D with D = N0 + N1 + N2; the N_i are cross products of the vertices relative to the
+  // pixel at tau, a_i = v_i(tau) - p (local frame: v_0(tau) - p = -(q - tau g))
+  const float sw = wv[0] * gw[0] + wv[1] * gw[1] + wv[2] * gw[2];
+  const float qtx = ev.qx - k[3].w, qty = ev.qy - k[5].x;
+  const float ax[3] = {-qtx, Vtx[1] - qtx, Vtx[2] - qtx}, ay[3] = {-qty, Vty[1] - qty, Vty[2] - qty};
+  float ex[3], ey[3];
+  edge_backward((gw[0] - sw) * iD, (gw[1] - sw) * iD, (gw[2] - sw) * iD, ax, ay, ex, ey);
+  // F(tau) = lerp of the two keyframes; F(X) is keyframe X
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      gax[q] = fmaf(1.f - tau, gtx[q], gax[q]);
-      gay[q] = fmaf(1.f - tau, gty[q], gay[q]);
-      gbx[q] = fmaf(tau, gtx[q], gbx[q]);
-      gby[q] = fmaf(tau, gty[q], gby[q]);
-      if (X == 0) {
-        gax[q] += gXx[q];
-        gay[q] += gXy[q];
-      } else {
-        gbx[q] += gXx[q];
-        gby[q] += gXy[q];
-      }
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      gax[q] += gtx[q];
-      gay[q] += gty[q];
+  for (int q = 0; q < 3; ++q) {
+    gtx[q] += ex[q];
+    gty[q] += ey[q];
+    gax[q] = fmaf(1.f - tau, gtx[q], gax[q]);
+    gay[q] = fmaf(1.f - tau, gty[q], gay[q]);
+    gbx[q] = fmaf(tau, gtx[q], gbx[q]);
+    gby[q] = fmaf(tau, gty[q], gby[q]);
+    if (X == 0) {
+      gax[q] += gXx[q];
+      gay[q] += gXy[q];
+    } else {
+      gbx[q] += gXx[q];
+      gby[q] += gXy[q];
     }
   }
 }
@@ -175,11 +171,85 @@ struct BwdSoftGradPairs {
   float4* gslot_a;
   float4* gslot_b;
   float gax[3], gay[3], gbx[3], gby[3];
+  // with at most two samples per group the fast solver's pairs read the term's coefficients at
+  // each sample time, formed once per candidate when its chunk is laid out (8 rows per sample:
+  // soft_affine's k[0..4], (k[5].x, 1 / D, w1u, w1v), (w1c, w2u, w2v, w2c), the box at tau dilated
+  // by m); otherwise they read the staged record and form the coefficients per pair
+  static constexpr bool kAff = MOVING && SPT == 2;
+  __device__ __forceinline__ void stage(const TriRec* rec, uint32_t sm) {
+    const int lane = threadIdx.x & 31;
+    if constexpr (kAff) {
+      const float4 o = __ldg(&rec->f4[kR_O]), e2 = __ldg(&rec->f4[kR_E2]), d = __ldg(&rec->f4[kR_D]);
+      const float4 g = __ldg(&rec->f4[kR_G]), a = __ldg(&rec->f4[kR_A]);
+      const float4 b = __ldg(&rec->f4[kR_BB]), db = __ldg(&rec->f4[kR_DBB]);
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        if (!((sm >> i) & 1u)) continue;
+        const float tau = __ldg(&grp->tau[i]);
+        const int X = (xbits >> i) & 1u;
+        const float D = fmaf(fmaf(a.w, tau, a.z), tau, e2.z);
+        float4* row = ws->coef[lane] + 8 * i;
+        if (!(fabsf(D) > kDetMin)) {
+          row[7] = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);  // no pixel passes
+          continue;
+        }
+        const SoftAffine sa = soft_affine(o, e2, d, g, a, __ldg(&rec->f4[X ? kR_IL1 : kR_IL0]), tau, X, D);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) row[q] = sa.k[q];
+        row[5] = make_float4(sa.k[5].x, __fdividef(1.0f, D), sa.w1u, sa.w1v);
+        row[6] = make_float4(sa.w1c, sa.w2u, sa.w2v, sa.w2c);
+        row[7] = make_float4(fmaf(tau, db.x, b.x) - m, fmaf(tau, db.y, b.y) + m, fmaf(tau, db.z, b.z) - m,
+                             fmaf(tau, db.w, b.w) + m);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < kRecF4; ++q)
+        if (MOVING || q == kR_O || q == kR_E2 || q == kR_Z || q == kR_BB || q == kR_IL0) ws->coef[lane][q] = __ldg(&rec->f4[q]);
+    }
+  }
+  // the factor's share of dL/dd: gd = dL/dalpha * prod_{l != j} (1 - A_l) * dA_j/dd
+  __device__ __forceinline__ float factor_grad(float d, float ga, int i, int p) const {
+    float A, dA;
+    const float f = soft_factor(d, inv_delta, prob, A, dA);
+    const float S = ws->logp[i][p];
+    const int nz = ws->nzero[i][p];
+    // the product of the other factors, each <= 1 (the bound keeps a factor that rounds to 0
+    // from turning it into infinity)
+    float excl;
+    if (nz == 0) excl = fminf(__expf(S - __logf(f)), 1.f);
+    else excl = (nz == 1 && f <= kTinyFactor) ? __expf(S) : 0.f;
+    return ga * excl * dA;
+  }
   __device__ __forceinline__ void pair(bool ok, int face, int p, uint32_t smp, int slot) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) gax[q] = gay[q] = gbx[q] = gby[q] = 0.f;
     if (!ok) return;
     const float u = ws->pu[p], v = ws->pv[p];
+    const float ga = ws->ga[p];
+    if constexpr (kAff) {
+      while (smp) {
+        const int i = __ffs(smp) - 1;
+        smp &= smp - 1u;
+        const float4* row = ws->coef[slot] + 8 * i;
+        const float4 bx = row[7];
+        if (!(u >= bx.x && u <= bx.y && v >= bx.z && v <= bx.w)) continue;
+        float4 k[6];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) k[q] = row[q];
+        const float4 r5 = row[5];
+        k[5] = make_float4(r5.x, 0.f, 0.f, 0.f);
+        // the term exactly as the forward's soft pass evaluates it (same coefficients)
+        const SoftEval ev = soft_affine_eval(k, u, v);
+        if (!(ev.d <= r2)) continue;
+        const float gd = factor_grad(ev.d, ga, i, p);
+        if (gd == 0.f) continue;
+        const float4 r6 = row[6];
+        const float w1 = fmaf(ev.qx, r5.z, fmaf(ev.qy, r5.w, r6.x));
+        const float w2 = fmaf(ev.qx, r6.y, fmaf(ev.qy, r6.z, r6.w));
+        soft_grad_fast(k, ev, w1, w2, r5.y, __ldg(&grp->tau[i]), (xbits >> i) & 1u, gd, gax, gay, gbx, gby);
+      }
+      return;
+    }
     // the candidate's record, staged in shared memory when its chunk was laid out
     float4 r[kRecF4];
     r[kR_O] = ws->coef[slot][kR_O];
@@ -194,51 +264,33 @@ struct BwdSoftGradPairs {
       r[kR_A] = ws->coef[slot][kR_A];
     }
     const PixelSetup<MOVING> ps = pixel_setup<MOVING>(r, u, v);
-    const float ga = ws->ga[p];
     while (smp) {
       const int i = __ffs(smp) - 1;
       smp &= smp - 1u;
       const float tau = MOVING ? __ldg(&grp->tau[i]) : 0.f;
       const int X = (xbits >> i) & 1u;
-      EdgeVals e;
-      SoftGeom sg;
       if (MOVING) {
-        // the term exactly as the forward's soft pass evaluates it (soft_affine), then the
-        // quantities the gradient needs
+        // the term exactly as the forward's soft pass evaluates it (soft_affine)
         if (!in_box_at(r, tau, m, u, v)) continue;
-        e.D = fmaf(fmaf(r[kR_A].w, tau, r[kR_A].z), tau, r[kR_E2].z);
-        if (!(fabsf(e.D) > kDetMin)) continue;
+        const float D = fmaf(fmaf(r[kR_A].w, tau, r[kR_A].z), tau, r[kR_E2].z);
+        if (!(fabsf(D) > kDetMin)) continue;
         const SoftAffine sa = soft_affine(r[kR_O], r[kR_E2], r[kR_D], r[kR_G], r[kR_A], X ? r[kR_IL1] : r[kR_IL0], tau,
-                                          X, e.D);
+                                          X, D);
         const SoftEval ev = soft_affine_eval(sa.k, u, v);
         if (!(ev.d <= r2)) continue;
-        sg.d = ev.d;
-        sg.c = ev.c;
-        sg.w1 = fmaf(ev.qx, sa.w1u, fmaf(ev.qy, sa.w1v, sa.w1c));
-        sg.w2 = fmaf(ev.qx, sa.w2u, fmaf(ev.qy, sa.w2v, sa.w2c));
-        sg.ppx = ev.ppx;
-        sg.ppy = ev.ppy;
-        sg.rx = ev.rx;
-        sg.ry = ev.ry;
-        e.N1 = sg.w1 * e.D;
-        e.N2 = sg.w2 * e.D;
-        e.N0 = e.D - e.N1 - e.N2;
-      } else if (!soft_pair_term<MOVING>(r, ps, u, v, tau, X, m, r2, e, sg)) {
-        continue;
+        const float gd = factor_grad(ev.d, ga, i, p);
+        if (gd == 0.f) continue;
+        const float w1 = fmaf(ev.qx, sa.w1u, fmaf(ev.qy, sa.w1v, sa.w1c));
+        const float w2 = fmaf(ev.qx, sa.w2u, fmaf(ev.qy, sa.w2v, sa.w2c));
+        soft_grad_fast(sa.k, ev, w1, w2, __fdividef(1.0f, D), tau, X, gd, gax, gay, gbx, gby);
+      } else {
+        EdgeVals e;
+        SoftGeom sg;
+        if (!soft_pair_term<MOVING>(r, ps, u, v, tau, X, m, r2, e, sg)) continue;
+        const float gd = factor_grad(sg.d, ga, i, p);
+        if (gd == 0.f) continue;
+        soft_grad_plain(sg.c, sg.rx, sg.ry, gd, gax, gay);
       }
-      float A, dA;
-      const float f = soft_factor(sg.d, inv_delta, prob, A, dA);
-      const float S = ws->logp[i][p];
-      const int nz = ws->nzero[i][p];
-      // the product of the other factors, each <= 1 (the bound keeps a factor that rounds to 0
-      // from turning it into infinity)
-      float excl;
-      if (nz == 0) excl = fminf(__expf(S - __logf(f)), 1.f);
-      else excl = (nz == 1 && f <= kTinyFactor) ? __expf(S) : 0.f;
-      // alpha = 1 - prod(1 - A_l): d alpha / d d_j = excl dA_j/dd
-      const float gd = ga * excl * dA;
-      if (gd == 0.f) continue;
-      soft_grad_accumulate<MOVING>(r, ps, e, sg, tau, X, gd, gax, gay, gbx, gby);
     }
   }
   __device__ __forceinline__ void chunk_begin() {

@@ -523,7 +523,7 @@ __device__ __forceinline__ void raster_fwd_block(const RasterParams& P, int tile
 // Persistent forward raster: KIND 0 = plain solver only, 1 = fast solver only, 2 = mixed batch;
 // EXT: with the variants (see raster_fwd_block).
 template <int TW, int TH, int SPT, int KIND, bool EXT>
-__global__ void __launch_bounds__(kPersistentThreads, KIND == 0 ? 3 : 2) raster_fwd_persistent(WorkQueue Q) {
+__global__ void __launch_bounds__(kPersistentThreads, SPT <= 2 ? 3 : 2) raster_fwd_persistent(WorkQueue Q) {
   __shared__ CtaQueue cq;
   __shared__ RasterParams sp[kPersistentThreads / 32];
   __shared__ WarpScratch<SPT> ws[kPersistentThreads / 32];

@@ -393,10 +393,18 @@ struct WarpScratch {
                                     // contributions to its covered sample's winner (12 rows)
 };
 
-// The adjoint's scratch: 12-row tables and, per candidate of a chunk, its soft-term gradient summed
-// over the chunk's pair batches before one set of global atomics.
+// The adjoint's scratch: the staging table and, per candidate of a chunk, its soft-term gradient
+// summed over the chunk's pair batches before one set of global atomics.  Table rows: the plain
+// solver (SPT 1) stages 5 record fields (rows 0-3 and 9); the fast solver stages 8 rows of
+// coefficients per sample with up to two samples per group, its whole record (11 rows) with four.
+// The row count is odd, so that the 8 lanes of a 16-byte shared-memory access phase that read
+// the same row of different candidates fall in distinct banks.
 template <int SPT>
-struct BwdScratch : WarpScratch<SPT, SPT == 1 ? 10 : 12> {  // SPT 1: the plain solver (fewer values)
+constexpr int bwd_rows() {
+  return SPT == 1 ? 11 : (SPT == 2 ? 17 : 13);
+}
+template <int SPT>
+struct BwdScratch : WarpScratch<SPT, bwd_rows<SPT>()> {
   float grow[32][SPT == 1 ? 6 : 12];
 };
 
@@ -464,11 +472,11 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int r) {
 // Walk a bin list (warp-collective): fn.chunk_begin() before each chunk of 32 candidates that has
 // pairs, fn.pair(ok, face, p, samples, slot) on every lane for each batch of 32 pairs (ok false
 // on lanes without a pair), then fn.batch_end(face or -1, slot), and fn.chunk_end(face, has
-// pairs) on lane j for candidate j at the chunk's end.  slot is
-// the candidate's row in the chunk: with STAGE, lane j copies candidate j's record into
-// ws.coef[j] when the chunk is laid out, so that the chunk's pairs read their records from
-// shared memory instead of global memory.  allowed[i] = pixels taking part for sample i;
-// any_samples = OR of their samples.
+// pairs) on lane j for candidate j at the chunk's end.  slot is the candidate's row in the chunk:
+// with STAGE, lane j calls fn.stage(record, samples) for candidate j when the chunk is laid out,
+// so that what the chunk's pairs need of a candidate (its record, or its per-sample coefficients)
+// is read from ws.coef[j] in shared memory instead of global memory.  allowed[i] = pixels taking
+// part for sample i; any_samples = OR of their samples.
 template <int SPT, bool MOVING, bool STAGE = false, int ROWS = 6, typename Fn>
 __device__ __forceinline__ void for_pairs(const TriRec* recs_set, const int32_t* list, int beg, int end,
                                           const Group* grp, int n, const TileBox& tb, const BlockPix& bp, float m,
@@ -507,12 +515,7 @@ __device__ __forceinline__ void for_pairs(const TriRec* recs_set, const int32_t*
     ws.prefix[lane + 1] = incl;
     if (lane == 0) ws.prefix[0] = 0;
     fn.chunk_begin();
-    if (STAGE && pm) {
-      const TriRec* rec = recs_set + f;
-#pragma unroll
-      for (int q = 0; q < kRecF4; ++q)
-        if (MOVING || q == kR_O || q == kR_E2 || q == kR_Z || q == kR_BB || q == kR_IL0) ws.coef[lane][q] = __ldg(&rec->f4[q]);
-    }
+    if (STAGE && pm) fn.stage(recs_set + f, sm);
     __syncwarp();
     for (int b = 0; b < total; b += 32) {
       const int k = b + lane;
