@@ -154,10 +154,16 @@ __device__ __forceinline__ void soft_grad_fast(const float4 (&k)[6], const SoftE
 }
 
 // pass 3 of the adjoint: gradient of alpha = 1 - prod_j (1 - A_j) w.r.t. the vertex positions of
-// every soft candidate.  A batch's pairs of one face sit on consecutive lanes: they are summed by
-// a segmented warp reduction (as many halving steps as the batch's longest run needs) into the
-// face's row of the chunk in shared memory, and each face's row is added to the slot gradients
-// once, when its chunk is done.
+// every soft candidate, summed per candidate into its row of the chunk in shared memory; each row
+// is added to the slot gradients once, when its chunk is done.
+//   fast solver (batches)  a batch's pairs of one face sit on consecutive lanes: a segmented warp
+//                          sum (as many halving steps as the batch's longest run needs) gives one
+//                          head per face and batch, which adds the run's total to the row;
+//   plain solver (runs)    each lane sums its run of pairs in registers while they belong to one
+//                          candidate and adds the sum to the candidate's row when the candidate
+//                          changes (shared-memory atomics: a candidate's pairs may span runs).
+// The fast solver reads eight staged rows per term, which a batch's lanes of one candidate read as
+// broadcasts; the plain solver's terms are short, so the warp sum would dominate them.
 template <int SPT, bool MOVING>
 struct BwdSoftGradPairs {
   const TriRec* recs_set;
@@ -170,7 +176,8 @@ struct BwdSoftGradPairs {
   const int32_t* faces;
   float4* gslot_a;
   float4* gslot_b;
-  float gax[3], gay[3], gbx[3], gby[3];
+  float gax[3], gay[3], gbx[3], gby[3];  // this lane's sums
+  int cur;                               // runs: the candidate they belong to (-1: none)
   // with at most two samples per group the fast solver's pairs read the term's coefficients at
   // each sample time, formed once per candidate when its chunk is laid out (8 rows per sample:
   // soft_affine's k[0..4], (k[5].x, 1 / D, w1u, w1v), (w1c, w2u, w2v, w2c), the box at tau dilated
@@ -220,10 +227,23 @@ struct BwdSoftGradPairs {
     else excl = (nz == 1 && f <= kTinyFactor) ? __expf(S) : 0.f;
     return ga * excl * dA;
   }
+  // batches: this lane's pair only
   __device__ __forceinline__ void pair(bool ok, int face, int p, uint32_t smp, int slot) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) gax[q] = gay[q] = gbx[q] = gby[q] = 0.f;
-    if (!ok) return;
+    if (ok) accumulate(p, smp, slot);
+  }
+  // runs: the sums carry over while the candidate stays the same
+  __device__ __forceinline__ void pair_run(int face, int p, uint32_t smp, int slot) {
+    if (slot != cur) {
+      flush();
+      cur = slot;
+    }
+    accumulate(p, smp, slot);
+  }
+  // the soft terms of one pair (candidate slot of the chunk, block pixel p, samples smp), added
+  // to this lane's sums
+  __device__ __forceinline__ void accumulate(int p, uint32_t smp, int slot) {
     const float u = ws->pu[p], v = ws->pv[p];
     const float ga = ws->ga[p];
     if constexpr (kAff) {
@@ -293,10 +313,28 @@ struct BwdSoftGradPairs {
       }
     }
   }
+  // runs: this lane's sums of the current candidate into its row of the chunk
+  __device__ __forceinline__ void flush() {
+    if (cur >= 0) {
+      float* row = ws->grow[cur];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (gax[q] != 0.f) atomicAdd(row + 2 * q, gax[q]);
+        if (gay[q] != 0.f) atomicAdd(row + 2 * q + 1, gay[q]);
+        if (MOVING && gbx[q] != 0.f) atomicAdd(row + 6 + 2 * q, gbx[q]);
+        if (MOVING && gby[q] != 0.f) atomicAdd(row + 6 + 2 * q + 1, gby[q]);
+        gax[q] = gay[q] = gbx[q] = gby[q] = 0.f;
+      }
+    }
+    cur = -1;
+  }
   __device__ __forceinline__ void chunk_begin() {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < (MOVING ? 12 : 6); ++k) ws->grow[lane][k] = 0.f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) gax[q] = gay[q] = gbx[q] = gby[q] = 0.f;
+    cur = -1;
     __syncwarp();
   }
   // the batch's pairs of one face sit on consecutive lanes: a segmented warp sum (as many halving
@@ -342,7 +380,7 @@ struct BwdSoftGradPairs {
     }
     __syncwarp();  // the next batch's heads read the rows
   }
-  // candidate j's gradient summed over the chunk's batches: one set of atomics per face
+  // candidate j's gradient summed over the chunk's pairs: one set of atomics per face
   __device__ __forceinline__ void chunk_end(int face, bool had_pairs) {
     const int lane = threadIdx.x & 31;
     constexpr int NV = MOVING ? 12 : 6;
@@ -751,7 +789,7 @@ __device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile
       p3.faces = P.faces;
       p3.gslot_a = P.g_slot + (size_t)gq.slot_a * P.V * 2;
       p3.gslot_b = P.g_slot + (size_t)gq.slot_b * P.V * 2;
-      for_pairs<SPT, MOVING, true>(recs_set, P.soft.faces, sb, se, grp, n, B.tb, B.bp, m, allowed, any_s, ws, p3);
+      for_pairs<SPT, MOVING, true, !MOVING>(recs_set, P.soft.faces, sb, se, grp, n, B.tb, B.bp, m, allowed, any_s, ws, p3);
     }
     __syncwarp();  // the scratch is rewritten by the next group
   }

@@ -362,16 +362,14 @@ __device__ __forceinline__ float4 shfl_box(const float4& b, int src) {
 }
 
 // ---------------------------------------------------------------- compacted pair passes
-// A warp owns an 8 x 4 pixel block (lane p = pixel (p % 8, p / 8)).  Rather than evaluating a
-// candidate triangle on all 32 lanes when it touches a few of them, a pass walks its bin list
-// 32 candidates at a time in two steps:
+// A warp owns an 8 x 4 pixel block (lane p = pixel (p % 8, p / 8)).  The adjoint's soft pass does
+// not evaluate a candidate triangle on all 32 lanes when its box touches a few of the pixels; it
+// walks the bin list 32 candidates at a time in two steps:
 //   generation  lane j takes candidate j: its samples whose box meets the warp's rectangle, and
 //               the block pixels its box can touch that take part in the pass; a warp scan lays
 //               the (candidate, pixel) pairs out in candidate order;
-//   processing  the pairs go to the 32 lanes in order, so every lane evaluates a distinct pair.
-// Results per (sample, pixel) meet in the warp's shared scratch through shared-memory atomics:
-// the z-test winner as a 64-bit max of (inverse-depth bits, ~face), the soft product as a sum
-// of log factors (vanishing factors counted apart for the adjoint).
+//   processing  the pairs go to the lanes in batches of 32 consecutive pairs, or in 32 runs of
+//               consecutive pairs, one per lane (see for_pairs).
 
 constexpr uint32_t kFullMask = 0xffffffffu;
 
@@ -469,15 +467,21 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int r) {
   return pos;
 }
 
-// Walk a bin list (warp-collective): fn.chunk_begin() before each chunk of 32 candidates that has
-// pairs, fn.pair(ok, face, p, samples, slot) on every lane for each batch of 32 pairs (ok false
-// on lanes without a pair), then fn.batch_end(face or -1, slot), and fn.chunk_end(face, has
-// pairs) on lane j for candidate j at the chunk's end.  slot is the candidate's row in the chunk:
-// with STAGE, lane j calls fn.stage(record, samples) for candidate j when the chunk is laid out,
-// so that what the chunk's pairs need of a candidate (its record, or its per-sample coefficients)
-// is read from ws.coef[j] in shared memory instead of global memory.  allowed[i] = pixels taking
-// part for sample i; any_samples = OR of their samples.
-template <int SPT, bool MOVING, bool STAGE = false, int ROWS = 6, typename Fn>
+// Walk a bin list (warp-collective).  Per chunk of 32 candidates that has pairs: fn.chunk_begin()
+// on every lane; with STAGE, fn.stage(record, samples) on lane j for candidate j (what the chunk's
+// pairs need of a candidate, read from shared memory instead of global memory); then the pairs;
+// finally fn.chunk_end(face, has pairs) on lane j for candidate j.  The pairs go to the lanes in
+// one of two ways:
+//   batches (RUNS false)  pair k of batch b to lane k - 32 b: fn.pair(ok, face, p, samples, slot)
+//                         on every lane (ok false on lanes without a pair), then
+//                         fn.batch_end(face or -1, slot); a batch's pairs of one candidate sit on
+//                         consecutive lanes, which read its staged values as broadcasts;
+//   runs (RUNS true)      lane l takes the pairs [l K, (l + 1) K), K = ceil(pairs / 32):
+//                         fn.pair_run(face, p, samples, slot) for each, then fn.flush(); a lane's
+//                         pairs mostly share a candidate, so its sums stay in registers.
+// slot = the candidate's row in the chunk.  allowed[i] = pixels taking part for sample i;
+// any_samples = OR of their samples.
+template <int SPT, bool MOVING, bool STAGE, bool RUNS, int ROWS, typename Fn>
 __device__ __forceinline__ void for_pairs(const TriRec* recs_set, const int32_t* list, int beg, int end,
                                           const Group* grp, int n, const TileBox& tb, const BlockPix& bp, float m,
                                           const uint32_t (&allowed)[SPT], uint32_t any_samples,
@@ -517,20 +521,49 @@ __device__ __forceinline__ void for_pairs(const TriRec* recs_set, const int32_t*
     fn.chunk_begin();
     if (STAGE && pm) fn.stage(recs_set + f, sm);
     __syncwarp();
-    for (int b = 0; b < total; b += 32) {
-      const int k = b + lane;
-      int face = -1, p = 0, jj = 0;  // jj: last candidate whose first pair is at or before k
-      uint32_t smp = 0;
-      if (k < total) {
+    if constexpr (RUNS) {
+      const int K = (total + 31) >> 5;
+      const int k0 = lane * K, k1 = min(k0 + K, total);
+      if (k0 < k1) {
+        // the run's first pair: the last candidate whose first pair is at or before k0 (it has
+        // pairs, since the next prefix is above k0), and its pixels from the (k0 - prefix)-th on
+        int jj = 0;
 #pragma unroll
         for (int step = 16; step > 0; step >>= 1)
-          if (ws.prefix[jj + step] <= k) jj += step;
-        p = nth_set_bit(ws.pmask[jj], k - ws.prefix[jj]);
-        face = ws.face[jj];
-        smp = ws.smask[jj] & ws.pixs[p];
+          if (ws.prefix[jj + step] <= k0) jj += step;
+        uint32_t rem = ws.pmask[jj];
+        rem &= kFullMask << nth_set_bit(rem, k0 - ws.prefix[jj]);
+        for (int k = k0; k < k1; ++k) {
+          if (!rem) {  // the next candidate with pairs
+            do {
+              ++jj;
+            } while (ws.pmask[jj] == 0u);
+            rem = ws.pmask[jj];
+          }
+          const int p = __ffs(rem) - 1;
+          rem &= rem - 1u;
+          const uint32_t smp = ws.smask[jj] & ws.pixs[p];
+          if (smp) fn.pair_run(ws.face[jj], p, smp, jj);
+        }
+        fn.flush();
       }
-      fn.pair(smp != 0u, face, p, smp, jj);
-      fn.batch_end(face, jj);
+      __syncwarp();  // the runs' sums are in the chunk's rows
+    } else {
+      for (int b = 0; b < total; b += 32) {
+        const int k = b + lane;
+        int face = -1, p = 0, jj = 0;  // jj: last candidate whose first pair is at or before k
+        uint32_t smp = 0;
+        if (k < total) {
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1)
+            if (ws.prefix[jj + step] <= k) jj += step;
+          p = nth_set_bit(ws.pmask[jj], k - ws.prefix[jj]);
+          face = ws.face[jj];
+          smp = ws.smask[jj] & ws.pixs[p];
+        }
+        fn.pair(smp != 0u, face, p, smp, jj);
+        fn.batch_end(face, jj);
+      }
     }
     fn.chunk_end(f, pm != 0u);
   }
