@@ -153,6 +153,9 @@ __device__ __forceinline__ void soft_grad_fast(const float4 (&k)[6], const SoftE
   }
 }
 
+// pairs per lane slot of the fast solver's batches
+constexpr int kPairsPerLane = 2;
+
 // pass 3 of the adjoint: gradient of alpha = 1 - prod_j (1 - A_j) w.r.t. the vertex positions of
 // every soft candidate, summed per candidate into its row of the chunk in shared memory; each row
 // is added to the slot gradients once, when its chunk is done.
@@ -227,12 +230,12 @@ struct BwdSoftGradPairs {
     else excl = (nz == 1 && f <= kTinyFactor) ? __expf(S) : 0.f;
     return ga * excl * dA;
   }
-  // batches: this lane's pair only
-  __device__ __forceinline__ void pair(bool ok, int face, int p, uint32_t smp, int slot) {
+  // batches: the sums start from zero in every batch and take the lane's pairs
+  __device__ __forceinline__ void clear() {
 #pragma unroll
     for (int q = 0; q < 3; ++q) gax[q] = gay[q] = gbx[q] = gby[q] = 0.f;
-    if (ok) accumulate(p, smp, slot);
   }
+  __device__ __forceinline__ void pair(int face, int p, uint32_t smp, int slot) { accumulate(p, smp, slot); }
   // runs: the sums carry over while the candidate stays the same
   __device__ __forceinline__ void pair_run(int face, int p, uint32_t smp, int slot) {
     if (slot != cur) {
@@ -789,7 +792,8 @@ __device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile
       p3.faces = P.faces;
       p3.gslot_a = P.g_slot + (size_t)gq.slot_a * P.V * 2;
       p3.gslot_b = P.g_slot + (size_t)gq.slot_b * P.V * 2;
-      for_pairs<SPT, MOVING, true, !MOVING>(recs_set, P.soft.faces, sb, se, grp, n, B.tb, B.bp, m, allowed, any_s, ws, p3);
+      for_pairs<SPT, MOVING, true, !MOVING, kPairsPerLane>(recs_set, P.soft.faces, sb, se, grp, n, B.tb, B.bp, m, allowed,
+                                                          any_s, ws, p3);
     }
     __syncwarp();  // the scratch is rewritten by the next group
   }

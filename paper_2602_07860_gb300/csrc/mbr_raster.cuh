@@ -472,16 +472,18 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int r) {
 // pairs need of a candidate, read from shared memory instead of global memory); then the pairs;
 // finally fn.chunk_end(face, has pairs) on lane j for candidate j.  The pairs go to the lanes in
 // one of two ways:
-//   batches (RUNS false)  pair k of batch b to lane k - 32 b: fn.pair(ok, face, p, samples, slot)
-//                         on every lane (ok false on lanes without a pair), then
-//                         fn.batch_end(face or -1, slot); a batch's pairs of one candidate sit on
-//                         consecutive lanes, which read its staged values as broadcasts;
+//   batches (RUNS false)  a candidate's pairs are cut into lane slots of K consecutive pairs
+//                         (the last one may be short), and slot k of batch b goes to lane k - 32 b:
+//                         fn.clear() on every lane, fn.pair(face, p, samples, slot) for each of
+//                         the lane's pairs, then fn.batch_end(face or -1, slot); a batch's lanes
+//                         of one candidate are consecutive and read its staged values as
+//                         broadcasts, and each lane's K pairs share one place in the warp sum;
 //   runs (RUNS true)      lane l takes the pairs [l K, (l + 1) K), K = ceil(pairs / 32):
 //                         fn.pair_run(face, p, samples, slot) for each, then fn.flush(); a lane's
 //                         pairs mostly share a candidate, so its sums stay in registers.
 // slot = the candidate's row in the chunk.  allowed[i] = pixels taking part for sample i;
 // any_samples = OR of their samples.
-template <int SPT, bool MOVING, bool STAGE, bool RUNS, int ROWS, typename Fn>
+template <int SPT, bool MOVING, bool STAGE, bool RUNS, int K, int ROWS, typename Fn>
 __device__ __forceinline__ void for_pairs(const TriRec* recs_set, const int32_t* list, int beg, int end,
                                           const Group* grp, int n, const TileBox& tb, const BlockPix& bp, float m,
                                           const uint32_t (&allowed)[SPT], uint32_t any_samples,
@@ -504,7 +506,7 @@ __device__ __forceinline__ void for_pairs(const TriRec* recs_set, const int32_t*
         pm = box_pixel_mask(box, bp) & al;
       }
     }
-    int incl = __popc(pm);
+    int incl = RUNS ? __popc(pm) : (__popc(pm) + K - 1) / K;  // pairs (runs) or lane slots (batches)
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(kFullMask, incl, o);
@@ -551,17 +553,24 @@ __device__ __forceinline__ void for_pairs(const TriRec* recs_set, const int32_t*
     } else {
       for (int b = 0; b < total; b += 32) {
         const int k = b + lane;
-        int face = -1, p = 0, jj = 0;  // jj: last candidate whose first pair is at or before k
-        uint32_t smp = 0;
+        int face = -1, jj = 0;  // jj: last candidate whose first lane slot is at or before k
+        uint32_t rem = 0u;      // the slot's pixels: the candidate's from its K (k - prefix)-th on
         if (k < total) {
 #pragma unroll
           for (int step = 16; step > 0; step >>= 1)
             if (ws.prefix[jj + step] <= k) jj += step;
-          p = nth_set_bit(ws.pmask[jj], k - ws.prefix[jj]);
+          rem = ws.pmask[jj];
+          rem &= kFullMask << nth_set_bit(rem, K * (k - ws.prefix[jj]));
           face = ws.face[jj];
-          smp = ws.smask[jj] & ws.pixs[p];
         }
-        fn.pair(smp != 0u, face, p, smp, jj);
+        fn.clear();
+#pragma unroll 1
+        for (int t = 0; t < K && rem; ++t) {
+          const int p = __ffs(rem) - 1;
+          rem &= rem - 1u;
+          const uint32_t smp = ws.smask[jj] & ws.pixs[p];
+          if (smp) fn.pair(face, p, smp, jj);
+        }
         fn.batch_end(face, jj);
       }
     }
