@@ -736,13 +736,15 @@ __device__ __forceinline__ void raster_bwd_block(const RasterParams& P, int tile
         win[i] = -1;
         if (i < n && B.in_img) {
           const size_t o = (size_t)(gq.k0 + i) * plane + pix;
+          // both words at once (the value's meaning follows from the status)
           const uint8_t st = __ldg(P.s_stat + o);
+          const float sv = __ldg(P.s_val + o);
           if (st == kStatCovered) {
-            win[i] = __float_as_int(__ldg(P.s_val + o));
+            win[i] = __float_as_int(sv);
           } else if (alpha) {
             my_s |= 1u << i;
             ws.nzero[i][lane] = st;
-            ws.logp[i][lane] = __ldg(P.s_val + o);
+            ws.logp[i][lane] = sv;
           }
         }
       }
