@@ -48,7 +48,17 @@ def ref_window(steps):
 # compiled when captured: the entry is attached to the bench line only if the current kernel
 # sources hash to CAPTURED["sources"] and the run uses the captured tile / samples-per-group;
 # otherwise the line carries null.
-CAPTURED = {"sources": None, "tile": None, "spt": None, "kernels": {}}
+CAPTURED = {
+    "sources": "f1f22904d217f9d7", "tile": 8, "spt": 2,
+    "kernels": {
+        # profiles/raster_bwd_persistent_c2_fast.md
+        "raster_bwd_persistent": {"dram_bytes": 33810688 + 806400,
+                                  "pipes_pct": {"fma": 30.6, "alu": 33.8, "xu": 6.4, "lsu": 22.9, "issue_active": 59.5}},
+        # profiles/raster_fwd_persistent_c2_fast.md
+        "raster_fwd_persistent": {"dram_bytes": 17362432 + 243712,
+                                  "pipes_pct": {"fma": 32.2, "alu": 44.0, "xu": 10.0, "lsu": 28.3, "issue_active": 72.8}},
+    },
+}
 
 
 def kernel_sources_sha():
