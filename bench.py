@@ -373,6 +373,28 @@ def extra_workloads(mbr, scenes, torch, np, world):
                              ctx5.render_blur_backward(vv, ff, aa, mo, ca, T, H, W, G5, solver, reuse_forward=True)), 2)
         c5[solver] = {"fwdbwd_ms": ms, "samples_per_s": world * H * W * T / (ms / 1e3)}
     out["c5_large"] = c5
+    # the adjoint's per-sample state, kept (5 bytes per sample, written by the forward) or
+    # recomputed by the adjoint (mbr_set_state_budget 0), on c2 and c5; by default c2 keeps it and
+    # c5 (1.34 GB of state, above the 1 GiB default budget) recomputes it
+    modes = {}
+    s2m = scenes.config2()
+    v2m, f2m, a2m = mbr.mesh_tensors(s2m)
+    cases = (("c2", (v2m, f2m, a2m, mbr.motion_from_dict(s2m["motion"]), mbr.camera_from_dict(s2m["camera"]),
+                     s2m["T"], s2m["H"], s2m["W"]), 10),
+             ("c5", (vv, ff, aa, mo, ca, T, H, W), 2))
+    for label, (mv, mf, ma, mmo, mca, mT, mH, mW), reps in cases:
+        mG = torch.ones((mH, mW, 4), device=dev)
+        row = {"state_bytes_if_kept": mT * mH * mW * 5}
+        for mode, budget in (("kept", 1 << 34), ("recomputed", 0)):
+            cx = mbr.Context()
+            cx.set_state_budget(budget)
+            ms = timeit(lambda: (cx.render_blur(mv, mf, ma, mmo, mca, mT, mH, mW, "fast"),
+                                 cx.render_blur_backward(mv, mf, ma, mmo, mca, mT, mH, mW, mG, "fast",
+                                                         reuse_forward=True)), reps)
+            row[mode] = {"fwdbwd_ms": ms, "samples_per_s": world * mT * mH * mW / (ms / 1e3)}
+            cx.close()
+        modes[label] = row
+    out["adjoint_state_modes"] = modes
     # segmentation analysis on the benchmark workload: linear segments of the fast solver vs the
     # exact per-sub-frame render (plain): time and image error
     import dataclasses
