@@ -435,15 +435,33 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
   if ((rc = ensure(c, c->nrm, sizeof(float4) * (size_t)pp.n_slots * V, st))) return rc;
   if ((rc = ensure(c, c->recs, sizeof(TriRec) * (size_t)pp.n_sets * std::max(F, 1), st))) return rc;
   int* d_status = (int*)c->status.p;  // [0] this call, [1] raster launches (sticky until read)
-  CUDA_TRY(c, cudaMemsetAsync(d_status, 0, sizeof(int32_t), st));
-  CUDA_TRY(c, cudaMemsetAsync(c->nacc.p, 0, sizeof(float) * 3 * V, st));
+  // one launch clears this call's status word, the normal accumulators and both bin count arrays
+  ZeroList zl{};
+  zl.p[0] = d_status;
+  zl.n[0] = 1;
+  zl.p[1] = (int32_t*)c->nacc.p;
+  zl.n[1] = (size_t)3 * V;
+  const int tw = c->tile, th = c->tile;
+  long long nb = 0;
+  if (do_bins) {
+    pp.tiles_x = (W + tw - 1) / tw;
+    pp.tiles_y = (H + th - 1) / th;
+    pp.n_tiles = pp.tiles_x * pp.tiles_y;
+    nb = (long long)pp.G * pp.n_tiles;
+    if (nb > (1LL << 30)) return fail(c, MBR_ERR_ARG, "too many (group, tile) bins: %lld", nb);
+    // both count arrays in one buffer; after the scan they are the fill cursors
+    if ((rc = ensure(c, c->bin_counts, sizeof(int32_t) * 2 * (size_t)nb, st))) return rc;
+    zl.p[2] = (int32_t*)c->bin_counts.p;
+    zl.n[2] = 2 * (size_t)nb;
+  }
+  launch_zero(zl, st);
   launch_face_normals(mesh->verts, mesh->faces, F, V, (float*)c->nacc.p, d_status, st);
   launch_xform(mesh->verts, (const float*)c->nacc.p, V, pp.d_xf, pp.n_slots, cam->tan_half_fov,
                (float4*)c->pos.p, (float4*)c->nrm.p, st);
   launch_setup((const float4*)c->pos.p, mesh->faces, F, V, d_sets, pp.n_sets, cam->znear, (TriRec*)c->recs.p, st);
   CUDA_TRY(c, cudaGetLastError());
   pp.r = (float)std::sqrt((double)cam->delta * (double)kSoftCutoff);
-  c->stats.launches += (F > 0 ? 1 : 0) + 1 + (F > 0 ? 1 : 0);
+  c->stats.launches += 1 + (F > 0 ? 1 : 0) + 1 + (F > 0 ? 1 : 0);  // clear, normals, transform, setup
   c->stats.groups = pp.G;
   if (!do_bins) {
     CUDA_TRY(c, cudaMemcpyAsync(c->host_total, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -452,18 +470,10 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
     return MBR_OK;
   }
 
-  // a3 binning: core and soft bins: count -> scan (both) -> one sync for the totals -> fill
-  const int tw = c->tile, th = c->tile;
-  pp.tiles_x = (W + tw - 1) / tw;
-  pp.tiles_y = (H + th - 1) / th;
-  pp.n_tiles = pp.tiles_x * pp.tiles_y;
-  const long long nb = (long long)pp.G * pp.n_tiles;
-  if (nb > (1LL << 30)) return fail(c, MBR_ERR_ARG, "too many (group, tile) bins: %lld", nb);
+  // a3 binning: core and soft bins: count -> scan (both) -> one sync for the totals -> fill (the
+  // count arrays were cleared above)
   BinSet* sets2[2] = {&c->core, &c->soft};
   const float r_core = kCoreMargin, r_soft = pp.r + kCoreMargin;
-  // both count arrays in one buffer (one clear); after the scan they are the fill cursors
-  if ((rc = ensure(c, c->bin_counts, sizeof(int32_t) * 2 * (size_t)nb, st))) return rc;
-  CUDA_TRY(c, cudaMemsetAsync(c->bin_counts.p, 0, sizeof(int32_t) * 2 * (size_t)nb, st));
   BinTargets bt{};
   ScanPair sp{};
   for (int q = 0; q < 2; ++q) {
@@ -479,7 +489,7 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
   sp.n = (int)nb;
   launch_bin(false, (const TriRec*)c->recs.p, F, pp.d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles, r_core,
              r_soft, bt, d_status, st);
-  launch_scan_pair(sp, st);
+  const int scan_launches = launch_scan_pair(sp, st);
   CUDA_TRY(c, cudaGetLastError());
   // one read-back: [0] this call's status, [1] raster launches' status, [2], [3] list totals
   CUDA_TRY(c, cudaMemcpyAsync(c->host_total, d_status, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, st));
@@ -501,7 +511,7 @@ int prepare(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const mb
   launch_bin(true, (const TriRec*)c->recs.p, F, pp.d_groups, pp.G, W, H, tw, th, pp.tiles_x, pp.n_tiles, r_core,
              r_soft, bt, d_status, st);
   CUDA_TRY(c, cudaGetLastError());
-  c->stats.launches += (F > 0 ? 2 : 0) + 3;
+  c->stats.launches += (F > 0 ? 2 : 0) + scan_launches;
   c->stats.bin_entries = totals[0] + totals[1];
   pp.core_cap = (int)totals[0];
   pp.soft_cap = (int)totals[1];
@@ -764,15 +774,23 @@ int backward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, co
   if ((rc = ensure(c, c->gslot, gbytes, st))) return rc;
   if ((rc = ensure(c, c->gm, sizeof(float) * 3 * V, st))) return rc;
   if ((rc = ensure(c, c->galb, sizeof(float4) * V, st))) return rc;
-  CUDA_TRY(c, cudaMemsetAsync(c->gslot.p, 0, gbytes, st));
-  if (dl_dalbedo) CUDA_TRY(c, cudaMemsetAsync(c->galb.p, 0, sizeof(float4) * V, st));
+  // one launch clears the slot gradients and the albedo and texture gradients the raster adds to
+  ZeroList zl{};
+  zl.p[0] = (int32_t*)c->gslot.p;
+  zl.n[0] = gbytes / 4;
+  if (dl_dalbedo) {
+    zl.p[1] = (int32_t*)c->galb.p;
+    zl.n[1] = (size_t)4 * V;
+  }
   P.dl_dimage = (const float4*)dl_dimage;
   P.g_slot = (float4*)c->gslot.p;
   P.g_albedo = dl_dalbedo ? (float4*)c->galb.p : nullptr;
   if (mesh->texture && mesh->dl_dtexture) {
-    CUDA_TRY(c, cudaMemsetAsync(mesh->dl_dtexture, 0, sizeof(float) * 3 * (size_t)mesh->tex_h * mesh->tex_w, st));
+    zl.p[2] = (int32_t*)mesh->dl_dtexture;
+    zl.n[2] = (size_t)3 * mesh->tex_h * mesh->tex_w;
     P.g_tex = mesh->dl_dtexture;
   }
+  launch_zero(zl, st);
   // the forward raster's per-sample state (if it kept it; else the adjoint recomputes it), and the
   // units in the order of its measured cost
   if (pp.stored) {
@@ -791,7 +809,7 @@ int backward_impl(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, co
   CUDA_TRY(c, cudaGetLastError());
   if ((rc = time_end(c, 1, st))) return rc;
   if ((rc = check_waits_now(c, Q.status, st))) return rc;
-  c->stats.launches += 3 + 1 + 1 + (mesh->F > 0 ? 1 : 0);  // order, raster, slot chain, normals
+  c->stats.launches += 1 + 3 + 1 + 1 + (mesh->F > 0 ? 1 : 0);  // clear, order, raster, slot chain, normals
   c->stats.n_split = pp.n_split;
   launch_slot_chain(mesh->verts, (const float*)c->nacc.p, V, pp.d_xf, pp.n_slots, cam->tan_half_fov,
                     (const float4*)c->gslot.p, (const float4*)c->galb.p, dl_dverts, (float*)c->gm.p, dl_dalbedo, st);
@@ -903,7 +921,7 @@ int mbr_sdf_extract(mbr_ctx* c, int32_t n, const float* sdf, const float lo[3], 
   }
   sp.total = d_tot;
   sp.n = (int)n_edges;
-  launch_scan_pair(sp, st);
+  const int scan_launches = launch_scan_pair(sp, st);
   CUDA_TRY(c, cudaGetLastError());
   CUDA_TRY(c, cudaMemcpyAsync(c->host_total, d_tot, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(c, cudaStreamSynchronize(st));
@@ -914,7 +932,7 @@ int mbr_sdf_extract(mbr_ctx* c, int32_t n, const float* sdf, const float lo[3], 
                 counts[1], max_verts, max_faces);
   launch_sdf_write(n, sdf, lo, h, off, off + n_edges + 1, verts, vert_edges, faces, st);
   CUDA_TRY(c, cudaGetLastError());
-  c->stats.launches += 6;
+  c->stats.launches += 3 + scan_launches;
   return MBR_OK;
 }
 

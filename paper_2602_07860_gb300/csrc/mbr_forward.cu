@@ -12,6 +12,7 @@
 //   unit_*_kernel        visiting order of the raster's work units (largest estimate first)
 //   raster_fwd_count     work counters of the raster passes (measurement)
 //   count_kernel         N_cand (measurement)
+#include <algorithm>
 #include <cstdint>
 
 #include "mbr_internal.h"
@@ -260,6 +261,25 @@ __global__ void bin_smem_kernel(const TriRec* __restrict__ recs, int F, const Gr
           if (slot < t.off[q][(size_t)g * n_tiles + b + 1] && slot < t.cap[q]) t.list[q][slot] = f;
           else atomicOr(status, kStatusBinOverflow);
         }
+}
+
+// ---------------------------------------------------------------- clearing
+__global__ void zero_kernel(ZeroList z) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (z.p[k])
+      for (size_t i = t0; i < z.n[k]; i += stride) z.p[k][i] = 0;
+}
+
+void launch_zero(const ZeroList& z, cudaStream_t st) {
+  size_t most = 0;
+  for (int k = 0; k < 4; ++k)
+    if (z.p[k]) most = std::max(most, z.n[k]);
+  if (!most) return;
+  const int grid = (int)std::min<size_t>((most + 255) / 256, 1024);
+  zero_kernel<<<grid, 256, 0, st>>>(z);
 }
 
 // ---------------------------------------------------------------- exclusive scan (CSR offsets)
@@ -719,12 +739,13 @@ void launch_bin(bool fill, const TriRec* recs, int F, const Group* groups, int G
 
 size_t scan_temp_ints(int n) { return (size_t)(n + kScanBlock - 1) / kScanBlock + 1; }
 
-void launch_scan_pair(const ScanPair& sp, cudaStream_t st) {
+int launch_scan_pair(const ScanPair& sp, cudaStream_t st) {
   const int nb = (sp.n + kScanBlock - 1) / kScanBlock;
-  if (nb == 0) return;  // callers only scan non-empty bin arrays
+  if (nb == 0) return 0;  // callers only scan non-empty bin arrays
   scan_reduce_kernel<<<dim3(nb, 2), kScanThreads, 0, st>>>(sp);
   scan_sums_kernel<<<dim3(1, 2), kScanThreads, 0, st>>>(sp, nb);
   scan_apply_kernel<<<dim3(nb, 2), kScanThreads, 0, st>>>(sp);
+  return 3;
 }
 
 template <int TW, int TH, int KIND, bool EXT>

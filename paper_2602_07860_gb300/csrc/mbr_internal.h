@@ -37,7 +37,13 @@ struct ScanPair {
   int n;
 };
 size_t scan_temp_ints(int n);
-void launch_scan_pair(const ScanPair& sp, cudaStream_t st);
+// zero up to four buffers of 32-bit words in one launch (null entries are skipped)
+struct ZeroList {
+  int32_t* p[4];
+  size_t n[4];
+};
+void launch_zero(const ZeroList& z, cudaStream_t st);
+int launch_scan_pair(const ScanPair& sp, cudaStream_t st);  // returns the kernels launched
 // persistent raster launches; kind 0 plain only, 1 fast only, 2 mixed, plus kKindExt for the
 // kernels with the variants (texture colours, perspective-correct weights, sigmoid probability)
 constexpr int kKindMask = 3, kKindExt = 4;

@@ -478,7 +478,7 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int r) {
 //                         the lane's pairs, then fn.batch_end(face or -1, slot); a batch's lanes
 //                         of one candidate are consecutive and read its staged values as
 //                         broadcasts, and each lane's K pairs share one place in the warp sum;
-//   runs (RUNS true)      lane l takes the pairs [l K, (l + 1) K), K = ceil(pairs / 32):
+//   runs (RUNS true)      lane l takes the pairs [l n, (l + 1) n), n = ceil(pairs / 32):
 //                         fn.pair_run(face, p, samples, slot) for each, then fn.flush(); a lane's
 //                         pairs mostly share a candidate, so its sums stay in registers.
 // slot = the candidate's row in the chunk.  allowed[i] = pixels taking part for sample i;
@@ -524,8 +524,8 @@ __device__ __forceinline__ void for_pairs(const TriRec* recs_set, const int32_t*
     if (STAGE && pm) fn.stage(recs_set + f, sm);
     __syncwarp();
     if constexpr (RUNS) {
-      const int K = (total + 31) >> 5;
-      const int k0 = lane * K, k1 = min(k0 + K, total);
+      const int run = (total + 31) >> 5;
+      const int k0 = lane * run, k1 = min(k0 + run, total);
       if (k0 < k1) {
         // the run's first pair: the last candidate whose first pair is at or before k0 (it has
         // pairs, since the next prefix is above k0), and its pixels from the (k0 - prefix)-th on
