@@ -238,9 +238,6 @@ int validate(mbr_ctx* c, const mbr_mesh* mesh, const mbr_motion* motion, const m
   return MBR_OK;
 }
 
-// kernels launched by the front half: normals, transform, setup (+ bins: count, 3 scan, fill)
-constexpr int kFrontLaunches = 3, kBinLaunches = 5;
-
 // add the duration of a recorded event pair to the sums (waits for its end event)
 int harvest(mbr_ctx* c, int kind) {
   if (!c->pending[kind]) return MBR_OK;
