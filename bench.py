@@ -49,14 +49,14 @@ def ref_window(steps):
 # sources hash to CAPTURED["sources"] and the run uses the captured tile / samples-per-group;
 # otherwise the line carries null.
 CAPTURED = {
-    "sources": "f1f22904d217f9d7", "tile": 8, "spt": 2,
+    "sources": "df90c844e7d43555", "tile": 8, "spt": 2,
     "kernels": {
         # profiles/raster_bwd_persistent_c2_fast.md
-        "raster_bwd_persistent": {"dram_bytes": 33810688 + 806400,
-                                  "pipes_pct": {"fma": 30.6, "alu": 33.8, "xu": 6.4, "lsu": 22.9, "issue_active": 59.5}},
+        "raster_bwd_persistent": {"dram_bytes": 33804288 + 762624,
+                                  "pipes_pct": {"fma": 30.7, "alu": 33.9, "xu": 6.4, "lsu": 23.0, "issue_active": 59.7}},
         # profiles/raster_fwd_persistent_c2_fast.md
-        "raster_fwd_persistent": {"dram_bytes": 17362432 + 243712,
-                                  "pipes_pct": {"fma": 32.2, "alu": 44.0, "xu": 10.0, "lsu": 28.3, "issue_active": 72.8}},
+        "raster_fwd_persistent": {"dram_bytes": 17357568 + 233216,
+                                  "pipes_pct": {"fma": 32.3, "alu": 44.1, "xu": 10.0, "lsu": 28.4, "issue_active": 72.9}},
     },
 }
 
@@ -329,6 +329,11 @@ def extra_workloads(mbr, scenes, torch, np, world):
         if it in marks:
             track[it] = (float(img_loss), float((v - tgt_v).norm(dim=1).mean()))
 
+    # untimed warm-up: the loop's one-time costs (the batch plans and graph captures, and PyTorch's
+    # first use of the optimiser's and the loss terms' kernels, which a fresh process may have to
+    # compile for this GPU) stay out of the per-iteration time
+    recover_shape(tv, tf, ta, views, targets, s0["T"], s0["H"], s0["W"], iters=2, lr=1e-3, lap_weight=0.1,
+                  solver="fast")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     v_final, hist = recover_shape(tv, tf, ta, views, targets, s0["T"], s0["H"], s0["W"], iters=iters, lr=1e-3,
