@@ -400,6 +400,26 @@ def extra_workloads(mbr, scenes, torch, np, world):
             cx.close()
         modes[label] = row
     out["adjoint_state_modes"] = modes
+    # translation (one linear segment) at growing T: the plain solver places vertices, builds
+    # records and bins per sub-frame, the fast solver per keyframe (2 slots); fwd+bwd ms per solver
+    tsweep = {}
+    for Tn in (64, 256, 1024):
+        st_ = scenes.config2_translate(T=Tn)
+        tv_, tf_, ta_ = mbr.mesh_tensors(st_)
+        tmo, tca = mbr.motion_from_dict(st_["motion"]), mbr.camera_from_dict(st_["camera"])
+        tG = torch.ones((st_["H"], st_["W"], 4), device=dev)
+        row = {}
+        for solver in ("fast", "plain"):
+            cx = mbr.Context()
+            cx.set_tuning(8, 2 if solver == "fast" else 1, 0)
+            ms = timeit(lambda: (cx.render_blur(tv_, tf_, ta_, tmo, tca, Tn, st_["H"], st_["W"], solver),
+                                 cx.render_blur_backward(tv_, tf_, ta_, tmo, tca, Tn, st_["H"], st_["W"], tG, solver,
+                                                         reuse_forward=True)), 5)
+            row[solver] = {"fwdbwd_ms": ms, "samples_per_s": world * Tn * st_["H"] * st_["W"] / (ms / 1e3)}
+            cx.close()
+        row["speedup_fast_over_plain_fwdbwd"] = row["plain"]["fwdbwd_ms"] / row["fast"]["fwdbwd_ms"]
+        tsweep[str(Tn)] = row
+    out["translate_T_sweep"] = tsweep
     # segmentation analysis on the benchmark workload: linear segments of the fast solver vs the
     # exact per-sub-frame render (plain): time and image error
     import dataclasses
