@@ -92,6 +92,24 @@ def test_state_free_adjoint_matches_oracle(ctx_free, name, solver):
     _grad_check(ctx_free, GRAD_SCENES[name](), solver)
 
 
+@pytest.mark.parametrize("tile,spt", [(16, 4), (8, 4), (8, 1), (16, 1), (8, 2)])
+@pytest.mark.parametrize("state_free", [False, True])
+def test_adjoint_tuning_variants(tile, spt, state_free):
+    """The fast solver's adjoint at every tile size and samples-per-group choice the autotuner can
+    make: one sample per group, two (per-sample coefficients staged per candidate) and four (the
+    staged record, coefficients formed per pair), with stored and with recomputed state."""
+    import paper_2602_07860_gb300 as mbr
+    c = mbr.Context()
+    c.set_tuning(tile, spt, 0)
+    if state_free:
+        c.set_state_budget(0)
+    try:
+        _grad_check(c, scenes.small_scene("rotate", subdiv=2, T=20, H=45, W=61), "fast")
+        _grad_check(c, scenes.small_scene("translate", subdiv=2, T=16, H=40, W=48, d=(0.9, -0.3, 1.1)), "fast")
+    finally:
+        c.close()
+
+
 @pytest.mark.parametrize("solver", ["plain", "fast"])
 def test_state_free_adjoint_at_T256(ctx_free, solver):
     """T = 256 sub-frames (the large workload's count) with no stored sample state."""
